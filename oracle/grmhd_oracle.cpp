@@ -1,0 +1,1291 @@
+// FP64 CPU oracle for the Valencia GRMHD meshblock stage (arXiv:2409.10384).
+//
+// TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, scalar statement of
+// what the GPU path must compute.  Only the test suite, the smoke check and the
+// CPU-baseline leg of the benchmark may load it.  It shares no code, header or
+// constant table with the CUDA library, and it includes nothing from it.
+//
+// Build: g++ -std=c++17 -O2 -ffp-contract=off -fopenmp -shared -fPIC
+//   (-ffp-contract=off: every a*b+c is two rounded operations, as written).
+// With -DORACLE_COUNT_FLOPS the scalar type becomes a counting wrapper and the
+// same source reports the algorithmic FP64 operation count of a stage.
+//
+// Notation follows the paper: D, S_i, tau conserved (Eq. 6), densitised
+// A~ = sqrt(gamma) A (Sec. 2), v^i Eulerian three-velocity, W Lorentz factor,
+// w^i = W v^i the reconstructed velocity primitive (Sec. 3.2), alpha lapse,
+// beta^i shift, gamma_ij spatial metric (Eq. 5), K_ij extrinsic curvature.
+//
+// Readings where the paper is silent (all also listed in the design notes):
+//  * con2prim follows Kastaun, Kalinani & Ciolfi 2021 (cited in Sec. 3.4):
+//    master function f(mu), bracket [0, mu+] from the auxiliary function
+//    f_a(mu), Illinois regula falsi with a bisection safeguard, stopping on the
+//    bracket width, then one regula-falsi step on the final bracket.
+//  * PLM uses the harmonic-mean van Leer slope; WENO-Z uses Jiang-Shu
+//    smoothness indicators, linear weights (1,6,3)/10, tau5=|b0-b2|, p=1,
+//    eps=1e-40.
+//  * The ADM metric is interpolated to faces with the centred 4-point
+//    Lagrange weights (-1,9,9,-1)/16.
+//  * Wave speeds: fast magnetosonic speed in the Valencia eigenvalue formula.
+//  * Upwind CT: Gardiner & Stone 2005 edge EMF, upwinded by the sign of the
+//    face mass flux, average on ties.
+//  * Metric derivatives in the source terms: second-order centred differences.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <cstdlib>
+#include <vector>
+
+#ifdef ORACLE_COUNT_FLOPS
+struct FlopCounts { long long add, mul, div, sqrt, cmp; };
+static FlopCounts g_fc = {0, 0, 0, 0, 0};
+struct real {
+  double v;
+  real() : v(0.0) {}
+  real(double x) : v(x) {}
+};
+static inline real operator+(real a, real b) { g_fc.add++; return real(a.v + b.v); }
+static inline real operator-(real a, real b) { g_fc.add++; return real(a.v - b.v); }
+static inline real operator*(real a, real b) { g_fc.mul++; return real(a.v * b.v); }
+static inline real operator/(real a, real b) { g_fc.div++; return real(a.v / b.v); }
+static inline real operator-(real a) { return real(-a.v); }
+static inline real& operator+=(real& a, real b) { a = a + b; return a; }
+static inline real& operator-=(real& a, real b) { a = a - b; return a; }
+static inline real& operator*=(real& a, real b) { a = a * b; return a; }
+static inline bool operator<(real a, real b) { g_fc.cmp++; return a.v < b.v; }
+static inline bool operator>(real a, real b) { g_fc.cmp++; return a.v > b.v; }
+static inline bool operator<=(real a, real b) { g_fc.cmp++; return a.v <= b.v; }
+static inline bool operator>=(real a, real b) { g_fc.cmp++; return a.v >= b.v; }
+static inline bool operator==(real a, real b) { g_fc.cmp++; return a.v == b.v; }
+static inline real sqrt_(real a) { g_fc.sqrt++; return real(std::sqrt(a.v)); }
+static inline double val(real a) { return a.v; }
+static inline bool finite_(real a) { return std::isfinite(a.v); }
+#else
+typedef double real;
+static inline real sqrt_(real a) { return std::sqrt(a); }
+static inline double val(real a) { return a; }
+static inline bool finite_(real a) { return std::isfinite(a); }
+#endif
+
+static inline real abs_(real a) { return a < 0.0 ? -a : a; }
+static inline real max_(real a, real b) { return a < b ? b : a; }
+static inline real min_(real a, real b) { return b < a ? b : a; }
+
+extern "C" {
+
+// Parameters (mirrors the library's mhd_params field meaning, declared anew).
+typedef struct {
+  double gamma;      // ideal-gas adiabatic index (Sec. 3.4)
+  double rho_atm;    // atmosphere density (Sec. 3.3)
+  double T_atm;      // atmosphere temperature, T = P/rho (Sec. 3.3)
+  double f_thr;      // density floor threshold factor (Sec. 3.3)
+  double sigma_max;  // cap on B^2/D; <= 0 disables (Sec. 3.3)
+  double dmp_M;      // relaxed DMP factor M >= 1; <= 0 disables (Eq. 19)
+  double c2p_tol;    // relative bracket width for the root solve
+  double W_max;      // Lorentz-factor cap of the root solve
+  int recon;         // 0 donor cell, 1 PLM, 2 WENO-Z (Sec. 3.2)
+  int rsolver;       // 0 LLF, 1 HLLE (Sec. 3.2)
+  int fofc;          // first-order flux correction on/off (Sec. 3.3)
+  int rk_order;      // 2 or 3 (SSP RK, Sec. 3.2)
+  int c2p_maxit;     // iteration cap of the root solve
+  int pad_;
+} or_params;
+
+typedef struct {
+  int n[3];          // interior cells in x, y, z
+  int ng;            // ghost cells per side (>= 4)
+  double dx[3];      // cell widths
+  double* cons;      // [5][N3][N2][N1]  D~, S~_1..3, tau~
+  double* cons0;     // [5][...] U^n of the RK step (written at stage 1)
+  double* prim;      // [5][...] rho, w^1..3, P
+  double* bf[3];     // face B~: x [N3][N2][N1+1], y [N3][N2+1][N1], z [N3+1][N2][N1]
+  double* bf0[3];    // face B~ at t^n (written at stage 1)
+  double* bcc;       // [3][...] cell-centred B~ (face average)
+  const double* adm; // [16][...] alpha, beta^1..3, g_11,g_12,g_13,g_22,g_23,g_33, K_11..K_33
+  unsigned char* flags;  // [N3][N2][N1] con2prim / FOFC bits
+  double* flux[3];   // optional out: [7][face array of that direction]
+  double* emf[3];    // optional out: E_x [N3+1][N2+1][N1], E_y [N3+1][N2][N1+1], E_z [N3][N2+1][N1+1]
+  const unsigned char* fofc_mask;  // optional in: replaces the computed FOFC flags
+} or_block;
+
+typedef struct {
+  long long cells;       // con2prim calls on the stage input
+  long long iters;       // summed root-solve iterations
+  long long fails;       // failures (no bracket, cap, non-finite)
+  long long floors;      // cells where any floor fired
+  long long fofc_cells;  // cells flagged by FOFC (incl. DMP)
+  long long dmp_cells;   // cells flagged by the DMP test alone
+  long long fofc_faces;  // faces recomputed first order
+} or_stats;
+
+}  // extern "C"
+
+// Flag bits written per cell.
+enum {
+  F_FAIL = 1,     // root solve failed
+  F_DFLOOR = 2,   // D < f_thr rho_atm before the solve (atmosphere reset)
+  F_SIGMA = 4,    // B^2/D cap
+  F_TAU = 8,      // tau < tau_atm(D,B)
+  F_RHO = 16,     // rho < f_thr rho_atm after the solve
+  F_TEMP = 32,    // T floor (epsilon clamp at the root, or T < T_atm)
+  F_VMAX = 64,    // velocity cap active at the root
+  F_FOFC = 128    // FOFC flagged this cell in the current stage
+};
+static const int FLOOR_BITS = F_DFLOOR | F_SIGMA | F_TAU | F_RHO | F_TEMP | F_VMAX;
+
+// ---------------------------------------------------------------------------
+// Layout helpers.
+struct Grid {
+  int n1, n2, n3, ng, N1, N2, N3;
+  long ncell;
+  Grid(const or_block* b) {
+    n1 = b->n[0]; n2 = b->n[1]; n3 = b->n[2]; ng = b->ng;
+    N1 = n1 + 2 * ng; N2 = n2 + 2 * ng; N3 = n3 + 2 * ng;
+    ncell = (long)N1 * N2 * N3;
+  }
+  long c(int k, int j, int i) const { return ((long)k * N2 + j) * N1 + i; }
+  // face array of direction d, index (k,j,i) = face on the low side of cell (k,j,i)
+  long f(int d, int k, int j, int i) const {
+    if (d == 0) return ((long)k * N2 + j) * (N1 + 1) + i;
+    if (d == 1) return ((long)k * (N2 + 1) + j) * N1 + i;
+    return ((long)k * N2 + j) * N1 + i;
+  }
+  long nface(int d) const {
+    if (d == 0) return (long)N3 * N2 * (N1 + 1);
+    if (d == 1) return (long)N3 * (N2 + 1) * N1;
+    return (long)(N3 + 1) * N2 * N1;
+  }
+  // edge array of component c: E_x (k,j,i) at (i, j-1/2, k-1/2); E_y at (i-1/2, j, k-1/2);
+  // E_z at (i-1/2, j-1/2, k).
+  long e(int cc, int k, int j, int i) const {
+    if (cc == 0) return ((long)k * (N2 + 1) + j) * N1 + i;
+    if (cc == 1) return ((long)k * N2 + j) * (N1 + 1) + i;
+    return ((long)k * (N2 + 1) + j) * (N1 + 1) + i;
+  }
+  long nedge(int cc) const {
+    if (cc == 0) return (long)(N3 + 1) * (N2 + 1) * N1;
+    if (cc == 1) return (long)(N3 + 1) * N2 * (N1 + 1);
+    return (long)N3 * (N2 + 1) * (N1 + 1);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Metric helpers (Eq. 5).  g[6] = gamma_11, _12, _13, _22, _23, _33.
+static real metric_det(const real g[6]) {
+  return g[0] * (g[3] * g[5] - g[4] * g[4]) - g[1] * (g[1] * g[5] - g[4] * g[2]) +
+         g[2] * (g[1] * g[4] - g[3] * g[2]);
+}
+static void metric_inverse(const real g[6], real det, real gi[6]) {
+  gi[0] = (g[3] * g[5] - g[4] * g[4]) / det;
+  gi[1] = (g[2] * g[4] - g[1] * g[5]) / det;
+  gi[2] = (g[1] * g[4] - g[2] * g[3]) / det;
+  gi[3] = (g[0] * g[5] - g[2] * g[2]) / det;
+  gi[4] = (g[1] * g[2] - g[0] * g[4]) / det;
+  gi[5] = (g[0] * g[3] - g[1] * g[1]) / det;
+}
+// lower (or raise, with the inverse) a vector: out_i = g_ij in^j
+static void metric_apply(const real g[6], const real in[3], real out[3]) {
+  out[0] = g[0] * in[0] + g[1] * in[1] + g[2] * in[2];
+  out[1] = g[1] * in[0] + g[3] * in[1] + g[4] * in[2];
+  out[2] = g[2] * in[0] + g[4] * in[1] + g[5] * in[2];
+}
+static real dot3(const real a[3], const real b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+// component (a,b) of a symmetric 3x3 stored as 6
+static inline int sym(int a, int b) {
+  static const int t[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+  return t[a][b];
+}
+
+// ---------------------------------------------------------------------------
+// prim -> cons, Eq. 6 with the densitisation of Sec. 2.
+// prim = rho, w^1..3, P; Bd = densitised B~^i; out = D~, S~_i, tau~.
+static void prim_to_cons(const or_params& p, const real prim[5], const real Bd[3], const real g[6],
+                         real out[5]) {
+  real sdet = sqrt_(metric_det(g));
+  real B[3] = {Bd[0] / sdet, Bd[1] / sdet, Bd[2] / sdet};
+  real w[3] = {prim[1], prim[2], prim[3]};
+  real wl[3];
+  metric_apply(g, w, wl);
+  real W = sqrt_(1.0 + dot3(w, wl));
+  real v[3] = {w[0] / W, w[1] / W, w[2] / W};
+  real vl[3] = {wl[0] / W, wl[1] / W, wl[2] / W};
+  real Bl[3];
+  metric_apply(g, B, Bl);
+  real B2 = dot3(B, Bl);
+  real Bv = dot3(B, vl);
+  real rho = prim[0], P = prim[4];
+  real h = 1.0 + p.gamma / (p.gamma - 1.0) * P / rho;  // h = 1 + eps + P/rho, eps = P/((G-1) rho)
+  real rhohW2 = rho * h * W * W;
+  real D = rho * W;
+  out[0] = sdet * D;
+  for (int i = 0; i < 3; i++) out[1 + i] = sdet * ((rhohW2 + B2) * vl[i] - Bv * Bl[i]);
+  out[4] = sdet * (rhohW2 + B2 - P - 0.5 * (Bv * Bv + B2 / (W * W)) - D);
+  (void)v;
+}
+
+// ---------------------------------------------------------------------------
+// con2prim (Sec. 3.4; Kastaun, Kalinani & Ciolfi 2021).
+struct KRP {
+  // undensitised, per unit D: q = tau/D, r_i = S_i/D, bb^i = B^i/sqrt(D)
+  real q, r2, b2, rb, rb2, rperp2;
+  real D;
+  real gam, eps_min, vmax2;
+};
+struct KRPEval {
+  real x, rbar2, qbar, vhat2, What, rhohat, eps_raw, eps, Phat, f;
+  bool vcap;
+};
+// master function f(mu) = mu - muhat(mu)
+static void krp_eval(const KRP& s, real mu, KRPEval& e) {
+  e.x = 1.0 / (1.0 + mu * s.b2);
+  e.rbar2 = s.r2 * e.x * e.x + mu * e.x * (1.0 + e.x) * s.rb2;
+  e.qbar = s.q - 0.5 * s.b2 - 0.5 * mu * mu * e.x * e.x * s.rperp2;
+  real v2 = mu * mu * e.rbar2;
+  e.vcap = v2 > s.vmax2;
+  e.vhat2 = e.vcap ? s.vmax2 : v2;
+  e.What = 1.0 / sqrt_(1.0 - e.vhat2);
+  e.rhohat = s.D / e.What;
+  e.eps_raw = e.What * (e.qbar - mu * e.rbar2) + e.vhat2 * e.What * e.What / (1.0 + e.What);
+  e.eps = e.eps_raw < s.eps_min ? s.eps_min : e.eps_raw;
+  e.Phat = (s.gam - 1.0) * e.rhohat * e.eps;
+  real ahat = e.Phat / (e.rhohat * (1.0 + e.eps));
+  real nuA = (1.0 + ahat) * (1.0 + e.eps) / e.What;
+  real nuB = (1.0 + ahat) * (1.0 + e.qbar - mu * e.rbar2);
+  real nu = max_(nuA, nuB);
+  real muhat = 1.0 / (nu + mu * e.rbar2);
+  e.f = mu - muhat;
+}
+// upper end of the bracket: the root of f_a(mu) = mu sqrt(h0^2 + rbar^2(mu)) - 1,
+// approached from above by three steps of mu <- 1/sqrt(h0^2 + rbar^2(mu)) started
+// at 1/sqrt(h0^2 + r_par^2) (rbar^2 decreases from r^2 to r_par^2).  h0 = 1.
+static real krp_mu_plus(const KRP& s) {
+  real rpar2 = s.b2 > 0.0 ? s.rb2 / s.b2 : s.r2;
+  real mu = 1.0 / sqrt_(1.0 + rpar2);
+  for (int it = 0; it < 3; it++) {
+    real x = 1.0 / (1.0 + mu * s.b2);
+    real rbar2 = s.r2 * x * x + mu * x * (1.0 + x) * s.rb2;
+    mu = 1.0 / sqrt_(1.0 + rbar2);
+  }
+  return mu;
+}
+
+struct C2POut {
+  real prim[5];
+  int flags;
+  int iters;
+  real mu;
+  real eps_margin;   // eps_raw/eps_min - 1 at the root (sign decides the T floor)
+};
+
+// Bracketed Illinois solve on [a,b] with f(a) < 0 <= f(b); returns the root.
+// On return *ok = false when the iteration cap is reached.
+static real illinois(const KRP& s, real a, real fa, real b, real fb, double tol, int maxit, int* iters,
+                     bool* ok) {
+  *ok = true;
+  *iters = 0;
+  if (fb == 0.0) return b;
+  real Fa = fa, Fb = fb;
+  int side = 0;
+  KRPEval e;
+  while (b - a > tol * b) {
+    if (*iters >= maxit) { *ok = false; break; }
+    (*iters)++;
+    real c = (a * Fb - b * Fa) / (Fb - Fa);
+    if (!(c > a && c < b)) c = 0.5 * (a + b);
+    krp_eval(s, c, e);
+    if (e.f < 0.0) {
+      a = c; fa = e.f; Fa = e.f;
+      if (side == -1) Fb = 0.5 * Fb;
+      side = -1;
+    } else if (e.f > 0.0) {
+      b = c; fb = e.f; Fb = e.f;
+      if (side == 1) Fa = 0.5 * Fa;
+      side = 1;
+    } else {
+      return c;
+    }
+  }
+  // one regula-falsi step on the final bracket with the true end values
+  return a - fa * (b - a) / (fb - fa);
+}
+
+// One cell.  cons (densitised) may be modified by the floors when write_back.
+// Bd = cell-centred densitised B~, g = gamma_ij.  mu_lo/mu_hi: optional bracket
+// guess (both < 0 to use the plain bracket).
+static void c2p_cell(const or_params& p, real cons[5], const real Bd[3], const real g[6], bool write_back,
+                     C2POut& o) {
+  o.flags = 0;
+  o.iters = 0;
+  o.mu = 0.0;
+  o.eps_margin = 0.0;
+  const real gam = p.gamma;
+  real det = metric_det(g);
+  real sdet = sqrt_(det);
+  real gi[6];
+  metric_inverse(g, det, gi);
+  real D = cons[0] / sdet;
+  real Sl[3] = {cons[1] / sdet, cons[2] / sdet, cons[3] / sdet};
+  real tau = cons[4] / sdet;
+  real B[3] = {Bd[0] / sdet, Bd[1] / sdet, Bd[2] / sdet};
+  real Bl[3];
+  metric_apply(g, B, Bl);
+  real B2 = dot3(B, Bl);
+  bool finite = finite_(D) && finite_(tau) && finite_(Sl[0]) && finite_(Sl[1]) && finite_(Sl[2]) &&
+                finite_(B2) && det > 0.0;
+  const real rho_atm = p.rho_atm, T_atm = p.T_atm;
+  const real eps_atm = T_atm / (gam - 1.0);
+  bool floored = false;
+  real rho = rho_atm, P = rho_atm * T_atm, w[3] = {0.0, 0.0, 0.0};
+  if (!finite) {
+    o.flags |= F_FAIL;
+  } else {
+    // floors on the conserved state before the solve (Sec. 3.3)
+    if (D < p.f_thr * rho_atm) {
+      D = rho_atm;
+      Sl[0] = Sl[1] = Sl[2] = 0.0;
+      tau = D * eps_atm + 0.5 * B2;
+      o.flags |= F_DFLOOR;
+    }
+    if (p.sigma_max > 0.0 && B2 > p.sigma_max * D) {
+      D = B2 / p.sigma_max;
+      o.flags |= F_SIGMA;
+    }
+    real tau_atm = D * eps_atm + 0.5 * B2;
+    if (tau < tau_atm) {
+      tau = tau_atm;
+      o.flags |= F_TAU;
+    }
+    KRP s;
+    s.D = D;
+    s.gam = gam;
+    s.eps_min = eps_atm;
+    s.vmax2 = 1.0 - 1.0 / (p.W_max * p.W_max);
+    s.q = tau / D;
+    real rl[3] = {Sl[0] / D, Sl[1] / D, Sl[2] / D};
+    real ru[3];
+    metric_apply(gi, rl, ru);
+    real sD = sqrt_(D);
+    real bu[3] = {B[0] / sD, B[1] / sD, B[2] / sD};
+    s.r2 = dot3(rl, ru);
+    s.b2 = B2 / D;
+    s.rb = dot3(rl, bu);
+    s.rb2 = s.rb * s.rb;
+    s.rperp2 = s.r2 * s.b2 - s.rb2;
+    if (s.rperp2 < 0.0) s.rperp2 = 0.0;
+    // bracket [0, mu+]; if f(mu+) < 0 the root lies in [mu+, 1/h0] = [mu+, 1]
+    KRPEval e0, e1;
+    real a = 0.0, b = krp_mu_plus(s);
+    krp_eval(s, a, e0);
+    krp_eval(s, b, e1);
+    if (e1.f < 0.0) {
+      a = b; e0 = e1;
+      b = 1.0;
+      krp_eval(s, b, e1);
+    }
+    bool ok = e0.f < 0.0 && e1.f >= 0.0;
+    real mu = 0.0;
+    if (ok) mu = illinois(s, a, e0.f, b, e1.f, p.c2p_tol, p.c2p_maxit, &o.iters, &ok);
+    if (!ok || !finite_(mu)) {
+      o.flags |= F_FAIL;
+    } else {
+      KRPEval e;
+      krp_eval(s, mu, e);
+      o.mu = mu;
+      o.eps_margin = e.eps_raw / s.eps_min - 1.0;
+      if (e.eps_raw < s.eps_min) o.flags |= F_TEMP;
+      if (e.vcap) o.flags |= F_VMAX;
+      rho = e.rhohat;
+      P = e.Phat;
+      // v^i = mu x (r^i + mu (r.bb) bb^i), w^i = W v^i; under the speed cap the
+      // velocity is rescaled to |v|^2 = vmax^2 so that it matches W
+      real vs = 1.0;
+      if (e.vcap) vs = sqrt_(s.vmax2 / (mu * mu * e.rbar2));
+      for (int i = 0; i < 3; i++) w[i] = e.What * vs * mu * e.x * (ru[i] + mu * s.rb * bu[i]);
+      // floors on the primitives after the solve (Sec. 3.3)
+      if (rho < p.f_thr * rho_atm) {
+        rho = rho_atm;
+        P = rho_atm * T_atm;
+        w[0] = w[1] = w[2] = 0.0;
+        o.flags |= F_RHO;
+      } else if (P < rho * T_atm) {
+        P = rho * T_atm;
+        o.flags |= F_TEMP;
+      }
+    }
+  }
+  if (o.flags & F_FAIL) {
+    // error policy: reset the cell to the static atmosphere
+    rho = rho_atm;
+    P = rho_atm * T_atm;
+    w[0] = w[1] = w[2] = 0.0;
+  }
+  floored = (o.flags & (FLOOR_BITS | F_FAIL)) != 0;
+  o.prim[0] = rho;
+  o.prim[1] = w[0];
+  o.prim[2] = w[1];
+  o.prim[3] = w[2];
+  o.prim[4] = P;
+  if (write_back && floored) prim_to_cons(p, o.prim, Bd, g, cons);
+}
+
+// ---------------------------------------------------------------------------
+// Reconstruction (Sec. 3.2).
+// PLM van Leer slope of the middle value
+static real vl_slope(real qm, real q0, real qp) {
+  real dl = q0 - qm, dr = qp - q0;
+  real pr = dl * dr;
+  return pr > 0.0 ? 2.0 * pr / (dl + dr) : real(0.0);
+}
+// WENO-Z value at the face between c and d of the stencil (a, b, c, d, e) centred on c.
+static real wenoz(real a, real b, real c, real d, real e) {
+  real q0 = (2.0 * a - 7.0 * b + 11.0 * c) / 6.0;
+  real q1 = (-b + 5.0 * c + 2.0 * d) / 6.0;
+  real q2 = (2.0 * c + 5.0 * d - e) / 6.0;
+  real t;
+  t = a - 2.0 * b + c;
+  real u = a - 4.0 * b + 3.0 * c;
+  real b0 = 13.0 / 12.0 * t * t + 0.25 * u * u;
+  t = b - 2.0 * c + d;
+  u = b - d;
+  real b1 = 13.0 / 12.0 * t * t + 0.25 * u * u;
+  t = c - 2.0 * d + e;
+  u = 3.0 * c - 4.0 * d + e;
+  real b2 = 13.0 / 12.0 * t * t + 0.25 * u * u;
+  const real epsw = 1e-40;
+  real tau5 = abs_(b0 - b2);
+  real a0 = 0.1 * (1.0 + tau5 / (b0 + epsw));
+  real a1 = 0.6 * (1.0 + tau5 / (b1 + epsw));
+  real a2 = 0.3 * (1.0 + tau5 / (b2 + epsw));
+  real s = a0 + a1 + a2;
+  return (a0 * q0 + a1 * q1 + a2 * q2) / s;
+}
+// left/right states at the face between stencil entries q[2] (cell -1) and q[3]
+// (cell 0), from q[0..5] = cells -3..+2 along the face normal.
+static void reconstruct(int recon, const real q[6], real* L, real* R) {
+  if (recon == 0) {
+    *L = q[2];
+    *R = q[3];
+  } else if (recon == 1) {
+    *L = q[2] + 0.5 * vl_slope(q[1], q[2], q[3]);
+    *R = q[3] - 0.5 * vl_slope(q[2], q[3], q[4]);
+  } else {
+    *L = wenoz(q[0], q[1], q[2], q[3], q[4]);
+    *R = wenoz(q[5], q[4], q[3], q[2], q[1]);
+  }
+}
+// floor on a reconstructed state (Sec. 3.3): s = rho, w^1..3, P
+static void face_floor(const or_params& p, real s[5]) {
+  if (s[0] < p.f_thr * p.rho_atm) {
+    s[0] = p.rho_atm;
+    s[1] = s[2] = s[3] = 0.0;
+    s[4] = p.rho_atm * p.T_atm;
+  } else if (s[4] < s[0] * p.T_atm) {
+    s[4] = s[0] * p.T_atm;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Physical flux and wave speeds on one side of a face (Eq. 8).
+// st = rho, w^1..3, P, B~^{t1}, B~^{t2}; Bn = B~^d from the face array;
+// m = alpha, beta^1..3, gamma_ij at the face.  Flux/state components:
+// D~, S~_1..3, tau~, B~^{t1}, B~^{t2} with t1 = (d+1)%3, t2 = (d+2)%3.
+struct Side {
+  real U[7], F[7], lm, lp;
+};
+static void face_side(const or_params& p, int d, const real st[7], real Bn, const real m[10], Side& o) {
+  const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  real alpha = m[0];
+  real beta[3] = {m[1], m[2], m[3]};
+  real g[6] = {m[4], m[5], m[6], m[7], m[8], m[9]};
+  real det = metric_det(g);
+  real sdet = sqrt_(det);
+  real gi[6];
+  metric_inverse(g, det, gi);
+  real Bt[3];
+  Bt[d] = Bn;
+  Bt[t1] = st[5];
+  Bt[t2] = st[6];
+  real B[3] = {Bt[0] / sdet, Bt[1] / sdet, Bt[2] / sdet};
+  real rho = st[0], P = st[4];
+  real w[3] = {st[1], st[2], st[3]};
+  real wl[3];
+  metric_apply(g, w, wl);
+  real W = sqrt_(1.0 + dot3(w, wl));
+  real v[3] = {w[0] / W, w[1] / W, w[2] / W};
+  real vl[3] = {wl[0] / W, wl[1] / W, wl[2] / W};
+  real Bl[3];
+  metric_apply(g, B, Bl);
+  real B2 = dot3(B, Bl);
+  real Bv = dot3(B, vl);
+  real v2 = dot3(v, vl);
+  real b2 = B2 / (W * W) + Bv * Bv;
+  real gam = p.gamma;
+  real h = 1.0 + gam / (gam - 1.0) * P / rho;
+  real rhohW2 = rho * h * W * W;
+  real D = rho * W;
+  real S[3];
+  for (int i = 0; i < 3; i++) S[i] = (rhohW2 + B2) * vl[i] - Bv * Bl[i];
+  real tau = rhohW2 + B2 - P - 0.5 * (Bv * Bv + B2 / (W * W)) - D;
+  real vh[3];
+  for (int i = 0; i < 3; i++) vh[i] = v[i] - beta[i] / alpha;
+  real Ptot = P + 0.5 * b2;
+  // b_i = B_i/W + W (B.v) v_i  (covariant spatial part of b^mu)
+  real bl[3];
+  for (int i = 0; i < 3; i++) bl[i] = Bl[i] / W + W * Bv * vl[i];
+  o.U[0] = sdet * D;
+  for (int i = 0; i < 3; i++) o.U[1 + i] = sdet * S[i];
+  o.U[4] = sdet * tau;
+  o.U[5] = Bt[t1];
+  o.U[6] = Bt[t2];
+  o.F[0] = alpha * o.U[0] * vh[d];
+  for (int i = 0; i < 3; i++) {
+    o.F[1 + i] = alpha * o.U[1 + i] * vh[d] - alpha * bl[i] * Bt[d] / W;
+    if (i == d) o.F[1 + i] += alpha * sdet * Ptot;
+  }
+  o.F[4] = alpha * o.U[4] * vh[d] - alpha * Bv * Bt[d] + alpha * sdet * Ptot * v[d];
+  o.F[5] = alpha * (Bt[t1] * vh[d] - Bt[d] * vh[t1]);
+  o.F[6] = alpha * (Bt[t2] * vh[d] - Bt[d] * vh[t2]);
+  // fast magnetosonic speed and the characteristic speeds along d
+  real cs2 = gam * P / (rho * h);
+  real va2 = b2 / (rho * h + b2);
+  real cf2 = cs2 + va2 - cs2 * va2;
+  real cf = sqrt_(cf2);
+  real vd = v[d];
+  real disc = (1.0 - v2) * (gi[sym(d, d)] * (1.0 - v2 * cf2) - vd * vd * (1.0 - cf2));
+  if (disc < 0.0) disc = 0.0;
+  real sq = sqrt_(disc);
+  real den = 1.0 - v2 * cf2;
+  o.lm = alpha * (vd * (1.0 - cf2) - cf * sq) / den - beta[d];
+  o.lp = alpha * (vd * (1.0 - cf2) + cf * sq) / den - beta[d];
+}
+
+// Riemann flux (Sec. 3.2): HLLE or LLF.
+static void riemann(int rsolver, const Side& L, const Side& R, real F[7]) {
+  if (rsolver == 1) {
+    real lL = min_(min_(L.lm, R.lm), real(0.0));
+    real lR = max_(max_(L.lp, R.lp), real(0.0));
+    if (lR == lL) {
+      for (int c = 0; c < 7; c++) F[c] = 0.5 * (L.F[c] + R.F[c]);
+    } else {
+      for (int c = 0; c < 7; c++)
+        F[c] = (lR * L.F[c] - lL * R.F[c] + lL * lR * (R.U[c] - L.U[c])) / (lR - lL);
+    }
+  } else {
+    real a = max_(max_(abs_(L.lm), abs_(L.lp)), max_(abs_(R.lm), abs_(R.lp)));
+    for (int c = 0; c < 7; c++) F[c] = 0.5 * (L.F[c] + R.F[c]) - 0.5 * a * (R.U[c] - L.U[c]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Block-level pieces.
+struct Ctx {
+  const or_params& p;
+  or_block* b;
+  Grid G;
+  int is[3], ie[3];
+  Ctx(const or_params& pp, or_block* bb) : p(pp), b(bb), G(bb) {
+    for (int d = 0; d < 3; d++) {
+      is[d] = b->ng;
+      ie[d] = b->ng + b->n[d] - 1;
+    }
+  }
+  double adm(int v, int k, int j, int i) const { return b->adm[(long)v * G.ncell + G.c(k, j, i)]; }
+};
+
+// cell-centred B~ from the face array (average of the two faces), all cells
+static void compute_bcc(Ctx& C) {
+  Grid& G = C.G;
+  for (int k = 0; k < G.N3; k++)
+    for (int j = 0; j < G.N2; j++)
+      for (int i = 0; i < G.N1; i++) {
+        long c = G.c(k, j, i);
+        C.b->bcc[0 * G.ncell + c] = val(0.5 * (real(C.b->bf[0][G.f(0, k, j, i)]) + real(C.b->bf[0][G.f(0, k, j, i + 1)])));
+        C.b->bcc[1 * G.ncell + c] = val(0.5 * (real(C.b->bf[1][G.f(1, k, j, i)]) + real(C.b->bf[1][G.f(1, k, j + 1, i)])));
+        C.b->bcc[2 * G.ncell + c] = val(0.5 * (real(C.b->bf[2][G.f(2, k, j, i)]) + real(C.b->bf[2][G.f(2, k + 1, j, i)])));
+      }
+}
+
+static void load_metric_cell(const Ctx& C, int k, int j, int i, real g[6]) {
+  for (int m = 0; m < 6; m++) g[m] = C.adm(4 + m, k, j, i);
+}
+
+// con2prim over the interior plus three ghost layers; floors write back.
+static void c2p_region(Ctx& C, or_stats* st) {
+  Grid& G = C.G;
+  const int h = 3;
+  long long iters = 0, fails = 0, floors = 0, cells = 0;
+#ifndef ORACLE_COUNT_FLOPS
+#pragma omp parallel for collapse(2) reduction(+ : iters, fails, floors, cells) schedule(static)
+#endif
+  for (int k = C.is[2] - h; k <= C.ie[2] + h; k++)
+    for (int j = C.is[1] - h; j <= C.ie[1] + h; j++)
+      for (int i = C.is[0] - h; i <= C.ie[0] + h; i++) {
+        long c = G.c(k, j, i);
+        real U[5], Bd[3], g[6];
+        for (int v = 0; v < 5; v++) U[v] = C.b->cons[v * G.ncell + c];
+        for (int v = 0; v < 3; v++) Bd[v] = C.b->bcc[v * G.ncell + c];
+        load_metric_cell(C, k, j, i, g);
+        C2POut o;
+        c2p_cell(C.p, U, Bd, g, true, o);
+        for (int v = 0; v < 5; v++) C.b->cons[v * G.ncell + c] = val(U[v]);
+        for (int v = 0; v < 5; v++) C.b->prim[v * G.ncell + c] = val(o.prim[v]);
+        C.b->flags[c] = (unsigned char)o.flags;
+        cells++;
+        iters += o.iters;
+        if (o.flags & F_FAIL) fails++;
+        if (o.flags & FLOOR_BITS) floors++;
+      }
+  if (st) {
+    st->cells += cells;
+    st->iters += iters;
+    st->fails += fails;
+    st->floors += floors;
+  }
+}
+
+// flux on one face of direction d at face index (k,j,i); donor forces first order
+static void face_flux(const Ctx& C, int d, int k, int j, int i, bool donor, real F[7]) {
+  const Grid& G = C.G;
+  const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  int off[3] = {0, 0, 0};
+  off[d] = 1;
+  // gather stencil of the 7 reconstructed variables along d: cells -3..+2
+  real L[7], R[7];
+  for (int v = 0; v < 7; v++) {
+    real q[6];
+    for (int m = -3; m <= 2; m++) {
+      int kk = k + m * off[2], jj = j + m * off[1], ii = i + m * off[0];
+      long c = G.c(kk, jj, ii);
+      if (v < 5)
+        q[m + 3] = C.b->prim[(long)v * G.ncell + c];
+      else
+        q[m + 3] = C.b->bcc[(long)(v == 5 ? t1 : t2) * G.ncell + c];
+    }
+    reconstruct(donor ? 0 : C.p.recon, q, &L[v], &R[v]);
+  }
+  face_floor(C.p, L);
+  face_floor(C.p, R);
+  // metric at the face: 4-point Lagrange interpolation along d
+  real m[10];
+  for (int v = 0; v < 10; v++) {
+    real a = C.adm(v, k - 2 * off[2], j - 2 * off[1], i - 2 * off[0]);
+    real bq = C.adm(v, k - off[2], j - off[1], i - off[0]);
+    real cq = C.adm(v, k, j, i);
+    real dq = C.adm(v, k + off[2], j + off[1], i + off[0]);
+    m[v] = (-a + 9.0 * bq + 9.0 * cq - dq) / 16.0;
+  }
+  real Bn = C.b->bf[d][G.f(d, k, j, i)];
+  Side sl, sr;
+  face_side(C.p, d, L, Bn, m, sl);
+  face_side(C.p, d, R, Bn, m, sr);
+  riemann(C.p.rsolver, sl, sr, F);
+}
+
+// the range of faces of direction d that a stage computes
+static void face_range(const Ctx& C, int d, int lo[3], int hi[3]) {
+  for (int a = 0; a < 3; a++) {
+    lo[a] = C.is[a] - 1;
+    hi[a] = C.ie[a] + 1;
+  }
+  lo[d] = C.is[d];
+  hi[d] = C.ie[d] + 1;
+}
+
+static void compute_fluxes(Ctx& C, std::vector<double> flux[3]) {
+  Grid& G = C.G;
+  for (int d = 0; d < 3; d++) {
+    flux[d].assign(7 * G.nface(d), 0.0);
+    int lo[3], hi[3];
+    face_range(C, d, lo, hi);
+#ifndef ORACLE_COUNT_FLOPS
+#pragma omp parallel for collapse(2) schedule(static)
+#endif
+    for (int k = lo[2]; k <= hi[2]; k++)
+      for (int j = lo[1]; j <= hi[1]; j++)
+        for (int i = lo[0]; i <= hi[0]; i++) {
+          real F[7];
+          face_flux(C, d, k, j, i, false, F);
+          long f = G.f(d, k, j, i);
+          for (int c = 0; c < 7; c++) flux[d][c * G.nface(d) + f] = val(F[c]);
+        }
+  }
+}
+
+static const double RK2_W[2][3] = {{0.0, 1.0, 1.0}, {0.5, 0.5, 0.5}};
+static const double RK3_W[3][3] = {{0.0, 1.0, 1.0}, {0.75, 0.25, 0.25}, {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0}};
+
+static bool is_interior(const Ctx& C, int k, int j, int i) {
+  return i >= C.is[0] && i <= C.ie[0] && j >= C.is[1] && j <= C.ie[1] && k >= C.is[2] && k <= C.ie[2];
+}
+
+// flux divergence -sum_d (F(+) - F(-))/dx_d of component v at cell (k,j,i)
+static real flux_div(const Ctx& C, std::vector<double> flux[3], int v, int k, int j, int i) {
+  const Grid& G = C.G;
+  real r = 0.0;
+  int off[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  for (int d = 0; d < 3; d++) {
+    long n = G.nface(d);
+    real fm = flux[d][v * n + G.f(d, k, j, i)];
+    real fp = flux[d][v * n + G.f(d, k + off[d][2], j + off[d][1], i + off[d][0])];
+    r = r - (fp - fm) / C.b->dx[d];
+  }
+  return r;
+}
+
+// FOFC (Sec. 3.3) with the optional relaxed DMP (Eq. 19).
+static void fofc(Ctx& C, std::vector<double> flux[3], double g0, double g1, double bdt, or_stats* st) {
+  Grid& G = C.G;
+  std::vector<unsigned char> flag(G.ncell, 0);
+  long long nf = 0, nd = 0;
+#ifndef ORACLE_COUNT_FLOPS
+#pragma omp parallel for collapse(2) reduction(+ : nf, nd) schedule(static)
+#endif
+  for (int k = C.is[2]; k <= C.ie[2]; k++)
+    for (int j = C.is[1]; j <= C.ie[1]; j++)
+      for (int i = C.is[0]; i <= C.ie[0]; i++) {
+        long c = G.c(k, j, i);
+        real Us[5];
+        for (int v = 0; v < 5; v++) {
+          real u = g1 * real(C.b->cons[v * G.ncell + c]);
+          if (g0 != 0.0) u = real(g0) * real(C.b->cons0[v * G.ncell + c]) + u;
+          Us[v] = u + bdt * flux_div(C, flux, v, k, j, i);
+        }
+        bool fl;
+        if (C.b->fofc_mask) {
+          fl = C.b->fofc_mask[c] != 0;
+        } else {
+          real Bd[3], g[6];
+          for (int v = 0; v < 3; v++) Bd[v] = C.b->bcc[v * G.ncell + c];
+          load_metric_cell(C, k, j, i, g);
+          real Uc[5] = {Us[0], Us[1], Us[2], Us[3], Us[4]};
+          C2POut o;
+          c2p_cell(C.p, Uc, Bd, g, false, o);
+          fl = (o.flags & (F_FAIL | FLOOR_BITS)) != 0;
+          if (!fl && C.p.dmp_M > 0.0) {
+            const real M = C.p.dmp_M;
+            const int vv[2] = {0, 4};
+            for (int t = 0; t < 2; t++) {
+              int v = vv[t];
+              real mn = C.b->cons[v * G.ncell + c], mx = mn;
+              for (int dk = -1; dk <= 1; dk++)
+                for (int dj = -1; dj <= 1; dj++)
+                  for (int di = -1; di <= 1; di++) {
+                    real u = C.b->cons[v * G.ncell + G.c(k + dk, j + dj, i + di)];
+                    mn = min_(mn, u);
+                    mx = max_(mx, u);
+                  }
+              real lo = mn > 0.0 ? mn / M : mn * M;
+              real hi = mx > 0.0 ? mx * M : mx / M;
+              if (Us[v] < lo || Us[v] > hi) fl = true;
+            }
+            if (fl) nd++;
+          }
+        }
+        if (fl) {
+          flag[c] = 1;
+          nf++;
+        }
+      }
+  long long nfaces = 0;
+  for (int d = 0; d < 3; d++) {
+    int lo[3], hi[3];
+    face_range(C, d, lo, hi);
+    int off[3] = {0, 0, 0};
+    off[d] = 1;
+    long n = G.nface(d);
+#ifndef ORACLE_COUNT_FLOPS
+#pragma omp parallel for collapse(2) reduction(+ : nfaces) schedule(static)
+#endif
+    for (int k = lo[2]; k <= hi[2]; k++)
+      for (int j = lo[1]; j <= hi[1]; j++)
+        for (int i = lo[0]; i <= hi[0]; i++) {
+          int km = k - off[2], jm = j - off[1], im = i - off[0];
+          bool a = is_interior(C, km, jm, im) && flag[G.c(km, jm, im)];
+          bool bb = is_interior(C, k, j, i) && flag[G.c(k, j, i)];
+          if (!(a || bb)) continue;
+          real F[7];
+          face_flux(C, d, k, j, i, true, F);
+          long f = G.f(d, k, j, i);
+          for (int c = 0; c < 7; c++) flux[d][c * n + f] = val(F[c]);
+          nfaces++;
+        }
+  }
+  for (int k = C.is[2]; k <= C.ie[2]; k++)
+    for (int j = C.is[1]; j <= C.ie[1]; j++)
+      for (int i = C.is[0]; i <= C.ie[0]; i++) {
+        long c = G.c(k, j, i);
+        if (flag[c]) C.b->flags[c] |= F_FOFC;
+        else C.b->flags[c] &= (unsigned char)~F_FOFC;
+      }
+  if (st) {
+    st->fofc_cells += nf;
+    st->dmp_cells += nd;
+    st->fofc_faces += nfaces;
+  }
+}
+
+// cell-centred E = -alpha (vhat x B~) on the interior plus one layer
+static void compute_ecc(Ctx& C, std::vector<double>& ecc) {
+  Grid& G = C.G;
+  ecc.assign(3 * G.ncell, 0.0);
+  for (int k = C.is[2] - 1; k <= C.ie[2] + 1; k++)
+    for (int j = C.is[1] - 1; j <= C.ie[1] + 1; j++)
+      for (int i = C.is[0] - 1; i <= C.ie[0] + 1; i++) {
+        long c = G.c(k, j, i);
+        real g[6];
+        load_metric_cell(C, k, j, i, g);
+        real alpha = C.adm(0, k, j, i);
+        real beta[3] = {C.adm(1, k, j, i), C.adm(2, k, j, i), C.adm(3, k, j, i)};
+        real w[3] = {C.b->prim[1 * G.ncell + c], C.b->prim[2 * G.ncell + c], C.b->prim[3 * G.ncell + c]};
+        real wl[3];
+        metric_apply(g, w, wl);
+        real W = sqrt_(1.0 + dot3(w, wl));
+        real vh[3];
+        for (int a = 0; a < 3; a++) vh[a] = w[a] / W - beta[a] / alpha;
+        real B[3] = {C.b->bcc[0 * G.ncell + c], C.b->bcc[1 * G.ncell + c], C.b->bcc[2 * G.ncell + c]};
+        ecc[0 * G.ncell + c] = val(-alpha * (vh[1] * B[2] - vh[2] * B[1]));
+        ecc[1 * G.ncell + c] = val(-alpha * (vh[2] * B[0] - vh[0] * B[2]));
+        ecc[2 * G.ncell + c] = val(-alpha * (vh[0] * B[1] - vh[1] * B[0]));
+      }
+}
+
+static real upwind(real fD, real lowv, real highv) {
+  if (fD > 0.0) return lowv;
+  if (fD < 0.0) return highv;
+  return 0.5 * (lowv + highv);
+}
+
+// Upwind constrained transport (Sec. 3.2; Gardiner & Stone 2005): edge EMF of
+// component cc at the edge (A-1/2, B-1/2, C) in the plane of axes a=(cc+1)%3,
+// b=(cc+2)%3.  On a-faces E_cc = -F_a[t1 comp], on b-faces E_cc = +F_b[t2 comp].
+static void compute_emf(Ctx& C, std::vector<double> flux[3], std::vector<double>& ecc, std::vector<double> emf[3]) {
+  Grid& G = C.G;
+  for (int cc = 0; cc < 3; cc++) {
+    emf[cc].assign(G.nedge(cc), 0.0);
+    const int a = (cc + 1) % 3, bax = (cc + 2) % 3;
+    int lo[3], hi[3];
+    for (int x = 0; x < 3; x++) {
+      lo[x] = C.is[x];
+      hi[x] = C.ie[x] + 1;
+    }
+    hi[cc] = C.ie[cc];
+    long na = G.nface(a), nb = G.nface(bax);
+    for (int k = lo[2]; k <= hi[2]; k++)
+      for (int j = lo[1]; j <= hi[1]; j++)
+        for (int i = lo[0]; i <= hi[0]; i++) {
+          // idx(A_off, B_off) -> (k,j,i) with offsets along a and b
+          auto at = [&](int da, int db, int& kk, int& jj, int& ii) {
+            int x[3] = {i, j, k};
+            x[a] += da;
+            x[bax] += db;
+            ii = x[0]; jj = x[1]; kk = x[2];
+          };
+          int kk, jj, ii;
+          // a-face (A-1/2, B) and (A-1/2, B-1)
+          at(0, 0, kk, jj, ii);
+          real Eaf_B = -real(flux[a][5 * na + G.f(a, kk, jj, ii)]);
+          real fDa_B = flux[a][0 * na + G.f(a, kk, jj, ii)];
+          at(0, -1, kk, jj, ii);
+          real Eaf_Bm = -real(flux[a][5 * na + G.f(a, kk, jj, ii)]);
+          real fDa_Bm = flux[a][0 * na + G.f(a, kk, jj, ii)];
+          // b-face (A, B-1/2) and (A-1, B-1/2)
+          at(0, 0, kk, jj, ii);
+          real Ebf_A = flux[bax][6 * nb + G.f(bax, kk, jj, ii)];
+          real fDb_A = flux[bax][0 * nb + G.f(bax, kk, jj, ii)];
+          at(-1, 0, kk, jj, ii);
+          real Ebf_Am = flux[bax][6 * nb + G.f(bax, kk, jj, ii)];
+          real fDb_Am = flux[bax][0 * nb + G.f(bax, kk, jj, ii)];
+          // cell-centred values at (A,B), (A-1,B), (A,B-1), (A-1,B-1)
+          at(0, 0, kk, jj, ii);
+          real E_AB = ecc[cc * G.ncell + G.c(kk, jj, ii)];
+          at(-1, 0, kk, jj, ii);
+          real E_AmB = ecc[cc * G.ncell + G.c(kk, jj, ii)];
+          at(0, -1, kk, jj, ii);
+          real E_ABm = ecc[cc * G.ncell + G.c(kk, jj, ii)];
+          at(-1, -1, kk, jj, ii);
+          real E_AmBm = ecc[cc * G.ncell + G.c(kk, jj, ii)];
+          // derivatives along b near the a-faces, upwinded across a
+          real dEb_q = upwind(fDa_B, E_AmB - Ebf_Am, E_AB - Ebf_A);       // at B-1/4
+          real dEb_tq = upwind(fDa_Bm, Ebf_Am - E_AmBm, Ebf_A - E_ABm);   // at B-3/4
+          // derivatives along a near the b-faces, upwinded across b
+          real dEa_q = upwind(fDb_A, E_ABm - Eaf_Bm, E_AB - Eaf_B);       // at A-1/4
+          real dEa_tq = upwind(fDb_Am, Eaf_Bm - E_AmBm, Eaf_B - E_AmB);   // at A-3/4
+          real E = 0.25 * (Eaf_B + Eaf_Bm + Ebf_A + Ebf_Am) + 0.25 * (dEb_tq - dEb_q) + 0.25 * (dEa_tq - dEa_q);
+          emf[cc][G.e(cc, k, j, i)] = val(E);
+        }
+  }
+}
+
+// Source terms of Eq. 9 at an interior cell (index 0: D~ has none).
+static void sources(const Ctx& C, int k, int j, int i, real Gs[5]) {
+  const Grid& G = C.G;
+  long c = G.c(k, j, i);
+  real g[6];
+  load_metric_cell(C, k, j, i, g);
+  real det = metric_det(g);
+  real sdet = sqrt_(det);
+  real gi[6];
+  metric_inverse(g, det, gi);
+  real alpha = C.adm(0, k, j, i);
+  real K[6];
+  for (int m = 0; m < 6; m++) K[m] = C.adm(10 + m, k, j, i);
+  // centred derivatives d_a of alpha, beta^i, gamma_ij
+  real dal[3], dbe[3][3], dg[3][6];
+  int off[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  for (int a = 0; a < 3; a++) {
+    int kp = k + off[a][2], jp = j + off[a][1], ip = i + off[a][0];
+    int km = k - off[a][2], jm = j - off[a][1], im = i - off[a][0];
+    real inv2dx = 1.0 / (2.0 * C.b->dx[a]);
+    dal[a] = (real(C.adm(0, kp, jp, ip)) - real(C.adm(0, km, jm, im))) * inv2dx;
+    for (int m = 0; m < 3; m++) dbe[a][m] = (real(C.adm(1 + m, kp, jp, ip)) - real(C.adm(1 + m, km, jm, im))) * inv2dx;
+    for (int m = 0; m < 6; m++) dg[a][m] = (real(C.adm(4 + m, kp, jp, ip)) - real(C.adm(4 + m, km, jm, im))) * inv2dx;
+  }
+  // fluid quantities
+  real rho = C.b->prim[0 * G.ncell + c], P = C.b->prim[4 * G.ncell + c];
+  real w[3] = {C.b->prim[1 * G.ncell + c], C.b->prim[2 * G.ncell + c], C.b->prim[3 * G.ncell + c]};
+  real wl[3];
+  metric_apply(g, w, wl);
+  real W = sqrt_(1.0 + dot3(w, wl));
+  real v[3] = {w[0] / W, w[1] / W, w[2] / W};
+  real vl[3] = {wl[0] / W, wl[1] / W, wl[2] / W};
+  real B[3];
+  for (int a = 0; a < 3; a++) B[a] = real(C.b->bcc[a * G.ncell + c]) / sdet;
+  real Bl[3];
+  metric_apply(g, B, Bl);
+  real B2 = dot3(B, Bl), Bv = dot3(B, vl);
+  real b2 = B2 / (W * W) + Bv * Bv;
+  real gam = C.p.gamma;
+  real h = 1.0 + gam / (gam - 1.0) * P / rho;
+  real Ptot = P + 0.5 * b2;
+  // bbar^i = gamma^ij b_j = B^i/W + W (B.v) v^i
+  real bb[3];
+  for (int a = 0; a < 3; a++) bb[a] = B[a] / W + W * Bv * v[a];
+  // densitised S^{ij} = sqrt(gamma) [ (rho h + b^2) W^2 v^i v^j + P_tot gamma^ij - bbar^i bbar^j ]
+  real Sij[6];
+  real e = (rho * h + b2) * W * W;
+  for (int a = 0; a < 3; a++)
+    for (int bq = a; bq < 3; bq++) Sij[sym(a, bq)] = sdet * (e * v[a] * v[bq] + Ptot * gi[sym(a, bq)] - bb[a] * bb[bq]);
+  real Sl[3] = {C.b->cons[1 * G.ncell + c], C.b->cons[2 * G.ncell + c], C.b->cons[3 * G.ncell + c]};
+  real Su[3];
+  metric_apply(gi, Sl, Su);
+  real E = real(C.b->cons[4 * G.ncell + c]) + real(C.b->cons[0 * G.ncell + c]);
+  Gs[0] = 0.0;
+  for (int a = 0; a < 3; a++) {
+    real t = 0.0;
+    for (int m = 0; m < 3; m++)
+      for (int n = 0; n < 3; n++) t = t + Sij[sym(m, n)] * dg[a][sym(m, n)];
+    real s2 = 0.0;
+    for (int m = 0; m < 3; m++) s2 = s2 + Sl[m] * dbe[a][m];
+    Gs[1 + a] = 0.5 * alpha * t + s2 - E * dal[a];
+  }
+  real kt = 0.0;
+  for (int m = 0; m < 3; m++)
+    for (int n = 0; n < 3; n++) kt = kt + K[sym(m, n)] * Sij[sym(m, n)];
+  real sd = 0.0;
+  for (int a = 0; a < 3; a++) sd = sd + Su[a] * dal[a];
+  Gs[4] = alpha * kt - sd;
+}
+
+// RK update of the interior cells and the interior faces (Sec. 3.2, Eq. 9).
+static void update(Ctx& C, std::vector<double> flux[3], std::vector<double> emf[3], double g0, double g1, double bdt) {
+  Grid& G = C.G;
+  const bool first = (g0 == 0.0);
+  std::vector<double> Unew(5 * G.ncell, 0.0);
+#ifndef ORACLE_COUNT_FLOPS
+#pragma omp parallel for collapse(2) schedule(static)
+#endif
+  for (int k = C.is[2]; k <= C.ie[2]; k++)
+    for (int j = C.is[1]; j <= C.ie[1]; j++)
+      for (int i = C.is[0]; i <= C.ie[0]; i++) {
+        long c = G.c(k, j, i);
+        real Gs[5];
+        sources(C, k, j, i, Gs);
+        for (int v = 0; v < 5; v++) {
+          real u = g1 * real(C.b->cons[v * G.ncell + c]);
+          if (!first) u = real(g0) * real(C.b->cons0[v * G.ncell + c]) + u;
+          Unew[v * G.ncell + c] = val(u + bdt * (flux_div(C, flux, v, k, j, i) + Gs[v]));
+        }
+      }
+  for (int k = C.is[2]; k <= C.ie[2]; k++)
+    for (int j = C.is[1]; j <= C.ie[1]; j++)
+      for (int i = C.is[0]; i <= C.ie[0]; i++) {
+        long c = G.c(k, j, i);
+        for (int v = 0; v < 5; v++) {
+          if (first) C.b->cons0[v * G.ncell + c] = C.b->cons[v * G.ncell + c];
+          C.b->cons[v * G.ncell + c] = Unew[v * G.ncell + c];
+        }
+      }
+  // face B~: B <- g0 B^n + g1 B - beta dt curl E
+  const double* dx = C.b->dx;
+  for (int d = 0; d < 3; d++) {
+    int lo[3], hi[3];
+    for (int x = 0; x < 3; x++) {
+      lo[x] = C.is[x];
+      hi[x] = C.ie[x];
+    }
+    hi[d] = C.ie[d] + 1;
+    for (int k = lo[2]; k <= hi[2]; k++)
+      for (int j = lo[1]; j <= hi[1]; j++)
+        for (int i = lo[0]; i <= hi[0]; i++) {
+          real curl;
+          if (d == 0)
+            curl = (real(emf[2][G.e(2, k, j + 1, i)]) - real(emf[2][G.e(2, k, j, i)])) / dx[1] -
+                   (real(emf[1][G.e(1, k + 1, j, i)]) - real(emf[1][G.e(1, k, j, i)])) / dx[2];
+          else if (d == 1)
+            curl = (real(emf[0][G.e(0, k + 1, j, i)]) - real(emf[0][G.e(0, k, j, i)])) / dx[2] -
+                   (real(emf[2][G.e(2, k, j, i + 1)]) - real(emf[2][G.e(2, k, j, i)])) / dx[0];
+          else
+            curl = (real(emf[1][G.e(1, k, j, i + 1)]) - real(emf[1][G.e(1, k, j, i)])) / dx[0] -
+                   (real(emf[0][G.e(0, k, j + 1, i)]) - real(emf[0][G.e(0, k, j, i)])) / dx[1];
+          long f = G.f(d, k, j, i);
+          real bnew = g1 * real(C.b->bf[d][f]);
+          if (!first) bnew = real(g0) * real(C.b->bf0[d][f]) + bnew;
+          bnew = bnew - bdt * curl;
+          if (first) C.b->bf0[d][f] = C.b->bf[d][f];
+          C.b->bf[d][f] = val(bnew);
+        }
+  }
+}
+
+static void stage_weights(int rk_order, int stage, double* g0, double* g1, double* be) {
+  const double* w = (rk_order == 2) ? RK2_W[stage] : RK3_W[stage];
+  *g0 = w[0];
+  *g1 = w[1];
+  *be = w[2];
+}
+
+extern "C" {
+
+// Eq. 6 on n cells.  prim [5][n], Bd [3][n] densitised, g [6][n]; cons [5][n] out.
+void or_prim2cons(const or_params* p, long n, const double* prim, const double* Bd, const double* g, double* cons) {
+#ifndef ORACLE_COUNT_FLOPS
+#pragma omp parallel for schedule(static)
+#endif
+  for (long c = 0; c < n; c++) {
+    real pr[5], b[3], gg[6], u[5];
+    for (int v = 0; v < 5; v++) pr[v] = prim[v * n + c];
+    for (int v = 0; v < 3; v++) b[v] = Bd[v * n + c];
+    for (int v = 0; v < 6; v++) gg[v] = g[v * n + c];
+    prim_to_cons(*p, pr, b, gg, u);
+    for (int v = 0; v < 5; v++) cons[v * n + c] = val(u[v]);
+  }
+}
+
+// con2prim on n independent cells.  cons [5][n] is updated in place when the
+// floors change it.  Optional outputs: iters [n], mu [n], eps_margin [n].
+void or_c2p_cells(const or_params* p, long n, double* cons, const double* Bd, const double* g, double* prim,
+                  unsigned char* flags, int* iters, double* mu, double* eps_margin) {
+#ifndef ORACLE_COUNT_FLOPS
+#pragma omp parallel for schedule(dynamic, 256)
+#endif
+  for (long c = 0; c < n; c++) {
+    real U[5], b[3], gg[6];
+    for (int v = 0; v < 5; v++) U[v] = cons[v * n + c];
+    for (int v = 0; v < 3; v++) b[v] = Bd[v * n + c];
+    for (int v = 0; v < 6; v++) gg[v] = g[v * n + c];
+    C2POut o;
+    c2p_cell(*p, U, b, gg, true, o);
+    for (int v = 0; v < 5; v++) cons[v * n + c] = val(U[v]);
+    for (int v = 0; v < 5; v++) prim[v * n + c] = val(o.prim[v]);
+    if (flags) flags[c] = (unsigned char)o.flags;
+    if (iters) iters[c] = o.iters;
+    if (mu) mu[c] = val(o.mu);
+    if (eps_margin) eps_margin[c] = val(o.eps_margin);
+  }
+}
+
+// The KRP master function f(mu) of one cell (undensitised floors NOT applied):
+// used by the brute-force bracket tests.  Returns f; out3 = {mu_plus, f(0), f(mu_plus)}.
+double or_c2p_master(const or_params* p, const double* cons5, const double* Bd3, const double* g6, double mu,
+                     double* out3) {
+  real g[6], det, sdet, gi[6];
+  for (int v = 0; v < 6; v++) g[v] = g6[v];
+  det = metric_det(g);
+  sdet = sqrt_(det);
+  metric_inverse(g, det, gi);
+  real D = cons5[0] / sdet;
+  real Sl[3] = {cons5[1] / sdet, cons5[2] / sdet, cons5[3] / sdet};
+  real tau = cons5[4] / sdet;
+  real B[3] = {Bd3[0] / sdet, Bd3[1] / sdet, Bd3[2] / sdet};
+  KRP s;
+  s.D = D;
+  s.gam = p->gamma;
+  s.eps_min = p->T_atm / (p->gamma - 1.0);
+  s.vmax2 = 1.0 - 1.0 / (p->W_max * p->W_max);
+  s.q = tau / D;
+  real rl[3] = {Sl[0] / D, Sl[1] / D, Sl[2] / D}, ru[3];
+  metric_apply(gi, rl, ru);
+  real sD = sqrt_(D);
+  real bu[3] = {B[0] / sD, B[1] / sD, B[2] / sD}, bl[3];
+  metric_apply(g, bu, bl);
+  s.r2 = dot3(rl, ru);
+  s.b2 = dot3(bu, bl);
+  s.rb = dot3(rl, bu);
+  s.rb2 = s.rb * s.rb;
+  s.rperp2 = s.r2 * s.b2 - s.rb2;
+  if (s.rperp2 < 0.0) s.rperp2 = 0.0;
+  KRPEval e;
+  if (out3) {
+    real mp = krp_mu_plus(s);
+    out3[0] = val(mp);
+    krp_eval(s, 0.0, e);
+    out3[1] = val(e.f);
+    krp_eval(s, mp, e);
+    out3[2] = val(e.f);
+  }
+  krp_eval(s, mu, e);
+  return val(e.f);
+}
+
+// Face B~ by the discrete curl of an edge vector potential, over all faces whose
+// four bounding edges exist.  A: [3] edge arrays in the emf layout.
+void or_bface_from_A(const or_block* b, const double* Ax, const double* Ay, const double* Az) {
+  Grid G(b);
+  const double* dx = b->dx;
+  for (int k = 0; k < G.N3; k++)
+    for (int j = 0; j < G.N2; j++)
+      for (int i = 0; i <= G.N1; i++)  // x-face (i-1/2, j, k): dAz/dy - dAy/dz
+        b->bf[0][G.f(0, k, j, i)] = (Az[G.e(2, k, j + 1, i)] - Az[G.e(2, k, j, i)]) / dx[1] -
+                                    (Ay[G.e(1, k + 1, j, i)] - Ay[G.e(1, k, j, i)]) / dx[2];
+  for (int k = 0; k < G.N3; k++)
+    for (int j = 0; j <= G.N2; j++)
+      for (int i = 0; i < G.N1; i++)  // y-face: dAx/dz - dAz/dx
+        b->bf[1][G.f(1, k, j, i)] = (Ax[G.e(0, k + 1, j, i)] - Ax[G.e(0, k, j, i)]) / dx[2] -
+                                    (Az[G.e(2, k, j, i + 1)] - Az[G.e(2, k, j, i)]) / dx[0];
+  for (int k = 0; k <= G.N3; k++)
+    for (int j = 0; j < G.N2; j++)
+      for (int i = 0; i < G.N1; i++)  // z-face: dAy/dx - dAx/dy
+        b->bf[2][G.f(2, k, j, i)] = (Ay[G.e(1, k, j, i + 1)] - Ay[G.e(1, k, j, i)]) / dx[0] -
+                                    (Ax[G.e(0, k, j + 1, i)] - Ax[G.e(0, k, j, i)]) / dx[1];
+}
+
+// cell-centred B~ on all cells
+void or_bcc(or_block* b, const or_params* p) {
+  Ctx C(*p, b);
+  compute_bcc(C);
+}
+
+// discrete divergence of face B~ at every cell: out [N3][N2][N1]
+void or_divb(const or_block* b, double* out) {
+  Grid G(b);
+  for (int k = 0; k < G.N3; k++)
+    for (int j = 0; j < G.N2; j++)
+      for (int i = 0; i < G.N1; i++)
+        out[G.c(k, j, i)] = (b->bf[0][G.f(0, k, j, i + 1)] - b->bf[0][G.f(0, k, j, i)]) / b->dx[0] +
+                            (b->bf[1][G.f(1, k, j + 1, i)] - b->bf[1][G.f(1, k, j, i)]) / b->dx[1] +
+                            (b->bf[2][G.f(2, k + 1, j, i)] - b->bf[2][G.f(2, k, j, i)]) / b->dx[2];
+}
+
+// con2prim over the stage region (interior + 3 ghost layers), floors written back
+void or_c2p_block(or_block* b, const or_params* p, or_stats* st) {
+  Ctx C(*p, b);
+  compute_bcc(C);
+  c2p_region(C, st);
+}
+
+// One RK stage (0-based) of order p->rk_order:
+//   bcc, con2prim (+floors), fluxes, [FOFC], CT EMFs, update of U and face B~.
+// At stage 0 the stage input is stored as U^n (cons0, bf0).
+int or_stage(or_block* b, const or_params* p, double dt, int stage, or_stats* st) {
+  if (b->ng < 4) return 1;
+  if (!(p->rk_order == 2 || p->rk_order == 3) || stage < 0 || stage >= p->rk_order) return 2;
+  Ctx C(*p, b);
+  double g0, g1, be;
+  stage_weights(p->rk_order, stage, &g0, &g1, &be);
+  compute_bcc(C);
+  c2p_region(C, st);
+  std::vector<double> flux[3];
+  compute_fluxes(C, flux);
+  if (p->fofc) fofc(C, flux, g0, g1, be * dt, st);
+  std::vector<double> ecc, emf[3];
+  compute_ecc(C, ecc);
+  compute_emf(C, flux, ecc, emf);
+  Grid& G = C.G;
+  for (int d = 0; d < 3; d++) {
+    if (b->flux[d]) std::memcpy(b->flux[d], flux[d].data(), sizeof(double) * 7 * G.nface(d));
+    if (b->emf[d]) std::memcpy(b->emf[d], emf[d].data(), sizeof(double) * G.nedge(d));
+  }
+  update(C, flux, emf, g0, g1, be * dt);
+  return 0;
+}
+
+// Reconstruction along a line of n values: L[f], R[f] for the faces f = 3..n-3
+// between entries f-1 and f (other entries untouched).
+void or_recon_line(int recon, long n, const double* q, double* L, double* R) {
+  for (long f = 3; f + 2 < n; f++) {
+    real s[6];
+    for (int m = 0; m < 6; m++) s[m] = q[f - 3 + m];
+    real l, r;
+    reconstruct(recon, s, &l, &r);
+    L[f] = val(l);
+    R[f] = val(r);
+  }
+}
+
+// One side of a face of direction d: st7 = rho, w^1..3, P, B~^{t1}, B~^{t2};
+// Bn = B~^d; m10 = alpha, beta^i, gamma_ij.  Out: U7, F7, speeds2 = {lambda-, lambda+}.
+void or_face_side(const or_params* p, int d, const double* st7, double Bn, const double* m10, double* U7,
+                  double* F7, double* speeds2) {
+  real st[7], m[10];
+  for (int v = 0; v < 7; v++) st[v] = st7[v];
+  for (int v = 0; v < 10; v++) m[v] = m10[v];
+  Side o;
+  face_side(*p, d, st, Bn, m, o);
+  for (int v = 0; v < 7; v++) {
+    U7[v] = val(o.U[v]);
+    F7[v] = val(o.F[v]);
+  }
+  speeds2[0] = val(o.lm);
+  speeds2[1] = val(o.lp);
+}
+
+// Riemann flux between two reconstructed states (after the face floor).
+void or_face_flux(const or_params* p, int d, const double* L7, const double* R7, double Bn, const double* m10,
+                  double* F7) {
+  real L[7], R[7], m[10];
+  for (int v = 0; v < 7; v++) {
+    L[v] = L7[v];
+    R[v] = R7[v];
+  }
+  for (int v = 0; v < 10; v++) m[v] = m10[v];
+  face_floor(*p, L);
+  face_floor(*p, R);
+  Side sl, sr;
+  face_side(*p, d, L, Bn, m, sl);
+  face_side(*p, d, R, Bn, m, sr);
+  real F[7];
+  riemann(p->rsolver, sl, sr, F);
+  for (int v = 0; v < 7; v++) F7[v] = val(F[v]);
+}
+
+// Upwind CT edge value from its neighbourhood, in the (a,b) plane of the edge:
+// e8 = {E_af(A-1/2,B), E_af(A-1/2,B-1), E_bf(A,B-1/2), E_bf(A-1,B-1/2),
+//       E_cc(A,B), E_cc(A-1,B), E_cc(A,B-1), E_cc(A-1,B-1)},
+// f4 = mass fluxes {F^a_D(A-1/2,B), F^a_D(A-1/2,B-1), F^b_D(A,B-1/2), F^b_D(A-1,B-1/2)}.
+double or_emf_edge(const double* e8, const double* f4) {
+  real Eaf_B = e8[0], Eaf_Bm = e8[1], Ebf_A = e8[2], Ebf_Am = e8[3];
+  real E_AB = e8[4], E_AmB = e8[5], E_ABm = e8[6], E_AmBm = e8[7];
+  real dEb_q = upwind(f4[0], E_AmB - Ebf_Am, E_AB - Ebf_A);
+  real dEb_tq = upwind(f4[1], Ebf_Am - E_AmBm, Ebf_A - E_ABm);
+  real dEa_q = upwind(f4[2], E_ABm - Eaf_Bm, E_AB - Eaf_B);
+  real dEa_tq = upwind(f4[3], Eaf_Bm - E_AmBm, Eaf_B - E_AmB);
+  return val(0.25 * (Eaf_B + Eaf_Bm + Ebf_A + Ebf_Am) + 0.25 * (dEb_tq - dEb_q) + 0.25 * (dEa_tq - dEa_q));
+}
+
+// Algorithmic FP64 operation counts (only meaningful in the counting build):
+// out = {add, mul, div, sqrt, cmp}.  Returns 1 in the counting build, else 0.
+int or_flop_counts(long long* out) {
+#ifdef ORACLE_COUNT_FLOPS
+  out[0] = g_fc.add; out[1] = g_fc.mul; out[2] = g_fc.div; out[3] = g_fc.sqrt; out[4] = g_fc.cmp;
+  return 1;
+#else
+  for (int i = 0; i < 5; i++) out[i] = 0;
+  return 0;
+#endif
+}
+void or_flop_reset(void) {
+#ifdef ORACLE_COUNT_FLOPS
+  g_fc = FlopCounts{0, 0, 0, 0, 0};
+#endif
+}
+
+}  // extern "C"

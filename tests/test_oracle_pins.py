@@ -1,0 +1,663 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test names the passage it pins.  None of them retypes an oracle formula:
+they use closed forms, the covariant definitions of Sec. 2 (tests/covariant.py),
+invariants (conservation, div B, symmetry), brute force, or printed inputs.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2409_10384_gb300 import synth
+from tests import covariant as cov
+from tests.helpers import fill_ghosts, init_from_faces, interior, rel_err, uniform_metric
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def rand_metric(rng):
+    h = rng.uniform(-0.15, 0.15, size=6)
+    g6 = h + np.array([1.0, 0, 0, 1.0, 0, 1.0])
+    return rng.uniform(0.5, 1.0), rng.uniform(-0.2, 0.2, size=3), g6
+
+
+def rand_state(rng):
+    rho = 10 ** rng.uniform(-3, 0)
+    P = rho * 10 ** rng.uniform(-3, 0.5)
+    w = rng.normal(size=3) * rng.uniform(0, 2)
+    Bd = rng.normal(size=3) * np.sqrt(rho) * rng.uniform(0, 2)
+    return rho, w, P, Bd
+
+
+# --------------------------------------------------------------------- Eq. 6
+
+def test_prim2cons_static_flat_hand_values():
+    """Eq. 6 with v = 0, B = 0 in flat space: D = rho, S = 0, tau = P/(Gamma-1)."""
+    p = O.params(gamma=5.0 / 3.0)
+    prim = np.array([[2.0], [0.0], [0.0], [0.0], [3.0]])
+    u = O.prim2cons(p, prim, np.zeros((3, 1)), np.array([[1.0], [0], [0], [1.0], [0], [1.0]]))
+    assert u[0, 0] == 2.0
+    assert np.all(u[1:4, 0] == 0.0)
+    assert abs(u[4, 0] - 4.5) < 1e-15
+
+
+def test_prim2cons_matches_covariant_projection():
+    """Eq. 6-7 against the projections of rho u^mu and T^{mu nu} (Eq. 2) on n."""
+    rng = np.random.default_rng(11)
+    p = O.params(gamma=1.4)
+    for _ in range(200):
+        a, be, g6 = rand_metric(rng)
+        rho, w, P, Bd = rand_state(rng)
+        f = cov.fluid(a, be, g6, rho, w, P, Bd, p.gamma)
+        u = O.prim2cons(p, np.array([[rho], [w[0]], [w[1]], [w[2]], [P]]), Bd.reshape(3, 1), g6.reshape(6, 1))[:, 0]
+        ref = cov.conserved(f)
+        scale = np.abs(ref).max()
+        assert np.max(np.abs(u - ref)) <= 1e-12 * scale, (u, ref)
+
+
+# --------------------------------------------------------------------- Eq. 8
+
+def test_face_fluxes_match_covariant_currents():
+    """Eq. 8 (one side of a face) against sqrt(-g) times the covariant currents
+    rho u^j, T^j_i, -n_nu T^{j nu} - rho u^j, (*F)^{ij} (Eq. 1, 3, 4c)."""
+    rng = np.random.default_rng(12)
+    p = O.params(gamma=5.0 / 3.0)
+    for _ in range(200):
+        a, be, g6 = rand_metric(rng)
+        rho, w, P, Bd = rand_state(rng)
+        f = cov.fluid(a, be, g6, rho, w, P, Bd, p.gamma)
+        for d in range(3):
+            t1, t2 = (d + 1) % 3, (d + 2) % 3
+            st = [rho, w[0], w[1], w[2], P, Bd[t1], Bd[t2]]
+            U, F, sp = O.face_side(p, d, st, Bd[d], [a, *be, *g6])
+            refF = cov.fluxes(f, d)
+            refU = cov.conserved(f)
+            sF = np.abs(refF).max() + np.abs(refU).max()
+            assert np.max(np.abs(F - refF)) <= 1e-12 * sF, (d, F, refF)
+            assert np.max(np.abs(U[:5] - refU)) <= 1e-12 * np.abs(refU).max()
+            assert U[5] == Bd[t1] and U[6] == Bd[t2]
+            assert sp[0] <= sp[1]
+
+
+def test_speeds_velocity_addition_lapse_shift():
+    """Unmagnetised wave speeds: the Eulerian speeds are the relativistic sum of
+    v and c_s; coordinate speeds are alpha*lambda - beta (Eq. 5)."""
+    gam = 4.0 / 3.0
+    p = O.params(gamma=gam)
+    rng = np.random.default_rng(13)
+    for _ in range(50):
+        rho, P = 10 ** rng.uniform(-2, 0), 10 ** rng.uniform(-2, 0)
+        v = rng.uniform(-0.95, 0.95)
+        W = 1.0 / np.sqrt(1 - v * v)
+        h = 1 + gam / (gam - 1) * P / rho
+        cs = np.sqrt(gam * P / (rho * h))
+        alpha, bx = rng.uniform(0.3, 1.0), rng.uniform(-0.3, 0.3)
+        _, _, sp = O.face_side(p, 0, [rho, W * v, 0, 0, P, 0, 0], 0.0, [alpha, bx, 0, 0, 1, 0, 0, 1, 0, 1])
+        lm, lp = cov.speeds_flat_hydro(v, cs)
+        assert abs(sp[0] - (alpha * lm - bx)) < 1e-13
+        assert abs(sp[1] - (alpha * lp - bx)) < 1e-13
+
+
+@pytest.mark.parametrize("rs", [0, 1])
+def test_riemann_consistency_equal_states(rs):
+    """An approximate Riemann solver returns the physical flux when U_L = U_R
+    (Sec. 3.2, LLF and HLLE)."""
+    rng = np.random.default_rng(14)
+    p = O.params(gamma=5.0 / 3.0, rsolver=rs, rho_atm=1e-20, T_atm=1e-20)
+    for _ in range(100):
+        a, be, g6 = rand_metric(rng)
+        rho, w, P, Bd = rand_state(rng)
+        for d in range(3):
+            t1, t2 = (d + 1) % 3, (d + 2) % 3
+            st = [rho, *w, P, Bd[t1], Bd[t2]]
+            m = [a, *be, *g6]
+            F = O.face_flux(p, d, st, st, Bd[d], m)
+            _, Fp, _ = O.face_side(p, d, st, Bd[d], m)
+            assert np.max(np.abs(F - Fp)) <= 1e-14 * (np.abs(Fp).max() + 1e-300)
+
+
+def test_hlle_is_upwind_for_supersonic_flow():
+    """HLLE with every characteristic speed positive returns the left flux."""
+    p = O.params(gamma=5.0 / 3.0, rsolver=1)
+    m = [1.0, 0, 0, 0, 1, 0, 0, 1, 0, 1]
+    L = [1.0, 5.0, 0.1, 0.0, 0.01, 0.0, 0.0]
+    R = [0.8, 4.0, -0.1, 0.1, 0.02, 0.0, 0.0]
+    F = O.face_flux(p, 0, L, R, 0.0, m)
+    _, FL, spL = O.face_side(p, 0, L, 0.0, m)
+    _, _, spR = O.face_side(p, 0, R, 0.0, m)
+    assert min(spL[0], spR[0]) > 0
+    assert np.max(np.abs(F - FL)) <= 1e-14 * np.abs(FL).max()
+
+
+# ----------------------------------------------------------------- Sec. 3.2
+
+@pytest.mark.parametrize("recon", [0, 1, 2])
+def test_reconstruction_constant_and_linear(recon):
+    q = np.full(16, 3.25)
+    L, R = O.recon_line(recon, q)
+    f = slice(3, 14)
+    assert np.all(L[f] == 3.25) and np.all(R[f] == 3.25)
+    q = 0.7 * np.arange(16) - 2.0
+    L, R = O.recon_line(recon, q)
+    face = 0.7 * (np.arange(16) - 0.5) - 2.0
+    if recon == 0:
+        assert np.all(L[f] == q[2:13]) and np.all(R[f] == q[3:14])
+    else:
+        assert np.max(np.abs(L[f] - face[f])) < 1e-13
+        assert np.max(np.abs(R[f] - face[f])) < 1e-13
+
+
+def test_plm_van_leer_hand_values():
+    """Harmonic van Leer slope: (0,1,3) -> slope 4/3; at an extremum -> 0."""
+    q = np.array([0.0, 0.0, 0.0, 1.0, 3.0, 4.0, 4.0, 4.0, 4.0])
+    L, R = O.recon_line(1, q)
+    # face between q[3]=1 and q[4]=3: L from cell 3 slope(0,1,3) = 2*1*2/3
+    assert abs(L[4] - (1.0 + 0.5 * 4.0 / 3.0)) < 1e-15
+    q = np.array([0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0])
+    L, R = O.recon_line(1, q)
+    assert L[4] == 1.0 and R[3] == 1.0
+
+
+def test_wenoz_order_and_eno_step():
+    """WENO-Z: fifth-order convergence on smooth data; at a step the
+    face value comes from the smooth one-sided stencil (Borges et al. 2008)."""
+    errs = []
+    for n in (32, 64, 128):
+        x = (np.arange(-3, n + 3) + 0.5) / n
+        q = n * (np.cos(2 * np.pi * (x - 0.5 / n)) - np.cos(2 * np.pi * (x + 0.5 / n))) / (2 * np.pi)  # cell averages of sin
+        L, R = O.recon_line(2, q)
+        xf = np.arange(-3, n + 3) / n
+        ex = np.sin(2 * np.pi * xf)
+        f = slice(3, n + 3)
+        errs.append(max(np.abs(L[f] - ex[f]).max(), np.abs(R[f] - ex[f]).max()))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > 4.5), rates
+    q = np.array([0.0] * 6 + [1.0] * 6)
+    L, R = O.recon_line(2, q)
+    assert abs(L[6]) < 1e-30 and abs(R[6] - 1.0) < 1e-30
+
+
+# ---------------------------------------------------------------- Sec. 3.4
+
+def _stress(n, seed=4, gamma=2.0):
+    prim, Bd, g = synth.c2p_stress(n, seed=seed, gamma=gamma)
+    p = O.params(gamma=gamma, rho_atm=1e-20, T_atm=1e-14, f_thr=0.0)
+    return p, prim, Bd, g, O.prim2cons(p, prim, Bd, g)
+
+
+def _P_tol(p, cons, g, P):
+    """|dP| <= 1e-10 |P| + 1e-12 (Gamma-1)(D+tau): P is recovered as a difference
+    of terms of size (D+tau)/D, so its absolute error scales with that."""
+    det = g[0] * (g[3] * g[5] - g[4] ** 2) - g[1] * (g[1] * g[5] - g[4] * g[2]) + g[2] * (g[1] * g[4] - g[3] * g[2])
+    sd = np.sqrt(det)
+    return 1e-10 * np.abs(P) + 1e-12 * (p.gamma - 1.0) * (cons[0] + cons[4]) / sd
+
+
+def test_c2p_round_trip_stress_distribution():
+    """prim -> cons -> prim over the con2prim stress distribution."""
+    p, prim, Bd, g, cons = _stress(20000)
+    r = O.c2p_cells(p, cons, Bd, g)
+    assert np.all(r["flags"] == 0)
+    assert rel_err(r["prim"][0], prim[0], 0.0) < 1e-10
+    W = np.sqrt(1 + (prim[1:4] ** 2).sum(0))
+    assert np.max(np.abs(r["prim"][1:4] - prim[1:4]) / W) < 1e-10
+    assert np.all(np.abs(r["prim"][4] - prim[4]) <= _P_tol(p, cons, g, prim[4]))
+    assert r["iters"].max() < 30
+
+
+def test_c2p_master_function_vanishes_at_one_over_hW():
+    """The KRP root is mu = 1/(h W) of the state that produced the conserved
+    variables (definition of mu)."""
+    p, prim, Bd, g, cons = _stress(300, seed=7)
+    for c in range(300):
+        rho, w, P = prim[0, c], prim[1:4, c], prim[4, c]
+        gg = np.array([[g[0, c], g[1, c], g[2, c]], [g[1, c], g[3, c], g[4, c]], [g[2, c], g[4, c], g[5, c]]])
+        W = np.sqrt(1 + w @ gg @ w)
+        h = 1 + p.gamma / (p.gamma - 1) * P / rho
+        mu = 1.0 / (h * W)
+        f, _ = O.c2p_master(p, cons[:, c], Bd[:, c], g[:, c], mu)
+        assert abs(f) <= 1e-11 * mu, (c, f, mu)
+
+
+def test_c2p_bruteforce_bisection():
+    """Brute force: bisection of f to machine precision inside [0, 1] agrees with
+    the solver's root; the solver's bracket ends have the right signs."""
+    p, prim, Bd, g, cons = _stress(400, seed=9)
+    r = O.c2p_cells(p, cons, Bd, g)
+    for c in range(400):
+        f0, (mup, fa, fp) = O.c2p_master(p, cons[:, c], Bd[:, c], g[:, c], 0.0)
+        assert fa < 0.0
+        f1, _ = O.c2p_master(p, cons[:, c], Bd[:, c], g[:, c], 1.0)
+        assert f1 >= 0.0
+        lo, hi = 0.0, 1.0
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            if mid in (lo, hi):
+                break
+            fm, _ = O.c2p_master(p, cons[:, c], Bd[:, c], g[:, c], mid)
+            if fm < 0:
+                lo = mid
+            else:
+                hi = mid
+        # For cold relativistic cells f is pure rounding noise (~5e-15) over a band
+        # of ~3e-13 mu around the root, so the root is defined only to that level.
+        assert abs(r["mu"][c] - lo) <= 1e-12 * lo, (c, r["mu"][c], lo)
+
+
+def test_c2p_unmagnetised_reduces_to_hydro():
+    """B = 0: the magnetised master function reduces to the hydro recovery, and
+    the round trip holds with few iterations."""
+    prim, Bd, g = synth.c2p_stress(3000, seed=5)
+    p = O.params(gamma=2.0, rho_atm=1e-20, T_atm=1e-14, f_thr=0.0)
+    Bd[...] = 0.0
+    cons = O.prim2cons(p, prim, Bd, g)
+    r = O.c2p_cells(p, cons, Bd, g)
+    assert np.all(r["flags"] == 0)
+    assert rel_err(r["prim"][0], prim[0], 0.0) < 1e-10
+    assert np.all(np.abs(r["prim"][4] - prim[4]) <= _P_tol(p, cons, g, prim[4]))
+
+
+def test_c2p_floors_and_failures():
+    """Sec. 3.3 atmosphere policy and the error policy, per case."""
+    gam = 2.0
+    p = O.params(gamma=gam, rho_atm=1e-10, T_atm=1e-8, f_thr=1.0)
+    g = np.array([[1.0], [0], [0], [1.0], [0], [1.0]])
+    Bd = np.array([[0.0], [1e-6], [0.0]])
+    # (a) D below f_thr rho_atm -> atmosphere, B untouched
+    cons = np.array([[1e-12], [1e-13], [0.0], [0.0], [1e-20]])
+    r = O.c2p_cells(p, cons, Bd, g)
+    assert r["flags"][0] & O.F_DFLOOR
+    assert r["prim"][0, 0] == p.rho_atm and np.all(r["prim"][1:4, 0] == 0.0)
+    assert abs(r["prim"][4, 0] - p.rho_atm * p.T_atm) <= 1e-15 * p.rho_atm * p.T_atm
+    assert abs(r["cons"][0, 0] - p.rho_atm) < 1e-24
+    # (b) tau below tau_atm(D, B) = D T_atm/(Gamma-1) + B^2/2 (v = 0)
+    cons = np.array([[1e-3], [0.0], [0.0], [0.0], [1e-30]])
+    r = O.c2p_cells(p, cons, Bd, g)
+    assert r["flags"][0] & O.F_TAU
+    assert abs(r["prim"][4, 0] / r["prim"][0, 0] - p.T_atm) < 1e-12 * p.T_atm
+    # (c) NaN input -> failure, static atmosphere
+    cons = np.array([[np.nan], [0.0], [0.0], [0.0], [1.0]])
+    r = O.c2p_cells(p, cons, Bd, g)
+    assert r["flags"][0] & O.F_FAIL and r["prim"][0, 0] == p.rho_atm
+    # (d) momentum beyond what D, tau allow -> speed cap, finite result
+    cons = np.array([[1.0], [50.0], [0.0], [0.0], [1.0]])
+    r = O.c2p_cells(p, cons, Bd, g)
+    assert np.all(np.isfinite(r["prim"][:, 0]))
+    assert r["flags"][0] & (O.F_VMAX | O.F_FAIL | O.F_TEMP)
+    # (e) cold state (T below T_atm) -> temperature floor, rho and w kept
+    prim = np.array([[1e-3], [0.3], [0.0], [0.0], [1e-3 * 1e-9]])
+    cons = O.prim2cons(p, prim, Bd, g)
+    r = O.c2p_cells(p, cons, Bd, g)
+    assert r["flags"][0] & O.F_TEMP
+    assert abs(r["prim"][4, 0] - r["prim"][0, 0] * p.T_atm) <= 1e-14 * r["prim"][4, 0]
+    assert abs(r["prim"][1, 0] - 0.3) < 1e-6
+
+
+# ------------------------------------------------------------- stage level
+
+def _small_block(p, n, adm, prim_cell, Bd):
+    N = [x + 8 for x in n]
+    prim = np.zeros((5, N[2], N[1], N[0]))
+    for v in range(5):
+        prim[v] = prim_cell[v]
+    bf = [np.full((N[2], N[1], N[0] + 1), Bd[0]), np.full((N[2], N[1] + 1, N[0]), Bd[1]),
+          np.full((N[2] + 1, N[1], N[0]), Bd[2])]
+    return init_from_faces(O, p, n, 4, (0.1, 0.1, 0.1), adm, prim, bf)
+
+
+@pytest.mark.parametrize("recon,rs", [(1, 1), (2, 0), (2, 1)])
+def test_uniform_state_curved_metric_fluxes_and_steady(recon, rs):
+    """Uniform fluid in a uniform curved metric: every face flux equals the
+    covariant current, and the state does not change (Eqs. 8-9, K = 0)."""
+    p = O.params(gamma=5.0 / 3.0, recon=recon, rsolver=rs, rk_order=3)
+    a, be, g6 = 0.8, (0.1, -0.05, 0.02), (1.1, 0.05, -0.02, 0.95, 0.03, 1.2)
+    n = (4, 5, 6)
+    adm = uniform_metric([x + 8 for x in n], a, be, g6)
+    rho, w, P, Bd = 0.5, np.array([0.2, -0.3, 0.1]), 0.3, np.array([0.2, 0.1, -0.3])
+    b = _small_block(p, n, adm, [rho, *w, P], Bd)
+    U0 = b.cons.copy()
+    out = O.stage(p, b, 0.01, 0, keep=True)
+    f = cov.fluid(a, np.array(be), np.array(g6), rho, w, P, Bd, p.gamma)
+    for d in range(3):
+        ref = cov.fluxes(f, d)
+        F = out["flux"][d]
+        # faces the stage computes: interior along d, one extra layer transversally
+        sl = [slice(None)] * 4
+        for ax in range(3):
+            arr = 3 - ax
+            lo, hi = (4, 4 + n[ax] + 1) if ax == d else (3, 4 + n[ax] + 1)
+            sl[arr] = slice(lo, hi)
+        Fi = F[tuple(sl)]
+        for c in range(7):
+            assert np.max(np.abs(Fi[c] - ref[c])) <= 1e-13 * (np.abs(ref).max()), (d, c)
+    I = (slice(None),) + interior(b)
+    assert np.max(np.abs(b.cons[I] - U0[I])) <= 1e-14 * np.abs(U0[I]).max()
+
+
+def test_sources_match_covariant_form():
+    """Eq. 9 against the covariant sources: S~_i gets (1/2) sqrt(-g) T^{mu nu}
+    d_i g_{mu nu}; tau~ gets sqrt(-g)(K_ij S^ij - S^i d_i alpha / alpha), with
+    S^ij, S^i the spatial projections of T.  Linear ADM fields make the centred
+    differences exact."""
+    p = O.params(gamma=5.0 / 3.0, recon=0, rsolver=1, rk_order=2)
+    n = (3, 3, 3)
+    N = [x + 8 for x in n]
+    dx = (0.1, 0.1, 0.1)
+    z, y, x = np.meshgrid(*[(np.arange(Nd) - 4 + 0.5) * dx[0] for Nd in N[::-1]], indexing="ij")
+    ga = dict(alpha=(0.8, 0.03, -0.02, 0.01), b1=(0.1, 0.02, 0.0, -0.01), b2=(-0.05, 0.0, 0.03, 0.01),
+              b3=(0.02, -0.01, 0.01, 0.02))
+    gl = [(1.1, 0.02, 0.01, -0.01), (0.05, 0.0, 0.01, 0.0), (-0.02, 0.01, 0.0, 0.01),
+          (0.95, -0.01, 0.02, 0.0), (0.03, 0.0, -0.01, 0.01), (1.2, 0.01, 0.0, 0.02)]
+    K6 = (0.01, -0.02, 0.005, 0.015, 0.01, -0.01)
+    lin = lambda c: c[0] + c[1] * x + c[2] * y + c[3] * z
+    adm = np.zeros((16,) + x.shape)
+    adm[0] = lin(ga["alpha"])
+    adm[1], adm[2], adm[3] = lin(ga["b1"]), lin(ga["b2"]), lin(ga["b3"])
+    for c in range(6):
+        adm[4 + c] = lin(gl[c])
+        adm[10 + c] = K6[c]
+    rho, w, P, Bd = 0.5, np.array([0.2, -0.3, 0.1]), 0.3, np.array([0.2, 0.1, -0.3])
+    b = _small_block(p, n, adm, [rho, *w, P], Bd)
+    U0 = b.cons.copy()
+    dt = 1e-3
+    out = O.stage(p, b, dt, 0, keep=True)
+    F = out["flux"]
+    for (k, j, i) in [(5, 5, 5), (4, 6, 5), (6, 4, 4)]:
+        div = np.zeros(5)
+        div -= (F[0][:5, k, j, i + 1] - F[0][:5, k, j, i]) / dx[0]
+        div -= (F[1][:5, k, j + 1, i] - F[1][:5, k, j, i]) / dx[1]
+        div -= (F[2][:5, k + 1, j, i] - F[2][:5, k, j, i]) / dx[2]
+        G = (b.cons[:, k, j, i] - U0[:, k, j, i]) / dt - div
+        xx, yy, zz = x[k, j, i], y[k, j, i], z[k, j, i]
+        ev = lambda c: c[0] + c[1] * xx + c[2] * yy + c[3] * zz
+        al = ev(ga["alpha"])
+        be = np.array([ev(ga["b1"]), ev(ga["b2"]), ev(ga["b3"])])
+        g6 = np.array([ev(c) for c in gl])
+        # the stage's primitives in this cell (con2prim of the same cons)
+        pr = b.prim[:, k, j, i]
+        f = cov.fluid(al, be, g6, pr[0], pr[1:4], pr[4], Bd, p.gamma)
+        # d_i g_{mu nu} from the exact derivatives of the linear ADM fields
+        dal = np.array(ga["alpha"][1:])
+        dbe = np.array([ga["b1"][1:], ga["b2"][1:], ga["b3"][1:]])  # [comp][dir]
+        dg6 = np.array([c[1:] for c in gl])                           # [comp][dir]
+        gm = f["g"]
+        src_S = np.zeros(3)
+        for a in range(3):
+            dg = np.array([[dg6[0, a], dg6[1, a], dg6[2, a]], [dg6[1, a], dg6[3, a], dg6[4, a]],
+                           [dg6[2, a], dg6[4, a], dg6[5, a]]])
+            dbl = dg @ be + gm @ dbe[:, a]          # d_a beta_i
+            dG = np.zeros((4, 4))
+            dG[0, 0] = -2 * al * dal[a] + dbl @ be + (gm @ be) @ dbe[:, a]
+            dG[0, 1:] = dbl
+            dG[1:, 0] = dbl
+            dG[1:, 1:] = dg
+            src_S[a] = 0.5 * al * f["sdet"] * np.sum(f["T"] * dG)
+        # spatial projections of T: gamma^i_mu = delta^i_mu + n^i n_mu
+        nup = np.array([1 / al, *(-be / al)])
+        nlo = f["n_lo"]
+        proj = np.eye(4)[1:] + np.outer(nup[1:], nlo)
+        Sij = proj @ f["T"] @ proj.T
+        Si = -(proj @ f["T"] @ nlo)
+        Km = np.array([[K6[0], K6[1], K6[2]], [K6[1], K6[3], K6[4]], [K6[2], K6[4], K6[5]]])
+        src_tau = al * f["sdet"] * (np.sum(Km * Sij) - Si @ dal / al)
+        scale = np.abs(src_S).max() + abs(src_tau)
+        assert abs(G[0]) < 1e-10 * scale
+        assert np.max(np.abs(G[1:4] - src_S)) < 1e-9 * scale, (G[1:4], src_S)
+        assert abs(G[4] - src_tau) < 1e-9 * scale, (G[4], src_tau)
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_ssp_rk_amplification_factor(order):
+    """SSP-RK2/3 (Sec. 3.2): a static unmagnetised fluid with constant K_ij obeys
+    d tau~/dt = lambda tau~, lambda = alpha (Gamma-1) gamma^ij K_ij (Eq. 9), so one
+    step multiplies tau~ by the Taylor polynomial of exp(lambda dt) of the order."""
+    gam = 5.0 / 3.0
+    p = O.params(gamma=gam, recon=1, rsolver=1, rk_order=order, rho_atm=1e-20, T_atm=1e-20)
+    n = (2, 2, 2)
+    a = 0.9
+    K6 = (0.3, 0.0, 0.0, 0.2, 0.0, 0.1)
+    adm = uniform_metric([x + 8 for x in n], a, (0, 0, 0), (1, 0, 0, 1, 0, 1), K6)
+    b = _small_block(p, n, adm, [1.0, 0, 0, 0, 0.5], np.zeros(3))
+    tau0 = b.cons[4, 5, 5, 5]
+    dt = 0.05
+    for s in range(order):
+        fill_ghosts(b, ("periodic",) * 3)
+        O.stage(p, b, dt, s)
+    z = a * (gam - 1) * (0.3 + 0.2 + 0.1) * dt
+    R = 1 + z + z * z / 2 + (z ** 3 / 6 if order == 3 else 0.0)
+    assert abs(b.cons[4, 5, 5, 5] / tau0 - R) < 1e-13
+
+
+def _periodic_block(p):
+    inp = synth.periodic_flat(1)
+    return O.init_block(p, inp.n, inp.ng, inp.dx, inp.adm, inp.prim, inp.A)
+
+
+def test_periodic_flat_conservation_and_divb():
+    """Flat periodic block: no sources (Eq. 9 vanishes), so the sums of D~, S~_i,
+    tau~ are conserved to round-off, and CT keeps div B~ at round-off (Sec. 4.3)."""
+    p = O.params(gamma=5.0 / 3.0, recon=1, rsolver=1, rk_order=2)
+    b = _periodic_block(p)
+    I = (slice(None),) + interior(b)
+    s0 = b.cons[I].sum(axis=(1, 2, 3))
+    Bmax = max(np.abs(x).max() for x in b.bf)
+    for _ in range(2):
+        O.step(p, b, 0.25 / 32, fill=lambda bb: fill_ghosts(bb))
+    s1 = b.cons[I].sum(axis=(1, 2, 3))
+    scale = np.abs(b.cons[I]).sum(axis=(1, 2, 3))
+    assert np.all(np.abs(s1 - s0) <= 1e-14 * scale)
+    fill_ghosts(b)
+    div = O.divb(b)[interior(b)]
+    assert np.abs(div).max() * (1.0 / 32) / Bmax < 1e-13
+
+
+def test_fofc_smooth_flow_is_identity():
+    """FOFC on a smooth flow with no floors flags nothing and changes nothing."""
+    p0 = O.params(gamma=5.0 / 3.0, recon=2, rsolver=1, rk_order=2, fofc=0)
+    p1 = O.params(gamma=5.0 / 3.0, recon=2, rsolver=1, rk_order=2, fofc=1)
+    b0 = _periodic_block(p0)
+    b1 = b0.copy()
+    O.stage(p0, b0, 0.25 / 32, 0)
+    st = O.stage(p1, b1, 0.25 / 32, 0)
+    assert st["fofc_cells"] == 0 and st["fofc_faces"] == 0
+    assert np.array_equal(b0.cons, b1.cons)
+    for d in range(3):
+        assert np.array_equal(b0.bf[d], b1.bf[d])
+
+
+def test_fofc_mask_gives_donor_fluxes_on_exactly_those_faces():
+    """A flagged cell has all six face fluxes recomputed first order (donor cell,
+    same Riemann solver); all other faces keep the high-order flux (Sec. 3.3)."""
+    pho = O.params(gamma=5.0 / 3.0, recon=2, rsolver=1, rk_order=2, fofc=1)
+    plo = O.params(gamma=5.0 / 3.0, recon=0, rsolver=1, rk_order=2, fofc=0)
+    base = _periodic_block(pho)
+    N = base.cons.shape[1:]
+    rng = np.random.default_rng(3)
+    mask = np.zeros(N, np.uint8)
+    I = interior(base)
+    sub = mask[I]
+    sub[rng.random(sub.shape) < 0.05] = 1
+    mask[I] = sub
+    bm, bh, bl = base.copy(), base.copy(), base.copy()
+    om = O.stage(pho, bm, 0.25 / 32, 0, mask=mask, keep=True)
+    oh = O.stage(pho, bh, 0.25 / 32, 0, mask=np.zeros(N, np.uint8), keep=True)
+    ol = O.stage(plo, bl, 0.25 / 32, 0, keep=True)
+    for d in range(3):
+        off = [0, 0, 0]
+        off[2 - d] = 1
+        fm = np.zeros_like(om["flux"][d][0], dtype=bool)
+        # face (k,j,i) touches cells (k,j,i)-e_d and (k,j,i)
+        sh = fm.shape
+        m0 = np.zeros(sh, bool)
+        m1 = np.zeros(sh, bool)
+        m0[: N[0], : N[1], : N[2]] |= mask.astype(bool)
+        m1[off[0]: off[0] + N[0], off[1]: off[1] + N[1], off[2]: off[2] + N[2]] |= mask.astype(bool)
+        fm = m0 | m1
+        computed = np.abs(oh["flux"][d][0]) + np.abs(ol["flux"][d][0]) > 0
+        for c in range(7):
+            a = om["flux"][d][c]
+            assert np.array_equal(a[fm & computed], ol["flux"][d][c][fm & computed])
+            assert np.array_equal(a[~fm], oh["flux"][d][c][~fm])
+
+
+def test_dmp_truth_table_and_infinite_M():
+    """Relaxed DMP (Eq. 19) on D~ and tau~ with the 27-cell neighbourhood of the
+    stage input; M -> infinity reduces FOFC+DMP to FOFC."""
+    gam = 5.0 / 3.0
+    pf = O.params(gamma=gam, recon=2, rsolver=1, rk_order=2, fofc=1, dmp_M=0.0)
+    pinf = O.params(gamma=gam, recon=2, rsolver=1, rk_order=2, fofc=1, dmp_M=1e300)
+    pM = O.params(gamma=gam, recon=2, rsolver=1, rk_order=2, fofc=1, dmp_M=1.0)
+    base = _periodic_block(pf)
+    b1, b2 = base.copy(), base.copy()
+    O.stage(pf, b1, 0.25 / 32, 0)
+    O.stage(pinf, b2, 0.25 / 32, 0)
+    assert np.array_equal(b1.cons, b2.cons)
+    # M = 1: expected flags from U* = U + dt L_flux and the neighbourhood min/max
+    b3 = base.copy()
+    bh = base.copy()
+    dt = 0.25 / 32
+    oh = O.stage(O.params(gamma=gam, recon=2, rsolver=1, rk_order=2, fofc=0), bh, dt, 0, keep=True)
+    O.c2p_block(pf, b3)  # stage-input state after con2prim floors (none here)
+    U = b3.cons
+    F = oh["flux"]
+    I = interior(base)
+    N = U.shape[1:]
+    div = np.zeros_like(U)
+    div[:, :, :, :] -= (F[0][:5, :, :, 1:] - F[0][:5, :, :, :-1]) / base.dx[0]
+    div[:, :, :, :] -= (F[1][:5, :, 1:, :] - F[1][:5, :, :-1, :]) / base.dx[1]
+    div[:, :, :, :] -= (F[2][:5, 1:, :, :] - F[2][:5, :-1, :, :]) / base.dx[2]
+    Us = U + dt * div
+    expect = np.zeros(N, bool)
+    for v in (0, 4):
+        mx = np.full(N, -np.inf)
+        mn = np.full(N, np.inf)
+        for dk in (-1, 0, 1):
+            for dj in (-1, 0, 1):
+                for di in (-1, 0, 1):
+                    r = np.roll(U[v], (-dk, -dj, -di), axis=(0, 1, 2))
+                    mx = np.maximum(mx, r)
+                    mn = np.minimum(mn, r)
+        M = 1.0
+        lo = np.where(mn > 0, mn / M, mn * M)
+        hi = np.where(mx > 0, mx * M, mx / M)
+        expect |= (Us[v] < lo) | (Us[v] > hi)
+    bm = base.copy()
+    st = O.stage(pM, bm, dt, 0)
+    got = (bm.flags[I] & O.F_FOFC) != 0
+    assert st["fofc_cells"] == int(got.sum())
+    assert np.array_equal(got, expect[I])
+    assert got.sum() > 0
+
+
+def _tube(test, n=64, recon=1, rs=1):
+    tab = json.load(open(os.path.join(HERE, "golden", "balsara_tab1.json")))["tests"][str(test)]
+    L, R = np.array(tab["L"]), np.array(tab["R"])
+    gam = L[0]
+    p = O.params(gamma=gam, recon=recon, rsolver=rs, rk_order=2, rho_atm=1e-10, T_atm=1e-12, f_thr=0.1)
+    nn = (n, 2, 2)
+    N = (n + 8, 10, 10)
+    adm = uniform_metric(N)
+    xc = (np.arange(N[0]) - 4 + 0.5) / n
+    left = xc < 0.5
+    prim = np.zeros((5, N[2], N[1], N[0]))
+    st = np.where(left[None, :], L[1:, None], R[1:, None])   # [8][N1]
+    W = 1 / np.sqrt(1 - (st[2] ** 2 + st[3] ** 2 + st[4] ** 2))
+    prim[0] = st[0]
+    prim[1], prim[2], prim[3] = W * st[2], W * st[3], W * st[4]
+    prim[4] = st[1]
+    bf = [np.full((N[2], N[1], N[0] + 1), L[6]),
+          np.broadcast_to(st[6], (N[2], N[1] + 1, N[0])).copy(),
+          np.broadcast_to(st[7], (N[2] + 1, N[1], N[0])).copy()]
+    b = init_from_faces(O, p, nn, 4, (1.0 / n, 1.0, 1.0), adm, prim, bf)
+    return p, b
+
+
+def test_balsara4_mirror_symmetry_and_transverse_uniformity():
+    """Balsara test 4 (Table 1) is mirror symmetric about x = 0.5 (rho, P even;
+    v^x, B^y, B^z odd); the scheme keeps that and keeps y/z uniformity."""
+    p, b = _tube(4, n=64)
+    modes = ("outflow", "periodic", "periodic")
+    for _ in range(10):
+        O.step(p, b, 0.2 / 64, fill=lambda bb: fill_ghosts(bb, modes))
+    assert np.all(b.flags[interior(b)] & O.F_FAIL == 0)
+    I = interior(b)
+    rho = b.prim[0][I]
+    assert np.all(rho > 0)
+    # transverse uniformity (exact): the interior is two cells wide in y and z
+    ref = b.cons[:, 4, 4, :]
+    for k in (4, 5):
+        for j in (4, 5):
+            assert np.array_equal(b.cons[:, k, j, :], ref)
+    line = b.cons[:, 4, 4, 4:68]
+    mir = line[:, ::-1]
+    sgn = np.array([1, -1, 1, 1, 1])
+    scale = np.abs(line).max(axis=1, keepdims=True)
+    assert np.max(np.abs(line - sgn[:, None] * mir) / scale) < 1e-12
+    by = b.bf[1][4, 4, 4:68]
+    assert np.max(np.abs(by + by[::-1])) < 1e-12 * np.abs(by).max()
+
+
+def test_balsara1_runs_without_failures():
+    """Balsara test 1 (Table 1): 20 RK2 steps, positive density, no con2prim failure."""
+    p, b = _tube(1, n=64, recon=2)
+    modes = ("outflow", "periodic", "periodic")
+    for _ in range(20):
+        O.step(p, b, 0.25 / 64, fill=lambda bb: fill_ghosts(bb, modes))
+    I = interior(b)
+    assert np.all(b.flags[I] & O.F_FAIL == 0)
+    assert np.all(b.prim[0][I] > 0) and np.all(b.prim[4][I] > 0)
+    assert b.prim[0][I].max() <= 1.1 and b.prim[0][I].min() >= 0.1
+
+
+def test_emf_edge_exact_for_quadratic_upwind():
+    """The upwind edge EMF is exact for a field quadratic along a (upwinded from
+    the low side) and linear along b, and equals the arithmetic mean on ties."""
+    A, B = 3.0, 5.0
+    E = lambda a, b: (a ** 2) + 0.7 * b + 0.3
+    e8 = [E(A - 0.5, B), E(A - 0.5, B - 1), E(A, B - 0.5), E(A - 1, B - 0.5),
+          E(A, B), E(A - 1, B), E(A, B - 1), E(A - 1, B - 1)]
+    got = O.emf_edge(e8, [1.0, 1.0, 1.0, 1.0])
+    assert abs(got - E(A - 0.5, B - 0.5)) < 1e-13
+    # quadratic along b, upwinded from the low side in a as well
+    E2 = lambda a, b: 0.2 * a + b ** 2
+    e8 = [E2(A - 0.5, B), E2(A - 0.5, B - 1), E2(A, B - 0.5), E2(A - 1, B - 0.5),
+          E2(A, B), E2(A - 1, B), E2(A, B - 1), E2(A - 1, B - 1)]
+    got = O.emf_edge(e8, [1.0, 1.0, -1.0, -1.0])
+    assert abs(got - E2(A - 0.5, B - 0.5)) < 1e-13
+    z = O.emf_edge(e8, [0.0, 0.0, 0.0, 0.0])
+    avg = 0.5 * (O.emf_edge(e8, [1.0, 1.0, 1.0, 1.0]) + O.emf_edge(e8, [-1.0, -1.0, -1.0, -1.0]))
+    assert abs(z - avg) < 1e-13
+
+
+def test_flop_counting_build_matches_plain_build():
+    """The op-counting build computes bit-identical results and counts > 0."""
+    p = O.params(gamma=2.0, recon=2, rsolver=1, rk_order=3, fofc=1, rho_atm=1e-12, T_atm=1e-10)
+    inp = synth.star_subblock(sub=8, corner=(60, 60, 60))
+    b = O.init_block(p, inp.n, inp.ng, inp.dx, inp.adm, inp.prim, inp.A)
+    c = O.flop_counts(p, b, 0.1, 0)
+    assert c["add"] > 0 and c["mul"] > 0 and c["div"] > 0 and c["sqrt"] > 0
+    b1, b2 = b.copy(), b.copy()
+    O.stage(p, b1, 0.1, 0)
+    O.stage(p, b2, 0.1, 0, counting=True)
+    assert np.array_equal(b1.cons, b2.cons)
+
+
+def test_emf_edge_ignores_downstream_cell():
+    """Upwinding (Gardiner & Stone 2005): with every mass flux positive the edge
+    EMF cannot depend on the cell-centred E of the downstream cell (A, B); with
+    every flux negative it cannot depend on the cell (A-1, B-1)."""
+    rng = np.random.default_rng(21)
+    for _ in range(20):
+        e8 = rng.normal(size=8)
+        pos, neg = [1.0] * 4, [-1.0] * 4
+        e8b = e8.copy()
+        e8b[4] += 1.0                       # E_cc(A, B)
+        assert O.emf_edge(e8, pos) == O.emf_edge(e8b, pos)
+        assert O.emf_edge(e8, neg) != O.emf_edge(e8b, neg)
+        e8c = e8.copy()
+        e8c[7] += 1.0                       # E_cc(A-1, B-1)
+        assert O.emf_edge(e8, neg) == O.emf_edge(e8c, neg)
+        assert O.emf_edge(e8, pos) != O.emf_edge(e8c, pos)
