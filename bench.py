@@ -1,0 +1,330 @@
+"""Benchmark: GRMHD zone-cycles/s of the meshblock RHS + update on GB300.
+
+Workload (one "step" = one SSP-RK3 step of every stage of the hot path):
+a 128^3 (+4 ghosts) FP64 star in a conformally flat dynamical metric with
+seeded shift and extrinsic curvature; WENO-Z + HLLE + FOFC + upwind CT,
+con2prim (Kastaun et al. 2021) with atmosphere floors, Eq. 9 sources.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank advances its own replica (the path has no exchange
+step between ranks on one box); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_INT = 128   # interior cells per side of the benchmarked block (--n changes it for profiling)
+NG = 4
+METRIC = "GRMHD zone-cycles/s on 1 GB300; con2prim cells/s learned-guess vs plain @1e-10"
+UNIT = "zone-cycles/s"
+WORKLOAD = "star128_wenoz_hlle_fofc_ct_rk3"
+PARAMS = dict(gamma=2.0, rho_atm=1e-12, T_atm=1e-10, f_thr=0.1, sigma_max=0.0, dmp_M=0.0, c2p_tol=1e-10,
+              W_max=1e3, recon=2, rsolver=1, fofc=1, rk_order=3, c2p_maxit=64)
+CFL = 0.25
+
+# Algorithmic FP64 operations per unit (add + mul + div + sqrt, each counted
+# once), from the op-counting build of the CPU oracle on sub-blocks of this
+# workload (oracle.flop_phases; re-derived by tests/test_flop_table.py):
+# unit = face for the flux kernels, region cell for con2prim, interior cell
+# for the FOFC estimate and the update, flagged face for the FOFC recompute.
+FLOPS_PER_UNIT = {"flux": 1576.0, "c2p": 450.0, "fofc_flag": 450.0, "fofc_fix": 595.0, "update": 443.5,
+                  "emf": 36.1}
+FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (dense), the profiling recipe's unit table
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.idx = gpu_id
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.idx)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def star_inputs():
+    from paper_2409_10384_gb300 import synth
+    return synth.star_uniform(seed=2, n=N_INT, ng=NG)
+
+
+WORKLOAD_NAME = lambda: WORKLOAD if N_INT == 128 else WORKLOAD.replace("star128", f"star{N_INT}")
+
+
+# ----------------------------------------------------------------- CPU oracle
+
+def oracle_sample(max_seconds: float = 12.0, max_steps: int = 20, sub: int = 64):
+    """The FP64 CPU oracle (OpenMP over the host cores) on a bounded sample of
+    the workload: RK3 steps of a sub^3 sub-block of the 128^3 star."""
+    import oracle as O
+    from paper_2409_10384_gb300 import synth
+    O.build()
+    p = O.params(**PARAMS)
+    inp = synth.star_subblock(seed=2, n_full=N_INT, sub=sub, corner=(32, 32, 32))
+    b = O.init_block(p, inp.n, inp.ng, inp.dx, inp.adm, inp.prim, inp.A)
+    dt = CFL * inp.dx[0]
+    steps, t0 = 0, time.perf_counter()
+    while steps < max_steps:
+        O.step(p, b, dt)
+        steps += 1
+        if time.perf_counter() - t0 > max_seconds:
+            break
+    el = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    threads = int(os.environ.get("OMP_NUM_THREADS", cores))
+    return dict(value=sub ** 3 * steps / el, unit=UNIT, cores=threads, kind="oracle",
+                sample=f"{steps} RK3 step(s) of a {sub}^3 sub-block of the 128^3 star, {el:.1f} s")
+
+
+def run_reference(args):
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    import oracle as O
+    from paper_2409_10384_gb300 import synth
+    O.build()
+    p = O.params(**PARAMS)
+    sub = 48
+    inp = synth.star_subblock(seed=2, n_full=N_INT, sub=sub, corner=(40, 40, 40))
+    b = O.init_block(p, inp.n, inp.ng, inp.dx, inp.adm, inp.prim, inp.A)
+    dt = CFL * inp.dx[0]
+    for _ in range(args.warmup):
+        O.step(p, b, dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.step(p, b, dt)
+    el = time.perf_counter() - t0
+    v = sub ** 3 * args.steps / el
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"{sub}^3 sub-block of the 128^3 star per step",
+                       "l2": "inputs larger than L2 not applicable (CPU)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} RK3 steps of a {sub}^3 sub-block of the 128^3 star"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- GPU path
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2409_10384_gb300 import build as B
+    from paper_2409_10384_gb300 import grmhd as G
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    B.build()
+
+    inp = star_inputs()
+    ctx = G.Context(G.params(**PARAMS, c2p_guess=0))
+    blk = G.DeviceBlock(inp.n, inp.ng, inp.dx, inp.adm)
+    blk.prim.copy_(torch.from_numpy(inp.prim))
+    A = [torch.from_numpy(a).cuda() for a in inp.A]
+    ctx.init_block(blk, A)
+    del A
+    torch.cuda.synchronize()
+    dt = CFL * inp.dx[0]
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    zones = N_INT ** 3
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (also captures the graph used by the e2e leg)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            ctx.step([blk], dt, graph=False, stream=stream)
+    stream.synchronize()
+
+    # device-timed region: inputs resident in HBM (working set ~1 GB > L2)
+    ctx.profile(True)
+    ctx.profile_read()
+    ctx.reset_stats(stream)
+    uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    clk = ClockSampler(uuid if uuid.startswith("GPU-") else f"GPU-{uuid}")
+    barrier()
+    clk.start()
+    time.sleep(0.3)
+    launches0 = ctx.launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.step([blk], dt, graph=False, stream=stream)
+        e1.record(stream)
+    stream.synchronize()
+    barrier()
+    clocks = clk.stop()
+    launches = ctx.launches() - launches0
+    ms = e0.elapsed_time(e1)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    stats = ctx.read_stats(stream)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * zones * args.steps / (ms_max * 1e-3)
+
+    # end-to-end through the public API with host buffers: each step copies the
+    # state (cons, face B~) and the metric from pinned host memory, advances one
+    # RK3 step and reads the state back.
+    host = {
+        "cons": torch.empty_like(blk.cons, device="cpu").pin_memory(),
+        "adm": torch.empty_like(blk.adm, device="cpu").pin_memory(),
+        "bf": [torch.empty_like(x, device="cpu").pin_memory() for x in blk.bf],
+    }
+    host["cons"].copy_(blk.cons)
+    host["adm"].copy_(blk.adm)
+    for d in range(3):
+        host["bf"][d].copy_(blk.bf[d])
+    h2d = host["cons"].numel() * 8 + host["adm"].numel() * 8 + sum(x.numel() * 8 for x in host["bf"])
+    d2h = host["cons"].numel() * 8 + sum(x.numel() * 8 for x in host["bf"])
+    barrier()
+    with torch.cuda.stream(stream):
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        for _ in range(args.steps):
+            ctx.step_host(blk, host, dt, stream)
+        e3.record(stream)
+    stream.synchronize()
+    barrier()
+    ms_e2e = e2.elapsed_time(e3)
+    t = torch.tensor([ms_e2e], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = world * zones * args.steps / (float(t.item()) * 1e-3)
+
+    # roofline of the dominant kernel (largest share of the timed region)
+    kern = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(kern, key=lambda k: kern[k][0])
+    dom_ms, dom_n = kern[dom]
+    n = N_INT
+    units = {"flux_x": (n + 1) * (n + 2) ** 2, "flux_y": (n + 1) * (n + 2) ** 2, "flux_z": (n + 1) * (n + 2) ** 2,
+             "c2p": (n + 6) ** 3, "fofc_flag": n ** 3, "update": n ** 3, "emf": 3 * (n + 1) ** 2 * n,
+             "fofc_fix": max(stats["fofc_faces"] / max(kern.get("fofc_fix", (0, 1))[1], 1), 1.0)}
+    key = "flux" if dom.startswith("flux") else dom
+    flops = FLOPS_PER_UNIT.get(key, 0.0) * units.get(dom, 0)
+    achieved = flops / (dom_ms / dom_n * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": dom,
+                "peak_source": "nominal FP64 1.25 TFLOP/s (recipe unit table); FP64 is not in MEASURED_PEAKS.json"}
+    shares = {k: round(v[0] / sum(x[0] for x in kern.values()), 4) for k, v in kern.items()}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME(), "interior": [n, n, n], "ghosts": NG, "zones_per_gpu": zones,
+                       "parallelism": f"replicas{world}", "l2": "working set ~1 GB > 129 MB L2, no flush",
+                       "rk": "SSP-RK3", "recon": "WENO-Z", "riemann": "HLLE", "fofc": True, "ct": "upwind"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches), "roofline": roofline, "kernel_share": shares,
+            "c2p_stats": stats, "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_baseline:
+        line["cpu_baseline"] = oracle_sample()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    ctx.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=128, help="interior cells per side (profiling cases only)")
+    ap.add_argument("--no-baseline", action="store_true", help="skip the CPU-oracle leg (profiling cases)")
+    args = ap.parse_args()
+    global N_INT
+    N_INT = args.n
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,178 @@
+/*
+ * libgrmhd — GB300 (sm_103a) Valencia GRMHD meshblock right-hand side and
+ * update in a 3+1 metric, after arXiv:2409.10384 (AthenaK, Sec. 2-3).
+ *
+ * All state arrays are caller-owned DEVICE memory (e.g. torch tensors), FP64,
+ * structure-of-arrays, ghost-inclusive, index [var][k][j][i] with i fastest:
+ *   N_d = n_d + 2*ng,  cell (k,j,i) at offset (k*N2 + j)*N1 + i.
+ * Face arrays hold the densitised field B~ = sqrt(gamma) B on the low face of
+ * each index: x [N3][N2][N1+1], y [N3][N2+1][N1], z [N3+1][N2][N1].
+ * Edge arrays (vector potential in mhd_init_block): A_x at (i, j-1/2, k-1/2)
+ * [N3+1][N2+1][N1], A_y at (i-1/2, j, k-1/2) [N3+1][N2][N1+1], A_z at
+ * (i-1/2, j-1/2, k) [N3][N2+1][N1+1].
+ *
+ * Errors: every entry point returns 0 on success or a negative MHD_E* code;
+ * mhd_strerror() names it.  Per-cell con2prim failures are not errors: they
+ * set flag bits and count in mhd_stats (the FOFC of Sec. 3.3 consumes them).
+ * Calls are asynchronous on the given cudaStream_t (passed as void*; NULL =
+ * legacy default stream) unless stated otherwise.  No call allocates device
+ * memory except mhd_init (context), the first call that sees a new block list
+ * (scratch sized for it) and mhd_mlp_train (training buffers).
+ */
+#ifndef GRMHD_H
+#define GRMHD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mhd_ctx mhd_ctx; /* opaque; owns scratch only, never state */
+
+/* Error codes. */
+#define MHD_OK 0
+#define MHD_EINVAL (-1)    /* bad argument (NULL pointer, size, parameter) */
+#define MHD_ECUDA (-2)     /* a CUDA runtime call failed */
+#define MHD_ENOMEM (-3)    /* scratch allocation failed */
+#define MHD_ESTATE (-4)    /* call out of order (e.g. rk_update before rhs) */
+#define MHD_ENOMLP (-5)    /* learned guess requested but no network loaded */
+
+/* Per-cell flag bits written to mhd_block.flags (and mhd_c2p_cells). */
+#define MHD_F_FAIL 1u      /* root solve failed: cell reset to atmosphere */
+#define MHD_F_DFLOOR 2u    /* D < f_thr*rho_atm before the solve (Sec. 3.3) */
+#define MHD_F_SIGMA 4u     /* B^2/D cap applied (Sec. 3.3) */
+#define MHD_F_TAU 8u       /* tau < tau_atm(D,B) (Sec. 3.3) */
+#define MHD_F_RHO 16u      /* rho < f_thr*rho_atm after the solve */
+#define MHD_F_TEMP 32u     /* temperature floor T_atm */
+#define MHD_F_VMAX 64u     /* Lorentz-factor cap W_max active */
+#define MHD_F_FOFC 128u    /* FOFC recomputed this cell's faces (Sec. 3.3) */
+
+/* Method parameters (Sec. 3.2-3.4).  Units G = c = 1, m_b = 1: T = P/rho. */
+typedef struct {
+  double gamma;     /* ideal-gas index, P = (gamma-1) rho eps (Sec. 3.4) */
+  double rho_atm;   /* atmosphere density (Sec. 3.3) */
+  double T_atm;     /* atmosphere temperature (Sec. 3.3) */
+  double f_thr;     /* floor threshold factor: rho < f_thr*rho_atm (Sec. 3.3) */
+  double sigma_max; /* cap on B^2/D; <= 0 disables (Sec. 3.3) */
+  double dmp_M;     /* relaxed DMP factor M >= 1 (Eq. 19); <= 0 disables */
+  double c2p_tol;   /* relative width of the final root bracket (1e-10) */
+  double W_max;     /* Lorentz-factor cap of the root solve (1e3) */
+  int recon;        /* 0 donor cell, 1 PLM (van Leer), 2 WENO-Z (Sec. 3.2) */
+  int rsolver;      /* 0 LLF, 1 HLLE (Sec. 3.2) */
+  int fofc;         /* 1: first-order flux correction (Sec. 3.3) */
+  int rk_order;     /* 2 or 3: SSP-RK (Sec. 3.2) */
+  int c2p_maxit;    /* cap on root-solve iterations (64) */
+  int c2p_guess;    /* 0 plain bracket, 1 learned bracket (needs a network) */
+} mhd_params;
+
+/* One meshblock: views into caller-owned device arrays. */
+typedef struct {
+  int n[3];            /* interior cells (x, y, z); each >= 1 */
+  int ng;              /* ghost cells per side; must be >= 4 */
+  double dx[3];        /* cell widths */
+  double* cons;        /* [5] D~, S~_1, S~_2, S~_3, tau~ (Eq. 6, densitised) */
+  double* cons0;       /* [5] U^n of the RK step; written by stage 0 */
+  double* prim;        /* [5] rho, w^i = W v^i, P; written by mhd_c2p */
+  double* bf[3];       /* face B~ (layout above) */
+  double* bf0[3];      /* face B~ at t^n; written by stage 0 */
+  double* bcc;         /* [3] cell-centred B~ (face average); written by mhd_c2p */
+  const double* adm;   /* [16] alpha, beta^1..3, gamma_11,12,13,22,23,33, K_11..K_33 (Eq. 5, 9) */
+  unsigned char* flags;/* [N3][N2][N1] MHD_F_* bits */
+} mhd_block;
+
+/* Counters accumulated on the device since the last mhd_reset_stats. */
+typedef struct {
+  long long cells;      /* con2prim solves on stage inputs */
+  long long iters;      /* summed root iterations of those solves */
+  long long fails;      /* failures (MHD_F_FAIL) */
+  long long floors;     /* cells where a floor fired */
+  long long fofc_cells; /* cells flagged by FOFC (incl. DMP) */
+  long long dmp_cells;  /* cells flagged by the DMP test */
+  long long fofc_faces; /* faces recomputed at first order */
+} mhd_stats;
+
+/* Create a context on the current device.  *out receives it.  Copies p. */
+int mhd_init(const mhd_params* p, mhd_ctx** out);
+/* Replace the parameters (validated as in mhd_init). */
+int mhd_set_params(mhd_ctx* ctx, const mhd_params* p);
+/* Free the context and all its scratch (synchronises the device). */
+void mhd_finalize(mhd_ctx* ctx);
+const char* mhd_strerror(int code);
+
+/* Initial data: face B~ = discrete curl of the edge potential A (so div B~ = 0
+ * to round-off, Sec. 4.3), bcc = face average, cons = Eq. 6 of blk->prim on
+ * every cell.  A[c] are device arrays in the edge layout above. */
+int mhd_init_block(mhd_ctx* ctx, mhd_block* blk, const double* const A[3], void* stream);
+
+/* Eq. 6 on n independent cells: prim [5][n], Bd [3][n] (densitised),
+ * g [6][n] (gamma_ij) -> cons [5][n].  Device pointers. */
+int mhd_prim2cons(mhd_ctx* ctx, long n, const double* prim, const double* Bd, const double* g, double* cons,
+                  void* stream);
+
+/* con2prim (Sec. 3.4, Kastaun et al. 2021 bracketed root) with the atmosphere
+ * floors of Sec. 3.3 on n independent cells.  cons [5][n] is overwritten where
+ * a floor changed it; prim [5][n] and flags [n] are written; iters [n] (may be
+ * NULL) receives the root iterations.  Device pointers. */
+int mhd_c2p_cells(mhd_ctx* ctx, long n, double* cons, const double* Bd, const double* g, double* prim,
+                  unsigned char* flags, int* iters, void* stream);
+
+/* con2prim of every cell within 3 of the interior of each block (the stencil
+ * region of WENO-Z), with bcc and the cell-centred EMF; floors write back to
+ * cons.  This is step 1 of a stage. */
+int mhd_c2p(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, void* stream);
+
+/* Steps 2-4 of stage `stage` (0-based) with time step dt: reconstruction and
+ * Riemann fluxes (Eq. 8) on every face the update needs, FOFC (+DMP) and the
+ * upwind-CT edge EMFs, all into context scratch.  Requires mhd_c2p. */
+int mhd_rhs(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, double dt, int stage, void* stream);
+
+/* Step 5: U <- g0 U^n + g1 U + b dt (-div F + G) (Eq. 9 sources), face B~ <-
+ * g0 B^n + g1 B - b dt curl E, with the SSP-RK weights of `stage`.  Stage 0
+ * also stores U and face B~ as U^n.  Requires mhd_rhs on the same blocks. */
+int mhd_rk_update(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, double dt, int stage, void* stream);
+
+/* A full RK step (rk_order stages of c2p, rhs, update).  Ghost zones are not
+ * refreshed between stages (they keep their values).  With graph != 0 the
+ * launches are captured once into a CUDA graph per (block list, dt) and
+ * replayed. */
+int mhd_step(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, double dt, int graph, void* stream);
+
+/* Copy the counters to *out (synchronises the stream) / zero them. */
+int mhd_read_stats(mhd_ctx* ctx, mhd_stats* out, void* stream);
+int mhd_reset_stats(mhd_ctx* ctx, void* stream);
+
+/* Copy a scratch array of block b of the last block list into dst (device or
+ * host memory, count elements; count must equal the array size, which
+ * count == 0 queries into *size).  which = 0..2: face fluxes of direction
+ * x, y, z ([7][face array]: D~, S~_1..3, tau~, then B~ of the transverse
+ * directions (d+1)%3 and (d+2)%3); 3..5: edge EMFs E_x, E_y, E_z (edge layout
+ * above).  Synchronises the stream. */
+int mhd_scratch_copy(mhd_ctx* ctx, int b, int which, double* dst, long count, long* size, void* stream);
+
+/* Kernel launches this context has issued so far (a graph replay counts the
+ * kernels it contains). */
+long long mhd_kernel_launches(const mhd_ctx* ctx);
+
+/* Kernel kinds for per-kernel timing. */
+#define MHD_K_C2P 0        /* con2prim of the stencil region */
+#define MHD_K_FLUX_X 1     /* reconstruction + Riemann flux, x faces */
+#define MHD_K_FLUX_Y 2
+#define MHD_K_FLUX_Z 3
+#define MHD_K_FOFC_FLAG 4  /* FOFC estimate, con2prim of U*, DMP */
+#define MHD_K_FOFC_FIX 5   /* first-order recompute of flagged faces */
+#define MHD_K_EMF 6        /* upwind CT edge EMFs */
+#define MHD_K_UPDATE 7     /* RK update of U with the Eq. 9 sources */
+#define MHD_K_FACEB 8      /* RK update of the face B~ */
+#define MHD_NKERNEL 9
+
+/* enable != 0: bracket every kernel launched outside stream capture by CUDA
+ * events on its own stream.  mhd_profile_read waits for them and returns, per
+ * kind, the summed milliseconds (ms[MHD_NKERNEL]) and launch counts
+ * (count[MHD_NKERNEL]) since the previous read. */
+int mhd_profile(mhd_ctx* ctx, int enable);
+int mhd_profile_read(mhd_ctx* ctx, double* ms, long long* count);
+const char* mhd_kernel_name(int kind);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRMHD_H */

@@ -104,6 +104,8 @@ def lib(counting: bool = False):
             L.or_flop_counts.argtypes = [C.POINTER(C.c_longlong)]
             L.or_flop_counts.restype = C.c_int
             L.or_flop_reset.argtypes = []
+            L.or_flop_phases.argtypes = [C.POINTER(C.c_longlong)]
+            L.or_flop_phases.restype = C.c_int
             _LIBS[counting] = L
             del dp
         return _LIBS[counting]
@@ -286,6 +288,27 @@ def step(p: Params, b: Block, dt: float, fill=None) -> list:
             fill(b)
         stats.append(stage(p, b, dt, s))
     return stats
+
+
+PHASES = ("c2p", "flux", "fofc_flag", "fofc_fix", "emf", "update")
+
+
+def flop_phases(p: Params, b: Block, dt: float, stage_idx: int) -> dict:
+    """Algorithmic FP64 operations of each phase of one stage (counting build):
+    {phase: {add, mul, div, sqrt, cmp}} plus the stage stats."""
+    L = lib(True)
+    L.or_flop_reset()
+    st = stage(p, b.copy(), dt, stage_idx, counting=True)
+    out = (C.c_longlong * 30)()
+    L.or_flop_phases(out)
+    cum = [[int(out[5 * k + m]) for m in range(5)] for k in range(6)]
+    res = {}
+    prev = [0] * 5
+    for k, name in enumerate(PHASES):
+        res[name] = dict(zip(("add", "mul", "div", "sqrt", "cmp"), (cum[k][m] - prev[m] for m in range(5))))
+        prev = cum[k]
+    res["stats"] = st
+    return res
 
 
 def flop_counts(p: Params, b: Block, dt: float, stage_idx: int) -> dict:

@@ -38,6 +38,10 @@
 #ifdef ORACLE_COUNT_FLOPS
 struct FlopCounts { long long add, mul, div, sqrt, cmp; };
 static FlopCounts g_fc = {0, 0, 0, 0, 0};
+// cumulative counts at the end of each stage phase: c2p, fluxes, FOFC flag,
+// FOFC recompute, CT EMFs, update
+static FlopCounts g_phase[6];
+#define PHASE(k) (g_phase[k] = g_fc)
 struct real {
   double v;
   real() : v(0.0) {}
@@ -64,6 +68,7 @@ typedef double real;
 static inline real sqrt_(real a) { return std::sqrt(a); }
 static inline double val(real a) { return a; }
 static inline bool finite_(real a) { return std::isfinite(a); }
+#define PHASE(k) ((void)0)
 #endif
 
 static inline real abs_(real a) { return a < 0.0 ? -a : a; }
@@ -785,6 +790,7 @@ static void fofc(Ctx& C, std::vector<double> flux[3], double g0, double g1, doub
           nf++;
         }
       }
+  PHASE(2);
   long long nfaces = 0;
   for (int d = 0; d < 3; d++) {
     int lo[3], hi[3];
@@ -1193,18 +1199,24 @@ int or_stage(or_block* b, const or_params* p, double dt, int stage, or_stats* st
   stage_weights(p->rk_order, stage, &g0, &g1, &be);
   compute_bcc(C);
   c2p_region(C, st);
+  PHASE(0);
   std::vector<double> flux[3];
   compute_fluxes(C, flux);
+  PHASE(1);
   if (p->fofc) fofc(C, flux, g0, g1, be * dt, st);
+  else PHASE(2);
+  PHASE(3);
   std::vector<double> ecc, emf[3];
   compute_ecc(C, ecc);
   compute_emf(C, flux, ecc, emf);
+  PHASE(4);
   Grid& G = C.G;
   for (int d = 0; d < 3; d++) {
     if (b->flux[d]) std::memcpy(b->flux[d], flux[d].data(), sizeof(double) * 7 * G.nface(d));
     if (b->emf[d]) std::memcpy(b->emf[d], emf[d].data(), sizeof(double) * G.nedge(d));
   }
   update(C, flux, emf, g0, g1, be * dt);
+  PHASE(5);
   return 0;
 }
 
@@ -1279,6 +1291,21 @@ int or_flop_counts(long long* out) {
   return 1;
 #else
   for (int i = 0; i < 5; i++) out[i] = 0;
+  return 0;
+#endif
+}
+// cumulative counts at the end of each phase of the last stage:
+// out[6][5] = {add, mul, div, sqrt, cmp} after c2p, fluxes, FOFC flag, FOFC
+// recompute, CT, update.  Returns 1 in the counting build, else 0.
+int or_flop_phases(long long* out) {
+#ifdef ORACLE_COUNT_FLOPS
+  for (int k = 0; k < 6; k++) {
+    out[5 * k + 0] = g_phase[k].add; out[5 * k + 1] = g_phase[k].mul; out[5 * k + 2] = g_phase[k].div;
+    out[5 * k + 3] = g_phase[k].sqrt; out[5 * k + 4] = g_phase[k].cmp;
+  }
+  return 1;
+#else
+  for (int i = 0; i < 30; i++) out[i] = 0;
   return 0;
 #endif
 }

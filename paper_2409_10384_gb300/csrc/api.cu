@@ -1,0 +1,535 @@
+// C-ABI of libgrmhd: context, block lists, scratch, launch sequencing and the
+// CUDA-graph step.  Declarations and argument conventions: include/grmhd.h.
+#include <cstring>
+#include <vector>
+
+#include "grmhd.h"
+#include "internal.h"
+
+using namespace grmhd;
+
+struct mhd_ctx {
+  mhd_params hp;
+  Par P;
+  int dev = 0, nsm = 1;
+  int occ_c2p[2] = {1, 1}, occ_face[5] = {1, 1, 1, 1, 1}, occ_upd[3] = {1, 1, 1};
+  // current block list
+  std::vector<mhd_block> key;
+  std::vector<DevBlock> hblk;
+  std::vector<long long> hpre;
+  DevBlock* dblk = nullptr;
+  long long* dpre = nullptr;
+  char* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  long long list_version = 0;
+  int grid[W_NKIND] = {0};
+  // counters
+  unsigned long long* dstats = nullptr;
+  long long launches = 0;
+  // rhs/update ordering
+  long long rhs_list = -1;
+  int rhs_stage = -1;
+  // graph cache
+  cudaGraphExec_t gexec = nullptr;
+  long long g_list = -1, g_par = -1;
+  double g_dt = 0.0;
+  cudaStream_t g_stream = nullptr;
+  long long par_version = 0;
+  int g_launches = 0;
+  // per-kernel CUDA-event timing of non-captured launches
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Rec { int kind; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  double prof_ms[MHD_NKERNEL] = {0};
+  long long prof_n[MHD_NKERNEL] = {0};
+};
+
+namespace {
+
+int set_par(mhd_ctx* c, const mhd_params* p) {
+  if (!p) return MHD_EINVAL;
+  if (!(p->gamma > 1.0) || !(p->rho_atm > 0.0) || !(p->T_atm > 0.0) || !(p->f_thr >= 0.0) || !(p->c2p_tol > 0.0) ||
+      !(p->W_max > 1.0) || p->recon < 0 || p->recon > 2 || p->rsolver < 0 || p->rsolver > 1 ||
+      (p->rk_order != 2 && p->rk_order != 3) || p->c2p_maxit < 1 || p->c2p_guess < 0 || p->c2p_guess > 1 ||
+      (p->dmp_M > 0.0 && p->dmp_M < 1.0))
+    return MHD_EINVAL;
+  c->hp = *p;
+  Par& P = c->P;
+  P.gam = p->gamma;
+  P.gm1 = p->gamma - 1.0;
+  P.gfac = p->gamma / (p->gamma - 1.0);
+  P.rho_atm = p->rho_atm;
+  P.T_atm = p->T_atm;
+  P.rho_thr = p->f_thr * p->rho_atm;
+  P.eps_atm = p->T_atm / (p->gamma - 1.0);
+  P.P_atm = p->rho_atm * p->T_atm;
+  P.sigma_max = p->sigma_max;
+  P.dmp_M = p->dmp_M;
+  P.tol = p->c2p_tol;
+  P.vmax2 = 1.0 - 1.0 / (p->W_max * p->W_max);
+  P.recon = p->recon;
+  P.rsolver = p->rsolver;
+  P.fofc = p->fofc ? 1 : 0;
+  P.rk_order = p->rk_order;
+  P.maxit = p->c2p_maxit;
+  P.guess = p->c2p_guess;
+  c->par_version++;
+  return MHD_OK;
+}
+
+inline int cuda_ok(cudaError_t e) { return e == cudaSuccess ? MHD_OK : MHD_ECUDA; }
+
+long long ncell_of(const mhd_block& b) {
+  return (long long)(b.n[0] + 2 * b.ng) * (b.n[1] + 2 * b.ng) * (b.n[2] + 2 * b.ng);
+}
+
+int check_block(const mhd_block& b) {
+  if (b.n[0] < 1 || b.n[1] < 1 || b.n[2] < 1 || b.ng < 4) return MHD_EINVAL;
+  if (!b.cons || !b.cons0 || !b.prim || !b.bcc || !b.adm || !b.flags) return MHD_EINVAL;
+  for (int d = 0; d < 3; d++)
+    if (!b.bf[d] || !b.bf0[d] || !(b.dx[d] > 0.0)) return MHD_EINVAL;
+  return MHD_OK;
+}
+
+void destroy_graph(mhd_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+  c->g_list = -1;
+}
+
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Upload a new block list (descriptors, work prefix sums) and size scratch.
+int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
+  if (!blocks || nb < 1) return MHD_EINVAL;
+  if ((int)c->key.size() == nb && std::memcmp(c->key.data(), blocks, sizeof(mhd_block) * nb) == 0) return MHD_OK;
+  for (int i = 0; i < nb; i++) {
+    int r = check_block(blocks[i]);
+    if (r) return r;
+  }
+  destroy_graph(c);
+  cudaDeviceSynchronize();
+  std::vector<DevBlock> hb(nb);
+  std::vector<long long> pre((size_t)W_NKIND * (nb + 1), 0);
+  size_t need = 0;
+  for (int i = 0; i < nb; i++) {
+    const mhd_block& s = blocks[i];
+    DevBlock& b = hb[i];
+    std::memset(&b, 0, sizeof(b));
+    for (int d = 0; d < 3; d++) {
+      b.n[d] = s.n[d];
+      b.N[d] = s.n[d] + 2 * s.ng;
+      b.dx[d] = s.dx[d];
+      b.idx[d] = 1.0 / s.dx[d];
+      b.bf[d] = s.bf[d];
+      b.bf0[d] = s.bf0[d];
+    }
+    b.ng = s.ng;
+    b.ncell = ncell_of(s);
+    b.cons = s.cons; b.cons0 = s.cons0; b.prim = s.prim; b.bcc = s.bcc; b.adm = s.adm; b.flags = s.flags;
+    const long long N0 = b.N[0], N1 = b.N[1], N2 = b.N[2];
+    const long long nf[3] = {N2 * N1 * (N0 + 1), N2 * (N1 + 1) * N0, (N2 + 1) * N1 * N0};
+    const long long ne[3] = {(N2 + 1) * (N1 + 1) * N0, (N2 + 1) * N1 * (N0 + 1), N2 * (N1 + 1) * (N0 + 1)};
+    need += al256(sizeof(double) * 7 * (nf[0] + nf[1] + nf[2]));
+    need += al256(sizeof(double) * (ne[0] + ne[1] + ne[2]));
+    need += al256(sizeof(double) * 3 * b.ncell);
+    need += al256((size_t)b.ncell);
+    const long long n0 = s.n[0], n1 = s.n[1], n2 = s.n[2];
+    long long items[W_NKIND];
+    items[W_C2P] = (n0 + 6) * (n1 + 6) * (n2 + 6);
+    items[W_FX] = (n0 + 1) * (n1 + 2) * (n2 + 2);
+    items[W_FY] = (n0 + 2) * (n1 + 1) * (n2 + 2);
+    items[W_FZ] = (n0 + 2) * (n1 + 2) * (n2 + 1);
+    items[W_CELL] = n0 * n1 * n2;
+    items[W_EDGE] = (n0 + 1) * (n1 + 1) * (n2 + 1);
+    items[W_FACE] = (n0 + 1) * n1 * n2 + n0 * (n1 + 1) * n2 + n0 * n1 * (n2 + 1);
+    items[W_INIT] = b.ncell;
+    for (int k = 0; k < W_NKIND; k++) pre[(size_t)k * (nb + 1) + i + 1] = pre[(size_t)k * (nb + 1) + i] + items[k];
+  }
+  if (need > c->scratch_bytes) {
+    if (c->scratch) cudaFree(c->scratch);
+    c->scratch = nullptr;
+    c->scratch_bytes = 0;
+    if (cudaMalloc(&c->scratch, need) != cudaSuccess) return MHD_ENOMEM;
+    c->scratch_bytes = need;
+  }
+  char* p = c->scratch;
+  for (int i = 0; i < nb; i++) {
+    DevBlock& b = hb[i];
+    const long long N0 = b.N[0], N1 = b.N[1], N2 = b.N[2];
+    const long long nf[3] = {N2 * N1 * (N0 + 1), N2 * (N1 + 1) * N0, (N2 + 1) * N1 * N0};
+    const long long ne[3] = {(N2 + 1) * (N1 + 1) * N0, (N2 + 1) * N1 * (N0 + 1), N2 * (N1 + 1) * (N0 + 1)};
+    double* f = (double*)p;
+    b.flux[0] = f;
+    b.flux[1] = f + 7 * nf[0];
+    b.flux[2] = f + 7 * (nf[0] + nf[1]);
+    p += al256(sizeof(double) * 7 * (nf[0] + nf[1] + nf[2]));
+    double* e = (double*)p;
+    b.emf[0] = e;
+    b.emf[1] = e + ne[0];
+    b.emf[2] = e + ne[0] + ne[1];
+    p += al256(sizeof(double) * (ne[0] + ne[1] + ne[2]));
+    b.ecc = (double*)p;
+    p += al256(sizeof(double) * 3 * b.ncell);
+    b.fflag = (unsigned char*)p;
+    p += al256((size_t)b.ncell);
+  }
+  if (c->dblk) cudaFree(c->dblk);
+  if (c->dpre) cudaFree(c->dpre);
+  c->dblk = nullptr;
+  c->dpre = nullptr;
+  if (cudaMalloc(&c->dblk, sizeof(DevBlock) * nb) != cudaSuccess) return MHD_ENOMEM;
+  if (cudaMalloc(&c->dpre, sizeof(long long) * pre.size()) != cudaSuccess) return MHD_ENOMEM;
+  if (cudaMemcpy(c->dblk, hb.data(), sizeof(DevBlock) * nb, cudaMemcpyHostToDevice) != cudaSuccess) return MHD_ECUDA;
+  if (cudaMemcpy(c->dpre, pre.data(), sizeof(long long) * pre.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return MHD_ECUDA;
+  c->hblk = hb;
+  c->hpre = pre;
+  c->key.assign(blocks, blocks + nb);
+  c->list_version++;
+  c->rhs_list = -1;
+  // grid sizes: one wave of resident CTAs, capped by the work
+  auto grid_of = [&](int kind, int threads, int occ) {
+    long long tot = pre[(size_t)kind * (nb + 1) + nb];
+    long long g = (tot + threads - 1) / threads;
+    long long cap = (long long)c->nsm * (occ > 0 ? occ : 1);
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+  };
+  c->grid[W_C2P] = grid_of(W_C2P, 128, c->occ_c2p[1]);
+  c->grid[W_FX] = grid_of(W_FX, 128, c->occ_face[0]);
+  c->grid[W_FY] = grid_of(W_FY, 128, c->occ_face[1]);
+  c->grid[W_FZ] = grid_of(W_FZ, 128, c->occ_face[2]);
+  c->grid[W_CELL] = grid_of(W_CELL, 128, c->occ_face[3]);
+  c->grid[W_EDGE] = grid_of(W_EDGE, 128, c->occ_upd[0]);
+  c->grid[W_FACE] = grid_of(W_FACE, 256, c->occ_upd[2]);
+  c->grid[W_INIT] = grid_of(W_CELL, 128, c->occ_upd[1]);
+  return MHD_OK;
+}
+
+cudaEvent_t get_event(mhd_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
+  return st != cudaStreamCaptureStatusNone;
+}
+
+// Launch one kernel, bracketed by CUDA events on its stream when profiling.
+template <class F>
+void timed(mhd_ctx* c, int kind, cudaStream_t s, F&& launch) {
+  const bool on = c->prof && !capturing(s);
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (on) {
+    a = get_event(c);
+    b = get_event(c);
+    cudaEventRecord(a, s);
+  }
+  launch();
+  c->launches += 1;
+  if (on) {
+    cudaEventRecord(b, s);
+    c->recs.push_back({kind, a, b});
+  }
+}
+
+Work work_of(const mhd_ctx* c) {
+  Work w;
+  w.blk = c->dblk;
+  w.pre = c->dpre;
+  w.nblocks = (int)c->key.size();
+  return w;
+}
+
+int enqueue_c2p(mhd_ctx* c, cudaStream_t s) {
+  Work w = work_of(c);
+  timed(c, MHD_K_C2P, s, [&] { launch_c2p_block(w, c->P, c->dstats, s, c->grid[W_C2P]); });
+  return cuda_ok(cudaGetLastError());
+}
+
+int enqueue_rhs(mhd_ctx* c, double dt, int stage, cudaStream_t s) {
+  double g0, g1, be;
+  rk_weights(c->P.rk_order, stage, g0, g1, be);
+  Work w = work_of(c);
+  const int gf[3] = {c->grid[W_FX], c->grid[W_FY], c->grid[W_FZ]};
+  for (int d = 0; d < 3; d++)
+    timed(c, MHD_K_FLUX_X + d, s, [&] { launch_flux_dir(d, w, c->P, s, gf[d]); });
+  if (c->P.fofc) {
+    timed(c, MHD_K_FOFC_FLAG, s, [&] { launch_fofc_flag(w, c->P, g0, g1, be * dt, c->dstats, s, c->grid[W_CELL]); });
+    for (int d = 0; d < 3; d++)
+      timed(c, MHD_K_FOFC_FIX, s, [&] { launch_fofc_fix(d, w, c->P, c->dstats, s, gf[d]); });
+  }
+  timed(c, MHD_K_EMF, s, [&] { launch_emf(w, s, c->grid[W_EDGE]); });
+  c->rhs_list = c->list_version;
+  c->rhs_stage = stage;
+  return cuda_ok(cudaGetLastError());
+}
+
+int enqueue_update(mhd_ctx* c, double dt, int stage, cudaStream_t s) {
+  double g0, g1, be;
+  rk_weights(c->P.rk_order, stage, g0, g1, be);
+  Work w = work_of(c);
+  const int first = stage == 0 ? 1 : 0;
+  timed(c, MHD_K_UPDATE, s, [&] { launch_update_cells(w, c->P, g0, g1, be * dt, first, s, c->grid[W_INIT]); });
+  timed(c, MHD_K_FACEB, s, [&] { launch_update_faces(w, g0, g1, be * dt, first, s, c->grid[W_FACE]); });
+  return cuda_ok(cudaGetLastError());
+}
+
+int enqueue_step(mhd_ctx* c, double dt, cudaStream_t s) {
+  for (int st = 0; st < c->P.rk_order; st++) {
+    int r = enqueue_c2p(c, s);
+    if (!r) r = enqueue_rhs(c, dt, st, s);
+    if (!r) r = enqueue_update(c, dt, st, s);
+    if (r) return r;
+  }
+  return MHD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mhd_init(const mhd_params* p, mhd_ctx** out) {
+  if (!out || !p) return MHD_EINVAL;
+  *out = nullptr;
+  mhd_ctx* c = new mhd_ctx();
+  int r = set_par(c, p);
+  if (r) { delete c; return r; }
+  if (cudaGetDevice(&c->dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess) {
+    delete c;
+    return MHD_ECUDA;
+  }
+  if (occupancy_c2p(c->occ_c2p) || occupancy_face(c->occ_face) || occupancy_update(c->occ_upd)) {
+    delete c;
+    return MHD_ECUDA;
+  }
+  if (cudaMalloc(&c->dstats, sizeof(unsigned long long) * 8) != cudaSuccess) {
+    delete c;
+    return MHD_ENOMEM;
+  }
+  if (cudaMemset(c->dstats, 0, sizeof(unsigned long long) * 8) != cudaSuccess) {
+    cudaFree(c->dstats);
+    delete c;
+    return MHD_ECUDA;
+  }
+  *out = c;
+  return MHD_OK;
+}
+
+int mhd_set_params(mhd_ctx* c, const mhd_params* p) {
+  if (!c) return MHD_EINVAL;
+  int r = set_par(c, p);
+  if (!r) destroy_graph(c);
+  return r;
+}
+
+void mhd_finalize(mhd_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  destroy_graph(c);
+  if (c->scratch) cudaFree(c->scratch);
+  if (c->dblk) cudaFree(c->dblk);
+  if (c->dpre) cudaFree(c->dpre);
+  if (c->dstats) cudaFree(c->dstats);
+  for (auto& r : c->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+}
+
+const char* mhd_strerror(int code) {
+  switch (code) {
+    case MHD_OK: return "ok";
+    case MHD_EINVAL: return "invalid argument";
+    case MHD_ECUDA: return "CUDA runtime error";
+    case MHD_ENOMEM: return "device allocation failed";
+    case MHD_ESTATE: return "call out of order";
+    case MHD_ENOMLP: return "learned guess requested but no network loaded";
+    default: return "unknown error";
+  }
+}
+
+int mhd_init_block(mhd_ctx* c, mhd_block* blk, const double* const A[3], void* stream) {
+  if (!c || !blk || !A || !A[0] || !A[1] || !A[2]) return MHD_EINVAL;
+  int r = check_block(*blk);
+  if (r) return r;
+  DevBlock b;
+  std::memset(&b, 0, sizeof(b));
+  for (int d = 0; d < 3; d++) {
+    b.n[d] = blk->n[d];
+    b.N[d] = blk->n[d] + 2 * blk->ng;
+    b.dx[d] = blk->dx[d];
+    b.idx[d] = 1.0 / blk->dx[d];
+    b.bf[d] = blk->bf[d];
+  }
+  b.ng = blk->ng;
+  b.ncell = ncell_of(*blk);
+  b.cons = blk->cons; b.prim = blk->prim; b.bcc = blk->bcc; b.adm = blk->adm;
+  launch_init_block(b, c->P, A, (cudaStream_t)stream, c->nsm);
+  c->launches += 2;
+  return cuda_ok(cudaGetLastError());
+}
+
+int mhd_prim2cons(mhd_ctx* c, long n, const double* prim, const double* Bd, const double* g, double* cons,
+                  void* stream) {
+  if (!c || n < 0 || (n > 0 && (!prim || !Bd || !g || !cons))) return MHD_EINVAL;
+  if (n == 0) return MHD_OK;
+  launch_p2c_cells(c->P, n, prim, Bd, g, cons, (cudaStream_t)stream, c->nsm);
+  c->launches += 1;
+  return cuda_ok(cudaGetLastError());
+}
+
+int mhd_c2p_cells(mhd_ctx* c, long n, double* cons, const double* Bd, const double* g, double* prim,
+                  unsigned char* flags, int* iters, void* stream) {
+  if (!c || n < 0 || (n > 0 && (!cons || !Bd || !g || !prim || !flags))) return MHD_EINVAL;
+  if (n == 0) return MHD_OK;
+  long long nb = (n + 127) / 128;
+  long long cap = (long long)c->nsm * c->occ_c2p[0];
+  int grid = (int)(nb < cap ? nb : cap);
+  launch_c2p_cells(c->P, n, cons, Bd, g, prim, flags, iters, nullptr, c->dstats, (cudaStream_t)stream, grid);
+  c->launches += 1;
+  return cuda_ok(cudaGetLastError());
+}
+
+int mhd_c2p(mhd_ctx* c, const mhd_block* blocks, int nb, void* stream) {
+  if (!c) return MHD_EINVAL;
+  int r = prepare(c, blocks, nb);
+  if (r) return r;
+  return enqueue_c2p(c, (cudaStream_t)stream);
+}
+
+int mhd_rhs(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, int stage, void* stream) {
+  if (!c || !(dt > 0.0) || stage < 0 || stage >= c->P.rk_order) return MHD_EINVAL;
+  int r = prepare(c, blocks, nb);
+  if (r) return r;
+  return enqueue_rhs(c, dt, stage, (cudaStream_t)stream);
+}
+
+int mhd_rk_update(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, int stage, void* stream) {
+  if (!c || !(dt > 0.0) || stage < 0 || stage >= c->P.rk_order) return MHD_EINVAL;
+  int r = prepare(c, blocks, nb);
+  if (r) return r;
+  if (c->rhs_list != c->list_version || c->rhs_stage != stage) return MHD_ESTATE;
+  r = enqueue_update(c, dt, stage, (cudaStream_t)stream);
+  c->rhs_list = -1;
+  return r;
+}
+
+int mhd_step(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, int graph, void* stream) {
+  if (!c || !(dt > 0.0)) return MHD_EINVAL;
+  int r = prepare(c, blocks, nb);
+  if (r) return r;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!graph) return enqueue_step(c, dt, s);
+  if (!s) return MHD_EINVAL;  // the legacy default stream cannot be captured
+  if (!(c->gexec && c->g_list == c->list_version && c->g_par == c->par_version && c->g_dt == dt && c->g_stream == s)) {
+    destroy_graph(c);
+    long long before = c->launches;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MHD_ECUDA;
+    int er = enqueue_step(c, dt, s);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(s, &g);
+    if (er || ce != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return er ? er : MHD_ECUDA;
+    }
+    ce = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) { c->gexec = nullptr; return MHD_ECUDA; }
+    c->g_launches = (int)(c->launches - before);
+    c->launches = before;
+    c->g_list = c->list_version;
+    c->g_par = c->par_version;
+    c->g_dt = dt;
+    c->g_stream = s;
+  }
+  c->launches += c->g_launches;
+  return cuda_ok(cudaGraphLaunch(c->gexec, s));
+}
+
+int mhd_read_stats(mhd_ctx* c, mhd_stats* out, void* stream) {
+  if (!c || !out) return MHD_EINVAL;
+  unsigned long long h[8];
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(h, c->dstats, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ECUDA;
+  out->cells = (long long)h[0];
+  out->iters = (long long)h[1];
+  out->fails = (long long)h[2];
+  out->floors = (long long)h[3];
+  out->fofc_cells = (long long)h[4];
+  out->dmp_cells = (long long)h[5];
+  out->fofc_faces = (long long)h[6];
+  return MHD_OK;
+}
+
+int mhd_reset_stats(mhd_ctx* c, void* stream) {
+  if (!c) return MHD_EINVAL;
+  return cuda_ok(cudaMemsetAsync(c->dstats, 0, sizeof(unsigned long long) * 8, (cudaStream_t)stream));
+}
+
+int mhd_scratch_copy(mhd_ctx* c, int b, int which, double* dst, long count, long* size, void* stream) {
+  if (!c || b < 0 || b >= (int)c->hblk.size() || which < 0 || which > 5) return MHD_EINVAL;
+  const DevBlock& d = c->hblk[b];
+  const long long N0 = d.N[0], N1 = d.N[1], N2 = d.N[2];
+  const long long nf[3] = {N2 * N1 * (N0 + 1), N2 * (N1 + 1) * N0, (N2 + 1) * N1 * N0};
+  const long long ne[3] = {(N2 + 1) * (N1 + 1) * N0, (N2 + 1) * N1 * (N0 + 1), N2 * (N1 + 1) * (N0 + 1)};
+  const double* src = which < 3 ? d.flux[which] : d.emf[which - 3];
+  long n = (long)(which < 3 ? 7 * nf[which] : ne[which - 3]);
+  if (size) *size = n;
+  if (count == 0) return MHD_OK;
+  if (!dst || count != n) return MHD_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDefault, s) != cudaSuccess) return MHD_ECUDA;
+  return cuda_ok(cudaStreamSynchronize(s));
+}
+
+long long mhd_kernel_launches(const mhd_ctx* c) { return c ? c->launches : 0; }
+
+int mhd_profile(mhd_ctx* c, int enable) {
+  if (!c) return MHD_EINVAL;
+  c->prof = enable != 0;
+  return MHD_OK;
+}
+
+int mhd_profile_read(mhd_ctx* c, double* ms, long long* count) {
+  if (!c || !ms || !count) return MHD_EINVAL;
+  for (auto& r : c->recs) {
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return MHD_ECUDA;
+    float t = 0.0f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return MHD_ECUDA;
+    c->prof_ms[r.kind] += t;
+    c->prof_n[r.kind] += 1;
+    c->ev_pool.push_back(r.a);
+    c->ev_pool.push_back(r.b);
+  }
+  c->recs.clear();
+  for (int k = 0; k < MHD_NKERNEL; k++) {
+    ms[k] = c->prof_ms[k];
+    count[k] = c->prof_n[k];
+    c->prof_ms[k] = 0.0;
+    c->prof_n[k] = 0;
+  }
+  return MHD_OK;
+}
+
+const char* mhd_kernel_name(int kind) {
+  static const char* names[MHD_NKERNEL] = {"c2p", "flux_x", "flux_y", "flux_z", "fofc_flag",
+                                           "fofc_fix", "emf", "update", "faceb"};
+  return (kind >= 0 && kind < MHD_NKERNEL) ? names[kind] : "unknown";
+}
+
+}  // extern "C"

@@ -1,0 +1,503 @@
+// Device-side data structures and physics functions of libgrmhd (sm_103a).
+//
+// GB300 has a narrow FP64 pipe (about 2 DFMA per clock per SM; a double
+// divide costs ~6 DFMA slots, a square root ~10) next to a wide FP32/INT
+// pipe, so the per-cell arithmetic below is arranged to issue as few FP64
+// divides and square roots as possible: reciprocals are shared, 1/W comes from
+// rsqrt, and the con2prim root is sought on a division-free function with the
+// same sign and root as the master function of Kastaun et al. (2021).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace grmhd {
+
+enum : unsigned {
+  F_FAIL = 1u, F_DFLOOR = 2u, F_SIGMA = 4u, F_TAU = 8u, F_RHO = 16u, F_TEMP = 32u, F_VMAX = 64u, F_FOFC = 128u
+};
+constexpr unsigned FLOOR_BITS = F_DFLOOR | F_SIGMA | F_TAU | F_RHO | F_TEMP | F_VMAX;
+
+// Parameters with derived constants, passed by value to every kernel.
+struct Par {
+  double gam, gm1, gfac;        // Gamma, Gamma-1, Gamma/(Gamma-1)
+  double rho_atm, T_atm, rho_thr, eps_atm, P_atm;
+  double sigma_max, dmp_M, tol, vmax2;
+  int recon, rsolver, fofc, rk_order, maxit, guess;
+};
+
+// One meshblock as seen by the kernels: caller arrays plus context scratch.
+struct DevBlock {
+  int n[3], ng, N[3];
+  long long ncell;
+  double dx[3], idx[3];
+  double *cons, *cons0, *prim, *bcc;
+  double *bf[3], *bf0[3];
+  const double* adm;
+  unsigned char* flags;
+  double* flux[3];   // [7][face array of direction d]
+  double* emf[3];    // edge arrays E_x, E_y, E_z
+  double* ecc;       // [3][ncell] cell-centred E = -alpha (vhat x B~)
+  unsigned char* fflag;  // [ncell] FOFC flag of the current stage
+};
+
+// Work lists: item ranges of every block for one kernel kind.
+enum WorkKind { W_C2P = 0, W_FX, W_FY, W_FZ, W_CELL, W_EDGE, W_FACE, W_INIT, W_NKIND };
+
+struct Work {
+  const DevBlock* blk;          // device array [nblocks]
+  const long long* pre;         // device [W_NKIND][nblocks+1] item prefix sums
+  int nblocks;
+};
+
+// ---------------------------------------------------------------- indexing
+__device__ __forceinline__ long long cidx(const DevBlock& b, int k, int j, int i) {
+  return ((long long)k * b.N[1] + j) * b.N[0] + i;
+}
+__device__ __forceinline__ long long fidx(const DevBlock& b, int d, int k, int j, int i) {
+  if (d == 0) return ((long long)k * b.N[1] + j) * (b.N[0] + 1) + i;
+  if (d == 1) return ((long long)k * (b.N[1] + 1) + j) * b.N[0] + i;
+  return ((long long)k * b.N[1] + j) * b.N[0] + i;
+}
+__device__ __forceinline__ long long nface(const DevBlock& b, int d) {
+  if (d == 0) return (long long)b.N[2] * b.N[1] * (b.N[0] + 1);
+  if (d == 1) return (long long)b.N[2] * (b.N[1] + 1) * b.N[0];
+  return (long long)(b.N[2] + 1) * b.N[1] * b.N[0];
+}
+__device__ __forceinline__ long long eidx(const DevBlock& b, int c, int k, int j, int i) {
+  if (c == 0) return ((long long)k * (b.N[1] + 1) + j) * b.N[0] + i;
+  if (c == 1) return ((long long)k * b.N[1] + j) * (b.N[0] + 1) + i;
+  return ((long long)k * (b.N[1] + 1) + j) * (b.N[0] + 1) + i;
+}
+
+// block owning global item `it` of kind K (binary search of the prefix sums)
+__device__ __forceinline__ int find_block(const Work& w, int K, long long it) {
+  const long long* p = w.pre + (long long)K * (w.nblocks + 1);
+  int lo = 0, hi = w.nblocks;  // p[lo] <= it < p[hi]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (p[mid] <= it) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// ------------------------------------------------------------- metric (Eq. 5)
+struct Metric {
+  double g[6], gi[6], sdet, isdet;
+};
+__device__ __forceinline__ void metric_setup(Metric& m) {
+  const double* g = m.g;
+  double c0 = g[3] * g[5] - g[4] * g[4];
+  double c1 = g[2] * g[4] - g[1] * g[5];
+  double c2 = g[1] * g[4] - g[2] * g[3];
+  double det = g[0] * c0 + g[1] * c1 + g[2] * c2;
+  double isd = rsqrt(det);
+  double idet = isd * isd;
+  m.isdet = isd;
+  m.sdet = det * isd;
+  m.gi[0] = c0 * idet;
+  m.gi[1] = c1 * idet;
+  m.gi[2] = c2 * idet;
+  m.gi[3] = (g[0] * g[5] - g[2] * g[2]) * idet;
+  m.gi[4] = (g[1] * g[2] - g[0] * g[4]) * idet;
+  m.gi[5] = (g[0] * g[3] - g[1] * g[1]) * idet;
+}
+__device__ __forceinline__ void lower3(const double* g, const double* u, double* l) {
+  l[0] = g[0] * u[0] + g[1] * u[1] + g[2] * u[2];
+  l[1] = g[1] * u[0] + g[3] * u[1] + g[4] * u[2];
+  l[2] = g[2] * u[0] + g[4] * u[1] + g[5] * u[2];
+}
+__device__ __forceinline__ double dot3(const double* a, const double* b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// ----------------------------------------------------- prim -> cons (Eq. 6)
+// prim = rho, w^i = W v^i, P;  Bd = densitised B~;  out = D~, S~_i, tau~.
+__device__ __forceinline__ void prim2cons(const Par& P, const double* prim, const double* Bd, const Metric& m,
+                                          double* out) {
+  double B[3] = {Bd[0] * m.isdet, Bd[1] * m.isdet, Bd[2] * m.isdet};
+  double w[3] = {prim[1], prim[2], prim[3]};
+  double wl[3], Bl[3];
+  lower3(m.g, w, wl);
+  lower3(m.g, B, Bl);
+  double W2 = 1.0 + dot3(w, wl);
+  double iW = rsqrt(W2);
+  double W = W2 * iW;
+  double vl[3] = {wl[0] * iW, wl[1] * iW, wl[2] * iW};
+  double B2 = dot3(B, Bl);
+  double Bv = dot3(B, vl);
+  double rho = prim[0], p = prim[4];
+  double rhoh = rho + P.gfac * p;
+  double e = rhoh * W2;
+  double D = rho * W;
+  double eB = e + B2;
+  out[0] = m.sdet * D;
+  out[1] = m.sdet * (eB * vl[0] - Bv * Bl[0]);
+  out[2] = m.sdet * (eB * vl[1] - Bv * Bl[1]);
+  out[3] = m.sdet * (eB * vl[2] - Bv * Bl[2]);
+  out[4] = m.sdet * ((e - D) + B2 - p - 0.5 * (Bv * Bv + B2 * iW * iW));
+}
+
+// --------------------------------------------------------- con2prim (Sec. 3.4)
+// Kastaun, Kalinani & Ciolfi (2021) variables per unit D.
+struct KS {
+  double qh;      // q - b^2/2
+  double r2, b2, rb2, rperp2, gam, eps_min, vmax2;
+};
+struct KEval {
+  double x, rbar2, W, eps, eps_raw, G;
+  bool vcap;
+};
+// G(mu) = mu (1 + Gamma eps + mu rbar^2 W) - W.  For an ideal gas with only the
+// lower eps clamp, G = W (nu + mu rbar^2) f(mu) with nu = (1 + Gamma eps)/W >= 0,
+// i.e. the KRP master function f times a positive factor: same sign, same root.
+__device__ __forceinline__ void kev(const KS& s, double mu, KEval& e) {
+  double x = 1.0 / fma(mu, s.b2, 1.0);
+  double mux = mu * x;
+  double rbar2 = x * fma(s.r2, x, mu * (1.0 + x) * s.rb2);
+  double qbar = s.qh - 0.5 * mux * mux * s.rperp2;
+  double v2 = mu * mu * rbar2;
+  e.vcap = v2 > s.vmax2;
+  double vh2 = e.vcap ? s.vmax2 : v2;
+  double W = rsqrt(1.0 - vh2);
+  double wm1 = vh2 * W * W / (1.0 + W);  // W - 1 without cancellation
+  e.eps_raw = fma(W, qbar - mu * rbar2, wm1);
+  e.eps = e.eps_raw < s.eps_min ? s.eps_min : e.eps_raw;
+  e.x = x;
+  e.rbar2 = rbar2;
+  e.W = W;
+  e.G = mu * fma(mu * rbar2, W, fma(s.gam, e.eps, 1.0)) - W;
+}
+
+// Upper bracket end: three steps of mu <- 1/sqrt(1 + rbar^2(mu)) from
+// 1/sqrt(1 + r_par^2); every iterate bounds the root of
+// f_a(mu) = mu sqrt(1 + rbar^2(mu)) - 1 from above (h_min = 1).
+__device__ __forceinline__ double mu_plus(const KS& s) {
+  double rpar2 = s.b2 > 0.0 ? s.rb2 / s.b2 : s.r2;
+  double mu = rsqrt(1.0 + rpar2);
+#pragma unroll
+  for (int it = 0; it < 3; it++) {
+    double x = 1.0 / fma(mu, s.b2, 1.0);
+    double rbar2 = x * fma(s.r2, x, mu * (1.0 + x) * s.rb2);
+    mu = rsqrt(1.0 + rbar2);
+  }
+  return mu;
+}
+
+// Illinois regula falsi with bisection safeguard on [a,b], G(a) < 0 <= G(b);
+// stops when b - a <= tol b, then one regula-falsi step with the true end
+// values.  Returns false when the iteration cap is reached.
+__device__ __forceinline__ bool illinois(const KS& s, double a, double Ga, double b, double Gb, double tol, int maxit,
+                                         double& root, int& iters) {
+  iters = 0;
+  if (Gb == 0.0) { root = b; return true; }
+  double Fa = Ga, Fb = Gb;
+  int side = 0;
+  KEval e;
+  while (b - a > tol * b) {
+    if (iters >= maxit) return false;
+    iters++;
+    double c = (a * Fb - b * Fa) / (Fb - Fa);
+    if (!(c > a && c < b)) c = 0.5 * (a + b);
+    kev(s, c, e);
+    if (e.G < 0.0) {
+      a = c; Ga = e.G; Fa = e.G;
+      if (side == -1) Fb *= 0.5;
+      side = -1;
+    } else if (e.G > 0.0) {
+      b = c; Gb = e.G; Fb = e.G;
+      if (side == 1) Fa *= 0.5;
+      side = 1;
+    } else {
+      root = c;
+      return true;
+    }
+  }
+  root = a - Ga * (b - a) / (Gb - Ga);
+  return true;
+}
+
+// The con2prim of one cell.  U: densitised conserved state (overwritten with
+// the floored state when write_cons and a floor fired); Bd: cell-centred B~;
+// m: metric with inverse.  lo/hi: optional bracket guess (lo < 0: none).
+__device__ __forceinline__ void con2prim(const Par& P, double* U, const double* Bd, const Metric& m, double* prim,
+                                         unsigned& flags, int& iters, bool write_cons, double glo = -1.0,
+                                         double ghi = -1.0) {
+  flags = 0;
+  iters = 0;
+  const double isd = m.isdet;
+  double D = U[0] * isd, tau = U[4] * isd;
+  double Sl[3] = {U[1] * isd, U[2] * isd, U[3] * isd};
+  double B[3] = {Bd[0] * isd, Bd[1] * isd, Bd[2] * isd};
+  double Bl[3];
+  lower3(m.g, B, Bl);
+  double B2 = dot3(B, Bl);
+  double rho = P.rho_atm, p = P.P_atm, w0 = 0.0, w1 = 0.0, w2 = 0.0;
+  bool fin = isfinite(D) && isfinite(tau) && isfinite(Sl[0]) && isfinite(Sl[1]) && isfinite(Sl[2]) &&
+             isfinite(B2) && m.sdet > 0.0;
+  if (!fin) {
+    flags |= F_FAIL;
+  } else {
+    if (D < P.rho_thr) {
+      D = P.rho_atm;
+      Sl[0] = Sl[1] = Sl[2] = 0.0;
+      tau = fma(D, P.eps_atm, 0.5 * B2);
+      flags |= F_DFLOOR;
+    }
+    if (P.sigma_max > 0.0 && B2 > P.sigma_max * D) {
+      D = B2 / P.sigma_max;
+      flags |= F_SIGMA;
+    }
+    double tau_atm = fma(D, P.eps_atm, 0.5 * B2);
+    if (tau < tau_atm) {
+      tau = tau_atm;
+      flags |= F_TAU;
+    }
+    KS s;
+    double iD = 1.0 / D;
+    double rl[3] = {Sl[0] * iD, Sl[1] * iD, Sl[2] * iD};
+    double ru[3];
+    lower3(m.gi, rl, ru);
+    double isD = sqrt(iD);
+    double bu[3] = {B[0] * isD, B[1] * isD, B[2] * isD};
+    s.b2 = B2 * iD;
+    s.r2 = dot3(rl, ru);
+    double rb = dot3(rl, bu);
+    s.rb2 = rb * rb;
+    double rp = s.r2 * s.b2 - s.rb2;
+    s.rperp2 = rp > 0.0 ? rp : 0.0;
+    s.qh = fma(tau, iD, -0.5 * s.b2);
+    s.gam = P.gam;
+    s.eps_min = P.eps_atm;
+    s.vmax2 = P.vmax2;
+    // bracket: G(0) = -1 exactly (v = 0, W = 1)
+    KEval e;
+    double a = 0.0, Ga = -1.0, b, Gb;
+    bool have = false;
+    if (glo >= 0.0 && ghi > glo) {
+      // learned bracket, verified by the signs at both ends
+      KEval el, eh;
+      kev(s, glo, el);
+      kev(s, ghi, eh);
+      if (el.G < 0.0 && eh.G >= 0.0) {
+        a = glo; Ga = el.G; b = ghi; Gb = eh.G; have = true;
+      } else if (el.G >= 0.0) {
+        b = glo; Gb = el.G; have = true;              // root in [0, glo]
+      } else {
+        a = ghi; Ga = eh.G;                            // root above ghi
+      }
+      iters += 2;
+    }
+    if (!have) {
+      double mp = mu_plus(s);
+      if (mp <= a) mp = 1.0;
+      kev(s, mp, e);
+      b = mp; Gb = e.G;
+      if (Gb < 0.0) {
+        a = mp; Ga = Gb;
+        b = 1.0;
+        kev(s, b, e);
+        Gb = e.G;
+      }
+    }
+    double mu = 0.0;
+    int it = 0;
+    bool ok = (Ga < 0.0) && (Gb >= 0.0) && illinois(s, a, Ga, b, Gb, P.tol, P.maxit, mu, it);
+    iters += it;
+    if (!ok || !isfinite(mu)) {
+      flags |= F_FAIL;
+    } else {
+      kev(s, mu, e);
+      if (e.eps_raw < s.eps_min) flags |= F_TEMP;
+      if (e.vcap) flags |= F_VMAX;
+      double iW = e.W * (1.0 - (e.vcap ? s.vmax2 : mu * mu * e.rbar2));
+      rho = D * iW;
+      p = P.gm1 * rho * e.eps;
+      double vs = 1.0;
+      if (e.vcap) vs = sqrt(s.vmax2 / (mu * mu * e.rbar2));
+      double f = e.W * vs * mu * e.x;
+      double mrb = mu * rb;
+      w0 = f * fma(mrb, bu[0], ru[0]);
+      w1 = f * fma(mrb, bu[1], ru[1]);
+      w2 = f * fma(mrb, bu[2], ru[2]);
+      if (rho < P.rho_thr) {
+        rho = P.rho_atm; p = P.P_atm; w0 = w1 = w2 = 0.0;
+        flags |= F_RHO;
+      } else if (p < rho * P.T_atm) {
+        p = rho * P.T_atm;
+        flags |= F_TEMP;
+      }
+    }
+  }
+  if (flags & F_FAIL) {
+    rho = P.rho_atm; p = P.P_atm; w0 = w1 = w2 = 0.0;
+  }
+  prim[0] = rho; prim[1] = w0; prim[2] = w1; prim[3] = w2; prim[4] = p;
+  if (write_cons && (flags & (FLOOR_BITS | F_FAIL))) prim2cons(P, prim, Bd, m, U);
+}
+
+// -------------------------------------------------- reconstruction (Sec. 3.2)
+__device__ __forceinline__ double vl_slope(double qm, double q0, double qp) {
+  double dl = q0 - qm, dr = qp - q0;
+  double pr = dl * dr;
+  return pr > 0.0 ? 2.0 * pr / (dl + dr) : 0.0;
+}
+// WENO-Z value at the face between c and d, stencil (a,b,c,d,e) centred on c.
+// The three nonlinear weights share one division: omega_k is proportional to
+// d_k (beta_k + eps + tau5) prod_{m != k} (beta_m + eps).
+__device__ __forceinline__ double wenoz(double a, double b, double c, double d, double e) {
+  const double third = 1.0 / 3.0, sixth = 1.0 / 6.0;
+  double q0 = fma(third, a, fma(-7.0 * sixth, b, (11.0 * sixth) * c));
+  double q1 = fma(-sixth, b, fma(5.0 * sixth, c, third * d));
+  double q2 = fma(third, c, fma(5.0 * sixth, d, -sixth * e));
+  const double k13 = 13.0 / 12.0;
+  double t = a - 2.0 * b + c, u = a - 4.0 * b + 3.0 * c;
+  double b0 = fma(k13 * t, t, 0.25 * u * u);
+  t = b - 2.0 * c + d; u = b - d;
+  double b1 = fma(k13 * t, t, 0.25 * u * u);
+  t = c - 2.0 * d + e; u = 3.0 * c - 4.0 * d + e;
+  double b2 = fma(k13 * t, t, 0.25 * u * u);
+  const double eps = 1e-40;
+  double tau = fabs(b0 - b2);
+  double e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
+  double w0 = 0.1 * (e0 + tau) * (e1 * e2);
+  double w1 = 0.6 * (e1 + tau) * (e0 * e2);
+  double w2 = 0.3 * (e2 + tau) * (e0 * e1);
+  return fma(w0, q0, fma(w1, q1, w2 * q2)) / (w0 + w1 + w2);
+}
+// L/R states at the face between q[2] and q[3] from q[0..5] = cells -3..+2
+__device__ __forceinline__ void recon(int r, const double* q, double& L, double& R) {
+  if (r == 2) {
+    L = wenoz(q[0], q[1], q[2], q[3], q[4]);
+    R = wenoz(q[5], q[4], q[3], q[2], q[1]);
+  } else if (r == 1) {
+    L = fma(0.5, vl_slope(q[1], q[2], q[3]), q[2]);
+    R = fma(-0.5, vl_slope(q[2], q[3], q[4]), q[3]);
+  } else {
+    L = q[2];
+    R = q[3];
+  }
+}
+__device__ __forceinline__ void face_floor(const Par& P, double* s) {
+  if (s[0] < P.rho_thr) {
+    s[0] = P.rho_atm; s[1] = s[2] = s[3] = 0.0; s[4] = P.P_atm;
+  } else if (s[4] < s[0] * P.T_atm) {
+    s[4] = s[0] * P.T_atm;
+  }
+}
+
+// --------------------------------------------------------- face fluxes (Eq. 8)
+// Face metric: alpha, beta, gamma with inverse, plus 1/alpha.
+struct FaceMetric {
+  Metric m;
+  double alpha, beta[3];
+};
+struct Side {
+  double U[7], F[7], lm, lp;
+};
+// st = rho, w^1..3, P, B~^{t1}, B~^{t2}; Bn = B~^d.
+template <int d>
+__device__ __forceinline__ void face_side(const Par& P, const double* st, double Bn, const FaceMetric& fm, Side& o) {
+  constexpr int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  const Metric& m = fm.m;
+  double Bt[3];
+  Bt[d] = Bn; Bt[t1] = st[5]; Bt[t2] = st[6];
+  double B[3] = {Bt[0] * m.isdet, Bt[1] * m.isdet, Bt[2] * m.isdet};
+  double w[3] = {st[1], st[2], st[3]};
+  double wl[3], Bl[3];
+  lower3(m.g, w, wl);
+  lower3(m.g, B, Bl);
+  double W2 = 1.0 + dot3(w, wl);
+  double iW = rsqrt(W2);
+  double W = W2 * iW;
+  double v[3] = {w[0] * iW, w[1] * iW, w[2] * iW};
+  double vl[3] = {wl[0] * iW, wl[1] * iW, wl[2] * iW};
+  double B2 = dot3(B, Bl), Bv = dot3(B, vl), v2 = dot3(v, vl);
+  double iW2 = iW * iW;
+  double b2 = fma(B2, iW2, Bv * Bv);
+  double rho = st[0], p = st[4];
+  double rhoh = fma(P.gfac, p, rho);
+  double e = rhoh * W2;
+  double D = rho * W;
+  double eB = e + B2;
+  double sd = m.sdet;
+  double alpha = fm.alpha;
+  double avh[3];  // alpha vhat^i = alpha v^i - beta^i
+#pragma unroll
+  for (int a = 0; a < 3; a++) avh[a] = fma(alpha, v[a], -fm.beta[a]);
+  double Ptot = fma(0.5, b2, p);
+  o.U[0] = sd * D;
+#pragma unroll
+  for (int a = 0; a < 3; a++) o.U[1 + a] = sd * fma(eB, vl[a], -Bv * Bl[a]);
+  o.U[4] = sd * ((e - D) + B2 - p - 0.5 * fma(B2, iW2, Bv * Bv));
+  o.U[5] = Bt[t1];
+  o.U[6] = Bt[t2];
+  double avd = avh[d];
+  double aBn = alpha * Bn;
+  double aPs = alpha * sd * Ptot;
+  o.F[0] = o.U[0] * avd;
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    double bl = fma(W * Bv, vl[a], Bl[a] * iW);   // b_i = B_i/W + W (B.v) v_i
+    o.F[1 + a] = fma(o.U[1 + a], avd, -aBn * bl * iW);
+  }
+  o.F[1 + d] += aPs;
+  o.F[4] = fma(o.U[4], avd, fma(aPs, v[d], -aBn * Bv));
+  o.F[5] = fma(Bt[t1], avh[d], -Bn * avh[t1]);
+  o.F[6] = fma(Bt[t2], avh[d], -Bn * avh[t2]);
+  // fast magnetosonic speed (one division for c_s^2 and v_A^2)
+  double inv = 1.0 / (rhoh * (rhoh + b2));
+  double cs2 = P.gam * p * (rhoh + b2) * inv;
+  double va2 = b2 * rhoh * inv;
+  double cf2 = cs2 + va2 - cs2 * va2;
+  double cf = sqrt(cf2);
+  double vd = v[d];
+  double omc = 1.0 - cf2;
+  double den = 1.0 - v2 * cf2;
+  double disc = (1.0 - v2) * (m.gi[d == 0 ? 0 : (d == 1 ? 3 : 5)] * den - vd * vd * omc);
+  double sq = sqrt(disc > 0.0 ? disc : 0.0);
+  double ad = alpha / den;
+  double c1 = vd * omc, c2 = cf * sq;
+  o.lm = fma(ad, c1 - c2, -fm.beta[d]);
+  o.lp = fma(ad, c1 + c2, -fm.beta[d]);
+}
+
+__device__ __forceinline__ void riemann(int rs, const Side& L, const Side& R, double* F) {
+  if (rs == 1) {
+    double lL = fmin(fmin(L.lm, R.lm), 0.0);
+    double lR = fmax(fmax(L.lp, R.lp), 0.0);
+    if (lR == lL) {
+#pragma unroll
+      for (int c = 0; c < 7; c++) F[c] = 0.5 * (L.F[c] + R.F[c]);
+    } else {
+      double inv = 1.0 / (lR - lL);
+      double ll = lL * lR;
+#pragma unroll
+      for (int c = 0; c < 7; c++) F[c] = fma(lR, L.F[c], fma(-lL, R.F[c], ll * (R.U[c] - L.U[c]))) * inv;
+    }
+  } else {
+    double a = fmax(fmax(fabs(L.lm), fabs(L.lp)), fmax(fabs(R.lm), fabs(R.lp)));
+#pragma unroll
+    for (int c = 0; c < 7; c++) F[c] = 0.5 * (L.F[c] + R.F[c]) - 0.5 * a * (R.U[c] - L.U[c]);
+  }
+}
+
+// SSP-RK weights (g0, g1, beta) of a stage: U <- g0 U^n + g1 U + beta dt L(U)
+__host__ __device__ inline void rk_weights(int order, int stage, double& g0, double& g1, double& be) {
+  if (order == 2) {
+    if (stage == 0) { g0 = 0.0; g1 = 1.0; be = 1.0; }
+    else { g0 = 0.5; g1 = 0.5; be = 0.5; }
+  } else {
+    if (stage == 0) { g0 = 0.0; g1 = 1.0; be = 1.0; }
+    else if (stage == 1) { g0 = 0.75; g1 = 0.25; be = 0.25; }
+    else { g0 = 1.0 / 3.0; g1 = 2.0 / 3.0; be = 2.0 / 3.0; }
+  }
+}
+
+// Warp-level sum of per-thread counters, one atomic per warp.  Call where the
+// whole warp has converged (end of a kernel; blockDim a multiple of 32).
+__device__ __forceinline__ void warp_flush(unsigned long long* ctr, unsigned v) {
+  unsigned s = __reduce_add_sync(0xffffffffu, v);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(ctr, (unsigned long long)s);
+}
+
+}  // namespace grmhd

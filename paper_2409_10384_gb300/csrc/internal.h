@@ -1,0 +1,25 @@
+// Host-side launchers shared between the kernel translation units and the C-ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include "dev.cuh"
+
+namespace grmhd {
+void launch_init_block(const DevBlock& b, const Par& P, const double* const A[3], cudaStream_t s, int nsm);
+void launch_p2c_cells(const Par& P, long long n, const double* prim, const double* Bd, const double* g, double* cons,
+                      cudaStream_t s, int nsm);
+void launch_c2p_cells(const Par& P, long long n, double* cons, const double* Bd, const double* g, double* prim,
+                      unsigned char* flags, int* iters, const float* guess, unsigned long long* stats, cudaStream_t s,
+                      int grid);
+void launch_c2p_block(const Work& w, const Par& P, unsigned long long* stats, cudaStream_t s, int grid);
+void launch_flux_dir(int d, const Work& w, const Par& P, cudaStream_t s, int grid);
+void launch_fofc_flag(const Work& w, const Par& P, double g0, double g1, double bdt, unsigned long long* stats,
+                      cudaStream_t s, int grid);
+void launch_fofc_fix(int d, const Work& w, const Par& P, unsigned long long* stats, cudaStream_t s, int grid);
+void launch_emf(const Work& w, cudaStream_t s, int grid);
+void launch_update_cells(const Work& w, const Par& P, double g0, double g1, double bdt, int first, cudaStream_t s,
+                         int grid);
+void launch_update_faces(const Work& w, double g0, double g1, double bdt, int first, cudaStream_t s, int grid);
+int occupancy_c2p(int* per_sm);
+int occupancy_face(int* per_sm);
+int occupancy_update(int* per_sm);
+}  // namespace grmhd

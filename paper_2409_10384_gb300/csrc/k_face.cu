@@ -1,0 +1,212 @@
+// Face kernels: reconstruction (Sec. 3.2) and the LLF/HLLE flux of Eq. 8 with
+// the ADM metric interpolated to the face, and the first-order flux
+// correction of Sec. 3.3 with the relaxed DMP of Eq. 19.
+#include "dev.cuh"
+#include "internal.h"
+
+namespace grmhd {
+
+// Face index (k,j,i) of item `loc` of direction d: along d the interior faces,
+// transversally one extra layer each side (the CT stencil needs them).
+template <int d>
+__device__ __forceinline__ void face_coords(const DevBlock& b, long long loc, int& k, int& j, int& i) {
+  const int L0 = b.n[0] + (d == 0 ? 1 : 2), L1 = b.n[1] + (d == 1 ? 1 : 2);
+  int a0 = loc % L0; long long r = loc / L0; int a1 = r % L1; int a2 = r / L1;
+  i = a0 + b.ng - (d == 0 ? 0 : 1);
+  j = a1 + b.ng - (d == 1 ? 0 : 1);
+  k = a2 + b.ng - (d == 2 ? 0 : 1);
+}
+
+// Flux through face (k,j,i) of direction d; donor forces first order.
+template <int d>
+__device__ __forceinline__ void face_flux(const DevBlock& b, const Par& P, int k, int j, int i, bool donor,
+                                          double* F) {
+  constexpr int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  const long long nc = b.ncell;
+  const long long c0 = cidx(b, k, j, i);
+  const long long st = d == 0 ? 1 : (d == 1 ? (long long)b.N[0] : (long long)b.N[0] * b.N[1]);
+  const int r = donor ? 0 : P.recon;
+  double L[7], R[7];
+#pragma unroll
+  for (int v = 0; v < 7; v++) {
+    const double* a = v < 5 ? b.prim + v * nc : b.bcc + (v == 5 ? t1 : t2) * nc;
+    double q[6];
+    if (r == 2) {
+#pragma unroll
+      for (int m = 0; m < 6; m++) q[m] = a[c0 + (m - 3) * st];
+    } else if (r == 1) {
+#pragma unroll
+      for (int m = 1; m < 5; m++) q[m] = a[c0 + (m - 3) * st];
+      q[0] = q[5] = 0.0;
+    } else {
+      q[2] = a[c0 - st];
+      q[3] = a[c0];
+      q[0] = q[1] = q[4] = q[5] = 0.0;
+    }
+    recon(r, q, L[v], R[v]);
+  }
+  face_floor(P, L);
+  face_floor(P, R);
+  // ADM metric at the face: 4-point Lagrange (-1, 9, 9, -1)/16 along d
+  FaceMetric fm;
+  double mv[10];
+#pragma unroll
+  for (int v = 0; v < 10; v++) {
+    const double* a = b.adm + v * nc + c0;
+    double am = a[-2 * st], bm = a[-st], cm = a[0], dm = a[st];
+    mv[v] = fma(0.5625, bm + cm, -0.0625 * (am + dm));
+  }
+  fm.alpha = mv[0];
+  fm.beta[0] = mv[1]; fm.beta[1] = mv[2]; fm.beta[2] = mv[3];
+#pragma unroll
+  for (int v = 0; v < 6; v++) fm.m.g[v] = mv[4 + v];
+  metric_setup(fm.m);
+  const double Bn = b.bf[d][fidx(b, d, k, j, i)];
+  Side sl, sr;
+  face_side<d>(P, L, Bn, fm, sl);
+  face_side<d>(P, R, Bn, fm, sr);
+  riemann(P.rsolver, sl, sr, F);
+}
+
+template <int d>
+__global__ void __launch_bounds__(128) k_flux(Work w, Par P) {
+  const long long* pre = w.pre + (long long)(W_FX + d) * (w.nblocks + 1);
+  const long long tot = pre[w.nblocks];
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < tot; it += (long long)gridDim.x * blockDim.x) {
+    const int bi = find_block(w, W_FX + d, it);
+    const DevBlock& b = w.blk[bi];
+    int k, j, i;
+    face_coords<d>(b, it - pre[bi], k, j, i);
+    double F[7];
+    face_flux<d>(b, P, k, j, i, false, F);
+    const long long f = fidx(b, d, k, j, i), nf = nface(b, d);
+    double* out = b.flux[d];
+#pragma unroll
+    for (int c = 0; c < 7; c++) out[c * nf + f] = F[c];
+  }
+}
+
+__device__ __forceinline__ bool interior(const DevBlock& b, int k, int j, int i) {
+  return (unsigned)(i - b.ng) < (unsigned)b.n[0] && (unsigned)(j - b.ng) < (unsigned)b.n[1] &&
+         (unsigned)(k - b.ng) < (unsigned)b.n[2];
+}
+
+// FOFC flag: U* = g0 U^n + g1 U + b dt (-div F) (no sources, no CT, B at the
+// stage's bcc); flag when con2prim of U* fails or needs a floor, or (DMP)
+// when D~* or tau~* leaves [min/M, M max] of the 27 cells around (stage input).
+__global__ void __launch_bounds__(128) k_fofc_flag(Work w, Par P, double g0, double g1, double bdt,
+                                                   unsigned long long* stats) {
+  const long long* pre = w.pre + (long long)W_CELL * (w.nblocks + 1);
+  const long long tot = pre[w.nblocks];
+  unsigned s_flag = 0, s_dmp = 0;
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < tot; it += (long long)gridDim.x * blockDim.x) {
+    const int bi = find_block(w, W_CELL, it);
+    const DevBlock& b = w.blk[bi];
+    long long loc = it - pre[bi];
+    int i = loc % b.n[0]; long long r = loc / b.n[0]; int j = r % b.n[1]; int k = r / b.n[1];
+    i += b.ng; j += b.ng; k += b.ng;
+    const long long nc = b.ncell, c = cidx(b, k, j, i);
+    const long long fx0 = fidx(b, 0, k, j, i), fy0 = fidx(b, 1, k, j, i), fz0 = fidx(b, 2, k, j, i);
+    const long long fx1 = fx0 + 1, fy1 = fidx(b, 1, k, j + 1, i), fz1 = fidx(b, 2, k + 1, j, i);
+    const long long nx = nface(b, 0), ny = nface(b, 1), nz = nface(b, 2);
+    double U[5];
+#pragma unroll
+    for (int v = 0; v < 5; v++) {
+      double div = (b.flux[0][v * nx + fx1] - b.flux[0][v * nx + fx0]) * b.idx[0] +
+                   (b.flux[1][v * ny + fy1] - b.flux[1][v * ny + fy0]) * b.idx[1] +
+                   (b.flux[2][v * nz + fz1] - b.flux[2][v * nz + fz0]) * b.idx[2];
+      double u = g1 * b.cons[v * nc + c];
+      if (g0 != 0.0) u = fma(g0, b.cons0[v * nc + c], u);
+      U[v] = fma(-bdt, div, u);
+    }
+    Metric m;
+#pragma unroll
+    for (int v = 0; v < 6; v++) m.g[v] = b.adm[(4 + v) * nc + c];
+    metric_setup(m);
+    double Bd[3] = {b.bcc[c], b.bcc[nc + c], b.bcc[2 * nc + c]};
+    double pr[5];
+    unsigned fl;
+    int itn;
+    con2prim(P, U, Bd, m, pr, fl, itn, false);
+    bool flag = (fl & (FLOOR_BITS | F_FAIL)) != 0;
+    if (!flag && P.dmp_M > 0.0) {
+#pragma unroll
+      for (int t = 0; t < 2; t++) {
+        const int v = t == 0 ? 0 : 4;
+        const double* a = b.cons + v * nc;
+        double mn = a[c], mx = mn;
+        for (int dk = -1; dk <= 1; dk++)
+          for (int dj = -1; dj <= 1; dj++)
+#pragma unroll
+            for (int di = -1; di <= 1; di++) {
+              double u = a[cidx(b, k + dk, j + dj, i + di)];
+              mn = fmin(mn, u);
+              mx = fmax(mx, u);
+            }
+        const double M = P.dmp_M;
+        double lo = mn > 0.0 ? mn / M : mn * M;
+        double hi = mx > 0.0 ? mx * M : mx / M;
+        if (U[v] < lo || U[v] > hi) flag = true;
+      }
+      s_dmp += flag ? 1u : 0u;
+    }
+    b.fflag[c] = flag ? 1 : 0;
+    unsigned char f0 = b.flags[c];
+    b.flags[c] = flag ? (unsigned char)(f0 | F_FOFC) : (unsigned char)(f0 & ~F_FOFC);
+    s_flag += flag ? 1u : 0u;
+  }
+  warp_flush(&stats[4], s_flag);
+  warp_flush(&stats[5], s_dmp);
+}
+
+// First-order recompute of every face touching a flagged interior cell.
+template <int d>
+__global__ void __launch_bounds__(128) k_fofc_fix(Work w, Par P, unsigned long long* stats) {
+  const long long* pre = w.pre + (long long)(W_FX + d) * (w.nblocks + 1);
+  const long long tot = pre[w.nblocks];
+  unsigned s_faces = 0;
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < tot; it += (long long)gridDim.x * blockDim.x) {
+    const int bi = find_block(w, W_FX + d, it);
+    const DevBlock& b = w.blk[bi];
+    int k, j, i;
+    face_coords<d>(b, it - pre[bi], k, j, i);
+    const int km = k - (d == 2), jm = j - (d == 1), im = i - (d == 0);
+    bool fl = (interior(b, k, j, i) && b.fflag[cidx(b, k, j, i)]) ||
+              (interior(b, km, jm, im) && b.fflag[cidx(b, km, jm, im)]);
+    if (!fl) continue;
+    double F[7];
+    face_flux<d>(b, P, k, j, i, true, F);
+    const long long f = fidx(b, d, k, j, i), nf = nface(b, d);
+    double* out = b.flux[d];
+#pragma unroll
+    for (int c = 0; c < 7; c++) out[c * nf + f] = F[c];
+    s_faces++;
+  }
+  warp_flush(&stats[6], s_faces);
+}
+
+void launch_flux_dir(int d, const Work& w, const Par& P, cudaStream_t s, int grid) {
+  if (d == 0) k_flux<0><<<grid, 128, 0, s>>>(w, P);
+  else if (d == 1) k_flux<1><<<grid, 128, 0, s>>>(w, P);
+  else k_flux<2><<<grid, 128, 0, s>>>(w, P);
+}
+void launch_fofc_flag(const Work& w, const Par& P, double g0, double g1, double bdt, unsigned long long* stats,
+                      cudaStream_t s, int grid) {
+  k_fofc_flag<<<grid, 128, 0, s>>>(w, P, g0, g1, bdt, stats);
+}
+void launch_fofc_fix(int d, const Work& w, const Par& P, unsigned long long* stats, cudaStream_t s, int grid) {
+  if (d == 0) k_fofc_fix<0><<<grid, 128, 0, s>>>(w, P, stats);
+  else if (d == 1) k_fofc_fix<1><<<grid, 128, 0, s>>>(w, P, stats);
+  else k_fofc_fix<2><<<grid, 128, 0, s>>>(w, P, stats);
+}
+int occupancy_face(int* per_sm) {
+  cudaError_t e = cudaSuccess;
+  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_flux<0>, 128, 0));
+  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_flux<1>, 128, 0));
+  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[2], k_flux<2>, 128, 0));
+  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[3], k_fofc_flag, 128, 0));
+  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[4], k_fofc_fix<0>, 128, 0));
+  return e == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace grmhd

@@ -1,0 +1,302 @@
+"""Thin ctypes binding of libgrmhd (include/grmhd.h): argument marshalling only.
+
+Every step of the path runs in the library's CUDA kernels; this module turns
+torch tensors into the C structs and raw pointers the C-ABI takes.  There is no
+CPU fallback: if the compiled library is missing the import of ``lib()``
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+MHD_F_FAIL, MHD_F_DFLOOR, MHD_F_SIGMA, MHD_F_TAU, MHD_F_RHO, MHD_F_TEMP, MHD_F_VMAX, MHD_F_FOFC = (
+    1, 2, 4, 8, 16, 32, 64, 128)
+_ERR = {0: "ok", -1: "invalid argument", -2: "CUDA runtime error", -3: "device allocation failed",
+        -4: "call out of order", -5: "learned guess requested but no network loaded"}
+
+
+class mhd_params(C.Structure):
+    _fields_ = [
+        ("gamma", C.c_double), ("rho_atm", C.c_double), ("T_atm", C.c_double), ("f_thr", C.c_double),
+        ("sigma_max", C.c_double), ("dmp_M", C.c_double), ("c2p_tol", C.c_double), ("W_max", C.c_double),
+        ("recon", C.c_int), ("rsolver", C.c_int), ("fofc", C.c_int), ("rk_order", C.c_int),
+        ("c2p_maxit", C.c_int), ("c2p_guess", C.c_int),
+    ]
+
+
+class mhd_block(C.Structure):
+    _fields_ = [
+        ("n", C.c_int * 3), ("ng", C.c_int), ("dx", C.c_double * 3),
+        ("cons", C.c_void_p), ("cons0", C.c_void_p), ("prim", C.c_void_p),
+        ("bf", C.c_void_p * 3), ("bf0", C.c_void_p * 3), ("bcc", C.c_void_p), ("adm", C.c_void_p),
+        ("flags", C.c_void_p),
+    ]
+
+
+class mhd_stats(C.Structure):
+    _fields_ = [("cells", C.c_longlong), ("iters", C.c_longlong), ("fails", C.c_longlong),
+                ("floors", C.c_longlong), ("fofc_cells", C.c_longlong), ("dmp_cells", C.c_longlong),
+                ("fofc_faces", C.c_longlong)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+_LOCK = threading.Lock()
+_LIB = None
+
+# name -> (restype, argtypes)
+_VP, _I, _L, _D = C.c_void_p, C.c_int, C.c_long, C.c_double
+_SIGS = {
+    "mhd_init": (_I, [C.POINTER(mhd_params), C.POINTER(_VP)]),
+    "mhd_set_params": (_I, [_VP, C.POINTER(mhd_params)]),
+    "mhd_finalize": (None, [_VP]),
+    "mhd_strerror": (C.c_char_p, [_I]),
+    "mhd_init_block": (_I, [_VP, C.POINTER(mhd_block), C.POINTER(_VP), _VP]),
+    "mhd_prim2cons": (_I, [_VP, _L, _VP, _VP, _VP, _VP, _VP]),
+    "mhd_c2p_cells": (_I, [_VP, _L, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "mhd_c2p": (_I, [_VP, C.POINTER(mhd_block), _I, _VP]),
+    "mhd_rhs": (_I, [_VP, C.POINTER(mhd_block), _I, _D, _I, _VP]),
+    "mhd_rk_update": (_I, [_VP, C.POINTER(mhd_block), _I, _D, _I, _VP]),
+    "mhd_step": (_I, [_VP, C.POINTER(mhd_block), _I, _D, _I, _VP]),
+    "mhd_read_stats": (_I, [_VP, C.POINTER(mhd_stats), _VP]),
+    "mhd_reset_stats": (_I, [_VP, _VP]),
+    "mhd_scratch_copy": (_I, [_VP, _I, _I, _VP, _L, C.POINTER(_L), _VP]),
+    "mhd_kernel_launches": (C.c_longlong, [_VP]),
+    "mhd_profile": (_I, [_VP, _I]),
+    "mhd_profile_read": (_I, [_VP, _VP, _VP]),
+    "mhd_kernel_name": (C.c_char_p, [_I]),
+}
+MHD_NKERNEL = 9
+
+
+def header_symbols() -> list:
+    """Every function name declared in include/grmhd.h."""
+    h = open(os.path.join(_build.ROOT, "include", "grmhd.h")).read()
+    h = re.sub(r"/\*.*?\*/", "", h, flags=re.S)
+    return sorted(set(re.findall(r"\b(mhd_[a-z0-9_]+)\s*\(", h)))
+
+
+def lib(path: str | None = None):
+    """Load libgrmhd.so (built in-tree by ``build.build()``); raises if absent."""
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            p = path or _build.LIB
+            if not os.path.exists(p):
+                raise RuntimeError(f"libgrmhd.so not built ({p}); run paper_2409_10384_gb300.build.build()")
+            L = C.CDLL(p)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _LIB = L
+        return _LIB
+
+
+class MHDError(RuntimeError):
+    pass
+
+
+def check(rc: int, what: str = ""):
+    if rc != 0:
+        raise MHDError(f"{what}: {_ERR.get(rc, rc)} ({rc})")
+
+
+def params(**kw) -> mhd_params:
+    d = dict(gamma=5.0 / 3.0, rho_atm=1e-12, T_atm=1e-10, f_thr=0.1, sigma_max=0.0, dmp_M=0.0, c2p_tol=1e-10,
+             W_max=1e3, recon=1, rsolver=1, fofc=0, rk_order=2, c2p_maxit=64, c2p_guess=0)
+    d.update(kw)
+    p = mhd_params()
+    for k, v in d.items():
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "device, contiguous tensors only"
+    return C.c_void_p(t.data_ptr())
+
+
+def _sptr(stream):
+    if stream is None:
+        return None
+    return C.c_void_p(int(stream.cuda_stream))
+
+
+class DeviceBlock:
+    """Caller-owned device arrays of one meshblock (torch tensors, FP64)."""
+
+    def __init__(self, n, ng, dx, adm, device="cuda"):
+        import torch
+        self.n = tuple(int(x) for x in n)
+        self.ng = int(ng)
+        self.dx = tuple(float(x) for x in dx)
+        N1, N2, N3 = (x + 2 * self.ng for x in self.n)
+        self.N = (N1, N2, N3)
+        f64 = dict(dtype=torch.float64, device=device)
+        self.adm = torch.as_tensor(adm, **f64).contiguous()
+        assert tuple(self.adm.shape) == (16, N3, N2, N1)
+        self.cons = torch.zeros((5, N3, N2, N1), **f64)
+        self.cons0 = torch.zeros((5, N3, N2, N1), **f64)
+        self.prim = torch.zeros((5, N3, N2, N1), **f64)
+        self.bcc = torch.zeros((3, N3, N2, N1), **f64)
+        self.flags = torch.zeros((N3, N2, N1), dtype=torch.uint8, device=device)
+        shp = [(N3, N2, N1 + 1), (N3, N2 + 1, N1), (N3 + 1, N2, N1)]
+        self.bf = [torch.zeros(s, **f64) for s in shp]
+        self.bf0 = [torch.zeros(s, **f64) for s in shp]
+
+    def edge_shape(self, c):
+        N1, N2, N3 = self.N
+        return [(N3 + 1, N2 + 1, N1), (N3 + 1, N2, N1 + 1), (N3, N2 + 1, N1 + 1)][c]
+
+    def desc(self) -> mhd_block:
+        b = mhd_block()
+        b.n = (C.c_int * 3)(*self.n)
+        b.ng = self.ng
+        b.dx = (C.c_double * 3)(*self.dx)
+        b.cons, b.cons0, b.prim = self.cons.data_ptr(), self.cons0.data_ptr(), self.prim.data_ptr()
+        b.bcc, b.adm, b.flags = self.bcc.data_ptr(), self.adm.data_ptr(), self.flags.data_ptr()
+        for d in range(3):
+            b.bf[d] = self.bf[d].data_ptr()
+            b.bf0[d] = self.bf0[d].data_ptr()
+        return b
+
+
+def block_array(blocks) -> C.Array:
+    arr = (mhd_block * len(blocks))()
+    for i, b in enumerate(blocks):
+        arr[i] = b.desc()
+    return arr
+
+
+class Context:
+    """Owns one mhd_ctx.  Method names follow the C-ABI entry points."""
+
+    def __init__(self, p: mhd_params):
+        self.L = lib()
+        self.p = p
+        h = C.c_void_p()
+        check(self.L.mhd_init(C.byref(p), C.byref(h)), "mhd_init")
+        self.h = h
+        self._arr = None
+        self._key = None
+
+    def close(self):
+        if self.h:
+            self.L.mhd_finalize(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p: mhd_params):
+        check(self.L.mhd_set_params(self.h, C.byref(p)), "mhd_set_params")
+        self.p = p
+
+    def _blocks(self, blocks):
+        key = tuple(id(b) for b in blocks)
+        if key != self._key:
+            self._arr = block_array(blocks)
+            self._key = key
+        return self._arr, len(blocks)
+
+    def init_block(self, blk: DeviceBlock, A, stream=None):
+        d = blk.desc()
+        At = [a.contiguous() for a in A]
+        for c in range(3):
+            assert tuple(At[c].shape) == blk.edge_shape(c)
+        arr = (C.c_void_p * 3)(*[a.data_ptr() for a in At])
+        check(self.L.mhd_init_block(self.h, C.byref(d), arr, _sptr(stream)), "mhd_init_block")
+        self._keep = At
+
+    def prim2cons(self, prim, Bd, g, cons, stream=None):
+        n = prim.shape[1]
+        check(self.L.mhd_prim2cons(self.h, n, _ptr(prim), _ptr(Bd), _ptr(g), _ptr(cons), _sptr(stream)),
+              "mhd_prim2cons")
+
+    def c2p_cells(self, cons, Bd, g, prim, flags, iters=None, stream=None):
+        n = cons.shape[1]
+        check(self.L.mhd_c2p_cells(self.h, n, _ptr(cons), _ptr(Bd), _ptr(g), _ptr(prim), _ptr(flags),
+                                   _ptr(iters), _sptr(stream)), "mhd_c2p_cells")
+
+    def c2p(self, blocks, stream=None):
+        arr, nb = self._blocks(blocks)
+        check(self.L.mhd_c2p(self.h, arr, nb, _sptr(stream)), "mhd_c2p")
+
+    def rhs(self, blocks, dt, stage, stream=None):
+        arr, nb = self._blocks(blocks)
+        check(self.L.mhd_rhs(self.h, arr, nb, float(dt), int(stage), _sptr(stream)), "mhd_rhs")
+
+    def rk_update(self, blocks, dt, stage, stream=None):
+        arr, nb = self._blocks(blocks)
+        check(self.L.mhd_rk_update(self.h, arr, nb, float(dt), int(stage), _sptr(stream)), "mhd_rk_update")
+
+    def stage(self, blocks, dt, stage, stream=None):
+        self.c2p(blocks, stream)
+        self.rhs(blocks, dt, stage, stream)
+        self.rk_update(blocks, dt, stage, stream)
+
+    def step(self, blocks, dt, graph=False, stream=None):
+        arr, nb = self._blocks(blocks)
+        check(self.L.mhd_step(self.h, arr, nb, float(dt), int(bool(graph)), _sptr(stream)), "mhd_step")
+
+    def step_host(self, blk: DeviceBlock, host: dict, dt, stream=None, graph=False):
+        """One RK step of a block whose state lives in (pinned) host memory:
+        host["cons"], host["bf"][0..2] and host["adm"] are copied in, the step
+        runs, and the conserved state and face B~ are copied back, all on
+        `stream`."""
+        import torch
+        s = stream or torch.cuda.current_stream()
+        with torch.cuda.stream(s):
+            blk.cons.copy_(host["cons"], non_blocking=True)
+            blk.adm.copy_(host["adm"], non_blocking=True)
+            for d in range(3):
+                blk.bf[d].copy_(host["bf"][d], non_blocking=True)
+            self.step([blk], dt, graph=graph, stream=s)
+            host["cons"].copy_(blk.cons, non_blocking=True)
+            for d in range(3):
+                host["bf"][d].copy_(blk.bf[d], non_blocking=True)
+
+    def read_stats(self, stream=None) -> dict:
+        s = mhd_stats()
+        check(self.L.mhd_read_stats(self.h, C.byref(s), _sptr(stream)), "mhd_read_stats")
+        return s.as_dict()
+
+    def reset_stats(self, stream=None):
+        check(self.L.mhd_reset_stats(self.h, _sptr(stream)), "mhd_reset_stats")
+
+    def scratch(self, b: int, which: int, shape=None, stream=None):
+        """Host copy of a scratch array (fluxes 0..2, EMFs 3..5) of block b."""
+        n = C.c_long()
+        check(self.L.mhd_scratch_copy(self.h, int(b), int(which), None, 0, C.byref(n), _sptr(stream)),
+              "mhd_scratch_copy")
+        host = np.empty(n.value, np.float64)
+        check(self.L.mhd_scratch_copy(self.h, int(b), int(which), host.ctypes.data_as(C.c_void_p), n.value, None,
+                                      _sptr(stream)), "mhd_scratch_copy")
+        return host if shape is None else host.reshape(shape)
+
+    def launches(self) -> int:
+        return int(self.L.mhd_kernel_launches(self.h))
+
+    def profile(self, enable: bool):
+        check(self.L.mhd_profile(self.h, int(bool(enable))), "mhd_profile")
+
+    def profile_read(self) -> dict:
+        """{kernel name: (milliseconds, launches)} since the previous read."""
+        ms = (C.c_double * MHD_NKERNEL)()
+        n = (C.c_longlong * MHD_NKERNEL)()
+        check(self.L.mhd_profile_read(self.h, ms, n), "mhd_profile_read")
+        return {self.L.mhd_kernel_name(k).decode(): (ms[k], n[k]) for k in range(MHD_NKERNEL)}

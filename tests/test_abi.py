@@ -1,0 +1,49 @@
+"""Host-side checks of the C-ABI library (no GPU compute): it builds, loads and
+exports every entry point that include/grmhd.h declares; host-side argument
+validation rejects bad input before any device work."""
+import ctypes as C
+
+import pytest
+
+from paper_2409_10384_gb300 import build, grmhd
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return grmhd.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    names = grmhd.header_symbols()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(grmhd._SIGS)
+
+
+def test_strerror_names_every_code(L):
+    for code in (0, -1, -2, -3, -4, -5):
+        assert L.mhd_strerror(code).decode() == grmhd._ERR[code]
+    assert L.mhd_strerror(-99).decode() == "unknown error"
+
+
+def test_null_and_bad_arguments_rejected_without_device(L):
+    h = C.c_void_p()
+    assert L.mhd_init(None, C.byref(h)) == -1
+    p = grmhd.params(gamma=0.5)
+    assert L.mhd_init(C.byref(p), C.byref(h)) == -1
+    p = grmhd.params(rk_order=4)
+    assert L.mhd_init(C.byref(p), C.byref(h)) == -1
+    p = grmhd.params(dmp_M=0.5)
+    assert L.mhd_init(C.byref(p), C.byref(h)) == -1
+    assert L.mhd_c2p(None, None, 0, None) == -1
+    assert L.mhd_step(None, None, 1, 0.1, 0, None) == -1
+    assert L.mhd_kernel_launches(None) == 0
+
+
+def test_struct_layouts_match_header():
+    # mhd_params: 8 doubles + 6 ints; mhd_block: 3+1 ints, 3 doubles, 12 pointers; mhd_stats: 7 int64
+    assert C.sizeof(grmhd.mhd_params) == 8 * 8 + 6 * 4
+    assert C.sizeof(grmhd.mhd_block) == 16 + 24 + 12 * 8
+    assert C.sizeof(grmhd.mhd_stats) == 7 * 8

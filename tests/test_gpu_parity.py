@@ -1,0 +1,272 @@
+"""GPU (libgrmhd through its C-ABI) against the FP64 oracle, element by element.
+
+Bars: conserved variables and face fields 1e-12 per cell per substep, primitives
+1e-10 (relative, per cell, floored at 1e-10 of the field maximum); the pressure
+against its recovery scale (see tests/gpu_util.compare_prims).  FOFC flags are a
+threshold decision: the oracle is re-run with the GPU's flags injected for the
+value comparison, and every flag that differs must sit within rounding of its
+threshold.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2409_10384_gb300 import synth
+from tests import gpu_util as U
+from tests.helpers import fill_ghosts, interior, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2409_10384_gb300 import build, grmhd
+    build.build()
+    return grmhd
+
+
+def _ctx(G, p):
+    gp = G.params(**{k: getattr(p, k) for k, _ in p._fields_ if k != "pad_"})
+    return G.Context(gp)
+
+
+def test_prim2cons_cells(G):
+    import torch
+    p = O.params(gamma=2.0)
+    prim, Bd, g = synth.c2p_stress(50000, seed=4)
+    ref = O.prim2cons(p, prim, Bd, g)
+    ctx = _ctx(G, p)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    out = torch.zeros((5, prim.shape[1]), dtype=torch.float64, device="cuda")
+    ctx.prim2cons(t(prim), t(Bd), t(g), out)
+    got = out.cpu().numpy()
+    # D~ per cell; S~_i against the momentum magnitude of the cell; tau~ = E~ - D~
+    # against E~ (its absolute precision is that of D~)
+    assert rel_err(got[0], ref[0]) < U.CONS_TOL
+    smag = np.abs(ref[1:4]).max(axis=0)
+    assert np.max(np.abs(got[1:4] - ref[1:4]) / smag) < U.CONS_TOL
+    assert np.max(np.abs(got[4] - ref[4]) / (np.abs(ref[4]) + np.abs(ref[0]))) < U.CONS_TOL
+
+
+@pytest.mark.parametrize("n", [1, 33, 200000])
+def test_c2p_cells_stress(G, n):
+    import torch
+    p = O.params(gamma=2.0, rho_atm=1e-20, T_atm=1e-14, f_thr=0.0)
+    prim, Bd, g = synth.c2p_stress(n, seed=4)
+    cons = O.prim2cons(p, prim, Bd, g)
+    ref = O.c2p_cells(p, cons, Bd, g)
+    ctx = _ctx(G, p)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    dc = t(cons)
+    dp = torch.zeros((5, n), dtype=torch.float64, device="cuda")
+    fl = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    it = torch.zeros(n, dtype=torch.int32, device="cuda")
+    ctx.c2p_cells(dc, t(Bd), t(g), dp, fl, it)
+    got = dp.cpu().numpy()
+    assert np.array_equal(fl.cpu().numpy(), ref["flags"])
+    assert rel_err(got[0], ref["prim"][0], 0.0) < U.PRIM_TOL
+    W = np.sqrt(1 + (ref["prim"][1:4] ** 2).sum(0))
+    assert np.max(np.abs(got[1:4] - ref["prim"][1:4]) / W) < U.PRIM_TOL
+    det = g[0] * (g[3] * g[5] - g[4] ** 2) - g[1] * (g[1] * g[5] - g[4] * g[2]) + g[2] * (g[1] * g[4] - g[3] * g[2])
+    scale = (p.gamma - 1) * (cons[0] + cons[4]) / np.sqrt(det)
+    assert np.all(np.abs(got[4] - ref["prim"][4]) <= 1e-10 * np.abs(ref["prim"][4]) + 1e-12 * scale)
+    assert it.cpu().numpy().max() <= p.c2p_maxit + 2
+    st = ctx.read_stats()
+    assert st["cells"] == n and st["fails"] == 0
+
+
+def test_c2p_cells_floors_and_bad_input(G):
+    """Atmosphere floors and the error policy on hostile inputs: NaN, negative
+    D, tau below the floor, momentum beyond causality, a cold state."""
+    import torch
+    p = O.params(gamma=2.0, rho_atm=1e-10, T_atm=1e-8, f_thr=1.0)
+    g = np.tile(np.array([[1.0], [0], [0], [1.0], [0], [1.0]]), (1, 6))
+    Bd = np.tile(np.array([[0.0], [1e-6], [0.0]]), (1, 6))
+    prim_cold = np.array([[1e-3], [0.3], [0.0], [0.0], [1e-12]])
+    cold = O.prim2cons(p, prim_cold, Bd[:, :1], g[:, :1])[:, 0]
+    cons = np.array([
+        [np.nan, 0.0, 0.0, 0.0, 1.0],
+        [-1e-3, 0.0, 0.0, 0.0, 1e-3],
+        [1e-3, 0.0, 0.0, 0.0, 1e-30],
+        [1.0, 50.0, 0.0, 0.0, 1.0],
+        [1e-12, 1e-13, 0.0, 0.0, 1e-20],
+        list(cold),
+    ]).T.copy()
+    ref = O.c2p_cells(p, cons, Bd, g)
+    ctx = _ctx(G, p)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    dc = t(cons)
+    dp = torch.zeros((5, 6), dtype=torch.float64, device="cuda")
+    fl = torch.zeros(6, dtype=torch.uint8, device="cuda")
+    ctx.c2p_cells(dc, t(Bd), t(g), dp, fl)
+    got = dp.cpu().numpy()
+    assert np.array_equal(fl.cpu().numpy(), ref["flags"]), (fl.cpu().numpy(), ref["flags"])
+    assert np.all(np.isfinite(got))
+    for c in range(6):
+        assert np.allclose(got[:, c], ref["prim"][:, c], rtol=1e-10, atol=1e-300), c
+    gc = dc.cpu().numpy()
+    rc = ref["cons"][:, 1:]
+    assert np.allclose(gc[:4, 1:], rc[:4], rtol=1e-12, atol=0)
+    assert np.all(np.abs(gc[4, 1:] - rc[4]) <= 1e-12 * (np.abs(rc[4]) + np.abs(rc[0])))
+
+
+def test_init_block_matches_oracle(G):
+    import torch
+    p = O.params(gamma=5.0 / 3.0)
+    inp = synth.periodic_flat(1)
+    ob = O.init_block(p, inp.n, inp.ng, inp.dx, inp.adm, inp.prim, inp.A)
+    ctx = _ctx(G, p)
+    db = G.DeviceBlock(inp.n, inp.ng, inp.dx, inp.adm)
+    db.prim.copy_(torch.from_numpy(inp.prim))
+    ctx.init_block(db, [torch.from_numpy(a).cuda() for a in inp.A])
+    got = U.from_device(db)
+    for d in range(3):
+        assert rel_err(got["bf"][d], ob.bf[d]) < 1e-14
+    for v in range(5):
+        assert rel_err(got["cons"][v], ob.cons[v]) < 1e-13
+
+
+def _run_stage_pair(G, ctx, p, ob, dt, s, check_fluxes=True, inject=True):
+    """One stage on both sides from the same input; returns (oracle out, gpu dict)."""
+    db = U.to_device(G, ob)
+    ctx.stage([db], dt, s)
+    got = U.from_device(db)
+    mask = None
+    flips = []
+    if p.fofc and inject:
+        I = interior(ob)
+        gm = (got["flags"] & O.F_FOFC) != 0
+        mask = np.zeros(ob.cons.shape[1:], np.uint8)
+        mask[I] = gm[I]
+        own = ob.copy()
+        O.stage(p, own, dt, s)
+        om = (own.flags & O.F_FOFC) != 0
+        diff = np.argwhere(gm[I] != om[I])
+        if len(diff):
+            Us, Upost, bpost = U.ho_ustar(p, ob, dt, s)
+            cells = [tuple(int(x) + ob.ng for x in c) for c in diff]
+            okk = U.flip_is_rounding(p, Us, Upost, bpost, cells)
+            assert all(okk), f"FOFC flag flips away from a threshold at {[c for c, o in zip(cells, okk) if not o]}"
+            flips = cells
+    ref = ob.copy()
+    out = O.stage(p, ref, dt, s, mask=mask, keep=True)
+    ref.scales = U.term_scales(p, ob, out, dt, s)
+    if check_fluxes:
+        for d in range(3):
+            Fg = ctx.scratch(0, d, out["flux"][d].shape)
+            # compare the faces the stage computes (nonzero in the oracle's array)
+            m = np.any(out["flux"][d] != 0, axis=0)
+            # a flux is a difference of O(U) terms: compare against the field
+            # maximum; the tau~ flux carries the precision of the D~ flux
+            for c in range(7):
+                Fr = out["flux"][d][c][m]
+                sc = np.abs(Fr).max() + (np.abs(out["flux"][d][0][m]).max() if c == 4 else 0.0)
+                assert np.max(np.abs(Fg[c][m] - Fr)) <= 1e-13 * sc, ("flux", d, c)
+    return ref, got, flips
+
+
+def test_stage_periodic_flat_plm_hlle(G):
+    """Configuration 1: 32^3 + 4 ghosts, flat, Gamma 5/3, PLM + HLLE + CT, RK2."""
+    p = O.params(gamma=5.0 / 3.0, recon=1, rsolver=1, rk_order=2, fofc=0)
+    inp = synth.periodic_flat(1)
+    ob = O.init_block(p, inp.n, inp.ng, inp.dx, inp.adm, inp.prim, inp.A)
+    ctx = _ctx(G, p)
+    dt = 0.25 / 32
+    for s in range(2):
+        fill_ghosts(ob)
+        ref, got, _ = _run_stage_pair(G, ctx, p, ob, dt, s)
+        U.compare_prims(ref, got, p, f"stage {s}")
+        U.compare_state(ref, got, f"stage {s}", scales=ref.scales)
+        # next substep starts from the GPU result (per-substep parity)
+        ob.cons[...] = got["cons"]
+        ob.cons0[...] = got["cons0"]
+        for d in range(3):
+            ob.bf[d][...] = got["bf"][d]
+            ob.bf0[d][...] = got["bf0"][d]
+
+
+@pytest.mark.parametrize("where,recon,rs,dmp", [("surface", 2, 1, 0.0), ("surface", 2, 0, 1.1),
+                                                ("surface", 0, 1, 0.0), ("core", 2, 1, 0.0), ("core", 1, 0, 1.2)])
+def test_stage_star_fofc(G, where, recon, rs, dmp):
+    """Sub-blocks of the 128^3 star workload (dynamical metric with K_ij): over the
+    stellar surface (atmosphere, FOFC fires) and over the magnetised core;
+    WENO-Z/PLM/donor + HLLE/LLF + FOFC (+DMP) + CT, all three RK3 substeps."""
+    p = O.params(gamma=2.0, rho_atm=1e-12, T_atm=1e-10, f_thr=0.1, recon=recon, rsolver=rs, rk_order=3,
+                 fofc=1, dmp_M=dmp)
+    corner = (104, 52, 52) if where == "surface" else (52, 52, 52)
+    inp = synth.star_subblock(sub=24, corner=corner)
+    ob = O.init_block(p, inp.n, inp.ng, inp.dx, inp.adm, inp.prim, inp.A)
+    ctx = _ctx(G, p)
+    dt = 0.25 * inp.dx[0]
+    total_flips = 0
+    for s in range(3):
+        ref, got, flips = _run_stage_pair(G, ctx, p, ob, dt, s)
+        total_flips += len(flips)
+        U.compare_prims(ref, got, p, f"stage {s}")
+        U.compare_state(ref, got, f"stage {s}", scales=ref.scales)
+        ob.cons[...] = got["cons"]
+        ob.cons0[...] = got["cons0"]
+        for d in range(3):
+            ob.bf[d][...] = got["bf"][d]
+            ob.bf0[d][...] = got["bf0"][d]
+    st = ctx.read_stats()
+    if where == "surface":
+        assert st["fofc_cells"] > 0  # the surface and the atmosphere trigger FOFC
+    # every flip was verified above to sit within rounding of its threshold
+    assert total_flips <= 0.02 * 24 ** 3
+
+
+def test_graph_step_equals_stage_calls(G):
+    import torch
+    p = O.params(gamma=2.0, rho_atm=1e-12, T_atm=1e-10, recon=2, rsolver=1, rk_order=3, fofc=1)
+    inp = synth.star_subblock(sub=16, corner=(56, 56, 56))
+    ob = O.init_block(p, inp.n, inp.ng, inp.dx, inp.adm, inp.prim, inp.A)
+    ctx = _ctx(G, p)
+    dt = 0.25 * inp.dx[0]
+    a = U.to_device(G, ob)
+    b = U.to_device(G, ob)
+    for s in range(3):
+        ctx.stage([a], dt, s)
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        ctx.step([b], dt, graph=True, stream=stream)
+        ctx.step([b], dt, graph=True, stream=stream)   # replay
+    stream.synchronize()
+    torch.cuda.synchronize()
+    for s in range(3):
+        ctx.stage([a], dt, s)
+    torch.cuda.synchronize()
+    assert torch.equal(a.cons, b.cons)
+    for d in range(3):
+        assert torch.equal(a.bf[d], b.bf[d])
+
+
+def test_batched_uneven_blocks(G):
+    """Several blocks of different sizes and levels in one launch per kernel,
+    each against the oracle on its own."""
+    p = O.params(gamma=2.0, rho_atm=1e-12, T_atm=1e-10, recon=2, rsolver=1, rk_order=3, fofc=1)
+    st = synth.spacetime(3)
+    specs = [((8, 8, 8), 0.75, (-3.0, -3.0, -3.0)), ((12, 12, 12), 0.375, (-2.0, 0.5, -1.0)),
+             ((16, 16, 16), 0.1875, (0.3, -1.2, 0.4)), ((8, 8, 8), 0.75, (-40.0, -3.0, 5.0))]
+    obs = []
+    for n, dx, x0 in specs:
+        inp = synth.star_block(st, n, 4, (dx,) * 3, x0)
+        obs.append(O.init_block(p, inp.n, inp.ng, inp.dx, inp.adm, inp.prim, inp.A))
+    ctx = _ctx(G, p)
+    dt = 0.25 * 0.1875
+    dbs = [U.to_device(G, ob) for ob in obs]
+    ctx.stage(dbs, dt, 0)
+    for ob, db in zip(obs, dbs):
+        got = U.from_device(db)
+        I = interior(ob)
+        gm = (got["flags"] & O.F_FOFC) != 0
+        mask = np.zeros(ob.cons.shape[1:], np.uint8)
+        mask[I] = gm[I]
+        ref = ob.copy()
+        out = O.stage(p, ref, dt, 0, mask=mask, keep=True)
+        U.compare_prims(ref, got, p)
+        U.compare_state(ref, got, scales=U.term_scales(p, ob, out, dt, 0))
