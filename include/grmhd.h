@@ -35,6 +35,7 @@ typedef struct mhd_ctx mhd_ctx; /* opaque; owns scratch only, never state */
 #define MHD_ENOMEM (-3)    /* scratch allocation failed */
 #define MHD_ESTATE (-4)    /* call out of order (e.g. rk_update before rhs) */
 #define MHD_ENOMLP (-5)    /* learned guess requested but no network loaded */
+#define MHD_ETOOBIG (-6)   /* block too large for mhd_stage_noalloc's static scratch */
 
 /* Per-cell flag bits written to mhd_block.flags (and mhd_c2p_cells). */
 #define MHD_F_FAIL 1u      /* root solve failed: cell reset to atmosphere */
@@ -171,6 +172,27 @@ long long mhd_kernel_launches(const mhd_ctx* ctx);
 int mhd_profile(mhd_ctx* ctx, int enable);
 int mhd_profile_read(mhd_ctx* ctx, double* ms, long long* count);
 const char* mhd_kernel_name(int kind);
+
+/* Allocation-free stage (the paper has no counterpart: this serves callers).
+ * Some callers cannot let a library allocate device memory: a host code that
+ * gives its whole GPU memory budget to its own pool allocator, one that cannot
+ * accept the device-wide synchronisation a cudaFree implies inside a time
+ * step, or one with nowhere to keep a library context.  mhd_stage_noalloc runs
+ * one RK stage (`stage`, 0-based, of p->rk_order) of ONE block -- con2prim,
+ * fluxes, FOFC, CT EMFs and the update, the same kernels and results as
+ * mhd_c2p + mhd_rhs + mhd_rk_update -- with no context and without calling
+ * cudaMalloc, cudaFree or any allocating routine.  Its scratch is a
+ * file-scope device array of MHD_NOALLOC_SCRATCH_BYTES (16 MiB), held by
+ * every GPU that loads the library until the process exits; a block whose
+ * scratch does not fit (e.g. interior larger than 32^3 with 4 ghosts) is
+ * rejected with MHD_ETOOBIG before any device work.  The caller still owns
+ * every state array of `blk` (device memory).  The first call on a device,
+ * with that device current, looks up the array's device address; make that
+ * first call before any stream capture.  All calls share the array and it
+ * keeps the last call's contents: calls whose kernels overlap on the GPU
+ * race.  p->c2p_guess must be 0.  Counters are not reported. */
+#define MHD_NOALLOC_SCRATCH_BYTES (16u << 20)
+int mhd_stage_noalloc(const mhd_params* p, const mhd_block* blk, double dt, int stage, void* stream);
 
 #ifdef __cplusplus
 }

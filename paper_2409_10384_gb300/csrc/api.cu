@@ -358,6 +358,7 @@ const char* mhd_strerror(int code) {
     case MHD_ENOMEM: return "device allocation failed";
     case MHD_ESTATE: return "call out of order";
     case MHD_ENOMLP: return "learned guess requested but no network loaded";
+    case MHD_ETOOBIG: return "block exceeds the 16 MiB static scratch of mhd_stage_noalloc";
     default: return "unknown error";
   }
 }

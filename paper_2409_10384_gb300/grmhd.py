@@ -19,7 +19,8 @@ from . import build as _build
 MHD_F_FAIL, MHD_F_DFLOOR, MHD_F_SIGMA, MHD_F_TAU, MHD_F_RHO, MHD_F_TEMP, MHD_F_VMAX, MHD_F_FOFC = (
     1, 2, 4, 8, 16, 32, 64, 128)
 _ERR = {0: "ok", -1: "invalid argument", -2: "CUDA runtime error", -3: "device allocation failed",
-        -4: "call out of order", -5: "learned guess requested but no network loaded"}
+        -4: "call out of order", -5: "learned guess requested but no network loaded",
+        -6: "block exceeds the 16 MiB static scratch of mhd_stage_noalloc"}
 
 
 class mhd_params(C.Structure):
@@ -73,6 +74,7 @@ _SIGS = {
     "mhd_profile": (_I, [_VP, _I]),
     "mhd_profile_read": (_I, [_VP, _VP, _VP]),
     "mhd_kernel_name": (C.c_char_p, [_I]),
+    "mhd_stage_noalloc": (_I, [C.POINTER(mhd_params), C.POINTER(mhd_block), _D, _I, _VP]),
 }
 MHD_NKERNEL = 9
 
@@ -170,6 +172,13 @@ class DeviceBlock:
             b.bf[d] = self.bf[d].data_ptr()
             b.bf0[d] = self.bf0[d].data_ptr()
         return b
+
+
+def stage_noalloc(p: mhd_params, blk: DeviceBlock, dt: float, stage: int, stream=None) -> int:
+    """mhd_stage_noalloc on one block (no context, no device allocation);
+    returns the status code."""
+    d = blk.desc()
+    return int(lib().mhd_stage_noalloc(C.byref(p), C.byref(d), float(dt), int(stage), _sptr(stream)))
 
 
 def block_array(blocks) -> C.Array:
