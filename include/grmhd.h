@@ -154,16 +154,17 @@ int mhd_scratch_copy(mhd_ctx* ctx, int b, int which, double* dst, long count, lo
 long long mhd_kernel_launches(const mhd_ctx* ctx);
 
 /* Kernel kinds for per-kernel timing. */
-#define MHD_K_C2P 0        /* con2prim of the stencil region */
+#define MHD_K_C2P 0        /* con2prim of the stencil region (prep + finish) */
 #define MHD_K_FLUX_X 1     /* reconstruction + Riemann flux, x faces */
 #define MHD_K_FLUX_Y 2
 #define MHD_K_FLUX_Z 3
-#define MHD_K_FOFC_FLAG 4  /* FOFC estimate, con2prim of U*, DMP */
+#define MHD_K_FOFC_FLAG 4  /* FOFC estimate U*, its con2prim prep + finish, DMP */
 #define MHD_K_FOFC_FIX 5   /* first-order recompute of flagged faces */
 #define MHD_K_EMF 6        /* upwind CT edge EMFs */
 #define MHD_K_UPDATE 7     /* RK update of U with the Eq. 9 sources */
 #define MHD_K_FACEB 8      /* RK update of the face B~ */
-#define MHD_NKERNEL 9
+#define MHD_K_SOLVE 9      /* con2prim root solves (stage input and U*) */
+#define MHD_NKERNEL 10
 
 /* enable != 0: bracket every kernel launched outside stream capture by CUDA
  * events on its own stream.  mhd_profile_read waits for them and returns, per

@@ -1,5 +1,6 @@
 // C-ABI of libgrmhd: context, block lists, scratch, launch sequencing and the
 // CUDA-graph step.  Declarations and argument conventions: include/grmhd.h.
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -13,6 +14,12 @@ struct mhd_ctx {
   Par P;
   int dev = 0, nsm = 1;
   int occ_c2p[2] = {1, 1}, occ_face[5] = {1, 1, 1, 1, 1}, occ_upd[3] = {1, 1, 1};
+  int occ_krp[7] = {1, 1, 1, 1, 1, 1, 1};
+  // three-phase con2prim scratch: of the block list, and of independent cells
+  char* krp = nullptr;
+  long long krp_n = 0;
+  char* cells_buf = nullptr;
+  size_t cells_bytes = 0;
   // current block list
   std::vector<mhd_block> key;
   std::vector<DevBlock> hblk;
@@ -23,6 +30,8 @@ struct mhd_ctx {
   size_t scratch_bytes = 0;
   long long list_version = 0;
   int grid[W_NKIND] = {0};
+  int g_kprep = 1, g_kfin = 1, g_fprep = 1, g_ffin = 1, g_solve = 1;
+  int g_solve_cells() const { return nsm * (occ_krp[1] > 0 ? occ_krp[1] : 1); }
   // counters
   unsigned long long* dstats = nullptr;
   long long launches = 0;
@@ -147,6 +156,9 @@ int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
     items[W_INIT] = b.ncell;
     for (int k = 0; k < W_NKIND; k++) pre[(size_t)k * (nb + 1) + i + 1] = pre[(size_t)k * (nb + 1) + i] + items[k];
   }
+  const long long nkrp = std::max(pre[(size_t)W_C2P * (nb + 1) + nb], pre[(size_t)W_CELL * (nb + 1) + nb]);
+  const size_t krp_off = need;
+  need += al256(krp_bytes(nkrp));
   if (need > c->scratch_bytes) {
     if (c->scratch) cudaFree(c->scratch);
     c->scratch = nullptr;
@@ -175,6 +187,8 @@ int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
     b.fflag = (unsigned char*)p;
     p += al256((size_t)b.ncell);
   }
+  c->krp = c->scratch + krp_off;
+  c->krp_n = nkrp;
   if (c->dblk) cudaFree(c->dblk);
   if (c->dpre) cudaFree(c->dpre);
   c->dblk = nullptr;
@@ -205,6 +219,11 @@ int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
   c->grid[W_EDGE] = grid_of(W_EDGE, 128, c->occ_upd[0]);
   c->grid[W_FACE] = grid_of(W_FACE, 256, c->occ_upd[2]);
   c->grid[W_INIT] = grid_of(W_CELL, 128, c->occ_upd[1]);
+  c->g_kprep = grid_of(W_C2P, 128, c->occ_krp[0]);
+  c->g_kfin = grid_of(W_C2P, 128, c->occ_krp[2]);
+  c->g_fprep = grid_of(W_CELL, 128, c->occ_krp[3]);
+  c->g_ffin = grid_of(W_CELL, 128, c->occ_krp[4]);
+  c->g_solve = c->nsm * std::max(c->occ_krp[1], 1);
   return MHD_OK;
 }
 
@@ -253,7 +272,11 @@ Work work_of(const mhd_ctx* c) {
 
 int enqueue_c2p(mhd_ctx* c, cudaStream_t s) {
   Work w = work_of(c);
-  timed(c, MHD_K_C2P, s, [&] { launch_c2p_block(w, c->P, c->dstats, s, c->grid[W_C2P]); });
+  const long long n = c->hpre[(size_t)W_C2P * (c->key.size() + 1) + c->key.size()];
+  KrpBuf kb = krp_view(c->krp, n);
+  timed(c, MHD_K_C2P, s, [&] { launch_krp_prep_block(w, c->P, kb, s, c->g_kprep); });
+  timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, c->dstats, s, c->g_solve); });
+  timed(c, MHD_K_C2P, s, [&] { launch_krp_finish_block(w, c->P, kb, c->dstats, s, c->g_kfin); });
   return cuda_ok(cudaGetLastError());
 }
 
@@ -265,7 +288,11 @@ int enqueue_rhs(mhd_ctx* c, double dt, int stage, cudaStream_t s) {
   for (int d = 0; d < 3; d++)
     timed(c, MHD_K_FLUX_X + d, s, [&] { launch_flux_dir(d, w, c->P, s, gf[d]); });
   if (c->P.fofc) {
-    timed(c, MHD_K_FOFC_FLAG, s, [&] { launch_fofc_flag(w, c->P, g0, g1, be * dt, c->dstats, s, c->grid[W_CELL]); });
+    const long long n = c->hpre[(size_t)W_CELL * (c->key.size() + 1) + c->key.size()];
+    KrpBuf kb = krp_view(c->krp, n);
+    timed(c, MHD_K_FOFC_FLAG, s, [&] { launch_krp_prep_fofc(w, c->P, g0, g1, be * dt, kb, s, c->g_fprep); });
+    timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, c->dstats, s, c->g_solve); });
+    timed(c, MHD_K_FOFC_FLAG, s, [&] { launch_krp_finish_fofc(w, c->P, kb, c->dstats, s, c->g_ffin); });
     for (int d = 0; d < 3; d++)
       timed(c, MHD_K_FOFC_FIX, s, [&] { launch_fofc_fix(d, w, c->P, c->dstats, s, gf[d]); });
   }
@@ -310,7 +337,8 @@ int mhd_init(const mhd_params* p, mhd_ctx** out) {
     delete c;
     return MHD_ECUDA;
   }
-  if (occupancy_c2p(c->occ_c2p) || occupancy_face(c->occ_face) || occupancy_update(c->occ_upd)) {
+  if (occupancy_c2p(c->occ_c2p) || occupancy_face(c->occ_face) || occupancy_update(c->occ_upd) ||
+      occupancy_krp(c->occ_krp)) {
     delete c;
     return MHD_ECUDA;
   }
@@ -342,6 +370,7 @@ void mhd_finalize(mhd_ctx* c) {
   if (c->dblk) cudaFree(c->dblk);
   if (c->dpre) cudaFree(c->dpre);
   if (c->dstats) cudaFree(c->dstats);
+  if (c->cells_buf) cudaFree(c->cells_buf);
   for (auto& r : c->recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -397,11 +426,27 @@ int mhd_c2p_cells(mhd_ctx* c, long n, double* cons, const double* Bd, const doub
                   unsigned char* flags, int* iters, void* stream) {
   if (!c || n < 0 || (n > 0 && (!cons || !Bd || !g || !prim || !flags))) return MHD_EINVAL;
   if (n == 0) return MHD_OK;
-  long long nb = (n + 127) / 128;
-  long long cap = (long long)c->nsm * c->occ_c2p[0];
-  int grid = (int)(nb < cap ? nb : cap);
-  launch_c2p_cells(c->P, n, cons, Bd, g, prim, flags, iters, nullptr, c->dstats, (cudaStream_t)stream, grid);
-  c->launches += 1;
+  const size_t need = krp_bytes(n);
+  if (need > c->cells_bytes) {
+    cudaStreamSynchronize((cudaStream_t)stream);
+    if (c->cells_buf) cudaFree(c->cells_buf);
+    c->cells_buf = nullptr;
+    c->cells_bytes = 0;
+    if (cudaMalloc(&c->cells_buf, need) != cudaSuccess) return MHD_ENOMEM;
+    c->cells_bytes = need;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  KrpBuf kb = krp_view(c->cells_buf, n);
+  auto grid = [&](int occ) {
+    long long nb = (n + 127) / 128, cap = (long long)c->nsm * std::max(occ, 1);
+    return (int)std::max(1LL, std::min(nb, cap));
+  };
+  const float* guess = nullptr;
+  timed(c, MHD_K_C2P, s, [&] { launch_krp_prep_cells(c->P, kb, cons, Bd, g, guess, s, grid(c->occ_krp[5])); });
+  timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, c->dstats, s, c->g_solve_cells()); });
+  timed(c, MHD_K_C2P, s, [&] {
+    launch_krp_finish_cells(c->P, kb, cons, Bd, g, prim, flags, iters, c->dstats, s, grid(c->occ_krp[6]));
+  });
   return cuda_ok(cudaGetLastError());
 }
 
@@ -529,7 +574,7 @@ int mhd_profile_read(mhd_ctx* c, double* ms, long long* count) {
 
 const char* mhd_kernel_name(int kind) {
   static const char* names[MHD_NKERNEL] = {"c2p", "flux_x", "flux_y", "flux_z", "fofc_flag",
-                                           "fofc_fix", "emf", "update", "faceb"};
+                                           "fofc_fix", "emf", "update", "faceb", "c2p_solve"};
   return (kind >= 0 && kind < MHD_NKERNEL) ? names[kind] : "unknown";
 }
 

@@ -43,6 +43,16 @@ struct DevBlock {
 // Work lists: item ranges of every block for one kernel kind.
 enum WorkKind { W_C2P = 0, W_FX, W_FY, W_FZ, W_CELL, W_EDGE, W_FACE, W_INIT, W_NKIND };
 
+// Per-cell scratch of the three-phase con2prim (k_krp.cu).
+struct KrpBuf {
+  double* w;                 // [KW_N][n] KRP variables, bracket, root
+  int* it;                   // [n] iterations
+  unsigned char* st;         // [n] solve status
+  unsigned char* fl;         // [n] flags of the prep phase
+  unsigned long long* ctr;   // work-queue head of the root solve
+  long long n;
+};
+
 struct Work {
   const DevBlock* blk;          // device array [nblocks]
   const long long* pre;         // device [W_NKIND][nblocks+1] item prefix sums
@@ -216,14 +226,17 @@ __device__ __forceinline__ bool illinois(const KS& s, double a, double Ga, doubl
   return true;
 }
 
-// The con2prim of one cell.  U: densitised conserved state (overwritten with
-// the floored state when write_cons and a floor fired); Bd: cell-centred B~;
-// m: metric with inverse.  lo/hi: optional bracket guess (lo < 0: none).
-__device__ __forceinline__ void con2prim(const Par& P, double* U, const double* Bd, const Metric& m, double* prim,
-                                         unsigned& flags, int& iters, bool write_cons, double glo = -1.0,
-                                         double ghi = -1.0) {
+// Everything the root solve and the recovery need of one cell.
+struct KrpCell {
+  KS s;
+  double D, rb, ru[3], bu[3];
+};
+
+// Phase 1: undensitise, apply the floors on the conserved state (Sec. 3.3) and
+// form the KRP variables.  Returns false (F_FAIL set) on non-finite input.
+__device__ __forceinline__ bool krp_prep(const Par& P, const double* U, const double* Bd, const Metric& m,
+                                         KrpCell& k, unsigned& flags) {
   flags = 0;
-  iters = 0;
   const double isd = m.isdet;
   double D = U[0] * isd, tau = U[4] * isd;
   double Sl[3] = {U[1] * isd, U[2] * isd, U[3] * isd};
@@ -231,107 +244,146 @@ __device__ __forceinline__ void con2prim(const Par& P, double* U, const double* 
   double Bl[3];
   lower3(m.g, B, Bl);
   double B2 = dot3(B, Bl);
-  double rho = P.rho_atm, p = P.P_atm, w0 = 0.0, w1 = 0.0, w2 = 0.0;
   bool fin = isfinite(D) && isfinite(tau) && isfinite(Sl[0]) && isfinite(Sl[1]) && isfinite(Sl[2]) &&
              isfinite(B2) && m.sdet > 0.0;
   if (!fin) {
     flags |= F_FAIL;
-  } else {
-    if (D < P.rho_thr) {
-      D = P.rho_atm;
-      Sl[0] = Sl[1] = Sl[2] = 0.0;
-      tau = fma(D, P.eps_atm, 0.5 * B2);
-      flags |= F_DFLOOR;
-    }
-    if (P.sigma_max > 0.0 && B2 > P.sigma_max * D) {
-      D = B2 / P.sigma_max;
-      flags |= F_SIGMA;
-    }
-    double tau_atm = fma(D, P.eps_atm, 0.5 * B2);
-    if (tau < tau_atm) {
-      tau = tau_atm;
-      flags |= F_TAU;
-    }
-    KS s;
-    double iD = 1.0 / D;
-    double rl[3] = {Sl[0] * iD, Sl[1] * iD, Sl[2] * iD};
-    double ru[3];
-    lower3(m.gi, rl, ru);
-    double isD = sqrt(iD);
-    double bu[3] = {B[0] * isD, B[1] * isD, B[2] * isD};
-    s.b2 = B2 * iD;
-    s.r2 = dot3(rl, ru);
-    double rb = dot3(rl, bu);
-    s.rb2 = rb * rb;
-    double rp = s.r2 * s.b2 - s.rb2;
-    s.rperp2 = rp > 0.0 ? rp : 0.0;
-    s.qh = fma(tau, iD, -0.5 * s.b2);
-    s.gam = P.gam;
-    s.eps_min = P.eps_atm;
-    s.vmax2 = P.vmax2;
-    // bracket: G(0) = -1 exactly (v = 0, W = 1)
-    KEval e;
-    double a = 0.0, Ga = -1.0, b, Gb;
-    bool have = false;
-    if (glo >= 0.0 && ghi > glo) {
-      // learned bracket, verified by the signs at both ends
-      KEval el, eh;
-      kev(s, glo, el);
-      kev(s, ghi, eh);
-      if (el.G < 0.0 && eh.G >= 0.0) {
-        a = glo; Ga = el.G; b = ghi; Gb = eh.G; have = true;
-      } else if (el.G >= 0.0) {
-        b = glo; Gb = el.G; have = true;              // root in [0, glo]
-      } else {
-        a = ghi; Ga = eh.G;                            // root above ghi
-      }
-      iters += 2;
-    }
-    if (!have) {
-      double mp = mu_plus(s);
-      if (mp <= a) mp = 1.0;
-      kev(s, mp, e);
-      b = mp; Gb = e.G;
-      if (Gb < 0.0) {
-        a = mp; Ga = Gb;
-        b = 1.0;
-        kev(s, b, e);
-        Gb = e.G;
-      }
-    }
-    double mu = 0.0;
-    int it = 0;
-    bool ok = (Ga < 0.0) && (Gb >= 0.0) && illinois(s, a, Ga, b, Gb, P.tol, P.maxit, mu, it);
-    iters += it;
-    if (!ok || !isfinite(mu)) {
-      flags |= F_FAIL;
+    return false;
+  }
+  if (D < P.rho_thr) {
+    D = P.rho_atm;
+    Sl[0] = Sl[1] = Sl[2] = 0.0;
+    tau = fma(D, P.eps_atm, 0.5 * B2);
+    flags |= F_DFLOOR;
+  }
+  if (P.sigma_max > 0.0 && B2 > P.sigma_max * D) {
+    D = B2 / P.sigma_max;
+    flags |= F_SIGMA;
+  }
+  double tau_atm = fma(D, P.eps_atm, 0.5 * B2);
+  if (tau < tau_atm) {
+    tau = tau_atm;
+    flags |= F_TAU;
+  }
+  KS& s = k.s;
+  double iD = 1.0 / D;
+  double rl[3] = {Sl[0] * iD, Sl[1] * iD, Sl[2] * iD};
+  lower3(m.gi, rl, k.ru);
+  double isD = sqrt(iD);
+  k.bu[0] = B[0] * isD; k.bu[1] = B[1] * isD; k.bu[2] = B[2] * isD;
+  s.b2 = B2 * iD;
+  s.r2 = dot3(rl, k.ru);
+  k.rb = dot3(rl, k.bu);
+  s.rb2 = k.rb * k.rb;
+  double rp = s.r2 * s.b2 - s.rb2;
+  s.rperp2 = rp > 0.0 ? rp : 0.0;
+  s.qh = fma(tau, iD, -0.5 * s.b2);
+  s.gam = P.gam;
+  s.eps_min = P.eps_atm;
+  s.vmax2 = P.vmax2;
+  k.D = D;
+  return true;
+}
+
+// Phase 2a: a bracket [a,b] with G(a) < 0 <= G(b).  G(0) = -1 exactly (v = 0,
+// W = 1).  A learned guess [glo, ghi] is used when given and verified by the
+// signs at both ends; otherwise [0, mu+] (or [mu+, 1] when G(mu+) < 0).
+// Returns 0: solve needed; 1: root found (in mu); 2: no bracket (failure).
+__device__ __forceinline__ int krp_bracket(const KS& s, double glo, double ghi, double& a, double& b, double& Ga,
+                                           double& Gb, double& mu, int& iters) {
+  KEval e;
+  a = 0.0; Ga = -1.0; b = 1.0; Gb = 0.0;
+  iters = 0;
+  bool have = false;
+  if (glo >= 0.0 && ghi > glo) {
+    KEval el, eh;
+    kev(s, glo, el);
+    kev(s, ghi, eh);
+    if (el.G < 0.0 && eh.G >= 0.0) {
+      a = glo; Ga = el.G; b = ghi; Gb = eh.G; have = true;
+    } else if (el.G >= 0.0) {
+      b = glo; Gb = el.G; have = true;
     } else {
-      kev(s, mu, e);
-      if (e.eps_raw < s.eps_min) flags |= F_TEMP;
-      if (e.vcap) flags |= F_VMAX;
-      double iW = e.W * (1.0 - (e.vcap ? s.vmax2 : mu * mu * e.rbar2));
-      rho = D * iW;
-      p = P.gm1 * rho * e.eps;
-      double vs = 1.0;
-      if (e.vcap) vs = sqrt(s.vmax2 / (mu * mu * e.rbar2));
-      double f = e.W * vs * mu * e.x;
-      double mrb = mu * rb;
-      w0 = f * fma(mrb, bu[0], ru[0]);
-      w1 = f * fma(mrb, bu[1], ru[1]);
-      w2 = f * fma(mrb, bu[2], ru[2]);
-      if (rho < P.rho_thr) {
-        rho = P.rho_atm; p = P.P_atm; w0 = w1 = w2 = 0.0;
-        flags |= F_RHO;
-      } else if (p < rho * P.T_atm) {
-        p = rho * P.T_atm;
-        flags |= F_TEMP;
-      }
+      a = ghi; Ga = eh.G;
+    }
+    iters += 2;
+  }
+  if (!have) {
+    double mp = mu_plus(s);
+    if (mp <= a) mp = 1.0;
+    kev(s, mp, e);
+    b = mp; Gb = e.G;
+    if (Gb < 0.0) {
+      a = mp; Ga = Gb;
+      b = 1.0;
+      kev(s, b, e);
+      Gb = e.G;
+    }
+  }
+  if (!(Ga < 0.0 && Gb >= 0.0)) return 2;
+  if (Gb == 0.0) { mu = b; return 1; }
+  return 0;
+}
+
+// Phase 3: primitives at the root mu (Sec. 3.4 recovery) and the floors on
+// the primitives (Sec. 3.3).  On failure the static atmosphere.
+__device__ __forceinline__ void krp_finish(const Par& P, const KrpCell& k, double mu, bool ok, unsigned& flags,
+                                           double* prim) {
+  double rho = P.rho_atm, p = P.P_atm, w0 = 0.0, w1 = 0.0, w2 = 0.0;
+  if (!ok || !isfinite(mu)) {
+    flags |= F_FAIL;
+  } else {
+    const KS& s = k.s;
+    KEval e;
+    kev(s, mu, e);
+    if (e.eps_raw < s.eps_min) flags |= F_TEMP;
+    if (e.vcap) flags |= F_VMAX;
+    double iW = e.W * (1.0 - (e.vcap ? s.vmax2 : mu * mu * e.rbar2));
+    rho = k.D * iW;
+    p = P.gm1 * rho * e.eps;
+    double vs = 1.0;
+    if (e.vcap) vs = sqrt(s.vmax2 / (mu * mu * e.rbar2));
+    double f = e.W * vs * mu * e.x;
+    double mrb = mu * k.rb;
+    w0 = f * fma(mrb, k.bu[0], k.ru[0]);
+    w1 = f * fma(mrb, k.bu[1], k.ru[1]);
+    w2 = f * fma(mrb, k.bu[2], k.ru[2]);
+    if (rho < P.rho_thr) {
+      rho = P.rho_atm; p = P.P_atm; w0 = w1 = w2 = 0.0;
+      flags |= F_RHO;
+    } else if (p < rho * P.T_atm) {
+      p = rho * P.T_atm;
+      flags |= F_TEMP;
     }
   }
   if (flags & F_FAIL) {
     rho = P.rho_atm; p = P.P_atm; w0 = w1 = w2 = 0.0;
   }
   prim[0] = rho; prim[1] = w0; prim[2] = w1; prim[3] = w2; prim[4] = p;
+}
+
+// The con2prim of one cell in one thread.  U: densitised conserved state
+// (overwritten with the floored state when write_cons and a floor fired); Bd:
+// cell-centred B~; m: metric with inverse.  glo/ghi: optional bracket guess
+// (glo < 0: none).
+__device__ __forceinline__ void con2prim(const Par& P, double* U, const double* Bd, const Metric& m, double* prim,
+                                         unsigned& flags, int& iters, bool write_cons, double glo = -1.0,
+                                         double ghi = -1.0) {
+  KrpCell k;
+  iters = 0;
+  bool ok = krp_prep(P, U, Bd, m, k, flags);
+  double mu = 0.0;
+  if (ok) {
+    double a, b, Ga, Gb;
+    int st = krp_bracket(k.s, glo, ghi, a, b, Ga, Gb, mu, iters);
+    if (st == 2) ok = false;
+    else if (st == 0) {
+      int it = 0;
+      ok = illinois(k.s, a, Ga, b, Gb, P.tol, P.maxit, mu, it);
+      iters += it;
+    }
+  }
+  krp_finish(P, k, mu, ok, flags, prim);
   if (write_cons && (flags & (FLOOR_BITS | F_FAIL))) prim2cons(P, prim, Bd, m, U);
 }
 

@@ -19,6 +19,22 @@ void launch_emf(const Work& w, cudaStream_t s, int grid);
 void launch_update_cells(const Work& w, const Par& P, double g0, double g1, double bdt, int first, cudaStream_t s,
                          int grid);
 void launch_update_faces(const Work& w, double g0, double g1, double bdt, int first, cudaStream_t s, int grid);
+size_t krp_bytes(long long n);
+KrpBuf krp_view(void* base, long long n);
+void launch_krp_prep_block(const Work& w, const Par& P, const KrpBuf& kb, cudaStream_t s, int grid);
+void launch_krp_solve(const Par& P, const KrpBuf& kb, unsigned long long* stats, cudaStream_t s, int grid);
+void launch_krp_finish_block(const Work& w, const Par& P, const KrpBuf& kb, unsigned long long* stats,
+                             cudaStream_t s, int grid);
+void launch_krp_prep_fofc(const Work& w, const Par& P, double g0, double g1, double bdt, const KrpBuf& kb,
+                          cudaStream_t s, int grid);
+void launch_krp_finish_fofc(const Work& w, const Par& P, const KrpBuf& kb, unsigned long long* stats,
+                            cudaStream_t s, int grid);
+void launch_krp_prep_cells(const Par& P, const KrpBuf& kb, const double* cons, const double* Bd, const double* g,
+                           const float* guess, cudaStream_t s, int grid);
+void launch_krp_finish_cells(const Par& P, const KrpBuf& kb, double* cons, const double* Bd, const double* g,
+                             double* prim, unsigned char* flags, int* iters, unsigned long long* stats, cudaStream_t s,
+                             int grid);
+int occupancy_krp(int* per_sm);
 int occupancy_c2p(int* per_sm);
 int occupancy_face(int* per_sm);
 int occupancy_update(int* per_sm);

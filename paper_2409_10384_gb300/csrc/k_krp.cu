@@ -1,0 +1,440 @@
+// con2prim as three kernels (Sec. 3.4): a uniform prep (floors, KRP variables,
+// bracket), a root solve in which every lane refills itself from a global
+// work queue as soon as its Illinois iteration converges, and a uniform
+// finish (recovery, floors, write-back).  One thread per cell would leave most
+// lanes of a warp idle while the slowest cell iterates, and idle lanes still
+// occupy the narrow FP64 pipe; with refill the lanes stay busy until the
+// queue runs dry.
+#include "dev.cuh"
+#include "internal.h"
+
+namespace grmhd {
+
+// Slots of the per-cell scratch (SoA, [KW_N][n]).
+enum {
+  KW_QH = 0, KW_R2, KW_B2, KW_RB2, KW_RP2, KW_D, KW_RB, KW_RU0, KW_RU1, KW_RU2, KW_BU0, KW_BU1, KW_BU2,
+  KW_A, KW_B, KW_GA, KW_GB, KW_MU, KW_SDET, KW_ISDET, KW_USD, KW_UST, KW_N
+};
+// status: 0 solve needed, 1 root known, 2 no bracket / bad input, 3 iteration cap
+
+__device__ __forceinline__ void kw_store(const KrpBuf& kb, long long i, const KrpCell& k) {
+  const long long n = kb.n;
+  double* w = kb.w;
+  w[KW_QH * n + i] = k.s.qh; w[KW_R2 * n + i] = k.s.r2; w[KW_B2 * n + i] = k.s.b2;
+  w[KW_RB2 * n + i] = k.s.rb2; w[KW_RP2 * n + i] = k.s.rperp2;
+  w[KW_D * n + i] = k.D; w[KW_RB * n + i] = k.rb;
+  w[KW_RU0 * n + i] = k.ru[0]; w[KW_RU1 * n + i] = k.ru[1]; w[KW_RU2 * n + i] = k.ru[2];
+  w[KW_BU0 * n + i] = k.bu[0]; w[KW_BU1 * n + i] = k.bu[1]; w[KW_BU2 * n + i] = k.bu[2];
+}
+__device__ __forceinline__ void kw_load(const KrpBuf& kb, const Par& P, long long i, KrpCell& k) {
+  const long long n = kb.n;
+  const double* w = kb.w;
+  k.s.qh = w[KW_QH * n + i]; k.s.r2 = w[KW_R2 * n + i]; k.s.b2 = w[KW_B2 * n + i];
+  k.s.rb2 = w[KW_RB2 * n + i]; k.s.rperp2 = w[KW_RP2 * n + i];
+  k.s.gam = P.gam; k.s.eps_min = P.eps_atm; k.s.vmax2 = P.vmax2;
+  k.D = w[KW_D * n + i]; k.rb = w[KW_RB * n + i];
+  k.ru[0] = w[KW_RU0 * n + i]; k.ru[1] = w[KW_RU1 * n + i]; k.ru[2] = w[KW_RU2 * n + i];
+  k.bu[0] = w[KW_BU0 * n + i]; k.bu[1] = w[KW_BU1 * n + i]; k.bu[2] = w[KW_BU2 * n + i];
+}
+
+// prep of one cell: KRP variables, bracket (plain or learned), status
+__device__ __forceinline__ void prep_cell(const Par& P, const KrpBuf& kb, long long i, const double* U,
+                                          const double* Bd, const Metric& m, double glo, double ghi) {
+  KrpCell k;
+  unsigned fl;
+  const long long n = kb.n;
+  unsigned char st = 2;
+  int its = 0;
+  if (krp_prep(P, U, Bd, m, k, fl)) {
+    double a, b, Ga, Gb, mu = 0.0;
+    int r = krp_bracket(k.s, glo, ghi, a, b, Ga, Gb, mu, its);
+    st = (unsigned char)(r == 0 ? 0 : (r == 1 ? 1 : 2));
+    kb.w[KW_A * n + i] = a; kb.w[KW_B * n + i] = b;
+    kb.w[KW_GA * n + i] = Ga; kb.w[KW_GB * n + i] = Gb;
+    kb.w[KW_MU * n + i] = mu;
+  }
+  kw_store(kb, i, k);
+  kb.w[KW_SDET * n + i] = m.sdet;
+  kb.w[KW_ISDET * n + i] = m.isdet;
+  kb.st[i] = st;
+  kb.fl[i] = (unsigned char)fl;
+  kb.it[i] = its;
+}
+
+__device__ __forceinline__ void load_metric6(const double* g6, long long stride, long long c, Metric& m) {
+#pragma unroll
+  for (int v = 0; v < 6; v++) m.g[v] = g6[v * stride + c];
+  metric_setup(m);
+}
+
+// ------------------------------------------------------------------ root solve
+// Illinois regula falsi (as in `illinois`) with lane refill.  Reads the
+// bracket of every status-0 cell, writes mu, iterations and status 1 or 3.
+__global__ void __launch_bounds__(256) k_krp_solve(Par P, KrpBuf kb, unsigned long long* stats) {
+  const unsigned lane = threadIdx.x & 31;
+  const long long n = kb.n;
+  long long idx = -1;
+  bool done = false;
+  KS s;
+  s.gam = P.gam; s.eps_min = P.eps_atm; s.vmax2 = P.vmax2;
+  s.qh = s.r2 = s.b2 = s.rb2 = s.rperp2 = 0.0;
+  double a = 0.0, b = 1.0, Ga = -1.0, Gb = 1.0, Fa = -1.0, Fb = 1.0;
+  int side = 0, it = 0;
+  unsigned s_it = 0, s_cap = 0;
+  while (true) {
+    const bool need = idx < 0 && !done;
+    const unsigned m = __ballot_sync(0xffffffffu, need);
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      unsigned long long base = 0;
+      if ((int)lane == leader) base = atomicAdd(kb.ctr, (unsigned long long)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (need) {
+        const long long my = (long long)(base + __popc(m & ((1u << lane) - 1u)));
+        if (my >= n) {
+          done = true;
+        } else if (kb.st[my] == 0) {
+          idx = my;
+          const double* w = kb.w;
+          s.qh = w[KW_QH * n + my]; s.r2 = w[KW_R2 * n + my]; s.b2 = w[KW_B2 * n + my];
+          s.rb2 = w[KW_RB2 * n + my]; s.rperp2 = w[KW_RP2 * n + my];
+          a = w[KW_A * n + my]; b = w[KW_B * n + my];
+          Ga = w[KW_GA * n + my]; Gb = w[KW_GB * n + my];
+          Fa = Ga; Fb = Gb;
+          side = 0;
+          it = kb.it[my];
+        }
+      }
+    }
+    const bool act = idx >= 0;
+    if (__ballot_sync(0xffffffffu, act || !done) == 0) break;
+    if (!act) continue;
+    bool fin = !(b - a > P.tol * b), cap = false, exact = false;
+    double root = 0.0;
+    if (!fin) {
+      if (it >= P.maxit) {
+        cap = fin = true;
+      } else {
+        it++;
+        double c = (a * Fb - b * Fa) / (Fb - Fa);
+        if (!(c > a && c < b)) c = 0.5 * (a + b);
+        KEval e;
+        kev(s, c, e);
+        if (e.G < 0.0) {
+          a = c; Ga = e.G; Fa = e.G;
+          if (side == -1) Fb *= 0.5;
+          side = -1;
+        } else if (e.G > 0.0) {
+          b = c; Gb = e.G; Fb = e.G;
+          if (side == 1) Fa *= 0.5;
+          side = 1;
+        } else {
+          exact = fin = true;
+          root = c;
+        }
+        if (!fin) fin = !(b - a > P.tol * b);
+      }
+    }
+    if (fin) {
+      if (!exact && !cap) root = a - Ga * (b - a) / (Gb - Ga);
+      kb.w[KW_MU * n + idx] = root;
+      kb.it[idx] = it;
+      kb.st[idx] = cap ? 3 : 1;
+      s_it += it;
+      s_cap += cap ? 1u : 0u;
+      idx = -1;
+    }
+  }
+  warp_flush(&stats[1], s_it);
+  (void)s_cap;
+}
+
+// -------------------------------------------------------- block stage con2prim
+__global__ void __launch_bounds__(128) k_krp_prep_block(Work w, Par P, KrpBuf kb) {
+  const long long* pre = w.pre + (long long)W_C2P * (w.nblocks + 1);
+  const long long tot = pre[w.nblocks];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *kb.ctr = 0ull;
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < tot; it += (long long)gridDim.x * blockDim.x) {
+    const int bi = find_block(w, W_C2P, it);
+    const DevBlock& b = w.blk[bi];
+    long long loc = it - pre[bi];
+    const int R0 = b.n[0] + 6, R1 = b.n[1] + 6;
+    int ii = loc % R0; long long r = loc / R0; int jj = r % R1; int kk = r / R1;
+    const int i = ii + b.ng - 3, j = jj + b.ng - 3, k = kk + b.ng - 3;
+    const long long c = cidx(b, k, j, i), nc = b.ncell;
+    double Bd[3];
+    Bd[0] = 0.5 * (b.bf[0][fidx(b, 0, k, j, i)] + b.bf[0][fidx(b, 0, k, j, i + 1)]);
+    Bd[1] = 0.5 * (b.bf[1][fidx(b, 1, k, j, i)] + b.bf[1][fidx(b, 1, k, j + 1, i)]);
+    Bd[2] = 0.5 * (b.bf[2][fidx(b, 2, k, j, i)] + b.bf[2][fidx(b, 2, k + 1, j, i)]);
+#pragma unroll
+    for (int v = 0; v < 3; v++) b.bcc[v * nc + c] = Bd[v];
+    Metric m;
+    load_metric6(b.adm + 4 * nc, nc, c, m);
+    double U[5];
+#pragma unroll
+    for (int v = 0; v < 5; v++) U[v] = b.cons[v * nc + c];
+    prep_cell(P, kb, it, U, Bd, m, -1.0, -1.0);
+  }
+}
+
+__global__ void __launch_bounds__(128) k_krp_finish_block(Work w, Par P, KrpBuf kb, unsigned long long* stats) {
+  const long long* pre = w.pre + (long long)W_C2P * (w.nblocks + 1);
+  const long long tot = pre[w.nblocks];
+  const long long n = kb.n;
+  unsigned s_cells = 0, s_fail = 0, s_floor = 0;
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < tot; it += (long long)gridDim.x * blockDim.x) {
+    const int bi = find_block(w, W_C2P, it);
+    const DevBlock& b = w.blk[bi];
+    long long loc = it - pre[bi];
+    const int R0 = b.n[0] + 6, R1 = b.n[1] + 6;
+    int ii = loc % R0; long long r = loc / R0; int jj = r % R1; int kk = r / R1;
+    const int i = ii + b.ng - 3, j = jj + b.ng - 3, k = kk + b.ng - 3;
+    const long long c = cidx(b, k, j, i), nc = b.ncell;
+    KrpCell kc;
+    kw_load(kb, P, it, kc);
+    unsigned fl = kb.fl[it];
+    const unsigned char st = kb.st[it];
+    double pr[5];
+    krp_finish(P, kc, kb.w[KW_MU * n + it], st == 1, fl, pr);
+#pragma unroll
+    for (int v = 0; v < 5; v++) b.prim[v * nc + c] = pr[v];
+    const double Bd[3] = {b.bcc[c], b.bcc[nc + c], b.bcc[2 * nc + c]};
+    Metric m;
+#pragma unroll
+    for (int v = 0; v < 6; v++) m.g[v] = b.adm[(4 + v) * nc + c];
+    m.sdet = kb.w[KW_SDET * n + it];
+    m.isdet = kb.w[KW_ISDET * n + it];
+    if (fl & (FLOOR_BITS | F_FAIL)) {
+      double U[5];
+      prim2cons(P, pr, Bd, m, U);
+#pragma unroll
+      for (int v = 0; v < 5; v++) b.cons[v * nc + c] = U[v];
+    }
+    b.flags[c] = (unsigned char)fl;
+    if (ii >= 2 && ii <= b.n[0] + 3 && jj >= 2 && jj <= b.n[1] + 3 && kk >= 2 && kk <= b.n[2] + 3) {
+      const double alpha = b.adm[c];
+      const double be0 = b.adm[nc + c], be1 = b.adm[2 * nc + c], be2 = b.adm[3 * nc + c];
+      double wu[3] = {pr[1], pr[2], pr[3]}, wl[3];
+      lower3(m.g, wu, wl);
+      double iW = rsqrt(1.0 + dot3(wu, wl));
+      double a0 = fma(alpha * iW, wu[0], -be0), a1 = fma(alpha * iW, wu[1], -be1), a2 = fma(alpha * iW, wu[2], -be2);
+      b.ecc[c] = -(a1 * Bd[2] - a2 * Bd[1]);
+      b.ecc[nc + c] = -(a2 * Bd[0] - a0 * Bd[2]);
+      b.ecc[2 * nc + c] = -(a0 * Bd[1] - a1 * Bd[0]);
+    }
+    s_cells++;
+    s_fail += (fl & F_FAIL) ? 1u : 0u;
+    s_floor += (fl & FLOOR_BITS) ? 1u : 0u;
+  }
+  warp_flush(&stats[0], s_cells);
+  warp_flush(&stats[2], s_fail);
+  warp_flush(&stats[3], s_floor);
+}
+
+// ------------------------------------------------------------------ FOFC U*
+__device__ __forceinline__ void fofc_cell(const Work& w, long long it, int& bi, int& k, int& j, int& i) {
+  const long long* pre = w.pre + (long long)W_CELL * (w.nblocks + 1);
+  bi = find_block(w, W_CELL, it);
+  const DevBlock& b = w.blk[bi];
+  long long loc = it - pre[bi];
+  i = loc % b.n[0]; long long r = loc / b.n[0]; j = r % b.n[1]; k = r / b.n[1];
+  i += b.ng; j += b.ng; k += b.ng;
+}
+
+__global__ void __launch_bounds__(128) k_krp_prep_fofc(Work w, Par P, double g0, double g1, double bdt, KrpBuf kb) {
+  const long long tot = w.pre[(long long)W_CELL * (w.nblocks + 1) + w.nblocks];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *kb.ctr = 0ull;
+  const long long n = kb.n;
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < tot; it += (long long)gridDim.x * blockDim.x) {
+    int bi, k, j, i;
+    fofc_cell(w, it, bi, k, j, i);
+    const DevBlock& b = w.blk[bi];
+    const long long nc = b.ncell, c = cidx(b, k, j, i);
+    const long long fx0 = fidx(b, 0, k, j, i), fy0 = fidx(b, 1, k, j, i), fz0 = fidx(b, 2, k, j, i);
+    const long long fx1 = fx0 + 1, fy1 = fidx(b, 1, k, j + 1, i), fz1 = fidx(b, 2, k + 1, j, i);
+    const long long nx = nface(b, 0), ny = nface(b, 1), nz = nface(b, 2);
+    double U[5];
+#pragma unroll
+    for (int v = 0; v < 5; v++) {
+      double div = (b.flux[0][v * nx + fx1] - b.flux[0][v * nx + fx0]) * b.idx[0] +
+                   (b.flux[1][v * ny + fy1] - b.flux[1][v * ny + fy0]) * b.idx[1] +
+                   (b.flux[2][v * nz + fz1] - b.flux[2][v * nz + fz0]) * b.idx[2];
+      double u = g1 * b.cons[v * nc + c];
+      if (g0 != 0.0) u = fma(g0, b.cons0[v * nc + c], u);
+      U[v] = fma(-bdt, div, u);
+    }
+    Metric m;
+    load_metric6(b.adm + 4 * nc, nc, c, m);
+    const double Bd[3] = {b.bcc[c], b.bcc[nc + c], b.bcc[2 * nc + c]};
+    prep_cell(P, kb, it, U, Bd, m, -1.0, -1.0);
+    kb.w[KW_USD * n + it] = U[0];
+    kb.w[KW_UST * n + it] = U[4];
+  }
+}
+
+__global__ void __launch_bounds__(128) k_krp_finish_fofc(Work w, Par P, KrpBuf kb, unsigned long long* stats) {
+  const long long tot = w.pre[(long long)W_CELL * (w.nblocks + 1) + w.nblocks];
+  const long long n = kb.n;
+  unsigned s_flag = 0, s_dmp = 0;
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < tot; it += (long long)gridDim.x * blockDim.x) {
+    int bi, k, j, i;
+    fofc_cell(w, it, bi, k, j, i);
+    const DevBlock& b = w.blk[bi];
+    const long long nc = b.ncell, c = cidx(b, k, j, i);
+    KrpCell kc;
+    kw_load(kb, P, it, kc);
+    unsigned fl = kb.fl[it];
+    double pr[5];
+    krp_finish(P, kc, kb.w[KW_MU * n + it], kb.st[it] == 1, fl, pr);
+    bool flag = (fl & (FLOOR_BITS | F_FAIL)) != 0;
+    if (!flag && P.dmp_M > 0.0) {
+      const double Us[2] = {kb.w[KW_USD * n + it], kb.w[KW_UST * n + it]};
+#pragma unroll
+      for (int t = 0; t < 2; t++) {
+        const double* a = b.cons + (t == 0 ? 0 : 4) * nc;
+        double mn = a[c], mx = mn;
+        for (int dk = -1; dk <= 1; dk++)
+          for (int dj = -1; dj <= 1; dj++)
+#pragma unroll
+            for (int di = -1; di <= 1; di++) {
+              double u = a[cidx(b, k + dk, j + dj, i + di)];
+              mn = fmin(mn, u);
+              mx = fmax(mx, u);
+            }
+        const double M = P.dmp_M;
+        double lo = mn > 0.0 ? mn / M : mn * M;
+        double hi = mx > 0.0 ? mx * M : mx / M;
+        if (Us[t] < lo || Us[t] > hi) flag = true;
+      }
+      s_dmp += flag ? 1u : 0u;
+    }
+    b.fflag[c] = flag ? 1 : 0;
+    unsigned char f0 = b.flags[c];
+    b.flags[c] = flag ? (unsigned char)(f0 | F_FOFC) : (unsigned char)(f0 & ~F_FOFC);
+    s_flag += flag ? 1u : 0u;
+  }
+  warp_flush(&stats[4], s_flag);
+  warp_flush(&stats[5], s_dmp);
+}
+
+// ------------------------------------------------------- independent cells
+__global__ void __launch_bounds__(128) k_krp_prep_cells(Par P, KrpBuf kb, const double* __restrict__ cons,
+                                                        const double* __restrict__ Bd, const double* __restrict__ g,
+                                                        const float* __restrict__ guess) {
+  const long long n = kb.n;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *kb.ctr = 0ull;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    Metric m;
+    load_metric6(g, n, c, m);
+    double U[5], B[3];
+#pragma unroll
+    for (int v = 0; v < 5; v++) U[v] = cons[v * n + c];
+#pragma unroll
+    for (int v = 0; v < 3; v++) B[v] = Bd[v * n + c];
+    double lo = -1.0, hi = -1.0;
+    if (guess) {
+      lo = guess[2 * c];
+      hi = guess[2 * c + 1];
+    }
+    prep_cell(P, kb, c, U, B, m, lo, hi);
+  }
+}
+
+__global__ void __launch_bounds__(128) k_krp_finish_cells(Par P, KrpBuf kb, double* __restrict__ cons,
+                                                          const double* __restrict__ Bd, const double* __restrict__ g,
+                                                          double* __restrict__ prim, unsigned char* __restrict__ flags,
+                                                          int* __restrict__ iters_out, unsigned long long* stats) {
+  const long long n = kb.n;
+  unsigned s_cells = 0, s_fail = 0, s_floor = 0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    KrpCell kc;
+    kw_load(kb, P, c, kc);
+    unsigned fl = kb.fl[c];
+    double pr[5];
+    krp_finish(P, kc, kb.w[KW_MU * n + c], kb.st[c] == 1, fl, pr);
+#pragma unroll
+    for (int v = 0; v < 5; v++) prim[v * n + c] = pr[v];
+    if (fl & (FLOOR_BITS | F_FAIL)) {
+      Metric m;
+#pragma unroll
+      for (int v = 0; v < 6; v++) m.g[v] = g[v * n + c];
+      m.sdet = kb.w[KW_SDET * n + c];
+      m.isdet = kb.w[KW_ISDET * n + c];
+      const double B[3] = {Bd[c], Bd[n + c], Bd[2 * n + c]};
+      double U[5];
+      prim2cons(P, pr, B, m, U);
+#pragma unroll
+      for (int v = 0; v < 5; v++) cons[v * n + c] = U[v];
+    }
+    flags[c] = (unsigned char)fl;
+    if (iters_out) iters_out[c] = kb.it[c];
+    s_cells++;
+    s_fail += (fl & F_FAIL) ? 1u : 0u;
+    s_floor += (fl & FLOOR_BITS) ? 1u : 0u;
+  }
+  warp_flush(&stats[0], s_cells);
+  warp_flush(&stats[2], s_fail);
+  warp_flush(&stats[3], s_floor);
+}
+
+// ------------------------------------------------------------------ launchers
+size_t krp_bytes(long long n) {
+  return (size_t)n * (sizeof(double) * KW_N + sizeof(int) + 2) + 1024;
+}
+KrpBuf krp_view(void* base, long long n) {
+  KrpBuf kb;
+  char* p = (char*)base;
+  kb.n = n;
+  kb.w = (double*)p;
+  p += sizeof(double) * KW_N * n;
+  kb.it = (int*)p;
+  p += sizeof(int) * n;
+  kb.st = (unsigned char*)p;
+  p += n;
+  kb.fl = (unsigned char*)p;
+  p += n;
+  p = (char*)(((size_t)p + 255) & ~(size_t)255);
+  kb.ctr = (unsigned long long*)p;
+  return kb;
+}
+
+void launch_krp_prep_block(const Work& w, const Par& P, const KrpBuf& kb, cudaStream_t s, int grid) {
+  k_krp_prep_block<<<grid, 128, 0, s>>>(w, P, kb);
+}
+void launch_krp_solve(const Par& P, const KrpBuf& kb, unsigned long long* stats, cudaStream_t s, int grid) {
+  k_krp_solve<<<grid, 256, 0, s>>>(P, kb, stats);
+}
+void launch_krp_finish_block(const Work& w, const Par& P, const KrpBuf& kb, unsigned long long* stats,
+                             cudaStream_t s, int grid) {
+  k_krp_finish_block<<<grid, 128, 0, s>>>(w, P, kb, stats);
+}
+void launch_krp_prep_fofc(const Work& w, const Par& P, double g0, double g1, double bdt, const KrpBuf& kb,
+                          cudaStream_t s, int grid) {
+  k_krp_prep_fofc<<<grid, 128, 0, s>>>(w, P, g0, g1, bdt, kb);
+}
+void launch_krp_finish_fofc(const Work& w, const Par& P, const KrpBuf& kb, unsigned long long* stats,
+                            cudaStream_t s, int grid) {
+  k_krp_finish_fofc<<<grid, 128, 0, s>>>(w, P, kb, stats);
+}
+void launch_krp_prep_cells(const Par& P, const KrpBuf& kb, const double* cons, const double* Bd, const double* g,
+                           const float* guess, cudaStream_t s, int grid) {
+  k_krp_prep_cells<<<grid, 128, 0, s>>>(P, kb, cons, Bd, g, guess);
+}
+void launch_krp_finish_cells(const Par& P, const KrpBuf& kb, double* cons, const double* Bd, const double* g,
+                             double* prim, unsigned char* flags, int* iters, unsigned long long* stats, cudaStream_t s,
+                             int grid) {
+  k_krp_finish_cells<<<grid, 128, 0, s>>>(P, kb, cons, Bd, g, prim, flags, iters, stats);
+}
+int occupancy_krp(int* per_sm) {
+  cudaError_t e = cudaSuccess;
+  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_krp_prep_block, 128, 0));
+  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_krp_solve, 256, 0));
+  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[2], k_krp_finish_block, 128, 0));
+  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[3], k_krp_prep_fofc, 128, 0));
+  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[4], k_krp_finish_fofc, 128, 0));
+  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[5], k_krp_prep_cells, 128, 0));
+  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[6], k_krp_finish_cells, 128, 0));
+  return e == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace grmhd

@@ -76,7 +76,7 @@ _SIGS = {
     "mhd_kernel_name": (C.c_char_p, [_I]),
     "mhd_stage_noalloc": (_I, [C.POINTER(mhd_params), C.POINTER(mhd_block), _D, _I, _VP]),
 }
-MHD_NKERNEL = 9
+MHD_NKERNEL = 10
 
 
 def header_symbols() -> list:
