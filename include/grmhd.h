@@ -164,7 +164,8 @@ long long mhd_kernel_launches(const mhd_ctx* ctx);
 #define MHD_K_UPDATE 7     /* RK update of U with the Eq. 9 sources */
 #define MHD_K_FACEB 8      /* RK update of the face B~ */
 #define MHD_K_SOLVE 9      /* con2prim root solves (stage input and U*) */
-#define MHD_NKERNEL 10
+#define MHD_K_MLP 10       /* learned-guess network inference */
+#define MHD_NKERNEL 11
 
 /* enable != 0: bracket every kernel launched outside stream capture by CUDA
  * events on its own stream.  mhd_profile_read waits for them and returns, per
@@ -173,6 +174,44 @@ long long mhd_kernel_launches(const mhd_ctx* ctx);
 int mhd_profile(mhd_ctx* ctx, int enable);
 int mhd_profile_read(mhd_ctx* ctx, double* ms, long long* count);
 const char* mhd_kernel_name(int kind);
+
+/* Learned con2prim guess (not in the paper; the spec addition of this
+ * library).  A 5 -> 64 -> 64 -> 1 tanh network with BF16 operands and FP32
+ * accumulation on the tensor cores predicts log(mu) of the Kastaun et al. root
+ * from five features of the cell's KRP variables; with mhd_params.c2p_guess = 1
+ * mhd_c2p_cells evaluates the FP64 function at the guess, steps by a factor
+ * exp(+-delta) towards the root to close a bracket (falling back to [0, .] or
+ * [., 1]) and solves as before: same root, fewer FP64 iterations.
+ * Features: float [n][MHD_MLP_FSTRIDE] (5 used); targets: float log(mu) [n].
+ * State (get/set): MHD_MLP_NPARAM fp32 parameters (W1 [64][5], b1, W2
+ * [64][64], b2, w3, b3), then feature mean [5], feature 1/std [5], target
+ * mean, target std, delta.  Device pointers unless stated. */
+#define MHD_MLP_NPARAM 4609
+#define MHD_MLP_NSTATE (4609 + 13)
+#define MHD_MLP_FSTRIDE 8
+/* Allocate the network state and draw Glorot-uniform weights (seed). */
+int mhd_mlp_init(mhd_ctx* ctx, unsigned long long seed);
+/* Plain con2prim of n cells -> features and log(mu) of the root (training data). */
+int mhd_mlp_dataset(mhd_ctx* ctx, long n, const double* cons, const double* Bd, const double* g, float* feat,
+                    float* logmu, void* stream);
+/* Normalise, then Adam (cosine-decayed lr) over `epochs` passes of shuffled
+ * mini-batches, forward and backward on the tensor cores.  *loss_out: mean
+ * squared error (normalised units) of the last epoch.  Synchronises. */
+int mhd_mlp_train(mhd_ctx* ctx, const float* feat, const float* logmu, long n, int epochs, int batch, float lr,
+                  unsigned long long seed, float* loss_out, void* stream);
+/* delta = the `quantile` of |predicted - true log(mu)| on the given samples;
+ * enables the learned guess.  Synchronises. */
+int mhd_mlp_calibrate(mhd_ctx* ctx, const float* feat, const float* logmu, long n, double quantile,
+                      double* delta_out, void* stream);
+/* Predicted log(mu) of n samples. */
+int mhd_mlp_infer(mhd_ctx* ctx, const float* feat, long n, float* logmu_out, void* stream);
+/* Gradient (grad_out[MHD_MLP_NPARAM], device or host) and loss of the mean
+ * squared error over n samples in normalised units.  Synchronises. */
+int mhd_mlp_grad(mhd_ctx* ctx, const float* feat, const float* logmu, long n, float* grad_out, float* loss_out,
+                 void* stream);
+/* Copy the state out / in (host arrays of MHD_MLP_NSTATE floats). */
+int mhd_mlp_get(mhd_ctx* ctx, float* state);
+int mhd_mlp_set(mhd_ctx* ctx, const float* state);
 
 /* Allocation-free stage (the paper has no counterpart: this serves callers).
  * Some callers cannot let a library allocate device memory: a host code that

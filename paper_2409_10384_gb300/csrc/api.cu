@@ -1,6 +1,7 @@
 // C-ABI of libgrmhd: context, block lists, scratch, launch sequencing and the
 // CUDA-graph step.  Declarations and argument conventions: include/grmhd.h.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -20,6 +21,15 @@ struct mhd_ctx {
   long long krp_n = 0;
   char* cells_buf = nullptr;
   size_t cells_bytes = 0;
+  // learned con2prim guess (network state)
+  float* mlp = nullptr;             // [4 * MLP_NPARAM]: params, Adam m, Adam v, gradient
+  __nv_bfloat16* mlp_wb = nullptr;  // [MLP_NBF] bf16 operand copies
+  float* mlp_loss = nullptr;        // device scalar
+  double* mlp_acc = nullptr;        // [12] normalisation sums
+  MlpNorm nm;
+  double mlp_delta = 0.0;           // bracket half-width in log(mu)
+  int mlp_t = 0;                    // Adam step
+  bool mlp_ready = false;
   // current block list
   std::vector<mhd_block> key;
   std::vector<DevBlock> hblk;
@@ -60,7 +70,7 @@ int set_par(mhd_ctx* c, const mhd_params* p) {
   if (!p) return MHD_EINVAL;
   if (!(p->gamma > 1.0) || !(p->rho_atm > 0.0) || !(p->T_atm > 0.0) || !(p->f_thr >= 0.0) || !(p->c2p_tol > 0.0) ||
       !(p->W_max > 1.0) || p->recon < 0 || p->recon > 2 || p->rsolver < 0 || p->rsolver > 1 ||
-      (p->rk_order != 2 && p->rk_order != 3) || p->c2p_maxit < 1 || p->c2p_guess < 0 || p->c2p_guess > 1 ||
+      (p->rk_order != 2 && p->rk_order != 3) || p->c2p_maxit < 1 || p->c2p_guess < 0 || p->c2p_guess > 2 ||
       (p->dmp_M > 0.0 && p->dmp_M < 1.0))
     return MHD_EINVAL;
   c->hp = *p;
@@ -338,7 +348,7 @@ int mhd_init(const mhd_params* p, mhd_ctx** out) {
     return MHD_ECUDA;
   }
   if (occupancy_c2p(c->occ_c2p) || occupancy_face(c->occ_face) || occupancy_update(c->occ_upd) ||
-      occupancy_krp(c->occ_krp)) {
+      occupancy_krp(c->occ_krp) || mlp_setup_attrs()) {
     delete c;
     return MHD_ECUDA;
   }
@@ -371,6 +381,10 @@ void mhd_finalize(mhd_ctx* c) {
   if (c->dpre) cudaFree(c->dpre);
   if (c->dstats) cudaFree(c->dstats);
   if (c->cells_buf) cudaFree(c->cells_buf);
+  if (c->mlp) cudaFree(c->mlp);
+  if (c->mlp_wb) cudaFree(c->mlp_wb);
+  if (c->mlp_loss) cudaFree(c->mlp_loss);
+  if (c->mlp_acc) cudaFree(c->mlp_acc);
   for (auto& r : c->recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -422,32 +436,268 @@ int mhd_prim2cons(mhd_ctx* c, long n, const double* prim, const double* Bd, cons
   return cuda_ok(cudaGetLastError());
 }
 
-int mhd_c2p_cells(mhd_ctx* c, long n, double* cons, const double* Bd, const double* g, double* prim,
-                  unsigned char* flags, int* iters, void* stream) {
-  if (!c || n < 0 || (n > 0 && (!cons || !Bd || !g || !prim || !flags))) return MHD_EINVAL;
-  if (n == 0) return MHD_OK;
-  const size_t need = krp_bytes(n);
+}  // extern "C"
+
+namespace {
+
+// Grow-only buffer for independent-cell con2prim: KRP scratch, features, log(mu) guesses.
+int cells_scratch(mhd_ctx* c, long n, cudaStream_t s, KrpBuf* kb, float** feat, float** logmu) {
+  const size_t kbytes = al256(krp_bytes(n)), fbytes = al256(sizeof(float) * MLP_FSTRIDE * (size_t)n),
+               lbytes = al256(sizeof(float) * (size_t)n);
+  const size_t need = kbytes + fbytes + lbytes;
   if (need > c->cells_bytes) {
-    cudaStreamSynchronize((cudaStream_t)stream);
+    cudaStreamSynchronize(s);
     if (c->cells_buf) cudaFree(c->cells_buf);
     c->cells_buf = nullptr;
     c->cells_bytes = 0;
     if (cudaMalloc(&c->cells_buf, need) != cudaSuccess) return MHD_ENOMEM;
     c->cells_bytes = need;
   }
+  *kb = krp_view(c->cells_buf, n);
+  *feat = (float*)(c->cells_buf + kbytes);
+  *logmu = (float*)(c->cells_buf + kbytes + fbytes);
+  return MHD_OK;
+}
+
+int cells_grid(const mhd_ctx* c, long n, int occ) {
+  long long nb = (n + 127) / 128, cap = (long long)c->nsm * std::max(occ, 1);
+  return (int)std::max(1LL, std::min(nb, cap));
+}
+
+}  // namespace
+
+extern "C" {
+
+int mhd_c2p_cells(mhd_ctx* c, long n, double* cons, const double* Bd, const double* g, double* prim,
+                  unsigned char* flags, int* iters, void* stream) {
+  if (!c || n < 0 || (n > 0 && (!cons || !Bd || !g || !prim || !flags))) return MHD_EINVAL;
+  if (n == 0) return MHD_OK;
+  const int mode = c->P.guess;  // 0 plain, 1 learned + FP32 search, 2 FP32 search from the plain bracket
+  if (mode == 1 && !c->mlp_ready) return MHD_ENOMLP;
   cudaStream_t s = (cudaStream_t)stream;
-  KrpBuf kb = krp_view(c->cells_buf, n);
-  auto grid = [&](int occ) {
-    long long nb = (n + 127) / 128, cap = (long long)c->nsm * std::max(occ, 1);
-    return (int)std::max(1LL, std::min(nb, cap));
-  };
-  const float* guess = nullptr;
-  timed(c, MHD_K_C2P, s, [&] { launch_krp_prep_cells(c->P, kb, cons, Bd, g, guess, s, grid(c->occ_krp[5])); });
+  KrpBuf kb;
+  float *feat, *logmu;
+  int r = cells_scratch(c, n, s, &kb, &feat, &logmu);
+  if (r) return r;
+  timed(c, MHD_K_C2P, s, [&] {
+    launch_krp_prep_cells(c->P, kb, cons, Bd, g, mode != 0 ? 1 : 0, mode == 1 ? feat : nullptr, s,
+                          cells_grid(c, n, c->occ_krp[5]));
+  });
+  if (mode == 1)
+    timed(c, MHD_K_MLP, s, [&] { launch_mlp_infer(feat, n, c->nm, c->mlp_wb, c->mlp, logmu, s, c->nsm); });
+  if (mode != 0)
+    timed(c, MHD_K_C2P, s, [&] {
+      launch_krp_seed(c->P, kb, logmu, mode == 1 ? 1 : 0, (float)c->mlp_delta, s, cells_grid(c, n, c->occ_krp[5]));
+    });
   timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, c->dstats, s, c->g_solve_cells()); });
   timed(c, MHD_K_C2P, s, [&] {
-    launch_krp_finish_cells(c->P, kb, cons, Bd, g, prim, flags, iters, c->dstats, s, grid(c->occ_krp[6]));
+    launch_krp_finish_cells(c->P, kb, cons, Bd, g, prim, flags, iters, c->dstats, s, cells_grid(c, n, c->occ_krp[6]));
   });
   return cuda_ok(cudaGetLastError());
+}
+
+// ------------------------------------------------------------ learned guess
+int mhd_mlp_init(mhd_ctx* c, unsigned long long seed) {
+  if (!c) return MHD_EINVAL;
+  if (!c->mlp) {
+    if (cudaMalloc(&c->mlp, sizeof(float) * 4 * MLP_NPARAM) != cudaSuccess) return MHD_ENOMEM;
+    if (cudaMalloc(&c->mlp_wb, sizeof(__nv_bfloat16) * MLP_NBF) != cudaSuccess) return MHD_ENOMEM;
+    if (cudaMalloc(&c->mlp_loss, sizeof(float)) != cudaSuccess) return MHD_ENOMEM;
+    if (cudaMalloc(&c->mlp_acc, sizeof(double) * 12) != cudaSuccess) return MHD_ENOMEM;
+  }
+  // Glorot-uniform weights from a splitmix64 stream, zero biases
+  std::vector<float> h(4 * MLP_NPARAM, 0.0f);
+  unsigned long long x = seed ? seed : 0x9E3779B97F4A7C15ull;
+  auto uni = [&]() {
+    x += 0x9E3779B97F4A7C15ull;
+    unsigned long long z = x;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+  };
+  const double l1 = std::sqrt(6.0 / (MLP_NIN + MLP_NH)), l2 = std::sqrt(6.0 / (2 * MLP_NH)),
+               l3 = std::sqrt(6.0 / (MLP_NH + 1));
+  for (int i = 0; i < MLP_NH * MLP_NIN; i++) h[MLP_W1 + i] = (float)(l1 * uni());
+  for (int i = 0; i < MLP_NH * MLP_NH; i++) h[MLP_W2 + i] = (float)(l2 * uni());
+  for (int i = 0; i < MLP_NH; i++) h[MLP_W3 + i] = (float)(l3 * uni());
+  if (cudaMemcpy(c->mlp, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess) return MHD_ECUDA;
+  launch_mlp_pack(c->mlp, c->mlp_wb, nullptr);
+  for (int f = 0; f < MLP_NIN; f++) {
+    c->nm.fmean[f] = 0.0f;
+    c->nm.finv[f] = 1.0f;
+  }
+  c->nm.ymean = 0.0f;
+  c->nm.ystd = 1.0f;
+  c->mlp_delta = 0.0;
+  c->mlp_t = 0;
+  c->mlp_ready = false;
+  return cuda_ok(cudaDeviceSynchronize());
+}
+
+int mhd_mlp_dataset(mhd_ctx* c, long n, const double* cons, const double* Bd, const double* g, float* feat,
+                    float* logmu, void* stream) {
+  if (!c || n <= 0 || !cons || !Bd || !g || !feat || !logmu) return MHD_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  KrpBuf kb;
+  float *f2, *l2;
+  int r = cells_scratch(c, n, s, &kb, &f2, &l2);
+  if (r) return r;
+  Par P = c->P;
+  launch_krp_prep_cells(P, kb, cons, Bd, g, 0, feat, s, cells_grid(c, n, c->occ_krp[5]));
+  launch_krp_solve(P, kb, c->dstats, s, c->g_solve_cells());
+  launch_mlp_logmu(kb, logmu, s, c->nsm);
+  c->launches += 3;
+  return cuda_ok(cudaGetLastError());
+}
+
+int mhd_mlp_train(mhd_ctx* c, const float* feat, const float* logmu, long n, int epochs, int batch, float lr,
+                  unsigned long long seed, float* loss_out, void* stream) {
+  if (!c || !c->mlp || !feat || !logmu || n < 64 || epochs < 1 || batch < 32 || !(lr > 0.0f)) return MHD_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  // normalisation of the features and the target
+  if (cudaMemsetAsync(c->mlp_acc, 0, sizeof(double) * 12, s) != cudaSuccess) return MHD_ECUDA;
+  launch_mlp_stats(feat, logmu, n, c->mlp_acc, s, c->nsm);
+  double acc[12];
+  if (cudaMemcpyAsync(acc, c->mlp_acc, sizeof(acc), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ECUDA;
+  for (int f = 0; f < MLP_NIN; f++) {
+    double m = acc[f] / n, v = acc[6 + f] / n - m * m;
+    c->nm.fmean[f] = (float)m;
+    c->nm.finv[f] = (float)(1.0 / std::sqrt(std::max(v, 1e-12)));
+  }
+  {
+    double m = acc[5] / n, v = acc[11] / n - m * m;
+    c->nm.ymean = (float)m;
+    c->nm.ystd = (float)std::sqrt(std::max(v, 1e-12));
+  }
+  float* w = c->mlp;
+  float* mm = c->mlp + MLP_NPARAM;
+  float* vv = c->mlp + 2 * MLP_NPARAM;
+  float* gr = c->mlp + 3 * MLP_NPARAM;
+  if (cudaMemsetAsync(mm, 0, sizeof(float) * 3 * MLP_NPARAM, s) != cudaSuccess) return MHD_ECUDA;
+  c->mlp_t = 0;
+  unsigned long long x = seed ? seed : 12345ull;
+  auto rnd = [&]() {
+    x ^= x << 13; x ^= x >> 7; x ^= x << 17;
+    return x;
+  };
+  auto gcd = [](unsigned long long a, unsigned long long b) {
+    while (b) { unsigned long long t = a % b; a = b; b = t; }
+    return a;
+  };
+  const long steps_per_epoch = (n + batch - 1) / batch;
+  const long total = steps_per_epoch * epochs;
+  for (int ep = 0; ep < epochs; ep++) {
+    unsigned long long pa = 1 + rnd() % (unsigned long long)(n - 1);
+    while (gcd(pa, (unsigned long long)n) != 1) pa = 1 + rnd() % (unsigned long long)(n - 1);
+    unsigned long long pb = rnd() % (unsigned long long)n;
+    if (ep == epochs - 1 && cudaMemsetAsync(c->mlp_loss, 0, sizeof(float), s) != cudaSuccess) return MHD_ECUDA;
+    for (long st = 0; st < steps_per_epoch; st++) {
+      const long off = st * batch;
+      const int b = (int)std::min<long>(batch, n - off);
+      launch_mlp_train_step(feat, logmu, n, (long long)pa, (long long)pb, off, b, c->nm, c->mlp_wb, w, gr,
+                            c->mlp_loss, s);
+      c->mlp_t++;
+      const double frac = (double)c->mlp_t / (double)total;
+      const float lr_t = (float)(lr * 0.5 * (1.0 + std::cos(3.141592653589793 * frac)));
+      launch_mlp_adam(w, mm, vv, gr, lr_t, c->mlp_t, c->mlp_wb, s);
+      c->launches += 3;
+    }
+  }
+  float L = 0.0f;
+  if (cudaMemcpyAsync(&L, c->mlp_loss, sizeof(float), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ECUDA;
+  if (loss_out) *loss_out = L / (float)n;
+  c->mlp_delta = 0.0;
+  c->mlp_ready = false;
+  return cuda_ok(cudaGetLastError());
+}
+
+int mhd_mlp_infer(mhd_ctx* c, const float* feat, long n, float* logmu_out, void* stream) {
+  if (!c || !c->mlp || !feat || !logmu_out || n < 0) return MHD_EINVAL;
+  if (n == 0) return MHD_OK;
+  launch_mlp_infer(feat, n, c->nm, c->mlp_wb, c->mlp, logmu_out, (cudaStream_t)stream, c->nsm);
+  c->launches += 1;
+  return cuda_ok(cudaGetLastError());
+}
+
+int mhd_mlp_calibrate(mhd_ctx* c, const float* feat, const float* logmu, long n, double quantile, double* delta_out,
+                      void* stream) {
+  if (!c || !c->mlp || !feat || !logmu || n < 1 || !(quantile > 0.0 && quantile <= 1.0)) return MHD_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  KrpBuf kb;
+  float *f2, *pred;
+  int r = cells_scratch(c, n, s, &kb, &f2, &pred);
+  if (r) return r;
+  launch_mlp_infer(feat, n, c->nm, c->mlp_wb, c->mlp, pred, s, c->nsm);
+  c->launches += 1;
+  std::vector<float> hp(n), ht(n);
+  if (cudaMemcpyAsync(hp.data(), pred, sizeof(float) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ECUDA;
+  if (cudaMemcpyAsync(ht.data(), logmu, sizeof(float) * n, cudaMemcpyDefault, s) != cudaSuccess) return MHD_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ECUDA;
+  std::vector<double> e(n);
+  for (long i = 0; i < n; i++) e[i] = std::fabs((double)hp[i] - (double)ht[i]);
+  long k = std::min<long>(n - 1, (long)std::ceil(quantile * n) - 1);
+  if (k < 0) k = 0;
+  std::nth_element(e.begin(), e.begin() + k, e.end());
+  c->mlp_delta = std::max(e[k], 1e-6);
+  c->mlp_ready = true;
+  if (delta_out) *delta_out = c->mlp_delta;
+  return MHD_OK;
+}
+
+int mhd_mlp_grad(mhd_ctx* c, const float* feat, const float* logmu, long n, float* grad_out, float* loss_out,
+                 void* stream) {
+  if (!c || !c->mlp || !feat || !logmu || n < 1 || n > (1L << 30) || !grad_out) return MHD_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  float* gr = c->mlp + 3 * MLP_NPARAM;
+  if (cudaMemsetAsync(gr, 0, sizeof(float) * MLP_NPARAM, s) != cudaSuccess) return MHD_ECUDA;
+  if (cudaMemsetAsync(c->mlp_loss, 0, sizeof(float), s) != cudaSuccess) return MHD_ECUDA;
+  launch_mlp_train_step(feat, logmu, n, 1, 0, 0, (int)n, c->nm, c->mlp_wb, c->mlp, gr, c->mlp_loss, s);
+  c->launches += 1;
+  if (cudaMemcpyAsync(grad_out, gr, sizeof(float) * MLP_NPARAM, cudaMemcpyDefault, s) != cudaSuccess)
+    return MHD_ECUDA;
+  float L = 0.0f;
+  if (cudaMemcpyAsync(&L, c->mlp_loss, sizeof(float), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ECUDA;
+  if (cudaMemsetAsync(gr, 0, sizeof(float) * MLP_NPARAM, s) != cudaSuccess) return MHD_ECUDA;
+  if (loss_out) *loss_out = L / (float)n;
+  return cuda_ok(cudaStreamSynchronize(s));
+}
+
+int mhd_mlp_get(mhd_ctx* c, float* state) {
+  if (!c || !c->mlp || !state) return MHD_EINVAL;
+  if (cudaMemcpy(state, c->mlp, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToHost) != cudaSuccess) return MHD_ECUDA;
+  float* t = state + MLP_NPARAM;
+  for (int f = 0; f < MLP_NIN; f++) {
+    t[f] = c->nm.fmean[f];
+    t[MLP_NIN + f] = c->nm.finv[f];
+  }
+  t[2 * MLP_NIN] = c->nm.ymean;
+  t[2 * MLP_NIN + 1] = c->nm.ystd;
+  t[2 * MLP_NIN + 2] = (float)c->mlp_delta;
+  return MHD_OK;
+}
+
+int mhd_mlp_set(mhd_ctx* c, const float* state) {
+  if (!c || !state) return MHD_EINVAL;
+  if (!c->mlp) {
+    int r = mhd_mlp_init(c, 1);
+    if (r) return r;
+  }
+  if (cudaMemcpy(c->mlp, state, sizeof(float) * MLP_NPARAM, cudaMemcpyHostToDevice) != cudaSuccess) return MHD_ECUDA;
+  launch_mlp_pack(c->mlp, c->mlp_wb, nullptr);
+  const float* t = state + MLP_NPARAM;
+  for (int f = 0; f < MLP_NIN; f++) {
+    c->nm.fmean[f] = t[f];
+    c->nm.finv[f] = t[MLP_NIN + f];
+  }
+  c->nm.ymean = t[2 * MLP_NIN];
+  c->nm.ystd = t[2 * MLP_NIN + 1];
+  c->mlp_delta = t[2 * MLP_NIN + 2];
+  c->mlp_ready = c->mlp_delta > 0.0;
+  return cuda_ok(cudaDeviceSynchronize());
 }
 
 int mhd_c2p(mhd_ctx* c, const mhd_block* blocks, int nb, void* stream) {
@@ -574,7 +824,7 @@ int mhd_profile_read(mhd_ctx* c, double* ms, long long* count) {
 
 const char* mhd_kernel_name(int kind) {
   static const char* names[MHD_NKERNEL] = {"c2p", "flux_x", "flux_y", "flux_z", "fofc_flag",
-                                           "fofc_fix", "emf", "update", "faceb", "c2p_solve"};
+                                           "fofc_fix", "emf", "update", "faceb", "c2p_solve", "mlp"};
   return (kind >= 0 && kind < MHD_NKERNEL) ? names[kind] : "unknown";
 }
 

@@ -4,8 +4,8 @@
 // divide costs ~6 DFMA slots, a square root ~10) next to a wide FP32/INT
 // pipe, so the per-cell arithmetic below is arranged to issue as few FP64
 // divides and square roots as possible: reciprocals are shared, 1/W comes from
-// rsqrt, and the con2prim root is sought on a division-free function with the
-// same sign and root as the master function of Kastaun et al. (2021).
+// rsqrt, and the con2prim master function of Kastaun et al. (2021) is written
+// with a single division.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -42,6 +42,27 @@ struct DevBlock {
 
 // Work lists: item ranges of every block for one kernel kind.
 enum WorkKind { W_C2P = 0, W_FX, W_FY, W_FZ, W_CELL, W_EDGE, W_FACE, W_INIT, W_NKIND };
+
+// Slots of the per-cell con2prim scratch (SoA, [KW_N][n]).
+enum {
+  KW_QH = 0, KW_R2, KW_B2, KW_RB2, KW_RP2, KW_D, KW_RB, KW_RU0, KW_RU1, KW_RU2, KW_BU0, KW_BU1, KW_BU2,
+  KW_A, KW_B, KW_GA, KW_GB, KW_MU, KW_SDET, KW_ISDET, KW_USD, KW_UST, KW_N
+};
+// solve status: 0 solve needed, 1 root known, 2 no bracket / bad input,
+// 3 iteration cap, 4 bracket to be built from the learned guess
+
+// Learned-guess network 5 -> 64 -> 64 -> 1: fp32 parameter offsets, bf16
+// operand copies (W1 padded to [64][16], W2 [64][64], w3 padded to [8][64]).
+constexpr int MLP_NIN = 5, MLP_NH = 64, MLP_FSTRIDE = 8;
+constexpr int MLP_W1 = 0, MLP_B1 = MLP_W1 + MLP_NH * MLP_NIN, MLP_W2 = MLP_B1 + MLP_NH,
+              MLP_B2 = MLP_W2 + MLP_NH * MLP_NH, MLP_W3 = MLP_B2 + MLP_NH, MLP_B3 = MLP_W3 + MLP_NH,
+              MLP_NPARAM = MLP_B3 + 1;
+constexpr int MLP_BF_W1 = 0, MLP_BF_W2 = MLP_NH * 16, MLP_BF_W3 = MLP_BF_W2 + MLP_NH * MLP_NH,
+              MLP_NBF = MLP_BF_W3 + 8 * MLP_NH;
+struct MlpNorm {
+  float fmean[MLP_NIN], finv[MLP_NIN];  // feature mean and 1/std
+  float ymean, ystd;                    // target (log mu) mean and std
+};
 
 // Per-cell scratch of the three-phase con2prim (k_krp.cu).
 struct KrpBuf {
@@ -157,9 +178,12 @@ struct KEval {
   double x, rbar2, W, eps, eps_raw, G;
   bool vcap;
 };
-// G(mu) = mu (1 + Gamma eps + mu rbar^2 W) - W.  For an ideal gas with only the
-// lower eps clamp, G = W (nu + mu rbar^2) f(mu) with nu = (1 + Gamma eps)/W >= 0,
-// i.e. the KRP master function f times a positive factor: same sign, same root.
+// The KRP master function f(mu) = mu - 1/(nu + mu rbar^2) with
+// nu = (1 + Gamma eps)/W, i.e. f = mu - W/(1 + Gamma eps + mu rbar^2 W).  For
+// an ideal gas with only the lower eps clamp, nu_A = (1+a)(1+eps)/W >= nu_B =
+// (1+a)(1 + qbar - mu rbar^2), so nu = max(nu_A, nu_B) = nu_A.  (Stored in the
+// field G.)  f is nearly linear near the root (mu -> mu-hat contracts), which
+// keeps regula falsi fast; a division-free multiple of it is not.
 __device__ __forceinline__ void kev(const KS& s, double mu, KEval& e) {
   double x = 1.0 / fma(mu, s.b2, 1.0);
   double mux = mu * x;
@@ -175,7 +199,12 @@ __device__ __forceinline__ void kev(const KS& s, double mu, KEval& e) {
   e.x = x;
   e.rbar2 = rbar2;
   e.W = W;
-  e.G = mu * fma(mu * rbar2, W, fma(s.gam, e.eps, 1.0)) - W;
+  e.G = mu - W / fma(mu * rbar2, W, fma(s.gam, e.eps, 1.0));
+}
+// f(0) = -1/(1 + Gamma eps(0)): at mu = 0, v = 0, W = 1 and eps = qbar = q_h.
+__device__ __forceinline__ double f_zero(const KS& s) {
+  double e0 = s.qh < s.eps_min ? s.eps_min : s.qh;
+  return -1.0 / fma(s.gam, e0, 1.0);
 }
 
 // Upper bracket end: three steps of mu <- 1/sqrt(1 + rbar^2(mu)) from
@@ -193,9 +222,29 @@ __device__ __forceinline__ double mu_plus(const KS& s) {
   return mu;
 }
 
-// Illinois regula falsi with bisection safeguard on [a,b], G(a) < 0 <= G(b);
-// stops when b - a <= tol b, then one regula-falsi step with the true end
-// values.  Returns false when the iteration cap is reached.
+// Five features of the KRP variables for the learned guess (FP32):
+// log q_h with q_h = q - b^2/2 >= 0 (the energy per D without the magnetic
+// b^2/2, which dominates q in magnetised cells), log(1 + r^2/(1+q_h)^2),
+// log(1 + b^2), the r-b alignment (r.b)^2/(r^2 b^2), log(1 + (r.b)^2/(1+q_h)^2).
+// Written with stride MLP_FSTRIDE.
+__device__ __forceinline__ void krp_features(const KS& s, float* f) {
+  const float qh = (float)s.qh;
+  const float r2 = (float)s.r2, b2 = (float)s.b2, rb2 = (float)s.rb2;
+  const float iq = 1.0f / ((1.0f + qh) * (1.0f + qh));
+  f[0] = __logf(fmaxf(qh, 1e-30f));
+  f[1] = log1pf(r2 * iq);
+  f[2] = log1pf(b2);
+  const float rb = r2 * b2;
+  f[3] = rb > 0.0f ? fminf(rb2 / rb, 1.0f) : 0.0f;
+  f[4] = log1pf(rb2 * iq);
+  f[5] = f[6] = f[7] = 0.0f;
+}
+
+// Illinois regula falsi with bisection safeguard on [a,b], f(a) < 0 <= f(b);
+// every point is nudged by tol b/4 away from the end replaced last, so the
+// bracket closes one step after the iterate converges; stops when b - a <=
+// tol b, then one regula-falsi step with the true end values.  Returns false
+// when the iteration cap is reached.
 __device__ __forceinline__ bool illinois(const KS& s, double a, double Ga, double b, double Gb, double tol, int maxit,
                                          double& root, int& iters) {
   iters = 0;
@@ -207,6 +256,10 @@ __device__ __forceinline__ bool illinois(const KS& s, double a, double Ga, doubl
     if (iters >= maxit) return false;
     iters++;
     double c = (a * Fb - b * Fa) / (Fb - Fa);
+    // nudge away from the end replaced last: once the iterate is within eta of
+    // the root the next point lands past it and closes the bracket
+    const double eta = 0.25 * tol * b;
+    c += side == -1 ? eta : (side == 1 ? -eta : 0.0);
     if (!(c > a && c < b)) c = 0.5 * (a + b);
     kev(s, c, e);
     if (e.G < 0.0) {
@@ -285,14 +338,14 @@ __device__ __forceinline__ bool krp_prep(const Par& P, const double* U, const do
   return true;
 }
 
-// Phase 2a: a bracket [a,b] with G(a) < 0 <= G(b).  G(0) = -1 exactly (v = 0,
-// W = 1).  A learned guess [glo, ghi] is used when given and verified by the
+// Phase 2a: a bracket [a,b] with f(a) < 0 <= f(b), with f(0) < 0 from
+// f_zero.  `iters` counts the evaluations of f it made.  A learned guess [glo, ghi] is used when given and verified by the
 // signs at both ends; otherwise [0, mu+] (or [mu+, 1] when G(mu+) < 0).
 // Returns 0: solve needed; 1: root found (in mu); 2: no bracket (failure).
 __device__ __forceinline__ int krp_bracket(const KS& s, double glo, double ghi, double& a, double& b, double& Ga,
                                            double& Gb, double& mu, int& iters) {
   KEval e;
-  a = 0.0; Ga = -1.0; b = 1.0; Gb = 0.0;
+  a = 0.0; Ga = f_zero(s); b = 1.0; Gb = 0.0;
   iters = 0;
   bool have = false;
   if (glo >= 0.0 && ghi > glo) {
@@ -312,11 +365,13 @@ __device__ __forceinline__ int krp_bracket(const KS& s, double glo, double ghi, 
     double mp = mu_plus(s);
     if (mp <= a) mp = 1.0;
     kev(s, mp, e);
+    iters++;
     b = mp; Gb = e.G;
     if (Gb < 0.0) {
       a = mp; Ga = Gb;
       b = 1.0;
       kev(s, b, e);
+      iters++;
       Gb = e.G;
     }
   }

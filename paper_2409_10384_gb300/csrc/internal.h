@@ -1,5 +1,6 @@
 // Host-side launchers shared between the kernel translation units and the C-ABI.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include "dev.cuh"
 
@@ -30,11 +31,23 @@ void launch_krp_prep_fofc(const Work& w, const Par& P, double g0, double g1, dou
 void launch_krp_finish_fofc(const Work& w, const Par& P, const KrpBuf& kb, unsigned long long* stats,
                             cudaStream_t s, int grid);
 void launch_krp_prep_cells(const Par& P, const KrpBuf& kb, const double* cons, const double* Bd, const double* g,
-                           const float* guess, cudaStream_t s, int grid);
+                           int learned, float* feat, cudaStream_t s, int grid);
 void launch_krp_finish_cells(const Par& P, const KrpBuf& kb, double* cons, const double* Bd, const double* g,
                              double* prim, unsigned char* flags, int* iters, unsigned long long* stats, cudaStream_t s,
                              int grid);
 int occupancy_krp(int* per_sm);
+int mlp_setup_attrs();
+void launch_mlp_infer(const float* feat, long long n, const MlpNorm& nm, const __nv_bfloat16* wb, const float* w,
+                      float* out, cudaStream_t s, int nsm);
+void launch_mlp_train_step(const float* feat, const float* target, long long n, long long pa, long long pb,
+                           long long off, int batch, const MlpNorm& nm, const __nv_bfloat16* wb, const float* w,
+                           float* grad, float* loss, cudaStream_t s);
+void launch_mlp_adam(float* w, float* m, float* v, float* grad, float lr, int t, __nv_bfloat16* wb, cudaStream_t s);
+void launch_mlp_pack(const float* w, __nv_bfloat16* wb, cudaStream_t s);
+void launch_mlp_logmu(const KrpBuf& kb, float* out, cudaStream_t s, int nsm);
+void launch_mlp_stats(const float* feat, const float* target, long long n, double* acc, cudaStream_t s, int nsm);
+void launch_krp_seed(const Par& P, const KrpBuf& kb, const float* logmu, int learned, float delta, cudaStream_t s,
+                     int grid);
 int occupancy_c2p(int* per_sm);
 int occupancy_face(int* per_sm);
 int occupancy_update(int* per_sm);

@@ -10,12 +10,6 @@
 
 namespace grmhd {
 
-// Slots of the per-cell scratch (SoA, [KW_N][n]).
-enum {
-  KW_QH = 0, KW_R2, KW_B2, KW_RB2, KW_RP2, KW_D, KW_RB, KW_RU0, KW_RU1, KW_RU2, KW_BU0, KW_BU1, KW_BU2,
-  KW_A, KW_B, KW_GA, KW_GB, KW_MU, KW_SDET, KW_ISDET, KW_USD, KW_UST, KW_N
-};
-// status: 0 solve needed, 1 root known, 2 no bracket / bad input, 3 iteration cap
 
 __device__ __forceinline__ void kw_store(const KrpBuf& kb, long long i, const KrpCell& k) {
   const long long n = kb.n;
@@ -37,21 +31,31 @@ __device__ __forceinline__ void kw_load(const KrpBuf& kb, const Par& P, long lon
   k.bu[0] = w[KW_BU0 * n + i]; k.bu[1] = w[KW_BU1 * n + i]; k.bu[2] = w[KW_BU2 * n + i];
 }
 
-// prep of one cell: KRP variables, bracket (plain or learned), status
+// prep of one cell: KRP variables and status; learned = false: the plain
+// bracket [0, mu+]; learned = true: status 4 (bracket from the network's
+// guess later).  feat (optional): the network's features of the cell.
 __device__ __forceinline__ void prep_cell(const Par& P, const KrpBuf& kb, long long i, const double* U,
-                                          const double* Bd, const Metric& m, double glo, double ghi) {
+                                          const double* Bd, const Metric& m, bool learned = false,
+                                          float* feat = nullptr) {
   KrpCell k;
   unsigned fl;
   const long long n = kb.n;
   unsigned char st = 2;
   int its = 0;
   if (krp_prep(P, U, Bd, m, k, fl)) {
-    double a, b, Ga, Gb, mu = 0.0;
-    int r = krp_bracket(k.s, glo, ghi, a, b, Ga, Gb, mu, its);
-    st = (unsigned char)(r == 0 ? 0 : (r == 1 ? 1 : 2));
-    kb.w[KW_A * n + i] = a; kb.w[KW_B * n + i] = b;
-    kb.w[KW_GA * n + i] = Ga; kb.w[KW_GB * n + i] = Gb;
-    kb.w[KW_MU * n + i] = mu;
+    if (feat) krp_features(k.s, feat + i * MLP_FSTRIDE);
+    if (learned) {
+      st = 4;
+    } else {
+      double a, b, Ga, Gb, mu = 0.0;
+      int r = krp_bracket(k.s, -1.0, -1.0, a, b, Ga, Gb, mu, its);
+      st = (unsigned char)(r == 0 ? 0 : (r == 1 ? 1 : 2));
+      kb.w[KW_A * n + i] = a; kb.w[KW_B * n + i] = b;
+      kb.w[KW_GA * n + i] = Ga; kb.w[KW_GB * n + i] = Gb;
+      kb.w[KW_MU * n + i] = mu;
+    }
+  } else if (feat) {
+    for (int f = 0; f < MLP_FSTRIDE; f++) feat[i * MLP_FSTRIDE + f] = 0.0f;
   }
   kw_store(kb, i, k);
   kb.w[KW_SDET * n + i] = m.sdet;
@@ -68,7 +72,8 @@ __device__ __forceinline__ void load_metric6(const double* g6, long long stride,
 }
 
 // ------------------------------------------------------------------ root solve
-// Illinois regula falsi (as in `illinois`) with lane refill.  Reads the
+// Illinois regula falsi with the end-point nudge (as in `illinois`) and lane
+// refill.  Reads the
 // bracket of every status-0 cell, writes mu, iterations and status 1 or 3.
 __global__ void __launch_bounds__(256) k_krp_solve(Par P, KrpBuf kb, unsigned long long* stats) {
   const unsigned lane = threadIdx.x & 31;
@@ -117,6 +122,8 @@ __global__ void __launch_bounds__(256) k_krp_solve(Par P, KrpBuf kb, unsigned lo
       } else {
         it++;
         double c = (a * Fb - b * Fa) / (Fb - Fa);
+        const double eta = 0.25 * P.tol * b;
+        c += side == -1 ? eta : (side == 1 ? -eta : 0.0);
         if (!(c > a && c < b)) c = 0.5 * (a + b);
         KEval e;
         kev(s, c, e);
@@ -173,7 +180,7 @@ __global__ void __launch_bounds__(128) k_krp_prep_block(Work w, Par P, KrpBuf kb
     double U[5];
 #pragma unroll
     for (int v = 0; v < 5; v++) U[v] = b.cons[v * nc + c];
-    prep_cell(P, kb, it, U, Bd, m, -1.0, -1.0);
+    prep_cell(P, kb, it, U, Bd, m);
   }
 }
 
@@ -266,7 +273,7 @@ __global__ void __launch_bounds__(128) k_krp_prep_fofc(Work w, Par P, double g0,
     Metric m;
     load_metric6(b.adm + 4 * nc, nc, c, m);
     const double Bd[3] = {b.bcc[c], b.bcc[nc + c], b.bcc[2 * nc + c]};
-    prep_cell(P, kb, it, U, Bd, m, -1.0, -1.0);
+    prep_cell(P, kb, it, U, Bd, m);
     kb.w[KW_USD * n + it] = U[0];
     kb.w[KW_UST * n + it] = U[4];
   }
@@ -320,7 +327,7 @@ __global__ void __launch_bounds__(128) k_krp_finish_fofc(Work w, Par P, KrpBuf k
 // ------------------------------------------------------- independent cells
 __global__ void __launch_bounds__(128) k_krp_prep_cells(Par P, KrpBuf kb, const double* __restrict__ cons,
                                                         const double* __restrict__ Bd, const double* __restrict__ g,
-                                                        const float* __restrict__ guess) {
+                                                        int learned, float* __restrict__ feat) {
   const long long n = kb.n;
   if (blockIdx.x == 0 && threadIdx.x == 0) *kb.ctr = 0ull;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
@@ -331,12 +338,7 @@ __global__ void __launch_bounds__(128) k_krp_prep_cells(Par P, KrpBuf kb, const 
     for (int v = 0; v < 5; v++) U[v] = cons[v * n + c];
 #pragma unroll
     for (int v = 0; v < 3; v++) B[v] = Bd[v * n + c];
-    double lo = -1.0, hi = -1.0;
-    if (guess) {
-      lo = guess[2 * c];
-      hi = guess[2 * c + 1];
-    }
-    prep_cell(P, kb, c, U, B, m, lo, hi);
+    prep_cell(P, kb, c, U, B, m, learned != 0, feat);
   }
 }
 
@@ -417,8 +419,8 @@ void launch_krp_finish_fofc(const Work& w, const Par& P, const KrpBuf& kb, unsig
   k_krp_finish_fofc<<<grid, 128, 0, s>>>(w, P, kb, stats);
 }
 void launch_krp_prep_cells(const Par& P, const KrpBuf& kb, const double* cons, const double* Bd, const double* g,
-                           const float* guess, cudaStream_t s, int grid) {
-  k_krp_prep_cells<<<grid, 128, 0, s>>>(P, kb, cons, Bd, g, guess);
+                           int learned, float* feat, cudaStream_t s, int grid) {
+  k_krp_prep_cells<<<grid, 128, 0, s>>>(P, kb, cons, Bd, g, learned, feat);
 }
 void launch_krp_finish_cells(const Par& P, const KrpBuf& kb, double* cons, const double* Bd, const double* g,
                              double* prim, unsigned char* flags, int* iters, unsigned long long* stats, cudaStream_t s,

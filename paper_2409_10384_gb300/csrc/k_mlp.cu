@@ -1,0 +1,490 @@
+// Learned con2prim guess: a 5 -> 64 -> 64 -> 1 tanh network with BF16
+// operands and FP32 accumulation on the tensor cores (mma.sync m16n8k16),
+// predicting log(mu) of the Kastaun et al. root from five features of the
+// KRP variables.  Hand-written inference, forward + backward training step,
+// Adam, and the bracket that the FP64 solve starts from.  The paper has no
+// such network; the FP64 bracketed solve stays the refinement and the judge.
+#include <cuda_bf16.h>
+
+#include "dev.cuh"
+#include "internal.h"
+
+namespace grmhd {
+
+namespace {
+
+__device__ __forceinline__ unsigned pack2(float lo, float hi) {
+  __nv_bfloat16 a = __float2bfloat16_rn(lo), b = __float2bfloat16_rn(hi);
+  return (unsigned)__bfloat16_as_ushort(a) | ((unsigned)__bfloat16_as_ushort(b) << 16);
+}
+__device__ __forceinline__ unsigned pack2b(__nv_bfloat16 a, __nv_bfloat16 b) {
+  return (unsigned)__bfloat16_as_ushort(a) | ((unsigned)__bfloat16_as_ushort(b) << 16);
+}
+__device__ __forceinline__ void mma16816(float* c, const unsigned* a, const unsigned* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+// A fragment (16x16) of an fp32 matrix, element (m,k) at A[m*sm + k*sk], origin (m0,k0)
+__device__ __forceinline__ void frag_a(const float* A, int sm, int sk, int m0, int k0, unsigned* a) {
+  const int g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3;
+  const int r0 = m0 + g, r1 = r0 + 8, c0 = k0 + 2 * t, c1 = c0 + 8;
+  a[0] = pack2(A[r0 * sm + c0 * sk], A[r0 * sm + (c0 + 1) * sk]);
+  a[1] = pack2(A[r1 * sm + c0 * sk], A[r1 * sm + (c0 + 1) * sk]);
+  a[2] = pack2(A[r0 * sm + c1 * sk], A[r0 * sm + (c1 + 1) * sk]);
+  a[3] = pack2(A[r1 * sm + c1 * sk], A[r1 * sm + (c1 + 1) * sk]);
+}
+// B fragment (16x8) of an fp32 matrix, element (k,n) at B[k*sk + n*sn], origin (k0,n0)
+__device__ __forceinline__ void frag_b(const float* B, int sk, int sn, int k0, int n0, unsigned* b) {
+  const int g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3;
+  const int n = n0 + g, k = k0 + 2 * t;
+  b[0] = pack2(B[k * sk + n * sn], B[(k + 1) * sk + n * sn]);
+  b[1] = pack2(B[(k + 8) * sk + n * sn], B[(k + 9) * sk + n * sn]);
+}
+// B fragment of a bf16 matrix
+__device__ __forceinline__ void frag_bh(const __nv_bfloat16* B, int sk, int sn, int k0, int n0, unsigned* b) {
+  const int g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3;
+  const int n = n0 + g, k = k0 + 2 * t;
+  b[0] = pack2b(B[k * sk + n * sn], B[(k + 1) * sk + n * sn]);
+  b[1] = pack2b(B[(k + 8) * sk + n * sn], B[(k + 9) * sk + n * sn]);
+}
+// store a C fragment (16x8) to an fp32 matrix C[m*ld + n] at origin (m0,n0)
+template <class F>
+__device__ __forceinline__ void frag_c_apply(const float* c, int m0, int n0, F&& f) {
+  const int g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3;
+  f(m0 + g, n0 + 2 * t, c[0]);
+  f(m0 + g, n0 + 2 * t + 1, c[1]);
+  f(m0 + g + 8, n0 + 2 * t, c[2]);
+  f(m0 + g + 8, n0 + 2 * t + 1, c[3]);
+}
+
+constexpr int NH = MLP_NH;
+// per-warp shared buffers (floats)
+constexpr int S_X = 0, S_H1 = 32 * 16, S_H2 = S_H1 + 32 * NH, S_DZ2 = S_H2 + 32 * NH, S_DZ1 = S_DZ2 + 32 * NH,
+              S_Y = S_DZ1 + 32 * NH, S_T = S_Y + 32, S_WARP = S_T + 32;
+
+// normalised features of the warp's 32 samples into Xs [32][16] (cols >= 5 zero)
+__device__ __forceinline__ void load_x(float* Xs, const float* feat, long long idx, bool valid, const MlpNorm& nm) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int f = 0; f < 16; f++) {
+    float v = 0.0f;
+    if (valid && f < MLP_NIN) v = (feat[idx * MLP_FSTRIDE + f] - nm.fmean[f]) * nm.finv[f];
+    Xs[lane * 16 + f] = v;
+  }
+}
+
+// forward of 32 samples: H1, H2 (fp32) and y (normalised output) in smem
+__device__ __forceinline__ void warp_forward(float* sw, const __nv_bfloat16* wb, const float* w) {
+  float* Xs = sw + S_X;
+  float* H1 = sw + S_H1;
+  float* H2 = sw + S_H2;
+  float* Y = sw + S_Y;
+  __syncwarp();
+  // layer 1: [32 x 16] x W1p^T, W1p [64][16] bf16
+  for (int mt = 0; mt < 2; mt++) {
+    unsigned a[4];
+    frag_a(Xs, 16, 1, 16 * mt, 0, a);
+    for (int nt = 0; nt < NH / 8; nt++) {
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+      unsigned b[2];
+      frag_bh(wb + MLP_BF_W1, 1, 16, 0, 8 * nt, b);
+      mma16816(c, a, b);
+      frag_c_apply(c, 16 * mt, 8 * nt, [&](int m, int n, float v) { H1[m * NH + n] = tanhf(v + w[MLP_B1 + n]); });
+    }
+  }
+  __syncwarp();
+  // layer 2: [32 x 64] x W2^T
+  for (int mt = 0; mt < 2; mt++) {
+    unsigned a[4][4];
+    for (int kt = 0; kt < 4; kt++) frag_a(H1, NH, 1, 16 * mt, 16 * kt, a[kt]);
+    for (int nt = 0; nt < NH / 8; nt++) {
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int kt = 0; kt < 4; kt++) {
+        unsigned b[2];
+        frag_bh(wb + MLP_BF_W2, 1, NH, 16 * kt, 8 * nt, b);
+        mma16816(c, a[kt], b);
+      }
+      frag_c_apply(c, 16 * mt, 8 * nt, [&](int m, int n, float v) { H2[m * NH + n] = tanhf(v + w[MLP_B2 + n]); });
+    }
+  }
+  __syncwarp();
+  // layer 3: [32 x 64] x W3p^T, W3p [8][64] (row 0 = w3)
+  for (int mt = 0; mt < 2; mt++) {
+    float c[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int kt = 0; kt < 4; kt++) {
+      unsigned a[4], b[2];
+      frag_a(H2, NH, 1, 16 * mt, 16 * kt, a);
+      frag_bh(wb + MLP_BF_W3, 1, NH, 16 * kt, 0, b);
+      mma16816(c, a, b);
+    }
+    frag_c_apply(c, 16 * mt, 0, [&](int m, int n, float v) {
+      if (n == 0) Y[m] = v + w[MLP_B3];
+    });
+  }
+  __syncwarp();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ inference
+// out[i] = predicted log(mu) (de-normalised) for n samples
+__global__ void __launch_bounds__(128) k_mlp_infer(const float* __restrict__ feat, long long n, MlpNorm nm,
+                                                  const __nv_bfloat16* __restrict__ wb, const float* __restrict__ w,
+                                                  float* __restrict__ out) {
+  extern __shared__ float smem[];
+  __nv_bfloat16* swb = (__nv_bfloat16*)smem;
+  float* sw0 = smem + (MLP_NBF + 1) / 2;
+  for (int i = threadIdx.x; i < MLP_NBF; i += blockDim.x) swb[i] = wb[i];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* sw = sw0 + warp * S_WARP;
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long base = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * 32; base < n; base += nwarps * 32) {
+    const long long idx = base + lane;
+    load_x(sw, feat, idx, idx < n, nm);
+    warp_forward(sw, swb, w);
+    if (idx < n) out[idx] = sw[S_Y + lane] * nm.ystd + nm.ymean;
+    __syncwarp();
+  }
+}
+
+// ----------------------------------------------------------------- training
+// One step over `batch` samples starting at `off` of the permutation
+// i -> (pa*i + pb) mod n: forward, MSE loss, backward, gradients summed into
+// grad (fp32, atomic) and the summed squared error into loss.
+__global__ void __launch_bounds__(64) k_mlp_train_step(const float* __restrict__ feat, const float* __restrict__ target,
+                                                      long long n, long long pa, long long pb, long long off,
+                                                      int batch, MlpNorm nm, const __nv_bfloat16* __restrict__ wb,
+                                                      const float* __restrict__ w, float* grad, float* loss) {
+  extern __shared__ float smem[];
+  __nv_bfloat16* swb = (__nv_bfloat16*)smem;
+  float* sg = smem + (MLP_NBF + 1) / 2;
+  float* sw0 = sg + MLP_NPARAM;
+  for (int i = threadIdx.x; i < MLP_NBF; i += blockDim.x) swb[i] = wb[i];
+  for (int i = threadIdx.x; i < MLP_NPARAM; i += blockDim.x) sg[i] = 0.0f;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* sw = sw0 + warp * S_WARP;
+  float* Xs = sw + S_X;
+  float* H1 = sw + S_H1;
+  float* H2 = sw + S_H2;
+  float* DZ2 = sw + S_DZ2;
+  float* DZ1 = sw + S_DZ1;
+  float* Y = sw + S_Y;
+  float* T = sw + S_T;
+  const int s = (blockIdx.x * (blockDim.x >> 5) + warp) * 32 + lane;
+  const bool valid = s < batch;
+  long long idx = 0;
+  if (valid) {
+    unsigned long long ii = (unsigned long long)((off + s) % n);
+    idx = (long long)(((unsigned long long)pa * ii + (unsigned long long)pb) % (unsigned long long)n);
+  }
+  load_x(Xs, feat, idx, valid, nm);
+  T[lane] = valid ? (target[idx] - nm.ymean) / nm.ystd : 0.0f;
+  warp_forward(sw, swb, w);
+  // dL/dy of the mean squared error over the batch
+  const float r = valid ? Y[lane] - T[lane] : 0.0f;
+  const float dy = 2.0f * r / (float)batch;
+  float sq = r * r;
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if (lane == 0) atomicAdd(loss, sq);
+  Y[lane] = dy;
+  __syncwarp();
+  // dZ2 = dy w3 (1 - H2^2); b3, w3 gradients
+  for (int j = 0; j < NH; j++) {
+    const float h = H2[lane * NH + j];
+    DZ2[lane * NH + j] = dy * w[MLP_W3 + j] * (1.0f - h * h);
+  }
+  {
+    float d3 = dy;
+    for (int o = 16; o > 0; o >>= 1) d3 += __shfl_xor_sync(0xffffffffu, d3, o);
+    if (lane == 0) atomicAdd(&sg[MLP_B3], d3);
+  }
+  __syncwarp();
+  for (int j = lane; j < NH; j += 32) {
+    float a = 0.f, b2 = 0.f;
+    for (int q = 0; q < 32; q++) {
+      a += Y[q] * H2[q * NH + j];
+      b2 += DZ2[q * NH + j];
+    }
+    atomicAdd(&sg[MLP_W3 + j], a);
+    atomicAdd(&sg[MLP_B2 + j], b2);
+  }
+  // dW2[j][i] = sum_s DZ2[s][j] H1[s][i]   (M = j, N = i, K = s)
+  for (int mt = 0; mt < 4; mt++)
+    for (int nt = 0; nt < 8; nt++) {
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int kt = 0; kt < 2; kt++) {
+        unsigned a[4], b[2];
+        frag_a(DZ2, 1, NH, 16 * mt, 16 * kt, a);
+        frag_b(H1, NH, 1, 16 * kt, 8 * nt, b);
+        mma16816(c, a, b);
+      }
+      frag_c_apply(c, 16 * mt, 8 * nt, [&](int m, int nn, float v) { atomicAdd(&sg[MLP_W2 + m * NH + nn], v); });
+    }
+  // dH1 = DZ2 W2 (M = s, N = i, K = j); dZ1 = dH1 (1 - H1^2)
+  for (int mt = 0; mt < 2; mt++)
+    for (int nt = 0; nt < 8; nt++) {
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int kt = 0; kt < 4; kt++) {
+        unsigned a[4], b[2];
+        frag_a(DZ2, NH, 1, 16 * mt, 16 * kt, a);
+        frag_bh(swb + MLP_BF_W2, NH, 1, 16 * kt, 8 * nt, b);
+        mma16816(c, a, b);
+      }
+      frag_c_apply(c, 16 * mt, 8 * nt, [&](int m, int nn, float v) {
+        const float h = H1[m * NH + nn];
+        DZ1[m * NH + nn] = v * (1.0f - h * h);
+      });
+    }
+  __syncwarp();
+  for (int j = lane; j < NH; j += 32) {
+    float b1 = 0.f;
+    for (int q = 0; q < 32; q++) b1 += DZ1[q * NH + j];
+    atomicAdd(&sg[MLP_B1 + j], b1);
+  }
+  // dW1[i][f] = sum_s DZ1[s][i] X[s][f]   (M = i, N = f (8), K = s)
+  for (int mt = 0; mt < 4; mt++) {
+    float c[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int kt = 0; kt < 2; kt++) {
+      unsigned a[4], b[2];
+      frag_a(DZ1, 1, NH, 16 * mt, 16 * kt, a);
+      frag_b(Xs, 16, 1, 16 * kt, 0, b);
+      mma16816(c, a, b);
+    }
+    frag_c_apply(c, 16 * mt, 0, [&](int m, int f, float v) {
+      if (f < MLP_NIN) atomicAdd(&sg[MLP_W1 + m * MLP_NIN + f], v);
+    });
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < MLP_NPARAM; i += blockDim.x) {
+    const float v = sg[i];
+    if (v != 0.0f) atomicAdd(&grad[i], v);
+  }
+}
+
+// Adam on the fp32 master weights; refreshes the bf16 operand copies and
+// clears the gradient for the next step.
+__global__ void k_mlp_adam(float* w, float* m, float* v, float* grad, float lr, float b1, float b2, float eps,
+                           float c1, float c2, __nv_bfloat16* wb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < MLP_NPARAM) {
+    const float g = grad[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * g;
+    const float vi = b2 * v[i] + (1.0f - b2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    grad[i] = 0.0f;
+  }
+}
+
+// bf16 operand copies: W1p [64][16] (zero padded), W2 [64][64], W3p [8][64]
+__global__ void k_mlp_pack(const float* w, __nv_bfloat16* wb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < MLP_NBF) {
+    float v = 0.0f;
+    if (i < MLP_BF_W2) {
+      const int r = i / 16, c = i % 16;
+      if (c < MLP_NIN) v = w[MLP_W1 + r * MLP_NIN + c];
+    } else if (i < MLP_BF_W3) {
+      v = w[MLP_W2 + (i - MLP_BF_W2)];
+    } else {
+      const int r = (i - MLP_BF_W3) / NH, c = (i - MLP_BF_W3) % NH;
+      if (r == 0) v = w[MLP_W3 + c];
+    }
+    wb[i] = __float2bfloat16_rn(v);
+  }
+}
+
+// sums and sums of squares of the features and the target (double atomics)
+__global__ void k_mlp_stats(const float* __restrict__ feat, const float* __restrict__ target, long long n,
+                            double* acc) {
+  double s[12] = {0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    for (int f = 0; f < MLP_NIN; f++) {
+      const double x = feat[i * MLP_FSTRIDE + f];
+      s[f] += x;
+      s[6 + f] += x * x;
+    }
+    const double t = target[i];
+    s[5] += t;
+    s[11] += t * t;
+  }
+  for (int k = 0; k < 12; k++) {
+    double v = s[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&acc[k], v);
+  }
+}
+
+// ------------------------------------------------- FP32 search, FP64 bracket
+// The master function in FP32 (the KRP variables rounded to float).  GB300's
+// FP32 pipe is ~60x wider than its FP64 pipe, so the root search runs here and
+// FP64 only verifies and refines.
+struct KSf {
+  float qh, r2, b2, rb2, rp2, gam, emin, vmax2;
+};
+__device__ __forceinline__ float f32_master(const KSf& s, float mu) {
+  const float x = 1.0f / fmaf(mu, s.b2, 1.0f);
+  const float mux = mu * x;
+  const float rbar2 = x * fmaf(s.r2, x, mu * (1.0f + x) * s.rb2);
+  const float qbar = s.qh - 0.5f * mux * mux * s.rp2;
+  const float v2 = fminf(mu * mu * rbar2, s.vmax2);
+  const float W = rsqrtf(1.0f - v2);
+  const float wm1 = v2 * W * W / (1.0f + W);
+  const float eps = fmaxf(fmaf(W, qbar - mu * rbar2, wm1), s.emin);
+  return mu - W / fmaf(mu * rbar2, W, fmaf(s.gam, eps, 1.0f));
+}
+__device__ __forceinline__ float f32_mu_plus(const KSf& s) {
+  const float rpar2 = s.b2 > 0.0f ? s.rb2 / s.b2 : s.r2;
+  float mu = rsqrtf(1.0f + rpar2);
+  for (int it = 0; it < 3; it++) {
+    const float x = 1.0f / fmaf(mu, s.b2, 1.0f);
+    mu = rsqrtf(1.0f + x * fmaf(s.r2, x, mu * (1.0f + x) * s.rb2));
+  }
+  return mu;
+}
+
+// Cells with status 4.  Starting pair: the network's guess mu_g and mu_g e^d
+// (learned = 1), or 0 and the FP32 mu+ (learned = 0).  Eight FP32 secant
+// steps give mu32; FP64 then evaluates f at mu32 and at mu32 (1 +- 4e-6)
+// towards the root.  A sign change is a bracket of relative width 4e-6; else
+// the bracket extends from the far point to 0 (f(0) < 0, no evaluation) or
+// 1 (f(1) >= 0 for a physical state).  The refill solve finishes from there.
+__global__ void __launch_bounds__(128) k_krp_seed(Par P, KrpBuf kb, const float* __restrict__ logmu, int learned,
+                                                  float delta) {
+  const long long n = kb.n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    if (kb.st[i] != 4) continue;
+    KS s;
+    const double* w = kb.w;
+    s.qh = w[KW_QH * n + i]; s.r2 = w[KW_R2 * n + i]; s.b2 = w[KW_B2 * n + i];
+    s.rb2 = w[KW_RB2 * n + i]; s.rperp2 = w[KW_RP2 * n + i];
+    s.gam = P.gam; s.eps_min = P.eps_atm; s.vmax2 = P.vmax2;
+    KSf sf;
+    sf.qh = (float)s.qh; sf.r2 = (float)s.r2; sf.b2 = (float)s.b2; sf.rb2 = (float)s.rb2; sf.rp2 = (float)s.rperp2;
+    sf.gam = (float)s.gam; sf.emin = fmaxf((float)s.eps_min, 1e-37f); sf.vmax2 = (float)s.vmax2;
+    // FP32 secant from the starting pair
+    float x0, x1;
+    if (learned) {
+      x0 = __expf(logmu[i]);
+      if (!(x0 > 1e-30f)) x0 = 1e-30f;
+      if (x0 > 1.0f) x0 = 1.0f;
+      x1 = fminf(x0 * __expf(delta), 1.0f);
+      if (x1 == x0) x1 = x0 * (1.0f - 1e-3f);
+    } else {
+      x0 = 0.0f;
+      x1 = f32_mu_plus(sf);
+    }
+    float f0 = f32_master(sf, x0), f1 = f32_master(sf, x1);
+    for (int it = 0; it < 8; it++) {
+      const float den = f1 - f0;
+      if (den == 0.0f || !(f1 == f1)) break;
+      float x2 = x1 - f1 * (x1 - x0) / den;
+      if (!(x2 > 0.0f && x2 <= 1.0f)) x2 = 0.5f * (x1 + (f1 < 0.0f ? 1.0f : 0.0f));
+      x0 = x1; f0 = f1;
+      x1 = x2; f1 = f32_master(sf, x2);
+    }
+    double m32 = (double)x1;
+    if (!(m32 > 1e-300 && m32 <= 1.0)) m32 = 0.5;
+    KEval e;
+    kev(s, m32, e);
+    int its = 1;
+    double a = 0.0, b = 1.0, Ga = f_zero(s), Gb = 0.0;
+    unsigned char st = 0;
+    if (e.G == 0.0) {
+      st = 1;
+      kb.w[KW_MU * n + i] = m32;
+    } else if (e.G < 0.0) {
+      a = m32; Ga = e.G;
+      double x = fmin(m32 * (1.0 + 4e-6), 1.0);
+      kev(s, x, e);
+      its++;
+      if (e.G >= 0.0) {
+        b = x; Gb = e.G;
+      } else {
+        a = x; Ga = e.G;
+        b = 1.0;
+        kev(s, b, e);
+        its++;
+        Gb = e.G;
+        if (!(Gb >= 0.0)) st = 2;
+      }
+      if (st == 0 && Gb == 0.0) { st = 1; kb.w[KW_MU * n + i] = b; }
+    } else {
+      b = m32; Gb = e.G;
+      double x = m32 * (1.0 - 4e-6);
+      kev(s, x, e);
+      its++;
+      if (e.G < 0.0) {
+        a = x; Ga = e.G;
+      } else if (e.G == 0.0) {
+        st = 1;
+        kb.w[KW_MU * n + i] = x;
+      } else {
+        b = x; Gb = e.G;
+      }
+    }
+    kb.w[KW_A * n + i] = a; kb.w[KW_B * n + i] = b;
+    kb.w[KW_GA * n + i] = Ga; kb.w[KW_GB * n + i] = Gb;
+    kb.it[i] = its;
+    kb.st[i] = st;
+  }
+}
+
+// log(mu) of solved cells (training targets); NaN where the solve failed
+__global__ void k_mlp_logmu(KrpBuf kb, float* out) {
+  const long long n = kb.n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = kb.st[i] == 1 ? (float)log(kb.w[KW_MU * n + i]) : __int_as_float(0x7fc00000);
+}
+
+// ------------------------------------------------------------------ launchers
+void launch_mlp_logmu(const KrpBuf& kb, float* out, cudaStream_t s, int nsm) {
+  k_mlp_logmu<<<nsm * 4, 256, 0, s>>>(kb, out);
+}
+size_t mlp_infer_smem() { return sizeof(float) * ((MLP_NBF + 1) / 2 + 4 * S_WARP); }
+size_t mlp_train_smem() { return sizeof(float) * ((MLP_NBF + 1) / 2 + MLP_NPARAM + 2 * S_WARP); }
+
+int mlp_setup_attrs() {
+  cudaError_t e1 = cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_infer_smem());
+  cudaError_t e2 =
+      cudaFuncSetAttribute(k_mlp_train_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_train_smem());
+  return (e1 == cudaSuccess && e2 == cudaSuccess) ? 0 : -1;
+}
+void launch_mlp_infer(const float* feat, long long n, const MlpNorm& nm, const __nv_bfloat16* wb, const float* w,
+                      float* out, cudaStream_t s, int nsm) {
+  long long warps = (n + 31) / 32;
+  long long blocks = (warps + 3) / 4;
+  int grid = (int)(blocks < (long long)nsm * 8 ? blocks : (long long)nsm * 8);
+  if (grid < 1) grid = 1;
+  k_mlp_infer<<<grid, 128, mlp_infer_smem(), s>>>(feat, n, nm, wb, w, out);
+}
+void launch_mlp_train_step(const float* feat, const float* target, long long n, long long pa, long long pb,
+                           long long off, int batch, const MlpNorm& nm, const __nv_bfloat16* wb, const float* w,
+                           float* grad, float* loss, cudaStream_t s) {
+  int grid = (batch + 63) / 64;
+  k_mlp_train_step<<<grid, 64, mlp_train_smem(), s>>>(feat, target, n, pa, pb, off, batch, nm, wb, w, grad, loss);
+}
+void launch_mlp_adam(float* w, float* m, float* v, float* grad, float lr, int t, __nv_bfloat16* wb, cudaStream_t s) {
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.0f / (1.0f - powf(b1, (float)t)), c2 = 1.0f / (1.0f - powf(b2, (float)t));
+  k_mlp_adam<<<(MLP_NPARAM + 255) / 256, 256, 0, s>>>(w, m, v, grad, lr, b1, b2, 1e-8f, c1, c2, wb);
+  k_mlp_pack<<<(MLP_NBF + 255) / 256, 256, 0, s>>>(w, wb);
+}
+void launch_mlp_pack(const float* w, __nv_bfloat16* wb, cudaStream_t s) {
+  k_mlp_pack<<<(MLP_NBF + 255) / 256, 256, 0, s>>>(w, wb);
+}
+void launch_mlp_stats(const float* feat, const float* target, long long n, double* acc, cudaStream_t s, int nsm) {
+  k_mlp_stats<<<nsm * 4, 256, 0, s>>>(feat, target, n, acc);
+}
+void launch_krp_seed(const Par& P, const KrpBuf& kb, const float* logmu, int learned, float delta, cudaStream_t s,
+                     int grid) {
+  k_krp_seed<<<grid, 128, 0, s>>>(P, kb, logmu, learned, delta);
+}
+
+}  // namespace grmhd

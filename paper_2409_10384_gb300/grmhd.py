@@ -75,8 +75,19 @@ _SIGS = {
     "mhd_profile_read": (_I, [_VP, _VP, _VP]),
     "mhd_kernel_name": (C.c_char_p, [_I]),
     "mhd_stage_noalloc": (_I, [C.POINTER(mhd_params), C.POINTER(mhd_block), _D, _I, _VP]),
+    "mhd_mlp_init": (_I, [_VP, C.c_ulonglong]),
+    "mhd_mlp_dataset": (_I, [_VP, _L, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "mhd_mlp_train": (_I, [_VP, _VP, _VP, _L, _I, _I, C.c_float, C.c_ulonglong, C.POINTER(C.c_float), _VP]),
+    "mhd_mlp_calibrate": (_I, [_VP, _VP, _VP, _L, _D, C.POINTER(_D), _VP]),
+    "mhd_mlp_infer": (_I, [_VP, _VP, _L, _VP, _VP]),
+    "mhd_mlp_grad": (_I, [_VP, _VP, _VP, _L, _VP, C.POINTER(C.c_float), _VP]),
+    "mhd_mlp_get": (_I, [_VP, _VP]),
+    "mhd_mlp_set": (_I, [_VP, _VP]),
 }
-MHD_NKERNEL = 10
+MHD_NKERNEL = 11
+MLP_NPARAM = 4609
+MLP_NSTATE = 4609 + 13
+MLP_FSTRIDE = 8
 
 
 def header_symbols() -> list:
@@ -296,6 +307,55 @@ class Context:
         check(self.L.mhd_scratch_copy(self.h, int(b), int(which), host.ctypes.data_as(C.c_void_p), n.value, None,
                                       _sptr(stream)), "mhd_scratch_copy")
         return host if shape is None else host.reshape(shape)
+
+    # ----------------------------------------------------- learned guess
+    def mlp_init(self, seed=1):
+        check(self.L.mhd_mlp_init(self.h, int(seed)), "mhd_mlp_init")
+
+    def mlp_dataset(self, cons, Bd, g, stream=None):
+        """(features [n][8] float32, log(mu) [n] float32) device tensors."""
+        import torch
+        n = cons.shape[1]
+        feat = torch.zeros((n, MLP_FSTRIDE), dtype=torch.float32, device="cuda")
+        logmu = torch.zeros(n, dtype=torch.float32, device="cuda")
+        check(self.L.mhd_mlp_dataset(self.h, n, _ptr(cons), _ptr(Bd), _ptr(g), _ptr(feat), _ptr(logmu),
+                                     _sptr(stream)), "mhd_mlp_dataset")
+        return feat, logmu
+
+    def mlp_train(self, feat, logmu, epochs=20, batch=4096, lr=3e-3, seed=7, stream=None) -> float:
+        loss = C.c_float()
+        check(self.L.mhd_mlp_train(self.h, _ptr(feat), _ptr(logmu), feat.shape[0], int(epochs), int(batch),
+                                   float(lr), int(seed), C.byref(loss), _sptr(stream)), "mhd_mlp_train")
+        return float(loss.value)
+
+    def mlp_calibrate(self, feat, logmu, quantile=0.999, stream=None) -> float:
+        d = C.c_double()
+        check(self.L.mhd_mlp_calibrate(self.h, _ptr(feat), _ptr(logmu), feat.shape[0], float(quantile),
+                                       C.byref(d), _sptr(stream)), "mhd_mlp_calibrate")
+        return float(d.value)
+
+    def mlp_infer(self, feat, stream=None):
+        import torch
+        out = torch.zeros(feat.shape[0], dtype=torch.float32, device="cuda")
+        check(self.L.mhd_mlp_infer(self.h, _ptr(feat), feat.shape[0], _ptr(out), _sptr(stream)), "mhd_mlp_infer")
+        return out
+
+    def mlp_grad(self, feat, logmu, stream=None):
+        g = np.zeros(MLP_NPARAM, np.float32)
+        loss = C.c_float()
+        check(self.L.mhd_mlp_grad(self.h, _ptr(feat), _ptr(logmu), feat.shape[0], g.ctypes.data_as(C.c_void_p),
+                                  C.byref(loss), _sptr(stream)), "mhd_mlp_grad")
+        return g, float(loss.value)
+
+    def mlp_get(self) -> np.ndarray:
+        st = np.zeros(MLP_NSTATE, np.float32)
+        check(self.L.mhd_mlp_get(self.h, st.ctypes.data_as(C.c_void_p)), "mhd_mlp_get")
+        return st
+
+    def mlp_set(self, state):
+        st = np.ascontiguousarray(state, np.float32)
+        assert st.size == MLP_NSTATE
+        check(self.L.mhd_mlp_set(self.h, st.ctypes.data_as(C.c_void_p)), "mhd_mlp_set")
 
     def launches(self) -> int:
         return int(self.L.mhd_kernel_launches(self.h))
