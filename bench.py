@@ -136,6 +136,88 @@ def oracle_sample(max_seconds: float = 12.0, max_steps: int = 20, sub: int = 64)
                 sample=f"{steps} RK3 step(s) of a {sub}^3 sub-block of the 128^3 star, {el:.1f} s")
 
 
+# ------------------------------------------------------- con2prim stress leg
+
+C2P_PARAMS = dict(gamma=2.0, rho_atm=1e-20, T_atm=1e-14, f_thr=0.0, sigma_max=0.0, dmp_M=0.0, c2p_tol=1e-10,
+                  W_max=1e3, recon=2, rsolver=1, fofc=0, rk_order=3, c2p_maxit=64)
+
+
+def c2p_leg(G, n=1 << 24, reps=5):
+    """con2prim on n independent stress cells (rho, T, W, sigma log-uniform,
+    perturbed metric): the plain KRP solve, the learned guess (network trained
+    here on a disjoint seed) and the FP32 search without the network, at the
+    same 1e-10 bracket; cells/s and FP64 evaluations per cell."""
+    import torch
+    from paper_2409_10384_gb300 import synth
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    ctx = G.Context(G.params(**C2P_PARAMS, c2p_guess=0))
+    t0 = time.perf_counter()
+    pr, Bd, g = synth.c2p_stress(1 << 20, seed=104)
+    dB, dg, dp = t(Bd), t(g), t(pr)
+    dc = torch.zeros_like(dp)
+    ctx.prim2cons(dp, dB, dg, dc)
+    feat, logmu = ctx.mlp_dataset(dc, dB, dg)
+    ctx.mlp_init(3)
+    loss = ctx.mlp_train(feat, logmu, epochs=30, batch=4096, lr=3e-3)
+    pr, Bd, g = synth.c2p_stress(1 << 18, seed=105)
+    dB, dg, dp = t(Bd), t(g), t(pr)
+    dc = torch.zeros_like(dp)
+    ctx.prim2cons(dp, dB, dg, dc)
+    vf, vl = ctx.mlp_dataset(dc, dB, dg)
+    delta = ctx.mlp_calibrate(vf, vl, 0.95)
+    train_s = time.perf_counter() - t0
+    del feat, logmu, vf, vl
+    # the test set, built on the device chunk by chunk
+    cons0 = torch.empty((5, n), dtype=torch.float64, device="cuda")
+    tB = torch.empty((3, n), dtype=torch.float64, device="cuda")
+    tg = torch.empty((6, n), dtype=torch.float64, device="cuda")
+    ch = 1 << 22
+    for k in range(0, n, ch):
+        m = min(ch, n - k)
+        pr, Bd, g = synth.c2p_stress(m, seed=4 + 1000 * (k // ch))
+        cB, cg, cp = t(Bd), t(g), t(pr)
+        cc = torch.empty((5, m), dtype=torch.float64, device="cuda")
+        ctx.prim2cons(cp, cB, cg, cc)
+        cons0[:, k:k + m] = cc
+        tB[:, k:k + m] = cB
+        tg[:, k:k + m] = cg
+    del cp, cB, cg, cc
+    res = {}
+    prims = {}
+    stream = torch.cuda.current_stream()
+    for name, mode in (("plain", 0), ("fp32_search", 2), ("learned", 1)):
+        ctx.set_params(G.params(**C2P_PARAMS, c2p_guess=mode))
+        cons = cons0.clone()
+        prim = torch.empty((5, n), dtype=torch.float64, device="cuda")
+        fl = torch.empty(n, dtype=torch.uint8, device="cuda")
+        it = torch.empty(n, dtype=torch.int32, device="cuda")
+        ctx.c2p_cells(cons, tB, tg, prim, fl, it)   # warm-up
+        ms = []
+        for _ in range(reps):
+            cons.copy_(cons0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.c2p_cells(cons, tB, tg, prim, fl, it)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        res[name] = {"cells_per_s": n / (float(np.median(ms)) * 1e-3), "ms": float(np.median(ms)),
+                     "fp64_evals_per_cell": float(it.double().mean().item()),
+                     "fails": int(((fl & 1) != 0).sum().item())}
+        prims[name] = prim
+    p0 = prims["plain"]
+    W = torch.sqrt(1 + (p0[1:4] ** 2).sum(0))
+    for name in ("learned", "fp32_search"):
+        d = prims[name]
+        res[name]["max_rel_diff_rho_vs_plain"] = float(((d[0] - p0[0]).abs() / p0[0]).max().item())
+        res[name]["max_diff_w_over_W_vs_plain"] = float(((d[1:4] - p0[1:4]).abs() / W).max().item())
+    res["speedup_learned_vs_plain"] = res["learned"]["cells_per_s"] / res["plain"]["cells_per_s"]
+    res.update({"cells": n, "tol": 1e-10, "train": {"samples": 1 << 20, "epochs": 30, "loss": loss,
+                "delta_q95": delta, "seconds": train_s}, "data": "synthetic stress cells (seeded)"})
+    ctx.close()
+    return res
+
+
 def run_reference(args):
     rank = _env_int("RANK", 0)
     if rank != 0:
@@ -297,6 +379,8 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches), "roofline": roofline, "kernel_share": shares,
             "c2p_stats": stats, "clocks": clocks}
+    if not args.no_c2p:
+        line["c2p"] = c2p_leg(G)
     if rank == 0 and world == 1 and not args.no_baseline:
         line["cpu_baseline"] = oracle_sample()
     if rank == 0:
@@ -316,6 +400,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=128, help="interior cells per side (profiling cases only)")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU-oracle leg (profiling cases)")
+    ap.add_argument("--no-c2p", action="store_true", help="skip the con2prim stress leg (profiling cases)")
     args = ap.parse_args()
     global N_INT
     N_INT = args.n

@@ -61,9 +61,12 @@ __device__ __forceinline__ void frag_c_apply(const float* c, int m0, int n0, F&&
 }
 
 constexpr int NH = MLP_NH;
-// per-warp shared buffers (floats)
+// per-warp shared buffers (floats) of the training step
 constexpr int S_X = 0, S_H1 = 32 * 16, S_H2 = S_H1 + 32 * NH, S_DZ2 = S_H2 + 32 * NH, S_DZ1 = S_DZ2 + 32 * NH,
               S_Y = S_DZ1 + 32 * NH, S_T = S_Y + 32, S_WARP = S_T + 32;
+// inference: the second hidden layer overwrites the first (each 16-row tile of
+// the first is read into registers before its rows are overwritten)
+constexpr int I_X = 0, I_H = 32 * 16, I_Y = I_H + 32 * NH, I_WARP = I_Y + 32;
 
 // normalised features of the warp's 32 samples into Xs [32][16] (cols >= 5 zero)
 __device__ __forceinline__ void load_x(float* Xs, const float* feat, long long idx, bool valid, const MlpNorm& nm) {
@@ -76,12 +79,10 @@ __device__ __forceinline__ void load_x(float* Xs, const float* feat, long long i
   }
 }
 
-// forward of 32 samples: H1, H2 (fp32) and y (normalised output) in smem
-__device__ __forceinline__ void warp_forward(float* sw, const __nv_bfloat16* wb, const float* w) {
-  float* Xs = sw + S_X;
-  float* H1 = sw + S_H1;
-  float* H2 = sw + S_H2;
-  float* Y = sw + S_Y;
+// forward of 32 samples: H1, H2 (fp32) and y (normalised output) in smem;
+// H2 may alias H1
+__device__ __forceinline__ void warp_forward(const float* Xs, float* H1, float* H2, float* Y,
+                                             const __nv_bfloat16* wb, const float* w) {
   __syncwarp();
   // layer 1: [32 x 16] x W1p^T, W1p [64][16] bf16
   for (int mt = 0; mt < 2; mt++) {
@@ -100,6 +101,7 @@ __device__ __forceinline__ void warp_forward(float* sw, const __nv_bfloat16* wb,
   for (int mt = 0; mt < 2; mt++) {
     unsigned a[4][4];
     for (int kt = 0; kt < 4; kt++) frag_a(H1, NH, 1, 16 * mt, 16 * kt, a[kt]);
+    __syncwarp();
     for (int nt = 0; nt < NH / 8; nt++) {
       float c[4] = {0.f, 0.f, 0.f, 0.f};
       for (int kt = 0; kt < 4; kt++) {
@@ -131,7 +133,7 @@ __device__ __forceinline__ void warp_forward(float* sw, const __nv_bfloat16* wb,
 
 // ------------------------------------------------------------------ inference
 // out[i] = predicted log(mu) (de-normalised) for n samples
-__global__ void __launch_bounds__(128) k_mlp_infer(const float* __restrict__ feat, long long n, MlpNorm nm,
+__global__ void __launch_bounds__(256) k_mlp_infer(const float* __restrict__ feat, long long n, MlpNorm nm,
                                                   const __nv_bfloat16* __restrict__ wb, const float* __restrict__ w,
                                                   float* __restrict__ out) {
   extern __shared__ float smem[];
@@ -140,13 +142,13 @@ __global__ void __launch_bounds__(128) k_mlp_infer(const float* __restrict__ fea
   for (int i = threadIdx.x; i < MLP_NBF; i += blockDim.x) swb[i] = wb[i];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* sw = sw0 + warp * S_WARP;
+  float* sw = sw0 + warp * I_WARP;
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
   for (long long base = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * 32; base < n; base += nwarps * 32) {
     const long long idx = base + lane;
-    load_x(sw, feat, idx, idx < n, nm);
-    warp_forward(sw, swb, w);
-    if (idx < n) out[idx] = sw[S_Y + lane] * nm.ystd + nm.ymean;
+    load_x(sw + I_X, feat, idx, idx < n, nm);
+    warp_forward(sw + I_X, sw + I_H, sw + I_H, sw + I_Y, swb, w);
+    if (idx < n) out[idx] = sw[I_Y + lane] * nm.ystd + nm.ymean;
     __syncwarp();
   }
 }
@@ -184,7 +186,7 @@ __global__ void __launch_bounds__(64) k_mlp_train_step(const float* __restrict__
   }
   load_x(Xs, feat, idx, valid, nm);
   T[lane] = valid ? (target[idx] - nm.ymean) / nm.ystd : 0.0f;
-  warp_forward(sw, swb, w);
+  warp_forward(Xs, H1, H2, Y, swb, w);
   // dL/dy of the mean squared error over the batch
   const float r = valid ? Y[lane] - T[lane] : 0.0f;
   const float dy = 2.0f * r / (float)batch;
@@ -350,8 +352,8 @@ __device__ __forceinline__ float f32_mu_plus(const KSf& s) {
 }
 
 // Cells with status 4.  Starting pair: the network's guess mu_g and mu_g e^d
-// (learned = 1), or 0 and the FP32 mu+ (learned = 0).  Eight FP32 secant
-// steps give mu32; FP64 then evaluates f at mu32 and at mu32 (1 +- 4e-6)
+// (learned = 1), or 0 and the FP32 mu+ (learned = 0).  Five (learned) or
+// eight FP32 secant steps give mu32; FP64 then evaluates f at mu32 and at mu32 (1 +- 4e-6)
 // towards the root.  A sign change is a bracket of relative width 4e-6; else
 // the bracket extends from the far point to 0 (f(0) < 0, no evaluation) or
 // 1 (f(1) >= 0 for a physical state).  The refill solve finishes from there.
@@ -381,7 +383,8 @@ __global__ void __launch_bounds__(128) k_krp_seed(Par P, KrpBuf kb, const float*
       x1 = f32_mu_plus(sf);
     }
     float f0 = f32_master(sf, x0), f1 = f32_master(sf, x1);
-    for (int it = 0; it < 8; it++) {
+    const int nsteps = learned ? 5 : 8;
+    for (int it = 0; it < nsteps; it++) {
       const float den = f1 - f0;
       if (den == 0.0f || !(f1 == f1)) break;
       float x2 = x1 - f1 * (x1 - x0) / den;
@@ -447,7 +450,7 @@ __global__ void k_mlp_logmu(KrpBuf kb, float* out) {
 void launch_mlp_logmu(const KrpBuf& kb, float* out, cudaStream_t s, int nsm) {
   k_mlp_logmu<<<nsm * 4, 256, 0, s>>>(kb, out);
 }
-size_t mlp_infer_smem() { return sizeof(float) * ((MLP_NBF + 1) / 2 + 4 * S_WARP); }
+size_t mlp_infer_smem() { return sizeof(float) * ((MLP_NBF + 1) / 2 + 8 * I_WARP); }
 size_t mlp_train_smem() { return sizeof(float) * ((MLP_NBF + 1) / 2 + MLP_NPARAM + 2 * S_WARP); }
 
 int mlp_setup_attrs() {
@@ -459,10 +462,10 @@ int mlp_setup_attrs() {
 void launch_mlp_infer(const float* feat, long long n, const MlpNorm& nm, const __nv_bfloat16* wb, const float* w,
                       float* out, cudaStream_t s, int nsm) {
   long long warps = (n + 31) / 32;
-  long long blocks = (warps + 3) / 4;
-  int grid = (int)(blocks < (long long)nsm * 8 ? blocks : (long long)nsm * 8);
+  long long blocks = (warps + 7) / 8;
+  int grid = (int)(blocks < (long long)nsm * 2 ? blocks : (long long)nsm * 2);
   if (grid < 1) grid = 1;
-  k_mlp_infer<<<grid, 128, mlp_infer_smem(), s>>>(feat, n, nm, wb, w, out);
+  k_mlp_infer<<<grid, 256, mlp_infer_smem(), s>>>(feat, n, nm, wb, w, out);
 }
 void launch_mlp_train_step(const float* feat, const float* target, long long n, long long pa, long long pb,
                            long long off, int batch, const MlpNorm& nm, const __nv_bfloat16* wb, const float* w,
