@@ -218,6 +218,58 @@ def c2p_leg(G, n=1 << 24, reps=5):
     return res
 
 
+# --------------------------------------------------------- batched AMR leg
+
+def amr_leg(G, steps=2):
+    """512 blocks of 16^3/32^3/64^3 (4:2:1) on 6 levels sampling the star:
+    one launch sequence per block, one batched launch per kernel, the batched
+    launches as a CUDA graph, and the graph after the autotuner."""
+    import torch
+    from paper_2409_10384_gb300 import synth
+    specs = synth.amr_blocks(seed=3)
+    st = synth.spacetime(3)
+    ctx = G.Context(G.params(**PARAMS, c2p_guess=0))
+    blocks = []
+    t0 = time.perf_counter()
+    for sp in specs:
+        inp = synth.star_block(st, (sp.n,) * 3, NG, (sp.dx,) * 3, sp.x0)
+        db = G.DeviceBlock(inp.n, inp.ng, inp.dx, inp.adm)
+        db.prim.copy_(torch.from_numpy(inp.prim))
+        ctx.init_block(db, [torch.from_numpy(a).cuda() for a in inp.A])
+        blocks.append(db)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    zones = sum(sp.n ** 3 for sp in specs)
+    dt = CFL * min(sp.dx for sp in specs)
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    out = {"blocks": len(specs), "sizes": {str(n): sum(1 for sp in specs if sp.n == n) for n in (16, 32, 64)},
+           "zones": zones, "levels": 6, "generate_s": gen_s}
+
+    def run(name, **kw):
+        with torch.cuda.stream(stream):
+            ctx.step(blocks, dt, stream=stream, **kw)
+            l0 = ctx.launches()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                ctx.step(blocks, dt, stream=stream, **kw)
+            e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"zone_cycles_per_s": zones / (ms * 1e-3), "ms_per_step": ms,
+                     "launches_per_step": (ctx.launches() - l0) // steps}
+
+    run("per_block", per_block=True)
+    run("batched")
+    run("batched_graph", graph=True)
+    with torch.cuda.stream(stream):
+        out["autotune"] = ctx.autotune(blocks, dt, stream=stream)
+    run("tuned_graph", graph=True)
+    ctx.close()
+    return out
+
+
 def run_reference(args):
     rank = _env_int("RANK", 0)
     if rank != 0:
@@ -379,8 +431,10 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches), "roofline": roofline, "kernel_share": shares,
             "c2p_stats": stats, "clocks": clocks}
-    if not args.no_c2p:
+    if not args.no_c2p and world == 1:
         line["c2p"] = c2p_leg(G)
+    if not args.no_amr and world == 1:
+        line["amr512"] = amr_leg(G)
     if rank == 0 and world == 1 and not args.no_baseline:
         line["cpu_baseline"] = oracle_sample()
     if rank == 0:
@@ -401,6 +455,7 @@ def main():
     ap.add_argument("--n", type=int, default=128, help="interior cells per side (profiling cases only)")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU-oracle leg (profiling cases)")
     ap.add_argument("--no-c2p", action="store_true", help="skip the con2prim stress leg (profiling cases)")
+    ap.add_argument("--no-amr", action="store_true", help="skip the batched AMR leg (profiling cases)")
     args = ap.parse_args()
     global N_INT
     N_INT = args.n

@@ -132,10 +132,23 @@ int mhd_rhs(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, double dt, int s
 int mhd_rk_update(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, double dt, int stage, void* stream);
 
 /* A full RK step (rk_order stages of c2p, rhs, update).  Ghost zones are not
- * refreshed between stages (they keep their values).  With graph != 0 the
- * launches are captured once into a CUDA graph per (block list, dt) and
- * replayed. */
+ * refreshed between stages (they keep their values).  graph = 0: each kernel
+ * launched once per stage over all blocks; 1: the same launches captured once
+ * into a CUDA graph per (block list, dt, parameters, stream) and replayed (the
+ * stream must not be the legacy default stream); 2: one launch sequence per
+ * block (a reference for the batched launches; same results). */
 int mhd_step(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, double dt, int graph, void* stream);
+
+/* Autotuner for a block list: times each tunable kernel (the two con2prim
+ * phases, the three flux directions, the two FOFC-estimate phases, the EMF
+ * and the cell update) at CTA sizes 64/128/256 and 1/2/4 waves of resident
+ * CTAs on these blocks and keeps the fastest for later launches of this
+ * context.  It runs con2prim (which applies the floors to cons, as the first
+ * step of a stage does) and the right-hand side of stage 0; the state is
+ * otherwise unchanged.  cfg_out (host, may be NULL): [MHD_NTUNE][2] CTA size
+ * and waves.  Synchronises the stream. */
+#define MHD_NTUNE 9
+int mhd_autotune(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, double dt, void* stream, int* cfg_out);
 
 /* Copy the counters to *out (synchronises the stream) / zero them. */
 int mhd_read_stats(mhd_ctx* ctx, mhd_stats* out, void* stream);

@@ -10,6 +10,9 @@
 
 using namespace grmhd;
 
+// tunable kernels
+enum TKind { T_C2P_PREP = 0, T_C2P_FIN, T_FX, T_FY, T_FZ, T_FOFC_PREP, T_FOFC_FIN, T_EMF, T_UPD, T_N };
+
 struct mhd_ctx {
   mhd_params hp;
   Par P;
@@ -41,6 +44,12 @@ struct mhd_ctx {
   long long list_version = 0;
   int grid[W_NKIND] = {0};
   int g_kprep = 1, g_kfin = 1, g_fprep = 1, g_ffin = 1, g_solve = 1;
+  // launch configuration (CTA size, waves of resident CTAs) per tunable kernel
+  struct Cfg {
+    int threads = 128, waves = 1;
+  } cfg[T_N];
+  int occ_t[T_N][3] = {{0}};   // occupancy at 64, 128, 256 threads
+  long long* dpre_blk = nullptr;  // per-block work tables [nb][W_NKIND][2] (per-block launches)
   int g_solve_cells() const { return nsm * (occ_krp[1] > 0 ? occ_krp[1] : 1); }
   // counters
   unsigned long long* dstats = nullptr;
@@ -65,6 +74,17 @@ struct mhd_ctx {
 };
 
 namespace {
+
+int tkind_items(int k) {
+  switch (k) {
+    case T_C2P_PREP: case T_C2P_FIN: return W_C2P;
+    case T_FX: return W_FX;
+    case T_FY: return W_FY;
+    case T_FZ: return W_FZ;
+    case T_FOFC_PREP: case T_FOFC_FIN: case T_UPD: return W_CELL;
+    default: return W_EDGE;
+  }
+}
 
 int set_par(mhd_ctx* c, const mhd_params* p) {
   if (!p) return MHD_EINVAL;
@@ -201,8 +221,20 @@ int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
   c->krp_n = nkrp;
   if (c->dblk) cudaFree(c->dblk);
   if (c->dpre) cudaFree(c->dpre);
+  if (c->dpre_blk) cudaFree(c->dpre_blk);
   c->dblk = nullptr;
   c->dpre = nullptr;
+  c->dpre_blk = nullptr;
+  {
+    std::vector<long long> pb((size_t)nb * W_NKIND * 2, 0);
+    for (int i = 0; i < nb; i++)
+      for (int k = 0; k < W_NKIND; k++)
+        pb[((size_t)i * W_NKIND + k) * 2 + 1] = pre[(size_t)k * (nb + 1) + i + 1] - pre[(size_t)k * (nb + 1) + i];
+    // Work::pre for one block is indexed [kind * 2 + {0,1}]
+    if (cudaMalloc(&c->dpre_blk, sizeof(long long) * pb.size()) != cudaSuccess) return MHD_ENOMEM;
+    if (cudaMemcpy(c->dpre_blk, pb.data(), sizeof(long long) * pb.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return MHD_ECUDA;
+  }
   if (cudaMalloc(&c->dblk, sizeof(DevBlock) * nb) != cudaSuccess) return MHD_ENOMEM;
   if (cudaMalloc(&c->dpre, sizeof(long long) * pre.size()) != cudaSuccess) return MHD_ENOMEM;
   if (cudaMemcpy(c->dblk, hb.data(), sizeof(DevBlock) * nb, cudaMemcpyHostToDevice) != cudaSuccess) return MHD_ECUDA;
@@ -272,6 +304,17 @@ void timed(mhd_ctx* c, int kind, cudaStream_t s, F&& launch) {
   }
 }
 
+int tidx(int threads) { return threads == 64 ? 0 : (threads == 128 ? 1 : 2); }
+
+// grid of a tunable kernel over `items` work items with its configuration
+int tgrid(const mhd_ctx* c, int k, long long items) {
+  const int th = c->cfg[k].threads;
+  long long g = (items + th - 1) / th;
+  long long cap = (long long)c->nsm * std::max(c->occ_t[k][tidx(th)], 1) * c->cfg[k].waves;
+  if (g > cap) g = cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
 Work work_of(const mhd_ctx* c) {
   Work w;
   w.blk = c->dblk;
@@ -280,46 +323,112 @@ Work work_of(const mhd_ctx* c) {
   return w;
 }
 
-int enqueue_c2p(mhd_ctx* c, cudaStream_t s) {
-  Work w = work_of(c);
-  const long long n = c->hpre[(size_t)W_C2P * (c->key.size() + 1) + c->key.size()];
-  KrpBuf kb = krp_view(c->krp, n);
-  timed(c, MHD_K_C2P, s, [&] { launch_krp_prep_block(w, c->P, kb, s, c->g_kprep); });
+// One launch sequence over the work `w` with `items[W_NKIND]` items per kind
+// (all blocks of the list, or one block for per-block launches).
+int enqueue_c2p(mhd_ctx* c, cudaStream_t s, const Work& w, const long long* items) {
+  KrpBuf kb = krp_view(c->krp, items[W_C2P]);
+  const mhd_ctx::Cfg& cp = c->cfg[T_C2P_PREP];
+  const mhd_ctx::Cfg& cf = c->cfg[T_C2P_FIN];
+  timed(c, MHD_K_C2P, s, [&] {
+    launch_krp_prep_block(w, c->P, kb, s, tgrid(c, T_C2P_PREP, items[W_C2P]), cp.threads);
+  });
   timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, c->dstats, s, c->g_solve); });
-  timed(c, MHD_K_C2P, s, [&] { launch_krp_finish_block(w, c->P, kb, c->dstats, s, c->g_kfin); });
+  timed(c, MHD_K_C2P, s, [&] {
+    launch_krp_finish_block(w, c->P, kb, c->dstats, s, tgrid(c, T_C2P_FIN, items[W_C2P]), cf.threads);
+  });
   return cuda_ok(cudaGetLastError());
 }
 
-int enqueue_rhs(mhd_ctx* c, double dt, int stage, cudaStream_t s) {
+int enqueue_rhs(mhd_ctx* c, double dt, int stage, cudaStream_t s, const Work& w, const long long* items) {
   double g0, g1, be;
   rk_weights(c->P.rk_order, stage, g0, g1, be);
-  Work w = work_of(c);
-  const int gf[3] = {c->grid[W_FX], c->grid[W_FY], c->grid[W_FZ]};
   for (int d = 0; d < 3; d++)
-    timed(c, MHD_K_FLUX_X + d, s, [&] { launch_flux_dir(d, w, c->P, s, gf[d]); });
+    timed(c, MHD_K_FLUX_X + d, s, [&] {
+      launch_flux_dir(d, w, c->P, s, tgrid(c, T_FX + d, items[W_FX + d]), c->cfg[T_FX + d].threads);
+    });
   if (c->P.fofc) {
-    const long long n = c->hpre[(size_t)W_CELL * (c->key.size() + 1) + c->key.size()];
-    KrpBuf kb = krp_view(c->krp, n);
-    timed(c, MHD_K_FOFC_FLAG, s, [&] { launch_krp_prep_fofc(w, c->P, g0, g1, be * dt, kb, s, c->g_fprep); });
+    KrpBuf kb = krp_view(c->krp, items[W_CELL]);
+    timed(c, MHD_K_FOFC_FLAG, s, [&] {
+      launch_krp_prep_fofc(w, c->P, g0, g1, be * dt, kb, s, tgrid(c, T_FOFC_PREP, items[W_CELL]),
+                           c->cfg[T_FOFC_PREP].threads);
+    });
     timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, c->dstats, s, c->g_solve); });
-    timed(c, MHD_K_FOFC_FLAG, s, [&] { launch_krp_finish_fofc(w, c->P, kb, c->dstats, s, c->g_ffin); });
-    for (int d = 0; d < 3; d++)
-      timed(c, MHD_K_FOFC_FIX, s, [&] { launch_fofc_fix(d, w, c->P, c->dstats, s, gf[d]); });
+    timed(c, MHD_K_FOFC_FLAG, s, [&] {
+      launch_krp_finish_fofc(w, c->P, kb, c->dstats, s, tgrid(c, T_FOFC_FIN, items[W_CELL]),
+                             c->cfg[T_FOFC_FIN].threads);
+    });
+    for (int d = 0; d < 3; d++) {
+      long long g = std::min<long long>((items[W_FX + d] + 127) / 128, (long long)c->nsm * c->occ_face[4]);
+      timed(c, MHD_K_FOFC_FIX, s, [&] { launch_fofc_fix(d, w, c->P, c->dstats, s, (int)std::max(1LL, g)); });
+    }
   }
-  timed(c, MHD_K_EMF, s, [&] { launch_emf(w, s, c->grid[W_EDGE]); });
+  timed(c, MHD_K_EMF, s, [&] {
+    launch_emf(w, s, tgrid(c, T_EMF, items[W_EDGE]), c->cfg[T_EMF].threads);
+  });
   c->rhs_list = c->list_version;
   c->rhs_stage = stage;
   return cuda_ok(cudaGetLastError());
 }
 
-int enqueue_update(mhd_ctx* c, double dt, int stage, cudaStream_t s) {
+int enqueue_update(mhd_ctx* c, double dt, int stage, cudaStream_t s, const Work& w, const long long* items) {
   double g0, g1, be;
   rk_weights(c->P.rk_order, stage, g0, g1, be);
-  Work w = work_of(c);
   const int first = stage == 0 ? 1 : 0;
-  timed(c, MHD_K_UPDATE, s, [&] { launch_update_cells(w, c->P, g0, g1, be * dt, first, s, c->grid[W_INIT]); });
-  timed(c, MHD_K_FACEB, s, [&] { launch_update_faces(w, g0, g1, be * dt, first, s, c->grid[W_FACE]); });
+  timed(c, MHD_K_UPDATE, s, [&] {
+    launch_update_cells(w, c->P, g0, g1, be * dt, first, s, tgrid(c, T_UPD, items[W_CELL]), c->cfg[T_UPD].threads);
+  });
+  long long gfa = std::min<long long>((items[W_FACE] + 255) / 256, (long long)c->nsm * std::max(c->occ_upd[2], 1));
+  timed(c, MHD_K_FACEB, s, [&] { launch_update_faces(w, g0, g1, be * dt, first, s, (int)std::max(1LL, gfa)); });
   return cuda_ok(cudaGetLastError());
+}
+
+// totals over the block list
+void list_items(const mhd_ctx* c, long long* items) {
+  const size_t nb = c->key.size();
+  for (int k = 0; k < W_NKIND; k++) items[k] = c->hpre[(size_t)k * (nb + 1) + nb];
+}
+// one block of the list
+void block_items(const mhd_ctx* c, int b, long long* items) {
+  const size_t nb = c->key.size();
+  for (int k = 0; k < W_NKIND; k++) items[k] = c->hpre[(size_t)k * (nb + 1) + b + 1] - c->hpre[(size_t)k * (nb + 1) + b];
+}
+Work block_work(const mhd_ctx* c, int b) {
+  Work w;
+  w.blk = c->dblk + b;
+  w.pre = c->dpre_blk + (size_t)b * W_NKIND * 2;
+  w.nblocks = 1;
+  return w;
+}
+
+int enqueue_c2p(mhd_ctx* c, cudaStream_t s) {
+  long long it[W_NKIND];
+  list_items(c, it);
+  return enqueue_c2p(c, s, work_of(c), it);
+}
+int enqueue_rhs(mhd_ctx* c, double dt, int stage, cudaStream_t s) {
+  long long it[W_NKIND];
+  list_items(c, it);
+  return enqueue_rhs(c, dt, stage, s, work_of(c), it);
+}
+int enqueue_update(mhd_ctx* c, double dt, int stage, cudaStream_t s) {
+  long long it[W_NKIND];
+  list_items(c, it);
+  return enqueue_update(c, dt, stage, s, work_of(c), it);
+}
+
+// every block on its own: one launch sequence per block and stage
+int enqueue_step_per_block(mhd_ctx* c, double dt, cudaStream_t s) {
+  for (int st = 0; st < c->P.rk_order; st++)
+    for (int b = 0; b < (int)c->key.size(); b++) {
+      long long it[W_NKIND];
+      block_items(c, b, it);
+      Work w = block_work(c, b);
+      int r = enqueue_c2p(c, s, w, it);
+      if (!r) r = enqueue_rhs(c, dt, st, s, w, it);
+      if (!r) r = enqueue_update(c, dt, st, s, w, it);
+      if (r) return r;
+    }
+  return MHD_OK;
 }
 
 int enqueue_step(mhd_ctx* c, double dt, cudaStream_t s) {
@@ -352,6 +461,16 @@ int mhd_init(const mhd_params* p, mhd_ctx** out) {
     delete c;
     return MHD_ECUDA;
   }
+  for (int ti = 0; ti < 3; ti++) {
+    const int th = 64 << ti;
+    c->occ_t[T_C2P_PREP][ti] = occ_krp_kernel(0, th);
+    c->occ_t[T_C2P_FIN][ti] = occ_krp_kernel(1, th);
+    c->occ_t[T_FOFC_PREP][ti] = occ_krp_kernel(2, th);
+    c->occ_t[T_FOFC_FIN][ti] = occ_krp_kernel(3, th);
+    for (int d = 0; d < 3; d++) c->occ_t[T_FX + d][ti] = occ_face_kernel(d, th);
+    c->occ_t[T_EMF][ti] = occ_update_kernel(0, th);
+    c->occ_t[T_UPD][ti] = occ_update_kernel(1, th);
+  }
   if (cudaMalloc(&c->dstats, sizeof(unsigned long long) * 8) != cudaSuccess) {
     delete c;
     return MHD_ENOMEM;
@@ -379,6 +498,7 @@ void mhd_finalize(mhd_ctx* c) {
   if (c->scratch) cudaFree(c->scratch);
   if (c->dblk) cudaFree(c->dblk);
   if (c->dpre) cudaFree(c->dpre);
+  if (c->dpre_blk) cudaFree(c->dpre_blk);
   if (c->dstats) cudaFree(c->dstats);
   if (c->cells_buf) cudaFree(c->cells_buf);
   if (c->mlp) cudaFree(c->mlp);
@@ -729,6 +849,7 @@ int mhd_step(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, int graph, 
   int r = prepare(c, blocks, nb);
   if (r) return r;
   cudaStream_t s = (cudaStream_t)stream;
+  if (graph == 2) return enqueue_step_per_block(c, dt, s);
   if (!graph) return enqueue_step(c, dt, s);
   if (!s) return MHD_EINVAL;  // the legacy default stream cannot be captured
   if (!(c->gexec && c->g_list == c->list_version && c->g_par == c->par_version && c->g_dt == dt && c->g_stream == s)) {
@@ -794,6 +915,83 @@ int mhd_scratch_copy(mhd_ctx* c, int b, int which, double* dst, long count, long
 }
 
 long long mhd_kernel_launches(const mhd_ctx* c) { return c ? c->launches : 0; }
+
+int mhd_autotune(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, void* stream, int* cfg_out) {
+  if (!c || !(dt > 0.0)) return MHD_EINVAL;
+  int r = prepare(c, blocks, nb);
+  if (r) return r;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool prof = c->prof;
+  c->prof = false;
+  // valid inputs for every kernel: con2prim and the right-hand side of stage 0
+  r = enqueue_c2p(c, s);
+  if (!r) r = enqueue_rhs(c, dt, 0, s);
+  if (r) { c->prof = prof; return r; }
+  long long it[W_NKIND];
+  list_items(c, it);
+  Work w = work_of(c);
+  double g0, g1, be;
+  rk_weights(c->P.rk_order, 0, g0, g1, be);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  // kernel kinds in an order that keeps the scratch valid: a prep phase is
+  // followed by its root solve before the finish phase is timed; the update is
+  // timed with weights (g0, g1, b dt) = (0, 1, 0), which leaves U unchanged.
+  const int order[T_N] = {T_C2P_PREP, T_C2P_FIN, T_FX, T_FY, T_FZ, T_FOFC_PREP, T_FOFC_FIN, T_EMF, T_UPD};
+  for (int oi = 0; oi < T_N; oi++) {
+    const int k = order[oi];
+    if ((k == T_FOFC_PREP || k == T_FOFC_FIN) && !c->P.fofc) continue;
+    const bool fofc_k = k == T_FOFC_PREP || k == T_FOFC_FIN;
+    KrpBuf kb = krp_view(c->krp, fofc_k ? it[W_CELL] : it[W_C2P]);
+    auto launch = [&]() {
+      const int th = c->cfg[k].threads;
+      switch (k) {
+        case T_C2P_PREP: launch_krp_prep_block(w, c->P, kb, s, tgrid(c, k, it[W_C2P]), th); break;
+        case T_C2P_FIN: launch_krp_finish_block(w, c->P, kb, c->dstats, s, tgrid(c, k, it[W_C2P]), th); break;
+        case T_FX: case T_FY: case T_FZ:
+          launch_flux_dir(k - T_FX, w, c->P, s, tgrid(c, k, it[W_FX + k - T_FX]), th);
+          break;
+        case T_FOFC_PREP:
+          launch_krp_prep_fofc(w, c->P, g0, g1, be * dt, kb, s, tgrid(c, k, it[W_CELL]), th);
+          break;
+        case T_FOFC_FIN: launch_krp_finish_fofc(w, c->P, kb, c->dstats, s, tgrid(c, k, it[W_CELL]), th); break;
+        case T_EMF: launch_emf(w, s, tgrid(c, k, it[W_EDGE]), th); break;
+        default: launch_update_cells(w, c->P, 0.0, 1.0, 0.0, 0, s, tgrid(c, k, it[W_CELL]), th); break;
+      }
+    };
+    mhd_ctx::Cfg best = c->cfg[k];
+    float best_ms = 1e30f;
+    for (int th = 64; th <= 256; th *= 2)
+      for (int wv = 1; wv <= 4; wv *= 2) {
+        c->cfg[k].threads = th;
+        c->cfg[k].waves = wv;
+        launch();
+        cudaEventRecord(e0, s);
+        for (int rep = 0; rep < 3; rep++) launch();
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return MHD_ECUDA; }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) { best_ms = ms; best = c->cfg[k]; }
+      }
+    c->cfg[k] = best;
+    if (k == T_C2P_PREP || k == T_FOFC_PREP) {
+      launch();
+      launch_krp_solve(c->P, kb, c->dstats, s, c->g_solve);
+    }
+    if (cfg_out) {
+      cfg_out[2 * k] = best.threads;
+      cfg_out[2 * k + 1] = best.waves;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->prof = prof;
+  c->rhs_list = -1;
+  destroy_graph(c);
+  return cuda_ok(cudaStreamSynchronize(s));
+}
 
 int mhd_profile(mhd_ctx* c, int enable) {
   if (!c) return MHD_EINVAL;

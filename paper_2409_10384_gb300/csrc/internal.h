@@ -12,24 +12,24 @@ void launch_c2p_cells(const Par& P, long long n, double* cons, const double* Bd,
                       unsigned char* flags, int* iters, const float* guess, unsigned long long* stats, cudaStream_t s,
                       int grid);
 void launch_c2p_block(const Work& w, const Par& P, unsigned long long* stats, cudaStream_t s, int grid);
-void launch_flux_dir(int d, const Work& w, const Par& P, cudaStream_t s, int grid);
+void launch_flux_dir(int d, const Work& w, const Par& P, cudaStream_t s, int grid, int threads = 128);
 void launch_fofc_flag(const Work& w, const Par& P, double g0, double g1, double bdt, unsigned long long* stats,
                       cudaStream_t s, int grid);
 void launch_fofc_fix(int d, const Work& w, const Par& P, unsigned long long* stats, cudaStream_t s, int grid);
-void launch_emf(const Work& w, cudaStream_t s, int grid);
+void launch_emf(const Work& w, cudaStream_t s, int grid, int threads = 128);
 void launch_update_cells(const Work& w, const Par& P, double g0, double g1, double bdt, int first, cudaStream_t s,
-                         int grid);
+                         int grid, int threads = 128);
 void launch_update_faces(const Work& w, double g0, double g1, double bdt, int first, cudaStream_t s, int grid);
 size_t krp_bytes(long long n);
 KrpBuf krp_view(void* base, long long n);
-void launch_krp_prep_block(const Work& w, const Par& P, const KrpBuf& kb, cudaStream_t s, int grid);
+void launch_krp_prep_block(const Work& w, const Par& P, const KrpBuf& kb, cudaStream_t s, int grid, int threads = 128);
 void launch_krp_solve(const Par& P, const KrpBuf& kb, unsigned long long* stats, cudaStream_t s, int grid);
 void launch_krp_finish_block(const Work& w, const Par& P, const KrpBuf& kb, unsigned long long* stats,
-                             cudaStream_t s, int grid);
+                             cudaStream_t s, int grid, int threads = 128);
 void launch_krp_prep_fofc(const Work& w, const Par& P, double g0, double g1, double bdt, const KrpBuf& kb,
-                          cudaStream_t s, int grid);
+                          cudaStream_t s, int grid, int threads = 128);
 void launch_krp_finish_fofc(const Work& w, const Par& P, const KrpBuf& kb, unsigned long long* stats,
-                            cudaStream_t s, int grid);
+                            cudaStream_t s, int grid, int threads = 128);
 void launch_krp_prep_cells(const Par& P, const KrpBuf& kb, const double* cons, const double* Bd, const double* g,
                            int learned, float* feat, cudaStream_t s, int grid);
 void launch_krp_finish_cells(const Par& P, const KrpBuf& kb, double* cons, const double* Bd, const double* g,
@@ -49,6 +49,9 @@ void launch_mlp_stats(const float* feat, const float* target, long long n, doubl
 void launch_krp_seed(const Par& P, const KrpBuf& kb, const float* logmu, int learned, float delta, cudaStream_t s,
                      int grid);
 int occupancy_c2p(int* per_sm);
+int occ_face_kernel(int kind, int threads);
+int occ_krp_kernel(int kind, int threads);
+int occ_update_kernel(int kind, int threads);
 int occupancy_face(int* per_sm);
 int occupancy_update(int* per_sm);
 }  // namespace grmhd

@@ -69,7 +69,7 @@ __device__ __forceinline__ void face_flux(const DevBlock& b, const Par& P, int k
 }
 
 template <int d>
-__global__ void __launch_bounds__(128) k_flux(Work w, Par P) {
+__global__ void __launch_bounds__(256) k_flux(Work w, Par P) {
   const long long* pre = w.pre + (long long)(W_FX + d) * (w.nblocks + 1);
   const long long tot = pre[w.nblocks];
   for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < tot; it += (long long)gridDim.x * blockDim.x) {
@@ -185,10 +185,10 @@ __global__ void __launch_bounds__(128) k_fofc_fix(Work w, Par P, unsigned long l
   warp_flush(&stats[6], s_faces);
 }
 
-void launch_flux_dir(int d, const Work& w, const Par& P, cudaStream_t s, int grid) {
-  if (d == 0) k_flux<0><<<grid, 128, 0, s>>>(w, P);
-  else if (d == 1) k_flux<1><<<grid, 128, 0, s>>>(w, P);
-  else k_flux<2><<<grid, 128, 0, s>>>(w, P);
+void launch_flux_dir(int d, const Work& w, const Par& P, cudaStream_t s, int grid, int threads) {
+  if (d == 0) k_flux<0><<<grid, threads, 0, s>>>(w, P);
+  else if (d == 1) k_flux<1><<<grid, threads, 0, s>>>(w, P);
+  else k_flux<2><<<grid, threads, 0, s>>>(w, P);
 }
 void launch_fofc_flag(const Work& w, const Par& P, double g0, double g1, double bdt, unsigned long long* stats,
                       cudaStream_t s, int grid) {
@@ -198,6 +198,13 @@ void launch_fofc_fix(int d, const Work& w, const Par& P, unsigned long long* sta
   if (d == 0) k_fofc_fix<0><<<grid, 128, 0, s>>>(w, P, stats);
   else if (d == 1) k_fofc_fix<1><<<grid, 128, 0, s>>>(w, P, stats);
   else k_fofc_fix<2><<<grid, 128, 0, s>>>(w, P, stats);
+}
+int occ_face_kernel(int kind, int threads) {
+  int o = 0;
+  if (kind == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_flux<0>, threads, 0);
+  else if (kind == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_flux<1>, threads, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_flux<2>, threads, 0);
+  return o;
 }
 int occupancy_face(int* per_sm) {
   cudaError_t e = cudaSuccess;

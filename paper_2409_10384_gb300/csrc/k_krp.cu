@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(256) k_krp_solve(Par P, KrpBuf kb, unsigned lo
 }
 
 // -------------------------------------------------------- block stage con2prim
-__global__ void __launch_bounds__(128) k_krp_prep_block(Work w, Par P, KrpBuf kb) {
+__global__ void __launch_bounds__(256) k_krp_prep_block(Work w, Par P, KrpBuf kb) {
   const long long* pre = w.pre + (long long)W_C2P * (w.nblocks + 1);
   const long long tot = pre[w.nblocks];
   if (blockIdx.x == 0 && threadIdx.x == 0) *kb.ctr = 0ull;
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(128) k_krp_prep_block(Work w, Par P, KrpBuf kb
   }
 }
 
-__global__ void __launch_bounds__(128) k_krp_finish_block(Work w, Par P, KrpBuf kb, unsigned long long* stats) {
+__global__ void __launch_bounds__(256) k_krp_finish_block(Work w, Par P, KrpBuf kb, unsigned long long* stats) {
   const long long* pre = w.pre + (long long)W_C2P * (w.nblocks + 1);
   const long long tot = pre[w.nblocks];
   const long long n = kb.n;
@@ -248,7 +248,7 @@ __device__ __forceinline__ void fofc_cell(const Work& w, long long it, int& bi, 
   i += b.ng; j += b.ng; k += b.ng;
 }
 
-__global__ void __launch_bounds__(128) k_krp_prep_fofc(Work w, Par P, double g0, double g1, double bdt, KrpBuf kb) {
+__global__ void __launch_bounds__(256) k_krp_prep_fofc(Work w, Par P, double g0, double g1, double bdt, KrpBuf kb) {
   const long long tot = w.pre[(long long)W_CELL * (w.nblocks + 1) + w.nblocks];
   if (blockIdx.x == 0 && threadIdx.x == 0) *kb.ctr = 0ull;
   const long long n = kb.n;
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(128) k_krp_prep_fofc(Work w, Par P, double g0,
   }
 }
 
-__global__ void __launch_bounds__(128) k_krp_finish_fofc(Work w, Par P, KrpBuf kb, unsigned long long* stats) {
+__global__ void __launch_bounds__(256) k_krp_finish_fofc(Work w, Par P, KrpBuf kb, unsigned long long* stats) {
   const long long tot = w.pre[(long long)W_CELL * (w.nblocks + 1) + w.nblocks];
   const long long n = kb.n;
   unsigned s_flag = 0, s_dmp = 0;
@@ -400,23 +400,23 @@ KrpBuf krp_view(void* base, long long n) {
   return kb;
 }
 
-void launch_krp_prep_block(const Work& w, const Par& P, const KrpBuf& kb, cudaStream_t s, int grid) {
-  k_krp_prep_block<<<grid, 128, 0, s>>>(w, P, kb);
+void launch_krp_prep_block(const Work& w, const Par& P, const KrpBuf& kb, cudaStream_t s, int grid, int threads) {
+  k_krp_prep_block<<<grid, threads, 0, s>>>(w, P, kb);
 }
 void launch_krp_solve(const Par& P, const KrpBuf& kb, unsigned long long* stats, cudaStream_t s, int grid) {
   k_krp_solve<<<grid, 256, 0, s>>>(P, kb, stats);
 }
 void launch_krp_finish_block(const Work& w, const Par& P, const KrpBuf& kb, unsigned long long* stats,
-                             cudaStream_t s, int grid) {
-  k_krp_finish_block<<<grid, 128, 0, s>>>(w, P, kb, stats);
+                             cudaStream_t s, int grid, int threads) {
+  k_krp_finish_block<<<grid, threads, 0, s>>>(w, P, kb, stats);
 }
 void launch_krp_prep_fofc(const Work& w, const Par& P, double g0, double g1, double bdt, const KrpBuf& kb,
-                          cudaStream_t s, int grid) {
-  k_krp_prep_fofc<<<grid, 128, 0, s>>>(w, P, g0, g1, bdt, kb);
+                          cudaStream_t s, int grid, int threads) {
+  k_krp_prep_fofc<<<grid, threads, 0, s>>>(w, P, g0, g1, bdt, kb);
 }
 void launch_krp_finish_fofc(const Work& w, const Par& P, const KrpBuf& kb, unsigned long long* stats,
-                            cudaStream_t s, int grid) {
-  k_krp_finish_fofc<<<grid, 128, 0, s>>>(w, P, kb, stats);
+                            cudaStream_t s, int grid, int threads) {
+  k_krp_finish_fofc<<<grid, threads, 0, s>>>(w, P, kb, stats);
 }
 void launch_krp_prep_cells(const Par& P, const KrpBuf& kb, const double* cons, const double* Bd, const double* g,
                            int learned, float* feat, cudaStream_t s, int grid) {
@@ -426,6 +426,14 @@ void launch_krp_finish_cells(const Par& P, const KrpBuf& kb, double* cons, const
                              double* prim, unsigned char* flags, int* iters, unsigned long long* stats, cudaStream_t s,
                              int grid) {
   k_krp_finish_cells<<<grid, 128, 0, s>>>(P, kb, cons, Bd, g, prim, flags, iters, stats);
+}
+int occ_krp_kernel(int kind, int threads) {
+  int o = 0;
+  if (kind == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_krp_prep_block, threads, 0);
+  else if (kind == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_krp_finish_block, threads, 0);
+  else if (kind == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_krp_prep_fofc, threads, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_krp_finish_fofc, threads, 0);
+  return o;
 }
 int occupancy_krp(int* per_sm) {
   cudaError_t e = cudaSuccess;

@@ -46,7 +46,7 @@ __device__ __forceinline__ double edge_emf(const DevBlock& b, int k, int j, int 
   return 0.25 * ((Eaf_B + Eaf_Bm) + (Ebf_A + Ebf_Am) + (dEb_tq - dEb_q) + (dEa_tq - dEa_q));
 }
 
-__global__ void __launch_bounds__(128) k_emf(Work w) {
+__global__ void __launch_bounds__(256) k_emf(Work w) {
   const long long* pre = w.pre + (long long)W_EDGE * (w.nblocks + 1);
   const long long tot = pre[w.nblocks];
   for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < tot; it += (long long)gridDim.x * blockDim.x) {
@@ -129,7 +129,7 @@ __device__ __forceinline__ void sources(const DevBlock& b, const Par& P, int k, 
   G[4] = fma(alpha, kt, -dot3(Su, dal));
 }
 
-__global__ void __launch_bounds__(128) k_update_cells(Work w, Par P, double g0, double g1, double bdt, int first) {
+__global__ void __launch_bounds__(256) k_update_cells(Work w, Par P, double g0, double g1, double bdt, int first) {
   const long long* pre = w.pre + (long long)W_CELL * (w.nblocks + 1);
   const long long tot = pre[w.nblocks];
   for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < tot; it += (long long)gridDim.x * blockDim.x) {
@@ -198,13 +198,19 @@ __global__ void __launch_bounds__(256) k_update_faces(Work w, double g0, double 
   }
 }
 
-void launch_emf(const Work& w, cudaStream_t s, int grid) { k_emf<<<grid, 128, 0, s>>>(w); }
+void launch_emf(const Work& w, cudaStream_t s, int grid, int threads) { k_emf<<<grid, threads, 0, s>>>(w); }
 void launch_update_cells(const Work& w, const Par& P, double g0, double g1, double bdt, int first, cudaStream_t s,
-                         int grid) {
-  k_update_cells<<<grid, 128, 0, s>>>(w, P, g0, g1, bdt, first);
+                         int grid, int threads) {
+  k_update_cells<<<grid, threads, 0, s>>>(w, P, g0, g1, bdt, first);
 }
 void launch_update_faces(const Work& w, double g0, double g1, double bdt, int first, cudaStream_t s, int grid) {
   k_update_faces<<<grid, 256, 0, s>>>(w, g0, g1, bdt, first);
+}
+int occ_update_kernel(int kind, int threads) {
+  int o = 0;
+  if (kind == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_emf, threads, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_update_cells, threads, 0);
+  return o;
 }
 int occupancy_update(int* per_sm) {
   cudaError_t e = cudaSuccess;

@@ -75,6 +75,7 @@ _SIGS = {
     "mhd_profile_read": (_I, [_VP, _VP, _VP]),
     "mhd_kernel_name": (C.c_char_p, [_I]),
     "mhd_stage_noalloc": (_I, [C.POINTER(mhd_params), C.POINTER(mhd_block), _D, _I, _VP]),
+    "mhd_autotune": (_I, [_VP, C.POINTER(mhd_block), _I, _D, _VP, _VP]),
     "mhd_mlp_init": (_I, [_VP, C.c_ulonglong]),
     "mhd_mlp_dataset": (_I, [_VP, _L, _VP, _VP, _VP, _VP, _VP, _VP]),
     "mhd_mlp_train": (_I, [_VP, _VP, _VP, _L, _I, _I, C.c_float, C.c_ulonglong, C.POINTER(C.c_float), _VP]),
@@ -269,9 +270,10 @@ class Context:
         self.rhs(blocks, dt, stage, stream)
         self.rk_update(blocks, dt, stage, stream)
 
-    def step(self, blocks, dt, graph=False, stream=None):
+    def step(self, blocks, dt, graph=False, stream=None, per_block=False):
         arr, nb = self._blocks(blocks)
-        check(self.L.mhd_step(self.h, arr, nb, float(dt), int(bool(graph)), _sptr(stream)), "mhd_step")
+        mode = 2 if per_block else int(bool(graph))
+        check(self.L.mhd_step(self.h, arr, nb, float(dt), mode, _sptr(stream)), "mhd_step")
 
     def step_host(self, blk: DeviceBlock, host: dict, dt, stream=None, graph=False):
         """One RK step of a block whose state lives in (pinned) host memory:
@@ -289,6 +291,14 @@ class Context:
             host["cons"].copy_(blk.cons, non_blocking=True)
             for d in range(3):
                 host["bf"][d].copy_(blk.bf[d], non_blocking=True)
+
+    def autotune(self, blocks, dt, stream=None) -> dict:
+        """Tune the launch configuration of this block list; {kernel: (CTA size, waves)}."""
+        arr, nb = self._blocks(blocks)
+        out = (C.c_int * 18)()
+        check(self.L.mhd_autotune(self.h, arr, nb, float(dt), _sptr(stream), out), "mhd_autotune")
+        names = ("c2p_prep", "c2p_finish", "flux_x", "flux_y", "flux_z", "fofc_prep", "fofc_finish", "emf", "update")
+        return {nm: (out[2 * k], out[2 * k + 1]) for k, nm in enumerate(names)}
 
     def read_stats(self, stream=None) -> dict:
         s = mhd_stats()

@@ -270,3 +270,41 @@ def test_batched_uneven_blocks(G):
         out = O.stage(p, ref, dt, 0, mask=mask, keep=True)
         U.compare_prims(ref, got, p)
         U.compare_state(ref, got, scales=U.term_scales(p, ob, out, dt, 0))
+
+
+def _uneven(G, p):
+    st = synth.spacetime(3)
+    specs = [((8, 8, 8), 0.75, (-3.0, -3.0, -3.0)), ((16, 16, 16), 0.375, (-2.0, 0.5, -1.0)),
+             ((12, 12, 12), 0.1875, (0.3, -1.2, 0.4)), ((8, 8, 8), 0.75, (-40.0, -3.0, 5.0))]
+    obs = []
+    for n, dx, x0 in specs:
+        inp = synth.star_block(st, n, 4, (dx,) * 3, x0)
+        obs.append(O.init_block(p, inp.n, inp.ng, inp.dx, inp.adm, inp.prim, inp.A))
+    return obs
+
+
+def test_per_block_launches_and_autotune_reproduce_batched(G):
+    """One launch sequence per block, and the autotuner's launch shapes, give
+    bit-identical results to the batched launches (launch shape never changes
+    the arithmetic of a cell or face)."""
+    import torch
+    p = O.params(gamma=2.0, rho_atm=1e-12, T_atm=1e-10, recon=2, rsolver=1, rk_order=3, fofc=1)
+    obs = _uneven(G, p)
+    kw = {k: getattr(p, k) for k, _ in p._fields_ if k != "pad_"}
+    dt = 0.25 * 0.1875
+    A = [U.to_device(G, ob) for ob in obs]
+    B = [U.to_device(G, ob) for ob in obs]
+    Cb = [U.to_device(G, ob) for ob in obs]
+    T = [U.to_device(G, ob) for ob in obs]
+    c1 = G.Context(G.params(**kw))
+    c1.step(A, dt)
+    c1.step(B, dt, per_block=True)
+    c2 = G.Context(G.params(**kw))
+    cfg = c2.autotune(T, dt)
+    assert all(th in (64, 128, 256) and wv in (1, 2, 4) for th, wv in cfg.values())
+    c2.step(Cb, dt)
+    torch.cuda.synchronize()
+    for a, b, c in zip(A, B, Cb):
+        assert torch.equal(a.cons, b.cons) and torch.equal(a.cons, c.cons)
+        for d in range(3):
+            assert torch.equal(a.bf[d], b.bf[d]) and torch.equal(a.bf[d], c.bf[d])
