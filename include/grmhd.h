@@ -150,6 +150,15 @@ int mhd_step(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, double dt, int 
 #define MHD_NTUNE 9
 int mhd_autotune(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, double dt, void* stream, int* cfg_out);
 
+/* Pin the launch shape of one tunable kernel (kind in the order of
+ * mhd_autotune's output, 0 .. MHD_NTUNE-1): threads per CTA (64, 128 or 256)
+ * and waves (1 .. 64; the grid is at most waves x resident CTAs per SM x SMs).
+ * The arithmetic of a cell or face does not depend on the launch shape.
+ * MHD_EINVAL on a bad kind or shape; a cached CUDA graph is dropped. */
+int mhd_set_launch(mhd_ctx* ctx, int kind, int threads, int waves);
+/* Current launch shape of a tunable kernel. */
+int mhd_get_launch(const mhd_ctx* ctx, int kind, int* threads, int* waves);
+
 /* Copy the counters to *out (synchronises the stream) / zero them. */
 int mhd_read_stats(mhd_ctx* ctx, mhd_stats* out, void* stream);
 int mhd_reset_stats(mhd_ctx* ctx, void* stream);

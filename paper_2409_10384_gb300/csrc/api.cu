@@ -78,9 +78,9 @@ namespace {
 int tkind_items(int k) {
   switch (k) {
     case T_C2P_PREP: case T_C2P_FIN: return W_C2P;
-    case T_FX: return W_FX;
-    case T_FY: return W_FY;
-    case T_FZ: return W_FZ;
+    case T_FX: return W_SX;
+    case T_FY: return W_SY;
+    case T_FZ: return W_SZ;
     case T_FOFC_PREP: case T_FOFC_FIN: case T_UPD: return W_CELL;
     default: return W_EDGE;
   }
@@ -184,6 +184,7 @@ int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
     items[W_EDGE] = (n0 + 1) * (n1 + 1) * (n2 + 1);
     items[W_FACE] = (n0 + 1) * n1 * n2 + n0 * (n1 + 1) * n2 + n0 * n1 * (n2 + 1);
     items[W_INIT] = b.ncell;
+    for (int d = 0; d < 3; d++) items[W_SX + d] = flux_seg_items(s.n, d);
     for (int k = 0; k < W_NKIND; k++) pre[(size_t)k * (nb + 1) + i + 1] = pre[(size_t)k * (nb + 1) + i] + items[k];
   }
   const long long nkrp = std::max(pre[(size_t)W_C2P * (nb + 1) + nb], pre[(size_t)W_CELL * (nb + 1) + nb]);
@@ -344,7 +345,7 @@ int enqueue_rhs(mhd_ctx* c, double dt, int stage, cudaStream_t s, const Work& w,
   rk_weights(c->P.rk_order, stage, g0, g1, be);
   for (int d = 0; d < 3; d++)
     timed(c, MHD_K_FLUX_X + d, s, [&] {
-      launch_flux_dir(d, w, c->P, s, tgrid(c, T_FX + d, items[W_FX + d]), c->cfg[T_FX + d].threads);
+      launch_flux_dir(d, w, c->P, s, tgrid(c, T_FX + d, items[W_SX + d]), c->cfg[T_FX + d].threads);
     });
   if (c->P.fofc) {
     KrpBuf kb = krp_view(c->krp, items[W_CELL]);
@@ -950,7 +951,7 @@ int mhd_autotune(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, void* s
         case T_C2P_PREP: launch_krp_prep_block(w, c->P, kb, s, tgrid(c, k, it[W_C2P]), th); break;
         case T_C2P_FIN: launch_krp_finish_block(w, c->P, kb, c->dstats, s, tgrid(c, k, it[W_C2P]), th); break;
         case T_FX: case T_FY: case T_FZ:
-          launch_flux_dir(k - T_FX, w, c->P, s, tgrid(c, k, it[W_FX + k - T_FX]), th);
+          launch_flux_dir(k - T_FX, w, c->P, s, tgrid(c, k, it[W_SX + k - T_FX]), th);
           break;
         case T_FOFC_PREP:
           launch_krp_prep_fofc(w, c->P, g0, g1, be * dt, kb, s, tgrid(c, k, it[W_CELL]), th);
@@ -991,6 +992,22 @@ int mhd_autotune(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, void* s
   c->rhs_list = -1;
   destroy_graph(c);
   return cuda_ok(cudaStreamSynchronize(s));
+}
+
+int mhd_set_launch(mhd_ctx* c, int kind, int threads, int waves) {
+  if (!c || kind < 0 || kind >= T_N || (threads != 64 && threads != 128 && threads != 256) || waves < 1 || waves > 64)
+    return MHD_EINVAL;
+  c->cfg[kind].threads = threads;
+  c->cfg[kind].waves = waves;
+  destroy_graph(c);
+  return MHD_OK;
+}
+
+int mhd_get_launch(const mhd_ctx* c, int kind, int* threads, int* waves) {
+  if (!c || kind < 0 || kind >= T_N || !threads || !waves) return MHD_EINVAL;
+  *threads = c->cfg[kind].threads;
+  *waves = c->cfg[kind].waves;
+  return MHD_OK;
 }
 
 int mhd_profile(mhd_ctx* c, int enable) {

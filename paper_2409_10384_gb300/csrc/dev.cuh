@@ -41,7 +41,18 @@ struct DevBlock {
 };
 
 // Work lists: item ranges of every block for one kernel kind.
-enum WorkKind { W_C2P = 0, W_FX, W_FY, W_FZ, W_CELL, W_EDGE, W_FACE, W_INIT, W_NKIND };
+enum WorkKind { W_C2P = 0, W_FX, W_FY, W_FZ, W_CELL, W_EDGE, W_FACE, W_INIT, W_SX, W_SY, W_SZ, W_NKIND };
+
+// Flux sweeps: the n_d + 1 faces of direction d on one transverse line (one
+// extra line on each side, for the CT stencil) are split into near-equal
+// segments of at most FLUX_SEG faces; one thread sweeps one segment.
+constexpr int FLUX_SEG = 16;
+__host__ __device__ inline int flux_nseg(int nd) { return (nd + FLUX_SEG) / FLUX_SEG; }
+__host__ __device__ inline long long flux_seg_items(const int* n, int d) {
+  long long t = 1;
+  for (int a = 0; a < 3; a++) t *= a == d ? (long long)flux_nseg(n[a]) : (long long)(n[a] + 2);
+  return t;
+}
 
 // Slots of the per-cell con2prim scratch (SoA, [KW_N][n]).
 enum {
@@ -443,47 +454,112 @@ __device__ __forceinline__ void con2prim(const Par& P, double* U, const double* 
 }
 
 // -------------------------------------------------- reconstruction (Sec. 3.2)
-__device__ __forceinline__ double vl_slope(double qm, double q0, double qp) {
-  double dl = q0 - qm, dr = qp - q0;
-  double pr = dl * dr;
-  return pr > 0.0 ? 2.0 * pr / (dl + dr) : 0.0;
-}
-// WENO-Z value at the face between c and d, stencil (a,b,c,d,e) centred on c.
-// The three nonlinear weights share one division: omega_k is proportional to
-// d_k (beta_k + eps + tau5) prod_{m != k} (beta_m + eps).
-__device__ __forceinline__ double wenoz(double a, double b, double c, double d, double e) {
-  const double third = 1.0 / 3.0, sixth = 1.0 / 6.0;
-  double q0 = fma(third, a, fma(-7.0 * sixth, b, (11.0 * sixth) * c));
-  double q1 = fma(-sixth, b, fma(5.0 * sixth, c, third * d));
-  double q2 = fma(third, c, fma(5.0 * sixth, d, -sixth * e));
+// The flux kernels sweep a line of cells along the face normal, so every cell
+// is reconstructed once and yields both of its face values: "hi" at x_{m+1/2}
+// (the left state of that face) and "lo" at x_{m-1/2} (the right state of the
+// face below).  With differences delta_k = x_{k+1} - x_k carried along the
+// sweep, each three-cell window is evaluated once and serves as stencil 0 of
+// the cell to its right, stencil 1 of its centre cell and stencil 2 of the
+// cell to its left.
+//
+// Smoothness of the window (x_{c-1}, x_c, x_{c+1}) from dl = x_c - x_{c-1} and
+// dr = x_{c+1} - x_c, in the three one-sided forms of WENO5 (Jiang & Shu):
+// 13/12 (x0 - 2x1 + x2)^2 + 1/4 u^2 with u = x0 - 4x1 + 3x2 (b0), x0 - x2 (b1)
+// or 3x0 - 4x1 + x2 (b2).  With t = x0 - 2x1 + x2 and h = (x2 - x0)/2 these
+// are 13/12 t^2 + (t + h)^2, + h^2 and + (t - h)^2.
+__device__ __forceinline__ void wz_window(double dl, double dr, double& b0, double& b1, double& b2) {
   const double k13 = 13.0 / 12.0;
-  double t = a - 2.0 * b + c, u = a - 4.0 * b + 3.0 * c;
-  double b0 = fma(k13 * t, t, 0.25 * u * u);
-  t = b - 2.0 * c + d; u = b - d;
-  double b1 = fma(k13 * t, t, 0.25 * u * u);
-  t = c - 2.0 * d + e; u = 3.0 * c - 4.0 * d + e;
-  double b2 = fma(k13 * t, t, 0.25 * u * u);
-  const double eps = 1e-40;
-  double tau = fabs(b0 - b2);
-  double e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
-  double w0 = 0.1 * (e0 + tau) * (e1 * e2);
-  double w1 = 0.6 * (e1 + tau) * (e0 * e2);
-  double w2 = 0.3 * (e2 + tau) * (e0 * e1);
-  return fma(w0, q0, fma(w1, q1, w2 * q2)) / (w0 + w1 + w2);
+  const double t = dr - dl;
+  const double h = 0.5 * (dl + dr);
+  const double kt2 = (k13 * t) * t;
+  const double h0 = t + h, h2 = t - h;
+  b0 = fma(h0, h0, kt2);
+  b1 = fma(h, h, kt2);
+  b2 = fma(h2, h2, kt2);
 }
-// L/R states at the face between q[2] and q[3] from q[0..5] = cells -3..+2
-__device__ __forceinline__ void recon(int r, const double* q, double& L, double& R) {
-  if (r == 2) {
-    L = wenoz(q[0], q[1], q[2], q[3], q[4]);
-    R = wenoz(q[5], q[4], q[3], q[2], q[1]);
-  } else if (r == 1) {
-    L = fma(0.5, vl_slope(q[1], q[2], q[3]), q[2]);
-    R = fma(-0.5, vl_slope(q[2], q[3], q[4]), q[3]);
-  } else {
-    L = q[2];
-    R = q[3];
+
+// Sliding state of one reconstructed variable at cell m of a sweep.
+struct RecVar {
+  double x1, x2;          // x_m, x_{m+1}
+  double d0, d1, d2;      // delta_{m-2}, delta_{m-1}, delta_m
+  double b0p, b0c, b1c;   // b0 of window m-1, b0 and b1 of window m
+};
+
+// R = 0 donor cell, 1 PLM with the van Leer limiter, 2 WENO-Z.
+// Start at cell m from x_{m-2} .. x_{m+1}.
+template <int R>
+__device__ __forceinline__ void rec_init(RecVar& s, double xm2, double xm1, double x0, double xp1) {
+  s.x1 = x0;
+  s.x2 = xp1;
+  s.d0 = xm1 - xm2;
+  s.d1 = x0 - xm1;
+  s.d2 = xp1 - x0;
+  if (R == 2) {
+    double u, v;
+    wz_window(s.d0, s.d1, s.b0p, u, v);
+    wz_window(s.d1, s.d2, s.b0c, s.b1c, v);
   }
 }
+
+// Face values of cell m given x_{m+2}; advances the state to cell m+1.
+// The WENO-Z weights follow Borges et al. (2008) with p = 1 and linear weights
+// (1, 6, 3)/10: omega_k ~ d_k (1 + tau5/(b_k + eps)); multiplied through by
+// the product of the three (b_k + eps) they need no division.  The two face
+// values of the cell share one reciprocal.
+template <int R>
+__device__ __forceinline__ void rec_step(RecVar& s, double xn, double& lo, double& hi) {
+  const double dn = xn - s.x2;  // delta_{m+1}
+  if (R == 2) {
+    double b0n, b1n, b2n;
+    wz_window(s.d2, dn, b0n, b1n, b2n);
+    const double eps = 1e-40;
+    const double b0 = s.b0p, b1 = s.b1c, b2 = b2n;
+    const double tau = fabs(b0 - b2);
+    const double e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
+    const double A0 = (e0 + tau) * (e1 * e2);
+    const double A1 = (e1 + tau) * (e0 * e2);
+    const double A2 = (e2 + tau) * (e0 * e1);
+    const double a1 = 6.0 * A1, a2h = 3.0 * A2, a0l = 3.0 * A0;
+    const double den_hi = A0 + a1 + a2h;   // stencils 0,1,2 of the value at m+1/2
+    const double den_lo = a0l + a1 + A2;   // mirrored: b2 pairs with weight 1, b0 with 3
+    // the three third-order candidates minus x_m, times 6
+    const double da = s.d0, db = s.d1, dc = s.d2, dd = dn;
+    const double k0 = fma(5.0, db, -2.0 * da);
+    const double k1 = fma(2.0, dc, db);
+    const double k2 = fma(4.0, dc, -dd);
+    const double m0 = fma(-5.0, dc, 2.0 * dd);
+    const double m1 = fma(2.0, db, dc);
+    const double m2 = fma(-4.0, db, da);
+    const double n_hi = fma(A0, k0, fma(a1, k1, a2h * k2));
+    const double n_lo = fma(A2, m0, fma(-a1, m1, a0l * m2));
+    const double pr = den_hi * den_lo;
+    if (__double2hiint(pr) < 0x7E000000) {   // pr < 2^993: one shared reciprocal
+      const double r = (1.0 / 6.0) / pr;
+      hi = fma(n_hi, den_lo * r, s.x1);
+      lo = fma(n_lo, den_hi * r, s.x1);
+    } else {
+      hi = s.x1 + n_hi / (6.0 * den_hi);
+      lo = s.x1 + n_lo / (6.0 * den_lo);
+    }
+    s.b0p = s.b0c;
+    s.b0c = b0n;
+    s.b1c = b1n;
+  } else if (R == 1) {
+    const double dl = s.d1, dr = s.d2;
+    const double pr = dl * dr;
+    const double h = pr > 0.0 ? pr / (dl + dr) : 0.0;   // half the van Leer slope
+    hi = s.x1 + h;
+    lo = s.x1 - h;
+  } else {
+    hi = lo = s.x1;
+  }
+  s.x1 = s.x2;
+  s.x2 = xn;
+  s.d0 = s.d1;
+  s.d1 = s.d2;
+  s.d2 = dn;
+}
+
 __device__ __forceinline__ void face_floor(const Par& P, double* s) {
   if (s[0] < P.rho_thr) {
     s[0] = P.rho_atm; s[1] = s[2] = s[3] = 0.0; s[4] = P.P_atm;
@@ -493,99 +569,138 @@ __device__ __forceinline__ void face_floor(const Par& P, double* s) {
 }
 
 // --------------------------------------------------------- face fluxes (Eq. 8)
-// Face metric: alpha, beta, gamma with inverse, plus 1/alpha.
+// Face metric: alpha, beta, gamma with inverse and sqrt(gamma).
 struct FaceMetric {
   Metric m;
   double alpha, beta[3];
 };
+// Conserved state and flux of one side, plus the pieces of its fast
+// magnetosonic speeds lambda = alpha (vq -/+ sq) / den - beta^d.
 struct Side {
-  double U[7], F[7], lm, lp;
+  double U[7], F[7], vq, sq, den;
 };
-// st = rho, w^1..3, P, B~^{t1}, B~^{t2}; Bn = B~^d.
+// st = rho, w^1..3 (= W v^i), P, B~^{t1}, B~^{t2}; Bn = B~^d.
+//
+// Speeds: with c_f^2 = c_s^2 + v_A^2 - c_s^2 v_A^2 = (Gamma P + b^2)/(rho h +
+// b^2) (c_s^2 = Gamma P/(rho h), v_A^2 = b^2/(rho h + b^2)), the roots of the
+// characteristic quadratic along d become
+//   lambda = alpha [v^d Q -/+ sqrt(N X / W^2)] / (Dn - v^2 N) - beta^d,
+//   N = Gamma P + b^2,  Dn = rho h + b^2,  Q = rho h - Gamma P,
+//   X = gamma^{dd} (Dn - v^2 N) - (v^d)^2 Q,
+// which needs one square root and (shared with the other side) one division.
 template <int d>
 __device__ __forceinline__ void face_side(const Par& P, const double* st, double Bn, const FaceMetric& fm, Side& o) {
   constexpr int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
   const Metric& m = fm.m;
   double Bt[3];
   Bt[d] = Bn; Bt[t1] = st[5]; Bt[t2] = st[6];
-  double B[3] = {Bt[0] * m.isdet, Bt[1] * m.isdet, Bt[2] * m.isdet};
-  double w[3] = {st[1], st[2], st[3]};
+  const double B[3] = {Bt[0] * m.isdet, Bt[1] * m.isdet, Bt[2] * m.isdet};
+  const double w[3] = {st[1], st[2], st[3]};
   double wl[3], Bl[3];
   lower3(m.g, w, wl);
   lower3(m.g, B, Bl);
-  double W2 = 1.0 + dot3(w, wl);
-  double iW = rsqrt(W2);
-  double W = W2 * iW;
-  double v[3] = {w[0] * iW, w[1] * iW, w[2] * iW};
-  double vl[3] = {wl[0] * iW, wl[1] * iW, wl[2] * iW};
-  double B2 = dot3(B, Bl), Bv = dot3(B, vl), v2 = dot3(v, vl);
-  double iW2 = iW * iW;
-  double b2 = fma(B2, iW2, Bv * Bv);
-  double rho = st[0], p = st[4];
-  double rhoh = fma(P.gfac, p, rho);
-  double e = rhoh * W2;
-  double D = rho * W;
-  double eB = e + B2;
-  double sd = m.sdet;
-  double alpha = fm.alpha;
+  const double W2 = fma(w[0], wl[0], fma(w[1], wl[1], fma(w[2], wl[2], 1.0)));
+  const double iW = rsqrt(W2);
+  const double iW2 = iW * iW;
+  const double W = W2 * iW;
+  const double Bw = dot3(B, wl);          // W (B.v)
+  const double Bv = Bw * iW;
+  const double B2 = dot3(B, Bl);
+  const double b2 = fma(B2, iW2, Bv * Bv);
+  const double rho = st[0], p = st[4];
+  const double rhoh = fma(P.gfac, p, rho);
+  const double eB = fma(rhoh, W2, B2);     // rho h W^2 + B^2
+  const double D = rho * W;
+  const double sd = m.sdet, alpha = fm.alpha;
+  const double aiW = alpha * iW;
   double avh[3];  // alpha vhat^i = alpha v^i - beta^i
 #pragma unroll
-  for (int a = 0; a < 3; a++) avh[a] = fma(alpha, v[a], -fm.beta[a]);
-  double Ptot = fma(0.5, b2, p);
+  for (int a = 0; a < 3; a++) avh[a] = fma(aiW, w[a], -fm.beta[a]);
+  const double Ptot = fma(0.5, b2, p);
+  const double sdeBW = sd * (eB * iW);
+  const double sdBv = sd * Bv;
   o.U[0] = sd * D;
 #pragma unroll
-  for (int a = 0; a < 3; a++) o.U[1 + a] = sd * fma(eB, vl[a], -Bv * Bl[a]);
-  o.U[4] = sd * ((e - D) + B2 - p - 0.5 * fma(B2, iW2, Bv * Bv));
+  for (int a = 0; a < 3; a++) o.U[1 + a] = fma(sdeBW, wl[a], -sdBv * Bl[a]);
+  o.U[4] = sd * ((eB - D) - Ptot);
   o.U[5] = Bt[t1];
   o.U[6] = Bt[t2];
-  double avd = avh[d];
-  double aBn = alpha * Bn;
-  double aPs = alpha * sd * Ptot;
+  const double avd = avh[d];
+  const double aBn = alpha * Bn;
+  const double aBi = aBn * iW2;
+  const double sdP = sd * Ptot;
   o.F[0] = o.U[0] * avd;
 #pragma unroll
-  for (int a = 0; a < 3; a++) {
-    double bl = fma(W * Bv, vl[a], Bl[a] * iW);   // b_i = B_i/W + W (B.v) v_i
-    o.F[1 + a] = fma(o.U[1 + a], avd, -aBn * bl * iW);
-  }
-  o.F[1 + d] += aPs;
-  o.F[4] = fma(o.U[4], avd, fma(aPs, v[d], -aBn * Bv));
-  o.F[5] = fma(Bt[t1], avh[d], -Bn * avh[t1]);
-  o.F[6] = fma(Bt[t2], avh[d], -Bn * avh[t2]);
-  // fast magnetosonic speed (one division for c_s^2 and v_A^2)
-  double inv = 1.0 / (rhoh * (rhoh + b2));
-  double cs2 = P.gam * p * (rhoh + b2) * inv;
-  double va2 = b2 * rhoh * inv;
-  double cf2 = cs2 + va2 - cs2 * va2;
-  double cf = sqrt(cf2);
-  double vd = v[d];
-  double omc = 1.0 - cf2;
-  double den = 1.0 - v2 * cf2;
-  double disc = (1.0 - v2) * (m.gi[d == 0 ? 0 : (d == 1 ? 3 : 5)] * den - vd * vd * omc);
-  double sq = sqrt(disc > 0.0 ? disc : 0.0);
-  double ad = alpha / den;
-  double c1 = vd * omc, c2 = cf * sq;
-  o.lm = fma(ad, c1 - c2, -fm.beta[d]);
-  o.lp = fma(ad, c1 + c2, -fm.beta[d]);
+  for (int a = 0; a < 3; a++) o.F[1 + a] = fma(o.U[1 + a], avd, -aBi * fma(Bw, wl[a], Bl[a]));  // b_i/W = (Bw w_i + B_i)/W^2
+  o.F[1 + d] = fma(alpha, sdP, o.F[1 + d]);
+  const double vd = w[d] * iW;
+  o.F[4] = fma(o.U[4], avd, fma(sdP, alpha * vd, -aBn * Bv));
+  o.F[5] = fma(Bt[t1], avd, -Bn * avh[t1]);
+  o.F[6] = fma(Bt[t2], avd, -Bn * avh[t2]);
+  const double gp = P.gam * p;
+  const double N = gp + b2;
+  const double Q = rhoh - gp;
+  const double den = fma(iW2 - 1.0, N, rhoh + b2);   // Dn - v^2 N, v^2 = 1 - 1/W^2
+  const double X = fma(m.gi[d == 0 ? 0 : (d == 1 ? 3 : 5)], den, -(vd * vd) * Q);
+  const double S = (N * iW2) * X;
+  o.sq = sqrt(S > 0.0 ? S : 0.0);
+  o.vq = vd * Q;
+  o.den = den;
 }
 
-__device__ __forceinline__ void riemann(int rs, const Side& L, const Side& R, double* F) {
+// LLF (rs 0) or HLLE (rs 1) flux from the two sides of a face of direction d.
+template <int d>
+__device__ __forceinline__ void riemann(int rs, const FaceMetric& fm, const Side& L, const Side& R, double* F) {
+  const double r = fm.alpha / (L.den * R.den);
+  const double aL = r * R.den, aR = r * L.den;
+  const double bd = fm.beta[d];
+  const double lmL = fma(aL, L.vq - L.sq, -bd), lpL = fma(aL, L.vq + L.sq, -bd);
+  const double lmR = fma(aR, R.vq - R.sq, -bd), lpR = fma(aR, R.vq + R.sq, -bd);
   if (rs == 1) {
-    double lL = fmin(fmin(L.lm, R.lm), 0.0);
-    double lR = fmax(fmax(L.lp, R.lp), 0.0);
+    const double lL = fmin(fmin(lmL, lmR), 0.0);
+    const double lR = fmax(fmax(lpL, lpR), 0.0);
     if (lR == lL) {
 #pragma unroll
       for (int c = 0; c < 7; c++) F[c] = 0.5 * (L.F[c] + R.F[c]);
     } else {
-      double inv = 1.0 / (lR - lL);
-      double ll = lL * lR;
+      const double inv = 1.0 / (lR - lL);
+      const double ll = lL * lR;
 #pragma unroll
       for (int c = 0; c < 7; c++) F[c] = fma(lR, L.F[c], fma(-lL, R.F[c], ll * (R.U[c] - L.U[c]))) * inv;
     }
   } else {
-    double a = fmax(fmax(fabs(L.lm), fabs(L.lp)), fmax(fabs(R.lm), fabs(R.lp)));
+    const double a = fmax(fmax(fabs(lmL), fabs(lpL)), fmax(fabs(lmR), fabs(lpR)));
 #pragma unroll
     for (int c = 0; c < 7; c++) F[c] = 0.5 * (L.F[c] + R.F[c]) - 0.5 * a * (R.U[c] - L.U[c]);
   }
+}
+
+// Interpolates the ADM variables to the face between the cells at a and a+st
+// (4-point Lagrange, weights (-1, 9, 9, -1)/16) and prepares the metric.
+__device__ __forceinline__ void face_metric(const double* adm, long long nc, long long a, long long st, FaceMetric& fm) {
+  double mv[10];
+#pragma unroll
+  for (int v = 0; v < 10; v++) {
+    const double* q = adm + v * nc + a;
+    mv[v] = fma(0.5625, q[0] + q[st], -0.0625 * (q[-st] + q[2 * st]));
+  }
+  fm.alpha = mv[0];
+  fm.beta[0] = mv[1]; fm.beta[1] = mv[2]; fm.beta[2] = mv[3];
+#pragma unroll
+  for (int v = 0; v < 6; v++) fm.m.g[v] = mv[4 + v];
+  metric_setup(fm.m);
+}
+
+// Flux through one face from its reconstructed (unfloored) states.
+template <int d>
+__device__ __forceinline__ void face_flux_states(const Par& P, double* L, double* R, double Bn, const FaceMetric& fm,
+                                                 double* F) {
+  face_floor(P, L);
+  face_floor(P, R);
+  Side sl, sr;
+  face_side<d>(P, L, Bn, fm, sl);
+  face_side<d>(P, R, Bn, fm, sr);
+  riemann<d>(P.rsolver, fm, sl, sr, F);
 }
 
 // SSP-RK weights (g0, g1, beta) of a stage: U <- g0 U^n + g1 U + beta dt L(U)

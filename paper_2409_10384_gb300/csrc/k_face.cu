@@ -17,72 +17,91 @@ __device__ __forceinline__ void face_coords(const DevBlock& b, long long loc, in
   k = a2 + b.ng - (d == 2 ? 0 : 1);
 }
 
-// Flux through face (k,j,i) of direction d; donor forces first order.
+// First-order (donor cell) flux through face (k,j,i) of direction d.
 template <int d>
-__device__ __forceinline__ void face_flux(const DevBlock& b, const Par& P, int k, int j, int i, bool donor,
-                                          double* F) {
+__device__ __forceinline__ void face_flux_donor(const DevBlock& b, const Par& P, int k, int j, int i, double* F) {
   constexpr int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
   const long long nc = b.ncell;
   const long long c0 = cidx(b, k, j, i);
   const long long st = d == 0 ? 1 : (d == 1 ? (long long)b.N[0] : (long long)b.N[0] * b.N[1]);
-  const int r = donor ? 0 : P.recon;
   double L[7], R[7];
 #pragma unroll
   for (int v = 0; v < 7; v++) {
     const double* a = v < 5 ? b.prim + v * nc : b.bcc + (v == 5 ? t1 : t2) * nc;
-    double q[6];
-    if (r == 2) {
-#pragma unroll
-      for (int m = 0; m < 6; m++) q[m] = a[c0 + (m - 3) * st];
-    } else if (r == 1) {
-#pragma unroll
-      for (int m = 1; m < 5; m++) q[m] = a[c0 + (m - 3) * st];
-      q[0] = q[5] = 0.0;
-    } else {
-      q[2] = a[c0 - st];
-      q[3] = a[c0];
-      q[0] = q[1] = q[4] = q[5] = 0.0;
-    }
-    recon(r, q, L[v], R[v]);
+    L[v] = a[c0 - st];
+    R[v] = a[c0];
   }
-  face_floor(P, L);
-  face_floor(P, R);
-  // ADM metric at the face: 4-point Lagrange (-1, 9, 9, -1)/16 along d
   FaceMetric fm;
-  double mv[10];
-#pragma unroll
-  for (int v = 0; v < 10; v++) {
-    const double* a = b.adm + v * nc + c0;
-    double am = a[-2 * st], bm = a[-st], cm = a[0], dm = a[st];
-    mv[v] = fma(0.5625, bm + cm, -0.0625 * (am + dm));
-  }
-  fm.alpha = mv[0];
-  fm.beta[0] = mv[1]; fm.beta[1] = mv[2]; fm.beta[2] = mv[3];
-#pragma unroll
-  for (int v = 0; v < 6; v++) fm.m.g[v] = mv[4 + v];
-  metric_setup(fm.m);
-  const double Bn = b.bf[d][fidx(b, d, k, j, i)];
-  Side sl, sr;
-  face_side<d>(P, L, Bn, fm, sl);
-  face_side<d>(P, R, Bn, fm, sr);
-  riemann(P.rsolver, sl, sr, F);
+  face_metric(b.adm, nc, c0 - st, st, fm);
+  face_flux_states<d>(P, L, R, b.bf[d][fidx(b, d, k, j, i)], fm, F);
 }
 
+// Segment `s` of the transverse line of item `loc`: (k,j,i) is the cell on the
+// upper side of the segment's first face, nf its number of faces.
 template <int d>
+__device__ __forceinline__ void seg_coords(const DevBlock& b, int loc, int& k, int& j, int& i, int& nf) {
+  const int ns = flux_nseg(b.n[d]), nd = b.n[d] + 1;
+  int s, a0, a1;
+  if (d == 0) {
+    s = loc % ns; int r = loc / ns; a0 = r % (b.n[1] + 2); a1 = r / (b.n[1] + 2);
+  } else if (d == 1) {
+    a0 = loc % (b.n[0] + 2); int r = loc / (b.n[0] + 2); a1 = r % (b.n[2] + 2); s = r / (b.n[2] + 2);
+  } else {
+    a0 = loc % (b.n[0] + 2); int r = loc / (b.n[0] + 2); a1 = r % (b.n[1] + 2); s = r / (b.n[1] + 2);
+  }
+  const int f0 = (int)((long long)s * nd / ns), f1 = (int)((long long)(s + 1) * nd / ns);
+  nf = f1 - f0;
+  const int g = b.ng;
+  if (d == 0) { i = g + f0; j = g - 1 + a0; k = g - 1 + a1; }
+  else if (d == 1) { j = g + f0; i = g - 1 + a0; k = g - 1 + a1; }
+  else { k = g + f0; i = g - 1 + a0; j = g - 1 + a1; }
+}
+
+// Fluxes of direction d, one thread per segment: the thread sweeps the cells
+// along d, reconstructing each once (order R) and finishing one face per cell.
+template <int d, int R>
 __global__ void __launch_bounds__(256) k_flux(Work w, Par P) {
-  const long long* pre = w.pre + (long long)(W_FX + d) * (w.nblocks + 1);
+  constexpr int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  const long long* pre = w.pre + (long long)(W_SX + d) * (w.nblocks + 1);
   const long long tot = pre[w.nblocks];
   for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < tot; it += (long long)gridDim.x * blockDim.x) {
-    const int bi = find_block(w, W_FX + d, it);
+    const int bi = find_block(w, W_SX + d, it);
     const DevBlock& b = w.blk[bi];
-    int k, j, i;
-    face_coords<d>(b, it - pre[bi], k, j, i);
-    double F[7];
-    face_flux<d>(b, P, k, j, i, false, F);
-    const long long f = fidx(b, d, k, j, i), nf = nface(b, d);
-    double* out = b.flux[d];
+    int k, j, i, nf;
+    seg_coords<d>(b, (int)(it - pre[bi]), k, j, i, nf);
+    const long long nc = b.ncell;
+    const long long st = d == 0 ? 1 : (d == 1 ? (long long)b.N[0] : (long long)b.N[0] * b.N[1]);
+    const long long fst = d == 0 ? 1 : (d == 1 ? (long long)b.N[0] : (long long)b.N[0] * b.N[1]);
+    const long long nfc = nface(b, d);
+    const double* src[7] = {b.prim, b.prim + nc, b.prim + 2 * nc, b.prim + 3 * nc, b.prim + 4 * nc,
+                            b.bcc + t1 * nc, b.bcc + t2 * nc};
+    long long c = cidx(b, k, j, i) - st;   // cell m below the first face
+    long long f = fidx(b, d, k, j, i);
+    RecVar rv[7];
+    double Ls[7];
 #pragma unroll
-    for (int c = 0; c < 7; c++) out[c * nf + f] = F[c];
+    for (int v = 0; v < 7; v++) {
+      const double* a = src[v] + c;
+      rec_init<R>(rv[v], a[-2 * st], a[-st], a[0], a[st]);
+      double lo;
+      rec_step<R>(rv[v], a[2 * st], lo, Ls[v]);
+    }
+    for (int q = 0; q < nf; q++) {
+      c += st;
+      double Rs[7], Lnext[7];
+#pragma unroll
+      for (int v = 0; v < 7; v++) rec_step<R>(rv[v], src[v][c + 2 * st], Rs[v], Lnext[v]);
+      FaceMetric fm;
+      face_metric(b.adm, nc, c - st, st, fm);
+      double F[7];
+      face_flux_states<d>(P, Ls, Rs, b.bf[d][f], fm, F);
+      double* out = b.flux[d];
+#pragma unroll
+      for (int v = 0; v < 7; v++) out[v * nfc + f] = F[v];
+#pragma unroll
+      for (int v = 0; v < 7; v++) Ls[v] = Lnext[v];
+      f += fst;
+    }
   }
 }
 
@@ -175,7 +194,7 @@ __global__ void __launch_bounds__(128) k_fofc_fix(Work w, Par P, unsigned long l
               (interior(b, km, jm, im) && b.fflag[cidx(b, km, jm, im)]);
     if (!fl) continue;
     double F[7];
-    face_flux<d>(b, P, k, j, i, true, F);
+    face_flux_donor<d>(b, P, k, j, i, F);
     const long long f = fidx(b, d, k, j, i), nf = nface(b, d);
     double* out = b.flux[d];
 #pragma unroll
@@ -185,10 +204,16 @@ __global__ void __launch_bounds__(128) k_fofc_fix(Work w, Par P, unsigned long l
   warp_flush(&stats[6], s_faces);
 }
 
+template <int d>
+void launch_flux_r(const Work& w, const Par& P, cudaStream_t s, int grid, int threads) {
+  if (P.recon == 2) k_flux<d, 2><<<grid, threads, 0, s>>>(w, P);
+  else if (P.recon == 1) k_flux<d, 1><<<grid, threads, 0, s>>>(w, P);
+  else k_flux<d, 0><<<grid, threads, 0, s>>>(w, P);
+}
 void launch_flux_dir(int d, const Work& w, const Par& P, cudaStream_t s, int grid, int threads) {
-  if (d == 0) k_flux<0><<<grid, threads, 0, s>>>(w, P);
-  else if (d == 1) k_flux<1><<<grid, threads, 0, s>>>(w, P);
-  else k_flux<2><<<grid, threads, 0, s>>>(w, P);
+  if (d == 0) launch_flux_r<0>(w, P, s, grid, threads);
+  else if (d == 1) launch_flux_r<1>(w, P, s, grid, threads);
+  else launch_flux_r<2>(w, P, s, grid, threads);
 }
 void launch_fofc_flag(const Work& w, const Par& P, double g0, double g1, double bdt, unsigned long long* stats,
                       cudaStream_t s, int grid) {
@@ -201,16 +226,16 @@ void launch_fofc_fix(int d, const Work& w, const Par& P, unsigned long long* sta
 }
 int occ_face_kernel(int kind, int threads) {
   int o = 0;
-  if (kind == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_flux<0>, threads, 0);
-  else if (kind == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_flux<1>, threads, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_flux<2>, threads, 0);
+  if (kind == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_flux<0, 2>, threads, 0);
+  else if (kind == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_flux<1, 2>, threads, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_flux<2, 2>, threads, 0);
   return o;
 }
 int occupancy_face(int* per_sm) {
   cudaError_t e = cudaSuccess;
-  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_flux<0>, 128, 0));
-  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_flux<1>, 128, 0));
-  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[2], k_flux<2>, 128, 0));
+  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_flux<0, 2>, 128, 0));
+  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_flux<1, 2>, 128, 0));
+  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[2], k_flux<2, 2>, 128, 0));
   e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[3], k_fofc_flag, 128, 0));
   e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[4], k_fofc_fix<0>, 128, 0));
   return e == cudaSuccess ? 0 : -1;

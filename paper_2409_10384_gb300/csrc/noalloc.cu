@@ -168,6 +168,7 @@ extern "C" int mhd_stage_noalloc(const mhd_params* p, const mhd_block* blk, doub
   items[W_EDGE] = (n0 + 1) * (n1 + 1) * (n2 + 1);
   items[W_FACE] = (n0 + 1) * n1 * n2 + n0 * (n1 + 1) * n2 + n0 * n1 * (n2 + 1);
   items[W_INIT] = ncell;
+  for (int d = 0; d < 3; d++) items[W_SX + d] = flux_seg_items(s.n, d);
   PreTable t;
   for (int k = 0; k < W_NKIND; k++) {
     t.v[2 * k] = 0;
@@ -193,7 +194,7 @@ extern "C" int mhd_stage_noalloc(const mhd_params* p, const mhd_block* blk, doub
   double g0, g1, be;
   rk_weights(P.rk_order, stage, g0, g1, be);
   launch_c2p_block(w, P, dstats, st, grid(W_C2P, 128));
-  for (int d = 0; d < 3; d++) launch_flux_dir(d, w, P, st, grid(W_FX + d, 128));
+  for (int d = 0; d < 3; d++) launch_flux_dir(d, w, P, st, grid(W_SX + d, 128));
   if (P.fofc) {
     launch_fofc_flag(w, P, g0, g1, be * dt, dstats, st, grid(W_CELL, 128));
     for (int d = 0; d < 3; d++) launch_fofc_fix(d, w, P, dstats, st, grid(W_FX + d, 128));

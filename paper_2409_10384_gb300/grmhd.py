@@ -76,6 +76,8 @@ _SIGS = {
     "mhd_kernel_name": (C.c_char_p, [_I]),
     "mhd_stage_noalloc": (_I, [C.POINTER(mhd_params), C.POINTER(mhd_block), _D, _I, _VP]),
     "mhd_autotune": (_I, [_VP, C.POINTER(mhd_block), _I, _D, _VP, _VP]),
+    "mhd_set_launch": (_I, [_VP, _I, _I, _I]),
+    "mhd_get_launch": (_I, [_VP, _I, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "mhd_mlp_init": (_I, [_VP, C.c_ulonglong]),
     "mhd_mlp_dataset": (_I, [_VP, _L, _VP, _VP, _VP, _VP, _VP, _VP]),
     "mhd_mlp_train": (_I, [_VP, _VP, _VP, _L, _I, _I, C.c_float, C.c_ulonglong, C.POINTER(C.c_float), _VP]),
@@ -186,6 +188,12 @@ class DeviceBlock:
         return b
 
 
+def _block_ptrs(b: DeviceBlock) -> tuple:
+    return (b.n, b.ng, b.dx, b.cons.data_ptr(), b.cons0.data_ptr(), b.prim.data_ptr(), b.bcc.data_ptr(),
+            b.adm.data_ptr(), b.flags.data_ptr()) + tuple(x.data_ptr() for x in b.bf) + \
+        tuple(x.data_ptr() for x in b.bf0)
+
+
 def stage_noalloc(p: mhd_params, blk: DeviceBlock, dt: float, stage: int, stream=None) -> int:
     """mhd_stage_noalloc on one block (no context, no device allocation);
     returns the status code."""
@@ -211,8 +219,10 @@ class Context:
         self.h = h
         self._arr = None
         self._key = None
+        self._held = []
 
     def close(self):
+        self._arr, self._key, self._held = None, None, []
         if self.h:
             self.L.mhd_finalize(self.h)
             self.h = C.c_void_p()
@@ -228,10 +238,16 @@ class Context:
         self.p = p
 
     def _blocks(self, blocks):
-        key = tuple(id(b) for b in blocks)
+        """Descriptor array of a block list, rebuilt whenever any device
+        pointer differs from the cached list's.  Object ids alone are not a
+        key: a freed block's id can be reused by a new block whose arrays live
+        elsewhere."""
+        blocks = list(blocks)
+        key = tuple(_block_ptrs(b) for b in blocks)
         if key != self._key:
             self._arr = block_array(blocks)
             self._key = key
+            self._held = blocks   # the cached descriptors point into these blocks
         return self._arr, len(blocks)
 
     def init_block(self, blk: DeviceBlock, A, stream=None):
@@ -299,6 +315,17 @@ class Context:
         check(self.L.mhd_autotune(self.h, arr, nb, float(dt), _sptr(stream), out), "mhd_autotune")
         names = ("c2p_prep", "c2p_finish", "flux_x", "flux_y", "flux_z", "fofc_prep", "fofc_finish", "emf", "update")
         return {nm: (out[2 * k], out[2 * k + 1]) for k, nm in enumerate(names)}
+
+    TUNABLE = ("c2p_prep", "c2p_finish", "flux_x", "flux_y", "flux_z", "fofc_prep", "fofc_finish", "emf", "update")
+
+    def set_launch(self, kernel: str, threads: int, waves: int):
+        """Pin the launch shape (CTA size, waves) of one tunable kernel."""
+        check(self.L.mhd_set_launch(self.h, self.TUNABLE.index(kernel), int(threads), int(waves)), "mhd_set_launch")
+
+    def get_launch(self, kernel: str):
+        t, w = C.c_int(), C.c_int()
+        check(self.L.mhd_get_launch(self.h, self.TUNABLE.index(kernel), C.byref(t), C.byref(w)), "mhd_get_launch")
+        return t.value, w.value
 
     def read_stats(self, stream=None) -> dict:
         s = mhd_stats()

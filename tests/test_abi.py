@@ -3,6 +3,8 @@ exports every entry point that include/grmhd.h declares; host-side argument
 validation rejects bad input before any device work."""
 import ctypes as C
 
+import numpy as np
+
 import pytest
 
 from paper_2409_10384_gb300 import build, grmhd
@@ -47,3 +49,24 @@ def test_struct_layouts_match_header():
     assert C.sizeof(grmhd.mhd_params) == 8 * 8 + 6 * 4
     assert C.sizeof(grmhd.mhd_block) == 16 + 24 + 12 * 8
     assert C.sizeof(grmhd.mhd_stats) == 7 * 8
+
+
+def test_block_list_cache_follows_device_pointers():
+    """The binding's descriptor cache must follow the arrays, not Python object
+    ids: a block freed and replaced by a new one (which CPython may give the
+    same id) has to be described by the new block's pointers."""
+    import torch
+    from paper_2409_10384_gb300 import grmhd as G
+    ctx = G.Context.__new__(G.Context)   # the cache logic alone; no library context
+    ctx._arr, ctx._key, ctx._held = None, None, []
+    adm = np.zeros((16, 10, 10, 10))
+    for _ in range(20):
+        b = G.DeviceBlock((2, 2, 2), 4, (1.0, 1.0, 1.0), adm, device="cpu")
+        arr, nb = ctx._blocks([b])
+        assert nb == 1
+        assert arr[0].cons == b.cons.data_ptr() and arr[0].prim == b.prim.data_ptr()
+        assert arr[0].bf[2] == b.bf[2].data_ptr() and arr[0].flags == b.flags.data_ptr()
+        b.cons = torch.zeros_like(b.cons)   # replaced array inside a live block
+        arr, _ = ctx._blocks([b])
+        assert arr[0].cons == b.cons.data_ptr()
+        del b
