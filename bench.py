@@ -142,6 +142,30 @@ C2P_PARAMS = dict(gamma=2.0, rho_atm=1e-20, T_atm=1e-14, f_thr=0.0, sigma_max=0.
                   W_max=1e3, recon=2, rsolver=1, fofc=0, rk_order=3, c2p_maxit=64)
 
 
+def train_guess(ctx, samples=1 << 20, epochs=30):
+    """Train the context's con2prim guess network on stress cells (seed 104)
+    solved by the plain FP64 con2prim, calibrate the bracket half-width on a
+    disjoint set (seed 105, 95th percentile); (loss, delta, seconds)."""
+    import torch
+    from paper_2409_10384_gb300 import synth
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    t0 = time.perf_counter()
+    pr, Bd, g = synth.c2p_stress(samples, seed=104)
+    dB, dg, dp = t(Bd), t(g), t(pr)
+    dc = torch.zeros_like(dp)
+    ctx.prim2cons(dp, dB, dg, dc)
+    feat, logmu = ctx.mlp_dataset(dc, dB, dg)
+    ctx.mlp_init(3)
+    loss = ctx.mlp_train(feat, logmu, epochs=epochs, batch=4096, lr=3e-3)
+    pr, Bd, g = synth.c2p_stress(samples // 4, seed=105)
+    dB, dg, dp = t(Bd), t(g), t(pr)
+    dc = torch.zeros_like(dp)
+    ctx.prim2cons(dp, dB, dg, dc)
+    vf, vl = ctx.mlp_dataset(dc, dB, dg)
+    delta = ctx.mlp_calibrate(vf, vl, 0.95)
+    return loss, delta, time.perf_counter() - t0
+
+
 def c2p_leg(G, n=1 << 24, reps=5):
     """con2prim on n independent stress cells (rho, T, W, sigma log-uniform,
     perturbed metric): the plain KRP solve, the learned guess (network trained
@@ -151,22 +175,7 @@ def c2p_leg(G, n=1 << 24, reps=5):
     from paper_2409_10384_gb300 import synth
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     ctx = G.Context(G.params(**C2P_PARAMS, c2p_guess=0))
-    t0 = time.perf_counter()
-    pr, Bd, g = synth.c2p_stress(1 << 20, seed=104)
-    dB, dg, dp = t(Bd), t(g), t(pr)
-    dc = torch.zeros_like(dp)
-    ctx.prim2cons(dp, dB, dg, dc)
-    feat, logmu = ctx.mlp_dataset(dc, dB, dg)
-    ctx.mlp_init(3)
-    loss = ctx.mlp_train(feat, logmu, epochs=30, batch=4096, lr=3e-3)
-    pr, Bd, g = synth.c2p_stress(1 << 18, seed=105)
-    dB, dg, dp = t(Bd), t(g), t(pr)
-    dc = torch.zeros_like(dp)
-    ctx.prim2cons(dp, dB, dg, dc)
-    vf, vl = ctx.mlp_dataset(dc, dB, dg)
-    delta = ctx.mlp_calibrate(vf, vl, 0.95)
-    train_s = time.perf_counter() - t0
-    del feat, logmu, vf, vl
+    loss, delta, train_s = train_guess(ctx)
     # the test set, built on the device chunk by chunk
     cons0 = torch.empty((5, n), dtype=torch.float64, device="cuda")
     tB = torch.empty((3, n), dtype=torch.float64, device="cuda")
@@ -266,6 +275,97 @@ def amr_leg(G, steps=2):
     with torch.cuda.stream(stream):
         out["autotune"] = ctx.autotune(blocks, dt, stream=stream)
     run("tuned_graph", graph=True)
+    ctx.close()
+    return out
+
+
+# ---------------------------------------------------- binary-shaped leg
+
+def bns_leg(G, steps=3):
+    """The binary-shaped run: ~2000 32^3 blocks on 6 levels around two stars
+    at x = -+15 with v^y = -+0.15 (nested refinement shells), WENO-Z + HLLE +
+    FOFC + CT, SSP-RK3, every block in one batched launch per kernel captured
+    as a CUDA graph after the autotuner.  zone-cycles/s with the learned-guess
+    con2prim and, for comparison, the plain and FP32-search solves; then the
+    per-block baryon-mass balance over ``steps`` steps with the ledger on."""
+    import torch
+    from paper_2409_10384_gb300 import synth
+    specs, centres = synth.bns_blocks(seed=5)
+    st = synth.spacetime(5, centres=centres, vy=(-0.15, 0.15))
+    ctx = G.Context(G.params(**PARAMS, c2p_guess=0))
+    loss, delta, train_s = train_guess(ctx)
+    blocks = []
+    t0 = time.perf_counter()
+    for sp in specs:
+        inp = synth.star_block(st, (sp.n,) * 3, NG, (sp.dx,) * 3, sp.x0)
+        db = G.DeviceBlock(inp.n, inp.ng, inp.dx, inp.adm)
+        db.prim.copy_(torch.from_numpy(inp.prim))
+        ctx.init_block(db, [torch.from_numpy(a).cuda() for a in inp.A])
+        blocks.append(db)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    zones = sum(sp.n ** 3 for sp in specs)
+    dt = CFL * min(sp.dx for sp in specs)
+    levels = {}
+    for sp in specs:
+        levels[str(sp.level)] = levels.get(str(sp.level), 0) + 1
+    out = {"blocks": len(specs), "block_interior": 32, "levels": levels, "zones": zones, "stars": [list(c) for c in centres],
+           "vy": [-0.15, 0.15], "generate_s": gen_s,
+           "guess_network": {"loss": loss, "delta_q95": delta, "train_s": train_s}}
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    # every mode starts from the same initial state
+    snap = [(b.cons.clone(), [x.clone() for x in b.bf]) for b in blocks]
+
+    def restore():
+        for b, (c0, f0) in zip(blocks, snap):
+            b.cons.copy_(c0)
+            for x, y in zip(b.bf, f0):
+                x.copy_(y)
+        torch.cuda.synchronize()
+
+    for name, mode in (("learned", 1), ("plain", 0), ("fp32_search", 2)):
+        restore()
+        ctx.set_params(G.params(**PARAMS, c2p_guess=mode))
+        with torch.cuda.stream(stream):
+            if mode == 1:
+                out["autotune"] = ctx.autotune(blocks, dt, stream=stream)
+            ctx.step(blocks, dt, graph=True, stream=stream)
+            ctx.reset_stats(stream)
+            l0 = ctx.launches()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                ctx.step(blocks, dt, graph=True, stream=stream)
+            e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        sts = ctx.read_stats(stream)
+        out[name] = {"zone_cycles_per_s": zones / (ms * 1e-3), "ms_per_step": ms,
+                     "launches_per_step": (ctx.launches() - l0) // steps,
+                     "c2p_fp64_evals_per_cell": sts["iters"] / max(sts["cells"], 1),
+                     "c2p_fails": sts["fails"], "fofc_cells_per_step": sts["fofc_cells"] / steps}
+    # baryon-mass balance per block and step (learned guess, graph launches)
+    restore()
+    del snap
+    ctx.set_params(G.params(**PARAMS, c2p_guess=1))
+    ctx.ledger(True)
+    res = []
+    glob = []
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            m0 = ctx.block_mass(blocks, stream)
+            ctx.step(blocks, dt, graph=True, stream=stream)
+            m1 = ctx.block_mass(blocks, stream)
+            bal = ctx.ledger_read(len(blocks), reset=True, stream=stream)
+            res.append(np.abs(m1 - m0 - bal) / np.abs(m0))
+            glob.append(abs((m1 - m0 - bal).sum()) / m0.sum())
+    ctx.ledger(False)
+    r = np.concatenate(res)
+    out["mass_balance"] = {"steps": steps, "per_block_max": float(r.max()), "per_block_median": float(np.median(r)),
+                           "global_max": float(max(glob)), "definition":
+                           "|M_after - M_before - (floor mass - dt sum_s b_s boundary D~ flux)| / M_before per block "
+                           "and RK3 step; global: summed over blocks / total mass"}
     ctx.close()
     return out
 
@@ -440,6 +540,10 @@ def run_ours(args):
         line["c2p"] = c2p_leg(G)
     if not args.no_amr and world == 1:
         line["amr512"] = amr_leg(G)
+        torch.cuda.empty_cache()
+    if not args.no_bns and world == 1:
+        line["bns"] = bns_leg(G)
+        torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_baseline:
         line["cpu_baseline"] = oracle_sample()
     if rank == 0:
@@ -461,6 +565,7 @@ def main():
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU-oracle leg (profiling cases)")
     ap.add_argument("--no-c2p", action="store_true", help="skip the con2prim stress leg (profiling cases)")
     ap.add_argument("--no-amr", action="store_true", help="skip the batched AMR leg (profiling cases)")
+    ap.add_argument("--no-bns", action="store_true", help="skip the binary-shaped leg (profiling cases)")
     args = ap.parse_args()
     global N_INT
     N_INT = args.n

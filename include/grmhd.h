@@ -62,7 +62,13 @@ typedef struct {
   int fofc;         /* 1: first-order flux correction (Sec. 3.3) */
   int rk_order;     /* 2 or 3: SSP-RK (Sec. 3.2) */
   int c2p_maxit;    /* cap on root-solve iterations (64) */
-  int c2p_guess;    /* 0 plain bracket, 1 learned bracket (needs a network) */
+  int c2p_guess;    /* root search of every con2prim (cells, stage input, FOFC U*):
+                       0 FP64 Illinois on the plain bracket [0, mu+];
+                       1 network guess of log(mu), FP32 secant steps, FP64 bracket
+                         of relative width 4e-6 around the FP32 root, FP64 solve
+                         (needs a network: MHD_ENOMLP otherwise);
+                       2 as 1 but the FP32 steps start from the plain bracket.
+                       The FP64 solve decides the root in every mode. */
 } mhd_params;
 
 /* One meshblock: views into caller-owned device arrays. */
@@ -175,6 +181,27 @@ int mhd_scratch_copy(mhd_ctx* ctx, int b, int which, double* dst, long count, lo
  * kernels it contains). */
 long long mhd_kernel_launches(const mhd_ctx* ctx);
 
+/* Baryon-mass ledger (a diagnostic, off by default).  The paper reports
+ * baryon-mass conservation to ~1e-11 through collapse (Sec. 4); with the
+ * ledger on, every RK stage folds, per block, the interior D~ dV that the
+ * stage's con2prim floors wrote (weight 1 in the first stage, where it becomes
+ * part of U^n, else the stage weight b_s) and -dt b_s times the outward D~ flux
+ * through the block's interior boundary (after FOFC), integrated over the face
+ * areas, into a running balance.  b_s = (1/6, 1/6, 2/3) for SSP-RK3 and
+ * (1/2, 1/2) for RK2: the weights with which each stage's L(U) enters
+ * U^{n+1}.  Over full steps, mass(after) - mass(before) - balance is then the
+ * round-off of the update alone.
+ * mhd_ledger: switch on/off; the next call re-plans the scratch, and a new
+ * block list starts from a zero balance.
+ * mhd_ledger_read: host out[nblocks] = the balance of each block of the last
+ * list since the last reset (reset != 0 zeroes it).  MHD_ESTATE when the
+ * ledger is off or no list was run.  Synchronises the stream.
+ * mhd_block_mass: host out[nblocks] = sum over interior cells of D~ dx dy dz.
+ * Synchronises the stream. */
+int mhd_ledger(mhd_ctx* ctx, int enable);
+int mhd_ledger_read(mhd_ctx* ctx, double* out, int reset, void* stream);
+int mhd_block_mass(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, double* out, void* stream);
+
 /* Kernel kinds for per-kernel timing. */
 #define MHD_K_C2P 0        /* con2prim of the stencil region (prep + finish) */
 #define MHD_K_FLUX_X 1     /* reconstruction + Riemann flux, x faces */
@@ -187,7 +214,8 @@ long long mhd_kernel_launches(const mhd_ctx* ctx);
 #define MHD_K_FACEB 8      /* RK update of the face B~ */
 #define MHD_K_SOLVE 9      /* con2prim root solves (stage input and U*) */
 #define MHD_K_MLP 10       /* learned-guess network inference */
-#define MHD_NKERNEL 11
+#define MHD_K_LEDGER 11    /* baryon-mass ledger (only with mhd_ledger on) */
+#define MHD_NKERNEL 12
 
 /* enable != 0: bracket every kernel launched outside stream capture by CUDA
  * events on its own stream.  mhd_profile_read waits for them and returns, per
@@ -201,9 +229,9 @@ const char* mhd_kernel_name(int kind);
  * library).  A 5 -> 64 -> 64 -> 1 tanh network with BF16 operands and FP32
  * accumulation on the tensor cores predicts log(mu) of the Kastaun et al. root
  * from five features of the cell's KRP variables; with mhd_params.c2p_guess = 1
- * mhd_c2p_cells evaluates the FP64 function at the guess, steps by a factor
- * exp(+-delta) towards the root to close a bracket (falling back to [0, .] or
- * [., 1]) and solves as before: same root, fewer FP64 iterations.
+ * every con2prim starts FP32 secant steps at the guess (second point at
+ * exp(delta) x guess), brackets their result in FP64 (relative width 4e-6,
+ * else out to 0 or 1) and solves as before: same root, fewer FP64 iterations.
  * Features: float [n][MHD_MLP_FSTRIDE] (5 used); targets: float log(mu) [n].
  * State (get/set): MHD_MLP_NPARAM fp32 parameters (W1 [64][5], b1, W2
  * [64][64], b2, w3, b3), then feature mean [5], feature 1/std [5], target

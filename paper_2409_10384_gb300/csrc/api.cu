@@ -50,6 +50,13 @@ struct mhd_ctx {
   } cfg[T_N];
   int occ_t[T_N][3] = {{0}};   // occupancy at 64, 128, 256 threads
   long long* dpre_blk = nullptr;  // per-block work tables [nb][W_NKIND][2] (per-block launches)
+  // block-list scratch of the guessed con2prim (c2p_guess 1, 2): features, log(mu)
+  float* gfeat = nullptr;
+  float* glogmu = nullptr;
+  // baryon-mass ledger [nb][2] (lf, la) and per-block mass sums [nb]
+  bool ledger_on = false;
+  double* dledger = nullptr;
+  double* dmass = nullptr;
   int g_solve_cells() const { return nsm * (occ_krp[1] > 0 ? occ_krp[1] : 1); }
   // counters
   unsigned long long* dstats = nullptr;
@@ -190,6 +197,17 @@ int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
   const long long nkrp = std::max(pre[(size_t)W_C2P * (nb + 1) + nb], pre[(size_t)W_CELL * (nb + 1) + nb]);
   const size_t krp_off = need;
   need += al256(krp_bytes(nkrp));
+  size_t feat_off = 0, logmu_off = 0;
+  if (c->P.guess != 0) {
+    feat_off = need;
+    need += al256(sizeof(float) * MLP_FSTRIDE * (size_t)nkrp);
+    logmu_off = need;
+    need += al256(sizeof(float) * (size_t)nkrp);
+  }
+  const size_t mass_off = need;
+  need += al256(sizeof(double) * (size_t)nb);
+  const size_t led_off = need;
+  if (c->ledger_on) need += al256(sizeof(double) * 2 * (size_t)nb);
   if (need > c->scratch_bytes) {
     if (c->scratch) cudaFree(c->scratch);
     c->scratch = nullptr;
@@ -220,6 +238,18 @@ int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
   }
   c->krp = c->scratch + krp_off;
   c->krp_n = nkrp;
+  c->gfeat = c->P.guess != 0 ? (float*)(c->scratch + feat_off) : nullptr;
+  c->glogmu = c->P.guess != 0 ? (float*)(c->scratch + logmu_off) : nullptr;
+  c->dmass = (double*)(c->scratch + mass_off);
+  c->dledger = c->ledger_on ? (double*)(c->scratch + led_off) : nullptr;
+  if (c->dledger && cudaMemset(c->dledger, 0, sizeof(double) * 2 * (size_t)nb) != cudaSuccess) return MHD_ECUDA;
+  for (int i = 0; i < nb; i++) {
+    DevBlock& b = hb[i];
+    b.id = i;
+    b.dV = b.dx[0] * b.dx[1] * b.dx[2];
+    b.lf = c->dledger ? c->dledger + 2 * (size_t)i : nullptr;
+    b.la = c->dledger ? c->dledger + 2 * (size_t)i + 1 : nullptr;
+  }
   if (c->dblk) cudaFree(c->dblk);
   if (c->dpre) cudaFree(c->dpre);
   if (c->dpre_blk) cudaFree(c->dpre_blk);
@@ -326,13 +356,32 @@ Work work_of(const mhd_ctx* c) {
 
 // One launch sequence over the work `w` with `items[W_NKIND]` items per kind
 // (all blocks of the list, or one block for per-block launches).
+// Between the prep and the FP64 root solve of a guessed con2prim (c2p_guess 1:
+// network guess; 2: FP32 search from the plain bracket): network inference on
+// the prep's features and the FP32 seed search that turns status-4 cells into
+// FP64 brackets.
+void c2p_seed(mhd_ctx* c, const KrpBuf& kb, long long n, cudaStream_t s) {
+  const int mode = c->P.guess;
+  if (mode == 0) return;
+  if (mode == 1)
+    timed(c, MHD_K_MLP, s, [&] { launch_mlp_infer(c->gfeat, n, c->nm, c->mlp_wb, c->mlp, c->glogmu, s, c->nsm); });
+  const long long g = std::max(1LL, std::min((n + 127) / 128, (long long)c->nsm * std::max(c->occ_krp[5], 1)));
+  timed(c, MHD_K_C2P, s, [&] {
+    launch_krp_seed(c->P, kb, c->glogmu, mode == 1 ? 1 : 0, (float)c->mlp_delta, s, (int)g);
+  });
+}
+
 int enqueue_c2p(mhd_ctx* c, cudaStream_t s, const Work& w, const long long* items) {
+  if (c->P.guess == 1 && !c->mlp_ready) return MHD_ENOMLP;
   KrpBuf kb = krp_view(c->krp, items[W_C2P]);
   const mhd_ctx::Cfg& cp = c->cfg[T_C2P_PREP];
   const mhd_ctx::Cfg& cf = c->cfg[T_C2P_FIN];
+  const int learned = c->P.guess != 0 ? 1 : 0;
+  float* feat = c->P.guess == 1 ? c->gfeat : nullptr;
   timed(c, MHD_K_C2P, s, [&] {
-    launch_krp_prep_block(w, c->P, kb, s, tgrid(c, T_C2P_PREP, items[W_C2P]), cp.threads);
+    launch_krp_prep_block(w, c->P, kb, s, tgrid(c, T_C2P_PREP, items[W_C2P]), cp.threads, learned, feat);
   });
+  c2p_seed(c, kb, items[W_C2P], s);
   timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, c->dstats, s, c->g_solve); });
   timed(c, MHD_K_C2P, s, [&] {
     launch_krp_finish_block(w, c->P, kb, c->dstats, s, tgrid(c, T_C2P_FIN, items[W_C2P]), cf.threads);
@@ -348,11 +397,14 @@ int enqueue_rhs(mhd_ctx* c, double dt, int stage, cudaStream_t s, const Work& w,
       launch_flux_dir(d, w, c->P, s, tgrid(c, T_FX + d, items[W_SX + d]), c->cfg[T_FX + d].threads);
     });
   if (c->P.fofc) {
+    if (c->P.guess == 1 && !c->mlp_ready) return MHD_ENOMLP;
     KrpBuf kb = krp_view(c->krp, items[W_CELL]);
     timed(c, MHD_K_FOFC_FLAG, s, [&] {
       launch_krp_prep_fofc(w, c->P, g0, g1, be * dt, kb, s, tgrid(c, T_FOFC_PREP, items[W_CELL]),
-                           c->cfg[T_FOFC_PREP].threads);
+                           c->cfg[T_FOFC_PREP].threads, c->P.guess != 0 ? 1 : 0,
+                           c->P.guess == 1 ? c->gfeat : nullptr);
     });
+    c2p_seed(c, kb, items[W_CELL], s);
     timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, c->dstats, s, c->g_solve); });
     timed(c, MHD_K_FOFC_FLAG, s, [&] {
       launch_krp_finish_fofc(w, c->P, kb, c->dstats, s, tgrid(c, T_FOFC_FIN, items[W_CELL]),
@@ -362,6 +414,12 @@ int enqueue_rhs(mhd_ctx* c, double dt, int stage, cudaStream_t s, const Work& w,
       long long g = std::min<long long>((items[W_FX + d] + 127) / 128, (long long)c->nsm * c->occ_face[4]);
       timed(c, MHD_K_FOFC_FIX, s, [&] { launch_fofc_fix(d, w, c->P, c->dstats, s, (int)std::max(1LL, g)); });
     }
+  }
+  if (c->ledger_on) {
+    // weight of this stage's L(U) in U^{n+1}; the floor mass of stage 0 enters U^n itself
+    const double b3[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0}, b2[2] = {0.5, 0.5};
+    const double bs = c->P.rk_order == 3 ? b3[stage] : b2[stage];
+    timed(c, MHD_K_LEDGER, s, [&] { launch_ledger_stage(w, stage == 0 ? 1.0 : bs, dt * bs, s); });
   }
   timed(c, MHD_K_EMF, s, [&] {
     launch_emf(w, s, tgrid(c, T_EMF, items[W_EDGE]), c->cfg[T_EMF].threads);
@@ -487,9 +545,50 @@ int mhd_init(const mhd_params* p, mhd_ctx** out) {
 
 int mhd_set_params(mhd_ctx* c, const mhd_params* p) {
   if (!c) return MHD_EINVAL;
+  const int old_guess = c->P.guess;
   int r = set_par(c, p);
   if (!r) destroy_graph(c);
+  if (!r && (old_guess != 0) != (c->P.guess != 0)) {
+    cudaDeviceSynchronize();
+    c->key.clear();   // the next call re-plans the scratch (guess buffers)
+  }
   return r;
+}
+
+int mhd_ledger(mhd_ctx* c, int enable) {
+  if (!c) return MHD_EINVAL;
+  if (c->ledger_on != (enable != 0)) {
+    cudaDeviceSynchronize();
+    c->ledger_on = enable != 0;
+    c->key.clear();
+    destroy_graph(c);
+  }
+  return MHD_OK;
+}
+
+int mhd_ledger_read(mhd_ctx* c, double* out, int reset, void* stream) {
+  if (!c || !out) return MHD_EINVAL;
+  if (!c->ledger_on || !c->dledger || c->key.empty()) return MHD_ESTATE;
+  const size_t nb = c->key.size();
+  std::vector<double> h(2 * nb);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(h.data(), c->dledger, sizeof(double) * 2 * nb, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return MHD_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ECUDA;
+  for (size_t i = 0; i < nb; i++) out[i] = h[2 * i + 1];
+  if (reset && cudaMemsetAsync(c->dledger, 0, sizeof(double) * 2 * nb, s) != cudaSuccess) return MHD_ECUDA;
+  return MHD_OK;
+}
+
+int mhd_block_mass(mhd_ctx* c, const mhd_block* blocks, int nb, double* out, void* stream) {
+  if (!c || !out) return MHD_EINVAL;
+  int r = prepare(c, blocks, nb);
+  if (r) return r;
+  cudaStream_t s = (cudaStream_t)stream;
+  launch_block_mass(work_of(c), c->dmass, s);
+  c->launches += 1;
+  if (cudaMemcpyAsync(out, c->dmass, sizeof(double) * nb, cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ECUDA;
+  return cuda_ok(cudaStreamSynchronize(s));
 }
 
 void mhd_finalize(mhd_ctx* c) {
@@ -948,13 +1047,17 @@ int mhd_autotune(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, void* s
     auto launch = [&]() {
       const int th = c->cfg[k].threads;
       switch (k) {
-        case T_C2P_PREP: launch_krp_prep_block(w, c->P, kb, s, tgrid(c, k, it[W_C2P]), th); break;
+        case T_C2P_PREP:
+          launch_krp_prep_block(w, c->P, kb, s, tgrid(c, k, it[W_C2P]), th, c->P.guess != 0 ? 1 : 0,
+                                c->P.guess == 1 ? c->gfeat : nullptr);
+          break;
         case T_C2P_FIN: launch_krp_finish_block(w, c->P, kb, c->dstats, s, tgrid(c, k, it[W_C2P]), th); break;
         case T_FX: case T_FY: case T_FZ:
           launch_flux_dir(k - T_FX, w, c->P, s, tgrid(c, k, it[W_SX + k - T_FX]), th);
           break;
         case T_FOFC_PREP:
-          launch_krp_prep_fofc(w, c->P, g0, g1, be * dt, kb, s, tgrid(c, k, it[W_CELL]), th);
+          launch_krp_prep_fofc(w, c->P, g0, g1, be * dt, kb, s, tgrid(c, k, it[W_CELL]), th, c->P.guess != 0 ? 1 : 0,
+                               c->P.guess == 1 ? c->gfeat : nullptr);
           break;
         case T_FOFC_FIN: launch_krp_finish_fofc(w, c->P, kb, c->dstats, s, tgrid(c, k, it[W_CELL]), th); break;
         case T_EMF: launch_emf(w, s, tgrid(c, k, it[W_EDGE]), th); break;
@@ -979,6 +1082,7 @@ int mhd_autotune(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, void* s
     c->cfg[k] = best;
     if (k == T_C2P_PREP || k == T_FOFC_PREP) {
       launch();
+      c2p_seed(c, kb, fofc_k ? it[W_CELL] : it[W_C2P], s);
       launch_krp_solve(c->P, kb, c->dstats, s, c->g_solve);
     }
     if (cfg_out) {
@@ -1039,7 +1143,7 @@ int mhd_profile_read(mhd_ctx* c, double* ms, long long* count) {
 
 const char* mhd_kernel_name(int kind) {
   static const char* names[MHD_NKERNEL] = {"c2p", "flux_x", "flux_y", "flux_z", "fofc_flag",
-                                           "fofc_fix", "emf", "update", "faceb", "c2p_solve", "mlp"};
+                                           "fofc_fix", "emf", "update", "faceb", "c2p_solve", "mlp", "ledger"};
   return (kind >= 0 && kind < MHD_NKERNEL) ? names[kind] : "unknown";
 }
 

@@ -38,6 +38,11 @@ struct DevBlock {
   double* emf[3];    // edge arrays E_x, E_y, E_z
   double* ecc;       // [3][ncell] cell-centred E = -alpha (vhat x B~)
   unsigned char* fflag;  // [ncell] FOFC flag of the current stage
+  // baryon-mass ledger (null when off): interior D~ dV added by the floors
+  // of the last con2prim (lf) and the running RK-weighted balance (la)
+  double *lf, *la;
+  double dV;         // cell volume dx dy dz
+  int id;            // index of the block in its list
 };
 
 // Work lists: item ranges of every block for one kernel kind.

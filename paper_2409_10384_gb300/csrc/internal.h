@@ -19,15 +19,21 @@ void launch_fofc_fix(int d, const Work& w, const Par& P, unsigned long long* sta
 void launch_emf(const Work& w, cudaStream_t s, int grid, int threads = 128);
 void launch_update_cells(const Work& w, const Par& P, double g0, double g1, double bdt, int first, cudaStream_t s,
                          int grid, int threads = 128);
+// baryon-mass ledger: fold the floor mass of the last con2prim (weight wF)
+// and -dtb x the outward boundary D~ flux of the stage into each block's
+// balance; interior mass sum D~ dV of each block into out[id]
+void launch_ledger_stage(const Work& w, double wF, double dtb, cudaStream_t s);
+void launch_block_mass(const Work& w, double* out, cudaStream_t s);
 void launch_update_faces(const Work& w, double g0, double g1, double bdt, int first, cudaStream_t s, int grid);
 size_t krp_bytes(long long n);
 KrpBuf krp_view(void* base, long long n);
-void launch_krp_prep_block(const Work& w, const Par& P, const KrpBuf& kb, cudaStream_t s, int grid, int threads = 128);
+void launch_krp_prep_block(const Work& w, const Par& P, const KrpBuf& kb, cudaStream_t s, int grid, int threads = 128,
+                           int learned = 0, float* feat = nullptr);
 void launch_krp_solve(const Par& P, const KrpBuf& kb, unsigned long long* stats, cudaStream_t s, int grid);
 void launch_krp_finish_block(const Work& w, const Par& P, const KrpBuf& kb, unsigned long long* stats,
                              cudaStream_t s, int grid, int threads = 128);
 void launch_krp_prep_fofc(const Work& w, const Par& P, double g0, double g1, double bdt, const KrpBuf& kb,
-                          cudaStream_t s, int grid, int threads = 128);
+                          cudaStream_t s, int grid, int threads = 128, int learned = 0, float* feat = nullptr);
 void launch_krp_finish_fofc(const Work& w, const Par& P, const KrpBuf& kb, unsigned long long* stats,
                             cudaStream_t s, int grid, int threads = 128);
 void launch_krp_prep_cells(const Par& P, const KrpBuf& kb, const double* cons, const double* Bd, const double* g,

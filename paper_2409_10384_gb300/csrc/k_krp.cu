@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(256) k_krp_solve(Par P, KrpBuf kb, unsigned lo
 }
 
 // -------------------------------------------------------- block stage con2prim
-__global__ void __launch_bounds__(256) k_krp_prep_block(Work w, Par P, KrpBuf kb) {
+__global__ void __launch_bounds__(256) k_krp_prep_block(Work w, Par P, KrpBuf kb, int learned, float* feat) {
   const long long* pre = w.pre + (long long)W_C2P * (w.nblocks + 1);
   const long long tot = pre[w.nblocks];
   if (blockIdx.x == 0 && threadIdx.x == 0) *kb.ctr = 0ull;
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(256) k_krp_prep_block(Work w, Par P, KrpBuf kb
     double U[5];
 #pragma unroll
     for (int v = 0; v < 5; v++) U[v] = b.cons[v * nc + c];
-    prep_cell(P, kb, it, U, Bd, m);
+    prep_cell(P, kb, it, U, Bd, m, learned != 0, feat);
   }
 }
 
@@ -214,8 +214,11 @@ __global__ void __launch_bounds__(256) k_krp_finish_block(Work w, Par P, KrpBuf 
     if (fl & (FLOOR_BITS | F_FAIL)) {
       double U[5];
       prim2cons(P, pr, Bd, m, U);
+      const double D0 = b.cons[c];
 #pragma unroll
       for (int v = 0; v < 5; v++) b.cons[v * nc + c] = U[v];
+      const bool inner = ii >= 3 && ii < b.n[0] + 3 && jj >= 3 && jj < b.n[1] + 3 && kk >= 3 && kk < b.n[2] + 3;
+      if (b.lf && inner && U[0] != D0) atomicAdd(b.lf, (U[0] - D0) * b.dV);
     }
     b.flags[c] = (unsigned char)fl;
     if (ii >= 2 && ii <= b.n[0] + 3 && jj >= 2 && jj <= b.n[1] + 3 && kk >= 2 && kk <= b.n[2] + 3) {
@@ -248,7 +251,8 @@ __device__ __forceinline__ void fofc_cell(const Work& w, long long it, int& bi, 
   i += b.ng; j += b.ng; k += b.ng;
 }
 
-__global__ void __launch_bounds__(256) k_krp_prep_fofc(Work w, Par P, double g0, double g1, double bdt, KrpBuf kb) {
+__global__ void __launch_bounds__(256) k_krp_prep_fofc(Work w, Par P, double g0, double g1, double bdt, KrpBuf kb,
+                                                        int learned, float* feat) {
   const long long tot = w.pre[(long long)W_CELL * (w.nblocks + 1) + w.nblocks];
   if (blockIdx.x == 0 && threadIdx.x == 0) *kb.ctr = 0ull;
   const long long n = kb.n;
@@ -273,7 +277,7 @@ __global__ void __launch_bounds__(256) k_krp_prep_fofc(Work w, Par P, double g0,
     Metric m;
     load_metric6(b.adm + 4 * nc, nc, c, m);
     const double Bd[3] = {b.bcc[c], b.bcc[nc + c], b.bcc[2 * nc + c]};
-    prep_cell(P, kb, it, U, Bd, m);
+    prep_cell(P, kb, it, U, Bd, m, learned != 0, feat);
     kb.w[KW_USD * n + it] = U[0];
     kb.w[KW_UST * n + it] = U[4];
   }
@@ -400,8 +404,9 @@ KrpBuf krp_view(void* base, long long n) {
   return kb;
 }
 
-void launch_krp_prep_block(const Work& w, const Par& P, const KrpBuf& kb, cudaStream_t s, int grid, int threads) {
-  k_krp_prep_block<<<grid, threads, 0, s>>>(w, P, kb);
+void launch_krp_prep_block(const Work& w, const Par& P, const KrpBuf& kb, cudaStream_t s, int grid, int threads,
+                           int learned, float* feat) {
+  k_krp_prep_block<<<grid, threads, 0, s>>>(w, P, kb, learned, feat);
 }
 void launch_krp_solve(const Par& P, const KrpBuf& kb, unsigned long long* stats, cudaStream_t s, int grid) {
   k_krp_solve<<<grid, 256, 0, s>>>(P, kb, stats);
@@ -411,8 +416,8 @@ void launch_krp_finish_block(const Work& w, const Par& P, const KrpBuf& kb, unsi
   k_krp_finish_block<<<grid, threads, 0, s>>>(w, P, kb, stats);
 }
 void launch_krp_prep_fofc(const Work& w, const Par& P, double g0, double g1, double bdt, const KrpBuf& kb,
-                          cudaStream_t s, int grid, int threads) {
-  k_krp_prep_fofc<<<grid, threads, 0, s>>>(w, P, g0, g1, bdt, kb);
+                          cudaStream_t s, int grid, int threads, int learned, float* feat) {
+  k_krp_prep_fofc<<<grid, threads, 0, s>>>(w, P, g0, g1, bdt, kb, learned, feat);
 }
 void launch_krp_finish_fofc(const Work& w, const Par& P, const KrpBuf& kb, unsigned long long* stats,
                             cudaStream_t s, int grid, int threads) {

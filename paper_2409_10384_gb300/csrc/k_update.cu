@@ -220,4 +220,75 @@ int occupancy_update(int* per_sm) {
   return e == cudaSuccess ? 0 : -1;
 }
 
+
+// ------------------------------------------------------ baryon-mass ledger
+// Block-wide sum of one double per thread (blockDim a multiple of 32, <= 1024).
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += sh[k];
+  return t;
+}
+
+// One CTA per block: the outward D~ flux through the block's interior
+// boundary, integrated over the face areas, folded into the balance:
+//   la += wF * lf - dtb * Phi,   lf = 0.
+__global__ void __launch_bounds__(256) k_ledger_stage(Work w, double wF, double dtb) {
+  __shared__ double sh[32];
+  const DevBlock& b = w.blk[blockIdx.x];
+  if (!b.la) return;
+  const int g = b.ng, n0 = b.n[0], n1 = b.n[1], n2 = b.n[2];
+  const long long m0 = (long long)n1 * n2, m1 = (long long)n0 * n2, m2 = (long long)n0 * n1;
+  const double A0 = b.dx[1] * b.dx[2], A1 = b.dx[0] * b.dx[2], A2 = b.dx[0] * b.dx[1];
+  double phi = 0.0;
+  for (long long q = threadIdx.x; q < 2 * (m0 + m1 + m2); q += blockDim.x) {
+    long long r = q;
+    int d = 0;
+    if (r >= 2 * m0) { r -= 2 * m0; d = 1; if (r >= 2 * m1) { r -= 2 * m1; d = 2; } }
+    const long long m = d == 0 ? m0 : (d == 1 ? m1 : m2);
+    const bool hi = r >= m;
+    if (hi) r -= m;
+    int i, j, k;
+    if (d == 0) { j = g + (int)(r % n1); k = g + (int)(r / n1); i = g + (hi ? n0 : 0); }
+    else if (d == 1) { i = g + (int)(r % n0); k = g + (int)(r / n0); j = g + (hi ? n1 : 0); }
+    else { i = g + (int)(r % n0); j = g + (int)(r / n0); k = g + (hi ? n2 : 0); }
+    const double F = b.flux[d][fidx(b, d, k, j, i)];   // component 0: D~
+    const double A = d == 0 ? A0 : (d == 1 ? A1 : A2);
+    phi += (hi ? F : -F) * A;
+  }
+  phi = block_sum(phi, sh);
+  if (threadIdx.x == 0) {
+    *b.la += wF * *b.lf - dtb * phi;
+    *b.lf = 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_block_mass(Work w, double* out) {
+  __shared__ double sh[32];
+  const DevBlock& b = w.blk[blockIdx.x];
+  const int g = b.ng, n0 = b.n[0], n1 = b.n[1];
+  const long long tot = (long long)n0 * n1 * b.n[2];
+  double s = 0.0;
+  for (long long q = threadIdx.x; q < tot; q += blockDim.x) {
+    const int i = g + (int)(q % n0);
+    const long long r = q / n0;
+    const int j = g + (int)(r % n1), k = g + (int)(r / n1);
+    s += b.cons[cidx(b, k, j, i)];
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) out[b.id] = s * b.dV;
+}
+
+void launch_ledger_stage(const Work& w, double wF, double dtb, cudaStream_t s) {
+  k_ledger_stage<<<w.nblocks, 256, 0, s>>>(w, wF, dtb);
+}
+void launch_block_mass(const Work& w, double* out, cudaStream_t s) {
+  k_block_mass<<<w.nblocks, 256, 0, s>>>(w, out);
+}
+
 }  // namespace grmhd

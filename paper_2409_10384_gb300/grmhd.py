@@ -77,6 +77,9 @@ _SIGS = {
     "mhd_stage_noalloc": (_I, [C.POINTER(mhd_params), C.POINTER(mhd_block), _D, _I, _VP]),
     "mhd_autotune": (_I, [_VP, C.POINTER(mhd_block), _I, _D, _VP, _VP]),
     "mhd_set_launch": (_I, [_VP, _I, _I, _I]),
+    "mhd_ledger": (_I, [_VP, _I]),
+    "mhd_ledger_read": (_I, [_VP, C.POINTER(C.c_double), _I, _VP]),
+    "mhd_block_mass": (_I, [_VP, C.POINTER(mhd_block), _I, C.POINTER(C.c_double), _VP]),
     "mhd_get_launch": (_I, [_VP, _I, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "mhd_mlp_init": (_I, [_VP, C.c_ulonglong]),
     "mhd_mlp_dataset": (_I, [_VP, _L, _VP, _VP, _VP, _VP, _VP, _VP]),
@@ -87,7 +90,7 @@ _SIGS = {
     "mhd_mlp_get": (_I, [_VP, _VP]),
     "mhd_mlp_set": (_I, [_VP, _VP]),
 }
-MHD_NKERNEL = 11
+MHD_NKERNEL = 12
 MLP_NPARAM = 4609
 MLP_NSTATE = 4609 + 13
 MLP_FSTRIDE = 8
@@ -326,6 +329,28 @@ class Context:
         t, w = C.c_int(), C.c_int()
         check(self.L.mhd_get_launch(self.h, self.TUNABLE.index(kernel), C.byref(t), C.byref(w)), "mhd_get_launch")
         return t.value, w.value
+
+    # --------------------------------------------------- baryon-mass ledger
+    def ledger(self, enable: bool = True):
+        """Switch the per-block baryon-mass ledger on or off."""
+        check(self.L.mhd_ledger(self.h, 1 if enable else 0), "mhd_ledger")
+        self._key = None   # the library re-plans its scratch on the next call
+
+    def ledger_read(self, nblocks: int, reset=False, stream=None) -> np.ndarray:
+        """Balance of each block since the last reset: floor mass plus
+        -dt b_s x boundary D~ flux, summed over stages with RK weights."""
+        out = np.zeros(nblocks)
+        check(self.L.mhd_ledger_read(self.h, out.ctypes.data_as(C.POINTER(C.c_double)), 1 if reset else 0,
+                                     _sptr(stream)), "mhd_ledger_read")
+        return out
+
+    def block_mass(self, blocks, stream=None) -> np.ndarray:
+        """Interior sum of D~ dx dy dz of every block."""
+        arr, nb = self._blocks(blocks)
+        out = np.zeros(nb)
+        check(self.L.mhd_block_mass(self.h, arr, nb, out.ctypes.data_as(C.POINTER(C.c_double)), _sptr(stream)),
+              "mhd_block_mass")
+        return out
 
     def read_stats(self, stream=None) -> dict:
         s = mhd_stats()

@@ -313,32 +313,43 @@ def amr_blocks(seed: int = 3, counts=((16, 293), (32, 146), (64, 73)), levels: i
 
 def bns_blocks(seed: int = 5, n: int = 32, levels: int = 6, dx0: float = 0.75, L: float = 96.0,
                target: int = 2000, sep: float = 15.0):
-    """Octree-style refinement of a two-star configuration (stars at x = +-sep):
-    a block of level l is refined while it meets rho > 1e-6 or lies within
-    r < 2^(5-l) 8 of a star, until about ``target`` leaf blocks."""
-    S = STAR
-    rcut = S["width"] * np.sqrt(np.log(S["rho_c"] / 1e-6))
+    """Block layout shaped like the paper's binary runs (Sec. 4.5, 5): 32^3
+    blocks on 6 levels over [-L/2, L/2]^3, two stars at x = -+sep.  A block of
+    level l is refined when its box comes within R_l = s 2^(5-l) 8 of a star
+    centre (nested refinement shells around each star); the scale s is the
+    largest (by bisection) whose leaf count does not exceed ``target``.
+    Returns (leaf BlockSpecs, star centres); ``seed`` is unused (the layout
+    is deterministic) and kept for the config-index convention."""
     centres = ((-sep, 0.0, 0.0), (sep, 0.0, 0.0))
     nb0 = int(round(L / (n * dx0)))
-    leaves = []
-    stack = [(0, (i, j, k)) for i in range(nb0) for j in range(nb0) for k in range(nb0)]
-    while stack:
-        lev, (i, j, k) = stack.pop()
-        dx = dx0 / 2 ** lev
-        ext = n * dx
-        x0 = (-L / 2 + i * ext, -L / 2 + j * ext, -L / 2 + k * ext)
-        refine = False
-        if lev < levels - 1:
-            for c in centres:
-                # distance from the star centre to the block box
-                d2 = sum(max(c[a] - (x0[a] + ext), 0.0, x0[a] - c[a]) ** 2 for a in range(3))
-                if d2 < max(rcut, 2 ** (5 - lev) * 8.0) ** 2 / 4 ** (lev // 2 + 1) * 4:
-                    refine = True
-        if refine and len(leaves) + len(stack) < target:
-            for ci in range(2):
-                for cj in range(2):
-                    for ck in range(2):
-                        stack.append((lev + 1, (2 * i + ci, 2 * j + cj, 2 * k + ck)))
+
+    def layout(scale):
+        leaves = []
+        stack = [(0, (i, j, k)) for k in range(nb0) for j in range(nb0) for i in range(nb0)]
+        while stack:
+            lev, (i, j, k) = stack.pop()
+            dx = dx0 / 2 ** lev
+            ext = n * dx
+            x0 = (-L / 2 + i * ext, -L / 2 + j * ext, -L / 2 + k * ext)
+            R = scale * 2 ** (levels - 1 - lev) * 8.0
+            near = any(sum(max(c[a] - (x0[a] + ext), 0.0, x0[a] - c[a]) ** 2 for a in range(3)) < R * R
+                       for c in centres)
+            if lev < levels - 1 and near:
+                for ck in range(2):
+                    for cj in range(2):
+                        for ci in range(2):
+                            stack.append((lev + 1, (2 * i + ci, 2 * j + cj, 2 * k + ck)))
+            else:
+                leaves.append(BlockSpec(n, lev, x0, dx))
+        return leaves
+
+    lo, hi = 0.0, 1.0
+    best = layout(lo)
+    for _ in range(40):
+        mid = 0.5 * (lo + hi)
+        cand = layout(mid)
+        if len(cand) <= target:
+            lo, best = mid, cand
         else:
-            leaves.append(BlockSpec(n, lev, x0, dx))
-    return leaves, centres
+            hi = mid
+    return best, centres
