@@ -42,6 +42,23 @@ CFL = 0.25
 FLOPS_PER_UNIT = {"flux": 1576.0, "c2p": 450.0, "fofc_flag": 450.0, "fofc_fix": 595.0, "update": 443.5,
                   "emf": 36.1}
 FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (dense), the profiling recipe's unit table
+# DRAM bytes (read + write) per unit of the kernels captured with ncu on the
+# 96^3 case of this workload (profiles/ncu_full_star96_flux.md,
+# profiles/ncu_full_star96_update.md); scaled to a launch by its units.
+TRAFFIC_PER_UNIT = {"flux_x": 897.2, "flux_y": 236.2, "flux_z": 229.8, "update": 463.7}
+# Algorithmic HBM bytes per zone and RK stage of one fused pass: read U (5),
+# U^n (5), face B~ (3), face B~^n (3) and the ADM variables with K_ij (16),
+# write U (5) and face B~ (3) = 40 doubles; the first stage reads neither U^n
+# nor B~^n (32).  SSP-RK3: 112 doubles = 896 B per zone-cycle.
+HBM_BYTES_PER_ZONE_CYCLE = (32 + 40 + 40) * 8.0
+
+
+def _measured_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def _env_int(k, d):
@@ -522,9 +539,17 @@ def run_ours(args):
     key = "flux" if dom.startswith("flux") else dom
     flops = FLOPS_PER_UNIT.get(key, 0.0) * units.get(dom, 0)
     achieved = flops / (dom_ms / dom_n * 1e-3) / 1e12
+    traffic = TRAFFIC_PER_UNIT[dom] * units[dom] if dom in TRAFFIC_PER_UNIT and n in (96, 128) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": dom,
-                "peak_source": "nominal FP64 1.25 TFLOP/s (recipe unit table); FP64 is not in MEASURED_PEAKS.json"}
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": dom,
+                "peak_source": "nominal FP64 1.25 TFLOP/s (recipe unit table); FP64 is not in MEASURED_PEAKS.json",
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per unit on the 96^3 case, "
+                                  "scaled by units"}
+    hbm_peak = _measured_hbm()
+    hbm = {"algorithmic_bytes_per_zone_cycle": HBM_BYTES_PER_ZONE_CYCLE,
+           "achieved_gbs": value * HBM_BYTES_PER_ZONE_CYCLE / 1e9, "peak_gbs": hbm_peak,
+           "frac": value * HBM_BYTES_PER_ZONE_CYCLE / 1e9 / hbm_peak if hbm_peak else None,
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm_peak else "absent"}
     shares = {k: round(v[0] / sum(x[0] for x in kern.values()), 4) for k, v in kern.items()}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -534,7 +559,7 @@ def run_ours(args):
                        "parallelism": f"replicas{world}", "l2": "working set ~1 GB > 129 MB L2, no flush",
                        "rk": "SSP-RK3", "recon": "WENO-Z", "riemann": "HLLE", "fofc": True, "ct": "upwind"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": int(launches), "launch_shapes": tuned, "roofline": roofline, "kernel_share": shares,
+            "gpu_launches": int(launches), "launch_shapes": tuned, "roofline": roofline, "hbm_roofline": hbm, "kernel_share": shares,
             "c2p_stats": stats, "clocks": clocks}
     if not args.no_c2p and world == 1:
         line["c2p"] = c2p_leg(G)
