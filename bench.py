@@ -33,6 +33,10 @@ WORKLOAD = "star128_wenoz_hlle_fofc_ct_rk3"
 PARAMS = dict(gamma=2.0, rho_atm=1e-12, T_atm=1e-10, f_thr=0.1, sigma_max=0.0, dmp_M=0.0, c2p_tol=1e-10,
               W_max=1e3, recon=2, rsolver=1, fofc=1, rk_order=3, c2p_maxit=64)
 CFL = 0.25
+# Root search of the timed con2prims (stage input and FOFC estimate): 0, the
+# plain FP64 bracket and Illinois solve.  On this mostly static star the FP32
+# search (2) costs about what it saves; on the moving binary it is faster.
+C2P_GUESS = 0
 
 # Algorithmic FP64 operations per unit (add + mul + div + sqrt, each counted
 # once), from the op-counting build of the CPU oracle on sub-blocks of this
@@ -45,7 +49,7 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (dense), the profiling recipe's u
 # DRAM bytes (read + write) per unit of the kernels captured with ncu on the
 # 96^3 case of this workload (profiles/ncu_full_star96_flux.md,
 # profiles/ncu_full_star96_update.md); scaled to a launch by its units.
-TRAFFIC_PER_UNIT = {"flux_x": 897.2, "flux_y": 236.2, "flux_z": 229.8, "update": 463.7}
+TRAFFIC_PER_UNIT = {"flux_x": 1173.0, "flux_y": 243.5, "flux_z": 239.5, "update": 463.7}
 # Algorithmic HBM bytes per zone and RK stage of one fused pass: read U (5),
 # U^n (5), face B~ (3), face B~^n (3) and the ADM variables with K_ij (16),
 # write U (5) and face B~ (3) = 40 doubles; the first stage reads neither U^n
@@ -440,7 +444,7 @@ def run_ours(args):
     B.build()
 
     inp = star_inputs()
-    ctx = G.Context(G.params(**PARAMS, c2p_guess=0))
+    ctx = G.Context(G.params(**PARAMS, c2p_guess=C2P_GUESS))
     blk = G.DeviceBlock(inp.n, inp.ng, inp.dx, inp.adm)
     blk.prim.copy_(torch.from_numpy(inp.prim))
     A = [torch.from_numpy(a).cuda() for a in inp.A]
@@ -557,7 +561,9 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME(), "interior": [n, n, n], "ghosts": NG, "zones_per_gpu": zones,
                        "parallelism": f"replicas{world}", "l2": "working set ~1 GB > 129 MB L2, no flush",
-                       "rk": "SSP-RK3", "recon": "WENO-Z", "riemann": "HLLE", "fofc": True, "ct": "upwind"},
+                       "rk": "SSP-RK3", "recon": "WENO-Z", "riemann": "HLLE", "fofc": True, "ct": "upwind",
+                       "con2prim": {0: "plain FP64", 1: "network + FP32 search + FP64",
+                                    2: "FP32 search + FP64"}[C2P_GUESS]},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches), "launch_shapes": tuned, "roofline": roofline, "hbm_roofline": hbm, "kernel_share": shares,
             "c2p_stats": stats, "clocks": clocks}

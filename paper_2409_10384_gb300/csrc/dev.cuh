@@ -565,6 +565,87 @@ __device__ __forceinline__ void rec_step(RecVar& s, double xn, double& lo, doubl
   s.d2 = dn;
 }
 
+// WENO-Z part of rec_step<2> without the division: x_m, the two numerators
+// and denominators of hi = x + n_hi / (6 den_hi), lo = x + n_lo / (6 den_lo);
+// advances the state to cell m+1.
+__device__ __forceinline__ void wz_parts(RecVar& s, double xn, double& x, double& n_hi, double& n_lo, double& d_hi,
+                                         double& d_lo) {
+  const double dn = xn - s.x2;
+  double b0n, b1n, b2n;
+  wz_window(s.d2, dn, b0n, b1n, b2n);
+  const double eps = 1e-40;
+  const double b0 = s.b0p, b1 = s.b1c, b2 = b2n;
+  const double tau = fabs(b0 - b2);
+  const double e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
+  const double A0 = (e0 + tau) * (e1 * e2);
+  const double A1 = (e1 + tau) * (e0 * e2);
+  const double A2 = (e2 + tau) * (e0 * e1);
+  const double a1 = 6.0 * A1, a2h = 3.0 * A2, a0l = 3.0 * A0;
+  d_hi = A0 + a1 + a2h;
+  d_lo = a0l + a1 + A2;
+  const double da = s.d0, db = s.d1, dc = s.d2, dd = dn;
+  n_hi = fma(A0, fma(5.0, db, -2.0 * da), fma(a1, fma(2.0, dc, db), a2h * fma(4.0, dc, -dd)));
+  n_lo = fma(A2, fma(-5.0, dc, 2.0 * dd), fma(-a1, fma(2.0, db, dc), a0l * fma(-4.0, db, da)));
+  x = s.x1;
+  s.b0p = s.b0c;
+  s.b0c = b0n;
+  s.b1c = b1n;
+  s.x1 = s.x2;
+  s.x2 = xn;
+  s.d0 = s.d1;
+  s.d1 = s.d2;
+  s.d2 = dn;
+}
+
+// The face values of N variables from wz_parts with one division for all
+// (Montgomery's simultaneous inversion): the products p_v = d_hi d_lo are
+// scaled to [1, 2) by their binary exponents (integer operations), chained,
+// inverted once and unchained; 1/(6 p_v) regains its exponent the same way.
+// Products outside [2^-959, 2^977] (never for physical data: eps = 1e-40
+// bounds them below by ~1e-238) take one division each.
+template <int N>
+__device__ __forceinline__ void wz_finish(const double* x, const double* n_hi, const double* n_lo,
+                                          const double* d_hi, const double* d_lo, double* hi, double* lo) {
+  double m[N];
+  int e[N];
+  bool ok = true;
+#pragma unroll
+  for (int v = 0; v < N; v++) {
+    const double p = d_hi[v] * d_lo[v];
+    const int h = __double2hiint(p);
+    const int ex = (h >> 20) & 0x7FF;
+    ok = ok && ex >= 64 && ex <= 2000;
+    m[v] = __hiloint2double((h & 0x000FFFFF) | 0x3FF00000, __double2loint(p));
+    e[v] = ex - 1023;
+  }
+  if (ok) {
+    double c[N];
+    c[0] = m[0];
+#pragma unroll
+    for (int v = 1; v < N; v++) c[v] = c[v - 1] * m[v];
+    double inv = (1.0 / 6.0) / c[N - 1];
+#pragma unroll
+    for (int v = N - 1; v >= 0; v--) {
+      double r;
+      if (v > 0) {
+        r = inv * c[v - 1];
+        inv *= m[v];
+      } else {
+        r = inv;
+      }
+      r = __hiloint2double(__double2hiint(r) - (e[v] << 20), __double2loint(r));
+      hi[v] = fma(n_hi[v], d_lo[v] * r, x[v]);
+      lo[v] = fma(n_lo[v], d_hi[v] * r, x[v]);
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < N; v++) {
+      hi[v] = x[v] + n_hi[v] / (6.0 * d_hi[v]);
+      lo[v] = x[v] + n_lo[v] / (6.0 * d_lo[v]);
+    }
+  }
+}
+
 __device__ __forceinline__ void face_floor(const Par& P, double* s) {
   if (s[0] < P.rho_thr) {
     s[0] = P.rho_atm; s[1] = s[2] = s[3] = 0.0; s[4] = P.P_atm;

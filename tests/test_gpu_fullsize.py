@@ -1,7 +1,7 @@
 """Full-size parity: the 128^3 star workload of bench.py (WENO-Z + HLLE + FOFC
 + CT, RK3), in bench.py's launch configuration (launch shapes picked by the
-autotuner), every substep of one RK3 step against the FP64 oracle on every
-cell and face.  Same bars and flag handling as tests/test_gpu_parity.py."""
+autotuner, and the con2prim root search bench.py times), every substep of one
+RK3 step against the FP64 oracle on every cell and face.  Same bars and flag handling as tests/test_gpu_parity.py."""
 import numpy as np
 import pytest
 
@@ -28,7 +28,7 @@ def test_star128_rk3_step_matches_oracle(G):
     p = O.params(**bench.PARAMS)
     inp = synth.star_uniform(seed=2, n=bench.N_INT, ng=bench.NG)
     ob = O.init_block(p, inp.n, inp.ng, inp.dx, inp.adm, inp.prim, inp.A)
-    ctx = G.Context(G.params(**bench.PARAMS))
+    ctx = G.Context(G.params(**bench.PARAMS, c2p_guess=bench.C2P_GUESS))
     dt = bench.CFL * inp.dx[0]
     ctx.autotune([U.to_device(G, ob)], dt)   # on a copy: the launch shapes bench.py times
     total_flips = 0
