@@ -463,8 +463,101 @@ static real wenoz(real a, real b, real c, real d, real e) {
   real s = a0 + a1 + a2;
   return (a0 * q0 + a1 * q1 + a2 * q2) / s;
 }
+// Piecewise-parabolic reconstruction (Sec. 3.2 cites Colella & Woodward 1984
+// as PPM4 and Colella & Sekora 2008 as PPMX).  a[0..4] = cells j-2..j+2;
+// returns the limited values at the faces j-1/2 (lo) and j+1/2 (hi) of cell j.
+//
+// PPM4, Colella & Woodward (1984): the monotonised average slope
+//   dm_k = min(|a_{k+1} - a_{k-1}|/2, 2|a_k - a_{k-1}|, 2|a_{k+1} - a_k|) sgn
+//   when a_k is not an extremum of its neighbours, else 0,
+// the interface value a_{k+1/2} = a_k + (a_{k+1} - a_k)/2 - (dm_{k+1} - dm_k)/6,
+// then the parabola of cell j is made monotone: flat at a local extremum, and
+// an end moved to 3 a_j - 2 (other end) where the parabola would overshoot.
+static real cw_slope(real am, real a0, real ap) {
+  real dl = a0 - am, dr = ap - a0;
+  if (!(dl * dr > 0.0)) return real(0.0);
+  real dc = 0.5 * (ap - am);
+  real m = min_(abs_(dc), min_(2.0 * abs_(dl), 2.0 * abs_(dr)));
+  return dc < 0.0 ? -m : m;
+}
+static void ppm4_cell(const real a[5], real* lo, real* hi) {
+  real s0 = cw_slope(a[0], a[1], a[2]);
+  real s1 = cw_slope(a[1], a[2], a[3]);
+  real s2 = cw_slope(a[2], a[3], a[4]);
+  real aL = a[1] + 0.5 * (a[2] - a[1]) - (s1 - s0) / 6.0;
+  real aR = a[2] + 0.5 * (a[3] - a[2]) - (s2 - s1) / 6.0;
+  real aj = a[2];
+  if (!((aR - aj) * (aj - aL) > 0.0)) {
+    aL = aj;
+    aR = aj;
+  } else {
+    real da = aR - aL, a6 = 6.0 * (aj - 0.5 * (aL + aR));
+    if (da * a6 > da * da) {
+      aL = 3.0 * aj - 2.0 * aR;
+    } else if (-(da * da) > da * a6) {
+      aR = 3.0 * aj - 2.0 * aL;
+    }
+  }
+  *lo = aL;
+  *hi = aR;
+}
+// PPMX, Colella & Sekora (2008): fourth-order interface values
+//   a_{k+1/2} = 7/12 (a_k + a_{k+1}) - 1/12 (a_{k-1} + a_{k+2}),
+// replaced where they leave [a_k, a_{k+1}] by (a_k + a_{k+1})/2 - D/6 with D the
+// limited second difference 3 (a_k - 2 a_{k+1/2} + a_{k+1}) (limited against
+// 1.25 x the neighbouring second differences of the same sign, else 0); then
+// at a local extremum of the cell (or of the data) the parabola's curvature is
+// limited the same way against the three second differences around j, and
+// away from extrema the CW84 overshoot correction applies.
+static real cs_d2lim(real d, real d1, real d2) {
+  const real C = 1.25;
+  if (d > 0.0 && d1 > 0.0 && d2 > 0.0) return min_(d, min_(C * d1, C * d2));
+  if (d < 0.0 && d1 < 0.0 && d2 < 0.0) return max_(d, max_(C * d1, C * d2));
+  return real(0.0);
+}
+static real cs_face(real am, real a0, real ap, real app) {
+  real f = 7.0 / 12.0 * (a0 + ap) - 1.0 / 12.0 * (am + app);
+  if ((f - a0) * (ap - f) < 0.0) {
+    real d = 3.0 * (a0 - 2.0 * f + ap);
+    real lim = cs_d2lim(d, am - 2.0 * a0 + ap, a0 - 2.0 * ap + app);
+    f = 0.5 * (a0 + ap) - lim / 6.0;
+  }
+  return f;
+}
+static void ppmx_cell(const real a[5], real* lo, real* hi) {
+  const real C = 1.25;
+  // a[-1] and a[+3] relative to the cell do not exist: the faces of cell j
+  // use a[0..3] (face j-1/2) and a[1..4] (face j+1/2)
+  real aL = cs_face(a[0], a[1], a[2], a[3]);
+  real aR = cs_face(a[1], a[2], a[3], a[4]);
+  real aj = a[2];
+  if (!((aR - aj) * (aj - aL) > 0.0) || !((a[1] - aj) * (aj - a[3]) > 0.0)) {
+    real d = 6.0 * (aL + aR) - 12.0 * aj;
+    real dc = a[1] - 2.0 * aj + a[3];
+    real dl = a[0] - 2.0 * a[1] + aj;
+    real dr = aj - 2.0 * a[3] + a[4];
+    real lim = real(0.0);
+    if (d > 0.0 && dc > 0.0 && dl > 0.0 && dr > 0.0) lim = min_(d, min_(C * dc, min_(C * dl, C * dr)));
+    if (d < 0.0 && dc < 0.0 && dl < 0.0 && dr < 0.0) lim = max_(d, max_(C * dc, max_(C * dl, C * dr)));
+    if (d == 0.0) {
+      aL = aj;
+      aR = aj;
+    } else {
+      real r = lim / d;
+      aL = aj + (aL - aj) * r;
+      aR = aj + (aR - aj) * r;
+    }
+  } else {
+    real dL = aL - aj, dR = aR - aj;
+    if (abs_(dR) >= 2.0 * abs_(dL)) aR = aj - 2.0 * dL;
+    if (abs_(dL) >= 2.0 * abs_(dR)) aL = aj - 2.0 * dR;
+  }
+  *lo = aL;
+  *hi = aR;
+}
 // left/right states at the face between stencil entries q[2] (cell -1) and q[3]
 // (cell 0), from q[0..5] = cells -3..+2 along the face normal.
+// recon: 0 donor cell, 1 PLM, 2 WENO-Z, 3 PPM4, 4 PPMX.
 static void reconstruct(int recon, const real q[6], real* L, real* R) {
   if (recon == 0) {
     *L = q[2];
@@ -472,9 +565,15 @@ static void reconstruct(int recon, const real q[6], real* L, real* R) {
   } else if (recon == 1) {
     *L = q[2] + 0.5 * vl_slope(q[1], q[2], q[3]);
     *R = q[3] - 0.5 * vl_slope(q[2], q[3], q[4]);
-  } else {
+  } else if (recon == 2) {
     *L = wenoz(q[0], q[1], q[2], q[3], q[4]);
     *R = wenoz(q[5], q[4], q[3], q[2], q[1]);
+  } else {
+    real lo, hi;
+    if (recon == 3) ppm4_cell(q, &lo, L);
+    else ppmx_cell(q, &lo, L);
+    if (recon == 3) ppm4_cell(q + 1, R, &hi);
+    else ppmx_cell(q + 1, R, &hi);
   }
 }
 // floor on a reconstructed state (Sec. 3.3): s = rho, w^1..3, P

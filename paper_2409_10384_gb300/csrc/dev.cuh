@@ -488,14 +488,86 @@ struct RecVar {
   double x1, x2;          // x_m, x_{m+1}
   double d0, d1, d2;      // delta_{m-2}, delta_{m-1}, delta_m
   double b0p, b0c, b1c;   // b0 of window m-1, b0 and b1 of window m
+  double xm2, xm1;        // PPM: x_{m-2}, x_{m-1}
+  double aL, dm;          // PPM: value at the face m-1/2; PPM4: limited slope of cell m
 };
 
-// R = 0 donor cell, 1 PLM with the van Leer limiter, 2 WENO-Z.
+// PPM4 (Colella & Woodward 1984): monotonised average slope of the middle value.
+__device__ __forceinline__ double cw_slope(double am, double a0, double ap) {
+  const double dl = a0 - am, dr = ap - a0;
+  if (!(dl * dr > 0.0)) return 0.0;
+  const double dc = 0.5 * (ap - am);
+  const double m = fmin(fabs(dc), fmin(2.0 * fabs(dl), 2.0 * fabs(dr)));
+  return dc < 0.0 ? -m : m;
+}
+// PPMX (Colella & Sekora 2008): limited second difference and face value.
+__device__ __forceinline__ double cs_d2lim(double d, double d1, double d2) {
+  const double C = 1.25;
+  if (d > 0.0 && d1 > 0.0 && d2 > 0.0) return fmin(d, fmin(C * d1, C * d2));
+  if (d < 0.0 && d1 < 0.0 && d2 < 0.0) return fmax(d, fmax(C * d1, C * d2));
+  return 0.0;
+}
+__device__ __forceinline__ double cs_face(double am, double a0, double ap, double app) {
+  double f = 7.0 / 12.0 * (a0 + ap) - 1.0 / 12.0 * (am + app);
+  if ((f - a0) * (ap - f) < 0.0) {
+    const double d = 3.0 * (a0 - 2.0 * f + ap);
+    f = 0.5 * (a0 + ap) - cs_d2lim(d, am - 2.0 * a0 + ap, a0 - 2.0 * ap + app) / 6.0;
+  }
+  return f;
+}
+// Limited parabola of cell j from its face values aL, aR and a_{j-2..j+2}.
+__device__ __forceinline__ void ppm4_limit(double aj, double& aL, double& aR) {
+  if (!((aR - aj) * (aj - aL) > 0.0)) {
+    aL = aj;
+    aR = aj;
+  } else {
+    const double da = aR - aL, a6 = 6.0 * (aj - 0.5 * (aL + aR));
+    if (da * a6 > da * da) aL = 3.0 * aj - 2.0 * aR;
+    else if (-(da * da) > da * a6) aR = 3.0 * aj - 2.0 * aL;
+  }
+}
+__device__ __forceinline__ void ppmx_limit(double am2, double am1, double aj, double ap1, double ap2, double& aL,
+                                           double& aR) {
+  const double C = 1.25;
+  if (!((aR - aj) * (aj - aL) > 0.0) || !((am1 - aj) * (aj - ap1) > 0.0)) {
+    const double d = 6.0 * (aL + aR) - 12.0 * aj;
+    const double dc = am1 - 2.0 * aj + ap1, dl = am2 - 2.0 * am1 + aj, dr = aj - 2.0 * ap1 + ap2;
+    double lim = 0.0;
+    if (d > 0.0 && dc > 0.0 && dl > 0.0 && dr > 0.0) lim = fmin(d, fmin(C * dc, fmin(C * dl, C * dr)));
+    if (d < 0.0 && dc < 0.0 && dl < 0.0 && dr < 0.0) lim = fmax(d, fmax(C * dc, fmax(C * dl, C * dr)));
+    if (d == 0.0) {
+      aL = aj;
+      aR = aj;
+    } else {
+      const double r = lim / d;
+      aL = aj + (aL - aj) * r;
+      aR = aj + (aR - aj) * r;
+    }
+  } else {
+    const double dL = aL - aj, dR = aR - aj;
+    if (fabs(dR) >= 2.0 * fabs(dL)) aR = aj - 2.0 * dL;
+    if (fabs(dL) >= 2.0 * fabs(dR)) aL = aj - 2.0 * dR;
+  }
+}
+
+// R = 0 donor cell, 1 PLM with the van Leer limiter, 2 WENO-Z, 3 PPM4, 4 PPMX.
 // Start at cell m from x_{m-2} .. x_{m+1}.
 template <int R>
 __device__ __forceinline__ void rec_init(RecVar& s, double xm2, double xm1, double x0, double xp1) {
   s.x1 = x0;
   s.x2 = xp1;
+  if (R >= 3) {
+    s.xm2 = xm2;
+    s.xm1 = xm1;
+    if (R == 3) {
+      const double dmm = cw_slope(xm2, xm1, x0);
+      s.dm = cw_slope(xm1, x0, xp1);
+      s.aL = xm1 + 0.5 * (x0 - xm1) - (s.dm - dmm) / 6.0;
+    } else {
+      s.aL = cs_face(xm2, xm1, x0, xp1);
+    }
+    return;
+  }
   s.d0 = xm1 - xm2;
   s.d1 = x0 - xm1;
   s.d2 = xp1 - x0;
@@ -513,6 +585,27 @@ __device__ __forceinline__ void rec_init(RecVar& s, double xm2, double xm1, doub
 // values of the cell share one reciprocal.
 template <int R>
 __device__ __forceinline__ void rec_step(RecVar& s, double xn, double& lo, double& hi) {
+  if (R >= 3) {
+    double aR, aL = s.aL;
+    if (R == 3) {
+      const double dmn = cw_slope(s.x1, s.x2, xn);
+      aR = s.x1 + 0.5 * (s.x2 - s.x1) - (dmn - s.dm) / 6.0;
+      s.dm = dmn;
+      s.aL = aR;
+      ppm4_limit(s.x1, aL, aR);
+    } else {
+      aR = cs_face(s.xm1, s.x1, s.x2, xn);
+      s.aL = aR;
+      ppmx_limit(s.xm2, s.xm1, s.x1, s.x2, xn, aL, aR);
+    }
+    lo = aL;
+    hi = aR;
+    s.xm2 = s.xm1;
+    s.xm1 = s.x1;
+    s.x1 = s.x2;
+    s.x2 = xn;
+    return;
+  }
   const double dn = xn - s.x2;  // delta_{m+1}
   if (R == 2) {
     double b0n, b1n, b2n;

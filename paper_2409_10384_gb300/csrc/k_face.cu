@@ -221,9 +221,13 @@ __global__ void __launch_bounds__(128) k_fofc_fix(Work w, Par P, unsigned long l
 
 template <int d>
 void launch_flux_r(const Work& w, const Par& P, cudaStream_t s, int grid, int threads) {
-  if (P.recon == 2) k_flux<d, 2><<<grid, threads, 0, s>>>(w, P);
-  else if (P.recon == 1) k_flux<d, 1><<<grid, threads, 0, s>>>(w, P);
-  else k_flux<d, 0><<<grid, threads, 0, s>>>(w, P);
+  switch (P.recon) {
+    case 4: k_flux<d, 4><<<grid, threads, 0, s>>>(w, P); break;
+    case 3: k_flux<d, 3><<<grid, threads, 0, s>>>(w, P); break;
+    case 2: k_flux<d, 2><<<grid, threads, 0, s>>>(w, P); break;
+    case 1: k_flux<d, 1><<<grid, threads, 0, s>>>(w, P); break;
+    default: k_flux<d, 0><<<grid, threads, 0, s>>>(w, P); break;
+  }
 }
 void launch_flux_dir(int d, const Work& w, const Par& P, cudaStream_t s, int grid, int threads) {
   if (d == 0) launch_flux_r<0>(w, P, s, grid, threads);

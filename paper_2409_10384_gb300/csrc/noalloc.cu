@@ -56,7 +56,7 @@ __global__ void k_noalloc_setup(DevBlock b, PreTable t, DevBlock* dblk, long lon
 int to_par(const mhd_params* p, Par& P) {
   if (!p) return MHD_EINVAL;
   if (!(p->gamma > 1.0) || !(p->rho_atm > 0.0) || !(p->T_atm > 0.0) || !(p->f_thr >= 0.0) || !(p->c2p_tol > 0.0) ||
-      !(p->W_max > 1.0) || p->recon < 0 || p->recon > 2 || p->rsolver < 0 || p->rsolver > 1 ||
+      !(p->W_max > 1.0) || p->recon < 0 || p->recon > 4 || p->rsolver < 0 || p->rsolver > 1 ||
       (p->rk_order != 2 && p->rk_order != 3) || p->c2p_maxit < 1 || p->c2p_guess != 0 ||
       (p->dmp_M > 0.0 && p->dmp_M < 1.0))
     return MHD_EINVAL;

@@ -154,17 +154,26 @@ def _run_stage_pair(G, ctx, p, ob, dt, s, check_fluxes=True, inject=True):
     ref = ob.copy()
     out = O.stage(p, ref, dt, s, mask=mask, keep=True)
     ref.scales = U.term_scales(p, ob, out, dt, s)
+    ref.exclude = None
     if check_fluxes:
+        ties = []
         for d in range(3):
             Fg = ctx.scratch(0, d, out["flux"][d].shape)
             # compare the faces the stage computes (nonzero in the oracle's array)
             m = np.any(out["flux"][d] != 0, axis=0)
             # a flux is a difference of O(U) terms: compare against the field
             # maximum; the tau~ flux carries the precision of the D~ flux
+            off = np.zeros(m.shape, bool)
             for c in range(7):
-                Fr = out["flux"][d][c][m]
-                sc = np.abs(Fr).max() + (np.abs(out["flux"][d][0][m]).max() if c == 4 else 0.0)
-                assert np.max(np.abs(Fg[c][m] - Fr)) <= 1e-13 * sc, ("flux", d, c)
+                sc = np.abs(out["flux"][d][c][m]).max() + (np.abs(out["flux"][d][0][m]).max() if c == 4 else 0.0)
+                off |= m & (np.abs(Fg[c] - out["flux"][d][c]) > 1e-13 * sc)
+            for face in np.argwhere(off):
+                face = tuple(int(x) for x in face)
+                assert U.recon_is_tie(p, ref, d, face), ("flux", d, face)
+                ties.append((d, face))
+        assert len(ties) <= 1e-3 * sum(np.prod(ob.face_shape(d)) for d in range(3)), len(ties)
+        if ties:
+            ref.exclude = U.tie_exclusions(ob, ties)
     return ref, got, flips
 
 
@@ -179,7 +188,7 @@ def test_stage_periodic_flat_plm_hlle(G):
         fill_ghosts(ob)
         ref, got, _ = _run_stage_pair(G, ctx, p, ob, dt, s)
         U.compare_prims(ref, got, p, f"stage {s}")
-        U.compare_state(ref, got, f"stage {s}", scales=ref.scales)
+        U.compare_state(ref, got, f"stage {s}", scales=ref.scales, exclude=ref.exclude)
         # next substep starts from the GPU result (per-substep parity)
         ob.cons[...] = got["cons"]
         ob.cons0[...] = got["cons0"]
@@ -189,11 +198,14 @@ def test_stage_periodic_flat_plm_hlle(G):
 
 
 @pytest.mark.parametrize("where,recon,rs,dmp", [("surface", 2, 1, 0.0), ("surface", 2, 0, 1.1),
-                                                ("surface", 0, 1, 0.0), ("core", 2, 1, 0.0), ("core", 1, 0, 1.2)])
+                                                ("surface", 0, 1, 0.0), ("core", 2, 1, 0.0), ("core", 1, 0, 1.2),
+                                                ("surface", 3, 1, 0.0), ("surface", 4, 1, 0.0),
+                                                ("core", 3, 0, 0.0), ("core", 4, 1, 1.2), ("surface", 4, 0, 1.1)])
 def test_stage_star_fofc(G, where, recon, rs, dmp):
     """Sub-blocks of the 128^3 star workload (dynamical metric with K_ij): over the
     stellar surface (atmosphere, FOFC fires) and over the magnetised core;
-    WENO-Z/PLM/donor + HLLE/LLF + FOFC (+DMP) + CT, all three RK3 substeps."""
+    WENO-Z/PLM/PPM4/PPMX/donor + HLLE/LLF + FOFC (+DMP) + CT, all three RK3
+    substeps."""
     p = O.params(gamma=2.0, rho_atm=1e-12, T_atm=1e-10, f_thr=0.1, recon=recon, rsolver=rs, rk_order=3,
                  fofc=1, dmp_M=dmp)
     corner = (104, 52, 52) if where == "surface" else (52, 52, 52)
@@ -206,7 +218,7 @@ def test_stage_star_fofc(G, where, recon, rs, dmp):
         ref, got, flips = _run_stage_pair(G, ctx, p, ob, dt, s)
         total_flips += len(flips)
         U.compare_prims(ref, got, p, f"stage {s}")
-        U.compare_state(ref, got, f"stage {s}", scales=ref.scales)
+        U.compare_state(ref, got, f"stage {s}", scales=ref.scales, exclude=ref.exclude)
         ob.cons[...] = got["cons"]
         ob.cons0[...] = got["cons0"]
         for d in range(3):

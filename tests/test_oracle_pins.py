@@ -134,7 +134,7 @@ def test_hlle_is_upwind_for_supersonic_flow():
 
 # ----------------------------------------------------------------- Sec. 3.2
 
-@pytest.mark.parametrize("recon", [0, 1, 2])
+@pytest.mark.parametrize("recon", [0, 1, 2, 3, 4])
 def test_reconstruction_constant_and_linear(recon):
     q = np.full(16, 3.25)
     L, R = O.recon_line(recon, q)
@@ -178,6 +178,86 @@ def test_wenoz_order_and_eno_step():
     q = np.array([0.0] * 6 + [1.0] * 6)
     L, R = O.recon_line(2, q)
     assert abs(L[6]) < 1e-30 and abs(R[6] - 1.0) < 1e-30
+
+
+def test_ppm_parabola_peak_hand_values():
+    """At the peak of the sampled parabola a_k = -k^2: CW84 (PPM4) flattens the
+    cell (both faces = a_j = 0); Colella & Sekora (PPMX) keeps the fourth-order
+    face values 7/12 (0 - 1) - 1/12 (-1 - 4) = -1/6 on both sides, because all
+    second differences equal -2 and the limited curvature is the unlimited one."""
+    k = np.arange(-6, 7, dtype=float)
+    q = -k * k
+    j = 6                      # index of k = 0
+    L, R = O.recon_line(3, q)
+    assert L[j + 1] == 0.0 and R[j] == 0.0     # hi face of cell j, lo face of cell j
+    L, R = O.recon_line(4, q)
+    assert abs(L[j + 1] + 1.0 / 6.0) < 1e-15 and abs(R[j] + 1.0 / 6.0) < 1e-15
+
+
+def test_ppm4_hand_values():
+    """CW84 on a = (0, 1, 3, 4, 4, ...): slopes dm = (0.5 -> min(1.5, 2, 4)=1.5 at
+    a=1 ...) give the interface 1 + (3-1)/2 - (dm(3) - dm(1))/6 between 1 and 3."""
+    q = np.array([0.0, 0.0, 0.0, 1.0, 3.0, 4.0, 4.0, 4.0, 4.0, 4.0])
+    dm = lambda am, a0, ap: 0.0 if (a0 - am) * (ap - a0) <= 0 else np.sign(ap - am) * min(
+        abs(ap - am) / 2, 2 * abs(a0 - am), 2 * abs(ap - a0))
+    face = 1.0 + 1.0 - (dm(1, 3, 4) - dm(0, 1, 3)) / 6.0        # between q[3] = 1 and q[4] = 3
+    L, R = O.recon_line(3, q)
+    # cell 4 (a = 3): its lo face is the interface above; its hi face 3 + 0.5 - (0 - dm(1,3,4))/6
+    hi4 = 3.0 + 0.5 - (dm(3, 4, 4) - dm(1, 3, 4)) / 6.0
+    lo4, a4 = face, 3.0
+    # the monotonicity constraint of CW84 on cell 4
+    da, a6 = hi4 - lo4, 6 * (a4 - 0.5 * (lo4 + hi4))
+    if da * a6 > da * da:
+        lo4 = 3 * a4 - 2 * hi4
+    elif -da * da > da * a6:
+        hi4 = 3 * a4 - 2 * lo4
+    assert abs(R[4] - lo4) < 1e-15 and abs(L[5] - hi4) < 1e-15
+
+
+@pytest.mark.parametrize("recon", [1, 2, 3, 4])
+def test_reconstruction_mirror_symmetry_and_no_new_extrema(recon):
+    """Reversing the data swaps the left and right states (any index or sign
+    slip breaks this).  On monotone data, no face value of the limited
+    methods (PLM, PPM4, PPMX) leaves the range of the three cells around it.
+    WENO-Z is not TVD and may overshoot by a small amount."""
+    rng = np.random.default_rng(3)
+    q = np.concatenate([rng.normal(size=20), np.full(5, 2.0), rng.normal(size=15) * 1e-3])
+    n = q.size
+    L, R = O.recon_line(recon, q)
+    Lr, Rr = O.recon_line(recon, q[::-1].copy())
+    for f in range(3, n - 2):
+        g = n - f
+        if 3 <= g < n - 2:
+            assert abs(Lr[f] - R[g]) <= 1e-14 * (1 + abs(R[g])) and abs(Rr[f] - L[g]) <= 1e-14 * (1 + abs(L[g]))
+    if recon == 2:
+        return
+    q = np.sort(rng.normal(size=40)) + np.repeat([0.0, 3.0], 20)    # monotone with a jump
+    L, R = O.recon_line(recon, q)
+    for f in range(3, q.size - 2):
+        lo3, hi3 = q[f - 2:f + 1].min(), q[f - 2:f + 1].max()      # cells f-2..f around cell f-1
+        assert lo3 - 1e-14 <= L[f] <= hi3 + 1e-14
+        lo3, hi3 = q[f - 1:f + 2].min(), q[f - 1:f + 2].max()
+        assert lo3 - 1e-14 <= R[f] <= hi3 + 1e-14
+
+
+def test_ppm_convergence_through_smooth_extrema():
+    """Cell averages of sin(2 pi x): PPMX (extremum-preserving) converges at
+    high order in the maximum norm, also at the two extrema; PPM4 clips the
+    extrema to first order there (Colella & Sekora 2008, Sec. 1)."""
+    err = {3: [], 4: []}
+    for n in (32, 64, 128, 256):
+        x = (np.arange(-3, n + 3) + 0.5) / n
+        q = n * (np.cos(2 * np.pi * (x - 0.5 / n)) - np.cos(2 * np.pi * (x + 0.5 / n))) / (2 * np.pi)
+        xf = np.arange(-3, n + 3) / n
+        ex = np.sin(2 * np.pi * xf)
+        f = slice(3, n + 3)
+        for r in (3, 4):
+            L, R = O.recon_line(r, q)
+            err[r].append(max(np.abs(L[f] - ex[f]).max(), np.abs(R[f] - ex[f]).max()))
+    rate = {r: np.log2(np.array(e[:-1]) / np.array(e[1:])) for r, e in err.items()}
+    assert np.all(rate[4][1:] > 2.9), rate
+    assert np.all(rate[3] < 2.2), rate
+    assert err[4][-1] < 0.05 * err[3][-1]
 
 
 # ---------------------------------------------------------------- Sec. 3.4
