@@ -57,6 +57,9 @@ typedef struct {
   double dmp_M;     /* relaxed DMP factor M >= 1 (Eq. 19); <= 0 disables */
   double c2p_tol;   /* relative width of the final root bracket (1e-10) */
   double W_max;     /* Lorentz-factor cap of the root solve (1e3) */
+  double alpha_exc; /* excision (Sec. 4.7): block con2prims floor every cell whose
+                       lapse is below alpha_exc to the static atmosphere (reported
+                       as F_DFLOOR); <= 0 disables */
   int recon;        /* 0 donor cell, 1 PLM (van Leer), 2 WENO-Z, 3 PPM4 (Colella &
                        Woodward 1984), 4 PPMX (Colella & Sekora 2008) (Sec. 3.2) */
   int rsolver;      /* 0 LLF, 1 HLLE (Sec. 3.2) */

@@ -87,7 +87,8 @@ typedef struct {
   double dmp_M;      // relaxed DMP factor M >= 1; <= 0 disables (Eq. 19)
   double c2p_tol;    // relative bracket width for the root solve
   double W_max;      // Lorentz-factor cap of the root solve
-  int recon;         // 0 donor cell, 1 PLM, 2 WENO-Z (Sec. 3.2)
+  double alpha_exc;  // excision: cells with lapse < alpha_exc are floored (Sec. 4.7); <= 0 disables
+  int recon;         // 0 donor cell, 1 PLM, 2 WENO-Z, 3 PPM4, 4 PPMX (Sec. 3.2)
   int rsolver;       // 0 LLF, 1 HLLE (Sec. 3.2)
   int fofc;          // first-order flux correction on/off (Sec. 3.3)
   int rk_order;      // 2 or 3 (SSP RK, Sec. 3.2)
@@ -316,8 +317,9 @@ static real illinois(const KRP& s, real a, real fa, real b, real fb, double tol,
 // One cell.  cons (densitised) may be modified by the floors when write_back.
 // Bd = cell-centred densitised B~, g = gamma_ij.  mu_lo/mu_hi: optional bracket
 // guess (both < 0 to use the plain bracket).
+// alpha: the lapse of the cell (for the excision floor; 1 where none applies)
 static void c2p_cell(const or_params& p, real cons[5], const real Bd[3], const real g[6], bool write_back,
-                     C2POut& o) {
+                     C2POut& o, real alpha = 1.0) {
   o.flags = 0;
   o.iters = 0;
   o.mu = 0.0;
@@ -343,8 +345,11 @@ static void c2p_cell(const or_params& p, real cons[5], const real Bd[3], const r
   if (!finite) {
     o.flags |= F_FAIL;
   } else {
-    // floors on the conserved state before the solve (Sec. 3.3)
-    if (D < p.f_thr * rho_atm) {
+    // floors on the conserved state before the solve (Sec. 3.3); inside the
+    // excision region alpha < alpha_exc (Sec. 4.7) every cell takes the same
+    // reset to the static atmosphere
+    const bool excise = p.alpha_exc > 0.0 && alpha < p.alpha_exc;
+    if (excise || D < p.f_thr * rho_atm) {
       D = rho_atm;
       Sl[0] = Sl[1] = Sl[2] = 0.0;
       tau = D * eps_atm + 0.5 * B2;
@@ -729,7 +734,7 @@ static void c2p_region(Ctx& C, or_stats* st) {
         for (int v = 0; v < 3; v++) Bd[v] = C.b->bcc[v * G.ncell + c];
         load_metric_cell(C, k, j, i, g);
         C2POut o;
-        c2p_cell(C.p, U, Bd, g, true, o);
+        c2p_cell(C.p, U, Bd, g, true, o, C.adm(0, k, j, i));
         for (int v = 0; v < 5; v++) C.b->cons[v * G.ncell + c] = val(U[v]);
         for (int v = 0; v < 5; v++) C.b->prim[v * G.ncell + c] = val(o.prim[v]);
         C.b->flags[c] = (unsigned char)o.flags;
@@ -862,7 +867,7 @@ static void fofc(Ctx& C, std::vector<double> flux[3], double g0, double g1, doub
           load_metric_cell(C, k, j, i, g);
           real Uc[5] = {Us[0], Us[1], Us[2], Us[3], Us[4]};
           C2POut o;
-          c2p_cell(C.p, Uc, Bd, g, false, o);
+          c2p_cell(C.p, Uc, Bd, g, false, o, C.adm(0, k, j, i));
           fl = (o.flags & (F_FAIL | FLOOR_BITS)) != 0;
           if (!fl && C.p.dmp_M > 0.0) {
             const real M = C.p.dmp_M;

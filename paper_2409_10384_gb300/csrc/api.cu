@@ -114,6 +114,7 @@ int set_par(mhd_ctx* c, const mhd_params* p) {
   P.dmp_M = p->dmp_M;
   P.tol = p->c2p_tol;
   P.vmax2 = 1.0 - 1.0 / (p->W_max * p->W_max);
+  P.alpha_exc = p->alpha_exc;
   P.recon = p->recon;
   P.rsolver = p->rsolver;
   P.fofc = p->fofc ? 1 : 0;

@@ -22,6 +22,7 @@ struct Par {
   double gam, gm1, gfac;        // Gamma, Gamma-1, Gamma/(Gamma-1)
   double rho_atm, T_atm, rho_thr, eps_atm, P_atm;
   double sigma_max, dmp_M, tol, vmax2;
+  double alpha_exc;             // excision lapse (<= 0: off)
   int recon, rsolver, fofc, rk_order, maxit, guess;
 };
 
@@ -303,8 +304,9 @@ struct KrpCell {
 
 // Phase 1: undensitise, apply the floors on the conserved state (Sec. 3.3) and
 // form the KRP variables.  Returns false (F_FAIL set) on non-finite input.
+// alpha: the cell's lapse, for the excision floor (1 where none applies).
 __device__ __forceinline__ bool krp_prep(const Par& P, const double* U, const double* Bd, const Metric& m,
-                                         KrpCell& k, unsigned& flags) {
+                                         KrpCell& k, unsigned& flags, double alpha = 1.0) {
   flags = 0;
   const double isd = m.isdet;
   double D = U[0] * isd, tau = U[4] * isd;
@@ -319,7 +321,8 @@ __device__ __forceinline__ bool krp_prep(const Par& P, const double* U, const do
     flags |= F_FAIL;
     return false;
   }
-  if (D < P.rho_thr) {
+  // inside the excision region (Sec. 4.7) every cell takes the D-floor reset
+  if (D < P.rho_thr || (P.alpha_exc > 0.0 && alpha < P.alpha_exc)) {
     D = P.rho_atm;
     Sl[0] = Sl[1] = Sl[2] = 0.0;
     tau = fma(D, P.eps_atm, 0.5 * B2);
@@ -436,13 +439,13 @@ __device__ __forceinline__ void krp_finish(const Par& P, const KrpCell& k, doubl
 // The con2prim of one cell in one thread.  U: densitised conserved state
 // (overwritten with the floored state when write_cons and a floor fired); Bd:
 // cell-centred B~; m: metric with inverse.  glo/ghi: optional bracket guess
-// (glo < 0: none).
+// (glo < 0: none); alpha: the lapse, for the excision floor.
 __device__ __forceinline__ void con2prim(const Par& P, double* U, const double* Bd, const Metric& m, double* prim,
                                          unsigned& flags, int& iters, bool write_cons, double glo = -1.0,
-                                         double ghi = -1.0) {
+                                         double ghi = -1.0, double alpha = 1.0) {
   KrpCell k;
   iters = 0;
-  bool ok = krp_prep(P, U, Bd, m, k, flags);
+  bool ok = krp_prep(P, U, Bd, m, k, flags, alpha);
   double mu = 0.0;
   if (ok) {
     double a, b, Ga, Gb;

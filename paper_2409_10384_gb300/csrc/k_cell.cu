@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(128) k_c2p_block(Work w, Par P, unsigned long 
     for (int v = 0; v < 5; v++) U[v] = b.cons[v * nc + c];
     unsigned fl;
     int itn;
-    con2prim(P, U, Bd, m, pr, fl, itn, true);
+    con2prim(P, U, Bd, m, pr, fl, itn, true, -1.0, -1.0, b.adm[c]);
 #pragma unroll
     for (int v = 0; v < 5; v++) b.prim[v * nc + c] = pr[v];
     if (fl & (FLOOR_BITS | F_FAIL)) {

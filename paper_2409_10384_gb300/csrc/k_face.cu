@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(128) k_fofc_flag(Work w, Par P, double g0, dou
     double pr[5];
     unsigned fl;
     int itn;
-    con2prim(P, U, Bd, m, pr, fl, itn, false);
+    con2prim(P, U, Bd, m, pr, fl, itn, false, -1.0, -1.0, b.adm[c]);
     bool flag = (fl & (FLOOR_BITS | F_FAIL)) != 0;
     if (!flag && P.dmp_M > 0.0) {
 #pragma unroll

@@ -36,13 +36,13 @@ __device__ __forceinline__ void kw_load(const KrpBuf& kb, const Par& P, long lon
 // guess later).  feat (optional): the network's features of the cell.
 __device__ __forceinline__ void prep_cell(const Par& P, const KrpBuf& kb, long long i, const double* U,
                                           const double* Bd, const Metric& m, bool learned = false,
-                                          float* feat = nullptr) {
+                                          float* feat = nullptr, double alpha = 1.0) {
   KrpCell k;
   unsigned fl;
   const long long n = kb.n;
   unsigned char st = 2;
   int its = 0;
-  if (krp_prep(P, U, Bd, m, k, fl)) {
+  if (krp_prep(P, U, Bd, m, k, fl, alpha)) {
     if (feat) krp_features(k.s, feat + i * MLP_FSTRIDE);
     if (learned) {
       st = 4;
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(256) k_krp_prep_block(Work w, Par P, KrpBuf kb
     double U[5];
 #pragma unroll
     for (int v = 0; v < 5; v++) U[v] = b.cons[v * nc + c];
-    prep_cell(P, kb, it, U, Bd, m, learned != 0, feat);
+    prep_cell(P, kb, it, U, Bd, m, learned != 0, feat, b.adm[c]);
   }
 }
 
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(256) k_krp_prep_fofc(Work w, Par P, double g0,
     Metric m;
     load_metric6(b.adm + 4 * nc, nc, c, m);
     const double Bd[3] = {b.bcc[c], b.bcc[nc + c], b.bcc[2 * nc + c]};
-    prep_cell(P, kb, it, U, Bd, m, learned != 0, feat);
+    prep_cell(P, kb, it, U, Bd, m, learned != 0, feat, b.adm[c]);
     kb.w[KW_USD * n + it] = U[0];
     kb.w[KW_UST * n + it] = U[4];
   }

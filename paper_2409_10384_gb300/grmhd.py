@@ -27,6 +27,7 @@ class mhd_params(C.Structure):
     _fields_ = [
         ("gamma", C.c_double), ("rho_atm", C.c_double), ("T_atm", C.c_double), ("f_thr", C.c_double),
         ("sigma_max", C.c_double), ("dmp_M", C.c_double), ("c2p_tol", C.c_double), ("W_max", C.c_double),
+        ("alpha_exc", C.c_double),
         ("recon", C.c_int), ("rsolver", C.c_int), ("fofc", C.c_int), ("rk_order", C.c_int),
         ("c2p_maxit", C.c_int), ("c2p_guess", C.c_int),
     ]
@@ -131,7 +132,7 @@ def check(rc: int, what: str = ""):
 
 def params(**kw) -> mhd_params:
     d = dict(gamma=5.0 / 3.0, rho_atm=1e-12, T_atm=1e-10, f_thr=0.1, sigma_max=0.0, dmp_M=0.0, c2p_tol=1e-10,
-             W_max=1e3, recon=1, rsolver=1, fofc=0, rk_order=2, c2p_maxit=64, c2p_guess=0)
+             W_max=1e3, alpha_exc=0.0, recon=1, rsolver=1, fofc=0, rk_order=2, c2p_maxit=64, c2p_guess=0)
     d.update(kw)
     p = mhd_params()
     for k, v in d.items():

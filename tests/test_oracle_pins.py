@@ -260,6 +260,35 @@ def test_ppm_convergence_through_smooth_extrema():
     assert err[4][-1] < 0.05 * err[3][-1]
 
 
+def test_excision_floor_alpha_below_threshold():
+    """Sec. 4.7: every cell with lapse below alpha_exc is reset to the static
+    atmosphere (rho_atm, v = 0, T = T_atm) and reported as a D floor; every
+    other cell is bitwise what it is without excision.  The lapse of the
+    synthetic star is psi^-2 with psi = 1 + 1.4/(2 sqrt(r^2 + 0.25)): 0.29 at
+    the cell centres nearest r = 0, so the threshold here is 0.4 (the paper
+    uses 0.2 for collapsing stars)."""
+    from paper_2409_10384_gb300 import synth
+    inp = synth.star_subblock(sub=12, corner=(58, 58, 58))
+    p0 = O.params(gamma=2.0, rho_atm=1e-12, T_atm=1e-10, recon=2, rsolver=1, rk_order=3)
+    p1 = O.params(gamma=2.0, rho_atm=1e-12, T_atm=1e-10, recon=2, rsolver=1, rk_order=3, alpha_exc=0.4)
+    a = O.init_block(p0, inp.n, inp.ng, inp.dx, inp.adm, inp.prim, inp.A)
+    b = a.copy()
+    O.c2p_block(p0, a)
+    O.c2p_block(p1, b)
+    g = a.ng - 3
+    R = tuple(slice(g, g + n + 6) for n in (a.n[2], a.n[1], a.n[0]))
+    alpha = inp.adm[0][R]
+    ex = alpha < 0.4
+    r = 0.75 * np.sqrt(3) / 2
+    assert ex.any() and (~ex).any() and abs(inp.adm[0].min() - (1 + 1.4 / (2 * np.sqrt(r * r + 0.25))) ** -2) < 1e-6
+    pa, pb = a.prim[(slice(None),) + R], b.prim[(slice(None),) + R]
+    assert np.all(pb[0][ex] == 1e-12) and np.all(pb[1:4][:, ex] == 0.0)
+    assert np.all(np.abs(pb[4][ex] / 1e-22 - 1.0) < 1e-12)
+    assert np.all((b.flags[R][ex] & O.F_DFLOOR) != 0)
+    assert np.array_equal(pa[:, ~ex], pb[:, ~ex]) and np.array_equal(a.flags[R][~ex], b.flags[R][~ex])
+    assert np.array_equal(a.cons[(slice(None),) + R][:, ~ex], b.cons[(slice(None),) + R][:, ~ex])
+
+
 # ---------------------------------------------------------------- Sec. 3.4
 
 def _stress(n, seed=4, gamma=2.0):
