@@ -57,6 +57,9 @@ struct mhd_ctx {
   bool ledger_on = false;
   double* dledger = nullptr;
   double* dmass = nullptr;
+  // neighbour table of the last ghost fill (grow-only)
+  int* dnbr = nullptr;
+  size_t dnbr_n = 0;
   int g_solve_cells() const { return nsm * (occ_krp[1] > 0 ? occ_krp[1] : 1); }
   // counters
   unsigned long long* dstats = nullptr;
@@ -193,6 +196,7 @@ int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
     items[W_FACE] = (n0 + 1) * n1 * n2 + n0 * (n1 + 1) * n2 + n0 * n1 * (n2 + 1);
     items[W_INIT] = b.ncell;
     for (int d = 0; d < 3; d++) items[W_SX + d] = flux_seg_items(s.n, d);
+    for (int d = 0; d < 3; d++) items[W_GFX + d] = nf[d];   // every entry of face array d
     for (int k = 0; k < W_NKIND; k++) pre[(size_t)k * (nb + 1) + i + 1] = pre[(size_t)k * (nb + 1) + i] + items[k];
   }
   const long long nkrp = std::max(pre[(size_t)W_C2P * (nb + 1) + nb], pre[(size_t)W_CELL * (nb + 1) + nb]);
@@ -581,6 +585,41 @@ int mhd_ledger_read(mhd_ctx* c, double* out, int reset, void* stream) {
   return MHD_OK;
 }
 
+int mhd_fill_ghosts(mhd_ctx* c, const mhd_block* blocks, int nb, const int* nbr, void* stream) {
+  if (!c || !nbr) return MHD_EINVAL;
+  int r = prepare(c, blocks, nb);
+  if (r) return r;
+  for (int i = 0; i < nb; i++)
+    for (int q = 0; q < 27; q++) {
+      const int v = nbr[(size_t)i * 27 + q];
+      if (v < -2 || v >= nb) return MHD_EINVAL;
+      if (v >= 0 && (blocks[v].ng != blocks[i].ng || blocks[v].n[0] != blocks[i].n[0] ||
+                     blocks[v].n[1] != blocks[i].n[1] || blocks[v].n[2] != blocks[i].n[2]))
+        return MHD_EINVAL;
+    }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)nb * 27;
+  if (n > c->dnbr_n) {
+    if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ECUDA;
+    if (c->dnbr) cudaFree(c->dnbr);
+    c->dnbr = nullptr;
+    c->dnbr_n = 0;
+    if (cudaMalloc(&c->dnbr, sizeof(int) * n) != cudaSuccess) return MHD_ENOMEM;
+    c->dnbr_n = n;
+  }
+  if (cudaMemcpyAsync(c->dnbr, nbr, sizeof(int) * n, cudaMemcpyHostToDevice, s) != cudaSuccess) return MHD_ECUDA;
+  long long it[W_NKIND];
+  list_items(c, it);
+  Work w = work_of(c);
+  for (int kind = 0; kind < 4; kind++) {
+    const long long items = kind == 0 ? it[W_INIT] : it[W_GFX + kind - 1];
+    const long long g = std::max(1LL, std::min((items + 255) / 256, (long long)c->nsm * 8));
+    launch_fill_ghosts(w, c->dnbr, kind, s, (int)g);
+    c->launches += 1;
+  }
+  return cuda_ok(cudaGetLastError());
+}
+
 int mhd_block_mass(mhd_ctx* c, const mhd_block* blocks, int nb, double* out, void* stream) {
   if (!c || !out) return MHD_EINVAL;
   int r = prepare(c, blocks, nb);
@@ -601,6 +640,7 @@ void mhd_finalize(mhd_ctx* c) {
   if (c->dpre) cudaFree(c->dpre);
   if (c->dpre_blk) cudaFree(c->dpre_blk);
   if (c->dstats) cudaFree(c->dstats);
+  if (c->dnbr) cudaFree(c->dnbr);
   if (c->cells_buf) cudaFree(c->cells_buf);
   if (c->mlp) cudaFree(c->mlp);
   if (c->mlp_wb) cudaFree(c->mlp_wb);

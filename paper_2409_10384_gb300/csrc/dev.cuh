@@ -47,7 +47,8 @@ struct DevBlock {
 };
 
 // Work lists: item ranges of every block for one kernel kind.
-enum WorkKind { W_C2P = 0, W_FX, W_FY, W_FZ, W_CELL, W_EDGE, W_FACE, W_INIT, W_SX, W_SY, W_SZ, W_NKIND };
+enum WorkKind { W_C2P = 0, W_FX, W_FY, W_FZ, W_CELL, W_EDGE, W_FACE, W_INIT, W_SX, W_SY, W_SZ, W_GFX, W_GFY, W_GFZ,
+                W_NKIND };
 
 // Flux sweeps: the n_d + 1 faces of direction d on one transverse line (one
 // extra line on each side, for the CT stencil) are split into near-equal

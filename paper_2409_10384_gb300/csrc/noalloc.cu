@@ -170,6 +170,7 @@ extern "C" int mhd_stage_noalloc(const mhd_params* p, const mhd_block* blk, doub
   items[W_FACE] = (n0 + 1) * n1 * n2 + n0 * (n1 + 1) * n2 + n0 * n1 * (n2 + 1);
   items[W_INIT] = ncell;
   for (int d = 0; d < 3; d++) items[W_SX + d] = flux_seg_items(s.n, d);
+  for (int d = 0; d < 3; d++) items[W_GFX + d] = nf[d];
   PreTable t;
   for (int k = 0; k < W_NKIND; k++) {
     t.v[2 * k] = 0;

@@ -79,6 +79,7 @@ _SIGS = {
     "mhd_autotune": (_I, [_VP, C.POINTER(mhd_block), _I, _D, _VP, _VP]),
     "mhd_set_launch": (_I, [_VP, _I, _I, _I]),
     "mhd_ledger": (_I, [_VP, _I]),
+    "mhd_fill_ghosts": (_I, [_VP, C.POINTER(mhd_block), _I, C.POINTER(C.c_int), _VP]),
     "mhd_ledger_read": (_I, [_VP, C.POINTER(C.c_double), _I, _VP]),
     "mhd_block_mass": (_I, [_VP, C.POINTER(mhd_block), _I, C.POINTER(C.c_double), _VP]),
     "mhd_get_launch": (_I, [_VP, _I, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
@@ -330,6 +331,14 @@ class Context:
         t, w = C.c_int(), C.c_int()
         check(self.L.mhd_get_launch(self.h, self.TUNABLE.index(kernel), C.byref(t), C.byref(w)), "mhd_get_launch")
         return t.value, w.value
+
+    def fill_ghosts(self, blocks, nbr, stream=None):
+        """Ghost zones from same-level neighbours: nbr int [nblocks][27]
+        (neighbour block index, -1 outflow, -2 untouched)."""
+        arr, nb = self._blocks(blocks)
+        t = np.ascontiguousarray(np.asarray(nbr, dtype=np.int32).reshape(nb, 27))
+        check(self.L.mhd_fill_ghosts(self.h, arr, nb, t.ctypes.data_as(C.POINTER(C.c_int)), _sptr(stream)),
+              "mhd_fill_ghosts")
 
     # --------------------------------------------------- baryon-mass ledger
     def ledger(self, enable: bool = True):
