@@ -205,17 +205,20 @@ long long mhd_kernel_launches(const mhd_ctx* ctx);
 /* Ghost zones of the blocks of a list from same-level neighbours: copies, no
  * prolongation or restriction.  The paper's AMR driver fills them with
  * prolongation and restriction at level changes (Sec. 2); that part is not
- * here.  nbr: host int [nblocks][27], entry (dz+1)*9 + (dy+1)*3 + (dx+1) for
- * the ghost region in direction (dx, dy, dz) (entry 13 is ignored):
- *   >= 0  the neighbouring block of the list in that direction (same n and
- *         ng; periodic wrap: the block across the domain, or the block
- *         itself), whose interior cells and faces there are copied;
- *   -1    zero-gradient outflow: the block's own boundary cells and faces;
+ * here.  nbr: host int [nblocks][6], the neighbour across each side, in the
+ * order -x, +x, -y, +y, -z, +z:
+ *   >= 0  a block of the list (same n and ng, and at least ng cells along
+ *         that axis; periodic wrap: the block across the domain, or the
+ *         block itself, which wraps modulo n for any n);
+ *   -1    zero-gradient outflow: copies of the block's own boundary layer;
  *   -2    leave these ghosts untouched.
- * Fills cons and the three face-field arrays (not cons0/bf0/prim: con2prim
- * recomputes prim and bcc on the ghost layers it needs).  MHD_EINVAL on a bad
- * entry or a neighbour of another size.  Asynchronous on the stream; nbr may
- * be reused after return. */
+ * The fill runs along x, then y, then z, each pass over the whole extent of
+ * the other axes (ghosts included), so edges and corners combine the sides'
+ * rules (e.g. outflow along x and periodic along y).  Fills cons and the
+ * three face-field arrays (not cons0/bf0/prim: con2prim recomputes prim and
+ * bcc on the ghost layers it needs).  MHD_EINVAL on a bad entry or a
+ * neighbour of another size.  Asynchronous on the stream; nbr may be reused
+ * after return. */
 int mhd_fill_ghosts(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, const int* nbr, void* stream);
 
 int mhd_ledger(mhd_ctx* ctx, int enable);

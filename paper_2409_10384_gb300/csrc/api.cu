@@ -590,15 +590,18 @@ int mhd_fill_ghosts(mhd_ctx* c, const mhd_block* blocks, int nb, const int* nbr,
   int r = prepare(c, blocks, nb);
   if (r) return r;
   for (int i = 0; i < nb; i++)
-    for (int q = 0; q < 27; q++) {
-      const int v = nbr[(size_t)i * 27 + q];
+    for (int q = 0; q < 6; q++) {
+      const int v = nbr[(size_t)i * 6 + q];
       if (v < -2 || v >= nb) return MHD_EINVAL;
       if (v >= 0 && (blocks[v].ng != blocks[i].ng || blocks[v].n[0] != blocks[i].n[0] ||
                      blocks[v].n[1] != blocks[i].n[1] || blocks[v].n[2] != blocks[i].n[2]))
         return MHD_EINVAL;
+      // another block supplies whole ghost layers only if it is at least ng
+      // wide along the axis (the block itself wraps modulo n)
+      if (v >= 0 && v != i && blocks[i].n[q / 2] < blocks[i].ng) return MHD_EINVAL;
     }
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t n = (size_t)nb * 27;
+  const size_t n = (size_t)nb * 6;
   if (n > c->dnbr_n) {
     if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ECUDA;
     if (c->dnbr) cudaFree(c->dnbr);
@@ -611,12 +614,13 @@ int mhd_fill_ghosts(mhd_ctx* c, const mhd_block* blocks, int nb, const int* nbr,
   long long it[W_NKIND];
   list_items(c, it);
   Work w = work_of(c);
-  for (int kind = 0; kind < 4; kind++) {
-    const long long items = kind == 0 ? it[W_INIT] : it[W_GFX + kind - 1];
-    const long long g = std::max(1LL, std::min((items + 255) / 256, (long long)c->nsm * 8));
-    launch_fill_ghosts(w, c->dnbr, kind, s, (int)g);
-    c->launches += 1;
-  }
+  for (int ax = 0; ax < 3; ax++)
+    for (int kind = 0; kind < 4; kind++) {
+      const long long items = kind == 0 ? it[W_INIT] : it[W_GFX + kind - 1];
+      const long long g = std::max(1LL, std::min((items + 255) / 256, (long long)c->nsm * 8));
+      launch_fill_ghosts(w, c->dnbr, kind, ax, s, (int)g);
+      c->launches += 1;
+    }
   return cuda_ok(cudaGetLastError());
 }
 

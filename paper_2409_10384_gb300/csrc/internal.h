@@ -22,7 +22,7 @@ void launch_update_cells(const Work& w, const Par& P, double g0, double g1, doub
 // baryon-mass ledger: fold the floor mass of the last con2prim (weight wF)
 // and -dtb x the outward boundary D~ flux of the stage into each block's
 // balance; interior mass sum D~ dV of each block into out[id]
-void launch_fill_ghosts(const Work& w, const int* nbr, int kind, cudaStream_t s, int grid);
+void launch_fill_ghosts(const Work& w, const int* nbr, int kind, int ax, cudaStream_t s, int grid);
 void launch_ledger_stage(const Work& w, double wF, double dtb, cudaStream_t s);
 void launch_block_mass(const Work& w, double* out, cudaStream_t s);
 void launch_update_faces(const Work& w, double g0, double g1, double bdt, int first, cudaStream_t s, int grid);

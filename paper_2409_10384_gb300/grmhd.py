@@ -333,10 +333,11 @@ class Context:
         return t.value, w.value
 
     def fill_ghosts(self, blocks, nbr, stream=None):
-        """Ghost zones from same-level neighbours: nbr int [nblocks][27]
-        (neighbour block index, -1 outflow, -2 untouched)."""
+        """Ghost zones from same-level neighbours: nbr int [nblocks][6] over
+        the sides -x, +x, -y, +y, -z, +z (neighbour block index, -1 outflow,
+        -2 untouched)."""
         arr, nb = self._blocks(blocks)
-        t = np.ascontiguousarray(np.asarray(nbr, dtype=np.int32).reshape(nb, 27))
+        t = np.ascontiguousarray(np.asarray(nbr, dtype=np.int32).reshape(nb, 6))
         check(self.L.mhd_fill_ghosts(self.h, arr, nb, t.ctypes.data_as(C.POINTER(C.c_int)), _sptr(stream)),
               "mhd_fill_ghosts")
 

@@ -353,3 +353,109 @@ def bns_blocks(seed: int = 5, n: int = 32, levels: int = 6, dx0: float = 0.75, L
         else:
             hi = mid
     return best, centres
+
+
+# ---------------------------------------------------------------------------
+# Flat-space test problems of Sec. 4.1-4.3 (initial data only).
+
+# Balsara shock tubes (Table 1): Gamma, then left and right states
+# (rho, P, v^x, v^y, v^z, B^x, B^y, B^z); discontinuity at x = 0.5.
+BALSARA = {
+    1: (2.0, (1.0, 1.0, 0.0, 0.0, 0.0, 0.5, 1.0, 0.0), (0.125, 0.1, 0.0, 0.0, 0.0, 0.5, -1.0, 0.0)),
+    2: (5.0 / 3.0, (1.0, 30.0, 0.0, 0.0, 0.0, 5.0, 6.0, 6.0), (1.0, 1.0, 0.0, 0.0, 0.0, 5.0, 0.7, 0.7)),
+    3: (5.0 / 3.0, (1.0, 1e3, 0.0, 0.0, 0.0, 10.0, 7.0, 7.0), (1.0, 0.1, 0.0, 0.0, 0.0, 10.0, 0.7, 0.7)),
+    4: (5.0 / 3.0, (1.0, 0.1, 0.999, 0.0, 0.0, 10.0, 7.0, 7.0), (1.0, 0.1, -0.999, 0.0, 0.0, 10.0, -7.0, -7.0)),
+    5: (5.0 / 3.0, (1.08, 0.95, 0.4, 0.3, 0.2, 2.0, 0.3, 0.3), (1.0, 1.0, -0.45, -0.2, 0.2, 2.0, -0.7, 0.5)),
+}
+
+
+def _flat_adm(shape):
+    adm = np.zeros((16,) + shape)
+    adm[0] = 1.0
+    adm[4] = adm[7] = adm[9] = 1.0
+    return adm
+
+
+def _w(vx, vy, vz):
+    W = 1.0 / np.sqrt(1.0 - (vx * vx + vy * vy + vz * vz))
+    return W * vx, W * vy, W * vz
+
+
+def balsara_tube(test: int, n: int, ny: int = 2, ng: int = 4) -> BlockInputs:
+    """Table 1 Riemann problem on x in [0, 1] (n cells), ny x ny cells of the
+    same width across.  Face B~ from an edge potential whose discrete curl is
+    exactly the piecewise-constant field: A_y = int_0^x B^z, A_z = B^x y -
+    int_0^x B^y (the jump sits on a face for even n)."""
+    _, Ls, Rs = BALSARA[test]
+    nn = (n, ny, ny)
+    dx = (1.0 / n,) * 3
+    x0 = (0.0, 0.0, 0.0)
+    x, y, z = _grid(nn, ng, dx, x0)
+    left = x < 0.5
+    pick = lambda a, b: np.where(left, a, b)
+    rho, P = pick(Ls[0], Rs[0]), pick(Ls[1], Rs[1])
+    wx, wy, wz = (pick(a, b) for a, b in zip(_w(*Ls[2:5]), _w(*Rs[2:5])))
+    prim = np.stack([rho, wx, wy, wz, P])
+    prim = np.ascontiguousarray(prim * np.ones_like(x))
+
+    def integral(xe, cL, cR):   # int_0^x of the piecewise-constant field
+        return np.where(xe < 0.5, cL * xe, cL * 0.5 + cR * (xe - 0.5))
+
+    A = []
+    stags = [(0, 1, 1), (1, 0, 1), (1, 1, 0)]
+    for c in range(3):
+        ex, ey, ez = _grid(nn, ng, dx, x0, stag=stags[c])
+        if c == 0:
+            a = np.zeros_like(ex)
+        elif c == 1:
+            a = integral(ex, Ls[7], Rs[7])
+        else:
+            a = Ls[5] * ey - integral(ex, Ls[6], Rs[6])
+        A.append(np.ascontiguousarray(a))
+    return BlockInputs(nn, ng, dx, x0, prim, tuple(A), _flat_adm(x.shape))
+
+
+def field_loop(n: int, ng: int = 4, A0: float = 1e-3, R: float = 0.3) -> BlockInputs:
+    """Magnetic loop advection (Sec. 4.3): A_z = A0 (R - r) inside r = R on the
+    periodic square [-0.5, 0.5]^2 (n x n cells, one cell across z), rho = 1,
+    P = 3, v = (1/1.2, 1/2.4, 0)."""
+    nn = (n, n, 1)
+    dx = (1.0 / n,) * 3
+    x0 = (-0.5, -0.5, 0.0)
+    x, y, z = _grid(nn, ng, dx, x0, wrap=True)
+    wx, wy, wz = _w(1.0 / 1.2, 1.0 / 2.4, 0.0)
+    prim = np.stack([np.ones_like(x), wx * np.ones_like(x), wy * np.ones_like(x), np.zeros_like(x),
+                     3.0 * np.ones_like(x)])
+    A = []
+    stags = [(0, 1, 1), (1, 0, 1), (1, 1, 0)]
+    for c in range(3):
+        ex, ey, ez = _grid(nn, ng, dx, x0, stag=stags[c], wrap=True)
+        if c < 2:
+            a = np.zeros_like(ex)
+        else:
+            r = np.sqrt(ex * ex + ey * ey)
+            a = np.where(r <= R, A0 * (R - r), 0.0)
+        A.append(np.ascontiguousarray(a))
+    return BlockInputs(nn, ng, dx, x0, np.ascontiguousarray(prim), tuple(A), _flat_adm(x.shape))
+
+
+def cylindrical_blast(bx: float, n: int, ng: int = 4, L: float = 12.0) -> BlockInputs:
+    """Magnetised cylindrical blast (Sec. 4.2, after Komissarov 1999) on
+    [-6, 6]^2 (n x n cells, one across z): rho = 1e-2, P = 1 inside r = 0.8,
+    rho = 1e-4, P = 3e-5 outside r = 1, log-linear in between (our reading of
+    "decay exponentially"); v = 0; B = (bx, 0, 0) from A_z = bx y."""
+    nn = (n, n, 1)
+    dx = (L / n,) * 3
+    x0 = (-L / 2, -L / 2, 0.0)
+    x, y, z = _grid(nn, ng, dx, x0)
+    r = np.sqrt(x * x + y * y)
+    t = np.clip((r - 0.8) / 0.2, 0.0, 1.0)
+    rho = np.exp((1 - t) * np.log(1e-2) + t * np.log(1e-4))
+    P = np.exp((1 - t) * np.log(1.0) + t * np.log(3e-5))
+    prim = np.stack([rho, np.zeros_like(x), np.zeros_like(x), np.zeros_like(x), P])
+    A = []
+    stags = [(0, 1, 1), (1, 0, 1), (1, 1, 0)]
+    for c in range(3):
+        ex, ey, ez = _grid(nn, ng, dx, x0, stag=stags[c])
+        A.append(np.ascontiguousarray(bx * ey if c == 2 else np.zeros_like(ex)))
+    return BlockInputs(nn, ng, dx, x0, np.ascontiguousarray(prim), tuple(A), _flat_adm(x.shape))

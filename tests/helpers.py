@@ -11,14 +11,19 @@ def interior(b):
 
 
 def _fill_axis(a, axis, n, ng, mode, stag):
+    if mode == "none":
+        return
     a_ = np.moveaxis(a, axis, -1)
     if mode == "periodic":
+        # every ghost index takes the interior index congruent modulo n (any n)
+        L = a_.shape[-1]
+        idx = np.arange(L)
         if stag:
-            a_[..., :ng] = a_[..., n:n + ng]
-            a_[..., n + ng + 1:] = a_[..., ng + 1:2 * ng + 1]
+            ghost = (idx < ng) | (idx > n + ng)
         else:
-            a_[..., :ng] = a_[..., n:n + ng]
-            a_[..., n + ng:] = a_[..., ng:2 * ng]
+            ghost = (idx < ng) | (idx >= n + ng)
+        src = ng + np.mod(idx - ng, n)
+        a_[..., ghost] = a_[..., src[ghost]]
     else:  # outflow: copy the edge value outward
         if stag:
             a_[..., :ng] = a_[..., ng:ng + 1]

@@ -60,13 +60,13 @@ def test_single_block(G, mode):
     b = _garbled(ob, 5)
     ex = b.copy()
     fill_ghosts(ex, (mode,) * 3)
-    _check(G, [b], [ex], np.full((1, 27), 0 if mode == "periodic" else -1))
+    _check(G, [b], [ex], np.full((1, 6), 0 if mode == "periodic" else -1))
 
 
 def test_two_blocks_tile_a_periodic_domain(G):
     """Blocks A (x in [0, n)) and B (x in [n, 2n)) of a periodic 2n x n x n
-    domain: every ghost region of A in a direction with dx = -+1 comes from B
-    and vice versa; y and z wrap onto the block itself."""
+    domain: A's x neighbours on both sides are B and vice versa; y and z wrap
+    onto the block itself."""
     p = O.params()
     n, g = 8, 4
     rng = np.random.default_rng(7)
@@ -91,28 +91,30 @@ def test_two_blocks_tile_a_periodic_domain(G):
         b.bf0 = [x.copy() for x in b.bf]
         blocks.append(b)
         expect.append(e)
-    nbr = np.zeros((2, 27), np.int32)
-    for ix in range(2):
-        for q in range(27):
-            dx = q % 3 - 1
-            nbr[ix, q] = (ix + dx) % 2
+    nbr = np.array([[1, 1, 0, 0, 0, 0], [0, 0, 1, 1, 1, 1]], np.int32)
     _check(G, blocks, expect, nbr)
 
 
-def test_untouched_directions(G):
-    """-2 leaves a region as it was; the others are filled."""
+def test_mixed_outflow_and_periodic_sides(G):
+    """Outflow along x, periodic along y and z, on a block thinner than its
+    ghost depth across (4 ghosts, 2 and 1 cells): the edges and corners
+    combine the rules of their sides, as the harness's axis-by-axis fill."""
+    p = O.params()
+    inp = synth.balsara_tube(1, 16, ny=2)
+    ob = O.init_block(p, inp.n, inp.ng, inp.dx, inp.adm, inp.prim, inp.A)
+    b = _garbled(ob, 11)
+    ex = b.copy()
+    fill_ghosts(ex, ("outflow", "periodic", "periodic"))
+    _check(G, [b], [ex], np.array([[-1, -1, 0, 0, 0, 0]], np.int32))
+
+
+def test_untouched_sides(G):
+    """-2 leaves the ghosts of a side as they were: with both z sides at -2,
+    the x and y passes still fill their ghosts in every z layer."""
     p = O.params()
     inp = synth.periodic_flat(seed=2, n=8)
     ob = O.init_block(p, inp.n, inp.ng, inp.dx, inp.adm, inp.prim, inp.A)
     b = _garbled(ob, 9)
     ex = b.copy()
-    fill_ghosts(ex)
-    nbr = np.zeros((1, 27), np.int32)
-    nbr[0, 4] = -2          # (dx, dy, dz) = (0, 0, -1): the whole low-z ghost slab
-    g = b.ng
-    n = b.n[0]
-    ex.cons[:, :g, g:g + n, g:g + n] = b.cons[:, :g, g:g + n, g:g + n]
-    for d in range(3):
-        sl = [slice(0, g), slice(g, g + n + (d == 1)), slice(g, g + n + (d == 0))]
-        ex.bf[d][tuple(sl)] = b.bf[d][tuple(sl)]
-    _check(G, [b], [ex], nbr)
+    fill_ghosts(ex, ("periodic", "periodic", "none"))
+    _check(G, [b], [ex], np.array([[0, 0, 0, 0, -2, -2]], np.int32))
