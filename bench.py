@@ -65,6 +65,18 @@ def _measured_hbm():
         return None
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest of a per-rank value over the process group (the slowest
+    replica sets the whole-job time); the value itself with one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _env_int(k, d):
     try:
         return int(os.environ.get(k, d))
@@ -496,10 +508,7 @@ def run_ours(args):
     prof = ctx.profile_read()
     ctx.profile(False)
     stats = ctx.read_stats(stream)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, "cuda")
     value = world * zones * args.steps / (ms_max * 1e-3)
 
     # end-to-end through the public API with host buffers: each step copies the
@@ -527,10 +536,7 @@ def run_ours(args):
     stream.synchronize()
     barrier()
     ms_e2e = e2.elapsed_time(e3)
-    t = torch.tensor([ms_e2e], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = world * zones * args.steps / (float(t.item()) * 1e-3)
+    e2e_value = world * zones * args.steps / (max_over_ranks(ms_e2e, world, "cuda") * 1e-3)
 
     # roofline of the dominant kernel (largest share of the timed region)
     kern = {k: v for k, v in prof.items() if v[1] > 0}
