@@ -71,7 +71,12 @@ typedef struct {
                        1 network guess of log(mu), FP32 secant steps, FP64 bracket
                          of relative width 4e-6 around the FP32 root, FP64 solve
                          (needs a network: MHD_ENOMLP otherwise);
-                       2 as 1 but the FP32 steps start from the plain bracket.
+                       2 as 1 but the FP32 steps start from the plain bracket;
+                       3 block con2prims: FP64 bracket of relative half-width
+                         1e-3 around the cell's root of the last stage-input
+                         con2prim (verified by the signs at both ends, else
+                         the plain bracket); the FOFC estimate starts from the
+                         same root.  A new block list starts without roots.
                        The FP64 solve decides the root in every mode. */
 } mhd_params;
 

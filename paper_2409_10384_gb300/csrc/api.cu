@@ -100,7 +100,7 @@ int set_par(mhd_ctx* c, const mhd_params* p) {
   if (!p) return MHD_EINVAL;
   if (!(p->gamma > 1.0) || !(p->rho_atm > 0.0) || !(p->T_atm > 0.0) || !(p->f_thr >= 0.0) || !(p->c2p_tol > 0.0) ||
       !(p->W_max > 1.0) || p->recon < 0 || p->recon > 4 || p->rsolver < 0 || p->rsolver > 1 ||
-      (p->rk_order != 2 && p->rk_order != 3) || p->c2p_maxit < 1 || p->c2p_guess < 0 || p->c2p_guess > 2 ||
+      (p->rk_order != 2 && p->rk_order != 3) || p->c2p_maxit < 1 || p->c2p_guess < 0 || p->c2p_guess > 3 ||
       (p->dmp_M > 0.0 && p->dmp_M < 1.0))
     return MHD_EINVAL;
   c->hp = *p;
@@ -185,6 +185,7 @@ int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
     need += al256(sizeof(double) * (ne[0] + ne[1] + ne[2]));
     need += al256(sizeof(double) * 3 * b.ncell);
     need += al256((size_t)b.ncell);
+    if (c->P.guess == 3) need += al256(sizeof(double) * (size_t)b.ncell);
     const long long n0 = s.n[0], n1 = s.n[1], n2 = s.n[2];
     long long items[W_NKIND];
     items[W_C2P] = (n0 + 6) * (n1 + 6) * (n2 + 6);
@@ -203,7 +204,7 @@ int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
   const size_t krp_off = need;
   need += al256(krp_bytes(nkrp));
   size_t feat_off = 0, logmu_off = 0;
-  if (c->P.guess != 0) {
+  if (c->P.guess == 1 || c->P.guess == 2) {
     feat_off = need;
     need += al256(sizeof(float) * MLP_FSTRIDE * (size_t)nkrp);
     logmu_off = need;
@@ -240,11 +241,18 @@ int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
     p += al256(sizeof(double) * 3 * b.ncell);
     b.fflag = (unsigned char*)p;
     p += al256((size_t)b.ncell);
+    b.mu = nullptr;
+    if (c->P.guess == 3) {
+      b.mu = (double*)p;
+      if (cudaMemset(b.mu, 0, sizeof(double) * (size_t)b.ncell) != cudaSuccess) return MHD_ECUDA;
+      p += al256(sizeof(double) * (size_t)b.ncell);
+    }
   }
   c->krp = c->scratch + krp_off;
   c->krp_n = nkrp;
-  c->gfeat = c->P.guess != 0 ? (float*)(c->scratch + feat_off) : nullptr;
-  c->glogmu = c->P.guess != 0 ? (float*)(c->scratch + logmu_off) : nullptr;
+  const bool seeded = c->P.guess == 1 || c->P.guess == 2;
+  c->gfeat = seeded ? (float*)(c->scratch + feat_off) : nullptr;
+  c->glogmu = seeded ? (float*)(c->scratch + logmu_off) : nullptr;
   c->dmass = (double*)(c->scratch + mass_off);
   c->dledger = c->ledger_on ? (double*)(c->scratch + led_off) : nullptr;
   if (c->dledger && cudaMemset(c->dledger, 0, sizeof(double) * 2 * (size_t)nb) != cudaSuccess) return MHD_ECUDA;
@@ -367,7 +375,7 @@ Work work_of(const mhd_ctx* c) {
 // FP64 brackets.
 void c2p_seed(mhd_ctx* c, const KrpBuf& kb, long long n, cudaStream_t s) {
   const int mode = c->P.guess;
-  if (mode == 0) return;
+  if (mode != 1 && mode != 2) return;
   if (mode == 1)
     timed(c, MHD_K_MLP, s, [&] { launch_mlp_infer(c->gfeat, n, c->nm, c->mlp_wb, c->mlp, c->glogmu, s, c->nsm); });
   const long long g = std::max(1LL, std::min((n + 127) / 128, (long long)c->nsm * std::max(c->occ_krp[5], 1)));
@@ -381,7 +389,7 @@ int enqueue_c2p(mhd_ctx* c, cudaStream_t s, const Work& w, const long long* item
   KrpBuf kb = krp_view(c->krp, items[W_C2P]);
   const mhd_ctx::Cfg& cp = c->cfg[T_C2P_PREP];
   const mhd_ctx::Cfg& cf = c->cfg[T_C2P_FIN];
-  const int learned = c->P.guess != 0 ? 1 : 0;
+  const int learned = (c->P.guess == 1 || c->P.guess == 2) ? 1 : 0;
   float* feat = c->P.guess == 1 ? c->gfeat : nullptr;
   timed(c, MHD_K_C2P, s, [&] {
     launch_krp_prep_block(w, c->P, kb, s, tgrid(c, T_C2P_PREP, items[W_C2P]), cp.threads, learned, feat);
@@ -406,7 +414,7 @@ int enqueue_rhs(mhd_ctx* c, double dt, int stage, cudaStream_t s, const Work& w,
     KrpBuf kb = krp_view(c->krp, items[W_CELL]);
     timed(c, MHD_K_FOFC_FLAG, s, [&] {
       launch_krp_prep_fofc(w, c->P, g0, g1, be * dt, kb, s, tgrid(c, T_FOFC_PREP, items[W_CELL]),
-                           c->cfg[T_FOFC_PREP].threads, c->P.guess != 0 ? 1 : 0,
+                           c->cfg[T_FOFC_PREP].threads, (c->P.guess == 1 || c->P.guess == 2) ? 1 : 0,
                            c->P.guess == 1 ? c->gfeat : nullptr);
     });
     c2p_seed(c, kb, items[W_CELL], s);
@@ -553,7 +561,7 @@ int mhd_set_params(mhd_ctx* c, const mhd_params* p) {
   const int old_guess = c->P.guess;
   int r = set_par(c, p);
   if (!r) destroy_graph(c);
-  if (!r && (old_guess != 0) != (c->P.guess != 0)) {
+  if (!r && old_guess != c->P.guess) {
     cudaDeviceSynchronize();
     c->key.clear();   // the next call re-plans the scratch (guess buffers)
   }
@@ -737,7 +745,9 @@ int mhd_c2p_cells(mhd_ctx* c, long n, double* cons, const double* Bd, const doub
                   unsigned char* flags, int* iters, void* stream) {
   if (!c || n < 0 || (n > 0 && (!cons || !Bd || !g || !prim || !flags))) return MHD_EINVAL;
   if (n == 0) return MHD_OK;
-  const int mode = c->P.guess;  // 0 plain, 1 learned + FP32 search, 2 FP32 search from the plain bracket
+  // 0 plain, 1 learned + FP32 search, 2 FP32 search from the plain bracket;
+  // independent cells have no previous root, so 3 solves as 0
+  const int mode = c->P.guess == 3 ? 0 : c->P.guess;
   if (mode == 1 && !c->mlp_ready) return MHD_ENOMLP;
   cudaStream_t s = (cudaStream_t)stream;
   KrpBuf kb;
@@ -1093,7 +1103,7 @@ int mhd_autotune(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, void* s
       const int th = c->cfg[k].threads;
       switch (k) {
         case T_C2P_PREP:
-          launch_krp_prep_block(w, c->P, kb, s, tgrid(c, k, it[W_C2P]), th, c->P.guess != 0 ? 1 : 0,
+          launch_krp_prep_block(w, c->P, kb, s, tgrid(c, k, it[W_C2P]), th, (c->P.guess == 1 || c->P.guess == 2) ? 1 : 0,
                                 c->P.guess == 1 ? c->gfeat : nullptr);
           break;
         case T_C2P_FIN: launch_krp_finish_block(w, c->P, kb, c->dstats, s, tgrid(c, k, it[W_C2P]), th); break;
@@ -1101,7 +1111,8 @@ int mhd_autotune(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, void* s
           launch_flux_dir(k - T_FX, w, c->P, s, tgrid(c, k, it[W_SX + k - T_FX]), th);
           break;
         case T_FOFC_PREP:
-          launch_krp_prep_fofc(w, c->P, g0, g1, be * dt, kb, s, tgrid(c, k, it[W_CELL]), th, c->P.guess != 0 ? 1 : 0,
+          launch_krp_prep_fofc(w, c->P, g0, g1, be * dt, kb, s, tgrid(c, k, it[W_CELL]), th,
+                               (c->P.guess == 1 || c->P.guess == 2) ? 1 : 0,
                                c->P.guess == 1 ? c->gfeat : nullptr);
           break;
         case T_FOFC_FIN: launch_krp_finish_fofc(w, c->P, kb, c->dstats, s, tgrid(c, k, it[W_CELL]), th); break;

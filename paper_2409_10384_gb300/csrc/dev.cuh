@@ -44,7 +44,11 @@ struct DevBlock {
   double *lf, *la;
   double dV;         // cell volume dx dy dz
   int id;            // index of the block in its list
+  double* mu;        // [ncell] con2prim root of the last stage-input con2prim
+                     // (c2p_guess 3; 0: none), else null
 };
+// Relative half-width of the bracket around a previous root (c2p_guess 3).
+constexpr double WARM_DELTA = 1e-3;
 
 // Work lists: item ranges of every block for one kernel kind.
 enum WorkKind { W_C2P = 0, W_FX, W_FY, W_FZ, W_CELL, W_EDGE, W_FACE, W_INIT, W_SX, W_SY, W_SZ, W_GFX, W_GFY, W_GFZ,

@@ -34,9 +34,11 @@ __device__ __forceinline__ void kw_load(const KrpBuf& kb, const Par& P, long lon
 // prep of one cell: KRP variables and status; learned = false: the plain
 // bracket [0, mu+]; learned = true: status 4 (bracket from the network's
 // guess later).  feat (optional): the network's features of the cell.
+// guess > 0: the cell's previous root; the FP64 bracket starts as
+// guess (1 -+ WARM_DELTA), verified by the signs at both ends (krp_bracket).
 __device__ __forceinline__ void prep_cell(const Par& P, const KrpBuf& kb, long long i, const double* U,
                                           const double* Bd, const Metric& m, bool learned = false,
-                                          float* feat = nullptr, double alpha = 1.0) {
+                                          float* feat = nullptr, double alpha = 1.0, double guess = 0.0) {
   KrpCell k;
   unsigned fl;
   const long long n = kb.n;
@@ -48,7 +50,10 @@ __device__ __forceinline__ void prep_cell(const Par& P, const KrpBuf& kb, long l
       st = 4;
     } else {
       double a, b, Ga, Gb, mu = 0.0;
-      int r = krp_bracket(k.s, -1.0, -1.0, a, b, Ga, Gb, mu, its);
+      const bool warm = guess > 0.0 && guess <= 1.0;
+      const double glo = warm ? guess * (1.0 - WARM_DELTA) : -1.0;
+      const double ghi = warm ? fmin(guess * (1.0 + WARM_DELTA), 1.0) : -1.0;
+      int r = krp_bracket(k.s, glo, ghi, a, b, Ga, Gb, mu, its);
       st = (unsigned char)(r == 0 ? 0 : (r == 1 ? 1 : 2));
       kb.w[KW_A * n + i] = a; kb.w[KW_B * n + i] = b;
       kb.w[KW_GA * n + i] = Ga; kb.w[KW_GB * n + i] = Gb;
@@ -180,7 +185,7 @@ __global__ void __launch_bounds__(256) k_krp_prep_block(Work w, Par P, KrpBuf kb
     double U[5];
 #pragma unroll
     for (int v = 0; v < 5; v++) U[v] = b.cons[v * nc + c];
-    prep_cell(P, kb, it, U, Bd, m, learned != 0, feat, b.adm[c]);
+    prep_cell(P, kb, it, U, Bd, m, learned != 0, feat, b.adm[c], b.mu ? b.mu[c] : 0.0);
   }
 }
 
@@ -202,7 +207,9 @@ __global__ void __launch_bounds__(256) k_krp_finish_block(Work w, Par P, KrpBuf 
     unsigned fl = kb.fl[it];
     const unsigned char st = kb.st[it];
     double pr[5];
-    krp_finish(P, kc, kb.w[KW_MU * n + it], st == 1, fl, pr);
+    const double root = kb.w[KW_MU * n + it];
+    krp_finish(P, kc, root, st == 1, fl, pr);
+    if (b.mu) b.mu[c] = (st == 1 && !(fl & F_FAIL)) ? root : 0.0;
 #pragma unroll
     for (int v = 0; v < 5; v++) b.prim[v * nc + c] = pr[v];
     const double Bd[3] = {b.bcc[c], b.bcc[nc + c], b.bcc[2 * nc + c]};
@@ -277,7 +284,7 @@ __global__ void __launch_bounds__(256) k_krp_prep_fofc(Work w, Par P, double g0,
     Metric m;
     load_metric6(b.adm + 4 * nc, nc, c, m);
     const double Bd[3] = {b.bcc[c], b.bcc[nc + c], b.bcc[2 * nc + c]};
-    prep_cell(P, kb, it, U, Bd, m, learned != 0, feat, b.adm[c]);
+    prep_cell(P, kb, it, U, Bd, m, learned != 0, feat, b.adm[c], b.mu ? b.mu[c] : 0.0);
     kb.w[KW_USD * n + it] = U[0];
     kb.w[KW_UST * n + it] = U[4];
   }

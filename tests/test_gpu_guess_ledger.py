@@ -42,7 +42,7 @@ def _train(G, ctx):
     ctx.mlp_calibrate(feat, logmu, 0.95)
 
 
-@pytest.mark.parametrize("guess", [1, 2])
+@pytest.mark.parametrize("guess", [1, 2, 3])
 def test_stage_with_guessed_con2prim_matches_oracle(G, guess):
     p = O.params(gamma=2.0, rho_atm=1e-12, T_atm=1e-10, recon=2, rsolver=1, rk_order=3, fofc=1)
     inp = synth.star_subblock(sub=24, corner=(96, 52, 52))   # outer star, surface, atmosphere
