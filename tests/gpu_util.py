@@ -52,8 +52,9 @@ def rk_w(p, stage):
 def term_scales(p, ob_in: O.Block, out: dict, dt: float, stage: int):
     """Magnitude of the terms that form each updated value (the scale of its
     rounding error): for U_v, g1|U_v| + g0|U^n_v| + b dt sum_d (|F_d(+)| +
-    |F_d(-)|)/dx_d; tau~ = E~ - D~ also carries the scale of D~, and the three
-    momentum components share the largest scale of the cell.  For a face B~,
+    |F_d(-)|)/dx_d; tau~ = E~ - D~ also carries the scale of D~, the three
+    momentum components share the largest scale of the cell, and they also
+    carry the pressure's rounding (Gamma-1)(D~ + |tau~|) through the faces.  For a face B~,
     g1|B| + g0|B^n| + b dt sum over its four edges of the term magnitude of the
     edge EMF (the four face EMFs it is built from) / dx, and the field
     magnitude of the two adjacent cells.  Inputs are taken after the con2prim
@@ -69,6 +70,11 @@ def term_scales(p, ob_in: O.Block, out: dict, dt: float, stage: int):
     T[:, :, :, :] += be * dt * (F[2][:5, 1:, :, :] + F[2][:5, :-1, :, :]) / ob_in.dx[2]
     T[4] += g1 * U[0] + (g0 * Un[0] if g0 else 0.0)
     T[1:4] = T[1:4].max(axis=0)
+    # the pressure recovered from tau~ = E~ - D~ has the absolute precision of
+    # (Gamma-1)(D~ + |tau~|), and the momentum update takes its differences
+    # over the faces: that rounding enters the momentum scale too
+    Pscale = (p.gamma - 1.0) * (U[0] + U[4])
+    T[1:4] += be * dt * 2.0 * Pscale * sum(1.0 / dx for dx in ob_in.dx)
     # term magnitude of every edge EMF: the four face EMFs it averages and
     # corrects (|F_a[5]| on a-faces, |F_b[6]| on b-faces)
     F0, F1, F2 = F
