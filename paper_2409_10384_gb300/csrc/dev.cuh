@@ -207,14 +207,30 @@ struct KEval {
 // field G.)  f is nearly linear near the root (mu -> mu-hat contracts), which
 // keeps regula falsi fast; a division-free multiple of it is not.
 __device__ __forceinline__ void kev(const KS& s, double mu, KEval& e) {
-  double x = 1.0 / fma(mu, s.b2, 1.0);
-  double mux = mu * x;
-  double rbar2 = x * fma(s.r2, x, mu * (1.0 + x) * s.rb2);
-  double qbar = s.qh - 0.5 * mux * mux * s.rperp2;
-  double v2 = mu * mu * rbar2;
-  e.vcap = v2 > s.vmax2;
-  double vh2 = e.vcap ? s.vmax2 : v2;
-  double W = rsqrt(1.0 - vh2);
+  // x = 1/d, rbar^2 and W from one rsqrt (the d, N, E, y of kev_g below)
+  const double d = fma(mu, s.b2, 1.0);
+  const double N = fma(mu * (d + 1.0), s.rb2, s.r2);
+  const double mu2 = mu * mu, d2 = d * d;
+  double W, x, id2, vh2;
+  e.vcap = mu2 * N > s.vmax2 * d2;
+  if (e.vcap) {
+    x = 1.0 / d;
+    id2 = x * x;
+    vh2 = s.vmax2;
+    W = rsqrt(1.0 - s.vmax2);
+  } else if (N == 0.0) {   // r = 0: at rest, W = 1 exactly (x multiplies r only)
+    x = id2 = vh2 = 0.0;
+    W = 1.0;
+  } else {
+    const double E = fma(-mu2, N, d2);
+    const double y = rsqrt(E * d2);
+    W = d2 * y;
+    id2 = (y * y) * E;
+    x = d * id2;
+    vh2 = (mu2 * N) * id2;
+  }
+  const double rbar2 = N * id2;
+  const double qbar = fma(-0.5 * mu2 * s.rperp2, id2, s.qh);
   double wm1 = vh2 * W * W / (1.0 + W);  // W - 1 without cancellation
   e.eps_raw = fma(W, qbar - mu * rbar2, wm1);
   e.eps = e.eps_raw < s.eps_min ? s.eps_min : e.eps_raw;
@@ -222,6 +238,46 @@ __device__ __forceinline__ void kev(const KS& s, double mu, KEval& e) {
   e.rbar2 = rbar2;
   e.W = W;
   e.G = mu - W / fma(mu * rbar2, W, fma(s.gam, e.eps, 1.0));
+}
+// f(mu) alone, with one division where kev takes two; for the bracket and
+// the root iteration (the recovery at the root uses kev).  With
+// d = 1 + mu b^2, N = r^2 + mu (d + 1) (r.b)^2 and E = d^2 - mu^2 N,
+//   rbar^2 = N / d^2,  1 - v^2 = E / d^2,
+// so y = 1/sqrt(E d^2) gives W = d^2 y and 1/d^2 = y^2 E.  Multiplying by
+// 1 + W clears the other two denominators:
+//   (1 + W) eps_raw = (1 + W) W (qbar - mu rbar^2) + v^2 W^2,
+//   f = mu - W (1 + W) / [(1 + W)(1 + mu rbar^2 W) + Gamma (1 + W) eps].
+// Under the velocity cap (mu^2 N > vmax^2 d^2) W is the capped value and
+// 1/d^2 takes a division; at r = 0 (N = 0) the state is at rest and W = 1
+// exactly, as 1/sqrt(1 - v^2) gives it.  The same function as kev up to
+// rounding.
+__device__ __forceinline__ double kev_g(const KS& s, double mu) {
+  const double d = fma(mu, s.b2, 1.0);
+  const double N = fma(mu * (d + 1.0), s.rb2, s.r2);
+  const double mu2 = mu * mu, d2 = d * d;
+  double W, id2, v2;
+  if (mu2 * N > s.vmax2 * d2) {
+    const double x = 1.0 / d;
+    id2 = x * x;
+    v2 = s.vmax2;
+    W = rsqrt(1.0 - s.vmax2);
+  } else if (N == 0.0) {   // r = 0 (then r_perp = 0 too): at rest, W = 1 exactly
+    id2 = v2 = 0.0;
+    W = 1.0;
+  } else {
+    const double E = fma(-mu2, N, d2);
+    const double y = rsqrt(E * d2);
+    W = d2 * y;
+    id2 = (y * y) * E;
+    v2 = (mu2 * N) * id2;
+  }
+  const double rbar2 = N * id2;
+  const double A = fma(-fma(0.5 * mu2, s.rperp2, mu * N), id2, s.qh);   // qbar - mu rbar^2
+  const double P1 = 1.0 + W;
+  const double T = fma(P1 * W, A, v2 * (W * W));                          // (1 + W) eps_raw
+  const double Te = T < s.eps_min * P1 ? s.eps_min * P1 : T;
+  const double Z = fma(P1, fma(mu * rbar2, W, 1.0), s.gam * Te);
+  return mu - (W * P1) / Z;
 }
 // f(0) = -1/(1 + Gamma eps(0)): at mu = 0, v = 0, W = 1 and eps = qbar = q_h.
 __device__ __forceinline__ double f_zero(const KS& s) {
@@ -237,9 +293,10 @@ __device__ __forceinline__ double mu_plus(const KS& s) {
   double mu = rsqrt(1.0 + rpar2);
 #pragma unroll
   for (int it = 0; it < 3; it++) {
-    double x = 1.0 / fma(mu, s.b2, 1.0);
-    double rbar2 = x * fma(s.r2, x, mu * (1.0 + x) * s.rb2);
-    mu = rsqrt(1.0 + rbar2);
+    // 1/sqrt(1 + rbar^2) = d / sqrt(d^2 + N) with d, N as in kev_g
+    const double d = fma(mu, s.b2, 1.0);
+    const double N = fma(mu * (d + 1.0), s.rb2, s.r2);
+    mu = d * rsqrt(fma(d, d, N));
   }
   return mu;
 }
@@ -273,7 +330,6 @@ __device__ __forceinline__ bool illinois(const KS& s, double a, double Ga, doubl
   if (Gb == 0.0) { root = b; return true; }
   double Fa = Ga, Fb = Gb;
   int side = 0;
-  KEval e;
   while (b - a > tol * b) {
     if (iters >= maxit) return false;
     iters++;
@@ -283,13 +339,13 @@ __device__ __forceinline__ bool illinois(const KS& s, double a, double Ga, doubl
     const double eta = 0.25 * tol * b;
     c += side == -1 ? eta : (side == 1 ? -eta : 0.0);
     if (!(c > a && c < b)) c = 0.5 * (a + b);
-    kev(s, c, e);
-    if (e.G < 0.0) {
-      a = c; Ga = e.G; Fa = e.G;
+    const double G = kev_g(s, c);
+    if (G < 0.0) {
+      a = c; Ga = G; Fa = G;
       if (side == -1) Fb *= 0.5;
       side = -1;
-    } else if (e.G > 0.0) {
-      b = c; Gb = e.G; Fb = e.G;
+    } else if (G > 0.0) {
+      b = c; Gb = G; Fb = G;
       if (side == 1) Fa *= 0.5;
       side = 1;
     } else {
@@ -343,10 +399,10 @@ __device__ __forceinline__ bool krp_prep(const Par& P, const double* U, const do
     flags |= F_TAU;
   }
   KS& s = k.s;
-  double iD = 1.0 / D;
+  const double isD = rsqrt(D);
+  const double iD = isD * isD;
   double rl[3] = {Sl[0] * iD, Sl[1] * iD, Sl[2] * iD};
   lower3(m.gi, rl, k.ru);
-  double isD = sqrt(iD);
   k.bu[0] = B[0] * isD; k.bu[1] = B[1] * isD; k.bu[2] = B[2] * isD;
   s.b2 = B2 * iD;
   s.r2 = dot3(rl, k.ru);
@@ -368,35 +424,30 @@ __device__ __forceinline__ bool krp_prep(const Par& P, const double* U, const do
 // Returns 0: solve needed; 1: root found (in mu); 2: no bracket (failure).
 __device__ __forceinline__ int krp_bracket(const KS& s, double glo, double ghi, double& a, double& b, double& Ga,
                                            double& Gb, double& mu, int& iters) {
-  KEval e;
   a = 0.0; Ga = f_zero(s); b = 1.0; Gb = 0.0;
   iters = 0;
   bool have = false;
   if (glo >= 0.0 && ghi > glo) {
-    KEval el, eh;
-    kev(s, glo, el);
-    kev(s, ghi, eh);
-    if (el.G < 0.0 && eh.G >= 0.0) {
-      a = glo; Ga = el.G; b = ghi; Gb = eh.G; have = true;
-    } else if (el.G >= 0.0) {
-      b = glo; Gb = el.G; have = true;
+    const double Gl = kev_g(s, glo), Gh = kev_g(s, ghi);
+    if (Gl < 0.0 && Gh >= 0.0) {
+      a = glo; Ga = Gl; b = ghi; Gb = Gh; have = true;
+    } else if (Gl >= 0.0) {
+      b = glo; Gb = Gl; have = true;
     } else {
-      a = ghi; Ga = eh.G;
+      a = ghi; Ga = Gh;
     }
     iters += 2;
   }
   if (!have) {
     double mp = mu_plus(s);
     if (mp <= a) mp = 1.0;
-    kev(s, mp, e);
     iters++;
-    b = mp; Gb = e.G;
+    b = mp; Gb = kev_g(s, mp);
     if (Gb < 0.0) {
       a = mp; Ga = Gb;
       b = 1.0;
-      kev(s, b, e);
       iters++;
-      Gb = e.G;
+      Gb = kev_g(s, b);
     }
   }
   if (!(Ga < 0.0 && Gb >= 0.0)) return 2;

@@ -130,14 +130,13 @@ __global__ void __launch_bounds__(256) k_krp_solve(Par P, KrpBuf kb, unsigned lo
         const double eta = 0.25 * P.tol * b;
         c += side == -1 ? eta : (side == 1 ? -eta : 0.0);
         if (!(c > a && c < b)) c = 0.5 * (a + b);
-        KEval e;
-        kev(s, c, e);
-        if (e.G < 0.0) {
-          a = c; Ga = e.G; Fa = e.G;
+        const double G = kev_g(s, c);
+        if (G < 0.0) {
+          a = c; Ga = G; Fa = G;
           if (side == -1) Fb *= 0.5;
           side = -1;
-        } else if (e.G > 0.0) {
-          b = c; Gb = e.G; Fb = e.G;
+        } else if (G > 0.0) {
+          b = c; Gb = G; Fb = G;
           if (side == 1) Fa *= 0.5;
           side = 1;
         } else {

@@ -394,42 +394,41 @@ __global__ void __launch_bounds__(128) k_krp_seed(Par P, KrpBuf kb, const float*
     }
     double m32 = (double)x1;
     if (!(m32 > 1e-300 && m32 <= 1.0)) m32 = 0.5;
-    KEval e;
-    kev(s, m32, e);
+    double G = kev_g(s, m32);
     int its = 1;
     double a = 0.0, b = 1.0, Ga = f_zero(s), Gb = 0.0;
     unsigned char st = 0;
-    if (e.G == 0.0) {
+    if (G == 0.0) {
       st = 1;
       kb.w[KW_MU * n + i] = m32;
-    } else if (e.G < 0.0) {
-      a = m32; Ga = e.G;
+    } else if (G < 0.0) {
+      a = m32; Ga = G;
       double x = fmin(m32 * (1.0 + 4e-6), 1.0);
-      kev(s, x, e);
+      G = kev_g(s, x);
       its++;
-      if (e.G >= 0.0) {
-        b = x; Gb = e.G;
+      if (G >= 0.0) {
+        b = x; Gb = G;
       } else {
-        a = x; Ga = e.G;
+        a = x; Ga = G;
         b = 1.0;
-        kev(s, b, e);
+        G = kev_g(s, b);
         its++;
-        Gb = e.G;
+        Gb = G;
         if (!(Gb >= 0.0)) st = 2;
       }
       if (st == 0 && Gb == 0.0) { st = 1; kb.w[KW_MU * n + i] = b; }
     } else {
-      b = m32; Gb = e.G;
+      b = m32; Gb = G;
       double x = m32 * (1.0 - 4e-6);
-      kev(s, x, e);
+      G = kev_g(s, x);
       its++;
-      if (e.G < 0.0) {
-        a = x; Ga = e.G;
-      } else if (e.G == 0.0) {
+      if (G < 0.0) {
+        a = x; Ga = G;
+      } else if (G == 0.0) {
         st = 1;
         kb.w[KW_MU * n + i] = x;
       } else {
-        b = x; Gb = e.G;
+        b = x; Gb = G;
       }
     }
     kb.w[KW_A * n + i] = a; kb.w[KW_B * n + i] = b;
