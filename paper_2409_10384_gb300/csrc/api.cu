@@ -160,6 +160,11 @@ int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
   }
   destroy_graph(c);
   cudaDeviceSynchronize();
+  std::vector<int> nn(3 * (size_t)nb);
+  for (int i = 0; i < nb; i++)
+    for (int d = 0; d < 3; d++) nn[3 * (size_t)i + d] = blocks[i].n[d];
+  int seg[3];
+  for (int d = 0; d < 3; d++) seg[d] = flux_seg_len((const int (*)[3])nn.data(), nb, d, c->nsm);
   std::vector<DevBlock> hb(nb);
   std::vector<long long> pre((size_t)W_NKIND * (nb + 1), 0);
   size_t need = 0;
@@ -176,6 +181,7 @@ int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
       b.bf0[d] = s.bf0[d];
     }
     b.ng = s.ng;
+    for (int d = 0; d < 3; d++) b.nseg[d] = flux_nseg(s.n[d], seg[d]);
     b.ncell = ncell_of(s);
     b.cons = s.cons; b.cons0 = s.cons0; b.prim = s.prim; b.bcc = s.bcc; b.adm = s.adm; b.flags = s.flags;
     const long long N0 = b.N[0], N1 = b.N[1], N2 = b.N[2];
@@ -196,7 +202,7 @@ int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
     items[W_EDGE] = (n0 + 1) * (n1 + 1) * (n2 + 1);
     items[W_FACE] = (n0 + 1) * n1 * n2 + n0 * (n1 + 1) * n2 + n0 * n1 * (n2 + 1);
     items[W_INIT] = b.ncell;
-    for (int d = 0; d < 3; d++) items[W_SX + d] = flux_seg_items(s.n, d);
+    for (int d = 0; d < 3; d++) items[W_SX + d] = flux_seg_items(s.n, d, seg[d]);
     for (int d = 0; d < 3; d++) items[W_GFX + d] = nf[d];   // every entry of face array d
     for (int k = 0; k < W_NKIND; k++) pre[(size_t)k * (nb + 1) + i + 1] = pre[(size_t)k * (nb + 1) + i] + items[k];
   }

@@ -29,6 +29,7 @@ struct Par {
 // One meshblock as seen by the kernels: caller arrays plus context scratch.
 struct DevBlock {
   int n[3], ng, N[3];
+  int nseg[3];       // flux-sweep segments per transverse line of direction d
   long long ncell;
   double dx[3], idx[3];
   double *cons, *cons0, *prim, *bcc;
@@ -56,13 +57,30 @@ enum WorkKind { W_C2P = 0, W_FX, W_FY, W_FZ, W_CELL, W_EDGE, W_FACE, W_INIT, W_S
 
 // Flux sweeps: the n_d + 1 faces of direction d on one transverse line (one
 // extra line on each side, for the CT stencil) are split into near-equal
-// segments of at most FLUX_SEG faces; one thread sweeps one segment.
+// segments of at most L faces; one thread sweeps one segment.  L is FLUX_SEG
+// unless the block list is too small to give every SM two waves of sweeps at
+// that length; then it halves (down to 1) until it does (flux_seg_len).
 constexpr int FLUX_SEG = 16;
-__host__ __device__ inline int flux_nseg(int nd) { return (nd + FLUX_SEG) / FLUX_SEG; }
-__host__ __device__ inline long long flux_seg_items(const int* n, int d) {
+// segments per line for an interior of n cells (n + 1 faces)
+__host__ __device__ inline int flux_nseg(int n, int L) { return (n + L) / L; }
+__host__ __device__ inline long long flux_seg_items(const int* n, int d, int L) {
   long long t = 1;
-  for (int a = 0; a < 3; a++) t *= a == d ? (long long)flux_nseg(n[a]) : (long long)(n[a] + 2);
+  for (int a = 0; a < 3; a++) t *= a == d ? (long long)flux_nseg(n[a], L) : (long long)(n[a] + 2);
   return t;
+}
+// Segment length of direction d for a list of nb blocks with interiors n[b][3]
+// on a GPU of nsm SMs: the largest L <= FLUX_SEG (a power of two) with at
+// least 2 nsm 256 segments, else 1.
+inline int flux_seg_len(const int (*n)[3], int nb, int d, int nsm) {
+  const long long target = 2LL * nsm * 256;
+  int L = FLUX_SEG;
+  while (L > 1) {
+    long long segs = 0;
+    for (int b = 0; b < nb; b++) segs += flux_seg_items(n[b], d, L);
+    if (segs >= target) break;
+    L /= 2;
+  }
+  return L;
 }
 
 // Slots of the per-cell con2prim scratch (SoA, [KW_N][n]).

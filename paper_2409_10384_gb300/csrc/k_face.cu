@@ -40,7 +40,7 @@ __device__ __forceinline__ void face_flux_donor(const DevBlock& b, const Par& P,
 // upper side of the segment's first face, nf its number of faces.
 template <int d>
 __device__ __forceinline__ void seg_coords(const DevBlock& b, int loc, int& k, int& j, int& i, int& nf) {
-  const int ns = flux_nseg(b.n[d]), nd = b.n[d] + 1;
+  const int ns = b.nseg[d], nd = b.n[d] + 1;
   int s, a0, a1;
   if (d == 0) {
     s = loc % ns; int r = loc / ns; a0 = r % (b.n[1] + 2); a1 = r / (b.n[1] + 2);

@@ -142,6 +142,11 @@ extern "C" int mhd_stage_noalloc(const mhd_params* p, const mhd_block* blk, doub
   }
   b.N[0] = (int)N0; b.N[1] = (int)N1; b.N[2] = (int)N2;
   b.ng = s.ng;
+  int seg[3];
+  for (int d = 0; d < 3; d++) {
+    seg[d] = flux_seg_len((const int (*)[3])s.n, 1, d, nsm);
+    b.nseg[d] = flux_nseg(s.n[d], seg[d]);
+  }
   b.ncell = ncell;
   b.cons = s.cons; b.cons0 = s.cons0; b.prim = s.prim; b.bcc = s.bcc; b.adm = s.adm; b.flags = s.flags;
   unsigned char* q = base + kOffData;
@@ -169,7 +174,7 @@ extern "C" int mhd_stage_noalloc(const mhd_params* p, const mhd_block* blk, doub
   items[W_EDGE] = (n0 + 1) * (n1 + 1) * (n2 + 1);
   items[W_FACE] = (n0 + 1) * n1 * n2 + n0 * (n1 + 1) * n2 + n0 * n1 * (n2 + 1);
   items[W_INIT] = ncell;
-  for (int d = 0; d < 3; d++) items[W_SX + d] = flux_seg_items(s.n, d);
+  for (int d = 0; d < 3; d++) items[W_SX + d] = flux_seg_items(s.n, d, seg[d]);
   for (int d = 0; d < 3; d++) items[W_GFX + d] = nf[d];
   PreTable t;
   for (int k = 0; k < W_NKIND; k++) {
