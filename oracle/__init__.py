@@ -55,6 +55,8 @@ class Params(C.Structure):
         ("alpha_exc", C.c_double),
         ("recon", C.c_int), ("rsolver", C.c_int), ("fofc", C.c_int), ("rk_order", C.c_int),
         ("c2p_maxit", C.c_int), ("pad_", C.c_int),
+        ("eos", C.c_int), ("eos_pieces", C.c_int), ("eos_K0", C.c_double), ("eos_gamma_th", C.c_double),
+        ("eos_rho", C.c_double * 3), ("eos_gamma", C.c_double * 4),
     ]
 
 
@@ -100,6 +102,9 @@ def lib(counting: bool = False):
                                        C.c_void_p, C.c_void_p, C.c_void_p]
             L.or_face_flux.argtypes = [C.POINTER(Params), C.c_int, C.c_void_p, C.c_void_p, C.c_double,
                                        C.c_void_p, C.c_void_p]
+            L.or_eos.argtypes = [C.POINTER(Params), C.c_double, C.c_double, C.c_void_p]
+            L.or_eos_press.argtypes = [C.POINTER(Params), C.c_double, C.c_double]
+            L.or_eos_press.restype = C.c_double
             L.or_emf_edge.argtypes = [C.c_void_p, C.c_void_p]
             L.or_emf_edge.restype = C.c_double
             L.or_flop_counts.argtypes = [C.POINTER(C.c_longlong)]
@@ -115,12 +120,31 @@ def lib(counting: bool = False):
 def params(**kw) -> Params:
     """Defaults: ideal gas Gamma=5/3, flat-space parity setup (configuration 1)."""
     d = dict(gamma=5.0 / 3.0, rho_atm=1e-12, T_atm=1e-10, f_thr=0.1, sigma_max=0.0, dmp_M=0.0,
-             c2p_tol=1e-10, W_max=1e3, alpha_exc=0.0, recon=1, rsolver=1, fofc=0, rk_order=2, c2p_maxit=64)
+             c2p_tol=1e-10, W_max=1e3, alpha_exc=0.0, recon=1, rsolver=1, fofc=0, rk_order=2, c2p_maxit=64,
+             eos=0, eos_pieces=1, eos_K0=100.0, eos_gamma_th=2.0, eos_rho=(0.0, 0.0, 0.0),
+             eos_gamma=(2.0, 2.0, 2.0, 2.0))
     d.update(kw)
     p = Params()
     for k, v in d.items():
-        setattr(p, k, v)
+        if k in ("eos_rho", "eos_gamma"):
+            arr = getattr(p, k)
+            for i, x in enumerate(v):
+                arr[i] = x
+        else:
+            setattr(p, k, v)
     return p
+
+
+def eos(p: Params, rho: float, P: float) -> dict:
+    """The oracle's EOS at (rho, P): cold pressure and eps, local index, eps,
+    h and rho h c_s^2."""
+    out = np.zeros(6)
+    lib().or_eos(C.byref(p), float(rho), float(P), _ptr(out))
+    return dict(zip(("Pc", "epsc", "Gi", "eps", "h", "chi"), out.tolist()))
+
+
+def eos_press(p: Params, rho: float, eps: float) -> float:
+    return float(lib().or_eos_press(C.byref(p), float(rho), float(eps)))
 
 
 def _ptr(a: np.ndarray | None):

@@ -61,11 +61,13 @@ static inline bool operator<=(real a, real b) { g_fc.cmp++; return a.v <= b.v; }
 static inline bool operator>=(real a, real b) { g_fc.cmp++; return a.v >= b.v; }
 static inline bool operator==(real a, real b) { g_fc.cmp++; return a.v == b.v; }
 static inline real sqrt_(real a) { g_fc.sqrt++; return real(std::sqrt(a.v)); }
+static inline real pow_(real a, real b) { g_fc.sqrt++; return real(std::pow(a.v, b.v)); }   // counted with sqrt
 static inline double val(real a) { return a.v; }
 static inline bool finite_(real a) { return std::isfinite(a.v); }
 #else
 typedef double real;
 static inline real sqrt_(real a) { return std::sqrt(a); }
+static inline real pow_(real a, real b) { return std::pow(a, b); }
 static inline double val(real a) { return a; }
 static inline bool finite_(real a) { return std::isfinite(a); }
 #define PHASE(k) ((void)0)
@@ -81,7 +83,7 @@ extern "C" {
 typedef struct {
   double gamma;      // ideal-gas adiabatic index (Sec. 3.4)
   double rho_atm;    // atmosphere density (Sec. 3.3)
-  double T_atm;      // atmosphere temperature, T = P/rho (Sec. 3.3)
+  double T_atm;      // atmosphere temperature, T = P/rho; hybrid EOS: the thermal P_th/rho (Sec. 3.3)
   double f_thr;      // density floor threshold factor (Sec. 3.3)
   double sigma_max;  // cap on B^2/D; <= 0 disables (Sec. 3.3)
   double dmp_M;      // relaxed DMP factor M >= 1; <= 0 disables (Eq. 19)
@@ -94,6 +96,16 @@ typedef struct {
   int rk_order;      // 2 or 3 (SSP RK, Sec. 3.2)
   int c2p_maxit;     // iteration cap of the root solve
   int pad_;
+  // equation of state (Sec. 3.4): eos = 0 ideal gas (gamma); eos = 1 hybrid
+  // piecewise polytrope: cold P_c = K_i rho^gamma_i on eos_pieces pieces split
+  // at the densities eos_rho[0..pieces-2], K_0 = eos_K0, plus a thermal ideal
+  // gas of index eos_gamma_th
+  int eos;
+  int eos_pieces;
+  double eos_K0;
+  double eos_gamma_th;
+  double eos_rho[3];
+  double eos_gamma[4];
 } or_params;
 
 typedef struct {
@@ -202,6 +214,76 @@ static inline int sym(int a, int b) {
 }
 
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Equation of state.  Sec. 3.4 names PrimitiveSolver's two analytic EOS: the
+// ideal gas and the piecewise-polytropic hybrid EOS; the paper gives no
+// formulas, so the hybrid EOS here is the standard one: a cold piecewise
+// polytrope (Read et al. 2009) P_c = K_i rho^G_i on [rho_{i-1}, rho_i), the K_i
+// fixed by the continuity of P_c, eps_c = a_i + K_i rho^(G_i - 1)/(G_i - 1) with
+// a_0 = 0 and the a_i fixed by the continuity of eps_c; plus a thermal ideal gas
+// P_th = (G_th - 1) rho (eps - eps_c(rho)).  The temperature is the thermal one,
+// T = P_th / rho (for the ideal gas, with no cold part, T = P / rho).
+//
+// Cold part at rho: P_c, eps_c and the local index G_i (ideal gas: 0, 0, gamma).
+static void eos_cold(const or_params& p, real rho, real& Pc, real& epsc, real& Gi) {
+  if (p.eos == 0) {
+    Pc = 0.0;
+    epsc = 0.0;
+    Gi = p.gamma;
+    return;
+  }
+  int i = 0;
+  while (i < p.eos_pieces - 1 && rho >= real(p.eos_rho[i])) i++;
+  real K = p.eos_K0, a = 0.0;
+  for (int j = 0; j < i; j++) {
+    const real rb = p.eos_rho[j], Gj = p.eos_gamma[j], Gn = p.eos_gamma[j + 1];
+    const real Kn = K * pow_(rb, Gj - Gn);
+    a = a + K * pow_(rb, Gj - 1.0) / (Gj - 1.0) - Kn * pow_(rb, Gn - 1.0) / (Gn - 1.0);
+    K = Kn;
+  }
+  Gi = p.eos_gamma[i];
+  Pc = K * pow_(rho, Gi);
+  epsc = a + K * pow_(rho, Gi - 1.0) / (Gi - 1.0);
+}
+static inline real eos_gth(const or_params& p) { return p.eos ? real(p.eos_gamma_th) : real(p.gamma); }
+// eps(rho, P)
+static real eos_eps(const or_params& p, real rho, real P) {
+  real Pc, epsc, Gi;
+  eos_cold(p, rho, Pc, epsc, Gi);
+  return epsc + (P - Pc) / ((eos_gth(p) - 1.0) * rho);
+}
+// P(rho, eps)
+static real eos_press(const or_params& p, real rho, real eps) {
+  real Pc, epsc, Gi;
+  eos_cold(p, rho, Pc, epsc, Gi);
+  return Pc + (eos_gth(p) - 1.0) * rho * (eps - epsc);
+}
+// specific enthalpy h = 1 + eps + P/rho
+static real eos_h(const or_params& p, real rho, real P) {
+  if (p.eos == 0) return 1.0 + p.gamma / (p.gamma - 1.0) * P / rho;
+  return 1.0 + eos_eps(p, rho, P) + P / rho;
+}
+// rho h c_s^2 = rho (dP/drho at fixed eps) + (P/rho)(dP/deps at fixed rho)
+//             = G_i P_c + G_th P_th  (ideal gas: gamma P)
+static real eos_chi(const or_params& p, real rho, real P) {
+  if (p.eos == 0) return p.gamma * P;
+  real Pc, epsc, Gi;
+  eos_cold(p, rho, Pc, epsc, Gi);
+  return Gi * Pc + eos_gth(p) * (P - Pc);
+}
+// pressure at the temperature floor, P_c(rho) + rho T_atm
+static real eos_pfloor(const or_params& p, real rho) {
+  real Pc, epsc, Gi;
+  eos_cold(p, rho, Pc, epsc, Gi);
+  return Pc + rho * p.T_atm;
+}
+// smallest eps at rho, eps_c(rho) + T_atm/(G_th - 1)
+static real eos_epsmin(const or_params& p, real rho) {
+  real Pc, epsc, Gi;
+  eos_cold(p, rho, Pc, epsc, Gi);
+  return epsc + p.T_atm / (eos_gth(p) - 1.0);
+}
+
 // prim -> cons, Eq. 6 with the densitisation of Sec. 2.
 // prim = rho, w^1..3, P; Bd = densitised B~^i; out = D~, S~_i, tau~.
 static void prim_to_cons(const or_params& p, const real prim[5], const real Bd[3], const real g[6],
@@ -219,7 +301,7 @@ static void prim_to_cons(const or_params& p, const real prim[5], const real Bd[3
   real B2 = dot3(B, Bl);
   real Bv = dot3(B, vl);
   real rho = prim[0], P = prim[4];
-  real h = 1.0 + p.gamma / (p.gamma - 1.0) * P / rho;  // h = 1 + eps + P/rho, eps = P/((G-1) rho)
+  real h = eos_h(p, rho, P);  // h = 1 + eps + P/rho
   real rhohW2 = rho * h * W * W;
   real D = rho * W;
   out[0] = sdet * D;
@@ -235,9 +317,10 @@ struct KRP {
   real q, r2, b2, rb, rb2, rperp2;
   real D;
   real gam, eps_min, vmax2;
+  const or_params* hyb;   // the hybrid EOS (eps_min and P then depend on rho); null: ideal gas
 };
 struct KRPEval {
-  real x, rbar2, qbar, vhat2, What, rhohat, eps_raw, eps, Phat, f;
+  real x, rbar2, qbar, vhat2, What, rhohat, eps_raw, eps, eps_min, Phat, f;
   bool vcap;
 };
 // master function f(mu) = mu - muhat(mu)
@@ -251,8 +334,9 @@ static void krp_eval(const KRP& s, real mu, KRPEval& e) {
   e.What = 1.0 / sqrt_(1.0 - e.vhat2);
   e.rhohat = s.D / e.What;
   e.eps_raw = e.What * (e.qbar - mu * e.rbar2) + e.vhat2 * e.What * e.What / (1.0 + e.What);
-  e.eps = e.eps_raw < s.eps_min ? s.eps_min : e.eps_raw;
-  e.Phat = (s.gam - 1.0) * e.rhohat * e.eps;
+  e.eps_min = s.hyb ? eos_epsmin(*s.hyb, e.rhohat) : s.eps_min;
+  e.eps = e.eps_raw < e.eps_min ? e.eps_min : e.eps_raw;
+  e.Phat = s.hyb ? eos_press(*s.hyb, e.rhohat, e.eps) : (s.gam - 1.0) * e.rhohat * e.eps;
   real ahat = e.Phat / (e.rhohat * (1.0 + e.eps));
   real nuA = (1.0 + ahat) * (1.0 + e.eps) / e.What;
   real nuB = (1.0 + ahat) * (1.0 + e.qbar - mu * e.rbar2);
@@ -339,9 +423,13 @@ static void c2p_cell(const or_params& p, real cons[5], const real Bd[3], const r
   bool finite = finite_(D) && finite_(tau) && finite_(Sl[0]) && finite_(Sl[1]) && finite_(Sl[2]) &&
                 finite_(B2) && det > 0.0;
   const real rho_atm = p.rho_atm, T_atm = p.T_atm;
-  const real eps_atm = T_atm / (gam - 1.0);
+  // eps of the temperature floor without the cold part (the tau floor), and
+  // the atmosphere's eps and pressure (with the cold part of the hybrid EOS)
+  const real eps_atm = T_atm / (eos_gth(p) - 1.0);
+  const real eps_atm_rho = p.eos ? eos_epsmin(p, rho_atm) : eps_atm;
+  const real P_atm = p.eos ? eos_pfloor(p, rho_atm) : rho_atm * T_atm;
   bool floored = false;
-  real rho = rho_atm, P = rho_atm * T_atm, w[3] = {0.0, 0.0, 0.0};
+  real rho = rho_atm, P = P_atm, w[3] = {0.0, 0.0, 0.0};
   if (!finite) {
     o.flags |= F_FAIL;
   } else {
@@ -352,7 +440,7 @@ static void c2p_cell(const or_params& p, real cons[5], const real Bd[3], const r
     if (excise || D < p.f_thr * rho_atm) {
       D = rho_atm;
       Sl[0] = Sl[1] = Sl[2] = 0.0;
-      tau = D * eps_atm + 0.5 * B2;
+      tau = D * eps_atm_rho + 0.5 * B2;
       o.flags |= F_DFLOOR;
     }
     if (p.sigma_max > 0.0 && B2 > p.sigma_max * D) {
@@ -368,6 +456,7 @@ static void c2p_cell(const or_params& p, real cons[5], const real Bd[3], const r
     s.D = D;
     s.gam = gam;
     s.eps_min = eps_atm;
+    s.hyb = p.eos ? &p : nullptr;
     s.vmax2 = 1.0 - 1.0 / (p.W_max * p.W_max);
     s.q = tau / D;
     real rl[3] = {Sl[0] / D, Sl[1] / D, Sl[2] / D};
@@ -400,8 +489,8 @@ static void c2p_cell(const or_params& p, real cons[5], const real Bd[3], const r
       KRPEval e;
       krp_eval(s, mu, e);
       o.mu = mu;
-      o.eps_margin = e.eps_raw / s.eps_min - 1.0;
-      if (e.eps_raw < s.eps_min) o.flags |= F_TEMP;
+      o.eps_margin = e.eps_raw / e.eps_min - 1.0;
+      if (e.eps_raw < e.eps_min) o.flags |= F_TEMP;
       if (e.vcap) o.flags |= F_VMAX;
       rho = e.rhohat;
       P = e.Phat;
@@ -413,19 +502,22 @@ static void c2p_cell(const or_params& p, real cons[5], const real Bd[3], const r
       // floors on the primitives after the solve (Sec. 3.3)
       if (rho < p.f_thr * rho_atm) {
         rho = rho_atm;
-        P = rho_atm * T_atm;
+        P = P_atm;
         w[0] = w[1] = w[2] = 0.0;
         o.flags |= F_RHO;
-      } else if (P < rho * T_atm) {
-        P = rho * T_atm;
-        o.flags |= F_TEMP;
+      } else {
+        const real Pf = p.eos ? eos_pfloor(p, rho) : rho * T_atm;
+        if (P < Pf) {
+          P = Pf;
+          o.flags |= F_TEMP;
+        }
       }
     }
   }
   if (o.flags & F_FAIL) {
     // error policy: reset the cell to the static atmosphere
     rho = rho_atm;
-    P = rho_atm * T_atm;
+    P = P_atm;
     w[0] = w[1] = w[2] = 0.0;
   }
   floored = (o.flags & (FLOOR_BITS | F_FAIL)) != 0;
@@ -586,9 +678,10 @@ static void face_floor(const or_params& p, real s[5]) {
   if (s[0] < p.f_thr * p.rho_atm) {
     s[0] = p.rho_atm;
     s[1] = s[2] = s[3] = 0.0;
-    s[4] = p.rho_atm * p.T_atm;
-  } else if (s[4] < s[0] * p.T_atm) {
-    s[4] = s[0] * p.T_atm;
+    s[4] = p.eos ? eos_pfloor(p, p.rho_atm) : real(p.rho_atm * p.T_atm);
+  } else {
+    const real Pf = p.eos ? eos_pfloor(p, s[0]) : s[0] * p.T_atm;
+    if (s[4] < Pf) s[4] = Pf;
   }
 }
 
@@ -627,8 +720,7 @@ static void face_side(const or_params& p, int d, const real st[7], real Bn, cons
   real Bv = dot3(B, vl);
   real v2 = dot3(v, vl);
   real b2 = B2 / (W * W) + Bv * Bv;
-  real gam = p.gamma;
-  real h = 1.0 + gam / (gam - 1.0) * P / rho;
+  real h = eos_h(p, rho, P);
   real rhohW2 = rho * h * W * W;
   real D = rho * W;
   real S[3];
@@ -654,7 +746,7 @@ static void face_side(const or_params& p, int d, const real st[7], real Bn, cons
   o.F[5] = alpha * (Bt[t1] * vh[d] - Bt[d] * vh[t1]);
   o.F[6] = alpha * (Bt[t2] * vh[d] - Bt[d] * vh[t2]);
   // fast magnetosonic speed and the characteristic speeds along d
-  real cs2 = gam * P / (rho * h);
+  real cs2 = eos_chi(p, rho, P) / (rho * h);
   real va2 = b2 / (rho * h + b2);
   real cf2 = cs2 + va2 - cs2 * va2;
   real cf = sqrt_(cf2);
@@ -1063,8 +1155,7 @@ static void sources(const Ctx& C, int k, int j, int i, real Gs[5]) {
   metric_apply(g, B, Bl);
   real B2 = dot3(B, Bl), Bv = dot3(B, vl);
   real b2 = B2 / (W * W) + Bv * Bv;
-  real gam = C.p.gamma;
-  real h = 1.0 + gam / (gam - 1.0) * P / rho;
+  real h = eos_h(C.p, rho, P);
   real Ptot = P + 0.5 * b2;
   // bbar^i = gamma^ij b_j = B^i/W + W (B.v) v^i
   real bb[3];
@@ -1203,6 +1294,22 @@ void or_c2p_cells(const or_params* p, long n, double* cons, const double* Bd, co
   }
 }
 
+// The EOS at (rho, P): out6 = {P_c, eps_c, G_i, eps, h, rho h c_s^2}; and
+// P(rho, eps).  Test hooks for the EOS pins.
+void or_eos(const or_params* p, double rho, double P, double* out6) {
+  real Pc, epsc, Gi;
+  eos_cold(*p, rho, Pc, epsc, Gi);
+  out6[0] = val(Pc);
+  out6[1] = val(epsc);
+  out6[2] = val(Gi);
+  out6[3] = val(p->eos ? eos_eps(*p, rho, P) : real(P) / ((p->gamma - 1.0) * real(rho)));
+  out6[4] = val(eos_h(*p, rho, P));
+  out6[5] = val(eos_chi(*p, rho, P));
+}
+double or_eos_press(const or_params* p, double rho, double eps) {
+  return val(p->eos ? eos_press(*p, rho, eps) : (real(p->gamma) - 1.0) * real(rho) * real(eps));
+}
+
 // The KRP master function f(mu) of one cell (undensitised floors NOT applied):
 // used by the brute-force bracket tests.  Returns f; out3 = {mu_plus, f(0), f(mu_plus)}.
 double or_c2p_master(const or_params* p, const double* cons5, const double* Bd3, const double* g6, double mu,
@@ -1219,7 +1326,8 @@ double or_c2p_master(const or_params* p, const double* cons5, const double* Bd3,
   KRP s;
   s.D = D;
   s.gam = p->gamma;
-  s.eps_min = p->T_atm / (p->gamma - 1.0);
+  s.eps_min = p->T_atm / (eos_gth(*p) - 1.0);
+  s.hyb = p->eos ? p : nullptr;
   s.vmax2 = 1.0 - 1.0 / (p->W_max * p->W_max);
   s.q = tau / D;
   real rl[3] = {Sl[0] / D, Sl[1] / D, Sl[2] / D}, ru[3];

@@ -770,3 +770,122 @@ def test_emf_edge_ignores_downstream_cell():
         e8c[7] += 1.0                       # E_cc(A-1, B-1)
         assert O.emf_edge(e8, neg) == O.emf_edge(e8c, neg)
         assert O.emf_edge(e8, pos) != O.emf_edge(e8c, pos)
+
+
+# ------------------------------------------------- Sec. 3.4: hybrid EOS
+# The hybrid EOS (cold piecewise polytrope + thermal ideal gas) that Sec. 3.4
+# names for PrimitiveSolver; the pins use its defining properties, not its
+# formulas: pressure and energy continuity at the dividing densities, the first
+# law for the cold curve, the adiabatic sound speed, the one-piece reduction to
+# the ideal gas, and the con2prim round trip.
+
+HYB = dict(eos=1, eos_pieces=3, eos_K0=1e-4, eos_gamma_th=1.8, eos_rho=(1e-8, 1e-4, 0.0),
+           eos_gamma=(1.7, 2.4, 2.1, 0.0))
+
+
+def test_hybrid_cold_curve_is_continuous():
+    """P_c and eps_c are continuous across each dividing density; G_i switches."""
+    p = O.params(gamma=2.0, **HYB)
+    for rb, (g0, g1) in zip((1e-8, 1e-4), ((1.7, 2.4), (2.4, 2.1))):
+        lo = O.eos(p, rb * (1 - 1e-13), 1.0)
+        hi = O.eos(p, rb * (1 + 1e-13), 1.0)
+        assert (lo["Gi"], hi["Gi"]) == (g0, g1)
+        assert abs(lo["Pc"] - hi["Pc"]) <= 1e-11 * hi["Pc"]
+        assert abs(lo["epsc"] - hi["epsc"]) <= 1e-11 * abs(hi["epsc"]) + 1e-20
+    # within a piece the cold pressure is a power law of the piece's index
+    for rho in (1e-10, 1e-6, 1e-2):
+        a, b = O.eos(p, rho, 1.0), O.eos(p, rho * 1.5, 1.0)
+        assert abs(np.log(b["Pc"] / a["Pc"]) / np.log(1.5) - a["Gi"]) < 1e-12
+
+
+def test_hybrid_cold_first_law():
+    """d eps_c / d rho = P_c / rho^2 (zero-temperature first law), by central
+    differences inside each piece."""
+    p = O.params(gamma=2.0, **HYB)
+    for rho in (3e-11, 2e-9, 5e-7, 3e-5, 2e-3, 5e-2):
+        h = rho * 1e-5
+        d = (O.eos(p, rho + h, 1.0)["epsc"] - O.eos(p, rho - h, 1.0)["epsc"]) / (2 * h)
+        assert abs(d / (O.eos(p, rho, 1.0)["Pc"] / rho ** 2) - 1.0) < 1e-7, rho
+
+
+def test_hybrid_adiabatic_sound_speed():
+    """rho h c_s^2 = rho (dP/drho) along an adiabat d eps = (P/rho^2) d rho,
+    from the oracle's P(rho, eps) by central differences."""
+    p = O.params(gamma=2.0, **HYB)
+    for rho in (3e-11, 2e-9, 5e-7, 3e-5, 2e-3):
+        for T in (1e-6, 1e-3, 0.3):
+            P = O.eos(p, rho, 1.0)["Pc"] + rho * T
+            e = O.eos(p, rho, P)
+            h = rho * 1e-5
+            dP = (O.eos_press(p, rho + h, e["eps"] + P / rho ** 2 * h) -
+                  O.eos_press(p, rho - h, e["eps"] - P / rho ** 2 * h)) / (2 * h)
+            assert abs(rho * dP / e["chi"] - 1.0) < 1e-6, (rho, T)
+            assert abs(e["h"] - (1.0 + e["eps"] + P / rho)) <= 1e-15 * e["h"]
+
+
+def test_hybrid_one_piece_reduces_to_ideal_gas():
+    """One piece with G_0 = G_th = Gamma is the ideal gas P = (Gamma-1) rho eps:
+    the same eps, h, c_s, prim -> cons, fluxes and con2prim (cold part ~0)."""
+    pi = O.params(gamma=2.0, rho_atm=1e-20, T_atm=1e-14, f_thr=0.0)
+    ph = O.params(gamma=2.0, rho_atm=1e-20, T_atm=1e-14, f_thr=0.0, eos=1, eos_pieces=1, eos_K0=1e-8,
+                  eos_gamma_th=2.0, eos_gamma=(2.0, 0.0, 0.0, 0.0))
+    for rho, P in ((1e-6, 1e-9), (1e-3, 1e-4), (0.5, 3.0)):
+        a, b = O.eos(pi, rho, P), O.eos(ph, rho, P)
+        for k in ("eps", "h", "chi"):
+            assert abs(a[k] - b[k]) <= 1e-13 * abs(a[k]), (k, a[k], b[k])
+        eps = a["eps"]
+        assert abs(O.eos_press(ph, rho, eps) - P) <= 1e-13 * P
+    prim, Bd, g = synth.c2p_stress(4000, seed=11)
+    ci, ch = O.prim2cons(pi, prim, Bd, g), O.prim2cons(ph, prim, Bd, g)
+    assert rel_err(ch, ci, 0.0) < 1e-13
+    ri, rh = O.c2p_cells(pi, ci, Bd, g), O.c2p_cells(ph, ci, Bd, g)
+    assert np.array_equal(ri["flags"], rh["flags"])
+    assert rel_err(rh["prim"][0], ri["prim"][0], 0.0) < 1e-11
+    assert np.all(np.abs(rh["prim"][4] - ri["prim"][4]) <= _P_tol(pi, ci, g, ri["prim"][4]))
+    rng = np.random.default_rng(12)
+    for _ in range(20):
+        al, be, g6 = rand_metric(rng)
+        m10 = np.concatenate([[al], be, g6])
+        L = np.array([*rand_state(rng)[:1], 0.1, -0.2, 0.05, 1e-3, 1e-3, -2e-3])
+        R = L * np.array([1.3, 0.5, 1.1, -1.0, 1.2, 0.8, 1.1])
+        L[4], R[4] = 0.3 * L[0], 0.5 * R[0]
+        Fi, Fh = O.face_flux(pi, 0, L, R, 2e-3, m10), O.face_flux(ph, 0, L, R, 2e-3, m10)
+        assert np.all(np.abs(Fi - Fh) <= 1e-12 * (np.abs(Fi).max() + 1e-300))
+
+
+def _hybrid_stress(n, seed, p):
+    """Stress cells with P = P_c(rho) + rho T (T above the floor)."""
+    prim, Bd, g = synth.c2p_stress(n, seed=seed)
+    T = prim[4] / prim[0]
+    prim[4] = np.array([O.eos(p, r, 1.0)["Pc"] for r in prim[0]]) + prim[0] * np.maximum(T, 10 * p.T_atm)
+    return prim, Bd, g
+
+
+def test_hybrid_c2p_round_trip():
+    """prim -> cons -> prim with the three-piece hybrid EOS over the stress
+    distribution, no floors."""
+    p = O.params(gamma=2.0, rho_atm=1e-20, T_atm=1e-14, f_thr=0.0, **HYB)
+    prim, Bd, g = _hybrid_stress(6000, 13, p)
+    cons = O.prim2cons(p, prim, Bd, g)
+    r = O.c2p_cells(p, cons, Bd, g)
+    assert np.all(r["flags"] == 0)
+    assert rel_err(r["prim"][0], prim[0], 0.0) < 1e-10
+    W = np.sqrt(1 + (prim[1:4] ** 2).sum(0))
+    assert np.max(np.abs(r["prim"][1:4] - prim[1:4]) / W) < 1e-10
+    assert np.all(np.abs(r["prim"][4] - prim[4]) <= _P_tol(p, cons, g, prim[4]))
+
+
+def test_hybrid_cold_matter_takes_the_temperature_floor():
+    """Matter on the cold curve (T = 0 < T_atm) is floored to P_c + rho T_atm
+    with F_TEMP; rho and w are kept."""
+    p = O.params(gamma=2.0, rho_atm=1e-20, T_atm=1e-10, f_thr=0.0, **HYB)
+    g = np.array([[1.0], [0], [0], [1.0], [0], [1.0]])
+    Bd = np.array([[0.0], [1e-6], [0.0]])
+    for rho in (1e-9, 1e-5, 1e-2):
+        Pc = O.eos(p, rho, 1.0)["Pc"]
+        prim = np.array([[rho], [0.2], [0.0], [0.0], [Pc]])
+        r = O.c2p_cells(p, O.prim2cons(p, prim, Bd, g), Bd, g)
+        assert r["flags"][0] & O.F_TEMP
+        rr = r["prim"][0, 0]
+        assert abs(r["prim"][4, 0] - (O.eos(p, rr, 1.0)["Pc"] + rr * p.T_atm)) <= 1e-13 * r["prim"][4, 0]
+        assert abs(r["prim"][0, 0] / rho - 1.0) < 1e-8 and abs(r["prim"][1, 0] - 0.2) < 1e-8
