@@ -78,6 +78,22 @@ typedef struct {
                          the plain bracket); the FOFC estimate starts from the
                          same root.  A new block list starts without roots.
                        The FP64 solve decides the root in every mode. */
+  int eos;          /* 0: ideal gas, P = (gamma-1) rho eps, T = P/rho.
+                       1: hybrid piecewise polytrope (Sec. 3.4 names it as
+                       PrimitiveSolver's second analytic EOS): a cold part
+                       P_c = K_i rho^eos_gamma[i] on eos_pieces (1..4) pieces
+                       split at the increasing densities eos_rho[0..pieces-2],
+                       with K_0 = eos_K0, the other K_i from the continuity of
+                       P_c and eps_c = a_i + K_i rho^(G_i-1)/(G_i-1) continuous
+                       (a_0 = 0); plus a thermal ideal gas
+                       P_th = (eos_gamma_th - 1) rho (eps - eps_c).  T = P_th/rho
+                       (the floors: P >= P_c + rho T_atm).  gamma is unused;
+                       c2p_guess 1 and 2 need eos = 0 (MHD_EINVAL otherwise). */
+  int eos_pieces;   /* 1..4 (eos = 1) */
+  double eos_K0;    /* K of the lowest-density piece (> 0) */
+  double eos_gamma_th;  /* thermal index (> 1) */
+  double eos_rho[3];    /* dividing densities, increasing, > 0 */
+  double eos_gamma[4];  /* piece indices (> 1) */
 } mhd_params;
 
 /* One meshblock: views into caller-owned device arrays. */

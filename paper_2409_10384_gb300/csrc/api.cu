@@ -83,6 +83,85 @@ struct mhd_ctx {
   long long prof_n[MHD_NKERNEL] = {0};
 };
 
+namespace grmhd {
+// Parameters -> kernel constants; validates every field.  allow_guess: the
+// learned and FP32-search con2prims (1, 2) and the warm start (3) are
+// accepted (the allocation-free path takes 0 only).
+int fill_par(const mhd_params* p, Par& P, bool allow_guess) {
+  if (!p) return MHD_EINVAL;
+  if (!(p->gamma > 1.0) || !(p->rho_atm > 0.0) || !(p->T_atm > 0.0) || !(p->f_thr >= 0.0) || !(p->c2p_tol > 0.0) ||
+      !(p->W_max > 1.0) || p->recon < 0 || p->recon > 4 || p->rsolver < 0 || p->rsolver > 1 ||
+      (p->rk_order != 2 && p->rk_order != 3) || p->c2p_maxit < 1 || p->c2p_guess < 0 ||
+      p->c2p_guess > (allow_guess ? 3 : 0) || (p->dmp_M > 0.0 && p->dmp_M < 1.0) || p->eos < 0 || p->eos > 1)
+    return MHD_EINVAL;
+  std::memset(&P, 0, sizeof(P));
+  P.eos = p->eos;
+  if (p->eos == 1) {
+    // hybrid EOS: pieces, K_i and eps_c constants a_i by continuity at the
+    // dividing densities; the FP32 root searches assume the ideal gas
+    const int np = p->eos_pieces;
+    if (np < 1 || np > 4 || !(p->eos_K0 > 0.0) || !(p->eos_gamma_th > 1.0) || p->c2p_guess == 1 ||
+        p->c2p_guess == 2)
+      return MHD_EINVAL;
+    for (int i = 0; i < np; i++)
+      if (!(p->eos_gamma[i] > 1.0)) return MHD_EINVAL;
+    for (int i = 0; i + 1 < np; i++)
+      if (!(p->eos_rho[i] > 0.0) || (i > 0 && !(p->eos_rho[i] > p->eos_rho[i - 1]))) return MHD_EINVAL;
+    P.npc = np;
+    P.Kpc[0] = p->eos_K0;
+    P.apc[0] = 0.0;
+    for (int i = 0; i < 4; i++) P.Gpc[i] = p->eos_gamma[i < np ? i : np - 1];
+    for (int i = 0; i < 3; i++) P.rpc[i] = i + 1 < np ? p->eos_rho[i] : 0.0;
+    for (int i = 1; i < 4; i++) {
+      if (i >= np) {
+        P.Kpc[i] = P.Kpc[i - 1];
+        P.apc[i] = P.apc[i - 1];
+        continue;
+      }
+      const double rb = p->eos_rho[i - 1], G0 = P.Gpc[i - 1], G1 = P.Gpc[i];
+      P.Kpc[i] = P.Kpc[i - 1] * std::pow(rb, G0 - G1);
+      P.apc[i] = P.apc[i - 1] + P.Kpc[i - 1] * std::pow(rb, G0 - 1.0) / (G0 - 1.0) -
+                 P.Kpc[i] * std::pow(rb, G1 - 1.0) / (G1 - 1.0);
+    }
+    P.Gth = p->eos_gamma_th;
+  } else {
+    P.Gth = p->gamma;
+  }
+  P.gth1 = P.Gth - 1.0;
+  P.gam = p->gamma;
+  P.gm1 = p->gamma - 1.0;
+  P.gfac = p->gamma / (p->gamma - 1.0);
+  P.rho_atm = p->rho_atm;
+  P.T_atm = p->T_atm;
+  P.rho_thr = p->f_thr * p->rho_atm;
+  P.eps_atm = p->T_atm / P.gth1;
+  if (p->eos == 1) {
+    // the cold triple at rho_atm, as eos_cold computes it on the device
+    int i = 0;
+    for (int j = 0; j < 3; j++) i += (j < P.npc - 1 && p->rho_atm >= P.rpc[j]) ? 1 : 0;
+    const double x = P.Kpc[i] * std::pow(p->rho_atm, P.Gpc[i] - 1.0);
+    P.Pc_atm = x * p->rho_atm;
+    P.epsc_atm = P.apc[i] + x / (P.Gpc[i] - 1.0);
+    P.G_atm = P.Gpc[i];
+  }
+  P.eps_atm_rho = P.epsc_atm + P.eps_atm;
+  P.P_atm = P.Pc_atm + p->rho_atm * p->T_atm;
+  P.sigma_max = p->sigma_max;
+  P.dmp_M = p->dmp_M;
+  P.tol = p->c2p_tol;
+  P.vmax2 = 1.0 - 1.0 / (p->W_max * p->W_max);
+  P.alpha_exc = p->alpha_exc;
+  P.recon = p->recon;
+  P.rsolver = p->rsolver;
+  P.fofc = p->fofc ? 1 : 0;
+  P.rk_order = p->rk_order;
+  P.maxit = p->c2p_maxit;
+  P.guess = p->c2p_guess;
+  return MHD_OK;
+}
+
+}  // namespace grmhd
+
 namespace {
 
 int tkind_items(int k) {
@@ -97,33 +176,11 @@ int tkind_items(int k) {
 }
 
 int set_par(mhd_ctx* c, const mhd_params* p) {
-  if (!p) return MHD_EINVAL;
-  if (!(p->gamma > 1.0) || !(p->rho_atm > 0.0) || !(p->T_atm > 0.0) || !(p->f_thr >= 0.0) || !(p->c2p_tol > 0.0) ||
-      !(p->W_max > 1.0) || p->recon < 0 || p->recon > 4 || p->rsolver < 0 || p->rsolver > 1 ||
-      (p->rk_order != 2 && p->rk_order != 3) || p->c2p_maxit < 1 || p->c2p_guess < 0 || p->c2p_guess > 3 ||
-      (p->dmp_M > 0.0 && p->dmp_M < 1.0))
-    return MHD_EINVAL;
+  Par P;
+  const int r = fill_par(p, P, true);
+  if (r) return r;
   c->hp = *p;
-  Par& P = c->P;
-  P.gam = p->gamma;
-  P.gm1 = p->gamma - 1.0;
-  P.gfac = p->gamma / (p->gamma - 1.0);
-  P.rho_atm = p->rho_atm;
-  P.T_atm = p->T_atm;
-  P.rho_thr = p->f_thr * p->rho_atm;
-  P.eps_atm = p->T_atm / (p->gamma - 1.0);
-  P.P_atm = p->rho_atm * p->T_atm;
-  P.sigma_max = p->sigma_max;
-  P.dmp_M = p->dmp_M;
-  P.tol = p->c2p_tol;
-  P.vmax2 = 1.0 - 1.0 / (p->W_max * p->W_max);
-  P.alpha_exc = p->alpha_exc;
-  P.recon = p->recon;
-  P.rsolver = p->rsolver;
-  P.fofc = p->fofc ? 1 : 0;
-  P.rk_order = p->rk_order;
-  P.maxit = p->c2p_maxit;
-  P.guess = p->c2p_guess;
+  c->P = P;
   c->par_version++;
   return MHD_OK;
 }

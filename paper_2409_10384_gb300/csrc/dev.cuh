@@ -19,11 +19,19 @@ constexpr unsigned FLOOR_BITS = F_DFLOOR | F_SIGMA | F_TAU | F_RHO | F_TEMP | F_
 
 // Parameters with derived constants, passed by value to every kernel.
 struct Par {
-  double gam, gm1, gfac;        // Gamma, Gamma-1, Gamma/(Gamma-1)
-  double rho_atm, T_atm, rho_thr, eps_atm, P_atm;
+  double gam, gm1, gfac;        // Gamma, Gamma-1, Gamma/(Gamma-1) (ideal gas)
+  double rho_atm, T_atm, rho_thr;
+  double eps_atm;               // T_atm/(G_th - 1): eps of the T floor without the cold part
+  double eps_atm_rho;           // the atmosphere's eps (hybrid: eps_c(rho_atm) + eps_atm)
+  double P_atm;                 // the atmosphere's pressure (hybrid: P_c(rho_atm) + rho_atm T_atm)
   double sigma_max, dmp_M, tol, vmax2;
   double alpha_exc;             // excision lapse (<= 0: off)
-  int recon, rsolver, fofc, rk_order, maxit, guess;
+  // hybrid EOS (eos = 1): pieces npc, dividing densities, K_i, G_i, eps_c
+  // constants a_i, thermal index, and the cold triple at rho_atm
+  double rpc[3], Kpc[4], Gpc[4], apc[4];
+  double Gth, gth1;             // G_th and G_th - 1 (ideal gas: Gamma, Gamma - 1)
+  double Pc_atm, epsc_atm, G_atm;
+  int recon, rsolver, fofc, rk_order, maxit, guess, eos, npc;
 };
 
 // One meshblock as seen by the kernels: caller arrays plus context scratch.
@@ -181,6 +189,45 @@ __device__ __forceinline__ double dot3(const double* a, const double* b) {
   return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
+// ------------------------------------------------------- EOS (Sec. 3.4)
+// Hybrid EOS: cold part at rho, P_c = K_i rho^G_i and eps_c = a_i +
+// K_i rho^(G_i-1)/(G_i-1) on the piece that holds rho (one pow).  The piece
+// constants come from the parameters (host side, by continuity).
+__device__ __forceinline__ void eos_cold(const Par& P, double rho, double& Pc, double& epsc, double& Gi) {
+  int i = 0;
+#pragma unroll
+  for (int j = 0; j < 3; j++) i += (j < P.npc - 1 && rho >= P.rpc[j]) ? 1 : 0;
+  const double K = i == 0 ? P.Kpc[0] : (i == 1 ? P.Kpc[1] : (i == 2 ? P.Kpc[2] : P.Kpc[3]));
+  const double a = i == 0 ? P.apc[0] : (i == 1 ? P.apc[1] : (i == 2 ? P.apc[2] : P.apc[3]));
+  Gi = i == 0 ? P.Gpc[0] : (i == 1 ? P.Gpc[1] : (i == 2 ? P.Gpc[2] : P.Gpc[3]));
+  const double x = K * pow(rho, Gi - 1.0);   // K rho^(G_i - 1)
+  Pc = x * rho;
+  epsc = a + x / (Gi - 1.0);
+}
+// rho h = rho + rho eps + P and rho h c_s^2 = G_i P_c + G_th P_th of the hybrid
+// EOS from rho, P and the cold triple at rho
+__device__ __forceinline__ void eos_hyb_rhoh_chi(const Par& P, double rho, double p, double Pc, double epsc, double Gi,
+                                                 double& rhoh, double& chi) {
+  const double Pth = p - Pc;
+  rhoh = rho + fma(rho, epsc, Pth / P.gth1) + p;
+  chi = fma(Gi, Pc, P.Gth * Pth);
+}
+// rho h at (rho, P), either EOS
+__device__ __forceinline__ double eos_rhoh(const Par& P, double rho, double p) {
+  if (P.eos == 0) return fma(P.gfac, p, rho);
+  double Pc, epsc, Gi, rhoh, chi;
+  eos_cold(P, rho, Pc, epsc, Gi);
+  eos_hyb_rhoh_chi(P, rho, p, Pc, epsc, Gi, rhoh, chi);
+  return rhoh;
+}
+// pressure of the temperature floor at rho: P_c(rho) + rho T_atm
+__device__ __forceinline__ double eos_pfloor(const Par& P, double rho) {
+  if (P.eos == 0) return rho * P.T_atm;
+  double Pc, epsc, Gi;
+  eos_cold(P, rho, Pc, epsc, Gi);
+  return fma(rho, P.T_atm, Pc);
+}
+
 // ----------------------------------------------------- prim -> cons (Eq. 6)
 // prim = rho, w^i = W v^i, P;  Bd = densitised B~;  out = D~, S~_i, tau~.
 __device__ __forceinline__ void prim2cons(const Par& P, const double* prim, const double* Bd, const Metric& m,
@@ -197,7 +244,7 @@ __device__ __forceinline__ void prim2cons(const Par& P, const double* prim, cons
   double B2 = dot3(B, Bl);
   double Bv = dot3(B, vl);
   double rho = prim[0], p = prim[4];
-  double rhoh = rho + P.gfac * p;
+  double rhoh = P.eos == 0 ? rho + P.gfac * p : eos_rhoh(P, rho, p);
   double e = rhoh * W2;
   double D = rho * W;
   double eB = e + B2;
@@ -213,9 +260,11 @@ __device__ __forceinline__ void prim2cons(const Par& P, const double* prim, cons
 struct KS {
   double qh;      // q - b^2/2
   double r2, b2, rb2, rperp2, gam, eps_min, vmax2;
+  double D;       // undensitised D (the hybrid EOS needs rho = D/W)
 };
 struct KEval {
   double x, rbar2, W, eps, eps_raw, G;
+  double eps_min, rho, P, Pc;   // hybrid EOS: eps floor at rho, rho = D/W, P, cold P_c
   bool vcap;
 };
 // The KRP master function f(mu) = mu - 1/(nu + mu rbar^2) with
@@ -297,8 +346,50 @@ __device__ __forceinline__ double kev_g(const KS& s, double mu) {
   const double Z = fma(P1, fma(mu * rbar2, W, 1.0), s.gam * Te);
   return mu - (W * P1) / Z;
 }
-// f(0) = -1/(1 + Gamma eps(0)): at mu = 0, v = 0, W = 1 and eps = qbar = q_h.
-__device__ __forceinline__ double f_zero(const KS& s) {
+// The master function with the hybrid EOS, in the general form of Kastaun
+// et al. (2021): rho = D/W, eps clamped below at eps_c(rho) + T_atm/(G_th-1),
+// P = P(rho, eps), a = P/(rho (1 + eps)), nu = max(nu_A, nu_B) with
+// nu_A = (1 + a)(1 + eps)/W and nu_B = (1 + a)(1 + qbar - mu rbar^2), and
+// f = mu - 1/(nu + mu rbar^2).  (With the ideal gas nu_A >= nu_B, which kev
+// uses; here nu_B can win where eps is clamped.)
+__device__ __forceinline__ void kev_hyb(const KS& s, const Par& P, double mu, KEval& e) {
+  const double x = 1.0 / fma(mu, s.b2, 1.0);
+  const double mux = mu * x;
+  const double rbar2 = x * fma(s.r2, x, mu * (1.0 + x) * s.rb2);
+  const double qbar = fma(-0.5 * mux * mux, s.rperp2, s.qh);
+  const double v2 = mu * mu * rbar2;
+  e.vcap = v2 > s.vmax2;
+  const double vh2 = e.vcap ? s.vmax2 : v2;
+  const double W = rsqrt(1.0 - vh2);
+  const double rho = s.D / W;
+  double Pc, epsc, Gi;
+  eos_cold(P, rho, Pc, epsc, Gi);
+  const double A = qbar - mu * rbar2;
+  e.eps_min = epsc + P.eps_atm;
+  e.eps_raw = fma(W, A, vh2 * W * W / (1.0 + W));
+  e.eps = e.eps_raw < e.eps_min ? e.eps_min : e.eps_raw;
+  const double Ph = fma(P.gth1 * rho, e.eps - epsc, Pc);
+  const double a1 = 1.0 + Ph / (rho * (1.0 + e.eps));
+  const double nu = fmax(a1 * (1.0 + e.eps) / W, a1 * (1.0 + A));
+  e.x = x;
+  e.rbar2 = rbar2;
+  e.W = W;
+  e.rho = rho;
+  e.P = Ph;
+  e.Pc = Pc;
+  e.G = mu - 1.0 / fma(mu, rbar2, nu);
+}
+// f(mu) for either EOS
+__device__ __forceinline__ double kev_G(const KS& s, const Par& P, double mu) {
+  if (P.eos == 0) return kev_g(s, mu);
+  KEval e;
+  kev_hyb(s, P, mu, e);
+  return e.G;
+}
+// f(0): at mu = 0, v = 0, W = 1 and eps = qbar = q_h; the ideal gas gives
+// -1/(1 + Gamma eps(0)).
+__device__ __forceinline__ double f_zero(const KS& s, const Par& P) {
+  if (P.eos != 0) return kev_G(s, P, 0.0);
   double e0 = s.qh < s.eps_min ? s.eps_min : s.qh;
   return -1.0 / fma(s.gam, e0, 1.0);
 }
@@ -342,8 +433,8 @@ __device__ __forceinline__ void krp_features(const KS& s, float* f) {
 // bracket closes one step after the iterate converges; stops when b - a <=
 // tol b, then one regula-falsi step with the true end values.  Returns false
 // when the iteration cap is reached.
-__device__ __forceinline__ bool illinois(const KS& s, double a, double Ga, double b, double Gb, double tol, int maxit,
-                                         double& root, int& iters) {
+__device__ __forceinline__ bool illinois(const KS& s, const Par& P, double a, double Ga, double b, double Gb,
+                                         double tol, int maxit, double& root, int& iters) {
   iters = 0;
   if (Gb == 0.0) { root = b; return true; }
   double Fa = Ga, Fb = Gb;
@@ -357,7 +448,7 @@ __device__ __forceinline__ bool illinois(const KS& s, double a, double Ga, doubl
     const double eta = 0.25 * tol * b;
     c += side == -1 ? eta : (side == 1 ? -eta : 0.0);
     if (!(c > a && c < b)) c = 0.5 * (a + b);
-    const double G = kev_g(s, c);
+    const double G = kev_G(s, P, c);
     if (G < 0.0) {
       a = c; Ga = G; Fa = G;
       if (side == -1) Fb *= 0.5;
@@ -404,7 +495,7 @@ __device__ __forceinline__ bool krp_prep(const Par& P, const double* U, const do
   if (D < P.rho_thr || (P.alpha_exc > 0.0 && alpha < P.alpha_exc)) {
     D = P.rho_atm;
     Sl[0] = Sl[1] = Sl[2] = 0.0;
-    tau = fma(D, P.eps_atm, 0.5 * B2);
+    tau = fma(D, P.eps_atm_rho, 0.5 * B2);
     flags |= F_DFLOOR;
   }
   if (P.sigma_max > 0.0 && B2 > P.sigma_max * D) {
@@ -432,6 +523,7 @@ __device__ __forceinline__ bool krp_prep(const Par& P, const double* U, const do
   s.gam = P.gam;
   s.eps_min = P.eps_atm;
   s.vmax2 = P.vmax2;
+  s.D = D;
   k.D = D;
   return true;
 }
@@ -440,13 +532,13 @@ __device__ __forceinline__ bool krp_prep(const Par& P, const double* U, const do
 // f_zero.  `iters` counts the evaluations of f it made.  A learned guess [glo, ghi] is used when given and verified by the
 // signs at both ends; otherwise [0, mu+] (or [mu+, 1] when G(mu+) < 0).
 // Returns 0: solve needed; 1: root found (in mu); 2: no bracket (failure).
-__device__ __forceinline__ int krp_bracket(const KS& s, double glo, double ghi, double& a, double& b, double& Ga,
-                                           double& Gb, double& mu, int& iters) {
-  a = 0.0; Ga = f_zero(s); b = 1.0; Gb = 0.0;
+__device__ __forceinline__ int krp_bracket(const KS& s, const Par& P, double glo, double ghi, double& a, double& b,
+                                           double& Ga, double& Gb, double& mu, int& iters) {
+  a = 0.0; Ga = f_zero(s, P); b = 1.0; Gb = 0.0;
   iters = 0;
   bool have = false;
   if (glo >= 0.0 && ghi > glo) {
-    const double Gl = kev_g(s, glo), Gh = kev_g(s, ghi);
+    const double Gl = kev_G(s, P, glo), Gh = kev_G(s, P, ghi);
     if (Gl < 0.0 && Gh >= 0.0) {
       a = glo; Ga = Gl; b = ghi; Gb = Gh; have = true;
     } else if (Gl >= 0.0) {
@@ -460,12 +552,12 @@ __device__ __forceinline__ int krp_bracket(const KS& s, double glo, double ghi, 
     double mp = mu_plus(s);
     if (mp <= a) mp = 1.0;
     iters++;
-    b = mp; Gb = kev_g(s, mp);
+    b = mp; Gb = kev_G(s, P, mp);
     if (Gb < 0.0) {
       a = mp; Ga = Gb;
       b = 1.0;
       iters++;
-      Gb = kev_g(s, b);
+      Gb = kev_G(s, P, b);
     }
   }
   if (!(Ga < 0.0 && Gb >= 0.0)) return 2;
@@ -483,12 +575,19 @@ __device__ __forceinline__ void krp_finish(const Par& P, const KrpCell& k, doubl
   } else {
     const KS& s = k.s;
     KEval e;
-    kev(s, mu, e);
-    if (e.eps_raw < s.eps_min) flags |= F_TEMP;
+    if (P.eos == 0) {
+      kev(s, mu, e);
+      if (e.eps_raw < s.eps_min) flags |= F_TEMP;
+      double iW = e.W * (1.0 - (e.vcap ? s.vmax2 : mu * mu * e.rbar2));
+      rho = k.D * iW;
+      p = P.gm1 * rho * e.eps;
+    } else {
+      kev_hyb(s, P, mu, e);
+      if (e.eps_raw < e.eps_min) flags |= F_TEMP;
+      rho = e.rho;
+      p = e.P;
+    }
     if (e.vcap) flags |= F_VMAX;
-    double iW = e.W * (1.0 - (e.vcap ? s.vmax2 : mu * mu * e.rbar2));
-    rho = k.D * iW;
-    p = P.gm1 * rho * e.eps;
     double vs = 1.0;
     if (e.vcap) vs = sqrt(s.vmax2 / (mu * mu * e.rbar2));
     double f = e.W * vs * mu * e.x;
@@ -499,9 +598,14 @@ __device__ __forceinline__ void krp_finish(const Par& P, const KrpCell& k, doubl
     if (rho < P.rho_thr) {
       rho = P.rho_atm; p = P.P_atm; w0 = w1 = w2 = 0.0;
       flags |= F_RHO;
-    } else if (p < rho * P.T_atm) {
-      p = rho * P.T_atm;
-      flags |= F_TEMP;
+    } else {
+      // T floor: P >= P_c(rho) + rho T_atm (the cold part at this rho is
+      // e.Pc for the hybrid EOS, 0 for the ideal gas)
+      const double pf = P.eos == 0 ? rho * P.T_atm : fma(rho, P.T_atm, e.Pc);
+      if (p < pf) {
+        p = pf;
+        flags |= F_TEMP;
+      }
     }
   }
   if (flags & F_FAIL) {
@@ -523,11 +627,11 @@ __device__ __forceinline__ void con2prim(const Par& P, double* U, const double* 
   double mu = 0.0;
   if (ok) {
     double a, b, Ga, Gb;
-    int st = krp_bracket(k.s, glo, ghi, a, b, Ga, Gb, mu, iters);
+    int st = krp_bracket(k.s, P, glo, ghi, a, b, Ga, Gb, mu, iters);
     if (st == 2) ok = false;
     else if (st == 0) {
       int it = 0;
-      ok = illinois(k.s, a, Ga, b, Gb, P.tol, P.maxit, mu, it);
+      ok = illinois(k.s, P, a, Ga, b, Gb, P.tol, P.maxit, mu, it);
       iters += it;
     }
   }
@@ -816,9 +920,17 @@ __device__ __forceinline__ void wz_finish(const double* x, const double* n_hi, c
   }
 }
 
-__device__ __forceinline__ void face_floor(const Par& P, double* s) {
+// E = 0 ideal gas; E = 1 hybrid EOS, which also returns the cold triple
+// (P_c, eps_c, G_i) at the floored density in cold[3] for face_side.
+template <int E = 0>
+__device__ __forceinline__ void face_floor(const Par& P, double* s, double* cold = nullptr) {
   if (s[0] < P.rho_thr) {
     s[0] = P.rho_atm; s[1] = s[2] = s[3] = 0.0; s[4] = P.P_atm;
+    if (E) { cold[0] = P.Pc_atm; cold[1] = P.epsc_atm; cold[2] = P.G_atm; }
+  } else if (E) {
+    eos_cold(P, s[0], cold[0], cold[1], cold[2]);
+    const double pf = fma(s[0], P.T_atm, cold[0]);
+    if (s[4] < pf) s[4] = pf;
   } else if (s[4] < s[0] * P.T_atm) {
     s[4] = s[0] * P.T_atm;
   }
@@ -844,8 +956,10 @@ struct Side {
 //   N = Gamma P + b^2,  Dn = rho h + b^2,  Q = rho h - Gamma P,
 //   X = gamma^{dd} (Dn - v^2 N) - (v^d)^2 Q,
 // which needs one square root and (shared with the other side) one division.
-template <int d>
-__device__ __forceinline__ void face_side(const Par& P, const double* st, double Bn, const FaceMetric& fm, Side& o) {
+// E = 1: the hybrid EOS, rho h and rho h c_s^2 from the cold triple in cold[3].
+template <int d, int E = 0>
+__device__ __forceinline__ void face_side(const Par& P, const double* st, double Bn, const FaceMetric& fm, Side& o,
+                                          const double* cold = nullptr) {
   constexpr int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
   const Metric& m = fm.m;
   double Bt[3];
@@ -864,7 +978,13 @@ __device__ __forceinline__ void face_side(const Par& P, const double* st, double
   const double B2 = dot3(B, Bl);
   const double b2 = fma(B2, iW2, Bv * Bv);
   const double rho = st[0], p = st[4];
-  const double rhoh = fma(P.gfac, p, rho);
+  double rhoh, gp;   // rho h and rho h c_s^2 (ideal gas: Gamma P)
+  if (E) {
+    eos_hyb_rhoh_chi(P, rho, p, cold[0], cold[1], cold[2], rhoh, gp);
+  } else {
+    rhoh = fma(P.gfac, p, rho);
+    gp = P.gam * p;
+  }
   const double eB = fma(rhoh, W2, B2);     // rho h W^2 + B^2
   const double D = rho * W;
   const double sd = m.sdet, alpha = fm.alpha;
@@ -893,7 +1013,6 @@ __device__ __forceinline__ void face_side(const Par& P, const double* st, double
   o.F[4] = fma(o.U[4], avd, fma(sdP, alpha * vd, -aBn * Bv));
   o.F[5] = fma(Bt[t1], avd, -Bn * avh[t1]);
   o.F[6] = fma(Bt[t2], avd, -Bn * avh[t2]);
-  const double gp = P.gam * p;
   const double N = gp + b2;
   const double Q = rhoh - gp;
   const double den = fma(iW2 - 1.0, N, rhoh + b2);   // Dn - v^2 N, v^2 = 1 - 1/W^2
@@ -948,14 +1067,15 @@ __device__ __forceinline__ void face_metric(const double* adm, long long nc, lon
 }
 
 // Flux through one face from its reconstructed (unfloored) states.
-template <int d>
+template <int d, int E = 0>
 __device__ __forceinline__ void face_flux_states(const Par& P, double* L, double* R, double Bn, const FaceMetric& fm,
                                                  double* F) {
-  face_floor(P, L);
-  face_floor(P, R);
+  double cl[3], cr[3];
+  face_floor<E>(P, L, cl);
+  face_floor<E>(P, R, cr);
   Side sl, sr;
-  face_side<d>(P, L, Bn, fm, sl);
-  face_side<d>(P, R, Bn, fm, sr);
+  face_side<d, E>(P, L, Bn, fm, sl, cl);
+  face_side<d, E>(P, R, Bn, fm, sr, cr);
   riemann<d>(P.rsolver, fm, sl, sr, F);
 }
 

@@ -3,8 +3,12 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include "dev.cuh"
+#include "grmhd.h"
 
 namespace grmhd {
+// mhd_params -> kernel constants, with validation (api.cu); allow_guess: accept
+// c2p_guess 1-3 (the allocation-free path takes 0 only)
+int fill_par(const mhd_params* p, Par& P, bool allow_guess);
 void launch_init_block(const DevBlock& b, const Par& P, const double* const A[3], cudaStream_t s, int nsm);
 void launch_p2c_cells(const Par& P, long long n, const double* prim, const double* Bd, const double* g, double* cons,
                       cudaStream_t s, int nsm);

@@ -33,7 +33,9 @@ __device__ __forceinline__ void face_flux_donor(const DevBlock& b, const Par& P,
   }
   FaceMetric fm;
   face_metric(b.adm, nc, c0 - st, st, fm);
-  face_flux_states<d>(P, L, R, b.bf[d][fidx(b, d, k, j, i)], fm, F);
+  const double Bn = b.bf[d][fidx(b, d, k, j, i)];
+  if (P.eos == 0) face_flux_states<d, 0>(P, L, R, Bn, fm, F);
+  else face_flux_states<d, 1>(P, L, R, Bn, fm, F);
 }
 
 // Segment `s` of the transverse line of item `loc`: (k,j,i) is the cell on the
@@ -59,7 +61,7 @@ __device__ __forceinline__ void seg_coords(const DevBlock& b, int loc, int& k, i
 
 // Fluxes of direction d, one thread per segment: the thread sweeps the cells
 // along d, reconstructing each once (order R) and finishing one face per cell.
-template <int d, int R>
+template <int d, int R, int E>
 __global__ void __launch_bounds__(256) k_flux(Work w, Par P) {
   constexpr int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
   const long long* pre = w.pre + (long long)(W_SX + d) * (w.nblocks + 1);
@@ -109,7 +111,7 @@ __global__ void __launch_bounds__(256) k_flux(Work w, Par P) {
       FaceMetric fm;
       face_metric(b.adm, nc, c - st, st, fm);
       double F[7];
-      face_flux_states<d>(P, Ls, Rs, b.bf[d][f], fm, F);
+      face_flux_states<d, E>(P, Ls, Rs, b.bf[d][f], fm, F);
       double* out = b.flux[d];
 #pragma unroll
       for (int v = 0; v < 7; v++) out[v * nfc + f] = F[v];
@@ -219,20 +221,26 @@ __global__ void __launch_bounds__(128) k_fofc_fix(Work w, Par P, unsigned long l
   warp_flush(&stats[6], s_faces);
 }
 
-template <int d>
+template <int d, int E>
 void launch_flux_r(const Work& w, const Par& P, cudaStream_t s, int grid, int threads) {
   switch (P.recon) {
-    case 4: k_flux<d, 4><<<grid, threads, 0, s>>>(w, P); break;
-    case 3: k_flux<d, 3><<<grid, threads, 0, s>>>(w, P); break;
-    case 2: k_flux<d, 2><<<grid, threads, 0, s>>>(w, P); break;
-    case 1: k_flux<d, 1><<<grid, threads, 0, s>>>(w, P); break;
-    default: k_flux<d, 0><<<grid, threads, 0, s>>>(w, P); break;
+    case 4: k_flux<d, 4, E><<<grid, threads, 0, s>>>(w, P); break;
+    case 3: k_flux<d, 3, E><<<grid, threads, 0, s>>>(w, P); break;
+    case 2: k_flux<d, 2, E><<<grid, threads, 0, s>>>(w, P); break;
+    case 1: k_flux<d, 1, E><<<grid, threads, 0, s>>>(w, P); break;
+    default: k_flux<d, 0, E><<<grid, threads, 0, s>>>(w, P); break;
   }
 }
 void launch_flux_dir(int d, const Work& w, const Par& P, cudaStream_t s, int grid, int threads) {
-  if (d == 0) launch_flux_r<0>(w, P, s, grid, threads);
-  else if (d == 1) launch_flux_r<1>(w, P, s, grid, threads);
-  else launch_flux_r<2>(w, P, s, grid, threads);
+  if (P.eos == 0) {
+    if (d == 0) launch_flux_r<0, 0>(w, P, s, grid, threads);
+    else if (d == 1) launch_flux_r<1, 0>(w, P, s, grid, threads);
+    else launch_flux_r<2, 0>(w, P, s, grid, threads);
+  } else {
+    if (d == 0) launch_flux_r<0, 1>(w, P, s, grid, threads);
+    else if (d == 1) launch_flux_r<1, 1>(w, P, s, grid, threads);
+    else launch_flux_r<2, 1>(w, P, s, grid, threads);
+  }
 }
 void launch_fofc_flag(const Work& w, const Par& P, double g0, double g1, double bdt, unsigned long long* stats,
                       cudaStream_t s, int grid) {
@@ -245,16 +253,16 @@ void launch_fofc_fix(int d, const Work& w, const Par& P, unsigned long long* sta
 }
 int occ_face_kernel(int kind, int threads) {
   int o = 0;
-  if (kind == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_flux<0, 2>, threads, 0);
-  else if (kind == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_flux<1, 2>, threads, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_flux<2, 2>, threads, 0);
+  if (kind == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_flux<0, 2, 0>, threads, 0);
+  else if (kind == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_flux<1, 2, 0>, threads, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_flux<2, 2, 0>, threads, 0);
   return o;
 }
 int occupancy_face(int* per_sm) {
   cudaError_t e = cudaSuccess;
-  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_flux<0, 2>, 128, 0));
-  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_flux<1, 2>, 128, 0));
-  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[2], k_flux<2, 2>, 128, 0));
+  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_flux<0, 2, 0>, 128, 0));
+  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_flux<1, 2, 0>, 128, 0));
+  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[2], k_flux<2, 2, 0>, 128, 0));
   e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[3], k_fofc_flag, 128, 0));
   e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[4], k_fofc_fix<0>, 128, 0));
   return e == cudaSuccess ? 0 : -1;

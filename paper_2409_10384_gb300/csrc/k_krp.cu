@@ -27,6 +27,7 @@ __device__ __forceinline__ void kw_load(const KrpBuf& kb, const Par& P, long lon
   k.s.rb2 = w[KW_RB2 * n + i]; k.s.rperp2 = w[KW_RP2 * n + i];
   k.s.gam = P.gam; k.s.eps_min = P.eps_atm; k.s.vmax2 = P.vmax2;
   k.D = w[KW_D * n + i]; k.rb = w[KW_RB * n + i];
+  k.s.D = k.D;
   k.ru[0] = w[KW_RU0 * n + i]; k.ru[1] = w[KW_RU1 * n + i]; k.ru[2] = w[KW_RU2 * n + i];
   k.bu[0] = w[KW_BU0 * n + i]; k.bu[1] = w[KW_BU1 * n + i]; k.bu[2] = w[KW_BU2 * n + i];
 }
@@ -53,7 +54,7 @@ __device__ __forceinline__ void prep_cell(const Par& P, const KrpBuf& kb, long l
       const bool warm = guess > 0.0 && guess <= 1.0;
       const double glo = warm ? guess * (1.0 - WARM_DELTA) : -1.0;
       const double ghi = warm ? fmin(guess * (1.0 + WARM_DELTA), 1.0) : -1.0;
-      int r = krp_bracket(k.s, glo, ghi, a, b, Ga, Gb, mu, its);
+      int r = krp_bracket(k.s, P, glo, ghi, a, b, Ga, Gb, mu, its);
       st = (unsigned char)(r == 0 ? 0 : (r == 1 ? 1 : 2));
       kb.w[KW_A * n + i] = a; kb.w[KW_B * n + i] = b;
       kb.w[KW_GA * n + i] = Ga; kb.w[KW_GB * n + i] = Gb;
@@ -88,6 +89,7 @@ __global__ void __launch_bounds__(256) k_krp_solve(Par P, KrpBuf kb, unsigned lo
   KS s;
   s.gam = P.gam; s.eps_min = P.eps_atm; s.vmax2 = P.vmax2;
   s.qh = s.r2 = s.b2 = s.rb2 = s.rperp2 = 0.0;
+  s.D = 1.0;
   double a = 0.0, b = 1.0, Ga = -1.0, Gb = 1.0, Fa = -1.0, Fb = 1.0;
   int side = 0, it = 0;
   unsigned s_it = 0, s_cap = 0;
@@ -108,6 +110,7 @@ __global__ void __launch_bounds__(256) k_krp_solve(Par P, KrpBuf kb, unsigned lo
           const double* w = kb.w;
           s.qh = w[KW_QH * n + my]; s.r2 = w[KW_R2 * n + my]; s.b2 = w[KW_B2 * n + my];
           s.rb2 = w[KW_RB2 * n + my]; s.rperp2 = w[KW_RP2 * n + my];
+          s.D = w[KW_D * n + my];
           a = w[KW_A * n + my]; b = w[KW_B * n + my];
           Ga = w[KW_GA * n + my]; Gb = w[KW_GB * n + my];
           Fa = Ga; Fb = Gb;
@@ -130,7 +133,7 @@ __global__ void __launch_bounds__(256) k_krp_solve(Par P, KrpBuf kb, unsigned lo
         const double eta = 0.25 * P.tol * b;
         c += side == -1 ? eta : (side == 1 ? -eta : 0.0);
         if (!(c > a && c < b)) c = 0.5 * (a + b);
-        const double G = kev_g(s, c);
+        const double G = kev_G(s, P, c);
         if (G < 0.0) {
           a = c; Ga = G; Fa = G;
           if (side == -1) Fb *= 0.5;

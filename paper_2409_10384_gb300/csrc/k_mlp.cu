@@ -367,6 +367,7 @@ __global__ void __launch_bounds__(128) k_krp_seed(Par P, KrpBuf kb, const float*
     s.qh = w[KW_QH * n + i]; s.r2 = w[KW_R2 * n + i]; s.b2 = w[KW_B2 * n + i];
     s.rb2 = w[KW_RB2 * n + i]; s.rperp2 = w[KW_RP2 * n + i];
     s.gam = P.gam; s.eps_min = P.eps_atm; s.vmax2 = P.vmax2;
+    s.D = w[KW_D * n + i];
     KSf sf;
     sf.qh = (float)s.qh; sf.r2 = (float)s.r2; sf.b2 = (float)s.b2; sf.rb2 = (float)s.rb2; sf.rp2 = (float)s.rperp2;
     sf.gam = (float)s.gam; sf.emin = fmaxf((float)s.eps_min, 1e-37f); sf.vmax2 = (float)s.vmax2;
@@ -396,7 +397,7 @@ __global__ void __launch_bounds__(128) k_krp_seed(Par P, KrpBuf kb, const float*
     if (!(m32 > 1e-300 && m32 <= 1.0)) m32 = 0.5;
     double G = kev_g(s, m32);
     int its = 1;
-    double a = 0.0, b = 1.0, Ga = f_zero(s), Gb = 0.0;
+    double a = 0.0, b = 1.0, Ga = f_zero(s, P), Gb = 0.0;
     unsigned char st = 0;
     if (G == 0.0) {
       st = 1;

@@ -99,7 +99,7 @@ __device__ __forceinline__ void sources(const DevBlock& b, const Par& P, int k, 
   lower3(m.g, B, Bl);
   double B2 = dot3(B, Bl), Bv = dot3(B, vl);
   double b2 = fma(B2, iW * iW, Bv * Bv);
-  double rhoh = fma(P.gfac, p, rho);
+  double rhoh = P.eos == 0 ? fma(P.gfac, p, rho) : eos_rhoh(P, rho, p);
   double Ptot = fma(0.5, b2, p);
   double WBv = W * Bv;
   double bb[3] = {fma(WBv, v[0], B[0] * iW), fma(WBv, v[1], B[1] * iW), fma(WBv, v[2], B[2] * iW)};

@@ -53,34 +53,7 @@ __global__ void k_noalloc_setup(DevBlock b, PreTable t, DevBlock* dblk, long lon
   }
 }
 
-int to_par(const mhd_params* p, Par& P) {
-  if (!p) return MHD_EINVAL;
-  if (!(p->gamma > 1.0) || !(p->rho_atm > 0.0) || !(p->T_atm > 0.0) || !(p->f_thr >= 0.0) || !(p->c2p_tol > 0.0) ||
-      !(p->W_max > 1.0) || p->recon < 0 || p->recon > 4 || p->rsolver < 0 || p->rsolver > 1 ||
-      (p->rk_order != 2 && p->rk_order != 3) || p->c2p_maxit < 1 || p->c2p_guess != 0 ||
-      (p->dmp_M > 0.0 && p->dmp_M < 1.0))
-    return MHD_EINVAL;
-  P.gam = p->gamma;
-  P.gm1 = p->gamma - 1.0;
-  P.gfac = p->gamma / (p->gamma - 1.0);
-  P.rho_atm = p->rho_atm;
-  P.T_atm = p->T_atm;
-  P.rho_thr = p->f_thr * p->rho_atm;
-  P.eps_atm = p->T_atm / (p->gamma - 1.0);
-  P.P_atm = p->rho_atm * p->T_atm;
-  P.sigma_max = p->sigma_max;
-  P.dmp_M = p->dmp_M;
-  P.tol = p->c2p_tol;
-  P.vmax2 = 1.0 - 1.0 / (p->W_max * p->W_max);
-  P.alpha_exc = p->alpha_exc;
-  P.recon = p->recon;
-  P.rsolver = p->rsolver;
-  P.fofc = p->fofc ? 1 : 0;
-  P.rk_order = p->rk_order;
-  P.maxit = p->c2p_maxit;
-  P.guess = 0;
-  return MHD_OK;
-}
+int to_par(const mhd_params* p, Par& P) { return fill_par(p, P, false); }
 
 // Per-device set-up on the first call with that device current: look up the
 // device address of the static array (host code cannot use its name as one).

@@ -49,6 +49,14 @@ def rk_w(p, stage):
     return [(0.0, 1.0, 1.0), (0.75, 0.25, 0.25), (1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0)][stage]
 
 
+def pgm1(p):
+    """The factor that turns an absolute error of eps into one of P: Gamma - 1
+    for the ideal gas; for the hybrid EOS the largest index minus 1."""
+    if not getattr(p, "eos", 0):
+        return p.gamma - 1.0
+    return max([p.eos_gamma_th] + [p.eos_gamma[i] for i in range(p.eos_pieces)]) - 1.0
+
+
 def term_scales(p, ob_in: O.Block, out: dict, dt: float, stage: int):
     """Magnitude of the terms that form each updated value (the scale of its
     rounding error): for U_v, g1|U_v| + g0|U^n_v| + b dt sum_d (|F_d(+)| +
@@ -73,7 +81,7 @@ def term_scales(p, ob_in: O.Block, out: dict, dt: float, stage: int):
     # the pressure recovered from tau~ = E~ - D~ has the absolute precision of
     # (Gamma-1)(D~ + |tau~|), and the momentum update takes its differences
     # over the faces: that rounding enters the momentum scale too
-    Pscale = (p.gamma - 1.0) * (U[0] + U[4])
+    Pscale = pgm1(p) * (U[0] + U[4])
     T[1:4] += be * dt * 2.0 * Pscale * sum(1.0 / dx for dx in ob_in.dx)
     # term magnitude of every edge EMF: the four face EMFs it averages and
     # corrects (|F_a[5]| on a-faces, |F_b[6]| on b-faces)
@@ -217,7 +225,7 @@ def compare_prims(ob: O.Block, got: dict, p, what=""):
     # P: absolute error scale (Gamma-1)(D~+tau~)/sqrt(gamma) of the recovery
     g = ob.adm[4:10][(slice(None),) + R]
     det = g[0] * (g[3] * g[5] - g[4] ** 2) - g[1] * (g[1] * g[5] - g[4] * g[2]) + g[2] * (g[1] * g[4] - g[3] * g[2])
-    scale = (p.gamma - 1.0) * np.abs(ob.cons[0][R] + ob.cons[4][R]) / np.sqrt(det)
+    scale = pgm1(p) * np.abs(ob.cons[0][R] + ob.cons[4][R]) / np.sqrt(det)
     dP = np.abs(got["prim"][4][R] - ob.prim[4][R])
     errs["P"] = float(np.max(dP / (1e-10 * np.abs(ob.prim[4][R]) + 1e-12 * scale)))
     bad = {k: e for k, e in errs.items() if not (e <= PRIM_TOL if k != "P" else e <= 1.0)}
