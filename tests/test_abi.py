@@ -39,6 +39,15 @@ def test_null_and_bad_arguments_rejected_without_device(L):
     assert L.mhd_init(C.byref(p), C.byref(h)) == -1
     p = grmhd.params(dmp_M=0.5)
     assert L.mhd_init(C.byref(p), C.byref(h)) == -1
+    # hybrid EOS: pieces out of range, non-increasing dividing densities, a
+    # thermal index <= 1, and the FP32 root searches (ideal gas only)
+    for kw in (dict(eos_pieces=0), dict(eos_pieces=5), dict(eos_rho=(1e-4, 1e-8, 0.0)),
+               dict(eos_gamma_th=1.0), dict(eos_K0=-1.0), dict(c2p_guess=1), dict(c2p_guess=2), dict(eos=2)):
+        d = dict(eos=1, eos_pieces=3, eos_K0=1e-4, eos_gamma_th=1.8, eos_rho=(1e-8, 1e-4, 0.0),
+                 eos_gamma=(1.7, 2.4, 2.1, 0.0))
+        d.update(kw)
+        p = grmhd.params(gamma=2.0, **d)
+        assert L.mhd_init(C.byref(p), C.byref(h)) == -1, kw
     assert L.mhd_c2p(None, None, 0, None) == -1
     assert L.mhd_step(None, None, 1, 0.1, 0, None) == -1
     assert L.mhd_kernel_launches(None) == 0

@@ -344,3 +344,51 @@ def test_per_block_launches_and_autotune_reproduce_batched(G):
         assert torch.equal(a.cons, b.cons) and torch.equal(a.cons, c.cons)
         for d in range(3):
             assert torch.equal(a.bf[d], b.bf[d]) and torch.equal(a.bf[d], c.bf[d])
+
+
+def test_degenerate_and_ragged_block_shapes(G):
+    """Blocks one cell thick along one or more directions, and non-cubic
+    blocks, in one batched stage (RK3 substeps 0 and 1), each against the
+    oracle; flux sweeps of one face and segment lengths that do not divide n."""
+    p = O.params(gamma=2.0, rho_atm=1e-12, T_atm=1e-10, recon=2, rsolver=1, rk_order=3, fofc=1)
+    st = synth.spacetime(3)
+    specs = [((1, 1, 1), 0.75, (-3.0, -3.0, -3.0)), ((1, 6, 2), 0.375, (-2.0, 0.5, -1.0)),
+             ((5, 1, 3), 0.375, (0.3, -1.2, 0.4)), ((17, 2, 9), 0.75, (-4.0, -3.0, 1.0)),
+             ((33, 3, 1), 0.1875, (-2.5, 0.2, 0.1))]
+    obs = []
+    for n, dx, x0 in specs:
+        inp = synth.star_block(st, n, 4, (dx,) * 3, x0)
+        obs.append(O.init_block(p, inp.n, inp.ng, inp.dx, inp.adm, inp.prim, inp.A))
+    ctx = _ctx(G, p)
+    dt = 0.25 * 0.1875
+    for s in range(2):
+        dbs = [U.to_device(G, ob) for ob in obs]
+        ctx.stage(dbs, dt, s)
+        for ob, db in zip(obs, dbs):
+            got = U.from_device(db)
+            I = interior(ob)
+            gm = (got["flags"] & O.F_FOFC) != 0
+            mask = np.zeros(ob.cons.shape[1:], np.uint8)
+            mask[I] = gm[I]
+            ref = ob.copy()
+            out = O.stage(p, ref, dt, s, mask=mask, keep=True)
+            U.compare_prims(ref, got, p, f"{ob.n} stage {s}")
+            U.compare_state(ref, got, f"{ob.n} stage {s}", scales=U.term_scales(p, ob, out, dt, s))
+            ob.cons[...] = got["cons"]
+            ob.cons0[...] = got["cons0"]
+            for d in range(3):
+                ob.bf[d][...] = got["bf"][d]
+                ob.bf0[d][...] = got["bf0"][d]
+
+
+def test_empty_inputs(G):
+    """Zero cells is a no-op; an empty block list is an argument error."""
+    import torch
+    p = O.params(gamma=2.0)
+    ctx = _ctx(G, p)
+    z = lambda *s: torch.zeros(s, dtype=torch.float64, device="cuda")
+    ctx.c2p_cells(z(5, 0), z(3, 0), z(6, 0), z(5, 0), torch.zeros(0, dtype=torch.uint8, device="cuda"))
+    ctx.prim2cons(z(5, 0), z(3, 0), z(6, 0), z(5, 0))
+    assert ctx.read_stats()["cells"] == 0
+    with pytest.raises(RuntimeError):
+        ctx.stage([], 0.1, 0)
