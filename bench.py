@@ -211,6 +211,7 @@ def c2p_leg(G, n=1 << 24, reps=5):
     loss, delta, train_s = train_guess(ctx)
     # the test set, built on the device chunk by chunk
     cons0 = torch.empty((5, n), dtype=torch.float64, device="cuda")
+    ptrue = torch.empty((5, n), dtype=torch.float64, device="cuda")   # the generating primitives
     tB = torch.empty((3, n), dtype=torch.float64, device="cuda")
     tg = torch.empty((6, n), dtype=torch.float64, device="cuda")
     ch = 1 << 22
@@ -221,6 +222,7 @@ def c2p_leg(G, n=1 << 24, reps=5):
         cc = torch.empty((5, m), dtype=torch.float64, device="cuda")
         ctx.prim2cons(cp, cB, cg, cc)
         cons0[:, k:k + m] = cc
+        ptrue[:, k:k + m] = cp
         tB[:, k:k + m] = cB
         tg[:, k:k + m] = cg
     del cp, cB, cg, cc
@@ -233,6 +235,7 @@ def c2p_leg(G, n=1 << 24, reps=5):
         prim = torch.empty((5, n), dtype=torch.float64, device="cuda")
         fl = torch.empty(n, dtype=torch.uint8, device="cuda")
         it = torch.empty(n, dtype=torch.int32, device="cuda")
+        ctx.reset_stats()
         ctx.c2p_cells(cons, tB, tg, prim, fl, it)   # warm-up
         ms = []
         for _ in range(reps):
@@ -243,9 +246,15 @@ def c2p_leg(G, n=1 << 24, reps=5):
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
+        st = ctx.read_stats()
+        Wt = torch.sqrt(1 + (ptrue[1:4] ** 2).sum(0))
         res[name] = {"cells_per_s": n / (float(np.median(ms)) * 1e-3), "ms": float(np.median(ms)),
                      "fp64_evals_per_cell": float(it.double().mean().item()),
-                     "fails": int(((fl & 1) != 0).sum().item())}
+                     "fp64_evals_p99": int(it.sort().values[int(0.99 * (n - 1))].item()),
+                     "guess_fallback_rate": st["guess_fallbacks"] / max(st["cells"], 1),
+                     "fails": int(((fl & 1) != 0).sum().item()),
+                     "max_rel_err_rho_vs_generating": float(((prim[0] - ptrue[0]).abs() / ptrue[0]).max().item()),
+                     "max_err_w_over_W_vs_generating": float(((prim[1:4] - ptrue[1:4]).abs() / Wt).max().item())}
         prims[name] = prim
     p0 = prims["plain"]
     W = torch.sqrt(1 + (p0[1:4] ** 2).sum(0))

@@ -120,6 +120,9 @@ typedef struct {
   long long fofc_cells; /* cells flagged by FOFC (incl. DMP) */
   long long dmp_cells;  /* cells flagged by the DMP test */
   long long fofc_faces; /* faces recomputed at first order */
+  long long guess_fallbacks; /* c2p_guess 1, 2: cells whose FP32 root did not
+                                bracket the FP64 root within 4e-6 (the bracket
+                                then extends to 0 or 1) */
 } mhd_stats;
 
 /* Create a context on the current device.  *out receives it.  Copies p. */

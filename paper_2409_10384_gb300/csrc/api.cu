@@ -443,7 +443,7 @@ void c2p_seed(mhd_ctx* c, const KrpBuf& kb, long long n, cudaStream_t s) {
     timed(c, MHD_K_MLP, s, [&] { launch_mlp_infer(c->gfeat, n, c->nm, c->mlp_wb, c->mlp, c->glogmu, s, c->nsm); });
   const long long g = std::max(1LL, std::min((n + 127) / 128, (long long)c->nsm * std::max(c->occ_krp[5], 1)));
   timed(c, MHD_K_C2P, s, [&] {
-    launch_krp_seed(c->P, kb, c->glogmu, mode == 1 ? 1 : 0, (float)c->mlp_delta, s, (int)g);
+    launch_krp_seed(c->P, kb, c->glogmu, mode == 1 ? 1 : 0, (float)c->mlp_delta, c->dstats, s, (int)g);
   });
 }
 
@@ -825,7 +825,8 @@ int mhd_c2p_cells(mhd_ctx* c, long n, double* cons, const double* Bd, const doub
     timed(c, MHD_K_MLP, s, [&] { launch_mlp_infer(feat, n, c->nm, c->mlp_wb, c->mlp, logmu, s, c->nsm); });
   if (mode != 0)
     timed(c, MHD_K_C2P, s, [&] {
-      launch_krp_seed(c->P, kb, logmu, mode == 1 ? 1 : 0, (float)c->mlp_delta, s, cells_grid(c, n, c->occ_krp[5]));
+      launch_krp_seed(c->P, kb, logmu, mode == 1 ? 1 : 0, (float)c->mlp_delta, c->dstats, s,
+                      cells_grid(c, n, c->occ_krp[5]));
     });
   timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, c->dstats, s, c->g_solve_cells()); });
   timed(c, MHD_K_C2P, s, [&] {
@@ -1108,6 +1109,7 @@ int mhd_read_stats(mhd_ctx* c, mhd_stats* out, void* stream) {
   out->fofc_cells = (long long)h[4];
   out->dmp_cells = (long long)h[5];
   out->fofc_faces = (long long)h[6];
+  out->guess_fallbacks = (long long)h[7];
   return MHD_OK;
 }
 

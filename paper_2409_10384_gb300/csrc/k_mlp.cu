@@ -358,8 +358,9 @@ __device__ __forceinline__ float f32_mu_plus(const KSf& s) {
 // the bracket extends from the far point to 0 (f(0) < 0, no evaluation) or
 // 1 (f(1) >= 0 for a physical state).  The refill solve finishes from there.
 __global__ void __launch_bounds__(128) k_krp_seed(Par P, KrpBuf kb, const float* __restrict__ logmu, int learned,
-                                                  float delta) {
+                                                  float delta, unsigned long long* stats) {
   const long long n = kb.n;
+  unsigned s_fb = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     if (kb.st[i] != 4) continue;
     KS s;
@@ -416,6 +417,7 @@ __global__ void __launch_bounds__(128) k_krp_seed(Par P, KrpBuf kb, const float*
         its++;
         Gb = G;
         if (!(Gb >= 0.0)) st = 2;
+        s_fb++;
       }
       if (st == 0 && Gb == 0.0) { st = 1; kb.w[KW_MU * n + i] = b; }
     } else {
@@ -430,6 +432,7 @@ __global__ void __launch_bounds__(128) k_krp_seed(Par P, KrpBuf kb, const float*
         kb.w[KW_MU * n + i] = x;
       } else {
         b = x; Gb = G;
+        s_fb++;
       }
     }
     kb.w[KW_A * n + i] = a; kb.w[KW_B * n + i] = b;
@@ -437,6 +440,7 @@ __global__ void __launch_bounds__(128) k_krp_seed(Par P, KrpBuf kb, const float*
     kb.it[i] = its;
     kb.st[i] = st;
   }
+  warp_flush(&stats[7], s_fb);
 }
 
 // log(mu) of solved cells (training targets); NaN where the solve failed
@@ -485,9 +489,9 @@ void launch_mlp_pack(const float* w, __nv_bfloat16* wb, cudaStream_t s) {
 void launch_mlp_stats(const float* feat, const float* target, long long n, double* acc, cudaStream_t s, int nsm) {
   k_mlp_stats<<<nsm * 4, 256, 0, s>>>(feat, target, n, acc);
 }
-void launch_krp_seed(const Par& P, const KrpBuf& kb, const float* logmu, int learned, float delta, cudaStream_t s,
-                     int grid) {
-  k_krp_seed<<<grid, 128, 0, s>>>(P, kb, logmu, learned, delta);
+void launch_krp_seed(const Par& P, const KrpBuf& kb, const float* logmu, int learned, float delta,
+                     unsigned long long* stats, cudaStream_t s, int grid) {
+  k_krp_seed<<<grid, 128, 0, s>>>(P, kb, logmu, learned, delta, stats);
 }
 
 }  // namespace grmhd

@@ -47,7 +47,7 @@ class mhd_block(C.Structure):
 class mhd_stats(C.Structure):
     _fields_ = [("cells", C.c_longlong), ("iters", C.c_longlong), ("fails", C.c_longlong),
                 ("floors", C.c_longlong), ("fofc_cells", C.c_longlong), ("dmp_cells", C.c_longlong),
-                ("fofc_faces", C.c_longlong)]
+                ("fofc_faces", C.c_longlong), ("guess_fallbacks", C.c_longlong)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

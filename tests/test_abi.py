@@ -54,10 +54,10 @@ def test_null_and_bad_arguments_rejected_without_device(L):
 
 
 def test_struct_layouts_match_header():
-    # mhd_params: 9 doubles + 8 ints + 9 doubles (EOS); mhd_block: 3+1 ints, 3 doubles, 12 pointers; mhd_stats: 7 int64
+    # mhd_params: 9 doubles + 8 ints + 9 doubles (EOS); mhd_block: 3+1 ints, 3 doubles, 12 pointers; mhd_stats: 8 int64
     assert C.sizeof(grmhd.mhd_params) == 9 * 8 + 8 * 4 + 9 * 8
     assert C.sizeof(grmhd.mhd_block) == 16 + 24 + 12 * 8
-    assert C.sizeof(grmhd.mhd_stats) == 7 * 8
+    assert C.sizeof(grmhd.mhd_stats) == 8 * 8
 
 
 def test_block_list_cache_follows_device_pointers():

@@ -123,8 +123,14 @@ def test_learned_con2prim_same_root_fewer_iterations(G):
         pr = torch.zeros_like(tprim)
         fl = torch.zeros(n, dtype=torch.uint8, device="cuda")
         it = torch.zeros(n, dtype=torch.int32, device="cuda")
+        ctx.reset_stats()
         ctx.c2p_cells(cc, tB, tg, pr, fl, it)
+        st = ctx.read_stats()
         out[guess] = (pr.cpu().numpy(), fl.cpu().numpy(), it.cpu().numpy())
+        # cells whose FP32 root missed the 4e-6 bracket: none without a guess,
+        # a small fraction with one
+        assert st["cells"] == n
+        assert st["guess_fallbacks"] == 0 if guess == 0 else st["guess_fallbacks"] <= 0.1 * n, (guess, st)
     p0, f0, i0 = out[0]
     cons = c0.cpu().numpy()
     det = g[0] * (g[3] * g[5] - g[4] ** 2) - g[1] * (g[1] * g[5] - g[4] * g[2]) + g[2] * (g[1] * g[4] - g[3] * g[2])
