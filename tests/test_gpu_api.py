@@ -1,0 +1,89 @@
+"""Entry points of the C-ABI not covered by the parity files: pinned launch
+shapes, the per-kernel profile, the network state round trip."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2409_10384_gb300 import synth
+from tests import gpu_util as U
+import tests.test_gpu_parity as T
+
+pytestmark = pytest.mark.gpu
+
+G = T.G
+
+
+def _star(G, p, sub=16, corner=(56, 56, 56)):
+    inp = synth.star_subblock(sub=sub, corner=corner)
+    ob = O.init_block(p, inp.n, inp.ng, inp.dx, inp.adm, inp.prim, inp.A)
+    return inp, ob
+
+
+def test_pinned_launch_shapes_are_bit_identical(G):
+    """Every tunable kernel pinned to other CTA sizes and waves gives the same
+    bits as the default shapes; get_launch reads back what set_launch pinned;
+    out-of-range shapes are rejected."""
+    p = O.params(gamma=2.0, rho_atm=1e-12, T_atm=1e-10, f_thr=0.1, recon=2, rsolver=1, rk_order=3, fofc=1)
+    inp, ob = _star(G, p)
+    dt = 0.25 * inp.dx[0]
+    ctx = T._ctx(G, p)
+    a = U.to_device(G, ob)
+    ctx.step([a], dt)
+    ref = U.from_device(a)
+    ctx2 = T._ctx(G, p)
+    for k, (th, wv) in zip(G.Context.TUNABLE, [(64, 1), (256, 2), (64, 3), (256, 1), (128, 4), (64, 2),
+                                                (256, 3), (128, 1), (256, 4)]):
+        ctx2.set_launch(k, th, wv)
+        assert ctx2.get_launch(k) == (th, wv)
+    b = U.to_device(G, ob)
+    ctx2.step([b], dt)
+    got = U.from_device(b)
+    for key in ("cons", "prim", "flags"):
+        assert np.array_equal(got[key], ref[key]), key
+    for d in range(3):
+        assert np.array_equal(got["bf"][d], ref["bf"][d])
+    for bad in ((96, 1), (128, 0), (128, 65)):
+        with pytest.raises(RuntimeError):
+            ctx2.set_launch("flux_x", *bad)
+
+
+def test_profile_counts_every_launch(G):
+    """Per-kernel CUDA-event profile: one entry per launch of the stage, the
+    launch total matching the context's counter, positive times."""
+    p = O.params(gamma=2.0, rho_atm=1e-12, T_atm=1e-10, f_thr=0.1, recon=2, rsolver=1, rk_order=3, fofc=1)
+    inp, ob = _star(G, p)
+    ctx = T._ctx(G, p)
+    a = U.to_device(G, ob)
+    ctx.step([a], 0.25 * inp.dx[0])    # first call: list set-up outside the profile
+    ctx.profile(True)
+    ctx.profile_read()
+    l0 = ctx.launches()
+    ctx.step([a], 0.25 * inp.dx[0])
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    n = sum(v[1] for v in prof.values())
+    assert n == ctx.launches() - l0
+    # per RK3 step: one launch per stage, the con2prim's prep and finish two
+    for name, k in (("flux_x", 3), ("flux_y", 3), ("flux_z", 3), ("c2p", 6), ("update", 3), ("emf", 3)):
+        assert prof[name][1] == k and prof[name][0] > 0.0, (name, prof[name])
+
+
+def test_network_state_round_trip(G):
+    """mlp_get / mlp_set carry the trained network (weights, normalisation,
+    bracket width) to another context: the same inference bits."""
+    import torch
+    p = O.params(gamma=2.0, rho_atm=1e-20, T_atm=1e-14, f_thr=0.0)
+    kw = {k: getattr(p, k) for k, _ in p._fields_ if k != "pad_"}
+    a = G.Context(G.params(**kw))
+    prim, Bd, g = synth.c2p_stress(20000, seed=31)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    cons = torch.zeros((5, prim.shape[1]), dtype=torch.float64, device="cuda")
+    a.prim2cons(t(prim), t(Bd), t(g), cons)
+    feat, logmu = a.mlp_dataset(cons, t(Bd), t(g))
+    a.mlp_init(5)
+    a.mlp_train(feat, logmu, epochs=2, batch=2048, lr=3e-3)
+    st = a.mlp_get()
+    b = G.Context(G.params(**kw))
+    b.mlp_set(st)
+    assert np.array_equal(b.mlp_get(), st)
+    assert torch.equal(a.mlp_infer(feat), b.mlp_infer(feat))

@@ -28,11 +28,18 @@ def G():
     return grmhd
 
 
-def test_noalloc_stage_matches_context_stage_twice(G):
+@pytest.mark.parametrize("eos", [0, 1])
+def test_noalloc_stage_matches_context_stage_twice(G, eos):
     import torch
-    p = O.params(gamma=2.0, rho_atm=1e-12, T_atm=1e-10, f_thr=0.1, recon=2, rsolver=1, rk_order=3, fofc=1)
-    inp = synth.star_subblock(sub=24, corner=(104, 52, 52))   # over the stellar surface: FOFC fires
-    ob = O.init_block(p, inp.n, inp.ng, inp.dx, inp.adm, inp.prim, inp.A)
+    from tests.test_gpu_hybrid_eos import HYB_STAR, _star_hyb
+    p = O.params(gamma=2.0, rho_atm=1e-12, T_atm=1e-10, f_thr=0.1, recon=2, rsolver=1, rk_order=3, fofc=1,
+                 **(HYB_STAR if eos else {}))
+    if eos:
+        inp, prim = _star_hyb(p, (104, 52, 52))
+    else:
+        inp = synth.star_subblock(sub=24, corner=(104, 52, 52))   # over the stellar surface: FOFC fires
+        prim = inp.prim
+    ob = O.init_block(p, inp.n, inp.ng, inp.dx, inp.adm, prim, inp.A)
     gp = G.params(**{k: getattr(p, k) for k, _ in p._fields_ if k != "pad_"})
     ctx = G.Context(gp)
     a = U.to_device(G, ob)
