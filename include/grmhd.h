@@ -272,8 +272,8 @@ int mhd_profile(mhd_ctx* ctx, int enable);
 int mhd_profile_read(mhd_ctx* ctx, double* ms, long long* count);
 const char* mhd_kernel_name(int kind);
 
-/* Learned con2prim guess (not in the paper; the spec addition of this
- * library).  A 5 -> 64 -> 64 -> 1 tanh network with BF16 operands and FP32
+/* Learned con2prim guess (not in the paper; an addition of this library).
+ * A 5 -> 64 -> 64 -> 1 tanh network with BF16 operands and FP32
  * accumulation on the tensor cores predicts log(mu) of the Kastaun et al. root
  * from five features of the cell's KRP variables; with mhd_params.c2p_guess = 1
  * every con2prim starts FP32 secant steps at the guess (second point at

@@ -3,7 +3,8 @@
 // predicting log(mu) of the Kastaun et al. root from five features of the
 // KRP variables.  Hand-written inference, forward + backward training step,
 // Adam, and the bracket that the FP64 solve starts from.  The paper has no
-// such network; the FP64 bracketed solve stays the refinement and the judge.
+// such network; the FP64 bracketed solve stays the refinement and decides the
+// root.
 #include <cuda_bf16.h>
 
 #include "dev.cuh"
