@@ -394,20 +394,16 @@ __device__ __forceinline__ double f_zero(const KS& s, const Par& P) {
   return -1.0 / fma(s.gam, e0, 1.0);
 }
 
-// Upper bracket end: three steps of mu <- 1/sqrt(1 + rbar^2(mu)) from
-// 1/sqrt(1 + r_par^2); every iterate bounds the root of
-// f_a(mu) = mu sqrt(1 + rbar^2(mu)) - 1 from above (h_min = 1).
+// Upper bracket end: 1/sqrt(1 + r_par^2).  rbar^2(mu) >= r_par^2 for every
+// mu (rbar^2 falls from r^2 at mu = 0 towards r_par^2), so this bounds the
+// root of f_a(mu) = mu sqrt(1 + rbar^2(mu)) - 1 (h_min = 1), and with it the
+// master function's root, from above.  The fixed-point steps
+// mu <- 1/sqrt(1 + rbar^2(mu)) from here tighten the bound, but on the star
+// workloads they left the Illinois evaluations per cell unchanged (5.47) and
+// cost 1.7% of the RK3 step, so the bracket starts from the bound itself.
 __device__ __forceinline__ double mu_plus(const KS& s) {
-  double rpar2 = s.b2 > 0.0 ? s.rb2 / s.b2 : s.r2;
-  double mu = rsqrt(1.0 + rpar2);
-#pragma unroll
-  for (int it = 0; it < 3; it++) {
-    // 1/sqrt(1 + rbar^2) = d / sqrt(d^2 + N) with d, N as in kev_g
-    const double d = fma(mu, s.b2, 1.0);
-    const double N = fma(mu * (d + 1.0), s.rb2, s.r2);
-    mu = d * rsqrt(fma(d, d, N));
-  }
-  return mu;
+  const double rpar2 = s.b2 > 0.0 ? s.rb2 / s.b2 : s.r2;
+  return rsqrt(1.0 + rpar2);
 }
 
 // Five features of the KRP variables for the learned guess (FP32):
