@@ -756,10 +756,7 @@ __device__ __forceinline__ void rec_init(RecVar& s, double xm2, double xm1, doub
 }
 
 // Face values of cell m given x_{m+2}; advances the state to cell m+1.
-// The WENO-Z weights follow Borges et al. (2008) with p = 1 and linear weights
-// (1, 6, 3)/10: omega_k ~ d_k (1 + tau5/(b_k + eps)); multiplied through by
-// the product of the three (b_k + eps) they need no division.  The two face
-// values of the cell share one reciprocal.
+// R = 0, 1, 3, 4; WENO-Z (R = 2) goes through wz_parts and wz_finish.
 template <int R>
 __device__ __forceinline__ void rec_step(RecVar& s, double xn, double& lo, double& hi) {
   if (R >= 3) {
@@ -783,43 +780,9 @@ __device__ __forceinline__ void rec_step(RecVar& s, double xn, double& lo, doubl
     s.x2 = xn;
     return;
   }
+  static_assert(R != 2, "WENO-Z: wz_parts / wz_finish");
   const double dn = xn - s.x2;  // delta_{m+1}
-  if (R == 2) {
-    double b0n, b1n, b2n;
-    wz_window(s.d2, dn, b0n, b1n, b2n);
-    const double eps = 1e-40;
-    const double b0 = s.b0p, b1 = s.b1c, b2 = b2n;
-    const double tau = fabs(b0 - b2);
-    const double e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
-    const double A0 = (e0 + tau) * (e1 * e2);
-    const double A1 = (e1 + tau) * (e0 * e2);
-    const double A2 = (e2 + tau) * (e0 * e1);
-    const double a1 = 6.0 * A1, a2h = 3.0 * A2, a0l = 3.0 * A0;
-    const double den_hi = A0 + a1 + a2h;   // stencils 0,1,2 of the value at m+1/2
-    const double den_lo = a0l + a1 + A2;   // mirrored: b2 pairs with weight 1, b0 with 3
-    // the three third-order candidates minus x_m, times 6
-    const double da = s.d0, db = s.d1, dc = s.d2, dd = dn;
-    const double k0 = fma(5.0, db, -2.0 * da);
-    const double k1 = fma(2.0, dc, db);
-    const double k2 = fma(4.0, dc, -dd);
-    const double m0 = fma(-5.0, dc, 2.0 * dd);
-    const double m1 = fma(2.0, db, dc);
-    const double m2 = fma(-4.0, db, da);
-    const double n_hi = fma(A0, k0, fma(a1, k1, a2h * k2));
-    const double n_lo = fma(A2, m0, fma(-a1, m1, a0l * m2));
-    const double pr = den_hi * den_lo;
-    if (__double2hiint(pr) < 0x7E000000) {   // pr < 2^993: one shared reciprocal
-      const double r = (1.0 / 6.0) / pr;
-      hi = fma(n_hi, den_lo * r, s.x1);
-      lo = fma(n_lo, den_hi * r, s.x1);
-    } else {
-      hi = s.x1 + n_hi / (6.0 * den_hi);
-      lo = s.x1 + n_lo / (6.0 * den_lo);
-    }
-    s.b0p = s.b0c;
-    s.b0c = b0n;
-    s.b1c = b1n;
-  } else if (R == 1) {
+  if (R == 1) {
     const double dl = s.d1, dr = s.d2;
     const double pr = dl * dr;
     const double h = pr > 0.0 ? pr / (dl + dr) : 0.0;   // half the van Leer slope
@@ -835,8 +798,11 @@ __device__ __forceinline__ void rec_step(RecVar& s, double xn, double& lo, doubl
   s.d2 = dn;
 }
 
-// WENO-Z part of rec_step<2> without the division: x_m, the two numerators
-// and denominators of hi = x + n_hi / (6 den_hi), lo = x + n_lo / (6 den_lo);
+// WENO-Z (Borges et al. 2008, p = 1, linear weights (1, 6, 3)/10:
+// omega_k ~ d_k (1 + tau5/(b_k + eps)), multiplied through by the product of
+// the three (b_k + eps) so that they need no division) of cell m given
+// x_{m+2}, without the final division: x_m, the two numerators and
+// denominators of hi = x + n_hi / (6 den_hi), lo = x + n_lo / (6 den_lo);
 // advances the state to cell m+1.
 __device__ __forceinline__ void wz_parts(RecVar& s, double xn, double& x, double& n_hi, double& n_lo, double& d_hi,
                                          double& d_lo) {

@@ -85,12 +85,12 @@ __global__ void __launch_bounds__(256) k_flux(Work w, Par P) {
     for (int v = 0; v < 7; v++) {
       const double* a = src[v] + c;
       rec_init<R>(rv[v], a[-2 * st], a[-st], a[0], a[st]);
-      if (R != 2) {
+      if constexpr (R != 2) {
         double lo;
         rec_step<R>(rv[v], a[2 * st], lo, Ls[v]);
       }
     }
-    if (R == 2) {
+    if constexpr (R == 2) {
       double x[7], nh[7], nl[7], dh[7], dl[7], lo[7];
 #pragma unroll
       for (int v = 0; v < 7; v++) wz_parts(rv[v], src[v][c + 2 * st], x[v], nh[v], nl[v], dh[v], dl[v]);
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(256) k_flux(Work w, Par P) {
     for (int q = 0; q < nf; q++) {
       c += st;
       double Rs[7], Lnext[7];
-      if (R == 2) {
+      if constexpr (R == 2) {
         double x[7], nh[7], nl[7], dh[7], dl[7];
 #pragma unroll
         for (int v = 0; v < 7; v++) wz_parts(rv[v], src[v][c + 2 * st], x[v], nh[v], nl[v], dh[v], dl[v]);
