@@ -152,7 +152,10 @@ int mhd_c2p_cells(mhd_ctx* ctx, long n, double* cons, const double* Bd, const do
 
 /* con2prim of every cell within 3 of the interior of each block (the stencil
  * region of WENO-Z), with bcc and the cell-centred EMF; floors write back to
- * cons.  This is step 1 of a stage. */
+ * cons.  This is step 1 of a stage.  It also keeps sqrt(gamma), 1/sqrt(gamma)
+ * and gamma^ij of every cell in context scratch for steps 2-5 of the same
+ * stage, so the ADM arrays must not change between mhd_c2p and mhd_rk_update
+ * of one stage (the metric is an input of the whole stage). */
 int mhd_c2p(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, void* stream);
 
 /* Steps 2-4 of stage `stage` (0-based) with time step dt: reconstruction and

@@ -248,6 +248,7 @@ int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
     need += al256(sizeof(double) * (ne[0] + ne[1] + ne[2]));
     need += al256(sizeof(double) * 3 * b.ncell);
     need += al256((size_t)b.ncell);
+    need += al256(sizeof(double) * 8 * (size_t)b.ncell);
     if (c->P.guess == 3) need += al256(sizeof(double) * (size_t)b.ncell);
     const long long n0 = s.n[0], n1 = s.n[1], n2 = s.n[2];
     long long items[W_NKIND];
@@ -304,6 +305,8 @@ int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
     p += al256(sizeof(double) * 3 * b.ncell);
     b.fflag = (unsigned char*)p;
     p += al256((size_t)b.ncell);
+    b.mc = (double*)p;
+    p += al256(sizeof(double) * 8 * (size_t)b.ncell);
     b.mu = nullptr;
     if (c->P.guess == 3) {
       b.mu = (double*)p;

@@ -55,6 +55,10 @@ struct DevBlock {
   int id;            // index of the block in its list
   double* mu;        // [ncell] con2prim root of the last stage-input con2prim
                      // (c2p_guess 3; 0: none), else null
+  double* mc;        // [8][ncell] metric of the stage region: sqrt(gamma),
+                     // 1/sqrt(gamma), gamma^ij; written by the stage-input
+                     // con2prim, read by the FOFC estimate and the update of
+                     // the same stage (null: each computes its own)
 };
 // Relative half-width of the bracket around a previous root (c2p_guess 3).
 constexpr double WARM_DELTA = 1e-3;
@@ -179,6 +183,27 @@ __device__ __forceinline__ void metric_setup(Metric& m) {
   m.gi[3] = (g[0] * g[5] - g[2] * g[2]) * idet;
   m.gi[4] = (g[1] * g[2] - g[0] * g[4]) * idet;
   m.gi[5] = (g[0] * g[3] - g[1] * g[1]) * idet;
+}
+// The stage's metric cache (DevBlock.mc) at cell c: store after metric_setup,
+// or load g from the ADM array and the rest from the cache.
+__device__ __forceinline__ void metric_store(double* mc, long long nc, long long c, const Metric& m) {
+  mc[c] = m.sdet;
+  mc[nc + c] = m.isdet;
+#pragma unroll
+  for (int v = 0; v < 6; v++) mc[(2 + v) * nc + c] = m.gi[v];
+}
+__device__ __forceinline__ void metric_cell(const double* adm, const double* mc, long long nc, long long c,
+                                            Metric& m) {
+#pragma unroll
+  for (int v = 0; v < 6; v++) m.g[v] = adm[(4 + v) * nc + c];
+  if (mc) {
+    m.sdet = mc[c];
+    m.isdet = mc[nc + c];
+#pragma unroll
+    for (int v = 0; v < 6; v++) m.gi[v] = mc[(2 + v) * nc + c];
+  } else {
+    metric_setup(m);
+  }
 }
 __device__ __forceinline__ void lower3(const double* g, const double* u, double* l) {
   l[0] = g[0] * u[0] + g[1] * u[1] + g[2] * u[2];

@@ -184,6 +184,7 @@ __global__ void __launch_bounds__(256) k_krp_prep_block(Work w, Par P, KrpBuf kb
     for (int v = 0; v < 3; v++) b.bcc[v * nc + c] = Bd[v];
     Metric m;
     load_metric6(b.adm + 4 * nc, nc, c, m);
+    if (b.mc) metric_store(b.mc, nc, c, m);
     double U[5];
 #pragma unroll
     for (int v = 0; v < 5; v++) U[v] = b.cons[v * nc + c];
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(256) k_krp_prep_fofc(Work w, Par P, double g0,
       U[v] = fma(-bdt, div, u);
     }
     Metric m;
-    load_metric6(b.adm + 4 * nc, nc, c, m);
+    metric_cell(b.adm, b.mc, nc, c, m);
     const double Bd[3] = {b.bcc[c], b.bcc[nc + c], b.bcc[2 * nc + c]};
     prep_cell(P, kb, it, U, Bd, m, learned != 0, feat, b.adm[c], b.mu ? b.mu[c] : 0.0);
     kb.w[KW_USD * n + it] = U[0];

@@ -68,9 +68,7 @@ __device__ __forceinline__ void sources(const DevBlock& b, const Par& P, int k, 
   const long long nc = b.ncell, c = cidx(b, k, j, i);
   const double* A = b.adm;
   Metric m;
-#pragma unroll
-  for (int v = 0; v < 6; v++) m.g[v] = A[(4 + v) * nc + c];
-  metric_setup(m);
+  metric_cell(A, b.mc, nc, c, m);
   const double alpha = A[c];
   const long long st[3] = {1, (long long)b.N[0], (long long)b.N[0] * b.N[1]};
   // centred derivatives of alpha, beta^i, gamma_ij
