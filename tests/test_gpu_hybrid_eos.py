@@ -122,16 +122,17 @@ def _star_hyb(p, corner):
     return inp, prim
 
 
-@pytest.mark.parametrize("where,recon,rs", [("surface", 2, 1), ("core", 2, 0), ("surface", 3, 1)])
-def test_hybrid_stage_star(G, where, recon, rs):
+@pytest.mark.parametrize("where,recon,rs,guess", [("surface", 2, 1, 0), ("core", 2, 0, 0), ("surface", 3, 1, 0),
+                                                 ("surface", 2, 1, 3)])
+def test_hybrid_stage_star(G, where, recon, rs, guess):
     """All three RK3 substeps of a star sub-block with the hybrid EOS and FOFC,
-    fluxes and states against the oracle."""
+    fluxes and states against the oracle; guess 3: the warm-started bracket."""
     p = O.params(gamma=2.0, rho_atm=1e-12, T_atm=1e-10, f_thr=0.1, recon=recon, rsolver=rs, rk_order=3,
                  fofc=1, **HYB_STAR)
     corner = (104, 52, 52) if where == "surface" else (52, 52, 52)
     inp, prim = _star_hyb(p, corner)
     ob = O.init_block(p, inp.n, inp.ng, inp.dx, inp.adm, prim, inp.A)
-    ctx = T._ctx(G, p)
+    ctx = G.Context(G.params(**{k: getattr(p, k) for k, _ in p._fields_ if k != "pad_"}, c2p_guess=guess))
     dt = 0.25 * inp.dx[0]
     for s in range(3):
         ref, got, flips = T._run_stage_pair(G, ctx, p, ob, dt, s)
