@@ -32,6 +32,7 @@ struct Par {
   double Gth, gth1;             // G_th and G_th - 1 (ideal gas: Gamma, Gamma - 1)
   double Pc_atm, epsc_atm, G_atm;
   int recon, rsolver, fofc, rk_order, maxit, guess, eos, npc;
+  int exc_on, sigma_on;         // alpha_exc > 0, sigma_max > 0
 };
 
 // One meshblock as seen by the kernels: caller arrays plus context scratch.
@@ -164,6 +165,25 @@ __device__ __forceinline__ int find_block(const Work& w, int K, long long it) {
 }
 
 // ------------------------------------------------------------- metric (Eq. 5)
+// Compares on the integer pipe.  An FP64 compare takes a slot of the narrow
+// FP64 pipe; from the bit patterns the answers are the same:
+//  lt0 / gt0 / eq0: x < 0, x > 0, x == 0 with IEEE semantics (false on NaN,
+//    +0 and -0 equal to 0);
+//  gt_nn(x, y): x > y for operands that are not NaN, at least one of them
+//    >= +0, and not the pair (+0, -0) - the signed order of the bit patterns.
+__device__ __forceinline__ bool lt0(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  return (u >> 63) && ((u & 0x7FFFFFFFFFFFFFFFull) - 1ull < 0x7FF0000000000000ull);
+}
+__device__ __forceinline__ bool gt0(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  return !(u >> 63) && (u - 1ull < 0x7FF0000000000000ull);
+}
+__device__ __forceinline__ bool eq0(double x) { return (__double_as_longlong(x) << 1) == 0; }
+__device__ __forceinline__ bool gt_nn(double x, double y) { return __double_as_longlong(x) > __double_as_longlong(y); }
+// finite (not inf, not NaN): the exponent field is not all ones
+__device__ __forceinline__ bool finite_bits(double x) { return (__double2hiint(x) & 0x7FF00000) != 0x7FF00000; }
+
 struct Metric {
   double g[6], gi[6], sdet, isdet;
 };
@@ -304,13 +324,13 @@ __device__ __forceinline__ void kev(const KS& s, double mu, KEval& e) {
   const double N = fma(mu * (d + 1.0), s.rb2, s.r2);
   const double mu2 = mu * mu, d2 = d * d;
   double W, x, id2, vh2;
-  e.vcap = mu2 * N > s.vmax2 * d2;
+  e.vcap = gt_nn(mu2 * N, s.vmax2 * d2);
   if (e.vcap) {
     x = 1.0 / d;
     id2 = x * x;
     vh2 = s.vmax2;
     W = rsqrt(1.0 - s.vmax2);
-  } else if (N == 0.0) {   // r = 0: at rest, W = 1 exactly (x multiplies r only)
+  } else if (eq0(N)) {   // r = 0: at rest, W = 1 exactly (x multiplies r only)
     x = id2 = vh2 = 0.0;
     W = 1.0;
   } else {
@@ -325,7 +345,7 @@ __device__ __forceinline__ void kev(const KS& s, double mu, KEval& e) {
   const double qbar = fma(-0.5 * mu2 * s.rperp2, id2, s.qh);
   double wm1 = vh2 * W * W / (1.0 + W);  // W - 1 without cancellation
   e.eps_raw = fma(W, qbar - mu * rbar2, wm1);
-  e.eps = e.eps_raw < s.eps_min ? s.eps_min : e.eps_raw;
+  e.eps = gt_nn(s.eps_min, e.eps_raw) ? s.eps_min : e.eps_raw;
   e.x = x;
   e.rbar2 = rbar2;
   e.W = W;
@@ -348,12 +368,12 @@ __device__ __forceinline__ double kev_g(const KS& s, double mu) {
   const double N = fma(mu * (d + 1.0), s.rb2, s.r2);
   const double mu2 = mu * mu, d2 = d * d;
   double W, id2, v2;
-  if (mu2 * N > s.vmax2 * d2) {
+  if (gt_nn(mu2 * N, s.vmax2 * d2)) {
     const double x = 1.0 / d;
     id2 = x * x;
     v2 = s.vmax2;
     W = rsqrt(1.0 - s.vmax2);
-  } else if (N == 0.0) {   // r = 0 (then r_perp = 0 too): at rest, W = 1 exactly
+  } else if (eq0(N)) {   // r = 0 (then r_perp = 0 too): at rest, W = 1 exactly
     id2 = v2 = 0.0;
     W = 1.0;
   } else {
@@ -367,7 +387,7 @@ __device__ __forceinline__ double kev_g(const KS& s, double mu) {
   const double A = fma(-fma(0.5 * mu2, s.rperp2, mu * N), id2, s.qh);   // qbar - mu rbar^2
   const double P1 = 1.0 + W;
   const double T = fma(P1 * W, A, v2 * (W * W));                          // (1 + W) eps_raw
-  const double Te = T < s.eps_min * P1 ? s.eps_min * P1 : T;
+  const double Te = gt_nn(s.eps_min * P1, T) ? s.eps_min * P1 : T;
   const double Z = fma(P1, fma(mu * rbar2, W, 1.0), s.gam * Te);
   return mu - (W * P1) / Z;
 }
@@ -415,7 +435,7 @@ __device__ __forceinline__ double kev_G(const KS& s, const Par& P, double mu) {
 // -1/(1 + Gamma eps(0)).
 __device__ __forceinline__ double f_zero(const KS& s, const Par& P) {
   if (P.eos != 0) return kev_G(s, P, 0.0);
-  double e0 = s.qh < s.eps_min ? s.eps_min : s.qh;
+  double e0 = gt_nn(s.eps_min, s.qh) ? s.eps_min : s.qh;
   return -1.0 / fma(s.gam, e0, 1.0);
 }
 
@@ -429,7 +449,7 @@ __device__ __forceinline__ double f_zero(const KS& s, const Par& P) {
 // per cell unchanged and saved 1.7% of the RK3 step, while relativistic cells
 // keep the tighter bracket.
 __device__ __forceinline__ double mu_plus(const KS& s) {
-  const double rpar2 = s.b2 > 0.0 ? s.rb2 / s.b2 : s.r2;
+  const double rpar2 = gt0(s.b2) ? s.rb2 / s.b2 : s.r2;
   double mu = rsqrt(1.0 + rpar2);
   if (s.r2 - rpar2 > 1e-3 * (1.0 + rpar2)) {
 #pragma unroll
@@ -469,10 +489,10 @@ __device__ __forceinline__ void krp_features(const KS& s, float* f) {
 __device__ __forceinline__ bool illinois(const KS& s, const Par& P, double a, double Ga, double b, double Gb,
                                          double tol, int maxit, double& root, int& iters) {
   iters = 0;
-  if (Gb == 0.0) { root = b; return true; }
+  if (eq0(Gb)) { root = b; return true; }
   double Fa = Ga, Fb = Gb;
   int side = 0;
-  while (b - a > tol * b) {
+  while (gt_nn(b - a, tol * b)) {
     if (iters >= maxit) return false;
     iters++;
     double c = (a * Fb - b * Fa) / (Fb - Fa);
@@ -480,13 +500,13 @@ __device__ __forceinline__ bool illinois(const KS& s, const Par& P, double a, do
     // the root the next point lands past it and closes the bracket
     const double eta = 0.25 * tol * b;
     c += side == -1 ? eta : (side == 1 ? -eta : 0.0);
-    if (!(c > a && c < b)) c = 0.5 * (a + b);
+    if (!(gt_nn(c, a) && gt_nn(b, c))) c = 0.5 * (a + b);
     const double G = kev_G(s, P, c);
-    if (G < 0.0) {
+    if (lt0(G)) {
       a = c; Ga = G; Fa = G;
       if (side == -1) Fb *= 0.5;
       side = -1;
-    } else if (G > 0.0) {
+    } else if (gt0(G)) {
       b = c; Gb = G; Fb = G;
       if (side == 1) Fa *= 0.5;
       side = 1;
@@ -518,20 +538,20 @@ __device__ __forceinline__ bool krp_prep(const Par& P, const double* U, const do
   double Bl[3];
   lower3(m.g, B, Bl);
   double B2 = dot3(B, Bl);
-  bool fin = isfinite(D) && isfinite(tau) && isfinite(Sl[0]) && isfinite(Sl[1]) && isfinite(Sl[2]) &&
-             isfinite(B2) && m.sdet > 0.0;
+  bool fin = finite_bits(D) && finite_bits(tau) && finite_bits(Sl[0]) && finite_bits(Sl[1]) &&
+             finite_bits(Sl[2]) && finite_bits(B2) && gt0(m.sdet);
   if (!fin) {
     flags |= F_FAIL;
     return false;
   }
   // inside the excision region (Sec. 4.7) every cell takes the D-floor reset
-  if (D < P.rho_thr || (P.alpha_exc > 0.0 && alpha < P.alpha_exc)) {
+  if (D < P.rho_thr || (P.exc_on && alpha < P.alpha_exc)) {
     D = P.rho_atm;
     Sl[0] = Sl[1] = Sl[2] = 0.0;
     tau = fma(D, P.eps_atm_rho, 0.5 * B2);
     flags |= F_DFLOOR;
   }
-  if (P.sigma_max > 0.0 && B2 > P.sigma_max * D) {
+  if (P.sigma_on && B2 > P.sigma_max * D) {
     D = B2 / P.sigma_max;
     flags |= F_SIGMA;
   }
@@ -551,7 +571,7 @@ __device__ __forceinline__ bool krp_prep(const Par& P, const double* U, const do
   k.rb = dot3(rl, k.bu);
   s.rb2 = k.rb * k.rb;
   double rp = s.r2 * s.b2 - s.rb2;
-  s.rperp2 = rp > 0.0 ? rp : 0.0;
+  s.rperp2 = gt0(rp) ? rp : 0.0;
   s.qh = fma(tau, iD, -0.5 * s.b2);
   s.gam = P.gam;
   s.eps_min = P.eps_atm;
@@ -572,9 +592,9 @@ __device__ __forceinline__ int krp_bracket(const KS& s, const Par& P, double glo
   bool have = false;
   if (glo >= 0.0 && ghi > glo) {
     const double Gl = kev_G(s, P, glo), Gh = kev_G(s, P, ghi);
-    if (Gl < 0.0 && Gh >= 0.0) {
+    if (lt0(Gl) && (eq0(Gh) || gt0(Gh))) {
       a = glo; Ga = Gl; b = ghi; Gb = Gh; have = true;
-    } else if (Gl >= 0.0) {
+    } else if (eq0(Gl) || gt0(Gl)) {
       b = glo; Gb = Gl; have = true;
     } else {
       a = ghi; Ga = Gh;
@@ -586,15 +606,15 @@ __device__ __forceinline__ int krp_bracket(const KS& s, const Par& P, double glo
     if (mp <= a) mp = 1.0;
     iters++;
     b = mp; Gb = kev_G(s, P, mp);
-    if (Gb < 0.0) {
+    if (lt0(Gb)) {
       a = mp; Ga = Gb;
       b = 1.0;
       iters++;
       Gb = kev_G(s, P, b);
     }
   }
-  if (!(Ga < 0.0 && Gb >= 0.0)) return 2;
-  if (Gb == 0.0) { mu = b; return 1; }
+  if (!(lt0(Ga) && (eq0(Gb) || gt0(Gb)))) return 2;
+  if (eq0(Gb)) { mu = b; return 1; }
   return 0;
 }
 
@@ -610,7 +630,7 @@ __device__ __forceinline__ void krp_finish(const Par& P, const KrpCell& k, doubl
     KEval e;
     if (P.eos == 0) {
       kev(s, mu, e);
-      if (e.eps_raw < s.eps_min) flags |= F_TEMP;
+      if (gt_nn(s.eps_min, e.eps_raw)) flags |= F_TEMP;
       double iW = e.W * (1.0 - (e.vcap ? s.vmax2 : mu * mu * e.rbar2));
       rho = k.D * iW;
       p = P.gm1 * rho * e.eps;

@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(256) k_krp_solve(Par P, KrpBuf kb, unsigned lo
     const bool act = idx >= 0;
     if (__ballot_sync(0xffffffffu, act || !done) == 0) break;
     if (!act) continue;
-    bool fin = !(b - a > P.tol * b), cap = false, exact = false;
+    bool fin = !gt_nn(b - a, P.tol * b), cap = false, exact = false;
     double root = 0.0;
     if (!fin) {
       if (it >= P.maxit) {
@@ -132,13 +132,13 @@ __global__ void __launch_bounds__(256) k_krp_solve(Par P, KrpBuf kb, unsigned lo
         double c = (a * Fb - b * Fa) / (Fb - Fa);
         const double eta = 0.25 * P.tol * b;
         c += side == -1 ? eta : (side == 1 ? -eta : 0.0);
-        if (!(c > a && c < b)) c = 0.5 * (a + b);
+        if (!(gt_nn(c, a) && gt_nn(b, c))) c = 0.5 * (a + b);
         const double G = kev_G(s, P, c);
-        if (G < 0.0) {
+        if (lt0(G)) {
           a = c; Ga = G; Fa = G;
           if (side == -1) Fb *= 0.5;
           side = -1;
-        } else if (G > 0.0) {
+        } else if (gt0(G)) {
           b = c; Gb = G; Fb = G;
           if (side == 1) Fa *= 0.5;
           side = 1;
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(256) k_krp_solve(Par P, KrpBuf kb, unsigned lo
           exact = fin = true;
           root = c;
         }
-        if (!fin) fin = !(b - a > P.tol * b);
+        if (!fin) fin = !gt_nn(b - a, P.tol * b);
       }
     }
     if (fin) {
