@@ -153,6 +153,7 @@ int fill_par(const mhd_params* p, Par& P, bool allow_guess) {
   P.alpha_exc = p->alpha_exc;
   P.exc_on = p->alpha_exc > 0.0 ? 1 : 0;
   P.sigma_on = p->sigma_max > 0.0 ? 1 : 0;
+  P.thr_pos = P.rho_thr > 0.0 ? 1 : 0;
   P.recon = p->recon;
   P.rsolver = p->rsolver;
   P.fofc = p->fofc ? 1 : 0;

@@ -33,6 +33,7 @@ struct Par {
   double Pc_atm, epsc_atm, G_atm;
   int recon, rsolver, fofc, rk_order, maxit, guess, eos, npc;
   int exc_on, sigma_on;         // alpha_exc > 0, sigma_max > 0
+  int thr_pos;                  // rho_thr > 0
 };
 
 // One meshblock as seen by the kernels: caller arrays plus context scratch.
@@ -181,6 +182,11 @@ __device__ __forceinline__ bool gt0(double x) {
 }
 __device__ __forceinline__ bool eq0(double x) { return (__double_as_longlong(x) << 1) == 0; }
 __device__ __forceinline__ bool gt_nn(double x, double y) { return __double_as_longlong(x) > __double_as_longlong(y); }
+// x < rho_thr for a finite x: with rho_thr > 0 the bit order decides exactly
+// (-0 included); with rho_thr = 0 it is the sign test
+__device__ __forceinline__ bool below_thr(const Par& P, double x) {
+  return P.thr_pos ? gt_nn(P.rho_thr, x) : lt0(x);
+}
 // finite (not inf, not NaN): the exponent field is not all ones
 __device__ __forceinline__ bool finite_bits(double x) { return (__double2hiint(x) & 0x7FF00000) != 0x7FF00000; }
 
@@ -451,7 +457,7 @@ __device__ __forceinline__ double f_zero(const KS& s, const Par& P) {
 __device__ __forceinline__ double mu_plus(const KS& s) {
   const double rpar2 = gt0(s.b2) ? s.rb2 / s.b2 : s.r2;
   double mu = rsqrt(1.0 + rpar2);
-  if (s.r2 - rpar2 > 1e-3 * (1.0 + rpar2)) {
+  if (gt_nn(s.r2 - rpar2, 1e-3 * (1.0 + rpar2))) {
 #pragma unroll
     for (int it = 0; it < 3; it++) {
       // 1/sqrt(1 + rbar^2) = d / sqrt(d^2 + N) with d, N as in kev_g
@@ -545,7 +551,7 @@ __device__ __forceinline__ bool krp_prep(const Par& P, const double* U, const do
     return false;
   }
   // inside the excision region (Sec. 4.7) every cell takes the D-floor reset
-  if (D < P.rho_thr || (P.exc_on && alpha < P.alpha_exc)) {
+  if (below_thr(P, D) || (P.exc_on && alpha < P.alpha_exc)) {
     D = P.rho_atm;
     Sl[0] = Sl[1] = Sl[2] = 0.0;
     tau = fma(D, P.eps_atm_rho, 0.5 * B2);
@@ -648,7 +654,7 @@ __device__ __forceinline__ void krp_finish(const Par& P, const KrpCell& k, doubl
     w0 = f * fma(mrb, k.bu[0], k.ru[0]);
     w1 = f * fma(mrb, k.bu[1], k.ru[1]);
     w2 = f * fma(mrb, k.bu[2], k.ru[2]);
-    if (rho < P.rho_thr) {
+    if (below_thr(P, rho)) {
       rho = P.rho_atm; p = P.P_atm; w0 = w1 = w2 = 0.0;
       flags |= F_RHO;
     } else {
@@ -943,7 +949,7 @@ __device__ __forceinline__ void wz_finish(const double* x, const double* n_hi, c
 // (P_c, eps_c, G_i) at the floored density in cold[3] for face_side.
 template <int E = 0>
 __device__ __forceinline__ void face_floor(const Par& P, double* s, double* cold = nullptr) {
-  if (s[0] < P.rho_thr) {
+  if (below_thr(P, s[0])) {
     s[0] = P.rho_atm; s[1] = s[2] = s[3] = 0.0; s[4] = P.P_atm;
     if (E) { cold[0] = P.Pc_atm; cold[1] = P.epsc_atm; cold[2] = P.G_atm; }
   } else if (E) {
