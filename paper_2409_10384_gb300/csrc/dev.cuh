@@ -75,6 +75,7 @@ enum WorkKind { W_C2P = 0, W_FX, W_FY, W_FZ, W_CELL, W_EDGE, W_FACE, W_INIT, W_S
 // unless the block list is too small to give every SM two waves of sweeps at
 // that length; then it halves (down to 1) until it does (flux_seg_len).
 constexpr int FLUX_SEG = 16;
+constexpr int FLUX_SEG_X = 8;
 // segments per line for an interior of n cells (n + 1 faces)
 __host__ __device__ inline int flux_nseg(int n, int L) { return (n + L) / L; }
 __host__ __device__ inline long long flux_seg_items(const int* n, int d, int L) {
@@ -87,7 +88,7 @@ __host__ __device__ inline long long flux_seg_items(const int* n, int d, int L) 
 // least 2 nsm 256 segments, else 1.
 inline int flux_seg_len(const int (*n)[3], int nb, int d, int nsm) {
   const long long target = 2LL * nsm * 256;
-  int L = FLUX_SEG;
+  int L = d == 0 ? FLUX_SEG_X : FLUX_SEG;
   while (L > 1) {
     long long segs = 0;
     for (int b = 0; b < nb; b++) segs += flux_seg_items(n[b], d, L);
