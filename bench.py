@@ -46,10 +46,13 @@ C2P_GUESS = 0
 FLOPS_PER_UNIT = {"flux": 1576.0, "c2p": 450.0, "fofc_flag": 450.0, "fofc_fix": 595.0, "update": 443.5,
                   "emf": 36.1}
 FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (dense), the profiling recipe's unit table
-# DRAM bytes (read + write) per unit of the kernels captured with ncu on the
-# 96^3 case of this workload (profiles/ncu_full_star96_flux.md,
-# profiles/ncu_full_star96_update.md); scaled to a launch by its units.
-TRAFFIC_PER_UNIT = {"flux_x": 1173.0, "flux_y": 243.5, "flux_z": 239.5, "update": 463.7}
+# DRAM bytes (read + write) per unit from ncu: the flux sweeps captured on the
+# 128^3 workload itself (one-pass metrics, profiles/ncu_full_star104_flux.md),
+# the update on the 96^3 case (profiles/ncu_full_star96_update.md), scaled to
+# a launch by its units.  The flux figures hold only at 128^3: the segment
+# lengths, and with them the x sweep's re-reads, depend on the size.
+TRAFFIC_PER_UNIT = {"flux_x": 309.4, "flux_y": 244.6, "flux_z": 242.8, "update": 585.0}
+TRAFFIC_SIZES = {"flux_x": (128,), "flux_y": (128,), "flux_z": (128,), "update": (96, 128)}
 # Algorithmic HBM bytes per zone and RK stage of one fused pass: read U (5),
 # U^n (5), face B~ (3), face B~^n (3) and the ADM variables with K_ij (16),
 # write U (5) and face B~ (3) = 40 doubles; the first stage reads neither U^n
@@ -558,12 +561,12 @@ def run_ours(args):
     key = "flux" if dom.startswith("flux") else dom
     flops = FLOPS_PER_UNIT.get(key, 0.0) * units.get(dom, 0)
     achieved = flops / (dom_ms / dom_n * 1e-3) / 1e12
-    traffic = TRAFFIC_PER_UNIT[dom] * units[dom] if dom in TRAFFIC_PER_UNIT and n in (96, 128) else None
+    traffic = TRAFFIC_PER_UNIT[dom] * units[dom] if n in TRAFFIC_SIZES.get(dom, ()) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": dom,
                 "peak_source": "nominal FP64 1.25 TFLOP/s (recipe unit table); FP64 is not in MEASURED_PEAKS.json",
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per unit on the 96^3 case, "
-                                  "scaled by units"}
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per unit (flux: the 128^3 "
+                                  "workload, one pass; update: the 96^3 case), scaled by units"}
     hbm_peak = _measured_hbm()
     hbm = {"algorithmic_bytes_per_zone_cycle": HBM_BYTES_PER_ZONE_CYCLE,
            "achieved_gbs": value * HBM_BYTES_PER_ZONE_CYCLE / 1e9, "peak_gbs": hbm_peak,

@@ -72,8 +72,10 @@ enum WorkKind { W_C2P = 0, W_FX, W_FY, W_FZ, W_CELL, W_EDGE, W_FACE, W_INIT, W_S
 // Flux sweeps: the n_d + 1 faces of direction d on one transverse line (one
 // extra line on each side, for the CT stencil) are split into near-equal
 // segments of at most L faces; one thread sweeps one segment.  L is FLUX_SEG
-// unless the block list is too small to give every SM two waves of sweeps at
-// that length; then it halves (down to 1) until it does (flux_seg_len).
+// (FLUX_SEG_X along x) unless the block list is too small to give every SM
+// two waves of sweeps at that length; then it halves (down to 1) until it
+// does (flux_seg_len).  The x sweep's lanes read neighbouring segments of one
+// line; at 16 faces the lines they hold exceed L2 and it re-reads them.
 constexpr int FLUX_SEG = 16;
 constexpr int FLUX_SEG_X = 8;
 // segments per line for an interior of n cells (n + 1 faces)
@@ -84,8 +86,8 @@ __host__ __device__ inline long long flux_seg_items(const int* n, int d, int L) 
   return t;
 }
 // Segment length of direction d for a list of nb blocks with interiors n[b][3]
-// on a GPU of nsm SMs: the largest L <= FLUX_SEG (a power of two) with at
-// least 2 nsm 256 segments, else 1.
+// on a GPU of nsm SMs: the largest L <= FLUX_SEG (FLUX_SEG_X for d = 0)
+// reached by halving, with at least 2 nsm 256 segments, else 1.
 inline int flux_seg_len(const int (*n)[3], int nb, int d, int nsm) {
   const long long target = 2LL * nsm * 256;
   int L = d == 0 ? FLUX_SEG_X : FLUX_SEG;
