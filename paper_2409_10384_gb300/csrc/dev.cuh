@@ -883,8 +883,12 @@ __device__ __forceinline__ void wz_parts(RecVar& s, double xn, double& x, double
   const double A1 = (e1 + tau) * (e0 * e2);
   const double A2 = (e2 + tau) * (e0 * e1);
   const double a1 = 6.0 * A1, a2h = 3.0 * A2, a0l = 3.0 * A0;
-  d_hi = A0 + a1 + a2h;
-  d_lo = a0l + a1 + A2;
+  // Explicit FMAs: left to the compiler, these sums would be contracted by
+  // the use count of each product, which differs where the caller drops the
+  // lower face value (the first cell of a sweep).  A face would then depend
+  // in its last bit on where its segment starts.
+  d_hi = fma(6.0, A1, fma(3.0, A2, A0));
+  d_lo = fma(6.0, A1, fma(3.0, A0, A2));
   const double da = s.d0, db = s.d1, dc = s.d2, dd = dn;
   n_hi = fma(A0, fma(5.0, db, -2.0 * da), fma(a1, fma(2.0, dc, db), a2h * fma(4.0, dc, -dd)));
   n_lo = fma(A2, fma(-5.0, dc, 2.0 * dd), fma(-a1, fma(2.0, db, dc), a0l * fma(-4.0, db, da)));

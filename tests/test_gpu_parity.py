@@ -346,6 +346,39 @@ def test_per_block_launches_and_autotune_reproduce_batched(G):
             assert torch.equal(a.bf[d], b.bf[d]) and torch.equal(a.bf[d], c.bf[d])
 
 
+def test_segment_length_leaves_every_face_unchanged(G):
+    """A face's flux does not depend on how its line is cut into sweep
+    segments.  Two ragged blocks stepped on their own get one-face segments
+    (too few sweeps for longer ones).  In one list with a 104^3 block they get
+    the 128^3 bench block's lengths: at most 8 faces along x, as equal
+    segments plus a remainder per line (16 + 6 and 24 + 7 faces here), and at
+    most 16 along y and z.  Every cell and face must agree bit for bit."""
+    import torch
+    p = O.params(gamma=2.0, rho_atm=1e-12, T_atm=1e-10, recon=2, rsolver=1, rk_order=3, fofc=1)
+    st = synth.spacetime(2)
+    specs = [((21, 13, 10), 0.75, (-6.0, -4.0, -3.0)), ((30, 9, 17), 0.375, (1.0, -2.0, 0.5))]
+    obs = []
+    for n, dx, x0 in specs:
+        inp = synth.star_block(st, n, 4, (dx,) * 3, x0)
+        obs.append(O.init_block(p, inp.n, inp.ng, inp.dx, inp.adm, inp.prim, inp.A))
+    dt = 0.25 * 0.375
+    alone = [U.to_device(G, ob) for ob in obs]
+    listed = [U.to_device(G, ob) for ob in obs]
+    ctx = _ctx(G, p)
+    big_in = synth.star_uniform(seed=2, n=104, ng=4)
+    big = G.DeviceBlock(big_in.n, big_in.ng, big_in.dx, big_in.adm)
+    big.prim.copy_(torch.from_numpy(big_in.prim))
+    ctx.init_block(big, [torch.from_numpy(a).cuda() for a in big_in.A])
+    ctx.step(alone, dt)
+    ctx.step([big] + listed, dt)
+    torch.cuda.synchronize()
+    for a, b in zip(alone, listed):
+        assert torch.equal(a.cons, b.cons) and torch.equal(a.prim, b.prim)
+        assert torch.equal(a.flags, b.flags)
+        for d in range(3):
+            assert torch.equal(a.bf[d], b.bf[d]), d
+
+
 def test_degenerate_and_ragged_block_shapes(G):
     """Blocks one cell thick along one or more directions, and non-cubic
     blocks, in one batched stage (RK3 substeps 0 and 1), each against the
