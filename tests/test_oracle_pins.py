@@ -889,3 +889,67 @@ def test_hybrid_cold_matter_takes_the_temperature_floor():
         rr = r["prim"][0, 0]
         assert abs(r["prim"][4, 0] - (O.eos(p, rr, 1.0)["Pc"] + rr * p.T_atm)) <= 1e-13 * r["prim"][4, 0]
         assert abs(r["prim"][0, 0] / rho - 1.0) < 1e-8 and abs(r["prim"][1, 0] - 0.2) < 1e-8
+
+
+def _cold_pressure(rho):
+    """P_c of HYB from its definition alone: K_0 rho^G_0 below the first
+    dividing density, and each next K_i fixed by the continuity of P_c."""
+    K, G, rb = [1e-4], HYB["eos_gamma"][:3], HYB["eos_rho"][:2]
+    for i in range(2):
+        K.append(K[i] * rb[i] ** (G[i] - G[i + 1]))
+    i = 0 if rho < rb[0] else (1 if rho < rb[1] else 2)
+    return K[i] * rho ** G[i]
+
+
+def test_hybrid_face_and_atmosphere_floors_are_the_cold_curve_plus_T_atm():
+    """Sec. 3.3 floors with the hybrid EOS: a reconstructed face state below
+    the temperature floor gives the flux of the same state at
+    P = P_c(rho) + rho T_atm (cold curve from its definition), and the density
+    floor's atmosphere carries P_c(rho_atm) + rho_atm T_atm."""
+    p = O.params(gamma=2.0, rho_atm=1e-12, T_atm=1e-6, f_thr=1.0, **HYB)
+    m10 = np.array([0.9, 0.05, -0.02, 0.01, 1.1, 0.03, 0.0, 0.95, -0.02, 1.05])
+    for rho in (3e-9, 2e-6, 1e-2):
+        Pf = _cold_pressure(rho) + rho * p.T_atm
+        L = np.array([rho, 0.1, -0.05, 0.02, 0.5 * _cold_pressure(rho), 1e-3 * np.sqrt(rho), -2e-3 * np.sqrt(rho)])
+        Lf = L.copy()
+        Lf[4] = Pf
+        R = np.array([1.2 * rho, 0.05, 0.02, -0.01, _cold_pressure(1.2 * rho) + 1.2 * rho * 1e-2,
+                      2e-3 * np.sqrt(rho), 1e-3 * np.sqrt(rho)])
+        Bn = 1e-3 * np.sqrt(rho)
+        F, Ff = O.face_flux(p, 0, L, R, Bn, m10), O.face_flux(p, 0, Lf, R, Bn, m10)
+        assert np.all(np.abs(F - Ff) <= 1e-12 * np.abs(Ff).max()), rho
+    g = np.array([[1.0], [0], [0], [1.0], [0], [1.0]])
+    r = O.c2p_cells(p, np.array([[1e-14], [0.0], [0.0], [0.0], [1e-30]]), np.zeros((3, 1)), g)
+    assert r["flags"][0] & O.F_DFLOOR
+    Pa = _cold_pressure(p.rho_atm) + p.rho_atm * p.T_atm
+    assert abs(r["prim"][4, 0] - Pa) <= 1e-12 * Pa
+
+
+@pytest.mark.parametrize("hybrid", [False, True])
+def test_clamped_con2prim_keeps_D_and_S(hybrid):
+    """Kastaun et al.'s solve with eps clamped at its minimum: the root is
+    taken with the clamped eps (P = P_c + rho T_atm), so the recovered state
+    still reproduces D~ and S~_i (only tau~ gains the floor's energy).  Cold
+    matter (T = 0 or T below T_atm = 1e-3) on a curved metric, with a field."""
+    kw = HYB if hybrid else {}
+    p = O.params(gamma=2.0, rho_atm=1e-20, T_atm=1e-3, f_thr=0.0, **kw)
+    Pc = _cold_pressure if hybrid else (lambda r: 0.0)
+    rng = np.random.default_rng(21)
+    rhos = np.array([3e-9, 5e-6, 2e-3, 0.05, 0.3])
+    n = 2 * rhos.size
+    rho = np.concatenate([rhos, rhos])
+    T = np.concatenate([np.zeros(rhos.size), 0.2 * p.T_atm * np.ones(rhos.size)])
+    w = rng.normal(size=(3, n)) * 0.5
+    prim = np.vstack([rho, w, np.array([Pc(r) for r in rho]) + rho * T])
+    Bd = rng.normal(size=(3, n)) * 0.3 * np.sqrt(rho)
+    g = np.tile(np.array([[1.1], [0.05], [0.0], [0.95], [0.02], [1.2]]), (1, n))
+    cons = O.prim2cons(p, prim, Bd, g)
+    r = O.c2p_cells(p, cons, Bd, g)
+    assert np.all(r["flags"] & O.F_TEMP) and not np.any(r["flags"] & O.F_FAIL)
+    back = O.prim2cons(p, r["prim"], Bd, g)
+    assert np.all(np.abs(back[0] - cons[0]) <= 1e-12 * cons[0])
+    S = np.abs(cons[1:4]).max(0)
+    assert np.all(np.abs(back[1:4] - cons[1:4]) <= 1e-12 * S)
+    rr = r["prim"][0]
+    Pf = np.array([Pc(x) for x in rr]) + rr * p.T_atm
+    assert np.all(np.abs(r["prim"][4] - Pf) <= 1e-12 * Pf)
