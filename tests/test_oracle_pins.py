@@ -132,6 +132,23 @@ def test_hlle_is_upwind_for_supersonic_flow():
     assert np.max(np.abs(F - FL)) <= 1e-14 * np.abs(FL).max()
 
 
+def test_llf_equals_hlle_on_mirror_states():
+    """LLF is the two-wave flux with both speeds at +-a, a the largest |lambda|
+    of the two sides.  States mirrored across the face (v^x -> -v^x, B^n = 0,
+    no shift, gamma_xy = gamma_xz = 0) make HLLE's bounds exactly -a and +a,
+    so the two solvers must agree."""
+    m10 = np.array([0.8, 0.0, 0.0, 0.0, 1.1, 0.0, 0.0, 0.9, 0.05, 1.2])
+    for rho, P, wx, bt in ((1.0, 0.7, 0.5, 0.3), (1e-3, 2e-5, 1.5, 0.02), (0.2, 0.5, 0.05, 0.0)):
+        L = np.array([rho, wx, 0.1, -0.05, P, bt, -0.5 * bt])
+        R = L.copy()
+        R[1] = -wx
+        F = {}
+        for rs in (0, 1):
+            p = O.params(gamma=2.0, rsolver=rs)
+            F[rs] = O.face_flux(p, 0, L, R, 0.0, m10)
+        assert np.all(np.abs(F[0] - F[1]) <= 1e-13 * np.abs(F[1]).max()), (F[0], F[1])
+
+
 # ----------------------------------------------------------------- Sec. 3.2
 
 @pytest.mark.parametrize("recon", [0, 1, 2, 3, 4])
@@ -258,6 +275,31 @@ def test_ppm_convergence_through_smooth_extrema():
     assert np.all(rate[4][1:] > 2.9), rate
     assert np.all(rate[3] < 2.2), rate
     assert err[4][-1] < 0.05 * err[3][-1]
+
+
+def test_wenoz_symmetric_stencil_takes_the_linear_weights():
+    """On a stencil symmetric about its centre, (a, b, c, b, a), the end
+    indicators beta_0 and beta_2 coincide, so WENO-Z's tau_5 = |beta_0 - beta_2|
+    vanishes and the weights are the linear ones whatever the kink at c: the
+    face value is the fifth-order (-a + 14 b + 47 c)/60 (Borges et al. 2008)."""
+    for a, b, c in ((0.0, 1.0, 5.0), (2.0, -1.0, 0.5), (1e-3, 3e-3, -2e-3)):
+        q = np.array([0.0, 0.0, a, b, c, b, a, 0.0, 0.0])
+        L, R = O.recon_line(2, q)
+        ex = (-a + 14.0 * b + 47.0 * c) / 60.0
+        assert abs(L[5] - ex) <= 1e-15 * max(abs(a), abs(b), abs(c))
+        assert abs(R[4] - ex) <= 1e-15 * max(abs(a), abs(b), abs(c))
+
+
+def test_ppmx_limited_interface_hand_value():
+    """Colella & Sekora (2008): the fourth-order interface value between 0 and 1
+    of the data (-10, 0, 1, 1.01) overshoots (7/12 + 8.99/12 = 1.3325 > 1), so it
+    is replaced by (0 + 1)/2 - D_lim/6 with D = 3 (0 - 2 f + 1) limited against
+    C = 1.25 times the neighbouring second differences (-9 and -0.99, all of
+    one sign): D_lim = max(-4.995, -11.25, -1.2375).  The cell below the face
+    keeps that value on monotone data."""
+    q = np.array([-40.0, -30.0, -20.0, -10.0, 0.0, 1.0, 1.01, 1.02, 1.03, 1.04])
+    L, R = O.recon_line(4, q)
+    assert abs(L[5] - (0.5 + 1.2375 / 6.0)) < 1e-15
 
 
 def test_excision_floor_alpha_below_threshold():
@@ -403,6 +445,36 @@ def test_c2p_floors_and_failures():
     assert r["flags"][0] & O.F_TEMP
     assert abs(r["prim"][4, 0] - r["prim"][0, 0] * p.T_atm) <= 1e-14 * r["prim"][4, 0]
     assert abs(r["prim"][1, 0] - 0.3) < 1e-6
+
+
+def test_c2p_floors_with_a_field_closed_forms():
+    """Sec. 3.3 floors in flat space (D~ = D, B^2 = sum B~_i^2) with a field
+    that matters: the magnetisation cap sets D = B^2/sigma_max; the tau floor
+    sets tau = D T_atm/(Gamma - 1) + B^2/2 (also for a tau above the first
+    term alone); the density floor resets to
+    rho_atm at rest with tau = rho_atm T_atm/(Gamma - 1) + B^2/2, which needs
+    no further tau floor."""
+    gam, T = 2.0, 1e-8
+    g = np.array([[1.0], [0], [0], [1.0], [0], [1.0]])
+    p = O.params(gamma=gam, rho_atm=1e-12, T_atm=T, f_thr=1.0, sigma_max=50.0)
+    Bd = np.array([[0.5], [0.0], [0.0]])
+    r = O.c2p_cells(p, np.array([[1e-3], [0.0], [0.0], [0.0], [1.0]]), Bd, g)
+    assert r["flags"][0] & O.F_SIGMA and not r["flags"][0] & O.F_FAIL
+    assert abs(r["cons"][0, 0] - 0.25 / 50.0) <= 1e-15 * 0.005
+    assert abs(r["prim"][0, 0] - 0.005) <= 1e-12 * 0.005
+    p = O.params(gamma=gam, rho_atm=1e-12, T_atm=T, f_thr=1.0)
+    Bd = np.array([[0.0], [0.1], [0.0]])
+    # tau = 1e-4 lies above D T_atm/(Gamma - 1) but below it + B^2/2
+    r = O.c2p_cells(p, np.array([[1e-3], [0.0], [0.0], [0.0], [1e-4]]), Bd, g)
+    tau = 1e-3 * T / (gam - 1.0) + 0.5 * 0.01
+    assert r["flags"][0] & O.F_TAU
+    assert abs(r["cons"][4, 0] - tau) <= 1e-15 * tau
+    assert abs(r["prim"][4, 0] / r["prim"][0, 0] - T) <= 1e-6 * T
+    r = O.c2p_cells(p, np.array([[1e-14], [1e-15], [0.0], [0.0], [1e-20]]), Bd, g)
+    tau = 1e-12 * T / (gam - 1.0) + 0.5 * 0.01
+    assert r["flags"][0] & O.F_DFLOOR and not r["flags"][0] & (O.F_TAU | O.F_FAIL)
+    assert abs(r["cons"][4, 0] - tau) <= 1e-15 * tau and r["cons"][0, 0] == 1e-12
+    assert np.all(r["prim"][1:4, 0] == 0.0)
 
 
 # ------------------------------------------------------------- stage level
