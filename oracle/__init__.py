@@ -22,8 +22,10 @@ from dataclasses import dataclass, field
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "grmhd_oracle.cpp")
-_BUILD = os.path.join(_HERE, "_build")
+# ORACLE_SRC / ORACLE_BUILD point the loader at another copy of the source and
+# its build folder (tests/mutation_sweep.py builds mutated copies there).
+_SRC = os.environ.get("ORACLE_SRC") or os.path.join(_HERE, "grmhd_oracle.cpp")
+_BUILD = os.environ.get("ORACLE_BUILD") or os.path.join(_HERE, "_build")
 _LOCK = threading.Lock()
 _LIBS: dict = {}
 
