@@ -70,8 +70,9 @@ enum WorkKind { W_C2P = 0, W_FX, W_FY, W_FZ, W_CELL, W_EDGE, W_FACE, W_INIT, W_S
                 W_NKIND };
 
 // Flux sweeps: the n_d + 1 faces of direction d on one transverse line (one
-// extra line on each side, for the CT stencil) are split into near-equal
-// segments of at most L faces; one thread sweeps one segment.  L is FLUX_SEG
+// extra line on each side, for the CT stencil) are split into ns = ceil((n_d +
+// 1)/L) segments of at most L faces (near-equal along y and z; along x equal
+// plus one remainder, see seg_coords); one thread sweeps one segment.  L is FLUX_SEG
 // (FLUX_SEG_X along x) unless the block list is too small to give every SM
 // two waves of sweeps at that length; then it halves (down to 1) until it
 // does (flux_seg_len).  The x sweep's lanes read neighbouring segments of one
