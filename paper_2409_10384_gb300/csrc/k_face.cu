@@ -38,42 +38,6 @@ __device__ __forceinline__ void face_flux_donor(const DevBlock& b, const Par& P,
   else face_flux_states<d, 1>(P, L, R, Bn, fm, F);
 }
 
-// Segment of the transverse line of item `loc`: (k,j,i) is the cell on the
-// upper side of the segment's first face, nf its number of faces.
-// y and z: the lanes of a warp take neighbouring lines (x fastest) at the same
-// segment index, so they sweep equal lengths; the segments are near-equal.
-// x: the lanes take neighbouring segments of a line, so every line gets ns - 1
-// segments of Lx = ceil(nd / ns) faces (items [0, (ns - 1) lines)) and one
-// remainder of nd - (ns - 1) Lx >= 1 faces (the items after them); a warp
-// then never mixes lengths, except where the two ranges meet.
-template <int d>
-__device__ __forceinline__ void seg_coords(const DevBlock& b, int loc, int& k, int& j, int& i, int& nf) {
-  const int ns = b.nseg[d], nd = b.n[d] + 1;
-  int a0, a1, f0;
-  if (d == 0) {
-    const int lines = (b.n[1] + 2) * (b.n[2] + 2), full = ns - 1, Lx = (nd + ns - 1) / ns;
-    int r;
-    if (loc < full * lines) {
-      const int s = loc % full;
-      r = loc / full; f0 = s * Lx; nf = Lx;
-    } else {
-      r = loc - full * lines; f0 = full * Lx; nf = nd - f0;
-    }
-    a0 = r % (b.n[1] + 2); a1 = r / (b.n[1] + 2);
-  } else {
-    int s;
-    a0 = loc % (b.n[0] + 2); int r = loc / (b.n[0] + 2);
-    if (d == 1) { a1 = r % (b.n[2] + 2); s = r / (b.n[2] + 2); }
-    else { a1 = r % (b.n[1] + 2); s = r / (b.n[1] + 2); }
-    f0 = (int)((long long)s * nd / ns);
-    nf = (int)((long long)(s + 1) * nd / ns) - f0;
-  }
-  const int g = b.ng;
-  if (d == 0) { i = g + f0; j = g - 1 + a0; k = g - 1 + a1; }
-  else if (d == 1) { j = g + f0; i = g - 1 + a0; k = g - 1 + a1; }
-  else { k = g + f0; i = g - 1 + a0; j = g - 1 + a1; }
-}
-
 // Fluxes of direction d, one thread per segment: the thread sweeps the cells
 // along d, reconstructing each once (order R) and finishing one face per cell.
 template <int d, int R, int E>
