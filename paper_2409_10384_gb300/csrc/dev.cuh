@@ -175,15 +175,15 @@ struct Work {
 };
 
 // ---------------------------------------------------------------- indexing
-__device__ __forceinline__ long long cidx(const DevBlock& b, int k, int j, int i) {
+__host__ __device__ __forceinline__ long long cidx(const DevBlock& b, int k, int j, int i) {
   return ((long long)k * b.N[1] + j) * b.N[0] + i;
 }
-__device__ __forceinline__ long long fidx(const DevBlock& b, int d, int k, int j, int i) {
+__host__ __device__ __forceinline__ long long fidx(const DevBlock& b, int d, int k, int j, int i) {
   if (d == 0) return ((long long)k * b.N[1] + j) * (b.N[0] + 1) + i;
   if (d == 1) return ((long long)k * (b.N[1] + 1) + j) * b.N[0] + i;
   return ((long long)k * b.N[1] + j) * b.N[0] + i;
 }
-__device__ __forceinline__ long long nface(const DevBlock& b, int d) {
+__host__ __device__ __forceinline__ long long nface(const DevBlock& b, int d) {
   if (d == 0) return (long long)b.N[2] * b.N[1] * (b.N[0] + 1);
   if (d == 1) return (long long)b.N[2] * (b.N[1] + 1) * b.N[0];
   return (long long)(b.N[2] + 1) * b.N[1] * b.N[0];
@@ -195,7 +195,7 @@ __device__ __forceinline__ long long eidx(const DevBlock& b, int c, int k, int j
 }
 
 // block owning global item `it` of kind K (binary search of the prefix sums)
-__device__ __forceinline__ int find_block(const Work& w, int K, long long it) {
+__host__ __device__ __forceinline__ int find_block(const Work& w, int K, long long it) {
   const long long* p = w.pre + (long long)K * (w.nblocks + 1);
   int lo = 0, hi = w.nblocks;  // p[lo] <= it < p[hi]
   while (hi - lo > 1) {
@@ -212,23 +212,40 @@ __device__ __forceinline__ int find_block(const Work& w, int K, long long it) {
 //    +0 and -0 equal to 0);
 //  gt_nn(x, y): x > y for operands that are not NaN, at least one of them
 //    >= +0, and not the pair (+0, -0) - the signed order of the bit patterns.
-__device__ __forceinline__ bool lt0(double x) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+// They are host functions too, so that tests/index_check.cu can compare them
+// with the IEEE comparisons on the CPU; only the bit reinterpretation differs.
+__host__ __device__ __forceinline__ long long dbits(double x) {
+#ifdef __CUDA_ARCH__
+  return __double_as_longlong(x);
+#else
+  long long u;
+  __builtin_memcpy(&u, &x, sizeof u);
+  return u;
+#endif
+}
+__host__ __device__ __forceinline__ bool lt0(double x) {
+  const unsigned long long u = (unsigned long long)dbits(x);
   return (u >> 63) && ((u & 0x7FFFFFFFFFFFFFFFull) - 1ull < 0x7FF0000000000000ull);
 }
-__device__ __forceinline__ bool gt0(double x) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+__host__ __device__ __forceinline__ bool gt0(double x) {
+  const unsigned long long u = (unsigned long long)dbits(x);
   return !(u >> 63) && (u - 1ull < 0x7FF0000000000000ull);
 }
-__device__ __forceinline__ bool eq0(double x) { return (__double_as_longlong(x) << 1) == 0; }
-__device__ __forceinline__ bool gt_nn(double x, double y) { return __double_as_longlong(x) > __double_as_longlong(y); }
+__host__ __device__ __forceinline__ bool eq0(double x) { return (dbits(x) << 1) == 0; }
+__host__ __device__ __forceinline__ bool gt_nn(double x, double y) { return dbits(x) > dbits(y); }
 // x < rho_thr for a finite x: with rho_thr > 0 the bit order decides exactly
 // (-0 included); with rho_thr = 0 it is the sign test
-__device__ __forceinline__ bool below_thr(const Par& P, double x) {
+__host__ __device__ __forceinline__ bool below_thr(const Par& P, double x) {
   return P.thr_pos ? gt_nn(P.rho_thr, x) : lt0(x);
 }
 // finite (not inf, not NaN): the exponent field is not all ones
-__device__ __forceinline__ bool finite_bits(double x) { return (__double2hiint(x) & 0x7FF00000) != 0x7FF00000; }
+__host__ __device__ __forceinline__ bool finite_bits(double x) {
+#ifdef __CUDA_ARCH__
+  return (__double2hiint(x) & 0x7FF00000) != 0x7FF00000;
+#else
+  return ((int)(dbits(x) >> 32) & 0x7FF00000) != 0x7FF00000;
+#endif
+}
 
 struct Metric {
   double g[6], gi[6], sdet, isdet;

@@ -1,11 +1,24 @@
-// Host check of the flux kernels' segment mapping (seg_coords, flux_nseg,
-// flux_seg_items in dev.cuh), compiled by tests/test_seg_coverage.py and run
-// on the CPU.  For every direction, segment length and block shape below,
-// the items of one launch must cover each face of each transverse line
-// exactly once (lines: the interior plus one on each side; faces: n_d + 1),
-// with 1 <= nf <= L, and along x every item before the remainders sweeps the
-// same number of faces.  Prints "ok" and exits 0, else the first failure.
+// Host check of the kernels' index logic in dev.cuh, compiled by
+// tests/test_index_logic.py and run on the CPU.
+//  - Flux segments (seg_coords, flux_nseg, flux_seg_items): for every
+//    direction, segment length and block shape below, the items of one launch
+//    cover each face of each transverse line exactly once (lines: the
+//    interior plus one on each side; faces: n_d + 1), with 1 <= nf <= L;
+//    along x every item before the remainders sweeps the same number of
+//    faces.  The cells a sweep reads (the five-cell stencils of the cells
+//    next to its faces, as k_flux does) lie inside the ghosted block, and its
+//    faces (fidx) inside the face array (nface).
+//  - find_block: on prefix sums with empty blocks, item it belongs to the
+//    block b returned, p[b] <= it < p[b + 1].
+//  - The integer-pipe compares (lt0, gt0, eq0, gt_nn, below_thr,
+//    finite_bits) against the IEEE comparisons they replace, on special
+//    values (+-0, subnormals, +-inf, NaNs of both signs) and random bit
+//    patterns, within each one's stated domain.
+// Prints "ok" and exits 0, else the first failure.
+#include <cmath>
 #include <cstdio>
+#include <cstring>
+#include <limits>
 #include <vector>
 
 #include "dev.cuh"
@@ -34,6 +47,26 @@ static bool check(const int n[3], int L) {
                   a1, a2);
       return false;
     }
+    // k_flux reconstructs the cells next to its faces, c .. c + nf st along d
+    // from the cell c below the first face, each from a five-cell stencil:
+    // it reads c - 2 st .. c + (nf + 2) st (the face metric's four-point
+    // stencils lie inside), and writes faces f .. f + (nf - 1) fst
+    const int N[3] = {n[0] + 2 * b.ng, n[1] + 2 * b.ng, n[2] + 2 * b.ng};
+    b.N[0] = N[0]; b.N[1] = N[1]; b.N[2] = N[2];
+    const int cc[3] = {i, j, k};
+    const int cd = cc[d] - 1;
+    if (cd - 2 < 0 || cd + nf + 2 >= N[d] || cc[t1] < 0 || cc[t1] >= N[t1] || cc[t2] < 0 || cc[t2] >= N[t2]) {
+      std::printf("d=%d n=%d,%d,%d L=%d loc=%lld: cells %d..%d of %d\n", d, n[0], n[1], n[2], L, loc, cd - 2,
+                  cd + nf + 2, N[d]);
+      return false;
+    }
+    const long long fl = grmhd::fidx(b, d, k, j, i);
+    const long long fst = d == 0 ? 1 : (d == 1 ? (long long)N[0] : (long long)N[0] * N[1]);
+    if (fl < 0 || fl + (nf - 1) * fst >= grmhd::nface(b, d)) {
+      std::printf("d=%d n=%d,%d,%d L=%d loc=%lld: faces %lld..%lld of %lld\n", d, n[0], n[1], n[2], L, loc, fl,
+                  fl + (nf - 1) * fst, grmhd::nface(b, d));
+      return false;
+    }
     if (d == 0 && loc < full_items) {
       if (first_nf < 0) first_nf = nf;
       if (nf != first_nf) {
@@ -51,7 +84,96 @@ static bool check(const int n[3], int L) {
   return true;
 }
 
+static bool check_find_block() {
+  unsigned long long x = 12345;
+  for (int trial = 0; trial < 200; trial++) {
+    const int nb = 1 + trial % 37;
+    std::vector<long long> pre((size_t)3 * (nb + 1), 0);
+    for (int K = 0; K < 3; K++)
+      for (int b = 0; b < nb; b++) {
+        x = x * 6364136223846793005ull + 1442695040888963407ull;
+        const long long sz = (x >> 33) % 4 == 0 ? 0 : (long long)((x >> 40) % 50);
+        pre[(size_t)K * (nb + 1) + b + 1] = pre[(size_t)K * (nb + 1) + b] + sz;
+      }
+    grmhd::Work w{nullptr, pre.data(), nb};
+    for (int K = 0; K < 3; K++) {
+      const long long* p = pre.data() + (size_t)K * (nb + 1);
+      for (long long it = 0; it < p[nb]; it++) {
+        const int b = grmhd::find_block(w, K, it);
+        if (b < 0 || b >= nb || !(p[b] <= it && it < p[b + 1])) {
+          std::printf("find_block: trial %d K %d item %lld -> block %d\n", trial, K, it, b);
+          return false;
+        }
+      }
+    }
+  }
+  return true;
+}
+
+static double from_bits(unsigned long long u) {
+  double x;
+  std::memcpy(&x, &u, sizeof x);
+  return x;
+}
+
+static bool check_compares() {
+  std::vector<double> v = {0.0, -0.0, 1.0, -1.0, 0.5, -2.5, 1e-300, -1e-300,
+                           std::numeric_limits<double>::denorm_min(), -std::numeric_limits<double>::denorm_min(),
+                           from_bits(0x000FFFFFFFFFFFFFull), from_bits(0x800FFFFFFFFFFFFFull),
+                           std::numeric_limits<double>::min(), -std::numeric_limits<double>::min(),
+                           std::numeric_limits<double>::max(), -std::numeric_limits<double>::max(),
+                           std::numeric_limits<double>::infinity(), -std::numeric_limits<double>::infinity(),
+                           from_bits(0x7FF8000000000000ull), from_bits(0xFFF8000000000000ull),
+                           from_bits(0x7FF0000000000001ull), from_bits(0xFFFFFFFFFFFFFFFFull), 1e-12, 1e-10};
+  unsigned long long x = 987654321;
+  for (int r = 0; r < 20000; r++) {
+    x = x * 6364136223846793005ull + 1442695040888963407ull;
+    v.push_back(from_bits(x));
+  }
+  for (double a : v) {
+    if (grmhd::lt0(a) != (a < 0.0) || grmhd::gt0(a) != (a > 0.0) || grmhd::eq0(a) != (a == 0.0) ||
+        grmhd::finite_bits(a) != (bool)std::isfinite(a)) {
+      std::printf("sign tests differ at %a\n", a);
+      return false;
+    }
+  }
+  // gt_nn(x, y) == (x > y): neither NaN, at least one >= +0, not (+0, -0)
+  auto in_domain = [](double a, double b) {
+    if (std::isnan(a) || std::isnan(b)) return false;
+    if (std::signbit(a) && std::signbit(b)) return false;
+    if (a == 0.0 && b == 0.0 && !std::signbit(a) && std::signbit(b)) return false;
+    return true;
+  };
+  long long pairs = 0;
+  for (size_t i = 0; i < v.size(); i += (i < 64 ? 1 : 97))
+    for (size_t j = 0; j < v.size(); j += (j < 64 ? 1 : 89)) {
+      const double a = v[i], b = v[j];
+      if (!in_domain(a, b)) continue;
+      pairs++;
+      if (grmhd::gt_nn(a, b) != (a > b)) {
+        std::printf("gt_nn(%a, %a) differs\n", a, b);
+        return false;
+      }
+    }
+  // below_thr(P, x) == (x < rho_thr) for finite x, rho_thr > 0 or = 0
+  for (double thr : {0.0, 1e-12, 1e-10, 1.0}) {
+    grmhd::Par P{};
+    P.rho_thr = thr;
+    P.thr_pos = thr > 0.0;
+    for (double a : v) {
+      if (!std::isfinite(a)) continue;
+      if (grmhd::below_thr(P, a) != (a < thr)) {
+        std::printf("below_thr(%g, %a) differs\n", thr, a);
+        return false;
+      }
+    }
+  }
+  return pairs > 1000;
+}
+
 int main() {
+  if (!check_find_block()) return 1;
+  if (!check_compares()) return 1;
   const int shapes[][3] = {{1, 1, 1},   {2, 3, 5},    {7, 1, 4},    {8, 8, 8},    {16, 9, 3},  {21, 13, 10},
                            {30, 9, 17}, {33, 3, 1},   {31, 2, 6},   {64, 5, 4},   {96, 3, 2},  {104, 2, 3},
                            {128, 2, 2}, {129, 3, 2},  {255, 2, 1},  {3, 128, 2},  {2, 3, 128}};
