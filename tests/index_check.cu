@@ -171,8 +171,26 @@ static bool check_compares() {
   return pairs > 1000;
 }
 
+// Segment lengths that flux_seg_len picks on 152 SMs (x, y, z).
+static bool check_seg_len() {
+  struct Case { int n; int L[3]; } cases[] = {{128, {8, 16, 16}}, {104, {8, 16, 16}}, {96, {8, 8, 8}},
+                                              {64, {2, 2, 2}}, {32, {1, 1, 1}}};
+  for (const Case& c : cases) {
+    const int n[1][3] = {{c.n, c.n, c.n}};
+    for (int d = 0; d < 3; d++) {
+      const int L = grmhd::flux_seg_len(n, 1, d, 152);
+      if (L != c.L[d]) {
+        std::printf("flux_seg_len(%d^3, d=%d) = %d, expected %d\n", c.n, d, L, c.L[d]);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
 int main() {
   if (!check_find_block()) return 1;
+  if (!check_seg_len()) return 1;
   if (!check_compares()) return 1;
   const int shapes[][3] = {{1, 1, 1},   {2, 3, 5},    {7, 1, 4},    {8, 8, 8},    {16, 9, 3},  {21, 13, 10},
                            {30, 9, 17}, {33, 3, 1},   {31, 2, 6},   {64, 5, 4},   {96, 3, 2},  {104, 2, 3},
