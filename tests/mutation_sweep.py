@@ -157,6 +157,51 @@ MUTATIONS = [
     ('WENO tau5',
      'real tau5 = abs_(b0 - b2);',
      'real tau5 = abs_(b0 - b1);'),
+    ('S^ij drops Ptot gamma^ij',
+     'Sij[sym(a, bq)] = sdet * (e * v[a] * v[bq] + Ptot * gi[sym(a, bq)] - bb[a] * bb[bq]);',
+     'Sij[sym(a, bq)] = sdet * (e * v[a] * v[bq] - bb[a] * bb[bq]);'),
+    ('S^ij bbar sign',
+     'Sij[sym(a, bq)] = sdet * (e * v[a] * v[bq] + Ptot * gi[sym(a, bq)] - bb[a] * bb[bq]);',
+     'Sij[sym(a, bq)] = sdet * (e * v[a] * v[bq] + Ptot * gi[sym(a, bq)] + bb[a] * bb[bq]);'),
+    ('bbar drops W Bv v',
+     'bb[a] = B[a] / W + W * Bv * v[a];',
+     'bb[a] = B[a] / W;'),
+    ('Gtau drops K S',
+     'Gs[4] = alpha * kt - sd;',
+     'Gs[4] = - sd;'),
+    ('source E uses tau only',
+     'real E = real(C.b->cons[4 * G.ncell + c]) + real(C.b->cons[0 * G.ncell + c]);',
+     'real E = real(C.b->cons[4 * G.ncell + c]);'),
+    ('source dgamma half',
+     'Gs[1 + a] = 0.5 * alpha * t + s2 - E * dal[a];',
+     'Gs[1 + a] = alpha * t + s2 - E * dal[a];'),
+    ('source Su not raised',
+     'sd = sd + Su[a] * dal[a];',
+     'sd = sd + Sl[a] * dal[a];'),
+    ('ecc sign',
+     'ecc[0 * G.ncell + c] = val(-alpha * (vh[1] * B[2] - vh[2] * B[1]));',
+     'ecc[0 * G.ncell + c] = val(alpha * (vh[1] * B[2] - vh[2] * B[1]));'),
+    ('ecc z component index',
+     'ecc[2 * G.ncell + c] = val(-alpha * (vh[0] * B[1] - vh[1] * B[0]));',
+     'ecc[2 * G.ncell + c] = val(-alpha * (vh[0] * B[2] - vh[2] * B[0]));'),
+    ('DMP upper bound',
+     'real hi = mx > 0.0 ? mx * M : mx / M;',
+     'real hi = mx > 0.0 ? mx / M : mx * M;'),
+    ('RK2 second weight',
+     'static const double RK2_W[2][3] = {{0.0, 1.0, 1.0}, {0.5, 0.5, 0.5}};',
+     'static const double RK2_W[2][3] = {{0.0, 1.0, 1.0}, {0.5, 0.5, 1.0}};'),
+    ('face floor threshold',
+     '  if (s[0] < p.f_thr * p.rho_atm) {\n    s[0] = p.rho_atm;',
+     '  if (s[0] < p.rho_atm) {\n    s[0] = p.rho_atm;'),
+    ('vcap no rescale',
+     'if (e.vcap) vs = sqrt_(s.vmax2 / (mu * mu * e.rbar2));',
+     'if (e.vcap) vs = 1.0;'),
+    ('source dal centred factor',
+     'real inv2dx = 1.0 / (2.0 * C.b->dx[a]);',
+     'real inv2dx = 1.0 / C.b->dx[a];'),
+    ('b2 drops Bv^2',
+     'real b2 = B2 / (W * W) + Bv * Bv;\n  real h = eos_h(C.p, rho, P);',
+     'real b2 = B2 / (W * W);\n  real h = eos_h(C.p, rho, P);'),
 ]
 
 # nu = max(nu_A, nu_B) in the master function: with eps_raw as defined and

@@ -477,6 +477,40 @@ def test_c2p_floors_with_a_field_closed_forms():
     assert np.all(r["prim"][1:4, 0] == 0.0)
 
 
+def test_c2p_speed_cap_returns_W_max():
+    """A state moving at W = 2000 > W_max = 1e3 is recovered at the cap: the
+    velocity is rescaled so that |w| = sqrt(W_max^2 - 1), flagged F_VMAX."""
+    p = O.params(gamma=2.0)
+    g = np.array([[1.0], [0], [0], [1.0], [0], [1.0]])
+    W = 2000.0
+    prim = np.array([[1.0], [np.sqrt(W * W - 1.0)], [0.0], [0.0], [1.0]])
+    Bd = np.array([[0.0], [0.01], [0.0]])
+    r = O.c2p_cells(p, O.prim2cons(p, prim, Bd, g), Bd, g)
+    assert r["flags"][0] & O.F_VMAX and not r["flags"][0] & O.F_FAIL
+    wr = r["prim"][1:4, 0]
+    assert abs(np.sqrt(1.0 + wr @ wr) / p.W_max - 1.0) < 1e-9
+    assert wr[0] > 0.0 and wr[1] == 0.0 and wr[2] == 0.0
+
+
+def test_face_floor_density_threshold():
+    """Sec. 3.3 on a reconstructed state: rho below f_thr rho_atm becomes the
+    static atmosphere (rho_atm, P_atm = rho_atm T_atm, v = 0, same B); rho between
+    f_thr rho_atm and rho_atm is kept.  Equal states on both sides make the
+    Riemann flux the physical flux of the (floored) state."""
+    p = O.params(gamma=2.0, rho_atm=1e-6, T_atm=1e-3, f_thr=0.1)
+    m10 = np.array([1.0, 0, 0, 0, 1.0, 0, 0, 1.0, 0, 1.0])
+    Bn = 3e-4
+    L = np.array([0.5e-6, 0.1, 0.05, -0.02, 0.5e-6 * 1e-2, 1e-4, -2e-4])
+    F = O.face_flux(p, 0, L, L, Bn, m10)
+    Fs = O.face_side(p, 0, L, Bn, m10)[1]
+    assert np.all(np.abs(F - Fs) <= 1e-15 * np.abs(Fs).max())
+    L[0], L[4] = 0.05e-6, 0.05e-6 * 1e-2
+    A = np.array([1e-6, 0.0, 0.0, 0.0, 1e-6 * 1e-3, 1e-4, -2e-4])
+    F = O.face_flux(p, 0, L, L, Bn, m10)
+    Fa = O.face_side(p, 0, A, Bn, m10)[1]
+    assert np.all(np.abs(F - Fa) <= 1e-15 * np.abs(Fa).max())
+
+
 # ------------------------------------------------------------- stage level
 
 def _small_block(p, n, adm, prim_cell, Bd):
@@ -516,6 +550,26 @@ def test_uniform_state_curved_metric_fluxes_and_steady(recon, rs):
             assert np.max(np.abs(Fi[c] - ref[c])) <= 1e-13 * (np.abs(ref).max()), (d, c)
     I = (slice(None),) + interior(b)
     assert np.max(np.abs(b.cons[I] - U0[I])) <= 1e-14 * np.abs(U0[I]).max()
+
+
+def test_uniform_state_edge_emf_is_minus_vt_cross_B():
+    """Uniform fluid and field in a uniform curved metric: the induction flux of
+    B~^b along a is vt^a B~^b - vt^b B~^a with vt = alpha v - beta, so every
+    edge EMF (face values averaged, upwind corrections zero) is
+    E = -(vt x B~) with the densitised B~ (Sec. 3.2, Gardiner & Stone 2005)."""
+    p = O.params(gamma=5.0 / 3.0, recon=2, rsolver=1, rk_order=3)
+    a, be, g6 = 0.8, np.array([0.1, -0.05, 0.02]), (1.1, 0.05, -0.02, 0.95, 0.03, 1.2)
+    n = (4, 5, 6)
+    adm = uniform_metric([x + 8 for x in n], a, tuple(be), g6)
+    rho, w, P, Bd = 0.5, np.array([0.2, -0.3, 0.1]), 0.3, np.array([0.2, 0.1, -0.3])
+    b = _small_block(p, n, adm, [rho, *w, P], Bd)
+    out = O.stage(p, b, 0.01, 0, keep=True)
+    gm = np.array([[g6[0], g6[1], g6[2]], [g6[1], g6[3], g6[4]], [g6[2], g6[4], g6[5]]])
+    v = w / np.sqrt(1.0 + w @ gm @ w)
+    E = -np.cross(a * v - be, Bd)
+    for c in range(3):
+        e = out["emf"][c][5:4 + n[2], 5:4 + n[1], 5:4 + n[0]]
+        assert e.size > 0 and np.max(np.abs(e - E[c])) <= 1e-14 * np.abs(E).max(), (c, e.ravel()[:3], E[c])
 
 
 def test_sources_match_covariant_form():
