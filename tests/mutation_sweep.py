@@ -202,6 +202,18 @@ MUTATIONS = [
     ('b2 drops Bv^2',
      'real b2 = B2 / (W * W) + Bv * Bv;\n  real h = eos_h(C.p, rho, P);',
      'real b2 = B2 / (W * W);\n  real h = eos_h(C.p, rho, P);'),
+    ('curl x-face drops dAy/dz',
+     '                                    (Ay[G.e(1, k + 1, j, i)] - Ay[G.e(1, k, j, i)]) / dx[2];',
+     '                                    (Ay[G.e(1, k + 1, j, i)] - Ay[G.e(1, k, j, i)]) / dx[2] * 0.0;'),
+    ('curl z-face spacing',
+     '        b->bf[2][G.f(2, k, j, i)] = (Ay[G.e(1, k, j, i + 1)] - Ay[G.e(1, k, j, i)]) / dx[0] -',
+     '        b->bf[2][G.f(2, k, j, i)] = (Ay[G.e(1, k, j, i + 1)] - Ay[G.e(1, k, j, i)]) / dx[1] -'),
+    ('bcc y average index',
+     'C.b->bcc[1 * G.ncell + c] = val(0.5 * (real(C.b->bf[1][G.f(1, k, j, i)]) + real(C.b->bf[1][G.f(1, k, j + 1, i)])));',
+     'C.b->bcc[1 * G.ncell + c] = val(0.5 * (real(C.b->bf[1][G.f(1, k, j, i)]) + real(C.b->bf[1][G.f(1, k, j, i)])));'),
+    ('illinois final regula falsi',
+     '  return a - fa * (b - a) / (fb - fa);\n}',
+     '  return 0.5 * (a + b);\n}'),
 ]
 
 # nu = max(nu_A, nu_B) in the master function: with eps_raw as defined and

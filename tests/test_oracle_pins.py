@@ -572,6 +572,40 @@ def test_uniform_state_edge_emf_is_minus_vt_cross_B():
         assert e.size > 0 and np.max(np.abs(e - E[c])) <= 1e-14 * np.abs(E).max(), (c, e.ravel()[:3], E[c])
 
 
+def test_face_field_from_linear_potential_and_cell_average():
+    """Initial data (Sec. 3.2 CT): linear edge potentials A_x = B_y z,
+    A_y = B_z x, A_z = B_x y are differenced exactly, so the discrete curl
+    gives the uniform field (B_x, B_y, B_z) on every face, on cells of unequal
+    sides.  The cell-centred B~ is the mean of a cell's two faces: a face
+    field linear along its own axis averages to the value at the centre."""
+    p = O.params(gamma=2.0)
+    n, ng, dx = (3, 4, 5), 4, (0.1, 0.2, 0.3)
+    N = [x + 2 * ng for x in n]
+    adm = uniform_metric(N)
+    Bx, By, Bz = 0.7, -0.4, 0.25
+    b = O.new_block(n, ng, dx, adm)
+    k = np.arange(N[2] + 1)[:, None, None] * dx[2]
+    j = np.arange(N[1] + 1)[None, :, None] * dx[1]
+    i = np.arange(N[0] + 1)[None, None, :] * dx[0]
+    A = [np.broadcast_to(By * k, b.edge_shape(0)).copy(), np.broadcast_to(Bz * i, b.edge_shape(1)).copy(),
+         np.broadcast_to(Bx * j, b.edge_shape(2)).copy()]
+    prim = np.zeros((5, N[2], N[1], N[0]))
+    prim[0], prim[4] = 1.0, 1.0
+    b = O.init_block(p, n, ng, dx, adm, prim, A)
+    for d, B in enumerate((Bx, By, Bz)):
+        assert np.max(np.abs(b.bf[d] - B)) <= 1e-14, d
+    # face fields linear along their own axis: B^d(face m) = m + 0.25 d
+    for d in range(3):
+        sh = b.face_shape(d)
+        m = np.arange(sh[2 - d], dtype=float) + 0.25 * d
+        b.bf[d][...] = m.reshape([-1 if ax == 2 - d else 1 for ax in range(3)])
+    O.bcc(p, b)
+    for d in range(3):
+        m = np.arange(N[d], dtype=float) + 0.5 + 0.25 * d
+        ref = np.broadcast_to(m.reshape([-1 if ax == 2 - d else 1 for ax in range(3)]), b.bcc[d].shape)
+        assert np.array_equal(b.bcc[d], ref), d
+
+
 def test_sources_match_covariant_form():
     """Eq. 9 against the covariant sources: S~_i gets (1/2) sqrt(-g) T^{mu nu}
     d_i g_{mu nu}; tau~ gets sqrt(-g)(K_ij S^ij - S^i d_i alpha / alpha), with
