@@ -229,6 +229,10 @@ long long mhd_kernel_launches(const mhd_ctx* ctx);
  * ledger is off or no list was run.  Synchronises the stream.
  * mhd_block_mass: host out[nblocks] = sum over interior cells of D~ dx dy dz.
  * Synchronises the stream. */
+int mhd_ledger(mhd_ctx* ctx, int enable);
+int mhd_ledger_read(mhd_ctx* ctx, double* out, int reset, void* stream);
+int mhd_block_mass(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, double* out, void* stream);
+
 /* Ghost zones of the blocks of a list from same-level neighbours: copies, no
  * prolongation or restriction.  The paper's AMR driver fills them with
  * prolongation and restriction at level changes (Sec. 2); that part is not
@@ -247,10 +251,6 @@ long long mhd_kernel_launches(const mhd_ctx* ctx);
  * neighbour of another size.  Asynchronous on the stream; nbr may be reused
  * after return. */
 int mhd_fill_ghosts(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, const int* nbr, void* stream);
-
-int mhd_ledger(mhd_ctx* ctx, int enable);
-int mhd_ledger_read(mhd_ctx* ctx, double* out, int reset, void* stream);
-int mhd_block_mass(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, double* out, void* stream);
 
 /* Kernel kinds for per-kernel timing. */
 #define MHD_K_C2P 0        /* con2prim of the stencil region (prep + finish) */
