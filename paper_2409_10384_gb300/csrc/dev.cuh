@@ -238,6 +238,18 @@ __host__ __device__ __forceinline__ bool gt_nn(double x, double y) { return dbit
 __host__ __device__ __forceinline__ bool below_thr(const Par& P, double x) {
   return P.thr_pos ? gt_nn(P.rho_thr, x) : lt0(x);
 }
+// CT upwinding (k_emf) by the sign of the face mass flux fD: (a - b) for
+// fD > 0, (c - d) for fD < 0, their average for fD = 0 (or NaN).  The sign test
+// reads the bit pattern on the integer pipe and only the chosen difference is
+// formed in FP64: the same values as comparing fD with 0 in FP64, with one
+// subtraction where the select form takes two subtractions, two compares and
+// an average.
+__host__ __device__ __forceinline__ double upw(double fD, double a, double b, double c, double d) {
+  const unsigned long long u = (unsigned long long)dbits(fD);
+  const unsigned long long mag = u & 0x7FFFFFFFFFFFFFFFull;
+  if (mag - 1ull < 0x7FF0000000000000ull) return (u >> 63) ? c - d : a - b;   // fD != 0, not NaN
+  return 0.5 * ((a - b) + (c - d));
+}
 // finite (not inf, not NaN): the exponent field is not all ones
 __host__ __device__ __forceinline__ bool finite_bits(double x) {
 #ifdef __CUDA_ARCH__

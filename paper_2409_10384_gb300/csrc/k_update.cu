@@ -5,18 +5,6 @@
 
 namespace grmhd {
 
-// Upwinding by the sign of the face mass flux fD: (a - b) for fD > 0, (c - d)
-// for fD < 0, their average for fD = 0 (or NaN).  The sign test reads the bit
-// pattern on the integer pipe and only the chosen difference is formed in
-// FP64: the same values as comparing fD with 0 in FP64, with one subtraction
-// where the select form takes two subtractions, two compares and an average.
-__device__ __forceinline__ double upw(double fD, double a, double b, double c, double d) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(fD);
-  const unsigned long long mag = u & 0x7FFFFFFFFFFFFFFFull;
-  if (mag - 1ull < 0x7FF0000000000000ull) return (u >> 63) ? c - d : a - b;   // fD != 0, not NaN
-  return 0.5 * ((a - b) + (c - d));
-}
-
 // Edge EMF of component cc at edge index (k,j,i) in the plane a = (cc+1)%3,
 // b = (cc+2)%3: on a-faces E_cc = -F_a[5], on b-faces E_cc = +F_b[6].
 template <int cc>

@@ -11,7 +11,8 @@
 //  - find_block: on prefix sums with empty blocks, item it belongs to the
 //    block b returned, p[b] <= it < p[b + 1].
 //  - The integer-pipe compares (lt0, gt0, eq0, gt_nn, below_thr,
-//    finite_bits) against the IEEE comparisons they replace, on special
+//    finite_bits, and upw of the CT upwinding) against the IEEE comparisons
+//    they replace, on special
 //    values (+-0, subnormals, +-inf, NaNs of both signs) and random bit
 //    patterns, within each one's stated domain.
 // Prints "ok" and exits 0, else the first failure.
@@ -166,6 +167,15 @@ static bool check_compares() {
         std::printf("below_thr(%g, %a) differs\n", thr, a);
         return false;
       }
+    }
+  }
+  // upw (CT upwinding) against the select form of FP64 compares
+  for (double f : v) {
+    const double a = 1.5, b = -0.25, c = 3.0, d = 0.75;
+    const double ref = f > 0.0 ? a - b : (f < 0.0 ? c - d : 0.5 * ((a - b) + (c - d)));
+    if (grmhd::upw(f, a, b, c, d) != ref) {
+      std::printf("upw(%a) differs\n", f);
+      return false;
     }
   }
   return pairs > 1000;
