@@ -214,6 +214,21 @@ MUTATIONS = [
     ('illinois final regula falsi',
      '  return a - fa * (b - a) / (fb - fa);\n}',
      '  return 0.5 * (a + b);\n}'),
+    ('illinois no halving',
+     '      if (side == -1) Fb = 0.5 * Fb;',
+     '      if (side == -1) Fb = 1.0 * Fb;'),
+    ('bracket no [mu+, 1] fallback',
+     '    if (e1.f < 0.0) {\n      a = b; e0 = e1;\n      b = 1.0;',
+     '    if (false) {\n      a = b; e0 = e1;\n      b = 1.0;'),
+    ('krp rb2 not squared',
+     '    s.rb2 = s.rb * s.rb;',
+     '    s.rb2 = s.rb;'),
+    ('krp b2 not per D',
+     '    s.b2 = B2 / D;',
+     '    s.b2 = B2;'),
+    ('fofc fix keeps high order',
+     '    reconstruct(donor ? 0 : C.p.recon, q, &L[v], &R[v]);',
+     '    reconstruct(C.p.recon, q, &L[v], &R[v]);'),
 ]
 
 # nu = max(nu_A, nu_B) in the master function: with eps_raw as defined and

@@ -477,6 +477,26 @@ def test_c2p_floors_with_a_field_closed_forms():
     assert np.all(r["prim"][1:4, 0] == 0.0)
 
 
+def test_c2p_cold_dust_root_at_the_bracket_end():
+    """Cold unmagnetised dust (P = 0, T_atm = 0, so h = 1): the root of the
+    master function is mu = 1/(h W) = 1/W = 1/sqrt(1 + r^2), the bracket's upper
+    end itself, where rounding can leave f(mu+) < 0; the solve then takes the
+    bracket [mu+, 1] (Kastaun et al.) and recovers every cell."""
+    p = O.params(gamma=2.0, rho_atm=1e-20, T_atm=0.0, f_thr=0.0)
+    n = 400
+    g = np.tile(np.array([[1.0], [0], [0], [1.0], [0], [1.0]]), (1, n))
+    rng = np.random.default_rng(5)
+    W = 10 ** rng.uniform(0, 2, n)
+    d = rng.normal(size=(3, n))
+    d /= np.linalg.norm(d, axis=0)
+    prim = np.vstack([10 ** rng.uniform(-6, 0, n), np.sqrt(W * W - 1.0) * d, np.zeros(n)])
+    Bd = np.zeros((3, n))
+    r = O.c2p_cells(p, O.prim2cons(p, prim, Bd, g), Bd, g)
+    assert not np.any(r["flags"] & O.F_FAIL)
+    assert np.max(np.abs(r["prim"][0] / prim[0] - 1.0)) < 1e-10
+    assert np.max(np.abs(r["prim"][1:4] - prim[1:4]) / W) < 1e-10
+
+
 def test_c2p_speed_cap_returns_W_max():
     """A state moving at W = 2000 > W_max = 1e3 is recovered at the cap: the
     velocity is rescaled so that |w| = sqrt(W_max^2 - 1), flagged F_VMAX."""
