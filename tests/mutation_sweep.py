@@ -229,6 +229,15 @@ MUTATIONS = [
     ('fofc fix keeps high order',
      '    reconstruct(donor ? 0 : C.p.recon, q, &L[v], &R[v]);',
      '    reconstruct(C.p.recon, q, &L[v], &R[v]);'),
+    ('post-solve rho floor removed',
+     '      if (rho < p.f_thr * rho_atm) {\n        rho = rho_atm;',
+     '      if (false) {\n        rho = rho_atm;'),
+    ('post-solve P floor removed',
+     '        if (P < Pf) {\n          P = Pf;',
+     '        if (false) {\n          P = Pf;'),
+    ('stage 0 keeps no U^n',
+     '          if (first) C.b->cons0[v * G.ncell + c] = C.b->cons[v * G.ncell + c];',
+     '          if (false) C.b->cons0[v * G.ncell + c] = C.b->cons[v * G.ncell + c];'),
 ]
 
 # nu = max(nu_A, nu_B) in the master function: with eps_raw as defined and

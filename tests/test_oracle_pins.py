@@ -1133,3 +1133,43 @@ def test_clamped_con2prim_keeps_D_and_S(hybrid):
     rr = r["prim"][0]
     Pf = np.array([Pc(x) for x in rr]) + rr * p.T_atm
     assert np.all(np.abs(r["prim"][4] - Pf) <= 1e-12 * Pf)
+
+
+@pytest.mark.parametrize("hybrid", [False, True])
+def test_clamped_pressure_is_never_below_the_floor(hybrid):
+    """Sec. 3.3: after the solve P >= P_c(rho) + rho T_atm holds exactly, also
+    where the clamped eps gives it only to rounding (the floor is formed as the
+    oracle forms it: its P_c, then + rho T_atm in FP64).  4000 cold cells."""
+    kw = HYB if hybrid else {}
+    p = O.params(gamma=2.0, rho_atm=1e-20, T_atm=1e-3, f_thr=0.0, **kw)
+    n = 4000
+    rng = np.random.default_rng(8)
+    rho = 10 ** rng.uniform(-8, 0, n)
+    Pc = np.array([O.eos(p, r, 1.0)["Pc"] for r in rho]) if hybrid else np.zeros(n)
+    prim = np.vstack([rho, rng.normal(size=(3, n)) * 0.5, Pc])
+    Bd = rng.normal(size=(3, n)) * 0.3 * np.sqrt(rho)
+    g = np.tile(np.array([[1.1], [0.05], [0.0], [0.95], [0.02], [1.2]]), (1, n))
+    r = O.c2p_cells(p, O.prim2cons(p, prim, Bd, g), Bd, g)
+    assert not np.any(r["flags"] & O.F_FAIL)
+    rr = r["prim"][0]
+    Pcr = np.array([O.eos(p, x, 1.0)["Pc"] for x in rr]) if hybrid else np.zeros(n)
+    assert np.all(r["prim"][4] >= Pcr + rr * p.T_atm)
+
+
+def test_post_solve_density_floor():
+    """Sec. 3.3: D~ above the pre-solve floor f_thr rho_atm, but moving at W = 10,
+    recovers rho = D/W below it: the cell becomes the static atmosphere
+    (rho_atm, v = 0, P = rho_atm T_atm), flagged F_RHO."""
+    p = O.params(gamma=2.0, rho_atm=1e-10, T_atm=1e-8, f_thr=0.1)
+    g = np.array([[1.0], [0], [0], [1.0], [0], [1.0]])
+    W = 10.0
+    rho = 0.15 * p.f_thr * p.rho_atm
+    prim = np.array([[rho], [np.sqrt(W * W - 1.0)], [0.0], [0.0], [rho * 1e-2]])
+    Bd = np.zeros((3, 1))
+    cons = O.prim2cons(p, prim, Bd, g)
+    assert cons[0, 0] > p.f_thr * p.rho_atm
+    r = O.c2p_cells(p, cons, Bd, g)
+    assert r["flags"][0] & O.F_RHO and not r["flags"][0] & O.F_DFLOOR
+    assert r["prim"][0, 0] == p.rho_atm and np.all(r["prim"][1:4, 0] == 0.0)
+    assert abs(r["prim"][4, 0] - p.rho_atm * p.T_atm) <= 1e-15 * p.rho_atm * p.T_atm
+
