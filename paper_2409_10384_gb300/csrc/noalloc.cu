@@ -4,10 +4,13 @@
 // has handed its whole GPU memory budget to its own pool allocator, or one
 // that cannot afford the device-wide synchronisation a cudaFree implies in the
 // middle of a time step, or one that has nowhere to keep a library context.
-// mhd_stage_noalloc serves them: it runs the same kernels as mhd_c2p +
-// mhd_rhs + mhd_rk_update, but its scratch (fluxes, EMFs, cell-centred E,
-// FOFC flags, the block descriptor and the work table) lives in the
-// file-scope array below, so no call allocates or frees anything.
+// mhd_stage_noalloc serves them: it gives the results of mhd_c2p + mhd_rhs +
+// mhd_rk_update (the same fluxes, CT and update kernels; its con2prim and
+// FOFC estimate are the one-thread-per-cell kernels k_c2p_block and
+// k_fofc_flag, which need no solve scratch, in place of the three-phase
+// ones), and its scratch (fluxes, EMFs, cell-centred E, FOFC flags, the block
+// descriptor and the work table) lives in the file-scope array below, so no
+// call allocates or frees anything.
 //
 // The array is MHD_NOALLOC_SCRATCH_BYTES (16 MiB) per device and stays
 // resident on every GPU that loads the library until the process exits.
@@ -49,7 +52,7 @@ __global__ void k_noalloc_setup(DevBlock b, PreTable t, DevBlock* dblk, long lon
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     *dblk = b;
     for (int k = 0; k < W_NKIND * 2; k++) dpre[k] = t.v[k];
-    for (int k = 0; k < 8; k++) st[k] = 0ull;
+    for (int k = 0; k < MHD_NSTATS; k++) st[k] = 0ull;
   }
 }
 
@@ -160,8 +163,14 @@ extern "C" int mhd_stage_noalloc(const mhd_params* p, const mhd_block* blk, doub
   static_assert(sizeof(DevBlock) <= kOffPre - kOffBlk, "descriptor slot");
   static_assert(sizeof(PreTable) <= kOffStats - kOffPre, "work table slot");
 
+  // A launch error left pending by the caller's earlier work is reported
+  // (and left pending) before anything is launched, so that every error seen
+  // after a launch below belongs to this call.
+  if (cudaPeekAtLastError() != cudaSuccess) return MHD_ECUDA;
   cudaStream_t st = (cudaStream_t)stream;
+  auto launched = [] { return cudaPeekAtLastError() == cudaSuccess; };
   k_noalloc_setup<<<1, 32, 0, st>>>(b, t, dblk, dpre, dstats);
+  if (!launched()) return MHD_ECUDA;
   Work w;
   w.blk = dblk;
   w.pre = dpre;
@@ -174,13 +183,23 @@ extern "C" int mhd_stage_noalloc(const mhd_params* p, const mhd_block* blk, doub
   double g0, g1, be;
   rk_weights(P.rk_order, stage, g0, g1, be);
   launch_c2p_block(w, P, dstats, st, grid(W_C2P, 128));
-  for (int d = 0; d < 3; d++) launch_flux_dir(d, w, P, st, grid(W_SX + d, 128));
+  if (!launched()) return MHD_ECUDA;
+  for (int d = 0; d < 3; d++) {
+    launch_flux_dir(d, w, P, st, grid(W_SX + d, 128));
+    if (!launched()) return MHD_ECUDA;
+  }
   if (P.fofc) {
     launch_fofc_flag(w, P, g0, g1, be * dt, dstats, st, grid(W_CELL, 128));
-    for (int d = 0; d < 3; d++) launch_fofc_fix(d, w, P, dstats, st, grid(W_FX + d, 128));
+    if (!launched()) return MHD_ECUDA;
+    for (int d = 0; d < 3; d++) {
+      launch_fofc_fix(d, w, P, dstats, st, grid(W_FX + d, 128));
+      if (!launched()) return MHD_ECUDA;
+    }
   }
   launch_emf(w, st, grid(W_EDGE, 128));
+  if (!launched()) return MHD_ECUDA;
   launch_update_cells(w, P, g0, g1, be * dt, stage == 0 ? 1 : 0, st, grid(W_CELL, 128));
+  if (!launched()) return MHD_ECUDA;
   launch_update_faces(w, g0, g1, be * dt, stage == 0 ? 1 : 0, st, grid(W_FACE, 256));
-  return cudaGetLastError() == cudaSuccess ? MHD_OK : MHD_ECUDA;
+  return launched() ? MHD_OK : MHD_ECUDA;
 }

@@ -28,12 +28,15 @@ def G():
     return grmhd
 
 
-@pytest.mark.parametrize("eos", [0, 1])
-def test_noalloc_stage_matches_context_stage_twice(G, eos):
+@pytest.mark.parametrize("eos,recon,dmp", [(0, 2, 0.0), (1, 2, 0.0), (0, 1, 1.1), (0, 4, 1.2)])
+def test_noalloc_stage_matches_context_stage_twice(G, eos, recon, dmp):
+    """Every RK3 stage in a row (the calls share the static array, which keeps
+    the previous call's contents), with WENO-Z, PLM or PPMX and with the DMP
+    test of the FOFC estimate on or off."""
     import torch
     from tests.test_gpu_hybrid_eos import HYB_STAR, _star_hyb
-    p = O.params(gamma=2.0, rho_atm=1e-12, T_atm=1e-10, f_thr=0.1, recon=2, rsolver=1, rk_order=3, fofc=1,
-                 **(HYB_STAR if eos else {}))
+    p = O.params(gamma=2.0, rho_atm=1e-12, T_atm=1e-10, f_thr=0.1, recon=recon, rsolver=1, rk_order=3, fofc=1,
+                 dmp_M=dmp, **(HYB_STAR if eos else {}))
     if eos:
         inp, prim = _star_hyb(p, (104, 52, 52))
     else:
@@ -45,7 +48,7 @@ def test_noalloc_stage_matches_context_stage_twice(G, eos):
     a = U.to_device(G, ob)
     b = U.to_device(G, ob)
     dt = 0.25 * inp.dx[0]
-    for s in range(2):   # two calls in a row
+    for s in range(3):   # three calls in a row
         ctx.stage([a], dt, s)
         assert G.stage_noalloc(gp, b, dt, s) == 0
         torch.cuda.synchronize()
