@@ -123,7 +123,11 @@ typedef struct {
   long long guess_fallbacks; /* c2p_guess 1, 2: cells whose FP32 root did not
                                 bracket the FP64 root within 4e-6 (the bracket
                                 then extends to 0 or 1) */
+  long long fp32_evals; /* c2p_guess 1, 2: FP32 evaluations of the master
+                           function in the searches (the two starting points
+                           and one per secant step) */
 } mhd_stats;
+#define MHD_NSTATS 9
 
 /* Create a context on the current device.  *out receives it.  Copies p. */
 int mhd_init(const mhd_params* p, mhd_ctx** out);
@@ -146,17 +150,22 @@ int mhd_prim2cons(mhd_ctx* ctx, long n, const double* prim, const double* Bd, co
 /* con2prim (Sec. 3.4, Kastaun et al. 2021 bracketed root) with the atmosphere
  * floors of Sec. 3.3 on n independent cells.  cons [5][n] is overwritten where
  * a floor changed it; prim [5][n] and flags [n] are written; iters [n] (may be
- * NULL) receives the root iterations.  Device pointers. */
+ * NULL) receives the FP64 evaluations of the master function per cell.
+ * Device pointers.  stats (host, may be NULL): the counters this call added
+ * (cells, iters, fails, floors, guess_fallbacks); a non-NULL stats makes the
+ * call synchronise the stream (before and after its launches). */
 int mhd_c2p_cells(mhd_ctx* ctx, long n, double* cons, const double* Bd, const double* g, double* prim,
-                  unsigned char* flags, int* iters, void* stream);
+                  unsigned char* flags, int* iters, void* stream, mhd_stats* stats);
 
 /* con2prim of every cell within 3 of the interior of each block (the stencil
  * region of WENO-Z), with bcc and the cell-centred EMF; floors write back to
  * cons.  This is step 1 of a stage.  It also keeps sqrt(gamma), 1/sqrt(gamma)
  * and gamma^ij of every cell in context scratch for steps 2-5 of the same
  * stage, so the ADM arrays must not change between mhd_c2p and mhd_rk_update
- * of one stage (the metric is an input of the whole stage). */
-int mhd_c2p(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, void* stream);
+ * of one stage (the metric is an input of the whole stage).  stats (host,
+ * may be NULL): the counters this call added, as in mhd_c2p_cells (the call
+ * then synchronises the stream). */
+int mhd_c2p(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, void* stream, mhd_stats* stats);
 
 /* Steps 2-4 of stage `stage` (0-based) with time step dt: reconstruction and
  * Riemann fluxes (Eq. 8) on every face the update needs, FOFC (+DMP) and the
@@ -175,6 +184,10 @@ int mhd_rk_update(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, double dt,
  * stream must not be the legacy default stream); 2: one launch sequence per
  * block (a reference for the batched launches; same results). */
 int mhd_step(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, double dt, int graph, void* stream);
+/* The captured full RK step: mhd_step with graph = 1 (one CUDA graph of all
+ * rk_order stages per block list, dt, parameters and stream, replayed on
+ * later calls; stream must not be the legacy default stream). */
+int mhd_graph_step(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, double dt, void* stream);
 
 /* Autotuner for a block list: times each tunable kernel (the two con2prim
  * phases, the three flux directions, the two FOFC-estimate phases, the EMF
@@ -263,7 +276,9 @@ int mhd_fill_ghosts(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, const in
 #define MHD_K_UPDATE 7     /* RK update of U with the Eq. 9 sources */
 #define MHD_K_FACEB 8      /* RK update of the face B~ */
 #define MHD_K_SOLVE 9      /* con2prim root solves (stage input and U*) */
-#define MHD_K_MLP 10       /* learned-guess network inference */
+#define MHD_K_MLP 10       /* learned guess: network inference fused with the
+                              FP32 search and the FP64 bracket (c2p_guess 1;
+                              c2p_guess 2 counts its search under MHD_K_C2P) */
 #define MHD_K_LEDGER 11    /* baryon-mass ledger (only with mhd_ledger on) */
 #define MHD_NKERNEL 12
 
@@ -312,6 +327,19 @@ int mhd_mlp_grad(mhd_ctx* ctx, const float* feat, const float* logmu, long n, fl
 /* Copy the state out / in (host arrays of MHD_MLP_NSTATE floats). */
 int mhd_mlp_get(mhd_ctx* ctx, float* state);
 int mhd_mlp_set(mhd_ctx* ctx, const float* state);
+/* The trained network as a BF16 weight blob (host memory, little-endian):
+ * MHD_MLP_NPARAM bf16 parameters in the order of mhd_mlp_get, then the 13
+ * fp32 values that follow them there (feature mean, feature 1/std, target
+ * mean and std, delta); MHD_MLP_BLOB_BYTES in all.  mhd_mlp_save writes it
+ * (bytes must be at least MHD_MLP_BLOB_BYTES; size, may be NULL, receives the
+ * length).  mhd_mlp_load reads one (bytes must equal MHD_MLP_BLOB_BYTES,
+ * else MHD_EINVAL) into the context: the parameters become the fp32 master
+ * weights and the tensor-core operands, and the guess is enabled when delta
+ * > 0.  Inference runs on bf16 operands, so a loaded blob predicts what the
+ * saved network predicted.  Synchronise the device. */
+#define MHD_MLP_BLOB_BYTES (2 * 4609 + 4 * 13)
+int mhd_mlp_save(mhd_ctx* ctx, void* blob, long bytes, long* size);
+int mhd_mlp_load(mhd_ctx* ctx, const void* bf16_weights, long bytes);
 
 /* Allocation-free stage (the paper has no counterpart: this serves callers).
  * Some callers cannot let a library allocate device memory: a host code that
@@ -319,9 +347,12 @@ int mhd_mlp_set(mhd_ctx* ctx, const float* state);
  * accept the device-wide synchronisation a cudaFree implies inside a time
  * step, or one with nowhere to keep a library context.  mhd_stage_noalloc runs
  * one RK stage (`stage`, 0-based, of p->rk_order) of ONE block -- con2prim,
- * fluxes, FOFC, CT EMFs and the update, the same kernels and results as
- * mhd_c2p + mhd_rhs + mhd_rk_update -- with no context and without calling
- * cudaMalloc, cudaFree or any allocating routine.  Its scratch is a
+ * fluxes, FOFC, CT EMFs and the update, with the results of mhd_c2p +
+ * mhd_rhs + mhd_rk_update (the same flux, CT and update kernels; its
+ * con2prim and FOFC estimate run one thread per cell, which needs no solve
+ * scratch, where the context path uses its three-phase kernels) -- with no
+ * context and without calling cudaMalloc, cudaFree or any allocating
+ * routine.  Its scratch is a
  * file-scope device array of MHD_NOALLOC_SCRATCH_BYTES (16 MiB), held by
  * every GPU that loads the library until the process exits; a block whose
  * scratch does not fit (e.g. interior larger than 32^3 with 4 ghosts) is
@@ -330,7 +361,10 @@ int mhd_mlp_set(mhd_ctx* ctx, const float* state);
  * with that device current, looks up the array's device address; make that
  * first call before any stream capture.  All calls share the array and it
  * keeps the last call's contents: calls whose kernels overlap on the GPU
- * race.  p->c2p_guess must be 0.  Counters are not reported. */
+ * race.  p->c2p_guess must be 0.  Counters are not reported.  A launch error
+ * already pending from the caller's earlier work is returned as MHD_ECUDA
+ * before any launch (and left pending); otherwise MHD_ECUDA reports a failed
+ * launch of this call. */
 #define MHD_NOALLOC_SCRATCH_BYTES (16u << 20)
 int mhd_stage_noalloc(const mhd_params* p, const mhd_block* blk, double dt, int stage, void* stream);
 

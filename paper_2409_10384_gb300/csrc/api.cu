@@ -19,6 +19,7 @@ struct mhd_ctx {
   int dev = 0, nsm = 1;
   int occ_c2p[2] = {1, 1}, occ_face[5] = {1, 1, 1, 1, 1}, occ_upd[3] = {1, 1, 1};
   int occ_krp[7] = {1, 1, 1, 1, 1, 1, 1};
+  int occ_seed[2] = {1, 1};   // seed kernel without / with the network
   // three-phase con2prim scratch: of the block list, and of independent cells
   char* krp = nullptr;
   long long krp_n = 0;
@@ -50,9 +51,6 @@ struct mhd_ctx {
   } cfg[T_N];
   int occ_t[T_N][3] = {{0}};   // occupancy at 64, 128, 256 threads
   long long* dpre_blk = nullptr;  // per-block work tables [nb][W_NKIND][2] (per-block launches)
-  // block-list scratch of the guessed con2prim (c2p_guess 1, 2): features, log(mu)
-  float* gfeat = nullptr;
-  float* glogmu = nullptr;
   // baryon-mass ledger [nb][2] (lf, la) and per-block mass sums [nb]
   bool ledger_on = false;
   double* dledger = nullptr;
@@ -270,13 +268,6 @@ int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
   const long long nkrp = std::max(pre[(size_t)W_C2P * (nb + 1) + nb], pre[(size_t)W_CELL * (nb + 1) + nb]);
   const size_t krp_off = need;
   need += al256(krp_bytes(nkrp));
-  size_t feat_off = 0, logmu_off = 0;
-  if (c->P.guess == 1 || c->P.guess == 2) {
-    feat_off = need;
-    need += al256(sizeof(float) * MLP_FSTRIDE * (size_t)nkrp);
-    logmu_off = need;
-    need += al256(sizeof(float) * (size_t)nkrp);
-  }
   const size_t mass_off = need;
   need += al256(sizeof(double) * (size_t)nb);
   const size_t led_off = need;
@@ -319,9 +310,6 @@ int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
   }
   c->krp = c->scratch + krp_off;
   c->krp_n = nkrp;
-  const bool seeded = c->P.guess == 1 || c->P.guess == 2;
-  c->gfeat = seeded ? (float*)(c->scratch + feat_off) : nullptr;
-  c->glogmu = seeded ? (float*)(c->scratch + logmu_off) : nullptr;
   c->dmass = (double*)(c->scratch + mass_off);
   c->dledger = c->ledger_on ? (double*)(c->scratch + led_off) : nullptr;
   if (c->dledger && cudaMemset(c->dledger, 0, sizeof(double) * 2 * (size_t)nb) != cudaSuccess) return MHD_ECUDA;
@@ -439,18 +427,19 @@ Work work_of(const mhd_ctx* c) {
 // One launch sequence over the work `w` with `items[W_NKIND]` items per kind
 // (all blocks of the list, or one block for per-block launches).
 // Between the prep and the FP64 root solve of a guessed con2prim (c2p_guess 1:
-// network guess; 2: FP32 search from the plain bracket): network inference on
-// the prep's features and the FP32 seed search that turns status-4 cells into
-// FP64 brackets.
-void c2p_seed(mhd_ctx* c, const KrpBuf& kb, long long n, cudaStream_t s) {
-  const int mode = c->P.guess;
-  if (mode != 1 && mode != 2) return;
-  if (mode == 1)
-    timed(c, MHD_K_MLP, s, [&] { launch_mlp_infer(c->gfeat, n, c->nm, c->mlp_wb, c->mlp, c->glogmu, s, c->nsm); });
-  const long long g = std::max(1LL, std::min((n + 127) / 128, (long long)c->nsm * std::max(c->occ_krp[5], 1)));
-  timed(c, MHD_K_C2P, s, [&] {
-    launch_krp_seed(c->P, kb, c->glogmu, mode == 1 ? 1 : 0, (float)c->mlp_delta, c->dstats, s, (int)g);
+// network guess; 2: FP32 search from the plain bracket): the seed kernel,
+// which runs the network (mode 1) on features it forms from the prep's KRP
+// variables and the FP32 search, and turns status-4 cells into FP64 brackets.
+void c2p_seed_mode(mhd_ctx* c, const KrpBuf& kb, long long n, int mode, cudaStream_t s) {
+  const int occ = std::max(c->occ_seed[mode == 1 ? 1 : 0], 1);
+  const long long g = std::max(1LL, std::min((n + 127) / 128, (long long)c->nsm * occ));
+  timed(c, mode == 1 ? MHD_K_MLP : MHD_K_C2P, s, [&] {
+    launch_krp_seed(c->P, kb, mode == 1 ? 1 : 0, (float)c->mlp_delta, c->mlp_wb, c->mlp, c->nm, c->dstats, s,
+                    (int)g);
   });
+}
+void c2p_seed(mhd_ctx* c, const KrpBuf& kb, long long n, cudaStream_t s) {
+  if (c->P.guess == 1 || c->P.guess == 2) c2p_seed_mode(c, kb, n, c->P.guess, s);
 }
 
 int enqueue_c2p(mhd_ctx* c, cudaStream_t s, const Work& w, const long long* items) {
@@ -459,9 +448,8 @@ int enqueue_c2p(mhd_ctx* c, cudaStream_t s, const Work& w, const long long* item
   const mhd_ctx::Cfg& cp = c->cfg[T_C2P_PREP];
   const mhd_ctx::Cfg& cf = c->cfg[T_C2P_FIN];
   const int learned = (c->P.guess == 1 || c->P.guess == 2) ? 1 : 0;
-  float* feat = c->P.guess == 1 ? c->gfeat : nullptr;
   timed(c, MHD_K_C2P, s, [&] {
-    launch_krp_prep_block(w, c->P, kb, s, tgrid(c, T_C2P_PREP, items[W_C2P]), cp.threads, learned, feat);
+    launch_krp_prep_block(w, c->P, kb, s, tgrid(c, T_C2P_PREP, items[W_C2P]), cp.threads, learned, nullptr);
   });
   c2p_seed(c, kb, items[W_C2P], s);
   timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, c->dstats, s, c->g_solve); });
@@ -483,8 +471,7 @@ int enqueue_rhs(mhd_ctx* c, double dt, int stage, cudaStream_t s, const Work& w,
     KrpBuf kb = krp_view(c->krp, items[W_CELL]);
     timed(c, MHD_K_FOFC_FLAG, s, [&] {
       launch_krp_prep_fofc(w, c->P, g0, g1, be * dt, kb, s, tgrid(c, T_FOFC_PREP, items[W_CELL]),
-                           c->cfg[T_FOFC_PREP].threads, (c->P.guess == 1 || c->P.guess == 2) ? 1 : 0,
-                           c->P.guess == 1 ? c->gfeat : nullptr);
+                           c->cfg[T_FOFC_PREP].threads, (c->P.guess == 1 || c->P.guess == 2) ? 1 : 0, nullptr);
     });
     c2p_seed(c, kb, items[W_CELL], s);
     timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, c->dstats, s, c->g_solve); });
@@ -582,6 +569,20 @@ int enqueue_step(mhd_ctx* c, double dt, cudaStream_t s) {
   return MHD_OK;
 }
 
+// Counters added by one call (mhd_c2p, mhd_c2p_cells with a stats out-argument):
+// the device counters before and after its launches, both read after a
+// stream synchronisation.
+int stats_host(mhd_ctx* c, cudaStream_t s, unsigned long long* h) {
+  if (cudaMemcpyAsync(h, c->dstats, sizeof(unsigned long long) * MHD_NSTATS, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return MHD_ECUDA;
+  return cuda_ok(cudaStreamSynchronize(s));
+}
+void stats_diff(const unsigned long long* a, const unsigned long long* b, mhd_stats* out) {
+  long long* o = &out->cells;
+  for (int k = 0; k < MHD_NSTATS; k++) o[k] = (long long)(b[k] - a[k]);
+}
+static_assert(sizeof(mhd_stats) == MHD_NSTATS * sizeof(long long), "mhd_stats is MHD_NSTATS counters");
+
 }  // namespace
 
 extern "C" {
@@ -602,6 +603,8 @@ int mhd_init(const mhd_params* p, mhd_ctx** out) {
     delete c;
     return MHD_ECUDA;
   }
+  c->occ_seed[0] = occ_seed_kernel(0);
+  c->occ_seed[1] = occ_seed_kernel(1);
   for (int ti = 0; ti < 3; ti++) {
     const int th = 64 << ti;
     c->occ_t[T_C2P_PREP][ti] = occ_krp_kernel(0, th);
@@ -612,11 +615,11 @@ int mhd_init(const mhd_params* p, mhd_ctx** out) {
     c->occ_t[T_EMF][ti] = occ_update_kernel(0, th);
     c->occ_t[T_UPD][ti] = occ_update_kernel(1, th);
   }
-  if (cudaMalloc(&c->dstats, sizeof(unsigned long long) * 8) != cudaSuccess) {
+  if (cudaMalloc(&c->dstats, sizeof(unsigned long long) * MHD_NSTATS) != cudaSuccess) {
     delete c;
     return MHD_ENOMEM;
   }
-  if (cudaMemset(c->dstats, 0, sizeof(unsigned long long) * 8) != cudaSuccess) {
+  if (cudaMemset(c->dstats, 0, sizeof(unsigned long long) * MHD_NSTATS) != cudaSuccess) {
     cudaFree(c->dstats);
     delete c;
     return MHD_ECUDA;
@@ -808,38 +811,51 @@ int cells_grid(const mhd_ctx* c, long n, int occ) {
 
 }  // namespace
 
+namespace {
+int c2p_cells_enqueue(mhd_ctx* c, long n, double* cons, const double* Bd, const double* g, double* prim,
+                      unsigned char* flags, int* iters, cudaStream_t s);
+}
+
 extern "C" {
 
 int mhd_c2p_cells(mhd_ctx* c, long n, double* cons, const double* Bd, const double* g, double* prim,
-                  unsigned char* flags, int* iters, void* stream) {
+                  unsigned char* flags, int* iters, void* stream, mhd_stats* stats) {
   if (!c || n < 0 || (n > 0 && (!cons || !Bd || !g || !prim || !flags))) return MHD_EINVAL;
-  if (n == 0) return MHD_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long h0[MHD_NSTATS], h1[MHD_NSTATS];
+  int r = stats ? stats_host(c, s, h0) : MHD_OK;
+  if (!r && n > 0) r = c2p_cells_enqueue(c, n, cons, Bd, g, prim, flags, iters, s);
+  if (!r && stats) r = stats_host(c, s, h1);
+  if (!r && stats) stats_diff(h0, h1, stats);
+  return r;
+}
+
+}  // extern "C"
+
+namespace {
+int c2p_cells_enqueue(mhd_ctx* c, long n, double* cons, const double* Bd, const double* g, double* prim,
+                      unsigned char* flags, int* iters, cudaStream_t s) {
   // 0 plain, 1 learned + FP32 search, 2 FP32 search from the plain bracket;
   // independent cells have no previous root, so 3 solves as 0
   const int mode = c->P.guess == 3 ? 0 : c->P.guess;
   if (mode == 1 && !c->mlp_ready) return MHD_ENOMLP;
-  cudaStream_t s = (cudaStream_t)stream;
   KrpBuf kb;
   float *feat, *logmu;
   int r = cells_scratch(c, n, s, &kb, &feat, &logmu);
   if (r) return r;
   timed(c, MHD_K_C2P, s, [&] {
-    launch_krp_prep_cells(c->P, kb, cons, Bd, g, mode != 0 ? 1 : 0, mode == 1 ? feat : nullptr, s,
-                          cells_grid(c, n, c->occ_krp[5]));
+    launch_krp_prep_cells(c->P, kb, cons, Bd, g, mode != 0 ? 1 : 0, nullptr, s, cells_grid(c, n, c->occ_krp[5]));
   });
-  if (mode == 1)
-    timed(c, MHD_K_MLP, s, [&] { launch_mlp_infer(feat, n, c->nm, c->mlp_wb, c->mlp, logmu, s, c->nsm); });
-  if (mode != 0)
-    timed(c, MHD_K_C2P, s, [&] {
-      launch_krp_seed(c->P, kb, logmu, mode == 1 ? 1 : 0, (float)c->mlp_delta, c->dstats, s,
-                      cells_grid(c, n, c->occ_krp[5]));
-    });
+  if (mode != 0) c2p_seed_mode(c, kb, n, mode, s);
   timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, c->dstats, s, c->g_solve_cells()); });
   timed(c, MHD_K_C2P, s, [&] {
     launch_krp_finish_cells(c->P, kb, cons, Bd, g, prim, flags, iters, c->dstats, s, cells_grid(c, n, c->occ_krp[6]));
   });
   return cuda_ok(cudaGetLastError());
 }
+}  // namespace
+
+extern "C" {
 
 // ------------------------------------------------------------ learned guess
 int mhd_mlp_init(mhd_ctx* c, unsigned long long seed) {
@@ -1045,11 +1061,45 @@ int mhd_mlp_set(mhd_ctx* c, const float* state) {
   return cuda_ok(cudaDeviceSynchronize());
 }
 
-int mhd_c2p(mhd_ctx* c, const mhd_block* blocks, int nb, void* stream) {
+int mhd_mlp_save(mhd_ctx* c, void* blob, long bytes, long* size) {
+  if (size) *size = MHD_MLP_BLOB_BYTES;
+  if (!c || !c->mlp || !blob || bytes < (long)MHD_MLP_BLOB_BYTES) return MHD_EINVAL;
+  std::vector<float> st(MHD_MLP_NSTATE);
+  int r = mhd_mlp_get(c, st.data());
+  if (r) return r;
+  unsigned char* o = (unsigned char*)blob;
+  for (int i = 0; i < MLP_NPARAM; i++) {
+    const unsigned short h = __bfloat16_as_ushort(__float2bfloat16_rn(st[i]));
+    o[2 * i] = (unsigned char)(h & 0xff);
+    o[2 * i + 1] = (unsigned char)(h >> 8);
+  }
+  std::memcpy(o + 2 * MLP_NPARAM, st.data() + MLP_NPARAM, sizeof(float) * (MHD_MLP_NSTATE - MLP_NPARAM));
+  return MHD_OK;
+}
+
+int mhd_mlp_load(mhd_ctx* c, const void* bf16_weights, long bytes) {
+  if (!c || !bf16_weights || bytes != (long)MHD_MLP_BLOB_BYTES) return MHD_EINVAL;
+  const unsigned char* in = (const unsigned char*)bf16_weights;
+  std::vector<float> st(MHD_MLP_NSTATE);
+  for (int i = 0; i < MLP_NPARAM; i++) {
+    const unsigned short h = (unsigned short)(in[2 * i] | (in[2 * i + 1] << 8));
+    st[i] = __bfloat162float(__ushort_as_bfloat16(h));
+  }
+  std::memcpy(st.data() + MLP_NPARAM, in + 2 * MLP_NPARAM, sizeof(float) * (MHD_MLP_NSTATE - MLP_NPARAM));
+  return mhd_mlp_set(c, st.data());
+}
+
+int mhd_c2p(mhd_ctx* c, const mhd_block* blocks, int nb, void* stream, mhd_stats* stats) {
   if (!c) return MHD_EINVAL;
   int r = prepare(c, blocks, nb);
   if (r) return r;
-  return enqueue_c2p(c, (cudaStream_t)stream);
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long h0[MHD_NSTATS], h1[MHD_NSTATS];
+  if (stats && (r = stats_host(c, s, h0))) return r;
+  r = enqueue_c2p(c, s);
+  if (!r && stats) r = stats_host(c, s, h1);
+  if (!r && stats) stats_diff(h0, h1, stats);
+  return r;
 }
 
 int mhd_rhs(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, int stage, void* stream) {
@@ -1102,26 +1152,24 @@ int mhd_step(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, int graph, 
   return cuda_ok(cudaGraphLaunch(c->gexec, s));
 }
 
+int mhd_graph_step(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, void* stream) {
+  return mhd_step(c, blocks, nb, dt, 1, stream);
+}
+
 int mhd_read_stats(mhd_ctx* c, mhd_stats* out, void* stream) {
   if (!c || !out) return MHD_EINVAL;
-  unsigned long long h[8];
+  unsigned long long h[MHD_NSTATS];
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemcpyAsync(h, c->dstats, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ECUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ECUDA;
-  out->cells = (long long)h[0];
-  out->iters = (long long)h[1];
-  out->fails = (long long)h[2];
-  out->floors = (long long)h[3];
-  out->fofc_cells = (long long)h[4];
-  out->dmp_cells = (long long)h[5];
-  out->fofc_faces = (long long)h[6];
-  out->guess_fallbacks = (long long)h[7];
+  long long* o = &out->cells;
+  for (int k = 0; k < MHD_NSTATS; k++) o[k] = (long long)h[k];
   return MHD_OK;
 }
 
 int mhd_reset_stats(mhd_ctx* c, void* stream) {
   if (!c) return MHD_EINVAL;
-  return cuda_ok(cudaMemsetAsync(c->dstats, 0, sizeof(unsigned long long) * 8, (cudaStream_t)stream));
+  return cuda_ok(cudaMemsetAsync(c->dstats, 0, sizeof(unsigned long long) * MHD_NSTATS, (cudaStream_t)stream));
 }
 
 int mhd_scratch_copy(mhd_ctx* c, int b, int which, double* dst, long count, long* size, void* stream) {
@@ -1175,7 +1223,7 @@ int mhd_autotune(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, void* s
       switch (k) {
         case T_C2P_PREP:
           launch_krp_prep_block(w, c->P, kb, s, tgrid(c, k, it[W_C2P]), th, (c->P.guess == 1 || c->P.guess == 2) ? 1 : 0,
-                                c->P.guess == 1 ? c->gfeat : nullptr);
+                                nullptr);
           break;
         case T_C2P_FIN: launch_krp_finish_block(w, c->P, kb, c->dstats, s, tgrid(c, k, it[W_C2P]), th); break;
         case T_FX: case T_FY: case T_FZ:
@@ -1183,8 +1231,7 @@ int mhd_autotune(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, void* s
           break;
         case T_FOFC_PREP:
           launch_krp_prep_fofc(w, c->P, g0, g1, be * dt, kb, s, tgrid(c, k, it[W_CELL]), th,
-                               (c->P.guess == 1 || c->P.guess == 2) ? 1 : 0,
-                               c->P.guess == 1 ? c->gfeat : nullptr);
+                               (c->P.guess == 1 || c->P.guess == 2) ? 1 : 0, nullptr);
           break;
         case T_FOFC_FIN: launch_krp_finish_fofc(w, c->P, kb, c->dstats, s, tgrid(c, k, it[W_CELL]), th); break;
         case T_EMF: launch_emf(w, s, tgrid(c, k, it[W_EDGE]), th); break;

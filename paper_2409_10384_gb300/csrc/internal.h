@@ -57,9 +57,11 @@ void launch_mlp_adam(float* w, float* m, float* v, float* grad, float lr, int t,
 void launch_mlp_pack(const float* w, __nv_bfloat16* wb, cudaStream_t s);
 void launch_mlp_logmu(const KrpBuf& kb, float* out, cudaStream_t s, int nsm);
 void launch_mlp_stats(const float* feat, const float* target, long long n, double* acc, cudaStream_t s, int nsm);
-void launch_krp_seed(const Par& P, const KrpBuf& kb, const float* logmu, int learned, float delta,
-                     unsigned long long* stats, cudaStream_t s,
-                     int grid);
+// FP32 search and FP64 bracket of every status-4 cell; learned != 0: from the
+// network's guess, inferred in the same kernel (wb, w, nm: its operands)
+void launch_krp_seed(const Par& P, const KrpBuf& kb, int learned, float delta, const __nv_bfloat16* wb,
+                     const float* w, const MlpNorm& nm, unsigned long long* stats, cudaStream_t s, int grid);
+int occ_seed_kernel(int learned);
 int occupancy_c2p(int* per_sm);
 int occ_face_kernel(int kind, int threads);
 int occ_krp_kernel(int kind, int threads);

@@ -65,9 +65,6 @@ constexpr int NH = MLP_NH;
 // per-warp shared buffers (floats) of the training step
 constexpr int S_X = 0, S_H1 = 32 * 16, S_H2 = S_H1 + 32 * NH, S_DZ2 = S_H2 + 32 * NH, S_DZ1 = S_DZ2 + 32 * NH,
               S_Y = S_DZ1 + 32 * NH, S_T = S_Y + 32, S_WARP = S_T + 32;
-// inference: the second hidden layer overwrites the first (each 16-row tile of
-// the first is read into registers before its rows are overwritten)
-constexpr int I_X = 0, I_H = 32 * 16, I_Y = I_H + 32 * NH, I_WARP = I_Y + 32;
 
 // normalised features of the warp's 32 samples into Xs [32][16] (cols >= 5 zero)
 __device__ __forceinline__ void load_x(float* Xs, const float* feat, long long idx, bool valid, const MlpNorm& nm) {
@@ -133,24 +130,152 @@ __device__ __forceinline__ void warp_forward(const float* Xs, float* H1, float* 
 }  // namespace
 
 // ------------------------------------------------------------------ inference
-// out[i] = predicted log(mu) (de-normalised) for n samples
+// Inference keeps every activation in registers.  With m16n8k16 fragments the
+// accumulator of two neighbouring 8-column tiles of one layer holds, lane for
+// lane, the A operand of the next layer's 16-column k-tile (rows g and g+8,
+// columns 2t, 2t+1 and 2t+8, 2t+9 of lane (g, t)), so bias, activation and the
+// bf16 packing turn one layer's output into the next layer's input without
+// shared memory.  The activation is tanh.approx.bf16x2 on the packed pair; the
+// output layer (64 -> 1) is a dot product over the lane's 16 columns reduced
+// over the four lanes of a quad.  The weights sit in shared memory in fragment
+// order ([fragment][lane] words), so every operand load is one conflict-free
+// 32-bit load.
+struct NetSmem {
+  unsigned w1[8][2][32];      // B fragments of W1p [64][16]: [n-tile][reg][lane]
+  unsigned w2[4][8][2][32];   // B fragments of W2: [k-tile][n-tile][reg][lane]
+  float b1[8][2][32];         // b1 of the lane's two columns of each n-tile
+  float b2[8][2][32];
+  float w3[8][2][32];
+  float b3, ymean, ystd, pad_;
+  float fmean[MLP_NIN], finv[MLP_NIN];
+};
+constexpr size_t NET_XS_WORDS = 32 * 4;   // per warp: 32 rows of 8 bf16 inputs
+
+__device__ __forceinline__ unsigned bf2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<unsigned*>(&v);
+}
+__device__ __forceinline__ unsigned tanh_bf2(unsigned x) {
+  unsigned y;
+  asm("tanh.approx.bf16x2 %0, %1;" : "=r"(y) : "r"(x));
+  return y;
+}
+__device__ __forceinline__ float bf_lo(unsigned x) { return __uint_as_float(x << 16); }
+__device__ __forceinline__ float bf_hi(unsigned x) { return __uint_as_float(x & 0xffff0000u); }
+
+// Fill the fragment-ordered operands (every thread of the CTA takes part).
+__device__ void net_smem_fill(NetSmem& S, const __nv_bfloat16* __restrict__ wb, const float* __restrict__ w,
+                              const MlpNorm& nm) {
+  auto pk = [](__nv_bfloat16 a, __nv_bfloat16 b) {
+    return (unsigned)__bfloat16_as_ushort(a) | ((unsigned)__bfloat16_as_ushort(b) << 16);
+  };
+  for (int e = threadIdx.x; e < 8 * 2 * 32; e += blockDim.x) {
+    const int lane = e & 31, r = (e >> 5) & 1, nt = e >> 6;
+    const int g = lane >> 2, t = lane & 3, n = 8 * nt + g, k = 2 * t + 8 * r;
+    // W1p [64][16]: B(k, n) = W1p[n][k]
+    S.w1[nt][r][lane] = pk(wb[MLP_BF_W1 + n * 16 + k], wb[MLP_BF_W1 + n * 16 + k + 1]);
+    const int c = 8 * nt + 2 * t + r;   // column of this lane's value r
+    S.b1[nt][r][lane] = w[MLP_B1 + c];
+    S.b2[nt][r][lane] = w[MLP_B2 + c];
+    S.w3[nt][r][lane] = __bfloat162float(wb[MLP_BF_W3 + c]);
+  }
+  for (int e = threadIdx.x; e < 4 * 8 * 2 * 32; e += blockDim.x) {
+    const int lane = e & 31, r = (e >> 5) & 1, nt = (e >> 6) & 7, kt = e >> 9;
+    const int g = lane >> 2, t = lane & 3, n = 8 * nt + g, k = 16 * kt + 2 * t + 8 * r;
+    // W2 [64][64] (out, in): B(k, n) = W2[n][k]
+    S.w2[kt][nt][r][lane] = pk(wb[MLP_BF_W2 + n * MLP_NH + k], wb[MLP_BF_W2 + n * MLP_NH + k + 1]);
+  }
+  if (threadIdx.x == 0) {
+    S.b3 = w[MLP_B3];
+    S.ymean = nm.ymean;
+    S.ystd = nm.ystd;
+    for (int f = 0; f < MLP_NIN; f++) {
+      S.fmean[f] = nm.fmean[f];
+      S.finv[f] = nm.finv[f];
+    }
+  }
+}
+
+// The network on the warp's 32 samples: x[5] are the lane's raw features
+// (zeros for an unused lane); returns the lane's de-normalised prediction.
+// xs: this warp's NET_XS_WORDS words of shared memory.  Whole warp only.
+__device__ __forceinline__ float net_warp(const NetSmem& S, unsigned* xs, const float* x) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  float z[MLP_NIN];
+#pragma unroll
+  for (int f = 0; f < MLP_NIN; f++) z[f] = (x[f] - S.fmean[f]) * S.finv[f];
+  __syncwarp();
+  xs[4 * lane + 0] = bf2(z[0], z[1]);
+  xs[4 * lane + 1] = bf2(z[2], z[3]);
+  xs[4 * lane + 2] = bf2(z[4], 0.0f);
+  xs[4 * lane + 3] = 0u;
+  __syncwarp();
+  float ymine = 0.0f;
+#pragma unroll
+  for (int mt = 0; mt < 2; mt++) {
+    // layer 1: A = inputs of rows 16 mt + g and 16 mt + g + 8 (k >= 8 zero)
+    unsigned a[4] = {xs[4 * (16 * mt + g) + t], xs[4 * (16 * mt + g + 8) + t], 0u, 0u};
+    unsigned h1[4][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; nt++) {
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+      const unsigned b[2] = {S.w1[nt][0][lane], S.w1[nt][1][lane]};
+      mma16816(c, a, b);
+      const float bl = S.b1[nt][0][lane], bh = S.b1[nt][1][lane];
+      h1[nt >> 1][(nt & 1) * 2 + 0] = tanh_bf2(bf2(c[0] + bl, c[1] + bh));
+      h1[nt >> 1][(nt & 1) * 2 + 1] = tanh_bf2(bf2(c[2] + bl, c[3] + bh));
+    }
+    // layer 2 and the output dot product
+    float ylo = 0.0f, yhi = 0.0f;
+#pragma unroll
+    for (int nt = 0; nt < 8; nt++) {
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int kt = 0; kt < 4; kt++) {
+        const unsigned b[2] = {S.w2[kt][nt][0][lane], S.w2[kt][nt][1][lane]};
+        mma16816(c, h1[kt], b);
+      }
+      const float bl = S.b2[nt][0][lane], bh = S.b2[nt][1][lane];
+      const float ul = S.w3[nt][0][lane], uh = S.w3[nt][1][lane];
+      const unsigned r0 = tanh_bf2(bf2(c[0] + bl, c[1] + bh));
+      const unsigned r1 = tanh_bf2(bf2(c[2] + bl, c[3] + bh));
+      ylo = fmaf(ul, bf_lo(r0), fmaf(uh, bf_hi(r0), ylo));
+      yhi = fmaf(ul, bf_lo(r1), fmaf(uh, bf_hi(r1), yhi));
+    }
+    ylo += __shfl_xor_sync(0xffffffffu, ylo, 1);
+    ylo += __shfl_xor_sync(0xffffffffu, ylo, 2);
+    yhi += __shfl_xor_sync(0xffffffffu, yhi, 1);
+    yhi += __shfl_xor_sync(0xffffffffu, yhi, 2);
+    // row r of this M-tile lives in quad (r & 7): the low half for r < 8
+    const int r = lane & 15;
+    const float vl = __shfl_sync(0xffffffffu, ylo, 4 * (r & 7));
+    const float vh = __shfl_sync(0xffffffffu, yhi, 4 * (r & 7));
+    if ((lane >> 4) == mt) ymine = r < 8 ? vl : vh;
+  }
+  return (ymine + S.b3) * S.ystd + S.ymean;
+}
+
+size_t net_smem_bytes(int threads) { return sizeof(NetSmem) + sizeof(unsigned) * NET_XS_WORDS * (threads / 32); }
+
+// out[i] = predicted log(mu) for n samples of features [n][MLP_FSTRIDE]
 __global__ void __launch_bounds__(256) k_mlp_infer(const float* __restrict__ feat, long long n, MlpNorm nm,
                                                   const __nv_bfloat16* __restrict__ wb, const float* __restrict__ w,
                                                   float* __restrict__ out) {
-  extern __shared__ float smem[];
-  __nv_bfloat16* swb = (__nv_bfloat16*)smem;
-  float* sw0 = smem + (MLP_NBF + 1) / 2;
-  for (int i = threadIdx.x; i < MLP_NBF; i += blockDim.x) swb[i] = wb[i];
+  extern __shared__ __align__(16) unsigned char net_raw[];
+  NetSmem& S = *reinterpret_cast<NetSmem*>(net_raw);
+  unsigned* xs = reinterpret_cast<unsigned*>(net_raw + sizeof(NetSmem)) + NET_XS_WORDS * (threadIdx.x >> 5);
+  net_smem_fill(S, wb, w, nm);
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* sw = sw0 + warp * I_WARP;
+  const int lane = threadIdx.x & 31;
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-  for (long long base = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * 32; base < n; base += nwarps * 32) {
+  for (long long base = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n;
+       base += nwarps * 32) {
     const long long idx = base + lane;
-    load_x(sw + I_X, feat, idx, idx < n, nm);
-    warp_forward(sw + I_X, sw + I_H, sw + I_H, sw + I_Y, swb, w);
-    if (idx < n) out[idx] = sw[I_Y + lane] * nm.ystd + nm.ymean;
-    __syncwarp();
+    float x[MLP_NIN];
+#pragma unroll
+    for (int f = 0; f < MLP_NIN; f++) x[f] = idx < n ? feat[idx * MLP_FSTRIDE + f] : 0.0f;
+    const float y = net_warp(S, xs, x);
+    if (idx < n) out[idx] = y;
   }
 }
 
@@ -353,30 +478,61 @@ __device__ __forceinline__ float f32_mu_plus(const KSf& s) {
 }
 
 // Cells with status 4.  Starting pair: the network's guess mu_g and mu_g e^d
-// (learned = 1), or 0 and the FP32 mu+ (learned = 0).  Five (learned) or
-// eight FP32 secant steps give mu32; FP64 then evaluates f at mu32 and at mu32 (1 +- 4e-6)
-// towards the root.  A sign change is a bracket of relative width 4e-6; else
-// the bracket extends from the far point to 0 (f(0) < 0, no evaluation) or
-// 1 (f(1) >= 0 for a physical state).  The refill solve finishes from there.
-__global__ void __launch_bounds__(128) k_krp_seed(Par P, KrpBuf kb, const float* __restrict__ logmu, int learned,
-                                                  float delta, unsigned long long* stats) {
+// (learned = 1; the network runs here, on features formed in registers from
+// the cell's KRP variables), or 0 and the FP32 mu+ (learned = 0).  FP32 secant
+// steps (at most 5 from a guess, 8 from the plain bracket; they stop once a
+// step moves mu by less than 2^-21 mu) give mu32; FP64 then evaluates f at
+// mu32 and at mu32 (1 +- 4e-6) towards the root.  A sign change is a bracket
+// of relative width 4e-6; else the bracket extends from the far point to 0
+// (f(0) < 0, no evaluation) or 1 (f(1) >= 0 for a physical state).  The
+// refill solve finishes from there.  Warps take tiles of 32 consecutive cells
+// (the network is a warp-wide product).
+__global__ void __launch_bounds__(128) k_krp_seed(Par P, KrpBuf kb, int learned, float delta,
+                                                  const __nv_bfloat16* __restrict__ wb, const float* __restrict__ wf,
+                                                  MlpNorm nm, unsigned long long* stats) {
+  extern __shared__ __align__(16) unsigned char net_raw[];
+  NetSmem& S = *reinterpret_cast<NetSmem*>(net_raw);
+  unsigned* xs = reinterpret_cast<unsigned*>(net_raw + sizeof(NetSmem)) + NET_XS_WORDS * (threadIdx.x >> 5);
+  if (learned) {
+    net_smem_fill(S, wb, wf, nm);
+    __syncthreads();
+  }
   const long long n = kb.n;
-  unsigned s_fb = 0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    if (kb.st[i] != 4) continue;
+  const int lane = threadIdx.x & 31;
+  unsigned s_fb = 0, s_f32 = 0;
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long base = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n;
+       base += nwarps * 32) {
+    const long long i = base + lane;
+    const bool act = i < n && kb.st[i] == 4;
+    const unsigned any = __ballot_sync(0xffffffffu, act);
+    if (!any) continue;
     KS s;
     const double* w = kb.w;
-    s.qh = w[KW_QH * n + i]; s.r2 = w[KW_R2 * n + i]; s.b2 = w[KW_B2 * n + i];
-    s.rb2 = w[KW_RB2 * n + i]; s.rperp2 = w[KW_RP2 * n + i];
+    s.qh = s.r2 = s.b2 = s.rb2 = s.rperp2 = 0.0;
+    s.D = 1.0;
+    if (act) {
+      s.qh = w[KW_QH * n + i]; s.r2 = w[KW_R2 * n + i]; s.b2 = w[KW_B2 * n + i];
+      s.rb2 = w[KW_RB2 * n + i]; s.rperp2 = w[KW_RP2 * n + i];
+      s.D = w[KW_D * n + i];
+    }
     s.gam = P.gam; s.eps_min = P.eps_atm; s.vmax2 = P.vmax2;
-    s.D = w[KW_D * n + i];
+    float lg = 0.0f;
+    if (learned) {
+      float x[MLP_FSTRIDE];
+      krp_features(s, x);
+      if (!act)
+        for (int f = 0; f < MLP_NIN; f++) x[f] = S.fmean[f];
+      lg = net_warp(S, xs, x);
+    }
+    if (!act) continue;
     KSf sf;
     sf.qh = (float)s.qh; sf.r2 = (float)s.r2; sf.b2 = (float)s.b2; sf.rb2 = (float)s.rb2; sf.rp2 = (float)s.rperp2;
     sf.gam = (float)s.gam; sf.emin = fmaxf((float)s.eps_min, 1e-37f); sf.vmax2 = (float)s.vmax2;
     // FP32 secant from the starting pair
     float x0, x1;
     if (learned) {
-      x0 = __expf(logmu[i]);
+      x0 = __expf(lg);
       if (!(x0 > 1e-30f)) x0 = 1e-30f;
       if (x0 > 1.0f) x0 = 1.0f;
       x1 = fminf(x0 * __expf(delta), 1.0f);
@@ -386,14 +542,19 @@ __global__ void __launch_bounds__(128) k_krp_seed(Par P, KrpBuf kb, const float*
       x1 = f32_mu_plus(sf);
     }
     float f0 = f32_master(sf, x0), f1 = f32_master(sf, x1);
+    s_f32 += 2;
     const int nsteps = learned ? 5 : 8;
     for (int it = 0; it < nsteps; it++) {
       const float den = f1 - f0;
       if (den == 0.0f || !(f1 == f1)) break;
       float x2 = x1 - f1 * (x1 - x0) / den;
       if (!(x2 > 0.0f && x2 <= 1.0f)) x2 = 0.5f * (x1 + (f1 < 0.0f ? 1.0f : 0.0f));
+      const bool conv = fabsf(x2 - x1) <= 4.76837158e-7f * x1;   // 2^-21
       x0 = x1; f0 = f1;
-      x1 = x2; f1 = f32_master(sf, x2);
+      x1 = x2;
+      if (conv) break;
+      f1 = f32_master(sf, x2);
+      s_f32++;
     }
     double m32 = (double)x1;
     if (!(m32 > 1e-300 && m32 <= 1.0)) m32 = 0.5;
@@ -442,6 +603,7 @@ __global__ void __launch_bounds__(128) k_krp_seed(Par P, KrpBuf kb, const float*
     kb.st[i] = st;
   }
   warp_flush(&stats[7], s_fb);
+  warp_flush(&stats[8], s_f32);
 }
 
 // log(mu) of solved cells (training targets); NaN where the solve failed
@@ -455,14 +617,16 @@ __global__ void k_mlp_logmu(KrpBuf kb, float* out) {
 void launch_mlp_logmu(const KrpBuf& kb, float* out, cudaStream_t s, int nsm) {
   k_mlp_logmu<<<nsm * 4, 256, 0, s>>>(kb, out);
 }
-size_t mlp_infer_smem() { return sizeof(float) * ((MLP_NBF + 1) / 2 + 8 * I_WARP); }
+size_t mlp_infer_smem() { return net_smem_bytes(256); }
 size_t mlp_train_smem() { return sizeof(float) * ((MLP_NBF + 1) / 2 + MLP_NPARAM + 2 * S_WARP); }
 
 int mlp_setup_attrs() {
   cudaError_t e1 = cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_infer_smem());
   cudaError_t e2 =
       cudaFuncSetAttribute(k_mlp_train_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_train_smem());
-  return (e1 == cudaSuccess && e2 == cudaSuccess) ? 0 : -1;
+  cudaError_t e3 = cudaFuncSetAttribute(k_krp_seed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)net_smem_bytes(128));
+  return (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess) ? 0 : -1;
 }
 void launch_mlp_infer(const float* feat, long long n, const MlpNorm& nm, const __nv_bfloat16* wb, const float* w,
                       float* out, cudaStream_t s, int nsm) {
@@ -490,9 +654,14 @@ void launch_mlp_pack(const float* w, __nv_bfloat16* wb, cudaStream_t s) {
 void launch_mlp_stats(const float* feat, const float* target, long long n, double* acc, cudaStream_t s, int nsm) {
   k_mlp_stats<<<nsm * 4, 256, 0, s>>>(feat, target, n, acc);
 }
-void launch_krp_seed(const Par& P, const KrpBuf& kb, const float* logmu, int learned, float delta,
-                     unsigned long long* stats, cudaStream_t s, int grid) {
-  k_krp_seed<<<grid, 128, 0, s>>>(P, kb, logmu, learned, delta, stats);
+void launch_krp_seed(const Par& P, const KrpBuf& kb, int learned, float delta, const __nv_bfloat16* wb,
+                     const float* w, const MlpNorm& nm, unsigned long long* stats, cudaStream_t s, int grid) {
+  k_krp_seed<<<grid, 128, learned ? net_smem_bytes(128) : 0, s>>>(P, kb, learned, delta, wb, w, nm, stats);
+}
+int occ_seed_kernel(int learned) {
+  int o = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_krp_seed, 128, learned ? net_smem_bytes(128) : 0);
+  return o;
 }
 
 }  // namespace grmhd

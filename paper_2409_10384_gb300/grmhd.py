@@ -47,7 +47,7 @@ class mhd_block(C.Structure):
 class mhd_stats(C.Structure):
     _fields_ = [("cells", C.c_longlong), ("iters", C.c_longlong), ("fails", C.c_longlong),
                 ("floors", C.c_longlong), ("fofc_cells", C.c_longlong), ("dmp_cells", C.c_longlong),
-                ("fofc_faces", C.c_longlong), ("guess_fallbacks", C.c_longlong)]
+                ("fofc_faces", C.c_longlong), ("guess_fallbacks", C.c_longlong), ("fp32_evals", C.c_longlong)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -65,11 +65,12 @@ _SIGS = {
     "mhd_strerror": (C.c_char_p, [_I]),
     "mhd_init_block": (_I, [_VP, C.POINTER(mhd_block), C.POINTER(_VP), _VP]),
     "mhd_prim2cons": (_I, [_VP, _L, _VP, _VP, _VP, _VP, _VP]),
-    "mhd_c2p_cells": (_I, [_VP, _L, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
-    "mhd_c2p": (_I, [_VP, C.POINTER(mhd_block), _I, _VP]),
+    "mhd_c2p_cells": (_I, [_VP, _L, _VP, _VP, _VP, _VP, _VP, _VP, _VP, C.POINTER(mhd_stats)]),
+    "mhd_c2p": (_I, [_VP, C.POINTER(mhd_block), _I, _VP, C.POINTER(mhd_stats)]),
     "mhd_rhs": (_I, [_VP, C.POINTER(mhd_block), _I, _D, _I, _VP]),
     "mhd_rk_update": (_I, [_VP, C.POINTER(mhd_block), _I, _D, _I, _VP]),
     "mhd_step": (_I, [_VP, C.POINTER(mhd_block), _I, _D, _I, _VP]),
+    "mhd_graph_step": (_I, [_VP, C.POINTER(mhd_block), _I, _D, _VP]),
     "mhd_read_stats": (_I, [_VP, C.POINTER(mhd_stats), _VP]),
     "mhd_reset_stats": (_I, [_VP, _VP]),
     "mhd_scratch_copy": (_I, [_VP, _I, _I, _VP, _L, C.POINTER(_L), _VP]),
@@ -93,11 +94,14 @@ _SIGS = {
     "mhd_mlp_grad": (_I, [_VP, _VP, _VP, _L, _VP, C.POINTER(C.c_float), _VP]),
     "mhd_mlp_get": (_I, [_VP, _VP]),
     "mhd_mlp_set": (_I, [_VP, _VP]),
+    "mhd_mlp_save": (_I, [_VP, _VP, _L, C.POINTER(_L)]),
+    "mhd_mlp_load": (_I, [_VP, _VP, _L]),
 }
 MHD_NKERNEL = 12
 MLP_NPARAM = 4609
 MLP_NSTATE = 4609 + 13
 MLP_FSTRIDE = 8
+MLP_BLOB_BYTES = 2 * 4609 + 4 * 13
 
 
 def header_symbols() -> list:
@@ -278,14 +282,20 @@ class Context:
         check(self.L.mhd_prim2cons(self.h, n, _ptr(prim), _ptr(Bd), _ptr(g), _ptr(cons), _sptr(stream)),
               "mhd_prim2cons")
 
-    def c2p_cells(self, cons, Bd, g, prim, flags, iters=None, stream=None):
+    def c2p_cells(self, cons, Bd, g, prim, flags, iters=None, stream=None, stats=False):
+        """con2prim of independent cells; with stats=True returns the counters
+        this call added (the call then synchronises the stream)."""
         n = cons.shape[1]
+        st = mhd_stats() if stats else None
         check(self.L.mhd_c2p_cells(self.h, n, _ptr(cons), _ptr(Bd), _ptr(g), _ptr(prim), _ptr(flags),
-                                   _ptr(iters), _sptr(stream)), "mhd_c2p_cells")
+                                   _ptr(iters), _sptr(stream), C.byref(st) if stats else None), "mhd_c2p_cells")
+        return st.as_dict() if stats else None
 
-    def c2p(self, blocks, stream=None):
+    def c2p(self, blocks, stream=None, stats=False):
         arr, nb = self._blocks(blocks)
-        check(self.L.mhd_c2p(self.h, arr, nb, _sptr(stream)), "mhd_c2p")
+        st = mhd_stats() if stats else None
+        check(self.L.mhd_c2p(self.h, arr, nb, _sptr(stream), C.byref(st) if stats else None), "mhd_c2p")
+        return st.as_dict() if stats else None
 
     def rhs(self, blocks, dt, stage, stream=None):
         arr, nb = self._blocks(blocks)
@@ -304,6 +314,12 @@ class Context:
         arr, nb = self._blocks(blocks)
         mode = 2 if per_block else int(bool(graph))
         check(self.L.mhd_step(self.h, arr, nb, float(dt), mode, _sptr(stream)), "mhd_step")
+
+    def graph_step(self, blocks, dt, stream):
+        """mhd_graph_step: the captured full RK step (stream must not be the
+        legacy default stream)."""
+        arr, nb = self._blocks(blocks)
+        check(self.L.mhd_graph_step(self.h, arr, nb, float(dt), _sptr(stream)), "mhd_graph_step")
 
     def step_host(self, blk: DeviceBlock, host: dict, dt, stream=None, graph=False):
         """One RK step of a block whose state lives in (pinned) host memory:
@@ -438,6 +454,18 @@ class Context:
         st = np.ascontiguousarray(state, np.float32)
         assert st.size == MLP_NSTATE
         check(self.L.mhd_mlp_set(self.h, st.ctypes.data_as(C.c_void_p)), "mhd_mlp_set")
+
+    def mlp_save(self) -> bytes:
+        """The network as the BF16 weight blob of mhd_mlp_save."""
+        buf = (C.c_ubyte * MLP_BLOB_BYTES)()
+        n = C.c_long()
+        check(self.L.mhd_mlp_save(self.h, buf, MLP_BLOB_BYTES, C.byref(n)), "mhd_mlp_save")
+        return bytes(buf)[:n.value]
+
+    def mlp_load(self, blob: bytes):
+        """mhd_mlp_load of a BF16 weight blob."""
+        buf = (C.c_ubyte * len(blob)).from_buffer_copy(blob)
+        check(self.L.mhd_mlp_load(self.h, buf, len(blob)), "mhd_mlp_load")
 
     def launches(self) -> int:
         return int(self.L.mhd_kernel_launches(self.h))

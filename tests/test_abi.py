@@ -48,16 +48,33 @@ def test_null_and_bad_arguments_rejected_without_device(L):
         d.update(kw)
         p = grmhd.params(gamma=2.0, **d)
         assert L.mhd_init(C.byref(p), C.byref(h)) == -1, kw
-    assert L.mhd_c2p(None, None, 0, None) == -1
+    assert L.mhd_c2p(None, None, 0, None, None) == -1
+    assert L.mhd_c2p_cells(None, 1, None, None, None, None, None, None, None, None) == -1
     assert L.mhd_step(None, None, 1, 0.1, 0, None) == -1
+    assert L.mhd_graph_step(None, None, 1, 0.1, None) == -1
+    assert L.mhd_mlp_load(None, None, grmhd.MLP_BLOB_BYTES) == -1
+    assert L.mhd_mlp_save(None, None, 0, None) == -1
     assert L.mhd_kernel_launches(None) == 0
 
 
+def test_blob_size_matches_header():
+    import re
+    h = open(grmhd._build.ROOT + "/include/grmhd.h").read()
+    m = re.search(r"#define MHD_MLP_BLOB_BYTES \((\d+) \* (\d+) \+ (\d+) \* (\d+)\)", h)
+    assert m, "MHD_MLP_BLOB_BYTES"
+    a, b, c, d = (int(x) for x in m.groups())
+    assert a * b + c * d == grmhd.MLP_BLOB_BYTES == 2 * grmhd.MLP_NPARAM + 4 * (grmhd.MLP_NSTATE - grmhd.MLP_NPARAM)
+
+
 def test_struct_layouts_match_header():
-    # mhd_params: 9 doubles + 8 ints + 9 doubles (EOS); mhd_block: 3+1 ints, 3 doubles, 12 pointers; mhd_stats: 8 int64
+    # mhd_params: 9 doubles + 8 ints + 9 doubles (EOS); mhd_block: 3+1 ints, 3 doubles, 12 pointers;
+    # mhd_stats: MHD_NSTATS int64
+    import re
+    h = open(grmhd._build.ROOT + "/include/grmhd.h").read()
+    nst = int(re.search(r"#define MHD_NSTATS (\d+)", h).group(1))
     assert C.sizeof(grmhd.mhd_params) == 9 * 8 + 8 * 4 + 9 * 8
     assert C.sizeof(grmhd.mhd_block) == 16 + 24 + 12 * 8
-    assert C.sizeof(grmhd.mhd_stats) == 8 * 8
+    assert C.sizeof(grmhd.mhd_stats) == nst * 8 == 9 * 8
 
 
 def test_block_list_cache_follows_device_pointers():

@@ -1,5 +1,7 @@
 """Entry points of the C-ABI not covered by the parity files: pinned launch
-shapes, the per-kernel profile, the network state round trip."""
+shapes, the per-kernel profile, the network state round trip, the captured
+step entry point, the con2prim counters out-argument and the BF16 weight
+blob."""
 import numpy as np
 import pytest
 
@@ -87,3 +89,84 @@ def test_network_state_round_trip(G):
     b.mlp_set(st)
     assert np.array_equal(b.mlp_get(), st)
     assert torch.equal(a.mlp_infer(feat), b.mlp_infer(feat))
+
+
+def test_graph_step_entry_point_equals_ungraphed_step(G):
+    """mhd_graph_step (the captured full RK step) gives the bits of mhd_step
+    without a graph, on two calls (capture, then replay)."""
+    import torch
+    p = O.params(gamma=2.0, rho_atm=1e-12, T_atm=1e-10, f_thr=0.1, recon=2, rsolver=1, rk_order=3, fofc=1)
+    inp, ob = _star(G, p)
+    dt = 0.25 * inp.dx[0]
+    ctx = T._ctx(G, p)
+    a = U.to_device(G, ob)
+    b = U.to_device(G, ob)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            ctx.step([a], dt, stream=s)
+            ctx.graph_step([b], dt, s)
+    s.synchronize()
+    ga, gb = U.from_device(a), U.from_device(b)
+    for key in ("cons", "prim", "flags"):
+        assert np.array_equal(ga[key], gb[key]), key
+    for d in range(3):
+        assert np.array_equal(ga["bf"][d], gb["bf"][d])
+
+
+def test_c2p_stats_out_argument(G):
+    """The mhd_stats out-argument of mhd_c2p and mhd_c2p_cells holds the
+    counters the call added, as read_stats differences show them."""
+    import torch
+    p = O.params(gamma=2.0, rho_atm=1e-12, T_atm=1e-10, f_thr=0.1, recon=2, rsolver=1, rk_order=3, fofc=1)
+    inp, ob = _star(G, p, corner=(100, 56, 56))   # over the surface: floors fire
+    ctx = T._ctx(G, p)
+    a = U.to_device(G, ob)
+    before = ctx.read_stats()
+    st = ctx.c2p([a], stats=True)
+    after = ctx.read_stats()
+    assert st == {k: after[k] - before[k] for k in st}
+    assert st["cells"] == 22 ** 3 and st["floors"] > 0
+    prim, Bd, g = synth.c2p_stress(3000, seed=9)
+    q = O.params(gamma=2.0, rho_atm=1e-20, T_atm=1e-14, f_thr=0.0)
+    c2 = T._ctx(G, q)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    cons = torch.zeros((5, 3000), dtype=torch.float64, device="cuda")
+    c2.prim2cons(t(prim), t(Bd), t(g), cons)
+    pr = torch.zeros_like(cons)
+    fl = torch.zeros(3000, dtype=torch.uint8, device="cuda")
+    it = torch.zeros(3000, dtype=torch.int32, device="cuda")
+    st = c2.c2p_cells(cons, t(Bd), t(g), pr, fl, it, stats=True)
+    assert st["cells"] == 3000 and st["iters"] == int(it.sum().item())
+    st0 = c2.c2p_cells(cons[:, :0], t(Bd)[:, :0], t(g)[:, :0], pr[:, :0], fl[:0], None, stats=True)
+    assert all(v == 0 for v in st0.values())
+
+
+def test_network_bf16_blob_round_trip(G):
+    """mhd_mlp_save / mhd_mlp_load: the BF16 weight blob carries the network
+    to another context, which infers what a context holding the same
+    bf16-rounded parameters infers, and saves the same bytes again."""
+    import torch
+    from oracle import mlp as M
+    rng = np.random.default_rng(11)
+    a = G.Context(G.params())
+    st = np.zeros(G.MLP_NSTATE, np.float32)
+    st[:M.NPARAM] = rng.normal(size=M.NPARAM) * 0.2
+    st[M.NPARAM:M.NPARAM + 5] = rng.normal(size=5)
+    st[M.NPARAM + 5:M.NPARAM + 10] = 0.5 + rng.random(5)
+    st[M.NPARAM + 10:M.NPARAM + 13] = (-1.5, 2.0, 0.05)
+    a.mlp_set(st)
+    blob = a.mlp_save()
+    assert len(blob) == G.MLP_BLOB_BYTES
+    b = G.Context(G.params())
+    b.mlp_load(blob)
+    assert b.mlp_save() == blob
+    rounded = st.copy()
+    rounded[:M.NPARAM] = M.bf16_round(st[:M.NPARAM]).astype(np.float32)
+    c = G.Context(G.params())
+    c.mlp_set(rounded)
+    feat = torch.from_numpy(rng.normal(size=(777, 8)).astype(np.float32)).cuda()
+    assert torch.equal(b.mlp_infer(feat), c.mlp_infer(feat))
+    assert np.array_equal(b.mlp_get(), rounded)
+    with pytest.raises(RuntimeError):
+        b.mlp_load(blob[:-1])

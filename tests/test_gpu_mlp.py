@@ -1,6 +1,7 @@
 """Learned con2prim guess on the GPU: the tensor-core network against the FP64
-reference (forward and gradients), and the learned con2prim against the plain
-one and the oracle (same root, fewer FP64 iterations)."""
+reference (forward and gradients), and the learned con2prim against the same
+con2prim without the network (the plain bracket and the FP32 search from it)
+and the oracle: the same root, and what the network saves."""
 import numpy as np
 import pytest
 
@@ -33,30 +34,50 @@ def _state(p, fmean=None, finv=None, ym=0.0, ys=1.0, delta=0.1):
 
 
 def _bf16_forward(p, X):
-    """The reference forward with the tensor-core operand roundings: weights,
-    inputs and hidden activations rounded to bf16, FP64 elsewhere."""
+    """The reference forward with the inference kernel's roundings: weights
+    and inputs rounded to bf16; each hidden layer's pre-activation rounded to
+    bf16, then tanh, rounded to bf16 (the kernel's activation works on packed
+    bf16 pairs); FP64 elsewhere.  Also the first-order bound on the output
+    change when every activation moves by one bf16 unit in the last place
+    (tanh' <= 1): sum_n |w3_n| u(H2_n) + sum_n |w3_n| sum_k |W2_nk| u(H1_k),
+    with u(h) = 2^-8 |h| + 2^-11 (an ulp, relative, plus an absolute floor for
+    the approximate tanh near zero)."""
     W1, b1, W2, b2, w3, b3 = M.unpack(p)
     r = M.bf16_round
-    H1 = np.tanh(r(X) @ r(W1).T + b1)
-    H2 = np.tanh(r(H1) @ r(W2).T + b2)
-    return r(H2) @ r(w3) + b3
+    H1 = r(np.tanh(r(r(X) @ r(W1).T + b1)))
+    H2 = r(np.tanh(r(H1 @ r(W2).T + b2)))
+    y = H2 @ r(w3) + b3
+    u1, u2 = 2.0 ** -8 * np.abs(H1) + 2.0 ** -11, 2.0 ** -8 * np.abs(H2) + 2.0 ** -11
+    bound = u2 @ np.abs(r(w3)) + (u1 @ np.abs(r(W2)).T) @ np.abs(r(w3))
+    return y, bound
 
 
 def test_forward_matches_reference(G):
+    """The register-chained tensor-core inference against the FP64 reference
+    with the same bf16 roundings, within the one-ulp-per-activation bound (and
+    within 5e-2 of the unrounded FP64 network)."""
     import torch
     rng = np.random.default_rng(1)
     p = (rng.normal(size=M.NPARAM) * 0.2).astype(np.float32)
     ctx = G.Context(G.params())
     ctx.mlp_set(_state(p))
-    n = 1000
+    n = 1000   # 31 full warp tiles and a ragged one
     X = rng.normal(size=(n, M.NIN)).astype(np.float32)
     feat = np.zeros((n, 8), np.float32)
     feat[:, :5] = X
     y = ctx.mlp_infer(torch.from_numpy(feat).cuda()).cpu().numpy()
-    ref = _bf16_forward(p.astype(np.float64), X.astype(np.float64))
-    assert np.max(np.abs(y - ref)) < 2e-3 * (1 + np.abs(ref).max())
+    ref, bound = _bf16_forward(p.astype(np.float64), X.astype(np.float64))
+    err = np.abs(y - ref)
+    assert np.all(err <= 2.0 * bound + 1e-5 * (1 + np.abs(ref))), float((err / bound).max())
     ref64, _ = M.forward(p.astype(np.float64), X.astype(np.float64))
     assert np.max(np.abs(y - ref64)) < 5e-2 * (1 + np.abs(ref64).max())
+    # a row depends on its own features only: the same sample alone, and in
+    # another lane of another tile, gives the same bits
+    one = ctx.mlp_infer(torch.from_numpy(feat[7:8].copy()).cuda()).cpu().numpy()
+    assert one[0] == y[7]
+    sh = np.roll(feat, 45, axis=0)
+    ysh = ctx.mlp_infer(torch.from_numpy(sh).cuda()).cpu().numpy()
+    assert np.array_equal(np.roll(y, 45), ysh)
 
 
 def test_gradients_match_reference(G):
@@ -91,7 +112,64 @@ def _cells(G, n, seed):
     return prim, Bd, g, t(Bd), t(g), t(prim)
 
 
-def test_learned_con2prim_same_root_fewer_iterations(G):
+def _modes(G, ctx, kw, cons0, tB, tg, modes=(0, 1, 2)):
+    """con2prim of the same cells in each c2p_guess mode: {mode: (prim, flags,
+    FP64 evaluations per cell, counters)} (host arrays)."""
+    import torch
+    n = cons0.shape[1]
+    out = {}
+    for guess in modes:
+        ctx.set_params(G.params(**kw, c2p_guess=guess))
+        cc = cons0.clone()
+        pr = torch.zeros_like(cons0)
+        fl = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        it = torch.zeros(n, dtype=torch.int32, device="cuda")
+        st = ctx.c2p_cells(cc, tB, tg, pr, fl, it, stats=True)
+        out[guess] = (pr.cpu().numpy(), fl.cpu().numpy(), it.cpu().numpy(), st)
+        assert st["cells"] == n and st["iters"] == int(out[guess][2].sum())
+        assert (st["fp32_evals"] == 0) == (guess == 0), st
+        # cells whose FP32 root missed the 4e-6 bracket: none without a
+        # search, a small fraction with one
+        assert st["guess_fallbacks"] == 0 if guess == 0 else st["guess_fallbacks"] <= 0.1 * n, (guess, st)
+    return out
+
+
+def _same_root(a, b, cons, g, gm1):
+    """The same root: identical flags, primitives within the parity bars."""
+    pa, fa = a[0], a[1]
+    pb, fb = b[0], b[1]
+    assert np.array_equal(fa, fb)
+    det = g[0] * (g[3] * g[5] - g[4] ** 2) - g[1] * (g[1] * g[5] - g[4] * g[2]) + g[2] * (g[1] * g[4] - g[3] * g[2])
+    scale = gm1 * np.abs(cons[0] + cons[4]) / np.sqrt(det)
+    W = np.sqrt(1 + (pb[1:4] ** 2).sum(0))
+    assert np.max(np.abs(pa[0] - pb[0]) / pb[0]) < 1e-10
+    assert np.max(np.abs(pa[1:4] - pb[1:4]) / W) < 1e-10
+    assert np.all(np.abs(pa[4] - pb[4]) <= 1e-10 * np.abs(pb[4]) + 1e-12 * scale)
+
+
+def _train(ctx, cons, B, g, vcons, vB, vg, epochs=30):
+    import torch
+    feat, logmu = ctx.mlp_dataset(cons, B, g)
+    ok = torch.isfinite(logmu)
+    ctx.mlp_init(3)
+    loss = ctx.mlp_train(feat[ok].contiguous(), logmu[ok].contiguous(), epochs=epochs, batch=4096, lr=3e-3)
+    vf, vl = ctx.mlp_dataset(vcons, vB, vg)
+    ok = torch.isfinite(vl)
+    delta = ctx.mlp_calibrate(vf[ok].contiguous(), vl[ok].contiguous(), 0.95)
+    return loss, delta
+
+
+def test_learned_con2prim_against_the_method_without_the_network(G):
+    """The learned guess (c2p_guess 1) against the same con2prim without the
+    network: the plain FP64 bracket (0) and the FP32 search from the plain
+    bracket (2), on the stress cells (network trained on disjoint seeds).
+    All three give the same root within the 1e-10 bar.  The network only
+    moves where the FP32 search starts; both searched modes hand the FP64
+    solve a bracket of relative width 4e-6 around an FP32 root, so the FP64
+    evaluations agree within 10% and are well below the plain solve's.  On
+    these cells (bracket half-width ~0.05 in log mu) the secant from the
+    plain bracket converges as fast as from the guess: the FP32 evaluations
+    are printed, not asserted lower (the binary states below show the gain)."""
     import torch
     p = O.params(gamma=2.0, rho_atm=1e-20, T_atm=1e-14, f_thr=0.0)
     kw = {k: getattr(p, k) for k, _ in p._fields_ if k != "pad_"}
@@ -100,52 +178,78 @@ def test_learned_con2prim_same_root_fewer_iterations(G):
     _, _, _, dB, dg, dprim = _cells(G, 300000, 104)
     cons = torch.zeros_like(dprim)
     ctx.prim2cons(dprim, dB, dg, cons)
-    feat, logmu = ctx.mlp_dataset(cons, dB, dg)
-    assert torch.isfinite(logmu).all()
-    ctx.mlp_init(3)
-    loss = ctx.mlp_train(feat, logmu, epochs=30, batch=4096, lr=3e-3)
-    assert loss < 0.02
     _, _, _, vB, vg, vprim = _cells(G, 100000, 105)
     vcons = torch.zeros_like(vprim)
     ctx.prim2cons(vprim, vB, vg, vcons)
-    vf, vl = ctx.mlp_dataset(vcons, vB, vg)
-    delta = ctx.mlp_calibrate(vf, vl, 0.95)
+    loss, delta = _train(ctx, cons, dB, dg, vcons, vB, vg)
+    assert loss < 0.02
     assert 0 < delta < 0.3
-    # test set: plain vs learned vs oracle
+    # test set: plain vs learned vs FP32 search vs oracle
     n = 50000
     prim, Bd, g, tB, tg, tprim = _cells(G, n, 106)
     c0 = torch.zeros_like(tprim)
     ctx.prim2cons(tprim, tB, tg, c0)
-    out = {}
-    for guess in (0, 1, 2):
-        ctx.set_params(G.params(**kw, c2p_guess=guess))
-        cc = c0.clone()
-        pr = torch.zeros_like(tprim)
-        fl = torch.zeros(n, dtype=torch.uint8, device="cuda")
-        it = torch.zeros(n, dtype=torch.int32, device="cuda")
-        ctx.reset_stats()
-        ctx.c2p_cells(cc, tB, tg, pr, fl, it)
-        st = ctx.read_stats()
-        out[guess] = (pr.cpu().numpy(), fl.cpu().numpy(), it.cpu().numpy())
-        # cells whose FP32 root missed the 4e-6 bracket: none without a guess,
-        # a small fraction with one
-        assert st["cells"] == n
-        assert st["guess_fallbacks"] == 0 if guess == 0 else st["guess_fallbacks"] <= 0.1 * n, (guess, st)
-    p0, f0, i0 = out[0]
+    out = _modes(G, ctx, kw, c0, tB, tg)
     cons = c0.cpu().numpy()
-    det = g[0] * (g[3] * g[5] - g[4] ** 2) - g[1] * (g[1] * g[5] - g[4] * g[2]) + g[2] * (g[1] * g[4] - g[3] * g[2])
-    scale = (p.gamma - 1) * (cons[0] + cons[4]) / np.sqrt(det)
-    W = np.sqrt(1 + (p0[1:4] ** 2).sum(0))
     ref = O.c2p_cells(p, cons, Bd, g)
     for guess in (1, 2):
-        p1, f1, i1 = out[guess]
-        # the same root: identical flags, primitives within the parity bars
-        assert np.array_equal(f0, f1)
-        assert np.max(np.abs(p1[0] - p0[0]) / p0[0]) < 1e-10
-        assert np.max(np.abs(p1[1:4] - p0[1:4]) / W) < 1e-10
-        assert np.all(np.abs(p1[4] - p0[4]) <= 1e-10 * np.abs(p0[4]) + 1e-12 * scale)
-        assert np.max(np.abs(p1[0] - ref["prim"][0]) / ref["prim"][0]) < 1e-10
-    # FP64 evaluations of the master function per cell (plain: + the mu+ steps)
-    print("FP64 evaluations per cell: plain %.2f  learned %.2f  fp32-search %.2f"
-          % (i0.mean(), out[1][2].mean(), out[2][2].mean()))
-    assert out[1][2].mean() < i0.mean()
+        _same_root(out[guess], out[0], cons, g, p.gamma - 1)
+        assert np.max(np.abs(out[guess][0][0] - ref["prim"][0]) / ref["prim"][0]) < 1e-10
+    _same_root(out[1], out[2], cons, g, p.gamma - 1)     # learned against the method without the network
+    ev = {k: float(out[k][2].mean()) for k in (0, 1, 2)}
+    f32 = {k: out[k][3]["fp32_evals"] / n for k in (1, 2)}
+    print("stress cells, FP64 evaluations per cell: plain %.3f  learned %.3f  fp32-search %.3f;  FP32 evaluations "
+          "per cell: learned %.2f  fp32-search %.2f (delta %.3g)" % (ev[0], ev[1], ev[2], f32[1], f32[2], delta))
+    assert ev[1] < 0.7 * ev[0] and ev[2] < 0.7 * ev[0]
+    assert abs(ev[1] - ev[2]) <= 0.1 * ev[2], ev
+
+
+def test_learned_guess_on_binary_states_saves_fp32_work(G):
+    """What the trained network gains over the method without it, on the
+    states the solver evolves: cells of blocks around the two moving stars of
+    the binary workload (v^y = -+0.15, dynamical metric), the network trained
+    on cells of other blocks and calibrated on a third set.  The root is the
+    same as without the network (1e-10 bar), the FP64 evaluations stay within
+    10% of the FP32 search's, and the network's start cuts the FP32
+    evaluations of the search by at least 20%."""
+    import torch
+    p = O.params(gamma=2.0, rho_atm=1e-12, T_atm=1e-10, f_thr=0.1)
+    kw = {k: getattr(p, k) for k, _ in p._fields_ if k != "pad_"}
+    ctx = G.Context(G.params(**kw, c2p_guess=0))
+    st = synth.spacetime(5, centres=((-15.0, 0.0, 0.0), (15.0, 0.0, 0.0)), vy=(-0.15, 0.15))
+
+    def cells(x0s, n=16, dx=0.375):
+        cs, bs, gs = [], [], []
+        for x0 in x0s:
+            inp = synth.star_block(st, (n,) * 3, 4, (dx,) * 3, x0)
+            db = G.DeviceBlock(inp.n, inp.ng, inp.dx, inp.adm)
+            db.prim.copy_(torch.from_numpy(inp.prim))
+            ctx.init_block(db, [torch.from_numpy(a).cuda() for a in inp.A])
+            cs.append(db.cons.reshape(5, -1))
+            bs.append(db.bcc.reshape(3, -1))
+            gs.append(db.adm.reshape(16, -1)[4:10])
+        return (torch.cat(cs, 1).contiguous(), torch.cat(bs, 1).contiguous(), torch.cat(gs, 1).contiguous())
+
+    # block corners around the star at x = +15 (core, inner and outer layers,
+    # surface) and the one at x = -15; disjoint sets for training,
+    # calibration and test
+    train = [(15.0 + a, b, c) for a in (-9.0, -3.0, 3.0, 9.0) for b in (-9.0, 3.0) for c in (-6.0, 0.0)] + \
+            [(-15.0 + a, b, -3.0) for a in (-6.0, 6.0) for b in (-6.0, 0.0)] + [(30.0, 0.0, 0.0), (40.0, 5.0, 5.0)]
+    calib = [(15.0 + a, -3.0, 3.0) for a in (-6.0, 0.0, 6.0)] + [(-12.0, 2.0, 2.0)]
+    test = [(12.0, -1.0, -2.0), (18.5, 1.0, 2.0), (-18.0, -2.0, 1.0), (33.0, -3.0, -3.0)]
+    c, b, g = cells(train)
+    vc, vb, vg = cells(calib)
+    loss, delta = _train(ctx, c, b, g, vc, vb, vg)
+    assert delta < 0.02, delta
+    tc, tb, tg = cells(test)
+    out = _modes(G, ctx, kw, tc, tb, tg, modes=(0, 1, 2))
+    n = tc.shape[1]
+    cons, gh = tc.cpu().numpy(), tg.cpu().numpy()
+    _same_root(out[1], out[2], cons, gh, p.gamma - 1)
+    _same_root(out[1], out[0], cons, gh, p.gamma - 1)
+    ev = {k: float(out[k][2].mean()) for k in (0, 1, 2)}
+    f32 = {k: out[k][3]["fp32_evals"] / n for k in (1, 2)}
+    print("binary states, FP64 evaluations per cell: plain %.3f  learned %.3f  fp32-search %.3f;  FP32 evaluations "
+          "per cell: learned %.2f  fp32-search %.2f (delta %.3g)" % (ev[0], ev[1], ev[2], f32[1], f32[2], delta))
+    assert abs(ev[1] - ev[2]) <= 0.1 * ev[2], ev
+    assert f32[1] < 0.8 * f32[2], f32
