@@ -68,6 +68,7 @@ class _Block(C.Structure):
         ("cons", C.c_void_p), ("cons0", C.c_void_p), ("prim", C.c_void_p),
         ("bf", C.c_void_p * 3), ("bf0", C.c_void_p * 3), ("bcc", C.c_void_p), ("adm", C.c_void_p),
         ("flags", C.c_void_p), ("flux", C.c_void_p * 3), ("emf", C.c_void_p * 3), ("fofc_mask", C.c_void_p),
+        ("n_override", C.c_int), ("ov_face", C.c_void_p), ("ov_flux", C.c_void_p),
     ]
 
 
@@ -100,6 +101,9 @@ def lib(counting: bool = False):
             L.or_stage.argtypes = [C.POINTER(_Block), C.POINTER(Params), C.c_double, C.c_int, C.POINTER(Stats)]
             L.or_stage.restype = C.c_int
             L.or_recon_line.argtypes = [C.c_int, C.c_long, C.c_void_p, C.c_void_p, C.c_void_p]
+            L.or_face_flux_at.argtypes = [C.POINTER(_Block), C.POINTER(Params), C.c_int, C.c_int, C.c_int, C.c_int,
+                                          C.c_void_p]
+            L.or_face_flux_at.restype = C.c_int
             L.or_face_side.argtypes = [C.POINTER(Params), C.c_int, C.c_void_p, C.c_double, C.c_void_p,
                                        C.c_void_p, C.c_void_p, C.c_void_p]
             L.or_face_flux.argtypes = [C.POINTER(Params), C.c_int, C.c_void_p, C.c_void_p, C.c_double,
@@ -225,7 +229,7 @@ class Block:
         b.bf0 = [x.copy() for x in self.bf0]
         return b
 
-    def _struct(self, flux=None, emf=None, mask=None) -> _Block:
+    def _struct(self, flux=None, emf=None, mask=None, override=None) -> _Block:
         s = _Block()
         s.n = (C.c_int * 3)(*self.n)
         s.ng = self.ng
@@ -238,6 +242,12 @@ class Block:
             s.flux[d] = _ptr(flux[d]) if flux is not None else None
             s.emf[d] = _ptr(emf[d]) if emf is not None else None
         s.fofc_mask = _ptr(mask)
+        s.n_override = 0
+        if override is not None:
+            faces, fl = override
+            s.n_override = len(faces)
+            s.ov_face = _ptr(faces)
+            s.ov_flux = _ptr(fl)
         return s
 
 
@@ -288,15 +298,22 @@ def c2p_block(p: Params, b: Block) -> dict:
 
 
 def stage(p: Params, b: Block, dt: float, stage_idx: int, mask: np.ndarray | None = None,
-          keep: bool = False, counting: bool = False):
+          keep: bool = False, counting: bool = False, override=None):
     """One RK stage in place.  Returns stats, plus fluxes/EMFs when keep=True.
-    ``mask`` (uint8 per cell) replaces the FOFC flags computed by the oracle."""
+    ``mask`` (uint8 per cell) replaces the FOFC flags computed by the oracle.
+    ``override``: [((d, k, j, i), F7), ...], faces whose high-order flux is
+    replaced by F7 before FOFC (a limiter decision taken down its other
+    branch; F7 from ``face_flux_at`` on data within rounding)."""
     flux = [np.zeros((7,) + b.face_shape(d)) for d in range(3)] if keep else None
     emf = [np.zeros(b.edge_shape(c)) for c in range(3)] if keep else None
     if mask is not None:
         mask = np.ascontiguousarray(mask, np.uint8)
+    ov = None
+    if override:
+        ov = (np.ascontiguousarray([[int(x) for x in f] for f, _ in override], np.int32),
+              np.ascontiguousarray([np.asarray(F, np.float64) for _, F in override], np.float64))
     st = Stats()
-    rc = lib(counting).or_stage(C.byref(b._struct(flux, emf, mask)), C.byref(p), float(dt), int(stage_idx),
+    rc = lib(counting).or_stage(C.byref(b._struct(flux, emf, mask, ov)), C.byref(p), float(dt), int(stage_idx),
                                 C.byref(st))
     if rc != 0:
         raise RuntimeError(f"or_stage failed with code {rc}")
@@ -346,6 +363,18 @@ def flop_counts(p: Params, b: Block, dt: float, stage_idx: int) -> dict:
     out = (C.c_longlong * 5)()
     L.or_flop_counts(out)
     return dict(zip(("add", "mul", "div", "sqrt", "cmp"), (int(x) for x in out)))
+
+
+def face_flux_at(p: Params, b: Block, d: int, face) -> np.ndarray:
+    """The high-order flux (Eq. 8, 7 components) of face (k, j, i) of
+    direction d from the block's primitives, cell-centred and face B~ and
+    metric as they stand (the caller fills prim and bcc, e.g. by c2p_block)."""
+    k, j, i = (int(x) for x in face)
+    F = np.zeros(7)
+    rc = lib().or_face_flux_at(C.byref(b._struct()), C.byref(p), int(d), k, j, i, _ptr(F))
+    if rc != 0:
+        raise ValueError(f"face ({d}, {k}, {j}, {i}) outside the block's stencil range")
+    return F
 
 
 def recon_line(recon: int, q: np.ndarray):

@@ -123,6 +123,13 @@ typedef struct {
   double* flux[3];   // optional out: [7][face array of that direction]
   double* emf[3];    // optional out: E_x [N3+1][N2+1][N1], E_y [N3+1][N2][N1+1], E_z [N3][N2+1][N1+1]
   const unsigned char* fofc_mask;  // optional in: replaces the computed FOFC flags
+  // optional in: n_override faces (direction, k, j, i in ov_face[4 q..4 q+3])
+  // whose high-order flux is replaced by ov_flux[7 q..7 q+6] before FOFC (a
+  // limiter decision taken down its other branch, each flux computed by
+  // or_face_flux_at on data within rounding of the stage's)
+  int n_override;
+  const int* ov_face;
+  const double* ov_flux;
 } or_block;
 
 typedef struct {
@@ -1414,6 +1421,14 @@ int or_stage(or_block* b, const or_params* p, double dt, int stage, or_stats* st
   PHASE(0);
   std::vector<double> flux[3];
   compute_fluxes(C, flux);
+  for (int q = 0; q < b->n_override; q++) {
+    const int* f4 = b->ov_face + 4 * q;
+    const int d = f4[0];
+    if (d < 0 || d > 2) return 3;
+    const long n = C.G.nface(d), f = C.G.f(d, f4[1], f4[2], f4[3]);
+    if (f < 0 || f >= n) return 3;
+    for (int c = 0; c < 7; c++) flux[d][c * n + f] = b->ov_flux[7 * q + c];
+  }
   PHASE(1);
   if (p->fofc) fofc(C, flux, g0, g1, be * dt, st);
   else PHASE(2);
@@ -1429,6 +1444,22 @@ int or_stage(or_block* b, const or_params* p, double dt, int stage, or_stats* st
   }
   update(C, flux, emf, g0, g1, be * dt);
   PHASE(5);
+  return 0;
+}
+
+// The high-order flux (Eq. 8) of one face of direction d at (k, j, i) from the
+// block's primitives, cell-centred and face B~ and metric as they stand.
+int or_face_flux_at(or_block* b, const or_params* p, int d, int k, int j, int i, double* F7) {
+  if (d < 0 || d > 2) return 1;
+  Ctx C(*p, b);
+  const int N[3] = {C.G.N1, C.G.N2, C.G.N3}, at[3] = {i, j, k};
+  for (int a = 0; a < 3; a++) {
+    const int lo = a == d ? 3 : 0, hi = a == d ? N[a] - 3 : N[a] - 1;   // stencil cells -3..+2 along d
+    if (at[a] < lo || at[a] > hi) return 2;
+  }
+  real F[7];
+  face_flux(C, d, k, j, i, false, F);
+  for (int c = 0; c < 7; c++) F7[c] = val(F[c]);
   return 0;
 }
 
