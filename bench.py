@@ -47,16 +47,23 @@ FLOPS_PER_UNIT = {"flux": 1576.0, "c2p": 450.0, "fofc_flag": 450.0, "fofc_fix": 
                   "emf": 36.1}
 FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (dense), the profiling recipe's unit table
 # DRAM bytes (read + write) per unit from ncu: the flux sweeps captured on the
-# 128^3 workload itself (one-pass metrics, profiles/ncu_full_star104_flux.md),
+# 128^3 workload itself (one-pass metrics, profiles/ncu_flux_star128_dram.md),
 # the update on the 96^3 case (profiles/ncu_full_star96_update.md), scaled to
 # a launch by its units.  The flux figures hold only at 128^3: the segment
 # lengths, and with them the x sweep's re-reads, depend on the size.
-TRAFFIC_PER_UNIT = {"flux_x": 309.4, "flux_y": 244.6, "flux_z": 242.8, "update": 585.0}
+TRAFFIC_PER_UNIT = {"flux_x": 295.6, "flux_y": 244.3, "flux_z": 241.5, "update": 585.0}
 TRAFFIC_SIZES = {"flux_x": (128,), "flux_y": (128,), "flux_z": (128,), "update": (96, 128)}
-# Kernels changed since their capture (the WENO-Z weight denominators became
-# explicit FMAs; no memory access changed): their traffic is reported as null,
-# with the last capture beside it, until they are captured again.
-TRAFFIC_STALE = {"flux_x", "flux_y", "flux_z"}
+# Kernels changed since their capture: their traffic is reported as null, with
+# the last capture beside it, until they are captured again.
+TRAFFIC_STALE = set()
+# FP64 thread instructions executed per face (ncu
+# sm__sass_thread_inst_executed_op_fp64_pred_on.sum per launch / faces, on the
+# 104^3 case, which has the 128^3 segment lengths; profiles/ncu_flux_star104_fp64.md),
+# for the issue-based fraction: executed FP64 instructions per second over
+# the pipe's 2 thread instructions per clock per SM at the sampled SM clock.
+FP64_INST_PER_UNIT = {"flux_x": 774.7, "flux_y": 743.5, "flux_z": 746.3}
+FP64_ISSUE_PER_CLK_SM = 2.0
+
 # Algorithmic HBM bytes per zone and RK stage of one fused pass: read U (5),
 # U^n (5), face B~ (3), face B~^n (3) and the ADM variables with K_ij (16),
 # write U (5) and face B~ (3) = 40 doubles; the first stage reads neither U^n
@@ -206,6 +213,88 @@ def train_guess(ctx, samples=1 << 20, epochs=30):
     return loss, delta, time.perf_counter() - t0
 
 
+def train_guess_blocks(ctx, blocks, per_block=640, epochs=30):
+    """Train the guess network on this block list's own states: cells sampled
+    from every block's con2prim region (conserved variables, cell-centred B~
+    and metric as the blocks hold them), solved by the plain con2prim;
+    calibrate the bracket half-width on a disjoint sample (95th percentile).
+    (loss, delta, seconds)"""
+    import torch
+    t0 = time.perf_counter()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(55)
+
+    def sample(k):
+        cs, bs, gs = [], [], []
+        for b in blocks:
+            N1, N2, N3 = b.N
+            ng = b.ng
+            # cells of the con2prim region (interior plus three ghost layers)
+            i = torch.randint(ng - 3, N1 - ng + 3, (k,), device="cuda", generator=gen)
+            j = torch.randint(ng - 3, N2 - ng + 3, (k,), device="cuda", generator=gen)
+            kk = torch.randint(ng - 3, N3 - ng + 3, (k,), device="cuda", generator=gen)
+            c = (kk * N2 + j) * N1 + i
+            cs.append(b.cons.reshape(5, -1)[:, c])
+            bs.append(b.bcc.reshape(3, -1)[:, c])
+            gs.append(b.adm.reshape(16, -1)[4:10, c])
+        return (torch.cat(cs, 1).contiguous(), torch.cat(bs, 1).contiguous(), torch.cat(gs, 1).contiguous())
+
+    dc, dB, dg = sample(per_block)
+    feat, logmu = ctx.mlp_dataset(dc, dB, dg)
+    ok = torch.isfinite(logmu)
+    feat, logmu = feat[ok].contiguous(), logmu[ok].contiguous()
+    ctx.mlp_init(3)
+    loss = ctx.mlp_train(feat, logmu, epochs=epochs, batch=4096, lr=3e-3)
+    vc, vB, vg = sample(per_block // 4)
+    vf, vl = ctx.mlp_dataset(vc, vB, vg)
+    ok = torch.isfinite(vl)
+    delta = ctx.mlp_calibrate(vf[ok].contiguous(), vl[ok].contiguous(), 0.95)
+    return loss, delta, time.perf_counter() - t0
+
+
+def periodic32_leg(G, steps=50):
+    """The 32^3 periodic flat block (Gamma 5/3, PLM + HLLE + CT, plain
+    con2prim, SSP-RK2): one RK2 step per iteration, launched directly and as
+    the captured graph, each with and without the periodic ghost fill
+    (mhd_fill_ghosts) before the step."""
+    import torch
+    from paper_2409_10384_gb300 import synth
+    p = dict(gamma=5.0 / 3.0, rho_atm=1e-12, T_atm=1e-10, f_thr=0.1, sigma_max=0.0, dmp_M=0.0, c2p_tol=1e-10,
+             W_max=1e3, recon=1, rsolver=1, fofc=0, rk_order=2, c2p_maxit=64, c2p_guess=0)
+    inp = synth.periodic_flat(1)
+    ctx = G.Context(G.params(**p))
+    blk = G.DeviceBlock(inp.n, inp.ng, inp.dx, inp.adm)
+    blk.prim.copy_(torch.from_numpy(inp.prim))
+    ctx.init_block(blk, [torch.from_numpy(a).cuda() for a in inp.A])
+    torch.cuda.synchronize()
+    dt = 0.25 / 32
+    nbr = [[0, 0, 0, 0, 0, 0]]
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    out = {"workload": "periodic32_flat_plm_hlle_ct_rk2", "zones": 32 ** 3}
+    for name, graph, fill in (("direct", False, False), ("graph", True, False), ("direct_with_fill", False, True),
+                              ("graph_with_fill", True, True)):
+        with torch.cuda.stream(stream):
+            for _ in range(5):
+                if fill:
+                    ctx.fill_ghosts([blk], nbr, stream)
+                ctx.step([blk], dt, graph=graph, stream=stream)
+            l0 = ctx.launches()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                if fill:
+                    ctx.fill_ghosts([blk], nbr, stream)
+                ctx.step([blk], dt, graph=graph, stream=stream)
+            e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"zone_cycles_per_s": 32 ** 3 / (ms * 1e-3), "ms_per_step": ms,
+                     "launches_per_step": (ctx.launches() - l0) / steps}
+    ctx.close()
+    return out
+
+
 def c2p_leg(G, n=1 << 24, reps=5):
     """con2prim on n independent stress cells (rho, T, W, sigma log-uniform,
     perturbed metric): the plain KRP solve, the learned guess (network trained
@@ -257,6 +346,7 @@ def c2p_leg(G, n=1 << 24, reps=5):
         Wt = torch.sqrt(1 + (ptrue[1:4] ** 2).sum(0))
         res[name] = {"cells_per_s": n / (float(np.median(ms)) * 1e-3), "ms": float(np.median(ms)),
                      "fp64_evals_per_cell": float(it.double().mean().item()),
+                     "fp32_evals_per_cell": st["fp32_evals"] / max(st["cells"], 1),
                      "fp64_evals_p99": int(it.sort().values[int(0.99 * (n - 1))].item()),
                      "guess_fallback_rate": st["guess_fallbacks"] / max(st["cells"], 1),
                      "fails": int(((fl & 1) != 0).sum().item()),
@@ -270,6 +360,9 @@ def c2p_leg(G, n=1 << 24, reps=5):
         res[name]["max_rel_diff_rho_vs_plain"] = float(((d[0] - p0[0]).abs() / p0[0]).max().item())
         res[name]["max_diff_w_over_W_vs_plain"] = float(((d[1:4] - p0[1:4]).abs() / W).max().item())
     res["speedup_learned_vs_plain"] = res["learned"]["cells_per_s"] / res["plain"]["cells_per_s"]
+    # the method without the network: the same FP32 search started from the plain bracket
+    res["speedup_learned_vs_fp32_search"] = res["learned"]["cells_per_s"] / res["fp32_search"]["cells_per_s"]
+    res["speedup_fp32_search_vs_plain"] = res["fp32_search"]["cells_per_s"] / res["plain"]["cells_per_s"]
     res.update({"cells": n, "tol": 1e-10, "train": {"samples": 1 << 20, "epochs": 30, "loss": loss,
                 "delta_q95": delta, "seconds": train_s}, "data": "synthetic stress cells (seeded)"})
     ctx.close()
@@ -342,7 +435,6 @@ def bns_leg(G, steps=3):
     specs, centres = synth.bns_blocks(seed=5)
     st = synth.spacetime(5, centres=centres, vy=(-0.15, 0.15))
     ctx = G.Context(G.params(**PARAMS, c2p_guess=0))
-    loss, delta, train_s = train_guess(ctx)
     blocks = []
     t0 = time.perf_counter()
     for sp in specs:
@@ -358,9 +450,11 @@ def bns_leg(G, steps=3):
     levels = {}
     for sp in specs:
         levels[str(sp.level)] = levels.get(str(sp.level), 0) + 1
+    loss, delta, train_s = train_guess_blocks(ctx, blocks)
     out = {"blocks": len(specs), "block_interior": 32, "levels": levels, "zones": zones, "stars": [list(c) for c in centres],
            "vy": [-0.15, 0.15], "generate_s": gen_s,
-           "guess_network": {"loss": loss, "delta_q95": delta, "train_s": train_s}}
+           "guess_network": {"loss": loss, "delta_q95": delta, "train_s": train_s,
+                             "data": "cons/prim pairs of this block list, solved by the plain con2prim"}}
     stream = torch.cuda.Stream()
     stream.wait_stream(torch.cuda.current_stream())
     # every mode starts from the same initial state
@@ -393,7 +487,11 @@ def bns_leg(G, steps=3):
         out[name] = {"zone_cycles_per_s": zones / (ms * 1e-3), "ms_per_step": ms,
                      "launches_per_step": (ctx.launches() - l0) // steps,
                      "c2p_fp64_evals_per_cell": sts["iters"] / max(sts["cells"], 1),
+                     "c2p_fp32_evals_per_cell": sts["fp32_evals"] / max(sts["cells"], 1),
                      "c2p_fails": sts["fails"], "fofc_cells_per_step": sts["fofc_cells"] / steps}
+    out["speedup_learned_vs_plain"] = out["learned"]["zone_cycles_per_s"] / out["plain"]["zone_cycles_per_s"]
+    out["speedup_learned_vs_fp32_search"] = (out["learned"]["zone_cycles_per_s"] /
+                                             out["fp32_search"]["zone_cycles_per_s"])
     # baryon-mass balance per block and step (learned guess, graph launches)
     restore()
     del snap
@@ -500,9 +598,9 @@ def run_ours(args):
             ctx.step([blk], dt, graph=False, stream=stream)
     stream.synchronize()
 
-    # device-timed region: inputs resident in HBM (working set ~1 GB > L2)
-    ctx.profile(True)
-    ctx.profile_read()
+    # device-timed region: inputs resident in HBM (working set ~1 GB > L2);
+    # no per-kernel events inside it
+    ctx.profile(False)
     ctx.reset_stats(stream)
     uuid = str(torch.cuda.get_device_properties(dev).uuid)
     clk = ClockSampler(uuid if uuid.startswith("GPU-") else f"GPU-{uuid}")
@@ -521,11 +619,23 @@ def run_ours(args):
     clocks = clk.stop()
     launches = ctx.launches() - launches0
     ms = e0.elapsed_time(e1)
-    prof = ctx.profile_read()
-    ctx.profile(False)
     stats = ctx.read_stats(stream)
     ms_max = max_over_ranks(ms, world, "cuda")
     value = world * zones * args.steps / (ms_max * 1e-3)
+
+    # a separate profiled pass (CUDA events around every launch, on the
+    # launch stream) for the per-kernel shares and the roofline's launch time
+    prof_steps = max(1, min(args.steps, 5))
+    ctx.profile(True)
+    ctx.profile_read()
+    ctx.reset_stats(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(prof_steps):
+            ctx.step([blk], dt, graph=False, stream=stream)
+    stream.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    pstats = ctx.read_stats(stream)
 
     # end-to-end through the public API with host buffers: each step copies the
     # state (cons, face B~) and the metric from pinned host memory, advances one
@@ -561,7 +671,7 @@ def run_ours(args):
     n = N_INT
     units = {"flux_x": (n + 1) * (n + 2) ** 2, "flux_y": (n + 1) * (n + 2) ** 2, "flux_z": (n + 1) * (n + 2) ** 2,
              "c2p": (n + 6) ** 3, "fofc_flag": n ** 3, "update": n ** 3, "emf": 3 * (n + 1) ** 2 * n,
-             "fofc_fix": max(stats["fofc_faces"] / max(kern.get("fofc_fix", (0, 1))[1], 1), 1.0)}
+             "fofc_fix": max(pstats["fofc_faces"] / max(kern.get("fofc_fix", (0, 1))[1], 1), 1.0)}
     key = "flux" if dom.startswith("flux") else dom
     flops = FLOPS_PER_UNIT.get(key, 0.0) * units.get(dom, 0)
     achieved = flops / (dom_ms / dom_n * 1e-3) / 1e12
@@ -569,9 +679,20 @@ def run_ours(args):
     traffic_last = None
     if dom in TRAFFIC_STALE:
         traffic, traffic_last = None, traffic
+    frac_issue = None
+    if dom in FP64_INST_PER_UNIT and n in TRAFFIC_SIZES.get(dom, ()) and clocks.get("sm_mhz"):
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        inst_rate = FP64_INST_PER_UNIT[dom] * units[dom] / (dom_ms / dom_n * 1e-3)
+        frac_issue = inst_rate / (FP64_ISSUE_PER_CLK_SM * nsm * clocks["sm_mhz"] * 1e6)
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": dom,
-                "peak_source": "nominal FP64 1.25 TFLOP/s (recipe unit table); FP64 is not in MEASURED_PEAKS.json",
+                "frac_issue": frac_issue,
+                "peak_source": "nominal FP64 1.25 TFLOP/s (recipe unit table; our DFMA probe reached 1.195); "
+                               "FP64 is not in MEASURED_PEAKS.json",
+                "achieved_source": "algorithmic FP64 operations of the op-counting oracle (add, mul, div, sqrt "
+                                   "each 1) x faces per launch / mean launch time from CUDA events",
+                "frac_issue_source": "ncu FP64 thread instructions per face x faces / launch time, over 2 per "
+                                     "clock per SM x SMs x the sampled SM clock",
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per unit (flux: the 128^3 "
                                   "workload, one pass; update: the 96^3 case), scaled by units",
                 "traffic_last_capture": traffic_last}
@@ -593,8 +714,13 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches), "launch_shapes": tuned, "roofline": roofline, "hbm_roofline": hbm, "kernel_share": shares,
             "c2p_stats": stats, "clocks": clocks}
+    line["profiled_pass"] = {"steps": prof_steps, "ms_per_step": sum(v[0] for v in kern.values()) / prof_steps,
+                             "note": "per-kernel CUDA events around every launch; the headline value is timed "
+                                     "without them"}
+    if not args.no_small and world == 1:
+        line["periodic32"] = periodic32_leg(G)
     if not args.no_c2p and world == 1:
-        line["c2p"] = c2p_leg(G)
+        line["c2p"] = c2p_leg(G, n=args.c2p_cells)
     if not args.no_amr and world == 1:
         line["amr512"] = amr_leg(G)
         torch.cuda.empty_cache()
@@ -623,6 +749,8 @@ def main():
     ap.add_argument("--no-c2p", action="store_true", help="skip the con2prim stress leg (profiling cases)")
     ap.add_argument("--no-amr", action="store_true", help="skip the batched AMR leg (profiling cases)")
     ap.add_argument("--no-bns", action="store_true", help="skip the binary-shaped leg (profiling cases)")
+    ap.add_argument("--no-small", action="store_true", help="skip the 32^3 periodic leg (profiling cases)")
+    ap.add_argument("--c2p-cells", type=int, default=1 << 24, help="cells of the con2prim leg (profiling cases)")
     args = ap.parse_args()
     global N_INT
     N_INT = args.n
