@@ -32,9 +32,13 @@ def pytest_terminal_summary(terminalreporter, exitstatus, config):
         prim = [k for k in r["bar"] if k in ("rho", "w1", "w2", "w3")]
         pl_c = [k for k in r["plain"] if k.startswith(("cons", "bf"))]
         pl_p = [k for k in r["plain"] if k.startswith("prim")]
-        f = lambda d, ks: max((d[k] for k in ks), default=0.0)
+        def f(d, ks):
+            if not ks:
+                return "0"
+            k = max(ks, key=lambda x: d[x])
+            return f"{d[k]:.2e} ({k})"
         tr.write_line(
-            f"{node}: calls {r['calls']}; cons+faceB bar {f(r['bar'], cons):.2e} | plain {f(r['plain'], pl_c):.2e}; "
-            f"prims bar {f(r['bar'], prim):.2e} (P/scale {r['bar'].get('P/bar', 0.0):.2f}) | plain "
-            f"{f(r['plain'], pl_p):.2e}; tie faces on the GPU's branch {r['ties']}; FOFC flags taken over "
+            f"{node}: calls {r['calls']}; cons+faceB bar {f(r['bar'], cons)} | plain {f(r['plain'], pl_c)}; "
+            f"prims bar {f(r['bar'], prim)}, P/scale {r['bar'].get('P/bar', 0.0):.2f} | plain "
+            f"{f(r['plain'], pl_p)}; tie faces on the GPU's branch {r['ties']}; FOFC flags taken over "
             f"{r['flips']}; cells excluded 0")
