@@ -45,6 +45,13 @@ C2P_GUESS = 0
 # for the FOFC estimate and the update, flagged face for the FOFC recompute.
 FLOPS_PER_UNIT = {"flux": 1576.0, "c2p": 450.0, "fofc_flag": 450.0, "fofc_fix": 595.0, "update": 443.5,
                   "emf": 36.1}
+# Of the flux's 1576, the face metric: the four-point interpolation of the ten
+# ADM variables (6 operations each) and, on each side, the determinant (14),
+# its square root (1) and the six inverse components (4 each) = 60 + 2 x 39.
+# The sweeps read it from the step's metric cache (k_metric_cache computes it
+# once per RK step), so a flux launch does 1576 - 138 of the oracle's operations
+# per face.
+FLOPS_FACE_METRIC = 138.0
 FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (dense), the profiling recipe's unit table
 # DRAM bytes (read + write) per unit from ncu: the flux sweeps captured on the
 # 128^3 workload itself (one-pass metrics, profiles/ncu_flux_star128_dram.md),
@@ -55,7 +62,7 @@ TRAFFIC_PER_UNIT = {"flux_x": 295.6, "flux_y": 244.3, "flux_z": 241.5, "update":
 TRAFFIC_SIZES = {"flux_x": (128,), "flux_y": (128,), "flux_z": (128,), "update": (96, 128)}
 # Kernels changed since their capture: their traffic is reported as null, with
 # the last capture beside it, until they are captured again.
-TRAFFIC_STALE = set()
+TRAFFIC_STALE = {"flux_x", "flux_y", "flux_z", "update"}
 # FP64 thread instructions executed per face (ncu
 # sm__sass_thread_inst_executed_op_fp64_pred_on.sum per launch / faces, on the
 # 104^3 case, which has the 128^3 segment lengths; profiles/ncu_flux_star104_fp64.md),
@@ -291,6 +298,19 @@ def periodic32_leg(G, steps=50):
         ms = e0.elapsed_time(e1) / steps
         out[name] = {"zone_cycles_per_s": 32 ** 3 / (ms * 1e-3), "ms_per_step": ms,
                      "launches_per_step": (ctx.launches() - l0) / steps}
+    # where a step's time goes: per-kernel CUDA events (direct launches), their
+    # sum against the step time of the graph (the rest is launch and drain)
+    ctx.profile(True)
+    ctx.profile_read()
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            ctx.step([blk], dt, graph=False, stream=stream)
+    stream.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    kern = {k: (v[0] / steps, v[1] // steps) for k, v in prof.items() if v[1] > 0}
+    out["kernels_ms_per_step"] = {k: round(v[0], 4) for k, v in kern.items()}
+    out["kernels_sum_ms_per_step"] = sum(v[0] for v in kern.values())
     ctx.close()
     return out
 
@@ -673,14 +693,15 @@ def run_ours(args):
              "c2p": (n + 6) ** 3, "fofc_flag": n ** 3, "update": n ** 3, "emf": 3 * (n + 1) ** 2 * n,
              "fofc_fix": max(pstats["fofc_faces"] / max(kern.get("fofc_fix", (0, 1))[1], 1), 1.0)}
     key = "flux" if dom.startswith("flux") else dom
-    flops = FLOPS_PER_UNIT.get(key, 0.0) * units.get(dom, 0)
+    flops = (FLOPS_PER_UNIT.get(key, 0.0) - (FLOPS_FACE_METRIC if key == "flux" else 0.0)) * units.get(dom, 0)
     achieved = flops / (dom_ms / dom_n * 1e-3) / 1e12
     traffic = TRAFFIC_PER_UNIT[dom] * units[dom] if n in TRAFFIC_SIZES.get(dom, ()) else None
     traffic_last = None
     if dom in TRAFFIC_STALE:
         traffic, traffic_last = None, traffic
     frac_issue = None
-    if dom in FP64_INST_PER_UNIT and n in TRAFFIC_SIZES.get(dom, ()) and clocks.get("sm_mhz"):
+    if dom in FP64_INST_PER_UNIT and dom not in TRAFFIC_STALE and n in TRAFFIC_SIZES.get(dom, ()) and \
+            clocks.get("sm_mhz"):
         nsm = torch.cuda.get_device_properties(dev).multi_processor_count
         inst_rate = FP64_INST_PER_UNIT[dom] * units[dom] / (dom_ms / dom_n * 1e-3)
         frac_issue = inst_rate / (FP64_ISSUE_PER_CLK_SM * nsm * clocks["sm_mhz"] * 1e6)

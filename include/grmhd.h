@@ -162,7 +162,9 @@ int mhd_c2p_cells(mhd_ctx* ctx, long n, double* cons, const double* Bd, const do
  * cons.  This is step 1 of a stage.  It also keeps sqrt(gamma), 1/sqrt(gamma)
  * and gamma^ij of every cell in context scratch for steps 2-5 of the same
  * stage, so the ADM arrays must not change between mhd_c2p and mhd_rk_update
- * of one stage (the metric is an input of the whole stage).  stats (host,
+ * of one stage (the metric is an input of the whole stage; it first computes
+ * the cell and face metric of the stage into context scratch, which the
+ * fluxes, the FOFC estimate and the update read).  stats (host,
  * may be NULL): the counters this call added, as in mhd_c2p_cells (the call
  * then synchronises the stream). */
 int mhd_c2p(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, void* stream, mhd_stats* stats);
@@ -177,7 +179,9 @@ int mhd_rhs(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, double dt, int s
  * also stores U and face B~ as U^n.  Requires mhd_rhs on the same blocks. */
 int mhd_rk_update(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, double dt, int stage, void* stream);
 
-/* A full RK step (rk_order stages of c2p, rhs, update).  Ghost zones are not
+/* A full RK step (rk_order stages of c2p, rhs, update).  The ADM variables are
+ * an input of the whole step: their cell and face metric is computed once,
+ * before the first stage, and every stage reads it.  Ghost zones are not
  * refreshed between stages (they keep their values).  graph = 0: each kernel
  * launched once per stage over all blocks; 1: the same launches captured once
  * into a CUDA graph per (block list, dt, parameters, stream) and replayed (the
@@ -280,7 +284,11 @@ int mhd_fill_ghosts(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, const in
                               FP32 search and the FP64 bracket (c2p_guess 1;
                               c2p_guess 2 counts its search under MHD_K_C2P) */
 #define MHD_K_LEDGER 11    /* baryon-mass ledger (only with mhd_ledger on) */
-#define MHD_NKERNEL 12
+#define MHD_K_METRIC 12    /* the step's metric: sqrt(gamma), gamma^ij of the con2prim
+                              region and the interpolated face metric (Eq. 8) of
+                              every swept face, once per RK step (mhd_step) or
+                              per mhd_c2p */
+#define MHD_NKERNEL 13
 
 /* enable != 0: bracket every kernel launched outside stream capture by CUDA
  * events on its own stream.  mhd_profile_read waits for them and returns, per

@@ -20,6 +20,7 @@ struct mhd_ctx {
   int occ_c2p[2] = {1, 1}, occ_face[5] = {1, 1, 1, 1, 1}, occ_upd[3] = {1, 1, 1};
   int occ_krp[7] = {1, 1, 1, 1, 1, 1, 1};
   int occ_seed[2] = {1, 1};   // seed kernel without / with the network
+  int occ_metric = 1;         // metric cache kernel
   // three-phase con2prim scratch: of the block list, and of independent cells
   char* krp = nullptr;
   long long krp_n = 0;
@@ -250,6 +251,8 @@ int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
     need += al256(sizeof(double) * 3 * b.ncell);
     need += al256((size_t)b.ncell);
     need += al256(sizeof(double) * 8 * (size_t)b.ncell);
+    for (int d = 0; d < 3; d++) need += al256(sizeof(double) * FMC_N * (size_t)fmc_count(s.n, d));
+    need += al256(sizeof(double) * DMC_N * (size_t)s.n[0] * s.n[1] * s.n[2]);
     if (c->P.guess == 3) need += al256(sizeof(double) * (size_t)b.ncell);
     const long long n0 = s.n[0], n1 = s.n[1], n2 = s.n[2];
     long long items[W_NKIND];
@@ -301,6 +304,12 @@ int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
     p += al256((size_t)b.ncell);
     b.mc = (double*)p;
     p += al256(sizeof(double) * 8 * (size_t)b.ncell);
+    for (int d = 0; d < 3; d++) {
+      b.fmc[d] = (double*)p;
+      p += al256(sizeof(double) * FMC_N * (size_t)fmc_count(b.n, d));
+    }
+    b.dmc = (double*)p;
+    p += al256(sizeof(double) * DMC_N * (size_t)b.n[0] * b.n[1] * b.n[2]);
     b.mu = nullptr;
     if (c->P.guess == 3) {
       b.mu = (double*)p;
@@ -442,8 +451,14 @@ void c2p_seed(mhd_ctx* c, const KrpBuf& kb, long long n, cudaStream_t s) {
   if (c->P.guess == 1 || c->P.guess == 2) c2p_seed_mode(c, kb, n, c->P.guess, s);
 }
 
-int enqueue_c2p(mhd_ctx* c, cudaStream_t s, const Work& w, const long long* items) {
+// refresh: first compute the metric cache of the step (cells and faces)
+int enqueue_c2p(mhd_ctx* c, cudaStream_t s, const Work& w, const long long* items, bool refresh) {
   if (c->P.guess == 1 && !c->mlp_ready) return MHD_ENOMLP;
+  if (refresh) {
+    const long long tot = items[W_C2P] + items[W_FX] + items[W_FY] + items[W_FZ] + items[W_CELL];
+    const long long g = std::max(1LL, std::min((tot + 255) / 256, (long long)c->nsm * std::max(c->occ_metric, 1)));
+    timed(c, MHD_K_METRIC, s, [&] { launch_metric_cache(w, s, (int)g); });
+  }
   KrpBuf kb = krp_view(c->krp, items[W_C2P]);
   const mhd_ctx::Cfg& cp = c->cfg[T_C2P_PREP];
   const mhd_ctx::Cfg& cf = c->cfg[T_C2P_FIN];
@@ -528,10 +543,10 @@ Work block_work(const mhd_ctx* c, int b) {
   return w;
 }
 
-int enqueue_c2p(mhd_ctx* c, cudaStream_t s) {
+int enqueue_c2p(mhd_ctx* c, cudaStream_t s, bool refresh) {
   long long it[W_NKIND];
   list_items(c, it);
-  return enqueue_c2p(c, s, work_of(c), it);
+  return enqueue_c2p(c, s, work_of(c), it, refresh);
 }
 int enqueue_rhs(mhd_ctx* c, double dt, int stage, cudaStream_t s) {
   long long it[W_NKIND];
@@ -551,7 +566,7 @@ int enqueue_step_per_block(mhd_ctx* c, double dt, cudaStream_t s) {
       long long it[W_NKIND];
       block_items(c, b, it);
       Work w = block_work(c, b);
-      int r = enqueue_c2p(c, s, w, it);
+      int r = enqueue_c2p(c, s, w, it, st == 0);
       if (!r) r = enqueue_rhs(c, dt, st, s, w, it);
       if (!r) r = enqueue_update(c, dt, st, s, w, it);
       if (r) return r;
@@ -559,9 +574,11 @@ int enqueue_step_per_block(mhd_ctx* c, double dt, cudaStream_t s) {
   return MHD_OK;
 }
 
+// The metric is an input of the whole step: its cache is computed once,
+// before the first stage.
 int enqueue_step(mhd_ctx* c, double dt, cudaStream_t s) {
   for (int st = 0; st < c->P.rk_order; st++) {
-    int r = enqueue_c2p(c, s);
+    int r = enqueue_c2p(c, s, st == 0);
     if (!r) r = enqueue_rhs(c, dt, st, s);
     if (!r) r = enqueue_update(c, dt, st, s);
     if (r) return r;
@@ -603,6 +620,7 @@ int mhd_init(const mhd_params* p, mhd_ctx** out) {
     delete c;
     return MHD_ECUDA;
   }
+  c->occ_metric = occ_metric_kernel();
   c->occ_seed[0] = occ_seed_kernel(0);
   c->occ_seed[1] = occ_seed_kernel(1);
   for (int ti = 0; ti < 3; ti++) {
@@ -1096,7 +1114,7 @@ int mhd_c2p(mhd_ctx* c, const mhd_block* blocks, int nb, void* stream, mhd_stats
   cudaStream_t s = (cudaStream_t)stream;
   unsigned long long h0[MHD_NSTATS], h1[MHD_NSTATS];
   if (stats && (r = stats_host(c, s, h0))) return r;
-  r = enqueue_c2p(c, s);
+  r = enqueue_c2p(c, s, true);
   if (!r && stats) r = stats_host(c, s, h1);
   if (!r && stats) stats_diff(h0, h1, stats);
   return r;
@@ -1198,7 +1216,7 @@ int mhd_autotune(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, void* s
   const bool prof = c->prof;
   c->prof = false;
   // valid inputs for every kernel: con2prim and the right-hand side of stage 0
-  r = enqueue_c2p(c, s);
+  r = enqueue_c2p(c, s, true);
   if (!r) r = enqueue_rhs(c, dt, 0, s);
   if (r) { c->prof = prof; return r; }
   long long it[W_NKIND];
@@ -1316,8 +1334,8 @@ int mhd_profile_read(mhd_ctx* c, double* ms, long long* count) {
 }
 
 const char* mhd_kernel_name(int kind) {
-  static const char* names[MHD_NKERNEL] = {"c2p", "flux_x", "flux_y", "flux_z", "fofc_flag",
-                                           "fofc_fix", "emf", "update", "faceb", "c2p_solve", "mlp", "ledger"};
+  static const char* names[MHD_NKERNEL] = {"c2p", "flux_x", "flux_y", "flux_z", "fofc_flag", "fofc_fix", "emf",
+                                           "update", "faceb", "c2p_solve", "mlp", "ledger", "metric"};
   return (kind >= 0 && kind < MHD_NKERNEL) ? names[kind] : "unknown";
 }
 

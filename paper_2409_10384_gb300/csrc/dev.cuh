@@ -57,11 +57,45 @@ struct DevBlock {
   int id;            // index of the block in its list
   double* mu;        // [ncell] con2prim root of the last stage-input con2prim
                      // (c2p_guess 3; 0: none), else null
-  double* mc;        // [8][ncell] metric of the stage region: sqrt(gamma),
-                     // 1/sqrt(gamma), gamma^ij; written by the stage-input
-                     // con2prim, read by the FOFC estimate and the update of
-                     // the same stage (null: each computes its own)
+  double* mc;        // [8][ncell] metric of the con2prim region: sqrt(gamma),
+                     // 1/sqrt(gamma), gamma^ij; written by k_metric_cache,
+                     // read by con2prim, the FOFC estimate and the update
+                     // (null: each computes its own)
+  double* dmc;       // [DMC_N][n0 n1 n2] centred derivatives of the ADM
+                     // variables at the interior cells (Eq. 9 sources),
+                     // written by k_metric_cache (null: the update takes them)
+  double* fmc[3];    // face metric of the faces the sweeps of direction d
+                     // visit ([FMC_N][fmc_count], fmc_index order); written
+                     // by k_metric_cache, read by k_flux (null: computed in
+                     // the sweep)
 };
+// Derivative cache: per axis a, the centred differences (q[+1] - q[-1]) / (2
+// dx_a) of alpha, beta^1..3 and gamma_ij at slots a * 10 + (0 .. 9).
+constexpr int DMC_N = 30;
+// Face metric cache: alpha, beta^1..3, gamma_ij (6), sqrt(gamma),
+// 1/sqrt(gamma) and gamma^{dd} of a face of direction d.
+constexpr int FMC_N = 13;
+// faces of direction d a stage sweeps: n_d + 1 along d, n + 2 across
+__host__ __device__ inline long long fmc_count(const int* n, int d) {
+  return (long long)(n[0] + (d == 0 ? 1 : 2)) * (n[1] + (d == 1 ? 1 : 2)) * (n[2] + (d == 2 ? 1 : 2));
+}
+// Face index (k,j,i) of item `loc` of direction d: along d the interior faces,
+// transversally one extra layer each side (the CT stencil needs them).
+template <int d>
+__host__ __device__ __forceinline__ void face_coords(const DevBlock& b, long long loc, int& k, int& j, int& i) {
+  const int L0 = b.n[0] + (d == 0 ? 1 : 2), L1 = b.n[1] + (d == 1 ? 1 : 2);
+  int a0 = loc % L0; long long r = loc / L0; int a1 = r % L1; int a2 = r / L1;
+  i = a0 + b.ng - (d == 0 ? 0 : 1);
+  j = a1 + b.ng - (d == 1 ? 0 : 1);
+  k = a2 + b.ng - (d == 2 ? 0 : 1);
+}
+// index of face (k,j,i) of direction d in its cache (the order of the
+// stage's face work items, face_coords: x fastest)
+__host__ __device__ inline long long fmc_index(const DevBlock& b, int d, int k, int j, int i) {
+  const int L0 = b.n[0] + (d == 0 ? 1 : 2), L1 = b.n[1] + (d == 1 ? 1 : 2);
+  const int a0 = i - b.ng + (d == 0 ? 0 : 1), a1 = j - b.ng + (d == 1 ? 0 : 1), a2 = k - b.ng + (d == 2 ? 0 : 1);
+  return ((long long)a2 * L1 + a1) * L0 + a0;
+}
 // Relative half-width of the bracket around a previous root (c2p_guess 3).
 constexpr double WARM_DELTA = 1e-3;
 
@@ -1162,6 +1196,47 @@ __device__ __forceinline__ void face_metric(const double* adm, long long nc, lon
 #pragma unroll
   for (int v = 0; v < 6; v++) fm.m.g[v] = mv[4 + v];
   metric_setup(fm.m);
+}
+
+// Centred derivatives of the ten ADM metric variables at cell c along each
+// axis (the derivative cache's slots), second order (Eq. 9 sources).
+__device__ __forceinline__ void adm_derivs(const DevBlock& b, long long c, double* D) {
+  const double* A = b.adm;
+  const long long nc = b.ncell;
+  const long long st[3] = {1, (long long)b.N[0], (long long)b.N[0] * b.N[1]};
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    const double h = 0.5 * b.idx[a];
+#pragma unroll
+    for (int v = 0; v < 10; v++) D[10 * a + v] = (A[v * nc + c + st[a]] - A[v * nc + c - st[a]]) * h;
+  }
+}
+
+// The face metric cache of direction d at index q (count n): store / load.
+template <int d>
+__device__ __forceinline__ void fmc_store(double* fc, long long n, long long q, const FaceMetric& fm) {
+  constexpr int gd = d == 0 ? 0 : (d == 1 ? 3 : 5);
+  fc[q] = fm.alpha;
+#pragma unroll
+  for (int a = 0; a < 3; a++) fc[(1 + a) * n + q] = fm.beta[a];
+#pragma unroll
+  for (int v = 0; v < 6; v++) fc[(4 + v) * n + q] = fm.m.g[v];
+  fc[10 * n + q] = fm.m.sdet;
+  fc[11 * n + q] = fm.m.isdet;
+  fc[12 * n + q] = fm.m.gi[gd];
+}
+// Only gamma^{dd} of the inverse is loaded: it is the one face_side reads.
+template <int d>
+__device__ __forceinline__ void fmc_load(const double* __restrict__ fc, long long n, long long q, FaceMetric& fm) {
+  constexpr int gd = d == 0 ? 0 : (d == 1 ? 3 : 5);
+  fm.alpha = fc[q];
+#pragma unroll
+  for (int a = 0; a < 3; a++) fm.beta[a] = fc[(1 + a) * n + q];
+#pragma unroll
+  for (int v = 0; v < 6; v++) fm.m.g[v] = fc[(4 + v) * n + q];
+  fm.m.sdet = fc[10 * n + q];
+  fm.m.isdet = fc[11 * n + q];
+  fm.m.gi[gd] = fc[12 * n + q];
 }
 
 // Flux through one face from its reconstructed (unfloored) states.

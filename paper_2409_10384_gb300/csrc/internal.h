@@ -16,7 +16,13 @@ void launch_c2p_cells(const Par& P, long long n, double* cons, const double* Bd,
                       unsigned char* flags, int* iters, const float* guess, unsigned long long* stats, cudaStream_t s,
                       int grid);
 void launch_c2p_block(const Work& w, const Par& P, unsigned long long* stats, cudaStream_t s, int grid);
+// flux sweeps reading the face metric cache (context path) / computing the
+// face metric in the sweep (allocation-free stage)
 void launch_flux_dir(int d, const Work& w, const Par& P, cudaStream_t s, int grid, int threads = 128);
+void launch_flux_dir_inline(int d, const Work& w, const Par& P, cudaStream_t s, int grid, int threads = 128);
+// metric of a step: cell cache (mc) of the con2prim region, face cache (fmc)
+void launch_metric_cache(const Work& w, cudaStream_t s, int grid);
+int occ_metric_kernel();
 void launch_fofc_flag(const Work& w, const Par& P, double g0, double g1, double bdt, unsigned long long* stats,
                       cudaStream_t s, int grid);
 void launch_fofc_fix(int d, const Work& w, const Par& P, unsigned long long* stats, cudaStream_t s, int grid);

@@ -2,20 +2,10 @@
 // the ADM metric interpolated to the face, and the first-order flux
 // correction of Sec. 3.3 with the relaxed DMP of Eq. 19.
 #include "dev.cuh"
+#include "flux_sweep.cuh"
 #include "internal.h"
 
 namespace grmhd {
-
-// Face index (k,j,i) of item `loc` of direction d: along d the interior faces,
-// transversally one extra layer each side (the CT stencil needs them).
-template <int d>
-__device__ __forceinline__ void face_coords(const DevBlock& b, long long loc, int& k, int& j, int& i) {
-  const int L0 = b.n[0] + (d == 0 ? 1 : 2), L1 = b.n[1] + (d == 1 ? 1 : 2);
-  int a0 = loc % L0; long long r = loc / L0; int a1 = r % L1; int a2 = r / L1;
-  i = a0 + b.ng - (d == 0 ? 0 : 1);
-  j = a1 + b.ng - (d == 1 ? 0 : 1);
-  k = a2 + b.ng - (d == 2 ? 0 : 1);
-}
 
 // First-order (donor cell) flux through face (k,j,i) of direction d.
 template <int d>
@@ -36,69 +26,6 @@ __device__ __forceinline__ void face_flux_donor(const DevBlock& b, const Par& P,
   const double Bn = b.bf[d][fidx(b, d, k, j, i)];
   if (P.eos == 0) face_flux_states<d, 0>(P, L, R, Bn, fm, F);
   else face_flux_states<d, 1>(P, L, R, Bn, fm, F);
-}
-
-// Fluxes of direction d, one thread per segment: the thread sweeps the cells
-// along d, reconstructing each once (order R) and finishing one face per cell.
-template <int d, int R, int E>
-__global__ void __launch_bounds__(256) k_flux(Work w, Par P) {
-  constexpr int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-  const long long* pre = w.pre + (long long)(W_SX + d) * (w.nblocks + 1);
-  const long long tot = pre[w.nblocks];
-  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < tot; it += (long long)gridDim.x * blockDim.x) {
-    const int bi = find_block(w, W_SX + d, it);
-    const DevBlock& b = w.blk[bi];
-    int k, j, i, nf;
-    seg_coords<d>(b, (int)(it - pre[bi]), k, j, i, nf);
-    const long long nc = b.ncell;
-    const long long st = d == 0 ? 1 : (d == 1 ? (long long)b.N[0] : (long long)b.N[0] * b.N[1]);
-    const long long fst = d == 0 ? 1 : (d == 1 ? (long long)b.N[0] : (long long)b.N[0] * b.N[1]);
-    const long long nfc = nface(b, d);
-    const double* src[7] = {b.prim, b.prim + nc, b.prim + 2 * nc, b.prim + 3 * nc, b.prim + 4 * nc,
-                            b.bcc + t1 * nc, b.bcc + t2 * nc};
-    long long c = cidx(b, k, j, i) - st;   // cell m below the first face
-    long long f = fidx(b, d, k, j, i);
-    RecVar rv[7];
-    double Ls[7];
-#pragma unroll
-    for (int v = 0; v < 7; v++) {
-      const double* a = src[v] + c;
-      rec_init<R>(rv[v], a[-2 * st], a[-st], a[0], a[st]);
-      if constexpr (R != 2) {
-        double lo;
-        rec_step<R>(rv[v], a[2 * st], lo, Ls[v]);
-      }
-    }
-    if constexpr (R == 2) {
-      double x[7], nh[7], nl[7], dh[7], dl[7], lo[7];
-#pragma unroll
-      for (int v = 0; v < 7; v++) wz_parts(rv[v], src[v][c + 2 * st], x[v], nh[v], nl[v], dh[v], dl[v]);
-      wz_finish<7>(x, nh, nl, dh, dl, Ls, lo);
-    }
-    for (int q = 0; q < nf; q++) {
-      c += st;
-      double Rs[7], Lnext[7];
-      if constexpr (R == 2) {
-        double x[7], nh[7], nl[7], dh[7], dl[7];
-#pragma unroll
-        for (int v = 0; v < 7; v++) wz_parts(rv[v], src[v][c + 2 * st], x[v], nh[v], nl[v], dh[v], dl[v]);
-        wz_finish<7>(x, nh, nl, dh, dl, Lnext, Rs);
-      } else {
-#pragma unroll
-        for (int v = 0; v < 7; v++) rec_step<R>(rv[v], src[v][c + 2 * st], Rs[v], Lnext[v]);
-      }
-      FaceMetric fm;
-      face_metric(b.adm, nc, c - st, st, fm);
-      double F[7];
-      face_flux_states<d, E>(P, Ls, Rs, b.bf[d][f], fm, F);
-      double* out = b.flux[d];
-#pragma unroll
-      for (int v = 0; v < 7; v++) out[v * nfc + f] = F[v];
-#pragma unroll
-      for (int v = 0; v < 7; v++) Ls[v] = Lnext[v];
-      f += fst;
-    }
-  }
 }
 
 __device__ __forceinline__ bool interior(const DevBlock& b, int k, int j, int i) {
@@ -200,26 +127,72 @@ __global__ void __launch_bounds__(128) k_fofc_fix(Work w, Par P, unsigned long l
   warp_flush(&stats[6], s_faces);
 }
 
-template <int d, int E>
-void launch_flux_r(const Work& w, const Par& P, cudaStream_t s, int grid, int threads) {
-  switch (P.recon) {
-    case 4: k_flux<d, 4, E><<<grid, threads, 0, s>>>(w, P); break;
-    case 3: k_flux<d, 3, E><<<grid, threads, 0, s>>>(w, P); break;
-    case 2: k_flux<d, 2, E><<<grid, threads, 0, s>>>(w, P); break;
-    case 1: k_flux<d, 1, E><<<grid, threads, 0, s>>>(w, P); break;
-    default: k_flux<d, 0, E><<<grid, threads, 0, s>>>(w, P); break;
+// The metric of one RK step (Z4c is not evolved: the ADM variables are an
+// input of the whole step): sqrt(gamma), 1/sqrt(gamma) and gamma^ij of every
+// cell of the con2prim region (DevBlock.mc), the interpolated face metric of
+// every face the flux sweeps visit (DevBlock.fmc) and the centred derivatives
+// of the metric at the interior cells (DevBlock.dmc, Eq. 9).  The context's RK step
+// runs it once, before its first stage; the stage-by-stage entry points run it
+// in every mhd_c2p.
+template <int d>
+__device__ __forceinline__ void face_metric_items(const Work& w) {
+  const long long* pre = w.pre + (long long)(W_FX + d) * (w.nblocks + 1);
+  const long long tot = pre[w.nblocks];
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < tot; it += (long long)gridDim.x * blockDim.x) {
+    const int bi = find_block(w, W_FX + d, it);
+    const DevBlock& b = w.blk[bi];
+    const long long loc = it - pre[bi];
+    int k, j, i;
+    face_coords<d>(b, loc, k, j, i);
+    const long long st = d == 0 ? 1 : (d == 1 ? (long long)b.N[0] : (long long)b.N[0] * b.N[1]);
+    FaceMetric fm;
+    face_metric(b.adm, b.ncell, cidx(b, k, j, i) - st, st, fm);
+    fmc_store<d>(b.fmc[d], fmc_count(b.n, d), loc, fm);   // loc = fmc_index(b, d, k, j, i)
   }
 }
-void launch_flux_dir(int d, const Work& w, const Par& P, cudaStream_t s, int grid, int threads) {
-  if (P.eos == 0) {
-    if (d == 0) launch_flux_r<0, 0>(w, P, s, grid, threads);
-    else if (d == 1) launch_flux_r<1, 0>(w, P, s, grid, threads);
-    else launch_flux_r<2, 0>(w, P, s, grid, threads);
-  } else {
-    if (d == 0) launch_flux_r<0, 1>(w, P, s, grid, threads);
-    else if (d == 1) launch_flux_r<1, 1>(w, P, s, grid, threads);
-    else launch_flux_r<2, 1>(w, P, s, grid, threads);
+__global__ void __launch_bounds__(256) k_metric_cache(Work w) {
+  const long long* pre = w.pre + (long long)W_C2P * (w.nblocks + 1);
+  const long long tot = pre[w.nblocks];
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < tot; it += (long long)gridDim.x * blockDim.x) {
+    const int bi = find_block(w, W_C2P, it);
+    const DevBlock& b = w.blk[bi];
+    const long long loc = it - pre[bi];
+    const int R0 = b.n[0] + 6, R1 = b.n[1] + 6;
+    const int ii = loc % R0; const long long r = loc / R0; const int jj = r % R1; const int kk = r / R1;
+    const long long nc = b.ncell, c = cidx(b, kk + b.ng - 3, jj + b.ng - 3, ii + b.ng - 3);
+    Metric m;
+#pragma unroll
+    for (int v = 0; v < 6; v++) m.g[v] = b.adm[(4 + v) * nc + c];
+    metric_setup(m);
+    metric_store(b.mc, nc, c, m);
   }
+  face_metric_items<0>(w);
+  face_metric_items<1>(w);
+  face_metric_items<2>(w);
+  // derivatives of the metric at the interior cells (Eq. 9 sources)
+  const long long* pc = w.pre + (long long)W_CELL * (w.nblocks + 1);
+  const long long tc = pc[w.nblocks];
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < tc; it += (long long)gridDim.x * blockDim.x) {
+    const int bi = find_block(w, W_CELL, it);
+    const DevBlock& b = w.blk[bi];
+    const long long loc = it - pc[bi];
+    const int i = loc % b.n[0]; const long long r = loc / b.n[0]; const int j = r % b.n[1]; const int k = r / b.n[1];
+    double D[DMC_N];
+    adm_derivs(b, cidx(b, k + b.ng, j + b.ng, i + b.ng), D);
+    const long long ni = (long long)b.n[0] * b.n[1] * b.n[2];
+#pragma unroll
+    for (int v = 0; v < DMC_N; v++) b.dmc[v * ni + loc] = D[v];
+  }
+}
+void launch_metric_cache(const Work& w, cudaStream_t s, int grid) { k_metric_cache<<<grid, 256, 0, s>>>(w); }
+int occ_metric_kernel() {
+  int o = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_metric_cache, 256, 0);
+  return o;
+}
+
+void launch_flux_dir(int d, const Work& w, const Par& P, cudaStream_t s, int grid, int threads) {
+  launch_flux_dir_c<1>(d, w, P, s, grid, threads);
 }
 void launch_fofc_flag(const Work& w, const Par& P, double g0, double g1, double bdt, unsigned long long* stats,
                       cudaStream_t s, int grid) {
@@ -232,16 +205,16 @@ void launch_fofc_fix(int d, const Work& w, const Par& P, unsigned long long* sta
 }
 int occ_face_kernel(int kind, int threads) {
   int o = 0;
-  if (kind == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_flux<0, 2, 0>, threads, 0);
-  else if (kind == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_flux<1, 2, 0>, threads, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_flux<2, 2, 0>, threads, 0);
+  if (kind == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_flux<0, 2, 0, 1>, threads, 0);
+  else if (kind == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_flux<1, 2, 0, 1>, threads, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_flux<2, 2, 0, 1>, threads, 0);
   return o;
 }
 int occupancy_face(int* per_sm) {
   cudaError_t e = cudaSuccess;
-  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_flux<0, 2, 0>, 128, 0));
-  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_flux<1, 2, 0>, 128, 0));
-  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[2], k_flux<2, 2, 0>, 128, 0));
+  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_flux<0, 2, 0, 1>, 128, 0));
+  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_flux<1, 2, 0, 1>, 128, 0));
+  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[2], k_flux<2, 2, 0, 1>, 128, 0));
   e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[3], k_fofc_flag, 128, 0));
   e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[4], k_fofc_fix<0>, 128, 0));
   return e == cudaSuccess ? 0 : -1;

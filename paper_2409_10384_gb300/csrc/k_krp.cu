@@ -183,8 +183,7 @@ __global__ void __launch_bounds__(256) k_krp_prep_block(Work w, Par P, KrpBuf kb
 #pragma unroll
     for (int v = 0; v < 3; v++) b.bcc[v * nc + c] = Bd[v];
     Metric m;
-    load_metric6(b.adm + 4 * nc, nc, c, m);
-    if (b.mc) metric_store(b.mc, nc, c, m);
+    metric_cell(b.adm, b.mc, nc, c, m);   // the step's metric cache (k_metric_cache)
     double U[5];
 #pragma unroll
     for (int v = 0; v < 5; v++) U[v] = b.cons[v * nc + c];

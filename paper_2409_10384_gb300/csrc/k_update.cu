@@ -59,24 +59,32 @@ __global__ void __launch_bounds__(256) k_emf(Work w) {
   }
 }
 
-// Sources of Eq. 9 at interior cell c (G[0] = 0 for D~).
+// Sources of Eq. 9 at interior cell (k, j, i) (G[0] = 0 for D~).
 __device__ __forceinline__ void sources(const DevBlock& b, const Par& P, int k, int j, int i, double* G) {
   const long long nc = b.ncell, c = cidx(b, k, j, i);
   const double* A = b.adm;
   Metric m;
   metric_cell(A, b.mc, nc, c, m);
   const double alpha = A[c];
-  const long long st[3] = {1, (long long)b.N[0], (long long)b.N[0] * b.N[1]};
-  // centred derivatives of alpha, beta^i, gamma_ij
+  // centred derivatives of alpha, beta^i, gamma_ij: from the step's cache, or
+  // taken here
+  double D[DMC_N];
+  if (b.dmc) {
+    const long long ni = (long long)b.n[0] * b.n[1] * b.n[2];
+    const long long q = ((long long)(k - b.ng) * b.n[1] + (j - b.ng)) * b.n[0] + (i - b.ng);
+#pragma unroll
+    for (int v = 0; v < DMC_N; v++) D[v] = b.dmc[v * ni + q];
+  } else {
+    adm_derivs(b, c, D);
+  }
   double dal[3], dbe[3][3], dg[3][6];
 #pragma unroll
   for (int a = 0; a < 3; a++) {
-    const double h = 0.5 * b.idx[a];
-    dal[a] = (A[c + st[a]] - A[c - st[a]]) * h;
+    dal[a] = D[10 * a];
 #pragma unroll
-    for (int v = 0; v < 3; v++) dbe[a][v] = (A[(1 + v) * nc + c + st[a]] - A[(1 + v) * nc + c - st[a]]) * h;
+    for (int v = 0; v < 3; v++) dbe[a][v] = D[10 * a + 1 + v];
 #pragma unroll
-    for (int v = 0; v < 6; v++) dg[a][v] = (A[(4 + v) * nc + c + st[a]] - A[(4 + v) * nc + c - st[a]]) * h;
+    for (int v = 0; v < 6; v++) dg[a][v] = D[10 * a + 4 + v];
   }
   const double* pr = b.prim;
   double rho = pr[c], p = pr[4 * nc + c];

@@ -185,7 +185,7 @@ extern "C" int mhd_stage_noalloc(const mhd_params* p, const mhd_block* blk, doub
   launch_c2p_block(w, P, dstats, st, grid(W_C2P, 128));
   if (!launched()) return MHD_ECUDA;
   for (int d = 0; d < 3; d++) {
-    launch_flux_dir(d, w, P, st, grid(W_SX + d, 128));
+    launch_flux_dir_inline(d, w, P, st, grid(W_SX + d, 128));
     if (!launched()) return MHD_ECUDA;
   }
   if (P.fofc) {

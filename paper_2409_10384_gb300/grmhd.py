@@ -97,7 +97,7 @@ _SIGS = {
     "mhd_mlp_save": (_I, [_VP, _VP, _L, C.POINTER(_L)]),
     "mhd_mlp_load": (_I, [_VP, _VP, _L]),
 }
-MHD_NKERNEL = 12
+MHD_NKERNEL = 13
 MLP_NPARAM = 4609
 MLP_NSTATE = 4609 + 13
 MLP_FSTRIDE = 8

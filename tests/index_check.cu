@@ -8,6 +8,9 @@
 //    faces.  The cells a sweep reads (the five-cell stencils of the cells
 //    next to its faces, as k_flux does) lie inside the ghosted block, and its
 //    faces (fidx) inside the face array (nface).
+//  - The face metric cache: fmc_index inverts face_coords (the metric
+//    kernel's store order), and a sweep's per-face index step lands on
+//    fmc_index of every face it visits, inside fmc_count.
 //  - find_block: on prefix sums with empty blocks, item it belongs to the
 //    block b returned, p[b] <= it < p[b + 1].
 //  - The integer-pipe compares (lt0, gt0, eq0, gt_nn, below_thr,
@@ -25,6 +28,26 @@
 #include "dev.cuh"
 
 using grmhd::DevBlock;
+
+// The metric cache kernel stores the face of work item `loc` (face_coords) at
+// index loc: fmc_index must invert face_coords over all fmc_count items.
+template <int d>
+static bool check_fmc(const int n[3]) {
+  DevBlock b{};
+  for (int a = 0; a < 3; a++) b.n[a] = n[a];
+  b.ng = 4;
+  const long long cnt = grmhd::fmc_count(n, d);
+  for (long long loc = 0; loc < cnt; loc++) {
+    int k, j, i;
+    grmhd::face_coords<d>(b, loc, k, j, i);
+    if (grmhd::fmc_index(b, d, k, j, i) != loc) {
+      std::printf("fmc d=%d n=%d,%d,%d: item %lld -> %lld\n", d, n[0], n[1], n[2], loc,
+                  grmhd::fmc_index(b, d, k, j, i));
+      return false;
+    }
+  }
+  return true;
+}
 
 template <int d>
 static bool check(const int n[3], int L) {
@@ -67,6 +90,21 @@ static bool check(const int n[3], int L) {
       std::printf("d=%d n=%d,%d,%d L=%d loc=%lld: faces %lld..%lld of %lld\n", d, n[0], n[1], n[2], L, loc, fl,
                   fl + (nf - 1) * fst, grmhd::nface(b, d));
       return false;
+    }
+    // the face metric cache: the sweep steps its index by qst per face; every
+    // face's index is fmc_index of that face and lies inside the cache
+    {
+      const long long q0 = grmhd::fmc_index(b, d, k, j, i), nq = grmhd::fmc_count(b.n, d);
+      const long long qst = d == 0 ? 1 : (d == 1 ? (long long)(n[0] + 2) : (long long)(n[0] + 2) * (n[1] + 2));
+      for (int q = 0; q < nf; q++) {
+        const int kk = k + (d == 2 ? q : 0), jj = j + (d == 1 ? q : 0), ii = i + (d == 0 ? q : 0);
+        const long long want = grmhd::fmc_index(b, d, kk, jj, ii);
+        if (want != q0 + q * qst || want < 0 || want >= nq) {
+          std::printf("d=%d n=%d,%d,%d L=%d loc=%lld face %d: cache index %lld, stepped %lld of %lld\n", d, n[0],
+                      n[1], n[2], L, loc, q, want, q0 + q * qst, nq);
+          return false;
+        }
+      }
     }
     if (d == 0 && loc < full_items) {
       if (first_nf < 0) first_nf = nf;
@@ -207,11 +245,13 @@ int main() {
                            {128, 2, 2}, {129, 3, 2},  {255, 2, 1},  {3, 128, 2},  {2, 3, 128}};
   const int Ls[] = {1, 2, 3, 4, 8, 16};
   int cases = 0;
-  for (const auto& n : shapes)
+  for (const auto& n : shapes) {
+    if (!check_fmc<0>(n) || !check_fmc<1>(n) || !check_fmc<2>(n)) return 1;
     for (int L : Ls) {
       if (!check<0>(n, L) || !check<1>(n, L) || !check<2>(n, L)) return 1;
       cases += 3;
     }
+  }
   std::printf("ok %d cases\n", cases);
   return 0;
 }
