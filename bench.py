@@ -52,23 +52,26 @@ FLOPS_PER_UNIT = {"flux": 1576.0, "c2p": 450.0, "fofc_flag": 450.0, "fofc_fix": 
 # once per RK step), so a flux launch does 1576 - 138 of the oracle's operations
 # per face.
 FLOPS_FACE_METRIC = 138.0
-FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (dense), the profiling recipe's unit table
-# DRAM bytes (read + write) per unit from ncu: the flux sweeps captured on the
-# 128^3 workload itself (one-pass metrics, profiles/ncu_flux_star128_dram.md),
-# the update on the 96^3 case (profiles/ncu_full_star96_update.md), scaled to
-# a launch by its units.  The flux figures hold only at 128^3: the segment
+# FP64 peak from the unit counts and the clock: 2 DFMA thread instructions per
+# clock per SM (ncu's FP64 pipe peak) x 2 flops x 152 SMs x 2070 MHz.  Our
+# FP64 FMA probe (8 independent DFMA chains per thread, 8 CTAs of 256 per SM)
+# measured 1.997 DFMA per clock per SM, 1.2568 TFLOP/s, on the same part.
+FP64_PEAK_TFLOPS = 2.0 * 2.0 * 152 * 2.070e9 / 1e12
+# DRAM bytes (read + write) per unit from ncu: the flux sweeps and the update
+# captured on the 128^3 workload itself (one-pass metrics,
+# profiles/ncu_flux_star128_dram.md), scaled to a launch by its units.  The flux figures hold only at 128^3: the segment
 # lengths, and with them the x sweep's re-reads, depend on the size.
-TRAFFIC_PER_UNIT = {"flux_x": 295.6, "flux_y": 244.3, "flux_z": 241.5, "update": 585.0}
-TRAFFIC_SIZES = {"flux_x": (128,), "flux_y": (128,), "flux_z": (128,), "update": (96, 128)}
+TRAFFIC_PER_UNIT = {"flux_x": 367.9, "flux_y": 242.6, "flux_z": 243.6, "update": 733.6}
+TRAFFIC_SIZES = {"flux_x": (128,), "flux_y": (128,), "flux_z": (128,), "update": (128,)}
 # Kernels changed since their capture: their traffic is reported as null, with
 # the last capture beside it, until they are captured again.
-TRAFFIC_STALE = {"flux_x", "flux_y", "flux_z", "update"}
+TRAFFIC_STALE = set()
 # FP64 thread instructions executed per face (ncu
 # sm__sass_thread_inst_executed_op_fp64_pred_on.sum per launch / faces, on the
 # 104^3 case, which has the 128^3 segment lengths; profiles/ncu_flux_star104_fp64.md),
 # for the issue-based fraction: executed FP64 instructions per second over
 # the pipe's 2 thread instructions per clock per SM at the sampled SM clock.
-FP64_INST_PER_UNIT = {"flux_x": 774.7, "flux_y": 743.5, "flux_z": 746.3}
+FP64_INST_PER_UNIT = {"flux_x": 715.7, "flux_y": 684.3, "flux_z": 687.3}
 FP64_ISSUE_PER_CLK_SM = 2.0
 
 # Algorithmic HBM bytes per zone and RK stage of one fused pass: read U (5),
@@ -708,8 +711,9 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": dom,
                 "frac_issue": frac_issue,
-                "peak_source": "nominal FP64 1.25 TFLOP/s (recipe unit table; our DFMA probe reached 1.195); "
-                               "FP64 is not in MEASURED_PEAKS.json",
+                "peak_source": "derived from unit counts and clock: 2 DFMA/clk/SM x 2 flop x 152 SMs x 2070 MHz "
+                               "(our DFMA probe: 1.997 DFMA/clk/SM, 1.2568 TFLOP/s); FP64 is not in "
+                               "MEASURED_PEAKS.json",
                 "achieved_source": "algorithmic FP64 operations of the op-counting oracle (add, mul, div, sqrt "
                                    "each 1) x faces per launch / mean launch time from CUDA events",
                 "frac_issue_source": "ncu FP64 thread instructions per face x faces / launch time, over 2 per "
@@ -772,9 +776,13 @@ def main():
     ap.add_argument("--no-bns", action="store_true", help="skip the binary-shaped leg (profiling cases)")
     ap.add_argument("--no-small", action="store_true", help="skip the 32^3 periodic leg (profiling cases)")
     ap.add_argument("--c2p-cells", type=int, default=1 << 24, help="cells of the con2prim leg (profiling cases)")
+    ap.add_argument("--c2p-guess", type=int, default=None,
+                    help="root search of the main leg's con2prims (default: the module's C2P_GUESS)")
     args = ap.parse_args()
-    global N_INT
+    global N_INT, C2P_GUESS
     N_INT = args.n
+    if args.c2p_guess is not None:
+        C2P_GUESS = args.c2p_guess
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -45,7 +45,7 @@ struct mhd_ctx {
   size_t scratch_bytes = 0;
   long long list_version = 0;
   int grid[W_NKIND] = {0};
-  int g_kprep = 1, g_kfin = 1, g_fprep = 1, g_ffin = 1, g_solve = 1;
+  int g_kprep = 1, g_kfin = 1, g_fprep = 1, g_ffin = 1;
   // launch configuration (CTA size, waves of resident CTAs) per tunable kernel
   struct Cfg {
     int threads = 128, waves = 1;
@@ -59,7 +59,14 @@ struct mhd_ctx {
   // neighbour table of the last ghost fill (grow-only)
   int* dnbr = nullptr;
   size_t dnbr_n = 0;
-  int g_solve_cells() const { return nsm * (occ_krp[1] > 0 ? occ_krp[1] : 1); }
+  // Grid of the refill root solve over n cells: one resident wave, capped by
+  // the cells (a lane per cell).  Fewer CTAs for a small list (a few cells
+  // per lane) measured slower: the 32^3 block's solve took 108 instead of 84
+  // us, its SMs FP64-bound while a third of them held work.
+  int solve_grid(long long n) const {
+    const long long full = (long long)nsm * (occ_krp[1] > 0 ? occ_krp[1] : 1);
+    return (int)std::max(1LL, std::min(full, (n + 255) / 256));
+  }
   // counters
   unsigned long long* dstats = nullptr;
   long long launches = 0;
@@ -375,7 +382,6 @@ int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
   c->g_kfin = grid_of(W_C2P, 128, c->occ_krp[2]);
   c->g_fprep = grid_of(W_CELL, 128, c->occ_krp[3]);
   c->g_ffin = grid_of(W_CELL, 128, c->occ_krp[4]);
-  c->g_solve = c->nsm * std::max(c->occ_krp[1], 1);
   return MHD_OK;
 }
 
@@ -467,7 +473,7 @@ int enqueue_c2p(mhd_ctx* c, cudaStream_t s, const Work& w, const long long* item
     launch_krp_prep_block(w, c->P, kb, s, tgrid(c, T_C2P_PREP, items[W_C2P]), cp.threads, learned, nullptr);
   });
   c2p_seed(c, kb, items[W_C2P], s);
-  timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, c->dstats, s, c->g_solve); });
+  timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, c->dstats, s, c->solve_grid(items[W_C2P])); });
   timed(c, MHD_K_C2P, s, [&] {
     launch_krp_finish_block(w, c->P, kb, c->dstats, s, tgrid(c, T_C2P_FIN, items[W_C2P]), cf.threads);
   });
@@ -489,7 +495,7 @@ int enqueue_rhs(mhd_ctx* c, double dt, int stage, cudaStream_t s, const Work& w,
                            c->cfg[T_FOFC_PREP].threads, (c->P.guess == 1 || c->P.guess == 2) ? 1 : 0, nullptr);
     });
     c2p_seed(c, kb, items[W_CELL], s);
-    timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, c->dstats, s, c->g_solve); });
+    timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, c->dstats, s, c->solve_grid(items[W_CELL])); });
     timed(c, MHD_K_FOFC_FLAG, s, [&] {
       launch_krp_finish_fofc(w, c->P, kb, c->dstats, s, tgrid(c, T_FOFC_FIN, items[W_CELL]),
                              c->cfg[T_FOFC_FIN].threads);
@@ -865,7 +871,7 @@ int c2p_cells_enqueue(mhd_ctx* c, long n, double* cons, const double* Bd, const 
     launch_krp_prep_cells(c->P, kb, cons, Bd, g, mode != 0 ? 1 : 0, nullptr, s, cells_grid(c, n, c->occ_krp[5]));
   });
   if (mode != 0) c2p_seed_mode(c, kb, n, mode, s);
-  timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, c->dstats, s, c->g_solve_cells()); });
+  timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, c->dstats, s, c->solve_grid(n)); });
   timed(c, MHD_K_C2P, s, [&] {
     launch_krp_finish_cells(c->P, kb, cons, Bd, g, prim, flags, iters, c->dstats, s, cells_grid(c, n, c->occ_krp[6]));
   });
@@ -924,7 +930,7 @@ int mhd_mlp_dataset(mhd_ctx* c, long n, const double* cons, const double* Bd, co
   if (r) return r;
   Par P = c->P;
   launch_krp_prep_cells(P, kb, cons, Bd, g, 0, feat, s, cells_grid(c, n, c->occ_krp[5]));
-  launch_krp_solve(P, kb, c->dstats, s, c->g_solve_cells());
+  launch_krp_solve(P, kb, c->dstats, s, c->solve_grid(n));
   launch_mlp_logmu(kb, logmu, s, c->nsm);
   c->launches += 3;
   return cuda_ok(cudaGetLastError());
@@ -1275,7 +1281,7 @@ int mhd_autotune(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, void* s
     if (k == T_C2P_PREP || k == T_FOFC_PREP) {
       launch();
       c2p_seed(c, kb, fofc_k ? it[W_CELL] : it[W_C2P], s);
-      launch_krp_solve(c->P, kb, c->dstats, s, c->g_solve);
+      launch_krp_solve(c->P, kb, c->dstats, s, c->solve_grid(fofc_k ? it[W_CELL] : it[W_C2P]));
     }
     if (cfg_out) {
       cfg_out[2 * k] = best.threads;
