@@ -177,7 +177,8 @@ enum {
   KW_A, KW_B, KW_GA, KW_GB, KW_MU, KW_SDET, KW_ISDET, KW_USD, KW_UST, KW_N
 };
 // solve status: 0 solve needed, 1 root known, 2 no bracket / bad input,
-// 3 iteration cap, 4 bracket to be built from the learned guess
+// 3 iteration cap, 4 bracket to be built from the learned guess, 5 FOFC
+// estimate flagged by a floor on U* before the solve (no solve)
 
 // Learned-guess network 5 -> 64 -> 64 -> 1: fp32 parameter offsets, bf16
 // operand copies (W1 padded to [64][16], W2 [64][64], w3 padded to [8][64]).

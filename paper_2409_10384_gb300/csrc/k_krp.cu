@@ -37,9 +37,14 @@ __device__ __forceinline__ void kw_load(const KrpBuf& kb, const Par& P, long lon
 // guess later).  feat (optional): the network's features of the cell.
 // guess > 0: the cell's previous root; the FP64 bracket starts as
 // guess (1 -+ WARM_DELTA), verified by the signs at both ends (krp_bracket).
+// fofc: the FOFC estimate, which only needs to know whether con2prim of U*
+// fails or a floor fires (Sec. 3.3); a floor on the conserved state decides
+// that before the solve, so such a cell gets status 5 (flagged, no bracket,
+// no solve, no recovery).
 __device__ __forceinline__ void prep_cell(const Par& P, const KrpBuf& kb, long long i, const double* U,
                                           const double* Bd, const Metric& m, bool learned = false,
-                                          float* feat = nullptr, double alpha = 1.0, double guess = 0.0) {
+                                          float* feat = nullptr, double alpha = 1.0, double guess = 0.0,
+                                          bool fofc = false) {
   KrpCell k;
   unsigned fl;
   const long long n = kb.n;
@@ -47,7 +52,9 @@ __device__ __forceinline__ void prep_cell(const Par& P, const KrpBuf& kb, long l
   int its = 0;
   if (krp_prep(P, U, Bd, m, k, fl, alpha)) {
     if (feat) krp_features(k.s, feat + i * MLP_FSTRIDE);
-    if (learned) {
+    if (fofc && (fl & (F_DFLOOR | F_SIGMA | F_TAU))) {
+      st = 5;
+    } else if (learned) {
       st = 4;
     } else {
       double a, b, Ga, Gb, mu = 0.0;
@@ -286,7 +293,7 @@ __global__ void __launch_bounds__(256) k_krp_prep_fofc(Work w, Par P, double g0,
     Metric m;
     metric_cell(b.adm, b.mc, nc, c, m);
     const double Bd[3] = {b.bcc[c], b.bcc[nc + c], b.bcc[2 * nc + c]};
-    prep_cell(P, kb, it, U, Bd, m, learned != 0, feat, b.adm[c], b.mu ? b.mu[c] : 0.0);
+    prep_cell(P, kb, it, U, Bd, m, learned != 0, feat, b.adm[c], b.mu ? b.mu[c] : 0.0, true);
     kb.w[KW_USD * n + it] = U[0];
     kb.w[KW_UST * n + it] = U[4];
   }
@@ -301,12 +308,16 @@ __global__ void __launch_bounds__(256) k_krp_finish_fofc(Work w, Par P, KrpBuf k
     fofc_cell(w, it, bi, k, j, i);
     const DevBlock& b = w.blk[bi];
     const long long nc = b.ncell, c = cidx(b, k, j, i);
-    KrpCell kc;
-    kw_load(kb, P, it, kc);
     unsigned fl = kb.fl[it];
-    double pr[5];
-    krp_finish(P, kc, kb.w[KW_MU * n + it], kb.st[it] == 1, fl, pr);
-    bool flag = (fl & (FLOOR_BITS | F_FAIL)) != 0;
+    const unsigned char st = kb.st[it];
+    bool flag = true;   // status 5: a floor on U* already flagged the cell
+    if (st != 5) {
+      KrpCell kc;
+      kw_load(kb, P, it, kc);
+      double pr[5];
+      krp_finish(P, kc, kb.w[KW_MU * n + it], st == 1, fl, pr);
+      flag = (fl & (FLOOR_BITS | F_FAIL)) != 0;
+    }
     if (!flag && P.dmp_M > 0.0) {
       const double Us[2] = {kb.w[KW_USD * n + it], kb.w[KW_UST * n + it]};
 #pragma unroll
