@@ -65,7 +65,7 @@ TRAFFIC_PER_UNIT = {"flux_x": 367.9, "flux_y": 242.6, "flux_z": 243.6, "update":
 TRAFFIC_SIZES = {"flux_x": (128,), "flux_y": (128,), "flux_z": (128,), "update": (128,)}
 # Kernels changed since their capture: their traffic is reported as null, with
 # the last capture beside it, until they are captured again.
-TRAFFIC_STALE = set()
+TRAFFIC_STALE = {"flux_x", "flux_y", "flux_z"}
 # FP64 thread instructions executed per face (ncu
 # sm__sass_thread_inst_executed_op_fp64_pred_on.sum per launch / faces, on the
 # 104^3 case, which has the 128^3 segment lengths; profiles/ncu_flux_star104_fp64.md),

@@ -1171,10 +1171,12 @@ __device__ __forceinline__ void riemann(int rs, const FaceMetric& fm, const Side
 #pragma unroll
       for (int c = 0; c < 7; c++) F[c] = 0.5 * (L.F[c] + R.F[c]);
     } else {
+      // (lR F_L - lL F_R + lL lR (U_R - U_L)) / (lR - lL), with the division's
+      // reciprocal folded into the three coefficients once per face
       const double inv = 1.0 / (lR - lL);
-      const double ll = lL * lR;
+      const double cR = lR * inv, cL = -lL * inv, cLR = (lL * lR) * inv;
 #pragma unroll
-      for (int c = 0; c < 7; c++) F[c] = fma(lR, L.F[c], fma(-lL, R.F[c], ll * (R.U[c] - L.U[c]))) * inv;
+      for (int c = 0; c < 7; c++) F[c] = fma(cR, L.F[c], fma(cL, R.F[c], cLR * (R.U[c] - L.U[c])));
     }
   } else {
     const double a = fmax(fmax(fabs(lmL), fabs(lpL)), fmax(fabs(lmR), fabs(lpR)));
