@@ -61,17 +61,17 @@ FP64_PEAK_TFLOPS = 2.0 * 2.0 * 152 * 2.070e9 / 1e12
 # captured on the 128^3 workload itself (one-pass metrics,
 # profiles/ncu_flux_star128_dram.md), scaled to a launch by its units.  The flux figures hold only at 128^3: the segment
 # lengths, and with them the x sweep's re-reads, depend on the size.
-TRAFFIC_PER_UNIT = {"flux_x": 367.9, "flux_y": 242.6, "flux_z": 243.6, "update": 733.6}
+TRAFFIC_PER_UNIT = {"flux_x": 364.5, "flux_y": 241.8, "flux_z": 243.6, "update": 733.6}
 TRAFFIC_SIZES = {"flux_x": (128,), "flux_y": (128,), "flux_z": (128,), "update": (128,)}
 # Kernels changed since their capture: their traffic is reported as null, with
 # the last capture beside it, until they are captured again.
-TRAFFIC_STALE = {"flux_x", "flux_y", "flux_z"}
+TRAFFIC_STALE = set()
 # FP64 thread instructions executed per face (ncu
 # sm__sass_thread_inst_executed_op_fp64_pred_on.sum per launch / faces, on the
 # 104^3 case, which has the 128^3 segment lengths; profiles/ncu_flux_star104_fp64.md),
 # for the issue-based fraction: executed FP64 instructions per second over
 # the pipe's 2 thread instructions per clock per SM at the sampled SM clock.
-FP64_INST_PER_UNIT = {"flux_x": 715.7, "flux_y": 684.3, "flux_z": 687.3}
+FP64_INST_PER_UNIT = {"flux_x": 711.7, "flux_y": 680.3, "flux_z": 683.3}
 FP64_ISSUE_PER_CLK_SM = 2.0
 
 # Algorithmic HBM bytes per zone and RK stage of one fused pass: read U (5),
