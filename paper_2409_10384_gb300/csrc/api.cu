@@ -21,6 +21,9 @@ struct mhd_ctx {
   int occ_krp[7] = {1, 1, 1, 1, 1, 1, 1};
   int occ_seed[2] = {1, 1};   // seed kernel without / with the network
   int occ_metric = 1;         // metric cache kernel
+  // side streams and events of the forked flux sweeps (y, z)
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
   // three-phase con2prim scratch: of the block list, and of independent cells
   char* krp = nullptr;
   long long krp_n = 0;
@@ -483,10 +486,27 @@ int enqueue_c2p(mhd_ctx* c, cudaStream_t s, const Work& w, const long long* item
 int enqueue_rhs(mhd_ctx* c, double dt, int stage, cudaStream_t s, const Work& w, const long long* items) {
   double g0, g1, be;
   rk_weights(c->P.rk_order, stage, g0, g1, be);
+  // The three sweeps read the stage's primitives and write their own flux
+  // arrays: y and z run on two side streams forked from s and joined back, so
+  // that one sweep's last wave overlaps the next one's first.  With the
+  // per-kernel profile on they run one after another on s, so that each
+  // launch's event time is its own.
+  const bool fork = !c->prof;
+  cudaStream_t fs[3] = {s, fork ? c->side[0] : s, fork ? c->side[1] : s};
+  if (fork) {
+    if (cudaEventRecord(c->ev_fork, s) != cudaSuccess) return MHD_ECUDA;
+    for (int d = 1; d < 3; d++)
+      if (cudaStreamWaitEvent(fs[d], c->ev_fork, 0) != cudaSuccess) return MHD_ECUDA;
+  }
   for (int d = 0; d < 3; d++)
-    timed(c, MHD_K_FLUX_X + d, s, [&] {
-      launch_flux_dir(d, w, c->P, s, tgrid(c, T_FX + d, items[W_SX + d]), c->cfg[T_FX + d].threads);
+    timed(c, MHD_K_FLUX_X + d, fs[d], [&] {
+      launch_flux_dir(d, w, c->P, fs[d], tgrid(c, T_FX + d, items[W_SX + d]), c->cfg[T_FX + d].threads);
     });
+  if (fork)
+    for (int d = 1; d < 3; d++) {
+      if (cudaEventRecord(c->ev_join[d - 1], fs[d]) != cudaSuccess) return MHD_ECUDA;
+      if (cudaStreamWaitEvent(s, c->ev_join[d - 1], 0) != cudaSuccess) return MHD_ECUDA;
+    }
   if (c->P.fofc) {
     if (c->P.guess == 1 && !c->mlp_ready) return MHD_ENOMLP;
     KrpBuf kb = krp_view(c->krp, items[W_CELL]);
@@ -523,11 +543,24 @@ int enqueue_update(mhd_ctx* c, double dt, int stage, cudaStream_t s, const Work&
   double g0, g1, be;
   rk_weights(c->P.rk_order, stage, g0, g1, be);
   const int first = stage == 0 ? 1 : 0;
+  // U and the face B~ are updated from different inputs (fluxes and sources;
+  // edge EMFs) into different arrays: the face update runs on a side stream
+  // beside the cell update (sequentially with the per-kernel profile on).
+  const bool fork = !c->prof;
+  cudaStream_t sf = fork ? c->side[0] : s;
+  if (fork) {
+    if (cudaEventRecord(c->ev_fork, s) != cudaSuccess) return MHD_ECUDA;
+    if (cudaStreamWaitEvent(sf, c->ev_fork, 0) != cudaSuccess) return MHD_ECUDA;
+  }
   timed(c, MHD_K_UPDATE, s, [&] {
     launch_update_cells(w, c->P, g0, g1, be * dt, first, s, tgrid(c, T_UPD, items[W_CELL]), c->cfg[T_UPD].threads);
   });
   long long gfa = std::min<long long>((items[W_FACE] + 255) / 256, (long long)c->nsm * std::max(c->occ_upd[2], 1));
-  timed(c, MHD_K_FACEB, s, [&] { launch_update_faces(w, g0, g1, be * dt, first, s, (int)std::max(1LL, gfa)); });
+  timed(c, MHD_K_FACEB, sf, [&] { launch_update_faces(w, g0, g1, be * dt, first, sf, (int)std::max(1LL, gfa)); });
+  if (fork) {
+    if (cudaEventRecord(c->ev_join[0], sf) != cudaSuccess) return MHD_ECUDA;
+    if (cudaStreamWaitEvent(s, c->ev_join[0], 0) != cudaSuccess) return MHD_ECUDA;
+  }
   return cuda_ok(cudaGetLastError());
 }
 
@@ -639,13 +672,30 @@ int mhd_init(const mhd_params* p, mhd_ctx** out) {
     c->occ_t[T_EMF][ti] = occ_update_kernel(0, th);
     c->occ_t[T_UPD][ti] = occ_update_kernel(1, th);
   }
+  auto release = [](mhd_ctx* x) {
+    for (int q = 0; q < 2; q++) {
+      if (x->side[q]) cudaStreamDestroy(x->side[q]);
+      if (x->ev_join[q]) cudaEventDestroy(x->ev_join[q]);
+    }
+    if (x->ev_fork) cudaEventDestroy(x->ev_fork);
+    if (x->dstats) cudaFree(x->dstats);
+    delete x;
+  };
+  bool ok = true;
+  for (int q = 0; q < 2; q++) ok = ok && cudaStreamCreateWithFlags(&c->side[q], cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int q = 0; q < 2; q++) ok = ok && cudaEventCreateWithFlags(&c->ev_join[q], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    release(c);
+    return MHD_ECUDA;
+  }
   if (cudaMalloc(&c->dstats, sizeof(unsigned long long) * MHD_NSTATS) != cudaSuccess) {
-    delete c;
+    c->dstats = nullptr;
+    release(c);
     return MHD_ENOMEM;
   }
   if (cudaMemset(c->dstats, 0, sizeof(unsigned long long) * MHD_NSTATS) != cudaSuccess) {
-    cudaFree(c->dstats);
-    delete c;
+    release(c);
     return MHD_ECUDA;
   }
   *out = c;
@@ -759,6 +809,11 @@ void mhd_finalize(mhd_ctx* c) {
     cudaEventDestroy(r.b);
   }
   for (auto e : c->ev_pool) cudaEventDestroy(e);
+  for (int q = 0; q < 2; q++) {
+    if (c->side[q]) cudaStreamDestroy(c->side[q]);
+    if (c->ev_join[q]) cudaEventDestroy(c->ev_join[q]);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   delete c;
 }
 
