@@ -65,13 +65,13 @@ TRAFFIC_PER_UNIT = {"flux_x": 364.5, "flux_y": 241.8, "flux_z": 243.6, "update":
 TRAFFIC_SIZES = {"flux_x": (128,), "flux_y": (128,), "flux_z": (128,), "update": (128,)}
 # Kernels changed since their capture: their traffic is reported as null, with
 # the last capture beside it, until they are captured again.
-TRAFFIC_STALE = set()
+TRAFFIC_STALE = {"flux_x", "flux_y", "flux_z"}
 # FP64 thread instructions executed per face (ncu
 # sm__sass_thread_inst_executed_op_fp64_pred_on.sum per launch / faces, on the
 # 104^3 case, which has the 128^3 segment lengths; profiles/ncu_flux_star104_fp64.md),
 # for the issue-based fraction: executed FP64 instructions per second over
 # the pipe's 2 thread instructions per clock per SM at the sampled SM clock.
-FP64_INST_PER_UNIT = {"flux_x": 711.7, "flux_y": 680.3, "flux_z": 683.3}
+FP64_INST_PER_UNIT = {"flux_x": 703.3, "flux_y": 672.1, "flux_z": 675.1}
 FP64_ISSUE_PER_CLK_SM = 2.0
 
 # Algorithmic HBM bytes per zone and RK stage of one fused pass: read U (5),

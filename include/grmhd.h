@@ -213,6 +213,15 @@ int mhd_set_launch(mhd_ctx* ctx, int kind, int threads, int waves);
 /* Current launch shape of a tunable kernel. */
 int mhd_get_launch(const mhd_ctx* ctx, int kind, int* threads, int* waves);
 
+/* Self-check of the library's fast reciprocal (the paper has no counterpart).
+ * The hot divisions (the master function of con2prim, its regula-falsi step,
+ * the WENO-Z weights and the HLLE speeds) multiply by an approximate FP64
+ * reciprocal refined by two Newton-Raphson steps, within ~1 ulp of the
+ * correctly rounded quotient.  For n device values x (normal, nonzero),
+ * rel_out[2i] and rel_out[2i+1] (device) receive the relative differences of
+ * 1 * r(x) and (x + 1) * r(x) from the correctly rounded 1/x and (x + 1)/x. */
+int mhd_check_rcp(const double* x, long n, double* rel_out, void* stream);
+
 /* Copy the counters to *out (synchronises the stream) / zero them. */
 int mhd_read_stats(mhd_ctx* ctx, mhd_stats* out, void* stream);
 int mhd_reset_stats(mhd_ctx* ctx, void* stream);

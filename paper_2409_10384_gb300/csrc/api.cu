@@ -1231,6 +1231,17 @@ int mhd_step(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, int graph, 
   return cuda_ok(cudaGraphLaunch(c->gexec, s));
 }
 
+int mhd_check_rcp(const double* x, long n, double* rel_out, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !rel_out))) return MHD_EINVAL;
+  if (n == 0) return MHD_OK;
+  int dev = 0, nsm = 1;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return MHD_ECUDA;
+  if (cudaPeekAtLastError() != cudaSuccess) return MHD_ECUDA;
+  launch_check_rcp(x, n, rel_out, (cudaStream_t)stream, nsm);
+  return cuda_ok(cudaPeekAtLastError());
+}
+
 int mhd_graph_step(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, void* stream) {
   return mhd_step(c, blocks, nb, dt, 1, stream);
 }

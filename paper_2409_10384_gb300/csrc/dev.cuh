@@ -294,6 +294,22 @@ __host__ __device__ __forceinline__ bool finite_bits(double x) {
 #endif
 }
 
+// Reciprocal for the hot divisions: the hardware's approximate FP64
+// reciprocal (rcp.approx.ftz.f64) refined by two Newton-Raphson steps for
+// 1/x (r <- r + r (1 - x r); each step squares the relative error), then
+// a / x = a * r.  Within ~1 ulp of the correctly rounded quotient, where a
+// correctly rounded division costs about twice the FP64 issue slots.  For
+// normal x only (the approximation flushes subnormals): callers use it on
+// denominators bounded away from zero.
+__device__ __forceinline__ double rcp_nr(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
 struct Metric {
   double g[6], gi[6], sdet, isdet;
 };
@@ -498,8 +514,8 @@ __device__ __forceinline__ double kev_g(const KS& s, double mu) {
   const double P1 = 1.0 + W;
   const double T = fma(P1 * W, A, v2 * (W * W));                          // (1 + W) eps_raw
   const double Te = gt_nn(s.eps_min * P1, T) ? s.eps_min * P1 : T;
-  const double Z = fma(P1, fma(mu * rbar2, W, 1.0), s.gam * Te);
-  return mu - (W * P1) / Z;
+  const double Z = fma(P1, fma(mu * rbar2, W, 1.0), s.gam * Te);   // >= 1
+  return mu - (W * P1) * rcp_nr(Z);
 }
 // The master function with the hybrid EOS, in the general form of Kastaun
 // et al. (2021): rho = D/W, eps clamped below at eps_c(rho) + T_atm/(G_th-1),
@@ -605,7 +621,7 @@ __device__ __forceinline__ bool illinois(const KS& s, const Par& P, double a, do
   while (gt_nn(b - a, tol * b)) {
     if (iters >= maxit) return false;
     iters++;
-    double c = (a * Fb - b * Fa) / (Fb - Fa);
+    double c = (a * Fb - b * Fa) * rcp_nr(Fb - Fa);   // Fb > 0 > Fa
     // nudge away from the end replaced last: once the iterate is within eta of
     // the root the next point lands past it and closes the bracket
     const double eta = 0.25 * tol * b;
@@ -1030,7 +1046,7 @@ __device__ __forceinline__ void wz_finish(const double* x, const double* n_hi, c
     c[0] = m[0];
 #pragma unroll
     for (int v = 1; v < N; v++) c[v] = c[v - 1] * m[v];
-    double inv = (1.0 / 6.0) / c[N - 1];
+    double inv = (1.0 / 6.0) * rcp_nr(c[N - 1]);   // c[N - 1] in [1, 2^N)
 #pragma unroll
     for (int v = N - 1; v >= 0; v--) {
       double r;
@@ -1159,7 +1175,7 @@ __device__ __forceinline__ void face_side(const Par& P, const double* st, double
 // LLF (rs 0) or HLLE (rs 1) flux from the two sides of a face of direction d.
 template <int d>
 __device__ __forceinline__ void riemann(int rs, const FaceMetric& fm, const Side& L, const Side& R, double* F) {
-  const double r = fm.alpha / (L.den * R.den);
+  const double r = fm.alpha * rcp_nr(L.den * R.den);   // den = rho h + b^2 - v^2 N > 0
   const double aL = r * R.den, aR = r * L.den;
   const double bd = fm.beta[d];
   const double lmL = fma(aL, L.vq - L.sq, -bd), lpL = fma(aL, L.vq + L.sq, -bd);
@@ -1173,7 +1189,8 @@ __device__ __forceinline__ void riemann(int rs, const FaceMetric& fm, const Side
     } else {
       // (lR F_L - lL F_R + lL lR (U_R - U_L)) / (lR - lL), with the division's
       // reciprocal folded into the three coefficients once per face
-      const double inv = 1.0 / (lR - lL);
+      const double dl = lR - lL;   // > 0 here
+      const double inv = gt_nn(dl, 1e-280) ? rcp_nr(dl) : 1.0 / dl;
       const double cR = lR * inv, cL = -lL * inv, cLR = (lL * lR) * inv;
 #pragma unroll
       for (int c = 0; c < 7; c++) F[c] = fma(cR, L.F[c], fma(cL, R.F[c], cLR * (R.U[c] - L.U[c])));

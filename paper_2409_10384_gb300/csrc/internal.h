@@ -23,6 +23,8 @@ void launch_flux_dir_inline(int d, const Work& w, const Par& P, cudaStream_t s, 
 // metric of a step: cell cache (mc) of the con2prim region, face cache (fmc)
 void launch_metric_cache(const Work& w, cudaStream_t s, int grid);
 int occ_metric_kernel();
+// the fast reciprocal (rcp_nr) against the correctly rounded division
+void launch_check_rcp(const double* x, long long n, double* out, cudaStream_t s, int nsm);
 void launch_fofc_flag(const Work& w, const Par& P, double g0, double g1, double bdt, unsigned long long* stats,
                       cudaStream_t s, int grid);
 void launch_fofc_fix(int d, const Work& w, const Par& P, unsigned long long* stats, cudaStream_t s, int grid);

@@ -182,6 +182,23 @@ __global__ void __launch_bounds__(128) k_c2p_block(Work w, Par P, unsigned long 
   warp_flush(&stats[3], s_floor);
 }
 
+// The fast reciprocal against the correctly rounded division: out[i] = the
+// relative difference of a * rcp_nr(x) from a / x, for a = 1 and a = x + 1.
+__global__ void k_check_rcp(const double* __restrict__ x, long long n, double* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    const double r = rcp_nr(v), q = 1.0 / v;
+    const double a = v + 1.0, qa = a / v, ra = a * r;
+    out[2 * i] = fabs(r - q) / fabs(q);
+    out[2 * i + 1] = qa != 0.0 ? fabs(ra - qa) / fabs(qa) : fabs(ra);
+  }
+}
+void launch_check_rcp(const double* x, long long n, double* out, cudaStream_t s, int nsm) {
+  long long nb = (n + 255) / 256;
+  int grid = (int)(nb < (long long)nsm * 8 ? nb : (long long)nsm * 8);
+  k_check_rcp<<<grid < 1 ? 1 : grid, 256, 0, s>>>(x, n, out);
+}
+
 // ------------------------------------------------------------------ launchers
 void launch_init_block(const DevBlock& b, const Par& P, const double* const A[3], cudaStream_t s, int nsm) {
   k_init_faces<<<nsm * 8, 256, 0, s>>>(b, A[0], A[1], A[2]);

@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(256) k_krp_solve(Par P, KrpBuf kb, unsigned lo
         cap = fin = true;
       } else {
         it++;
-        double c = (a * Fb - b * Fa) / (Fb - Fa);
+        double c = (a * Fb - b * Fa) * rcp_nr(Fb - Fa);   // Fb > 0 > Fa
         const double eta = 0.25 * P.tol * b;
         c += side == -1 ? eta : (side == 1 ? -eta : 0.0);
         if (!(gt_nn(c, a) && gt_nn(b, c))) c = 0.5 * (a + b);

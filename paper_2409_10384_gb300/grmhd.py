@@ -96,6 +96,7 @@ _SIGS = {
     "mhd_mlp_set": (_I, [_VP, _VP]),
     "mhd_mlp_save": (_I, [_VP, _VP, _L, C.POINTER(_L)]),
     "mhd_mlp_load": (_I, [_VP, _VP, _L]),
+    "mhd_check_rcp": (_I, [_VP, _L, _VP, _VP]),
 }
 MHD_NKERNEL = 13
 MLP_NPARAM = 4609
@@ -217,6 +218,15 @@ def stage_noalloc(p: mhd_params, blk: DeviceBlock, dt: float, stage: int, stream
     returns the status code."""
     d = blk.desc()
     return int(lib().mhd_stage_noalloc(C.byref(p), C.byref(d), float(dt), int(stage), _sptr(stream)))
+
+
+def check_rcp(x, stream=None):
+    """mhd_check_rcp: relative differences of the library's fast reciprocal
+    from the correctly rounded division, [n][2] (1/x, (x + 1)/x)."""
+    import torch
+    out = torch.empty((x.shape[0], 2), dtype=torch.float64, device="cuda")
+    check(lib().mhd_check_rcp(_ptr(x), x.shape[0], _ptr(out), _sptr(stream)), "mhd_check_rcp")
+    return out
 
 
 def block_array(blocks) -> C.Array:

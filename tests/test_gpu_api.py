@@ -170,3 +170,20 @@ def test_network_bf16_blob_round_trip(G):
     assert np.array_equal(b.mlp_get(), rounded)
     with pytest.raises(RuntimeError):
         b.mlp_load(blob[:-1])
+
+
+def test_fast_reciprocal_within_two_ulp_of_the_division(G):
+    """The reciprocal the hot divisions use (approximation refined by two
+    Newton-Raphson steps) against CUDA's correctly rounded division, on
+    log-uniform values over the normal range of both signs, powers of two and
+    their neighbours: within 2^-51 relative (two units in the last place)."""
+    import torch
+    rng = np.random.default_rng(21)
+    x = np.concatenate([10.0 ** rng.uniform(-280, 280, 400000) * rng.choice([-1.0, 1.0], 400000),
+                        2.0 ** np.arange(-900, 901, dtype=np.float64),
+                        np.nextafter(2.0 ** np.arange(-300, 301, dtype=np.float64), 0.0),
+                        np.nextafter(2.0 ** np.arange(-300, 301, dtype=np.float64), np.inf),
+                        np.array([1.0, 3.0, 6.0, 7.0, 1.0 / 3.0, 127.9999, 1e-280, 1e280])])
+    d = G.check_rcp(torch.from_numpy(np.ascontiguousarray(x)).cuda()).cpu().numpy()
+    assert np.all(np.isfinite(d))
+    assert d.max() <= 2.0 ** -51, float(d.max())
