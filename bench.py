@@ -61,17 +61,17 @@ FP64_PEAK_TFLOPS = 2.0 * 2.0 * 152 * 2.070e9 / 1e12
 # captured on the 128^3 workload itself (one-pass metrics,
 # profiles/ncu_flux_star128_dram.md), scaled to a launch by its units.  The flux figures hold only at 128^3: the segment
 # lengths, and with them the x sweep's re-reads, depend on the size.
-TRAFFIC_PER_UNIT = {"flux_x": 364.5, "flux_y": 241.8, "flux_z": 243.6, "update": 733.6}
+TRAFFIC_PER_UNIT = {"flux_x": 353.9, "flux_y": 241.0, "flux_z": 241.9, "update": 733.6}
 TRAFFIC_SIZES = {"flux_x": (128,), "flux_y": (128,), "flux_z": (128,), "update": (128,)}
 # Kernels changed since their capture: their traffic is reported as null, with
 # the last capture beside it, until they are captured again.
-TRAFFIC_STALE = {"flux_x", "flux_y", "flux_z"}
+TRAFFIC_STALE = set()
 # FP64 thread instructions executed per face (ncu
 # sm__sass_thread_inst_executed_op_fp64_pred_on.sum per launch / faces, on the
 # 104^3 case, which has the 128^3 segment lengths; profiles/ncu_flux_star104_fp64.md),
 # for the issue-based fraction: executed FP64 instructions per second over
 # the pipe's 2 thread instructions per clock per SM at the sampled SM clock.
-FP64_INST_PER_UNIT = {"flux_x": 703.3, "flux_y": 672.1, "flux_z": 675.1}
+FP64_INST_PER_UNIT = {"flux_x": 697.3, "flux_y": 669.1, "flux_z": 669.1}
 FP64_ISSUE_PER_CLK_SM = 2.0
 
 # Algorithmic HBM bytes per zone and RK stage of one fused pass: read U (5),
@@ -158,6 +158,27 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_local_cpus(dev):
+    """The host cores next to the GPU (its PCI device's local_cpulist), or None."""
+    try:
+        import torch
+        pr = torch.cuda.get_device_properties(dev)
+        bus = f"{pr.pci_domain_id:04x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+        with open(f"/sys/bus/pci/devices/{bus}/local_cpulist") as f:
+            txt = f.read().strip()
+        cpus = set()
+        for part in txt.split(","):
+            if "-" in part:
+                a, b = part.split("-")
+                cpus.update(range(int(a), int(b) + 1))
+            elif part:
+                cpus.add(int(part))
+        cpus &= os.sched_getaffinity(0)
+        return cpus or None
+    except (OSError, ValueError, AttributeError, RuntimeError):
+        return None
 
 
 def star_inputs():
@@ -663,15 +684,26 @@ def run_ours(args):
     # end-to-end through the public API with host buffers: each step copies the
     # state (cons, face B~) and the metric from pinned host memory, advances one
     # RK3 step and reads the state back.
-    host = {
-        "cons": torch.empty_like(blk.cons, device="cpu").pin_memory(),
-        "adm": torch.empty_like(blk.adm, device="cpu").pin_memory(),
-        "bf": [torch.empty_like(x, device="cpu").pin_memory() for x in blk.bf],
-    }
-    host["cons"].copy_(blk.cons)
-    host["adm"].copy_(blk.adm)
-    for d in range(3):
-        host["bf"][d].copy_(blk.bf[d])
+    # the pinned host buffers are allocated and first touched by a thread on
+    # the cores next to the GPU, so that their pages sit in the host memory
+    # nearest to it (the affinity is restored afterwards)
+    local = gpu_local_cpus(dev)
+    saved = os.sched_getaffinity(0) if local and hasattr(os, "sched_setaffinity") else None
+    if saved is not None:
+        os.sched_setaffinity(0, local)
+    try:
+        host = {
+            "cons": torch.empty_like(blk.cons, device="cpu").pin_memory(),
+            "adm": torch.empty_like(blk.adm, device="cpu").pin_memory(),
+            "bf": [torch.empty_like(x, device="cpu").pin_memory() for x in blk.bf],
+        }
+        host["cons"].copy_(blk.cons)
+        host["adm"].copy_(blk.adm)
+        for d in range(3):
+            host["bf"][d].copy_(blk.bf[d])
+    finally:
+        if saved is not None:
+            os.sched_setaffinity(0, saved)
     h2d = host["cons"].numel() * 8 + host["adm"].numel() * 8 + sum(x.numel() * 8 for x in host["bf"])
     d2h = host["cons"].numel() * 8 + sum(x.numel() * 8 for x in host["bf"])
     barrier()
@@ -736,7 +768,9 @@ def run_ours(args):
                        "rk": "SSP-RK3", "recon": "WENO-Z", "riemann": "HLLE", "fofc": True, "ct": "upwind",
                        "con2prim": {0: "plain FP64", 1: "network + FP32 search + FP64",
                                     2: "FP32 search + FP64"}[C2P_GUESS]},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "host_buffers_on_cpus": (f"{min(local)}-{max(local)} ({len(local)} cores next to the GPU)"
+                                             if local else "default placement")},
             "gpu_launches": int(launches), "launch_shapes": tuned, "roofline": roofline, "hbm_roofline": hbm, "kernel_share": shares,
             "c2p_stats": stats, "clocks": clocks}
     line["profiled_pass"] = {"steps": prof_steps, "ms_per_step": sum(v[0] for v in kern.values()) / prof_steps,

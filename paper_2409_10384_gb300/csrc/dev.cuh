@@ -469,13 +469,13 @@ __device__ __forceinline__ void kev(const KS& s, double mu, KEval& e) {
   }
   const double rbar2 = N * id2;
   const double qbar = fma(-0.5 * mu2 * s.rperp2, id2, s.qh);
-  double wm1 = vh2 * W * W / (1.0 + W);  // W - 1 without cancellation
+  double wm1 = vh2 * W * W * rcp_nr(1.0 + W);  // W - 1 without cancellation (1 + W >= 2)
   e.eps_raw = fma(W, qbar - mu * rbar2, wm1);
   e.eps = gt_nn(s.eps_min, e.eps_raw) ? s.eps_min : e.eps_raw;
   e.x = x;
   e.rbar2 = rbar2;
   e.W = W;
-  e.G = mu - W / fma(mu * rbar2, W, fma(s.gam, e.eps, 1.0));
+  e.G = mu - W * rcp_nr(fma(mu * rbar2, W, fma(s.gam, e.eps, 1.0)));   // denominator >= 1
 }
 // f(mu) alone, with one division where kev takes two; for the bracket and
 // the root iteration (the recovery at the root uses kev).  With
@@ -562,7 +562,7 @@ __device__ __forceinline__ double kev_G(const KS& s, const Par& P, double mu) {
 __device__ __forceinline__ double f_zero(const KS& s, const Par& P) {
   if (P.eos != 0) return kev_G(s, P, 0.0);
   double e0 = gt_nn(s.eps_min, s.qh) ? s.eps_min : s.qh;
-  return -1.0 / fma(s.gam, e0, 1.0);
+  return -rcp_nr(fma(s.gam, e0, 1.0));   // >= 1
 }
 
 // Upper bracket end.  rbar^2(mu) = r_perp^2 x^2 + r_par^2 >= r_par^2 for every
@@ -641,7 +641,7 @@ __device__ __forceinline__ bool illinois(const KS& s, const Par& P, double a, do
       return true;
     }
   }
-  root = a - Ga * (b - a) / (Gb - Ga);
+  root = a - Ga * (b - a) * rcp_nr(Gb - Ga);   // Gb > 0 > Ga
   return true;
 }
 
@@ -1167,7 +1167,9 @@ __device__ __forceinline__ void face_side(const Par& P, const double* st, double
   const double den = fma(iW2 - 1.0, N, rhoh + b2);   // Dn - v^2 N, v^2 = 1 - 1/W^2
   const double X = fma(m.gi[d == 0 ? 0 : (d == 1 ? 3 : 5)], den, -(vd * vd) * Q);
   const double S = (N * iW2) * X;
-  o.sq = sqrt(S > 0.0 ? S : 0.0);
+  // sqrt(S) as S rsqrt(S): within ~1 ulp, in fewer FP64 issue slots than the
+  // correctly rounded square root (S <= 0 or NaN: 0, as before)
+  o.sq = gt0(S) ? S * rsqrt(S) : 0.0;
   o.vq = vd * Q;
   o.den = den;
 }

@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(256) k_krp_solve(Par P, KrpBuf kb, unsigned lo
       }
     }
     if (fin) {
-      if (!exact && !cap) root = a - Ga * (b - a) / (Gb - Ga);
+      if (!exact && !cap) root = a - Ga * (b - a) * rcp_nr(Gb - Ga);   // Gb > 0 > Ga
       kb.w[KW_MU * n + idx] = root;
       kb.it[idx] = it;
       kb.st[idx] = cap ? 3 : 1;
