@@ -285,6 +285,15 @@ __host__ __device__ __forceinline__ double upw(double fD, double a, double b, do
   if (mag - 1ull < 0x7FF0000000000000ull) return (u >> 63) ? c - d : a - b;   // fD != 0, not NaN
   return 0.5 * ((a - b) + (c - d));
 }
+// min / max of two doubles that are not NaN, on the integer pipe: the key
+// u ^ ((u >> 63) & 0x7FF..F) of the bit pattern u orders doubles as numbers
+// (-0 below +0), and an FP64 min or max would take a slot of the FP64 pipe.
+__host__ __device__ __forceinline__ long long okey(double x) {
+  const long long u = dbits(x);
+  return u ^ ((u >> 63) & 0x7FFFFFFFFFFFFFFFll);
+}
+__host__ __device__ __forceinline__ double imin(double a, double b) { return okey(b) < okey(a) ? b : a; }
+__host__ __device__ __forceinline__ double imax(double a, double b) { return okey(b) > okey(a) ? b : a; }
 // finite (not inf, not NaN): the exponent field is not all ones
 __host__ __device__ __forceinline__ bool finite_bits(double x) {
 #ifdef __CUDA_ARCH__
@@ -996,9 +1005,11 @@ __device__ __forceinline__ void wz_parts(RecVar& s, double xn, double& x, double
   const double b0 = s.b0p, b1 = s.b1c, b2 = b2n;
   const double tau = fabs(b0 - b2);
   const double e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
-  const double A0 = (e0 + tau) * (e1 * e2);
-  const double A1 = (e1 + tau) * (e0 * e2);
-  const double A2 = (e2 + tau) * (e0 * e1);
+  // A_k = (e_k + tau) prod_{j != k} e_j = P + tau prod_{j != k} e_j, P = e0 e1 e2
+  const double p12 = e1 * e2, p02 = e0 * e2, p01 = e0 * e1, P3 = p01 * e2;
+  const double A0 = fma(tau, p12, P3);
+  const double A1 = fma(tau, p02, P3);
+  const double A2 = fma(tau, p01, P3);
   const double a1 = 6.0 * A1, a2h = 3.0 * A2, a0l = 3.0 * A0;
   // Explicit FMAs: left to the compiler, these sums would be contracted by
   // the use count of each product, which differs where the caller drops the
@@ -1183,16 +1194,18 @@ __device__ __forceinline__ void riemann(int rs, const FaceMetric& fm, const Side
   const double lmL = fma(aL, L.vq - L.sq, -bd), lpL = fma(aL, L.vq + L.sq, -bd);
   const double lmR = fma(aR, R.vq - R.sq, -bd), lpR = fma(aR, R.vq + R.sq, -bd);
   if (rs == 1) {
-    const double lL = fmin(fmin(lmL, lmR), 0.0);
-    const double lR = fmax(fmax(lpL, lpR), 0.0);
-    if (lR == lL) {
+    // min / max on the integer pipe: the speeds are finite for physical
+    // states (a NaN state is caught by the con2prim of the next stage)
+    const double lL = imin(imin(lmL, lmR), 0.0);
+    const double lR = imax(imax(lpL, lpR), 0.0);
+    const double dl = lR - lL;   // >= 0
+    if (eq0(dl)) {
 #pragma unroll
       for (int c = 0; c < 7; c++) F[c] = 0.5 * (L.F[c] + R.F[c]);
     } else {
       // (lR F_L - lL F_R + lL lR (U_R - U_L)) / (lR - lL), with the division's
       // reciprocal folded into the three coefficients once per face
-      const double dl = lR - lL;   // > 0 here
-      const double inv = gt_nn(dl, 1e-280) ? rcp_nr(dl) : 1.0 / dl;
+      const double inv = gt_nn(dl, 1e-280) ? rcp_nr(dl) : 1.0 / dl;   // dl > 0 here
       const double cR = lR * inv, cL = -lL * inv, cLR = (lL * lR) * inv;
 #pragma unroll
       for (int c = 0; c < 7; c++) F[c] = fma(cR, L.F[c], fma(cL, R.F[c], cLR * (R.U[c] - L.U[c])));
