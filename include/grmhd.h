@@ -68,16 +68,21 @@ typedef struct {
   int c2p_maxit;    /* cap on root-solve iterations (64) */
   int c2p_guess;    /* root search of every con2prim (cells, stage input, FOFC U*):
                        0 FP64 Illinois on the plain bracket [0, mu+];
-                       1 network guess of log(mu), FP32 secant steps, FP64 bracket
-                         of relative width 4e-6 around the FP32 root, FP64 solve
-                         (needs a network: MHD_ENOMLP otherwise);
-                       2 as 1 but the FP32 steps start from the plain bracket;
+                       1 network guess of log(mu), FP32 secant steps, then the
+                         FP64 polish: two FP64 evaluations of f (a Newton step
+                         with the FP32 slope, then the FP64 secant), whose
+                         result is the root when both steps contracted
+                         (|m1 - m0| <= 2^-16 m0, |m2 - m1| <= 2^-30 m2), else
+                         a bracket for the FP64 Illinois solve (needs a network:
+                         MHD_ENOMLP otherwise);
+                       2 as 1 but the FP32 steps start from [0, mu+];
                        3 block con2prims: FP64 bracket of relative half-width
                          1e-3 around the cell's root of the last stage-input
                          con2prim (verified by the signs at both ends, else
                          the plain bracket); the FOFC estimate starts from the
                          same root.  A new block list starts without roots.
-                       The FP64 solve decides the root in every mode. */
+                       Every mode finds the same root of f in FP64 (modes 1, 2
+                       within the rounding of f; not bit-identical to 0). */
   int eos;          /* 0: ideal gas, P = (gamma-1) rho eps, T = P/rho.
                        1: hybrid piecewise polytrope (Sec. 3.4 names it as
                        PrimitiveSolver's second analytic EOS): a cold part
@@ -120,9 +125,9 @@ typedef struct {
   long long fofc_cells; /* cells flagged by FOFC (incl. DMP) */
   long long dmp_cells;  /* cells flagged by the DMP test */
   long long fofc_faces; /* faces recomputed at first order */
-  long long guess_fallbacks; /* c2p_guess 1, 2: cells whose FP32 root did not
-                                bracket the FP64 root within 4e-6 (the bracket
-                                then extends to 0 or 1) */
+  long long guess_fallbacks; /* c2p_guess 1, 2: cells whose FP64 polish was not
+                                taken as the root (the FP64 solve then runs from
+                                the bracket its two evaluations give) */
   long long fp32_evals; /* c2p_guess 1, 2: FP32 evaluations of the master
                            function in the searches (the two starting points
                            and one per secant step) */
@@ -290,8 +295,9 @@ int mhd_fill_ghosts(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, const in
 #define MHD_K_FACEB 8      /* RK update of the face B~ */
 #define MHD_K_SOLVE 9      /* con2prim root solves (stage input and U*) */
 #define MHD_K_MLP 10       /* learned guess: network inference fused with the
-                              FP32 search and the FP64 bracket (c2p_guess 1;
-                              c2p_guess 2 counts its search under MHD_K_C2P) */
+                              FP32 search and the FP64 polish (c2p_guess 1;
+                              c2p_guess 2 runs its search and polish in the
+                              prep, under MHD_K_C2P) */
 #define MHD_K_LEDGER 11    /* baryon-mass ledger (only with mhd_ledger on) */
 #define MHD_K_METRIC 12    /* the step's metric: sqrt(gamma), gamma^ij of the con2prim
                               region and the interpolated face metric (Eq. 8) of
@@ -312,8 +318,8 @@ const char* mhd_kernel_name(int kind);
  * accumulation on the tensor cores predicts log(mu) of the Kastaun et al. root
  * from five features of the cell's KRP variables; with mhd_params.c2p_guess = 1
  * every con2prim starts FP32 secant steps at the guess (second point at
- * exp(delta) x guess), brackets their result in FP64 (relative width 4e-6,
- * else out to 0 or 1) and solves as before: same root, fewer FP64 iterations.
+ * exp(delta) x guess) and polishes their result in FP64 (c2p_guess above):
+ * the same root, with fewer FP32 steps than from the plain bracket.
  * Features: float [n][MHD_MLP_FSTRIDE] (5 used); targets: float log(mu) [n].
  * State (get/set): MHD_MLP_NPARAM fp32 parameters (W1 [64][5], b1, W2
  * [64][64], b2, w3, b3), then feature mean [5], feature 1/std [5], target

@@ -19,7 +19,7 @@ struct mhd_ctx {
   int dev = 0, nsm = 1;
   int occ_c2p[2] = {1, 1}, occ_face[5] = {1, 1, 1, 1, 1}, occ_upd[3] = {1, 1, 1};
   int occ_krp[7] = {1, 1, 1, 1, 1, 1, 1};
-  int occ_seed[2] = {1, 1};   // seed kernel without / with the network
+  int occ_seed = 1;   // the learned seed kernel
   int occ_metric = 1;         // metric cache kernel
   // side streams and events of the forked flux sweeps (y, z)
   cudaStream_t side[2] = {nullptr, nullptr};
@@ -444,20 +444,20 @@ Work work_of(const mhd_ctx* c) {
 
 // One launch sequence over the work `w` with `items[W_NKIND]` items per kind
 // (all blocks of the list, or one block for per-block launches).
-// Between the prep and the FP64 root solve of a guessed con2prim (c2p_guess 1:
-// network guess; 2: FP32 search from the plain bracket): the seed kernel,
-// which runs the network (mode 1) on features it forms from the prep's KRP
-// variables and the FP32 search, and turns status-4 cells into FP64 brackets.
-void c2p_seed_mode(mhd_ctx* c, const KrpBuf& kb, long long n, int mode, cudaStream_t s) {
-  const int occ = std::max(c->occ_seed[mode == 1 ? 1 : 0], 1);
-  const long long g = std::max(1LL, std::min((n + 127) / 128, (long long)c->nsm * occ));
-  timed(c, mode == 1 ? MHD_K_MLP : MHD_K_C2P, s, [&] {
-    launch_krp_seed(c->P, kb, mode == 1 ? 1 : 0, (float)c->mlp_delta, c->mlp_wb, c->mlp, c->nm, c->dstats, s,
-                    (int)g);
-  });
-}
+// The prep's con2prim start for c2p_guess g: 1 (learned) leaves status 4 for
+// the seed kernel, 2 runs the FP32 search and FP64 polish in the prep, 0 and
+// 3 take the FP64 bracket (3 from the previous root where there is one).
+int prep_mode(int g) { return g == 1 || g == 2 ? g : 0; }
+// Between the prep and the FP64 root solve of the learned con2prim (c2p_guess
+// 1): the seed kernel, which runs the network on features it forms from the
+// prep's KRP variables, the FP32 search and the FP64 polish, and turns
+// status-4 cells into roots or FP64 brackets.
 void c2p_seed(mhd_ctx* c, const KrpBuf& kb, long long n, cudaStream_t s) {
-  if (c->P.guess == 1 || c->P.guess == 2) c2p_seed_mode(c, kb, n, c->P.guess, s);
+  if (c->P.guess != 1) return;
+  const long long g = std::max(1LL, std::min((n + 127) / 128, (long long)c->nsm * std::max(c->occ_seed, 1)));
+  timed(c, MHD_K_MLP, s, [&] {
+    launch_krp_seed(c->P, kb, (float)c->mlp_delta, c->mlp_wb, c->mlp, c->nm, c->dstats, s, (int)g);
+  });
 }
 
 // refresh: first compute the metric cache of the step (cells and faces)
@@ -471,12 +471,12 @@ int enqueue_c2p(mhd_ctx* c, cudaStream_t s, const Work& w, const long long* item
   KrpBuf kb = krp_view(c->krp, items[W_C2P]);
   const mhd_ctx::Cfg& cp = c->cfg[T_C2P_PREP];
   const mhd_ctx::Cfg& cf = c->cfg[T_C2P_FIN];
-  const int learned = (c->P.guess == 1 || c->P.guess == 2) ? 1 : 0;
   timed(c, MHD_K_C2P, s, [&] {
-    launch_krp_prep_block(w, c->P, kb, s, tgrid(c, T_C2P_PREP, items[W_C2P]), cp.threads, learned, nullptr);
+    launch_krp_prep_block(w, c->P, kb, c->dstats, s, tgrid(c, T_C2P_PREP, items[W_C2P]), cp.threads,
+                          prep_mode(c->P.guess), nullptr);
   });
   c2p_seed(c, kb, items[W_C2P], s);
-  timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, c->dstats, s, c->solve_grid(items[W_C2P])); });
+  timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, s, c->solve_grid(items[W_C2P])); });
   timed(c, MHD_K_C2P, s, [&] {
     launch_krp_finish_block(w, c->P, kb, c->dstats, s, tgrid(c, T_C2P_FIN, items[W_C2P]), cf.threads);
   });
@@ -511,11 +511,11 @@ int enqueue_rhs(mhd_ctx* c, double dt, int stage, cudaStream_t s, const Work& w,
     if (c->P.guess == 1 && !c->mlp_ready) return MHD_ENOMLP;
     KrpBuf kb = krp_view(c->krp, items[W_CELL]);
     timed(c, MHD_K_FOFC_FLAG, s, [&] {
-      launch_krp_prep_fofc(w, c->P, g0, g1, be * dt, kb, s, tgrid(c, T_FOFC_PREP, items[W_CELL]),
-                           c->cfg[T_FOFC_PREP].threads, (c->P.guess == 1 || c->P.guess == 2) ? 1 : 0, nullptr);
+      launch_krp_prep_fofc(w, c->P, g0, g1, be * dt, kb, c->dstats, s, tgrid(c, T_FOFC_PREP, items[W_CELL]),
+                           c->cfg[T_FOFC_PREP].threads, prep_mode(c->P.guess), nullptr);
     });
     c2p_seed(c, kb, items[W_CELL], s);
-    timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, c->dstats, s, c->solve_grid(items[W_CELL])); });
+    timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, s, c->solve_grid(items[W_CELL])); });
     timed(c, MHD_K_FOFC_FLAG, s, [&] {
       launch_krp_finish_fofc(w, c->P, kb, c->dstats, s, tgrid(c, T_FOFC_FIN, items[W_CELL]),
                              c->cfg[T_FOFC_FIN].threads);
@@ -660,8 +660,7 @@ int mhd_init(const mhd_params* p, mhd_ctx** out) {
     return MHD_ECUDA;
   }
   c->occ_metric = occ_metric_kernel();
-  c->occ_seed[0] = occ_seed_kernel(0);
-  c->occ_seed[1] = occ_seed_kernel(1);
+  c->occ_seed = occ_seed_kernel();
   for (int ti = 0; ti < 3; ti++) {
     const int th = 64 << ti;
     c->occ_t[T_C2P_PREP][ti] = occ_krp_kernel(0, th);
@@ -914,8 +913,9 @@ int mhd_c2p_cells(mhd_ctx* c, long n, double* cons, const double* Bd, const doub
 namespace {
 int c2p_cells_enqueue(mhd_ctx* c, long n, double* cons, const double* Bd, const double* g, double* prim,
                       unsigned char* flags, int* iters, cudaStream_t s) {
-  // 0 plain, 1 learned + FP32 search, 2 FP32 search from the plain bracket;
-  // independent cells have no previous root, so 3 solves as 0
+  // 0 plain, 1 learned + FP32 search + FP64 polish, 2 FP32 search from the
+  // plain bracket + FP64 polish; independent cells have no previous root, so 3
+  // solves as 0
   const int mode = c->P.guess == 3 ? 0 : c->P.guess;
   if (mode == 1 && !c->mlp_ready) return MHD_ENOMLP;
   KrpBuf kb;
@@ -923,10 +923,10 @@ int c2p_cells_enqueue(mhd_ctx* c, long n, double* cons, const double* Bd, const 
   int r = cells_scratch(c, n, s, &kb, &feat, &logmu);
   if (r) return r;
   timed(c, MHD_K_C2P, s, [&] {
-    launch_krp_prep_cells(c->P, kb, cons, Bd, g, mode != 0 ? 1 : 0, nullptr, s, cells_grid(c, n, c->occ_krp[5]));
+    launch_krp_prep_cells(c->P, kb, cons, Bd, g, mode, nullptr, c->dstats, s, cells_grid(c, n, c->occ_krp[5]));
   });
-  if (mode != 0) c2p_seed_mode(c, kb, n, mode, s);
-  timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, c->dstats, s, c->solve_grid(n)); });
+  c2p_seed(c, kb, n, s);
+  timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, s, c->solve_grid(n)); });
   timed(c, MHD_K_C2P, s, [&] {
     launch_krp_finish_cells(c->P, kb, cons, Bd, g, prim, flags, iters, c->dstats, s, cells_grid(c, n, c->occ_krp[6]));
   });
@@ -984,8 +984,8 @@ int mhd_mlp_dataset(mhd_ctx* c, long n, const double* cons, const double* Bd, co
   int r = cells_scratch(c, n, s, &kb, &f2, &l2);
   if (r) return r;
   Par P = c->P;
-  launch_krp_prep_cells(P, kb, cons, Bd, g, 0, feat, s, cells_grid(c, n, c->occ_krp[5]));
-  launch_krp_solve(P, kb, c->dstats, s, c->solve_grid(n));
+  launch_krp_prep_cells(P, kb, cons, Bd, g, 0, feat, c->dstats, s, cells_grid(c, n, c->occ_krp[5]));
+  launch_krp_solve(P, kb, s, c->solve_grid(n));
   launch_mlp_logmu(kb, logmu, s, c->nsm);
   c->launches += 3;
   return cuda_ok(cudaGetLastError());
@@ -1312,7 +1312,7 @@ int mhd_autotune(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, void* s
       const int th = c->cfg[k].threads;
       switch (k) {
         case T_C2P_PREP:
-          launch_krp_prep_block(w, c->P, kb, s, tgrid(c, k, it[W_C2P]), th, (c->P.guess == 1 || c->P.guess == 2) ? 1 : 0,
+          launch_krp_prep_block(w, c->P, kb, c->dstats, s, tgrid(c, k, it[W_C2P]), th, prep_mode(c->P.guess),
                                 nullptr);
           break;
         case T_C2P_FIN: launch_krp_finish_block(w, c->P, kb, c->dstats, s, tgrid(c, k, it[W_C2P]), th); break;
@@ -1320,8 +1320,8 @@ int mhd_autotune(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, void* s
           launch_flux_dir(k - T_FX, w, c->P, s, tgrid(c, k, it[W_SX + k - T_FX]), th);
           break;
         case T_FOFC_PREP:
-          launch_krp_prep_fofc(w, c->P, g0, g1, be * dt, kb, s, tgrid(c, k, it[W_CELL]), th,
-                               (c->P.guess == 1 || c->P.guess == 2) ? 1 : 0, nullptr);
+          launch_krp_prep_fofc(w, c->P, g0, g1, be * dt, kb, c->dstats, s, tgrid(c, k, it[W_CELL]), th,
+                               prep_mode(c->P.guess), nullptr);
           break;
         case T_FOFC_FIN: launch_krp_finish_fofc(w, c->P, kb, c->dstats, s, tgrid(c, k, it[W_CELL]), th); break;
         case T_EMF: launch_emf(w, s, tgrid(c, k, it[W_EDGE]), th); break;
@@ -1347,7 +1347,7 @@ int mhd_autotune(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, void* s
     if (k == T_C2P_PREP || k == T_FOFC_PREP) {
       launch();
       c2p_seed(c, kb, fofc_k ? it[W_CELL] : it[W_C2P], s);
-      launch_krp_solve(c->P, kb, c->dstats, s, c->solve_grid(fofc_k ? it[W_CELL] : it[W_C2P]));
+      launch_krp_solve(c->P, kb, s, c->solve_grid(fofc_k ? it[W_CELL] : it[W_C2P]));
     }
     if (cfg_out) {
       cfg_out[2 * k] = best.threads;

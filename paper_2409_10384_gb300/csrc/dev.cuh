@@ -199,7 +199,10 @@ struct KrpBuf {
   int* it;                   // [n] iterations
   unsigned char* st;         // [n] solve status
   unsigned char* fl;         // [n] flags of the prep phase
-  unsigned long long* ctr;   // work-queue head of the root solve
+  unsigned long long* ctr;   // [0] work-queue head of the root solve; [1] nonzero
+                             // when a cell may have status 0 (set by the kernels
+                             // that give status 0, cleared by the finish after the
+                             // solve: the solve returns at once on 0)
   long long n;
 };
 
@@ -753,6 +756,125 @@ __device__ __forceinline__ int krp_bracket(const KS& s, const Par& P, double glo
   return 0;
 }
 
+// ------------------------------------------- FP32 start for the KRP root
+// The FP32 pipe issues about 64 times the FP64 one on this part, so a root
+// estimate in FP32 is nearly free next to one FP64 evaluation of f.  These are
+// the master function and the upper bracket end in FP32 (ideal gas), the
+// secant search, and the slope estimate that the FP64 polish uses.
+struct KSf {
+  float qh, r2, b2, rb2, rp2, gam, emin, vmax2;
+};
+__device__ __forceinline__ KSf ks_f32(const KS& s) {
+  KSf f;
+  f.qh = (float)s.qh; f.r2 = (float)s.r2; f.b2 = (float)s.b2; f.rb2 = (float)s.rb2; f.rp2 = (float)s.rperp2;
+  f.gam = (float)s.gam; f.emin = fmaxf((float)s.eps_min, 1e-37f); f.vmax2 = (float)s.vmax2;
+  return f;
+}
+__device__ __forceinline__ float f32_master(const KSf& s, float mu) {
+  const float x = 1.0f / fmaf(mu, s.b2, 1.0f);
+  const float mux = mu * x;
+  const float rbar2 = x * fmaf(s.r2, x, mu * (1.0f + x) * s.rb2);
+  const float qbar = s.qh - 0.5f * mux * mux * s.rp2;
+  const float v2 = fminf(mu * mu * rbar2, s.vmax2);
+  const float W = rsqrtf(1.0f - v2);
+  const float wm1 = v2 * W * W / (1.0f + W);
+  const float eps = fmaxf(fmaf(W, qbar - mu * rbar2, wm1), s.emin);
+  return mu - W / fmaf(mu * rbar2, W, fmaf(s.gam, eps, 1.0f));
+}
+__device__ __forceinline__ float f32_mu_plus(const KSf& s) {
+  const float rpar2 = s.b2 > 0.0f ? s.rb2 / s.b2 : s.r2;
+  float mu = rsqrtf(1.0f + rpar2);
+  for (int it = 0; it < 3; it++) {
+    const float x = 1.0f / fmaf(mu, s.b2, 1.0f);
+    mu = rsqrtf(1.0f + x * fmaf(s.r2, x, mu * (1.0f + x) * s.rb2));
+  }
+  return mu;
+}
+// FP32 secant steps from the pair (x0, x1), at most nsteps, stopping once a
+// step moves mu by less than 2^-21 mu; nf counts the FP32 evaluations of f.
+__device__ __forceinline__ float krp_secant32(const KSf& sf, float x0, float x1, int nsteps, unsigned& nf) {
+  float f0 = f32_master(sf, x0), f1 = f32_master(sf, x1);
+  nf += 2;
+  for (int it = 0; it < nsteps; it++) {
+    const float den = f1 - f0;
+    if (den == 0.0f || !(f1 == f1)) break;
+    float x2 = x1 - f1 * (x1 - x0) / den;
+    if (!(x2 > 0.0f && x2 <= 1.0f)) x2 = 0.5f * (x1 + (f1 < 0.0f ? 1.0f : 0.0f));
+    const bool conv = fabsf(x2 - x1) <= 4.76837158e-7f * x1;   // 2^-21
+    x0 = x1; f0 = f1;
+    x1 = x2;
+    if (conv) break;
+    f1 = f32_master(sf, x2);
+    nf++;
+  }
+  return x1;
+}
+// FP32 estimate of 1/f'(mu): the central difference over mu (1 -+ 2^-8).
+__device__ __forceinline__ float krp_islope32(const KSf& sf, float mu, unsigned& nf) {
+  const float h = 0.00390625f * mu;
+  nf += 2;
+  return (2.0f * h) / (f32_master(sf, mu + h) - f32_master(sf, mu - h));
+}
+
+// FP64 root of f from the FP32 estimate m0 and isl ~ 1/f'(m0): a Newton step
+// with the FP32 slope, m1 = m0 - f(m0) isl, then the FP64 secant through
+// (m0, f(m0)) and (m1, f(m1)), m2 = m1 - f(m1) (m1 - m0)/(f(m1) - f(m0)).
+// The secant's error is about |f''/(2 f')| |m0 - mu*| |m1 - mu*|, so m2 is
+// taken as the root (returns 1, root in mu) when both steps contracted:
+// |m1 - m0| <= 2^-16 m0 and |m2 - m1| <= 2^-30 m2.  Otherwise the two
+// evaluations give the bracket for the FP64 solve (returns 0): [m_lo, m_hi]
+// when f changes sign between them, [m_hi, 1] when both are negative (f(1) >=
+// 0 for a physical state: one more evaluation), [0, m_lo] when both are
+// positive (f(0) < 0 from f_zero); a non-finite value falls back to the plain
+// bracket.  Returns 2 when there is no bracket, as krp_bracket does.  its
+// counts the FP64 evaluations of f; fb is set when the root was not taken.
+__device__ __forceinline__ int krp_polish(const KS& s, const Par& P, double m0, double isl, double& a, double& b,
+                                          double& Ga, double& Gb, double& mu, int& its, bool& fb) {
+  fb = false;
+  if (!(m0 > 1e-300 && m0 <= 1.0)) m0 = 0.5;
+  const double G0 = kev_g(s, m0);
+  its = 1;
+  if (eq0(G0)) { mu = m0; return 1; }
+  double m1 = fma(-G0, isl, m0);
+  if (!(m1 > 0.0)) m1 = 0.5 * m0;
+  if (!(m1 <= 1.0)) m1 = 1.0;
+  const double G1 = kev_g(s, m1);
+  its = 2;
+  if (eq0(G1)) { mu = m1; return 1; }
+  const double dm = m1 - m0, dG = G1 - G0;
+  const bool fin = finite_bits(G0) && finite_bits(G1);
+  if (fin && !eq0(dG)) {
+    const double q = gt_nn(fabs(dG), 1e-280) ? dm * rcp_nr(dG) : dm / dG;
+    const double m2 = fma(-G1, q, m1);
+    if (!gt_nn(fabs(dm), 1.52587890625e-5 * m0) && !gt_nn(fabs(m2 - m1), 9.313225746154785e-10 * m2) &&
+        gt0(m2) && !gt_nn(m2, 1.0)) {
+      mu = m2;
+      return 1;
+    }
+  }
+  fb = true;
+  if (!fin) {
+    int e = 0;
+    const int r = krp_bracket(s, P, -1.0, -1.0, a, b, Ga, Gb, mu, e);
+    its += e;
+    return r;
+  }
+  const bool o = m0 <= m1;
+  const double lo = o ? m0 : m1, hi = o ? m1 : m0, Glo = o ? G0 : G1, Ghi = o ? G1 : G0;
+  if (lt0(Glo) && !lt0(Ghi)) {
+    a = lo; Ga = Glo; b = hi; Gb = Ghi;
+  } else if (lt0(Ghi)) {
+    a = hi; Ga = Ghi; b = 1.0;
+    Gb = kev_g(s, 1.0);
+    its++;
+  } else {
+    a = 0.0; Ga = f_zero(s, P); b = lo; Gb = Glo;
+  }
+  if (!(lt0(Ga) && (eq0(Gb) || gt0(Gb)))) return 2;
+  if (eq0(Gb)) { mu = b; return 1; }
+  return 0;
+}
+
 // Phase 3: primitives at the root mu (Sec. 3.4 recovery) and the floors on
 // the primitives (Sec. 3.3).  On failure the static atmosphere.
 __device__ __forceinline__ void krp_finish(const Par& P, const KrpCell& k, double mu, bool ok, unsigned& flags,
@@ -839,24 +961,26 @@ __device__ __forceinline__ void con2prim(const Par& P, double* U, const double* 
 // Smoothness of the window (x_{c-1}, x_c, x_{c+1}) from dl = x_c - x_{c-1} and
 // dr = x_{c+1} - x_c, in the three one-sided forms of WENO5 (Jiang & Shu):
 // 13/12 (x0 - 2x1 + x2)^2 + 1/4 u^2 with u = x0 - 4x1 + 3x2 (b0), x0 - x2 (b1)
-// or 3x0 - 4x1 + x2 (b2).  With t = x0 - 2x1 + x2 and h = (x2 - x0)/2 these
-// are 13/12 t^2 + (t + h)^2, + h^2 and + (t - h)^2.
-__device__ __forceinline__ void wz_window(double dl, double dr, double& b0, double& b1, double& b2) {
-  const double k13 = 13.0 / 12.0;
+// or 3x0 - 4x1 + x2 (b2).  Returned scaled by 4 and with the WENO-Z epsilon
+// added, e_k = 4 (b_k + eps) = 13/3 t^2 + eps4 + u_k^2 with t = dr - dl and
+// u_0 = 3 dr - dl, u_1 = dl + dr, u_2 = dr - 3 dl: the WENO-Z weights are
+// homogeneous of degree 0 in (b_k + eps, |b_0 - b_2|), so the common factor
+// changes only rounding, and eps rides in the shared term's FMA.
+constexpr double WZ_EPS4 = 4e-40;   // 4 eps, eps = 1e-40
+__device__ __forceinline__ void wz_window(double dl, double dr, double& e0, double& e1, double& e2) {
   const double t = dr - dl;
-  const double h = 0.5 * (dl + dr);
-  const double kt2 = (k13 * t) * t;
-  const double h0 = t + h, h2 = t - h;
-  b0 = fma(h0, h0, kt2);
-  b1 = fma(h, h, kt2);
-  b2 = fma(h2, h2, kt2);
+  const double kt2 = fma((13.0 / 3.0) * t, t, WZ_EPS4);
+  const double u0 = fma(3.0, dr, -dl), u1 = dl + dr, u2 = fma(-3.0, dl, dr);
+  e0 = fma(u0, u0, kt2);
+  e1 = fma(u1, u1, kt2);
+  e2 = fma(u2, u2, kt2);
 }
 
 // Sliding state of one reconstructed variable at cell m of a sweep.
 struct RecVar {
   double x1, x2;          // x_m, x_{m+1}
   double d0, d1, d2;      // delta_{m-2}, delta_{m-1}, delta_m
-  double b0p, b0c, b1c;   // b0 of window m-1, b0 and b1 of window m
+  double e0p, e0c, e1c;   // e0 of window m-1, e0 and e1 of window m (wz_window)
   double xm2, xm1;        // PPM: x_{m-2}, x_{m-1}
   double aL, dm;          // PPM: value at the face m-1/2; PPM4: limited slope of cell m
 };
@@ -942,8 +1066,8 @@ __device__ __forceinline__ void rec_init(RecVar& s, double xm2, double xm1, doub
   s.d2 = xp1 - x0;
   if (R == 2) {
     double u, v;
-    wz_window(s.d0, s.d1, s.b0p, u, v);
-    wz_window(s.d1, s.d2, s.b0c, s.b1c, v);
+    wz_window(s.d0, s.d1, s.e0p, u, v);
+    wz_window(s.d1, s.d2, s.e0c, s.e1c, v);
   }
 }
 
@@ -999,12 +1123,10 @@ __device__ __forceinline__ void rec_step(RecVar& s, double xn, double& lo, doubl
 __device__ __forceinline__ void wz_parts(RecVar& s, double xn, double& x, double& n_hi, double& n_lo, double& d_hi,
                                          double& d_lo) {
   const double dn = xn - s.x2;
-  double b0n, b1n, b2n;
-  wz_window(s.d2, dn, b0n, b1n, b2n);
-  const double eps = 1e-40;
-  const double b0 = s.b0p, b1 = s.b1c, b2 = b2n;
-  const double tau = fabs(b0 - b2);
-  const double e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
+  double e0n, e1n, e2n;
+  wz_window(s.d2, dn, e0n, e1n, e2n);
+  const double e0 = s.e0p, e1 = s.e1c, e2 = e2n;   // 4 (b_k + eps)
+  const double tau = fabs(e0 - e2);                 // 4 tau5
   // A_k = (e_k + tau) prod_{j != k} e_j = P + tau prod_{j != k} e_j, P = e0 e1 e2
   const double p12 = e1 * e2, p02 = e0 * e2, p01 = e0 * e1, P3 = p01 * e2;
   const double A0 = fma(tau, p12, P3);
@@ -1021,9 +1143,9 @@ __device__ __forceinline__ void wz_parts(RecVar& s, double xn, double& x, double
   n_hi = fma(A0, fma(5.0, db, -2.0 * da), fma(a1, fma(2.0, dc, db), a2h * fma(4.0, dc, -dd)));
   n_lo = fma(A2, fma(-5.0, dc, 2.0 * dd), fma(-a1, fma(2.0, db, dc), a0l * fma(-4.0, db, da)));
   x = s.x1;
-  s.b0p = s.b0c;
-  s.b0c = b0n;
-  s.b1c = b1n;
+  s.e0p = s.e0c;
+  s.e0c = e0n;
+  s.e1c = e1n;
   s.x1 = s.x2;
   s.x2 = xn;
   s.d0 = s.d1;
@@ -1035,8 +1157,8 @@ __device__ __forceinline__ void wz_parts(RecVar& s, double xn, double& x, double
 // (Montgomery's simultaneous inversion): the products p_v = d_hi d_lo are
 // scaled to [1, 2) by their binary exponents (integer operations), chained,
 // inverted once and unchained; 1/(6 p_v) regains its exponent the same way.
-// Products outside [2^-959, 2^977] (never for physical data: eps = 1e-40
-// bounds them below by ~1e-238) take one division each.
+// Products outside [2^-959, 2^977] (never for physical data: eps4 = 4e-40
+// bounds them below by ~4e-235) take one division each.
 template <int N>
 __device__ __forceinline__ void wz_finish(const double* x, const double* n_hi, const double* n_lo,
                                           const double* d_hi, const double* d_lo, double* hi, double* lo) {
@@ -1304,6 +1426,11 @@ __host__ __device__ inline void rk_weights(int order, int stage, double& g0, dou
 __device__ __forceinline__ void warp_flush(unsigned long long* ctr, unsigned v) {
   unsigned s = __reduce_add_sync(0xffffffffu, v);
   if ((threadIdx.x & 31) == 0 && s) atomicAdd(ctr, (unsigned long long)s);
+}
+// Marks the solve's work list as non-empty when any lane of the warp gave a
+// cell status 0 (every lane of the warp calls it).
+__device__ __forceinline__ void warp_mark_solve(const KrpBuf& kb, bool any0) {
+  if (__any_sync(0xffffffffu, any0) && (threadIdx.x & 31) == 0) kb.ctr[1] = 1ull;
 }
 
 }  // namespace grmhd

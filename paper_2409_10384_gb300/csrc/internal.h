@@ -40,17 +40,21 @@ void launch_block_mass(const Work& w, double* out, cudaStream_t s);
 void launch_update_faces(const Work& w, double g0, double g1, double bdt, int first, cudaStream_t s, int grid);
 size_t krp_bytes(long long n);
 KrpBuf krp_view(void* base, long long n);
-void launch_krp_prep_block(const Work& w, const Par& P, const KrpBuf& kb, cudaStream_t s, int grid, int threads = 128,
-                           int learned = 0, float* feat = nullptr);
-void launch_krp_solve(const Par& P, const KrpBuf& kb, unsigned long long* stats, cudaStream_t s, int grid);
+// mode: the prep's con2prim start (0 plain bracket, 1 status 4 for the seed
+// kernel's network, 2 FP32 search and FP64 polish); stats: the context's
+// counters (mode 2 adds its FP32 evaluations and polish fallbacks)
+void launch_krp_prep_block(const Work& w, const Par& P, const KrpBuf& kb, unsigned long long* stats, cudaStream_t s,
+                           int grid, int threads = 128, int mode = 0, float* feat = nullptr);
+void launch_krp_solve(const Par& P, const KrpBuf& kb, cudaStream_t s, int grid);
 void launch_krp_finish_block(const Work& w, const Par& P, const KrpBuf& kb, unsigned long long* stats,
                              cudaStream_t s, int grid, int threads = 128);
 void launch_krp_prep_fofc(const Work& w, const Par& P, double g0, double g1, double bdt, const KrpBuf& kb,
-                          cudaStream_t s, int grid, int threads = 128, int learned = 0, float* feat = nullptr);
+                          unsigned long long* stats, cudaStream_t s, int grid, int threads = 128, int mode = 0,
+                          float* feat = nullptr);
 void launch_krp_finish_fofc(const Work& w, const Par& P, const KrpBuf& kb, unsigned long long* stats,
                             cudaStream_t s, int grid, int threads = 128);
 void launch_krp_prep_cells(const Par& P, const KrpBuf& kb, const double* cons, const double* Bd, const double* g,
-                           int learned, float* feat, cudaStream_t s, int grid);
+                           int mode, float* feat, unsigned long long* stats, cudaStream_t s, int grid);
 void launch_krp_finish_cells(const Par& P, const KrpBuf& kb, double* cons, const double* Bd, const double* g,
                              double* prim, unsigned char* flags, int* iters, unsigned long long* stats, cudaStream_t s,
                              int grid);
@@ -65,11 +69,11 @@ void launch_mlp_adam(float* w, float* m, float* v, float* grad, float lr, int t,
 void launch_mlp_pack(const float* w, __nv_bfloat16* wb, cudaStream_t s);
 void launch_mlp_logmu(const KrpBuf& kb, float* out, cudaStream_t s, int nsm);
 void launch_mlp_stats(const float* feat, const float* target, long long n, double* acc, cudaStream_t s, int nsm);
-// FP32 search and FP64 bracket of every status-4 cell; learned != 0: from the
-// network's guess, inferred in the same kernel (wb, w, nm: its operands)
-void launch_krp_seed(const Par& P, const KrpBuf& kb, int learned, float delta, const __nv_bfloat16* wb,
-                     const float* w, const MlpNorm& nm, unsigned long long* stats, cudaStream_t s, int grid);
-int occ_seed_kernel(int learned);
+// Network guess (inferred in the kernel; wb, w, nm: its operands), FP32
+// search and FP64 polish of every status-4 cell
+void launch_krp_seed(const Par& P, const KrpBuf& kb, float delta, const __nv_bfloat16* wb, const float* w,
+                     const MlpNorm& nm, unsigned long long* stats, cudaStream_t s, int grid);
+int occ_seed_kernel();
 int occupancy_c2p(int* per_sm);
 int occ_face_kernel(int kind, int threads);
 int occ_krp_kernel(int kind, int threads);

@@ -32,19 +32,22 @@ __device__ __forceinline__ void kw_load(const KrpBuf& kb, const Par& P, long lon
   k.bu[0] = w[KW_BU0 * n + i]; k.bu[1] = w[KW_BU1 * n + i]; k.bu[2] = w[KW_BU2 * n + i];
 }
 
-// prep of one cell: KRP variables and status; learned = false: the plain
-// bracket [0, mu+]; learned = true: status 4 (bracket from the network's
-// guess later).  feat (optional): the network's features of the cell.
-// guess > 0: the cell's previous root; the FP64 bracket starts as
-// guess (1 -+ WARM_DELTA), verified by the signs at both ends (krp_bracket).
+// prep of one cell: KRP variables and status.  mode 0: the plain bracket
+// [0, mu+]; mode 1: status 4 (the seed kernel's network guess and FP32 search
+// come later); mode 2: the FP32 secant search from [0, mu+] and the FP64
+// polish here (krp_polish), the root when it is taken, else a bracket.
+// feat (optional): the network's features of the cell.  guess > 0 (mode 0):
+// the cell's previous root; the FP64 bracket starts as guess (1 -+
+// WARM_DELTA), verified by the signs at both ends (krp_bracket).
 // fofc: the FOFC estimate, which only needs to know whether con2prim of U*
 // fails or a floor fires (Sec. 3.3); a floor on the conserved state decides
 // that before the solve, so such a cell gets status 5 (flagged, no bracket,
-// no solve, no recovery).
-__device__ __forceinline__ void prep_cell(const Par& P, const KrpBuf& kb, long long i, const double* U,
-                                          const double* Bd, const Metric& m, bool learned = false,
-                                          float* feat = nullptr, double alpha = 1.0, double guess = 0.0,
-                                          bool fofc = false) {
+// no solve, no recovery).  nf32 / nfb count the FP32 evaluations and the
+// cells whose polish was not taken (mode 2).
+__device__ __forceinline__ unsigned char prep_cell(const Par& P, const KrpBuf& kb, long long i, const double* U,
+                                          const double* Bd, const Metric& m, int mode, unsigned& nf32,
+                                          unsigned& nfb, float* feat = nullptr, double alpha = 1.0,
+                                          double guess = 0.0, bool fofc = false) {
   KrpCell k;
   unsigned fl;
   const long long n = kb.n;
@@ -54,14 +57,24 @@ __device__ __forceinline__ void prep_cell(const Par& P, const KrpBuf& kb, long l
     if (feat) krp_features(k.s, feat + i * MLP_FSTRIDE);
     if (fofc && (fl & (F_DFLOOR | F_SIGMA | F_TAU))) {
       st = 5;
-    } else if (learned) {
+    } else if (mode == 1) {
       st = 4;
     } else {
-      double a, b, Ga, Gb, mu = 0.0;
-      const bool warm = guess > 0.0 && guess <= 1.0;
-      const double glo = warm ? guess * (1.0 - WARM_DELTA) : -1.0;
-      const double ghi = warm ? fmin(guess * (1.0 + WARM_DELTA), 1.0) : -1.0;
-      int r = krp_bracket(k.s, P, glo, ghi, a, b, Ga, Gb, mu, its);
+      double a = 0.0, b = 1.0, Ga = -1.0, Gb = 1.0, mu = 0.0;
+      int r;
+      if (mode == 2) {
+        const KSf sf = ks_f32(k.s);
+        const float m32 = krp_secant32(sf, 0.0f, f32_mu_plus(sf), 8, nf32);
+        const float isl = krp_islope32(sf, m32, nf32);
+        bool fb;
+        r = krp_polish(k.s, P, (double)m32, (double)isl, a, b, Ga, Gb, mu, its, fb);
+        nfb += fb ? 1u : 0u;
+      } else {
+        const bool warm = guess > 0.0 && guess <= 1.0;
+        const double glo = warm ? guess * (1.0 - WARM_DELTA) : -1.0;
+        const double ghi = warm ? fmin(guess * (1.0 + WARM_DELTA), 1.0) : -1.0;
+        r = krp_bracket(k.s, P, glo, ghi, a, b, Ga, Gb, mu, its);
+      }
       st = (unsigned char)(r == 0 ? 0 : (r == 1 ? 1 : 2));
       kb.w[KW_A * n + i] = a; kb.w[KW_B * n + i] = b;
       kb.w[KW_GA * n + i] = Ga; kb.w[KW_GB * n + i] = Gb;
@@ -76,6 +89,7 @@ __device__ __forceinline__ void prep_cell(const Par& P, const KrpBuf& kb, long l
   kb.st[i] = st;
   kb.fl[i] = (unsigned char)fl;
   kb.it[i] = its;
+  return st;
 }
 
 __device__ __forceinline__ void load_metric6(const double* g6, long long stride, long long c, Metric& m) {
@@ -88,7 +102,8 @@ __device__ __forceinline__ void load_metric6(const double* g6, long long stride,
 // Illinois regula falsi with the end-point nudge (as in `illinois`) and lane
 // refill.  Reads the
 // bracket of every status-0 cell, writes mu, iterations and status 1 or 3.
-__global__ void __launch_bounds__(256) k_krp_solve(Par P, KrpBuf kb, unsigned long long* stats) {
+__global__ void __launch_bounds__(256) k_krp_solve(Par P, KrpBuf kb) {
+  if (*(volatile unsigned long long*)&kb.ctr[1] == 0ull) return;   // no cell has status 0
   const unsigned lane = threadIdx.x & 31;
   const long long n = kb.n;
   long long idx = -1;
@@ -99,7 +114,6 @@ __global__ void __launch_bounds__(256) k_krp_solve(Par P, KrpBuf kb, unsigned lo
   s.D = 1.0;
   double a = 0.0, b = 1.0, Ga = -1.0, Gb = 1.0, Fa = -1.0, Fb = 1.0;
   int side = 0, it = 0;
-  unsigned s_it = 0, s_cap = 0;
   while (true) {
     const bool need = idx < 0 && !done;
     const unsigned m = __ballot_sync(0xffffffffu, need);
@@ -161,20 +175,19 @@ __global__ void __launch_bounds__(256) k_krp_solve(Par P, KrpBuf kb, unsigned lo
       kb.w[KW_MU * n + idx] = root;
       kb.it[idx] = it;
       kb.st[idx] = cap ? 3 : 1;
-      s_it += it;
-      s_cap += cap ? 1u : 0u;
       idx = -1;
     }
   }
-  warp_flush(&stats[1], s_it);
-  (void)s_cap;
 }
 
 // -------------------------------------------------------- block stage con2prim
-__global__ void __launch_bounds__(256) k_krp_prep_block(Work w, Par P, KrpBuf kb, int learned, float* feat) {
+__global__ void __launch_bounds__(256) k_krp_prep_block(Work w, Par P, KrpBuf kb, int mode, float* feat,
+                                                         unsigned long long* stats) {
   const long long* pre = w.pre + (long long)W_C2P * (w.nblocks + 1);
   const long long tot = pre[w.nblocks];
   if (blockIdx.x == 0 && threadIdx.x == 0) *kb.ctr = 0ull;
+  unsigned s_f32 = 0, s_fb = 0;
+  bool any0 = false;
   for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < tot; it += (long long)gridDim.x * blockDim.x) {
     const int bi = find_block(w, W_C2P, it);
     const DevBlock& b = w.blk[bi];
@@ -194,7 +207,12 @@ __global__ void __launch_bounds__(256) k_krp_prep_block(Work w, Par P, KrpBuf kb
     double U[5];
 #pragma unroll
     for (int v = 0; v < 5; v++) U[v] = b.cons[v * nc + c];
-    prep_cell(P, kb, it, U, Bd, m, learned != 0, feat, b.adm[c], b.mu ? b.mu[c] : 0.0);
+    any0 |= prep_cell(P, kb, it, U, Bd, m, mode, s_f32, s_fb, feat, b.adm[c], b.mu ? b.mu[c] : 0.0) == 0;
+  }
+  warp_mark_solve(kb, any0);
+  if (mode == 2) {
+    warp_flush(&stats[7], s_fb);
+    warp_flush(&stats[8], s_f32);
   }
 }
 
@@ -202,7 +220,8 @@ __global__ void __launch_bounds__(256) k_krp_finish_block(Work w, Par P, KrpBuf 
   const long long* pre = w.pre + (long long)W_C2P * (w.nblocks + 1);
   const long long tot = pre[w.nblocks];
   const long long n = kb.n;
-  unsigned s_cells = 0, s_fail = 0, s_floor = 0;
+  unsigned s_cells = 0, s_fail = 0, s_floor = 0, s_it = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) kb.ctr[1] = 0ull;   // the solve has run
   for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < tot; it += (long long)gridDim.x * blockDim.x) {
     const int bi = find_block(w, W_C2P, it);
     const DevBlock& b = w.blk[bi];
@@ -249,10 +268,12 @@ __global__ void __launch_bounds__(256) k_krp_finish_block(Work w, Par P, KrpBuf 
       b.ecc[2 * nc + c] = -(a0 * Bd[1] - a1 * Bd[0]);
     }
     s_cells++;
+    s_it += (unsigned)kb.it[it];
     s_fail += (fl & F_FAIL) ? 1u : 0u;
     s_floor += (fl & FLOOR_BITS) ? 1u : 0u;
   }
   warp_flush(&stats[0], s_cells);
+  warp_flush(&stats[1], s_it);
   warp_flush(&stats[2], s_fail);
   warp_flush(&stats[3], s_floor);
 }
@@ -268,10 +289,12 @@ __device__ __forceinline__ void fofc_cell(const Work& w, long long it, int& bi, 
 }
 
 __global__ void __launch_bounds__(256) k_krp_prep_fofc(Work w, Par P, double g0, double g1, double bdt, KrpBuf kb,
-                                                        int learned, float* feat) {
+                                                        int mode, float* feat, unsigned long long* stats) {
   const long long tot = w.pre[(long long)W_CELL * (w.nblocks + 1) + w.nblocks];
   if (blockIdx.x == 0 && threadIdx.x == 0) *kb.ctr = 0ull;
   const long long n = kb.n;
+  unsigned s_f32 = 0, s_fb = 0;
+  bool any0 = false;
   for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < tot; it += (long long)gridDim.x * blockDim.x) {
     int bi, k, j, i;
     fofc_cell(w, it, bi, k, j, i);
@@ -293,9 +316,14 @@ __global__ void __launch_bounds__(256) k_krp_prep_fofc(Work w, Par P, double g0,
     Metric m;
     metric_cell(b.adm, b.mc, nc, c, m);
     const double Bd[3] = {b.bcc[c], b.bcc[nc + c], b.bcc[2 * nc + c]};
-    prep_cell(P, kb, it, U, Bd, m, learned != 0, feat, b.adm[c], b.mu ? b.mu[c] : 0.0, true);
+    any0 |= prep_cell(P, kb, it, U, Bd, m, mode, s_f32, s_fb, feat, b.adm[c], b.mu ? b.mu[c] : 0.0, true) == 0;
     kb.w[KW_USD * n + it] = U[0];
     kb.w[KW_UST * n + it] = U[4];
+  }
+  warp_mark_solve(kb, any0);
+  if (mode == 2) {
+    warp_flush(&stats[7], s_fb);
+    warp_flush(&stats[8], s_f32);
   }
 }
 
@@ -303,6 +331,7 @@ __global__ void __launch_bounds__(256) k_krp_finish_fofc(Work w, Par P, KrpBuf k
   const long long tot = w.pre[(long long)W_CELL * (w.nblocks + 1) + w.nblocks];
   const long long n = kb.n;
   unsigned s_flag = 0, s_dmp = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) kb.ctr[1] = 0ull;   // the solve has run
   for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < tot; it += (long long)gridDim.x * blockDim.x) {
     int bi, k, j, i;
     fofc_cell(w, it, bi, k, j, i);
@@ -351,9 +380,12 @@ __global__ void __launch_bounds__(256) k_krp_finish_fofc(Work w, Par P, KrpBuf k
 // ------------------------------------------------------- independent cells
 __global__ void __launch_bounds__(128) k_krp_prep_cells(Par P, KrpBuf kb, const double* __restrict__ cons,
                                                         const double* __restrict__ Bd, const double* __restrict__ g,
-                                                        int learned, float* __restrict__ feat) {
+                                                        int mode, float* __restrict__ feat,
+                                                        unsigned long long* stats) {
   const long long n = kb.n;
   if (blockIdx.x == 0 && threadIdx.x == 0) *kb.ctr = 0ull;
+  unsigned s_f32 = 0, s_fb = 0;
+  bool any0 = false;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
     Metric m;
     load_metric6(g, n, c, m);
@@ -362,7 +394,12 @@ __global__ void __launch_bounds__(128) k_krp_prep_cells(Par P, KrpBuf kb, const 
     for (int v = 0; v < 5; v++) U[v] = cons[v * n + c];
 #pragma unroll
     for (int v = 0; v < 3; v++) B[v] = Bd[v * n + c];
-    prep_cell(P, kb, c, U, B, m, learned != 0, feat);
+    any0 |= prep_cell(P, kb, c, U, B, m, mode, s_f32, s_fb, feat) == 0;
+  }
+  warp_mark_solve(kb, any0);
+  if (mode == 2) {
+    warp_flush(&stats[7], s_fb);
+    warp_flush(&stats[8], s_f32);
   }
 }
 
@@ -371,7 +408,8 @@ __global__ void __launch_bounds__(128) k_krp_finish_cells(Par P, KrpBuf kb, doub
                                                           double* __restrict__ prim, unsigned char* __restrict__ flags,
                                                           int* __restrict__ iters_out, unsigned long long* stats) {
   const long long n = kb.n;
-  unsigned s_cells = 0, s_fail = 0, s_floor = 0;
+  unsigned s_cells = 0, s_fail = 0, s_floor = 0, s_it = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) kb.ctr[1] = 0ull;   // the solve has run
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
     KrpCell kc;
     kw_load(kb, P, c, kc);
@@ -395,10 +433,12 @@ __global__ void __launch_bounds__(128) k_krp_finish_cells(Par P, KrpBuf kb, doub
     flags[c] = (unsigned char)fl;
     if (iters_out) iters_out[c] = kb.it[c];
     s_cells++;
+    s_it += (unsigned)kb.it[c];
     s_fail += (fl & F_FAIL) ? 1u : 0u;
     s_floor += (fl & FLOOR_BITS) ? 1u : 0u;
   }
   warp_flush(&stats[0], s_cells);
+  warp_flush(&stats[1], s_it);
   warp_flush(&stats[2], s_fail);
   warp_flush(&stats[3], s_floor);
 }
@@ -424,28 +464,28 @@ KrpBuf krp_view(void* base, long long n) {
   return kb;
 }
 
-void launch_krp_prep_block(const Work& w, const Par& P, const KrpBuf& kb, cudaStream_t s, int grid, int threads,
-                           int learned, float* feat) {
-  k_krp_prep_block<<<grid, threads, 0, s>>>(w, P, kb, learned, feat);
+void launch_krp_prep_block(const Work& w, const Par& P, const KrpBuf& kb, unsigned long long* stats, cudaStream_t s,
+                           int grid, int threads, int mode, float* feat) {
+  k_krp_prep_block<<<grid, threads, 0, s>>>(w, P, kb, mode, feat, stats);
 }
-void launch_krp_solve(const Par& P, const KrpBuf& kb, unsigned long long* stats, cudaStream_t s, int grid) {
-  k_krp_solve<<<grid, 256, 0, s>>>(P, kb, stats);
+void launch_krp_solve(const Par& P, const KrpBuf& kb, cudaStream_t s, int grid) {
+  k_krp_solve<<<grid, 256, 0, s>>>(P, kb);
 }
 void launch_krp_finish_block(const Work& w, const Par& P, const KrpBuf& kb, unsigned long long* stats,
                              cudaStream_t s, int grid, int threads) {
   k_krp_finish_block<<<grid, threads, 0, s>>>(w, P, kb, stats);
 }
 void launch_krp_prep_fofc(const Work& w, const Par& P, double g0, double g1, double bdt, const KrpBuf& kb,
-                          cudaStream_t s, int grid, int threads, int learned, float* feat) {
-  k_krp_prep_fofc<<<grid, threads, 0, s>>>(w, P, g0, g1, bdt, kb, learned, feat);
+                          unsigned long long* stats, cudaStream_t s, int grid, int threads, int mode, float* feat) {
+  k_krp_prep_fofc<<<grid, threads, 0, s>>>(w, P, g0, g1, bdt, kb, mode, feat, stats);
 }
 void launch_krp_finish_fofc(const Work& w, const Par& P, const KrpBuf& kb, unsigned long long* stats,
                             cudaStream_t s, int grid, int threads) {
   k_krp_finish_fofc<<<grid, threads, 0, s>>>(w, P, kb, stats);
 }
 void launch_krp_prep_cells(const Par& P, const KrpBuf& kb, const double* cons, const double* Bd, const double* g,
-                           int learned, float* feat, cudaStream_t s, int grid) {
-  k_krp_prep_cells<<<grid, 128, 0, s>>>(P, kb, cons, Bd, g, learned, feat);
+                           int mode, float* feat, unsigned long long* stats, cudaStream_t s, int grid) {
+  k_krp_prep_cells<<<grid, 128, 0, s>>>(P, kb, cons, Bd, g, mode, feat, stats);
 }
 void launch_krp_finish_cells(const Par& P, const KrpBuf& kb, double* cons, const double* Bd, const double* g,
                              double* prim, unsigned char* flags, int* iters, unsigned long long* stats, cudaStream_t s,

@@ -449,57 +449,25 @@ __global__ void k_mlp_stats(const float* __restrict__ feat, const float* __restr
   }
 }
 
-// ------------------------------------------------- FP32 search, FP64 bracket
-// The master function in FP32 (the KRP variables rounded to float).  GB300's
-// FP32 pipe is ~60x wider than its FP64 pipe, so the root search runs here and
-// FP64 only verifies and refines.
-struct KSf {
-  float qh, r2, b2, rb2, rp2, gam, emin, vmax2;
-};
-__device__ __forceinline__ float f32_master(const KSf& s, float mu) {
-  const float x = 1.0f / fmaf(mu, s.b2, 1.0f);
-  const float mux = mu * x;
-  const float rbar2 = x * fmaf(s.r2, x, mu * (1.0f + x) * s.rb2);
-  const float qbar = s.qh - 0.5f * mux * mux * s.rp2;
-  const float v2 = fminf(mu * mu * rbar2, s.vmax2);
-  const float W = rsqrtf(1.0f - v2);
-  const float wm1 = v2 * W * W / (1.0f + W);
-  const float eps = fmaxf(fmaf(W, qbar - mu * rbar2, wm1), s.emin);
-  return mu - W / fmaf(mu * rbar2, W, fmaf(s.gam, eps, 1.0f));
-}
-__device__ __forceinline__ float f32_mu_plus(const KSf& s) {
-  const float rpar2 = s.b2 > 0.0f ? s.rb2 / s.b2 : s.r2;
-  float mu = rsqrtf(1.0f + rpar2);
-  for (int it = 0; it < 3; it++) {
-    const float x = 1.0f / fmaf(mu, s.b2, 1.0f);
-    mu = rsqrtf(1.0f + x * fmaf(s.r2, x, mu * (1.0f + x) * s.rb2));
-  }
-  return mu;
-}
-
-// Cells with status 4.  Starting pair: the network's guess mu_g and mu_g e^d
-// (learned = 1; the network runs here, on features formed in registers from
-// the cell's KRP variables), or 0 and the FP32 mu+ (learned = 0).  FP32 secant
-// steps (at most 5 from a guess, 8 from the plain bracket; they stop once a
-// step moves mu by less than 2^-21 mu) give mu32; FP64 then evaluates f at
-// mu32 and at mu32 (1 +- 4e-6) towards the root.  A sign change is a bracket
-// of relative width 4e-6; else the bracket extends from the far point to 0
-// (f(0) < 0, no evaluation) or 1 (f(1) >= 0 for a physical state).  The
-// refill solve finishes from there.  Warps take tiles of 32 consecutive cells
-// (the network is a warp-wide product).
-__global__ void __launch_bounds__(128) k_krp_seed(Par P, KrpBuf kb, int learned, float delta,
-                                                  const __nv_bfloat16* __restrict__ wb, const float* __restrict__ wf,
-                                                  MlpNorm nm, unsigned long long* stats) {
+// ------------------------------------ network guess, FP32 search, FP64 polish
+// Cells with status 4.  The network runs here, on features formed in
+// registers from the cell's KRP variables; its guess mu_g and mu_g e^delta
+// start at most 5 FP32 secant steps (krp_secant32, dev.cuh), and the FP64
+// polish (krp_polish) takes the root or leaves a bracket for the refill solve.
+// Warps take tiles of 32 consecutive cells (the network is a warp-wide
+// product).
+__global__ void __launch_bounds__(128) k_krp_seed(Par P, KrpBuf kb, float delta, const __nv_bfloat16* __restrict__ wb,
+                                                  const float* __restrict__ wf, MlpNorm nm,
+                                                  unsigned long long* stats) {
   extern __shared__ __align__(16) unsigned char net_raw[];
   NetSmem& S = *reinterpret_cast<NetSmem*>(net_raw);
   unsigned* xs = reinterpret_cast<unsigned*>(net_raw + sizeof(NetSmem)) + NET_XS_WORDS * (threadIdx.x >> 5);
-  if (learned) {
-    net_smem_fill(S, wb, wf, nm);
-    __syncthreads();
-  }
+  net_smem_fill(S, wb, wf, nm);
+  __syncthreads();
   const long long n = kb.n;
   const int lane = threadIdx.x & 31;
   unsigned s_fb = 0, s_f32 = 0;
+  bool any0 = false;
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
   for (long long base = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n;
        base += nwarps * 32) {
@@ -517,91 +485,33 @@ __global__ void __launch_bounds__(128) k_krp_seed(Par P, KrpBuf kb, int learned,
       s.D = w[KW_D * n + i];
     }
     s.gam = P.gam; s.eps_min = P.eps_atm; s.vmax2 = P.vmax2;
-    float lg = 0.0f;
-    if (learned) {
-      float x[MLP_FSTRIDE];
-      krp_features(s, x);
-      if (!act)
-        for (int f = 0; f < MLP_NIN; f++) x[f] = S.fmean[f];
-      lg = net_warp(S, xs, x);
-    }
+    float x[MLP_FSTRIDE];
+    krp_features(s, x);
+    if (!act)
+      for (int f = 0; f < MLP_NIN; f++) x[f] = S.fmean[f];
+    const float lg = net_warp(S, xs, x);
     if (!act) continue;
-    KSf sf;
-    sf.qh = (float)s.qh; sf.r2 = (float)s.r2; sf.b2 = (float)s.b2; sf.rb2 = (float)s.rb2; sf.rp2 = (float)s.rperp2;
-    sf.gam = (float)s.gam; sf.emin = fmaxf((float)s.eps_min, 1e-37f); sf.vmax2 = (float)s.vmax2;
-    // FP32 secant from the starting pair
-    float x0, x1;
-    if (learned) {
-      x0 = __expf(lg);
-      if (!(x0 > 1e-30f)) x0 = 1e-30f;
-      if (x0 > 1.0f) x0 = 1.0f;
-      x1 = fminf(x0 * __expf(delta), 1.0f);
-      if (x1 == x0) x1 = x0 * (1.0f - 1e-3f);
-    } else {
-      x0 = 0.0f;
-      x1 = f32_mu_plus(sf);
-    }
-    float f0 = f32_master(sf, x0), f1 = f32_master(sf, x1);
-    s_f32 += 2;
-    const int nsteps = learned ? 5 : 8;
-    for (int it = 0; it < nsteps; it++) {
-      const float den = f1 - f0;
-      if (den == 0.0f || !(f1 == f1)) break;
-      float x2 = x1 - f1 * (x1 - x0) / den;
-      if (!(x2 > 0.0f && x2 <= 1.0f)) x2 = 0.5f * (x1 + (f1 < 0.0f ? 1.0f : 0.0f));
-      const bool conv = fabsf(x2 - x1) <= 4.76837158e-7f * x1;   // 2^-21
-      x0 = x1; f0 = f1;
-      x1 = x2;
-      if (conv) break;
-      f1 = f32_master(sf, x2);
-      s_f32++;
-    }
-    double m32 = (double)x1;
-    if (!(m32 > 1e-300 && m32 <= 1.0)) m32 = 0.5;
-    double G = kev_g(s, m32);
-    int its = 1;
-    double a = 0.0, b = 1.0, Ga = f_zero(s, P), Gb = 0.0;
-    unsigned char st = 0;
-    if (G == 0.0) {
-      st = 1;
-      kb.w[KW_MU * n + i] = m32;
-    } else if (G < 0.0) {
-      a = m32; Ga = G;
-      double x = fmin(m32 * (1.0 + 4e-6), 1.0);
-      G = kev_g(s, x);
-      its++;
-      if (G >= 0.0) {
-        b = x; Gb = G;
-      } else {
-        a = x; Ga = G;
-        b = 1.0;
-        G = kev_g(s, b);
-        its++;
-        Gb = G;
-        if (!(Gb >= 0.0)) st = 2;
-        s_fb++;
-      }
-      if (st == 0 && Gb == 0.0) { st = 1; kb.w[KW_MU * n + i] = b; }
-    } else {
-      b = m32; Gb = G;
-      double x = m32 * (1.0 - 4e-6);
-      G = kev_g(s, x);
-      its++;
-      if (G < 0.0) {
-        a = x; Ga = G;
-      } else if (G == 0.0) {
-        st = 1;
-        kb.w[KW_MU * n + i] = x;
-      } else {
-        b = x; Gb = G;
-        s_fb++;
-      }
-    }
+    const KSf sf = ks_f32(s);
+    float x0 = __expf(lg);
+    if (!(x0 > 1e-30f)) x0 = 1e-30f;
+    if (x0 > 1.0f) x0 = 1.0f;
+    float x1 = fminf(x0 * __expf(delta), 1.0f);
+    if (x1 == x0) x1 = x0 * (1.0f - 1e-3f);
+    const float m32 = krp_secant32(sf, x0, x1, 5, s_f32);
+    const float isl = krp_islope32(sf, m32, s_f32);
+    double a = 0.0, b = 1.0, Ga = -1.0, Gb = 1.0, mu = 0.0;
+    int its = 0;
+    bool fb;
+    const int r = krp_polish(s, P, (double)m32, (double)isl, a, b, Ga, Gb, mu, its, fb);
+    s_fb += fb ? 1u : 0u;
     kb.w[KW_A * n + i] = a; kb.w[KW_B * n + i] = b;
     kb.w[KW_GA * n + i] = Ga; kb.w[KW_GB * n + i] = Gb;
+    kb.w[KW_MU * n + i] = mu;
     kb.it[i] = its;
-    kb.st[i] = st;
+    kb.st[i] = (unsigned char)(r == 0 ? 0 : (r == 1 ? 1 : 2));
+    any0 |= r == 0;
   }
+  warp_mark_solve(kb, any0);
   warp_flush(&stats[7], s_fb);
   warp_flush(&stats[8], s_f32);
 }
@@ -654,13 +564,13 @@ void launch_mlp_pack(const float* w, __nv_bfloat16* wb, cudaStream_t s) {
 void launch_mlp_stats(const float* feat, const float* target, long long n, double* acc, cudaStream_t s, int nsm) {
   k_mlp_stats<<<nsm * 4, 256, 0, s>>>(feat, target, n, acc);
 }
-void launch_krp_seed(const Par& P, const KrpBuf& kb, int learned, float delta, const __nv_bfloat16* wb,
-                     const float* w, const MlpNorm& nm, unsigned long long* stats, cudaStream_t s, int grid) {
-  k_krp_seed<<<grid, 128, learned ? net_smem_bytes(128) : 0, s>>>(P, kb, learned, delta, wb, w, nm, stats);
+void launch_krp_seed(const Par& P, const KrpBuf& kb, float delta, const __nv_bfloat16* wb, const float* w,
+                     const MlpNorm& nm, unsigned long long* stats, cudaStream_t s, int grid) {
+  k_krp_seed<<<grid, 128, net_smem_bytes(128), s>>>(P, kb, delta, wb, w, nm, stats);
 }
-int occ_seed_kernel(int learned) {
+int occ_seed_kernel() {
   int o = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_krp_seed, 128, learned ? net_smem_bytes(128) : 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_krp_seed, 128, net_smem_bytes(128));
   return o;
 }
 

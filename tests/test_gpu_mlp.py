@@ -128,9 +128,11 @@ def _modes(G, ctx, kw, cons0, tB, tg, modes=(0, 1, 2)):
         out[guess] = (pr.cpu().numpy(), fl.cpu().numpy(), it.cpu().numpy(), st)
         assert st["cells"] == n and st["iters"] == int(out[guess][2].sum())
         assert (st["fp32_evals"] == 0) == (guess == 0), st
-        # cells whose FP32 root missed the 4e-6 bracket: none without a
-        # search, a small fraction with one
-        assert st["guess_fallbacks"] == 0 if guess == 0 else st["guess_fallbacks"] <= 0.1 * n, (guess, st)
+        # cells whose FP64 polish was not taken as the root: none without a
+        # search; with one, the cells where the FP32 noise of f and of its
+        # slope left the two FP64 steps short of the contraction test (about
+        # a fifth of the stress cells, none of the star's)
+        assert st["guess_fallbacks"] == 0 if guess == 0 else st["guess_fallbacks"] <= 0.35 * n, (guess, st)
     return out
 
 
@@ -164,9 +166,10 @@ def test_learned_con2prim_against_the_method_without_the_network(G):
     network: the plain FP64 bracket (0) and the FP32 search from the plain
     bracket (2), on the stress cells (network trained on disjoint seeds).
     All three give the same root within the 1e-10 bar.  The network only
-    moves where the FP32 search starts; both searched modes hand the FP64
-    solve a bracket of relative width 4e-6 around an FP32 root, so the FP64
-    evaluations agree within 10% and are well below the plain solve's.  On
+    moves where the FP32 search starts; both searched modes polish an FP32
+    root with two FP64 evaluations (a bracket for the FP64 solve where the
+    polish is not taken), so the FP64 evaluations agree within 10% and are
+    well below the plain solve's.  On
     these cells (bracket half-width ~0.05 in log mu) the secant from the
     plain bracket converges as fast as from the guess: the FP32 evaluations
     are printed, not asserted lower (the binary states below show the gain)."""
