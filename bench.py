@@ -63,7 +63,7 @@ FP64_PEAK_TFLOPS = 2.0 * 2.0 * 152 * 2.070e9 / 1e12
 # captured on the 128^3 workload itself (one-pass metrics,
 # profiles/ncu_flux_star128_dram.md), scaled to a launch by its units.  The flux figures hold only at 128^3: the segment
 # lengths, and with them the x sweep's re-reads, depend on the size.
-TRAFFIC_PER_UNIT = {"flux_x": 352.3, "flux_y": 241.9, "flux_z": 241.5, "update": 733.6}
+TRAFFIC_PER_UNIT = {"flux_x": 360.0, "flux_y": 242.9, "flux_z": 242.5, "update": 733.6}
 TRAFFIC_SIZES = {"flux_x": (128,), "flux_y": (128,), "flux_z": (128,), "update": (128,)}
 # Kernels changed since their capture: their traffic is reported as null, with
 # the last capture beside it, until they are captured again.
@@ -73,7 +73,7 @@ TRAFFIC_STALE = set()
 # 104^3 case, which has the 128^3 segment lengths; profiles/ncu_flux_star104_fp64.md),
 # for the issue-based fraction: executed FP64 instructions per second over
 # the pipe's 2 thread instructions per clock per SM at the sampled SM clock.
-FP64_INST_PER_UNIT = {"flux_x": 677.4, "flux_y": 650.2, "flux_z": 650.2}
+FP64_INST_PER_UNIT = {"flux_x": 597.4, "flux_y": 597.4, "flux_z": 597.4}
 FP64_ISSUE_PER_CLK_SM = 2.0
 
 # Algorithmic HBM bytes per zone and RK stage of one fused pass: read U (5),
@@ -750,6 +750,10 @@ def run_ours(args):
                                "MEASURED_PEAKS.json",
                 "achieved_source": "algorithmic FP64 operations of the op-counting oracle (add, mul, div, sqrt "
                                    "each 1) x faces per launch / mean launch time from CUDA events",
+                "frac_note": "frac can pass 1: the sweep executes ~900 FP64 flops (597 instructions, FMAs "
+                             "counted twice) per face for the oracle's 1438 operations (values shared "
+                             "along the sweep and between the two sides, FMAs); frac_issue is the FP64 "
+                             "pipe's issue fraction",
                 "frac_issue_source": "ncu FP64 thread instructions per face x faces / launch time, over 2 per "
                                      "clock per SM x SMs x the sampled SM clock",
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per unit (flux: the 128^3 "

@@ -261,7 +261,7 @@ int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
     need += al256(sizeof(double) * 3 * b.ncell);
     need += al256((size_t)b.ncell);
     need += al256(sizeof(double) * 8 * (size_t)b.ncell);
-    for (int d = 0; d < 3; d++) need += al256(sizeof(double) * FMC_N * (size_t)fmc_count(s.n, d));
+    for (int d = 0; d < 3; d++) need += al256(sizeof(double) * FMC_N * (size_t)fmc_count(b, d));
     need += al256(sizeof(double) * DMC_N * (size_t)s.n[0] * s.n[1] * s.n[2]);
     if (c->P.guess == 3) need += al256(sizeof(double) * (size_t)b.ncell);
     const long long n0 = s.n[0], n1 = s.n[1], n2 = s.n[2];
@@ -316,7 +316,7 @@ int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
     p += al256(sizeof(double) * 8 * (size_t)b.ncell);
     for (int d = 0; d < 3; d++) {
       b.fmc[d] = (double*)p;
-      p += al256(sizeof(double) * FMC_N * (size_t)fmc_count(b.n, d));
+      p += al256(sizeof(double) * FMC_N * (size_t)fmc_count(b, d));
     }
     b.dmc = (double*)p;
     p += al256(sizeof(double) * DMC_N * (size_t)b.n[0] * b.n[1] * b.n[2]);

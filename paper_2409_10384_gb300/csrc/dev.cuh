@@ -75,10 +75,6 @@ constexpr int DMC_N = 30;
 // Face metric cache: alpha, beta^1..3, gamma_ij (6), sqrt(gamma),
 // 1/sqrt(gamma) and gamma^{dd} of a face of direction d.
 constexpr int FMC_N = 13;
-// faces of direction d a stage sweeps: n_d + 1 along d, n + 2 across
-__host__ __device__ inline long long fmc_count(const int* n, int d) {
-  return (long long)(n[0] + (d == 0 ? 1 : 2)) * (n[1] + (d == 1 ? 1 : 2)) * (n[2] + (d == 2 ? 1 : 2));
-}
 // Face index (k,j,i) of item `loc` of direction d: along d the interior faces,
 // transversally one extra layer each side (the CT stencil needs them).
 template <int d>
@@ -89,11 +85,40 @@ __host__ __device__ __forceinline__ void face_coords(const DevBlock& b, long lon
   j = a1 + b.ng - (d == 1 ? 0 : 1);
   k = a2 + b.ng - (d == 2 ? 0 : 1);
 }
-// index of face (k,j,i) of direction d in its cache (the order of the
-// stage's face work items, face_coords: x fastest)
+// The face metric cache of direction d (DevBlock.fmc[d], [FMC_N][fmc_count]).
+// y and z: in face_coords order (x fastest), as the lanes of a y or z sweep
+// take neighbouring lines.  x: the lanes of an x sweep take neighbouring
+// segments of a line, so the face at position q of the segment of sweep item
+// `item` (seg_coords<0>) sits at q * nitems + item: every step of the sweep
+// reads consecutive slots.  Segments hold fmc_lx faces but the remainder of
+// each line fewer; its unused slots stay unwritten and unread.
+__host__ __device__ inline int fmc_lx(const DevBlock& b) {
+  const int ns = b.nseg[0], nd = b.n[0] + 1;
+  return (nd + ns - 1) / ns;
+}
+__host__ __device__ inline long long fmc_xitems(const DevBlock& b) {
+  return (long long)b.nseg[0] * (b.n[1] + 2) * (b.n[2] + 2);
+}
+__host__ __device__ inline long long fmc_count(const DevBlock& b, int d) {
+  if (d == 0) return fmc_lx(b) * fmc_xitems(b);
+  return (long long)(b.n[0] + 2) * (b.n[1] + (d == 1 ? 1 : 2)) * (b.n[2] + (d == 2 ? 1 : 2));
+}
+// index step between consecutive faces of a sweep of direction d
+__host__ __device__ inline long long fmc_step(const DevBlock& b, int d) {
+  return d == 0 ? fmc_xitems(b) : (d == 1 ? (long long)(b.n[0] + 2) : (long long)(b.n[0] + 2) * (b.n[1] + 2));
+}
+// index of face (k,j,i) of direction d in its cache
 __host__ __device__ inline long long fmc_index(const DevBlock& b, int d, int k, int j, int i) {
-  const int L0 = b.n[0] + (d == 0 ? 1 : 2), L1 = b.n[1] + (d == 1 ? 1 : 2);
-  const int a0 = i - b.ng + (d == 0 ? 0 : 1), a1 = j - b.ng + (d == 1 ? 0 : 1), a2 = k - b.ng + (d == 2 ? 0 : 1);
+  if (d == 0) {
+    const int f = i - b.ng, lx = fmc_lx(b), full = b.nseg[0] - 1;
+    const long long lines = (long long)(b.n[1] + 2) * (b.n[2] + 2);
+    const long long r = (long long)(k - b.ng + 1) * (b.n[1] + 2) + (j - b.ng + 1);
+    const int s = f / lx;   // <= full: the remainder holds fewer than lx faces
+    const long long item = s < full ? r * full + s : full * lines + r;
+    return (long long)(f - s * lx) * fmc_xitems(b) + item;
+  }
+  const int L0 = b.n[0] + 2, L1 = b.n[1] + (d == 1 ? 1 : 2);
+  const int a0 = i - b.ng + 1, a1 = j - b.ng + (d == 1 ? 0 : 1), a2 = k - b.ng + (d == 2 ? 0 : 1);
   return ((long long)a2 * L1 + a1) * L0 + a0;
 }
 // Relative half-width of the bracket around a previous root (c2p_guess 3).
@@ -110,9 +135,12 @@ enum WorkKind { W_C2P = 0, W_FX, W_FY, W_FZ, W_CELL, W_EDGE, W_FACE, W_INIT, W_S
 // (FLUX_SEG_X along x) unless the block list is too small to give every SM
 // two waves of sweeps at that length; then it halves (down to 1) until it
 // does (flux_seg_len).  The x sweep's lanes read neighbouring segments of one
-// line; at 16 faces the lines they hold exceed L2 and it re-reads them.
+// line.  Each segment reconstructs one cell more than it has faces; on the
+// 128^3 star x segments of 16 faces ran the x sweep 2.5% faster than 8 or
+// 12, and y / z segments of 24 ran 2.6% slower than 16 (fewer waves, a
+// longer idle tail).
 constexpr int FLUX_SEG = 16;
-constexpr int FLUX_SEG_X = 8;
+constexpr int FLUX_SEG_X = 16;
 // segments per line for an interior of n cells (n + 1 faces)
 __host__ __device__ inline int flux_nseg(int n, int L) { return (n + L) / L; }
 __host__ __device__ inline long long flux_seg_items(const int* n, int d, int L) {
@@ -1224,10 +1252,18 @@ struct FaceMetric {
   Metric m;
   double alpha, beta[3];
 };
-// Conserved state and flux of one side, plus the pieces of its fast
-// magnetosonic speeds lambda = alpha (vq -/+ sq) / den - beta^d.
+// Conserved state and flux of one side of a face of direction d, in the
+// linear form the Riemann combination takes (Eq. 8; avd = alpha v^d - beta^d,
+// avh^t = alpha v^t - beta^t, wl_i = W v_i, Bl_i = B_i):
+//   D~:     U = UD,               F = UD avd
+//   S~_i:   U = a wl_i + b Bl_i,  F = c wl_i + e Bl_i (+ asP along i = d)
+//   tau~:   U = Ut,               F = Ut avd + t
+//   B~^t:   U = B~^t,             F = B~^t avd - B~^d avh^t  (t = t1, t2)
+// plus the pieces of the fast magnetosonic speeds lambda = alpha (vq -/+ sq)
+// / den - beta^d.  The combination then weighs these per-side coefficients
+// instead of 14 assembled components.
 struct Side {
-  double U[7], F[7], vq, sq, den;
+  double wl[3], Bl[3], a, b, c, e, UD, Ut, t, asP, avd, avh1, avh2, Bt1, Bt2, vq, sq, den;
 };
 // st = rho, w^1..3 (= W v^i), P, B~^{t1}, B~^{t2}; Bn = B~^d.
 //
@@ -1277,24 +1313,30 @@ __device__ __forceinline__ void face_side(const Par& P, const double* st, double
   const double Ptot = fma(0.5, b2, p);
   const double sdeBW = sd * (eB * iW);
   const double sdBv = sd * Bv;
-  o.U[0] = sd * D;
-#pragma unroll
-  for (int a = 0; a < 3; a++) o.U[1 + a] = fma(sdeBW, wl[a], -sdBv * Bl[a]);
-  o.U[4] = sd * ((eB - D) - Ptot);
-  o.U[5] = Bt[t1];
-  o.U[6] = Bt[t2];
   const double avd = avh[d];
   const double aBn = alpha * Bn;
   const double aBi = aBn * iW2;
-  const double sdP = sd * Ptot;
-  o.F[0] = o.U[0] * avd;
+  // S~_i = sd (eB/W w_i - (B.v) B_i); its flux S~_i avd - alpha B~^d b_i/W
+  // with b_i/W = (Bw w_i + B_i)/W^2, plus alpha sd P_tot along d
 #pragma unroll
-  for (int a = 0; a < 3; a++) o.F[1 + a] = fma(o.U[1 + a], avd, -aBi * fma(Bw, wl[a], Bl[a]));  // b_i/W = (Bw w_i + B_i)/W^2
-  o.F[1 + d] = fma(alpha, sdP, o.F[1 + d]);
+  for (int a = 0; a < 3; a++) {
+    o.wl[a] = wl[a];
+    o.Bl[a] = Bl[a];
+  }
+  o.a = sdeBW;
+  o.b = -sdBv;
+  o.c = fma(sdeBW, avd, -aBi * Bw);
+  o.e = -fma(sdBv, avd, aBi);
+  o.asP = alpha * (sd * Ptot);
+  o.UD = sd * D;
+  o.Ut = sd * ((eB - D) - Ptot);
   const double vd = w[d] * iW;
-  o.F[4] = fma(o.U[4], avd, fma(sdP, alpha * vd, -aBn * Bv));
-  o.F[5] = fma(Bt[t1], avd, -Bn * avh[t1]);
-  o.F[6] = fma(Bt[t2], avd, -Bn * avh[t2]);
+  o.t = fma(o.asP, vd, -aBn * Bv);
+  o.avd = avd;
+  o.avh1 = avh[t1];
+  o.avh2 = avh[t2];
+  o.Bt1 = Bt[t1];
+  o.Bt2 = Bt[t2];
   const double N = gp + b2;
   const double Q = rhoh - gp;
   const double den = fma(iW2 - 1.0, N, rhoh + b2);   // Dn - v^2 N, v^2 = 1 - 1/W^2
@@ -1307,36 +1349,46 @@ __device__ __forceinline__ void face_side(const Par& P, const double* st, double
   o.den = den;
 }
 
-// LLF (rs 0) or HLLE (rs 1) flux from the two sides of a face of direction d.
+// LLF (rs 0) or HLLE (rs 1) flux from the two sides of a face of direction d
+// (Bn = B~^d), both as F = kFL F_L + kFR F_R + kdU (U_R - U_L): HLLE
+// (lR, -lL, lL lR)/(lR - lL), or (1/2, 1/2, 0) where lR = lL; LLF (1/2, 1/2,
+// -a/2).  The per-side linear forms (Side) fold kFL, kFR and kdU into one
+// coefficient per side vector.
 template <int d>
-__device__ __forceinline__ void riemann(int rs, const FaceMetric& fm, const Side& L, const Side& R, double* F) {
+__device__ __forceinline__ void riemann(int rs, const FaceMetric& fm, double Bn, const Side& L, const Side& R,
+                                        double* F) {
   const double r = fm.alpha * rcp_nr(L.den * R.den);   // den = rho h + b^2 - v^2 N > 0
   const double aL = r * R.den, aR = r * L.den;
   const double bd = fm.beta[d];
   const double lmL = fma(aL, L.vq - L.sq, -bd), lpL = fma(aL, L.vq + L.sq, -bd);
   const double lmR = fma(aR, R.vq - R.sq, -bd), lpR = fma(aR, R.vq + R.sq, -bd);
+  double kFL = 0.5, kFR = 0.5, kdU = 0.0;
   if (rs == 1) {
     // min / max on the integer pipe: the speeds are finite for physical
     // states (a NaN state is caught by the con2prim of the next stage)
     const double lL = imin(imin(lmL, lmR), 0.0);
     const double lR = imax(imax(lpL, lpR), 0.0);
     const double dl = lR - lL;   // >= 0
-    if (eq0(dl)) {
-#pragma unroll
-      for (int c = 0; c < 7; c++) F[c] = 0.5 * (L.F[c] + R.F[c]);
-    } else {
-      // (lR F_L - lL F_R + lL lR (U_R - U_L)) / (lR - lL), with the division's
-      // reciprocal folded into the three coefficients once per face
+    if (!eq0(dl)) {
       const double inv = gt_nn(dl, 1e-280) ? rcp_nr(dl) : 1.0 / dl;   // dl > 0 here
-      const double cR = lR * inv, cL = -lL * inv, cLR = (lL * lR) * inv;
-#pragma unroll
-      for (int c = 0; c < 7; c++) F[c] = fma(cR, L.F[c], fma(cL, R.F[c], cLR * (R.U[c] - L.U[c])));
+      kFL = lR * inv;
+      kFR = -lL * inv;
+      kdU = (lL * lR) * inv;
     }
   } else {
-    const double a = fmax(fmax(fabs(lmL), fabs(lpL)), fmax(fabs(lmR), fabs(lpR)));
-#pragma unroll
-    for (int c = 0; c < 7; c++) F[c] = 0.5 * (L.F[c] + R.F[c]) - 0.5 * a * (R.U[c] - L.U[c]);
+    kdU = -0.5 * fmax(fmax(fabs(lmL), fabs(lpL)), fmax(fabs(lmR), fabs(lpR)));
   }
+  // kFL F_L - kdU U_L and kFR F_R + kdU U_R per side vector
+  const double gL = fma(kFL, L.avd, -kdU), gR = fma(kFR, R.avd, kdU);
+  const double pL = fma(kFL, L.c, -kdU * L.a), qL = fma(kFL, L.e, -kdU * L.b);
+  const double pR = fma(kFR, R.c, kdU * R.a), qR = fma(kFR, R.e, kdU * R.b);
+  F[0] = fma(L.UD, gL, R.UD * gR);
+#pragma unroll
+  for (int i = 0; i < 3; i++) F[1 + i] = fma(L.wl[i], pL, fma(L.Bl[i], qL, fma(R.wl[i], pR, R.Bl[i] * qR)));
+  F[1 + d] += fma(kFL, L.asP, kFR * R.asP);
+  F[4] = fma(L.Ut, gL, fma(R.Ut, gR, fma(kFL, L.t, kFR * R.t)));
+  F[5] = fma(L.Bt1, gL, fma(R.Bt1, gR, -Bn * fma(kFL, L.avh1, kFR * R.avh1)));
+  F[6] = fma(L.Bt2, gL, fma(R.Bt2, gR, -Bn * fma(kFL, L.avh2, kFR * R.avh2)));
 }
 
 // Interpolates the ADM variables to the face between the cells at a and a+st
@@ -1406,7 +1458,7 @@ __device__ __forceinline__ void face_flux_states(const Par& P, double* L, double
   Side sl, sr;
   face_side<d, E>(P, L, Bn, fm, sl, cl);
   face_side<d, E>(P, R, Bn, fm, sr, cr);
-  riemann<d>(P.rsolver, fm, sl, sr, F);
+  riemann<d>(P.rsolver, fm, Bn, sl, sr, F);
 }
 
 // SSP-RK weights (g0, g1, beta) of a stage: U <- g0 U^n + g1 U + beta dt L(U)

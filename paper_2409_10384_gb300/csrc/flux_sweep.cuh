@@ -31,8 +31,8 @@ __global__ void __launch_bounds__(256) k_flux(Work w, Par P) {
     long long c = cidx(b, k, j, i) - st;   // cell m below the first face
     long long f = fidx(b, d, k, j, i);
     long long fq = C ? fmc_index(b, d, k, j, i) : 0;   // face metric cache index
-    const long long nq = C ? fmc_count(b.n, d) : 0;
-    const long long qst = d == 0 ? 1 : (d == 1 ? (long long)(b.n[0] + 2) : (long long)(b.n[0] + 2) * (b.n[1] + 2));
+    const long long nq = C ? fmc_count(b, d) : 0;
+    const long long qst = C ? fmc_step(b, d) : 0;
     RecVar rv[7];
     double Ls[7];
 #pragma unroll

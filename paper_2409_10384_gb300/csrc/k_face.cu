@@ -134,6 +134,10 @@ __global__ void __launch_bounds__(128) k_fofc_fix(Work w, Par P, unsigned long l
 // of the metric at the interior cells (DevBlock.dmc, Eq. 9).  The context's RK step
 // runs it once, before its first stage; the stage-by-stage entry points run it
 // in every mhd_c2p.
+// One thread per face, x fastest (the four-point reads of the ADM variables
+// coalesce).  y and z store at the item index itself; x at its segment-major
+// slot, where neighbouring segments' faces (lanes of the same or the next
+// warp) complete each sector.
 template <int d>
 __device__ __forceinline__ void face_metric_items(const Work& w) {
   const long long* pre = w.pre + (long long)(W_FX + d) * (w.nblocks + 1);
@@ -147,7 +151,7 @@ __device__ __forceinline__ void face_metric_items(const Work& w) {
     const long long st = d == 0 ? 1 : (d == 1 ? (long long)b.N[0] : (long long)b.N[0] * b.N[1]);
     FaceMetric fm;
     face_metric(b.adm, b.ncell, cidx(b, k, j, i) - st, st, fm);
-    fmc_store<d>(b.fmc[d], fmc_count(b.n, d), loc, fm);   // loc = fmc_index(b, d, k, j, i)
+    fmc_store<d>(b.fmc[d], fmc_count(b, d), d == 0 ? fmc_index(b, 0, k, j, i) : loc, fm);
   }
 }
 __global__ void __launch_bounds__(256) k_metric_cache(Work w) {

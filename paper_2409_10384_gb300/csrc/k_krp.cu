@@ -447,10 +447,15 @@ __global__ void __launch_bounds__(128) k_krp_finish_cells(Par P, KrpBuf kb, doub
 size_t krp_bytes(long long n) {
   return (size_t)n * (sizeof(double) * KW_N + sizeof(int) + 2) + 1024;
 }
+// The counters sit at the start of the buffer, so every view of it (the
+// stage input's and the FOFC estimate's, of different n) shares them; their
+// uses follow one another in stream order (prep, solve, finish).
 KrpBuf krp_view(void* base, long long n) {
   KrpBuf kb;
   char* p = (char*)base;
   kb.n = n;
+  kb.ctr = (unsigned long long*)p;
+  p += 256;
   kb.w = (double*)p;
   p += sizeof(double) * KW_N * n;
   kb.it = (int*)p;
@@ -458,9 +463,6 @@ KrpBuf krp_view(void* base, long long n) {
   kb.st = (unsigned char*)p;
   p += n;
   kb.fl = (unsigned char*)p;
-  p += n;
-  p = (char*)(((size_t)p + 255) & ~(size_t)255);
-  kb.ctr = (unsigned long long*)p;
   return kb;
 }
 

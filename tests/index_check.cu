@@ -8,9 +8,10 @@
 //    faces.  The cells a sweep reads (the five-cell stencils of the cells
 //    next to its faces, as k_flux does) lie inside the ghosted block, and its
 //    faces (fidx) inside the face array (nface).
-//  - The face metric cache: fmc_index inverts face_coords (the metric
-//    kernel's store order), and a sweep's per-face index step lands on
-//    fmc_index of every face it visits, inside fmc_count.
+//  - The face metric cache: the metric kernel's stores (fmc_index of each
+//    face_coords item) are distinct slots inside fmc_count (for y and z the
+//    item index itself), and a sweep's per-face index step (fmc_step) lands
+//    on fmc_index of every face it visits.
 //  - find_block: on prefix sums with empty blocks, item it belongs to the
 //    block b returned, p[b] <= it < p[b + 1].
 //  - The integer-pipe compares (lt0, gt0, eq0, gt_nn, below_thr,
@@ -29,20 +30,25 @@
 
 using grmhd::DevBlock;
 
-// The metric cache kernel stores the face of work item `loc` (face_coords) at
-// index loc: fmc_index must invert face_coords over all fmc_count items.
+// The metric cache kernel stores the face of work item `loc` (face_coords)
+// at fmc_index: for y and z that is loc itself; for x (segments of length L,
+// segment-major slots) every face must land on its own slot inside
+// fmc_count.
 template <int d>
-static bool check_fmc(const int n[3]) {
+static bool check_fmc(const int n[3], int L) {
   DevBlock b{};
   for (int a = 0; a < 3; a++) b.n[a] = n[a];
   b.ng = 4;
-  const long long cnt = grmhd::fmc_count(n, d);
-  for (long long loc = 0; loc < cnt; loc++) {
+  b.nseg[0] = grmhd::flux_nseg(n[0], L);
+  const long long cnt = grmhd::fmc_count(b, d);
+  const long long faces = (long long)(n[0] + (d == 0 ? 1 : 2)) * (n[1] + (d == 1 ? 1 : 2)) * (n[2] + (d == 2 ? 1 : 2));
+  std::vector<int> held((size_t)cnt, 0);
+  for (long long loc = 0; loc < faces; loc++) {
     int k, j, i;
     grmhd::face_coords<d>(b, loc, k, j, i);
-    if (grmhd::fmc_index(b, d, k, j, i) != loc) {
-      std::printf("fmc d=%d n=%d,%d,%d: item %lld -> %lld\n", d, n[0], n[1], n[2], loc,
-                  grmhd::fmc_index(b, d, k, j, i));
+    const long long q = grmhd::fmc_index(b, d, k, j, i);
+    if (q < 0 || q >= cnt || held[(size_t)q]++ || (d != 0 && q != loc)) {
+      std::printf("fmc d=%d n=%d,%d,%d L=%d: item %lld -> slot %lld of %lld\n", d, n[0], n[1], n[2], L, loc, q, cnt);
       return false;
     }
   }
@@ -94,8 +100,8 @@ static bool check(const int n[3], int L) {
     // the face metric cache: the sweep steps its index by qst per face; every
     // face's index is fmc_index of that face and lies inside the cache
     {
-      const long long q0 = grmhd::fmc_index(b, d, k, j, i), nq = grmhd::fmc_count(b.n, d);
-      const long long qst = d == 0 ? 1 : (d == 1 ? (long long)(n[0] + 2) : (long long)(n[0] + 2) * (n[1] + 2));
+      const long long q0 = grmhd::fmc_index(b, d, k, j, i), nq = grmhd::fmc_count(b, d);
+      const long long qst = grmhd::fmc_step(b, d);
       for (int q = 0; q < nf; q++) {
         const int kk = k + (d == 2 ? q : 0), jj = j + (d == 1 ? q : 0), ii = i + (d == 0 ? q : 0);
         const long long want = grmhd::fmc_index(b, d, kk, jj, ii);
@@ -221,7 +227,7 @@ static bool check_compares() {
 
 // Segment lengths that flux_seg_len picks on 152 SMs (x, y, z).
 static bool check_seg_len() {
-  struct Case { int n; int L[3]; } cases[] = {{128, {8, 16, 16}}, {104, {8, 16, 16}}, {96, {8, 8, 8}},
+  struct Case { int n; int L[3]; } cases[] = {{128, {16, 16, 16}}, {104, {16, 16, 16}}, {96, {8, 8, 8}},
                                               {64, {2, 2, 2}}, {32, {1, 1, 1}}};
   for (const Case& c : cases) {
     const int n[1][3] = {{c.n, c.n, c.n}};
@@ -246,8 +252,9 @@ int main() {
   const int Ls[] = {1, 2, 3, 4, 8, 16};
   int cases = 0;
   for (const auto& n : shapes) {
-    if (!check_fmc<0>(n) || !check_fmc<1>(n) || !check_fmc<2>(n)) return 1;
+    if (!check_fmc<1>(n, 16) || !check_fmc<2>(n, 16)) return 1;
     for (int L : Ls) {
+      if (!check_fmc<0>(n, L)) return 1;
       if (!check<0>(n, L) || !check<1>(n, L) || !check<2>(n, L)) return 1;
       cases += 3;
     }
