@@ -197,6 +197,16 @@ int mhd_step(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, double dt, int 
  * rk_order stages per block list, dt, parameters and stream, replayed on
  * later calls; stream must not be the legacy default stream). */
 int mhd_graph_step(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, double dt, void* stream);
+/* mhd_step with graph = 0 whose stages wait for the CUDA event state_ready
+ * (a cudaEvent_t, recorded by the caller after its copies of the blocks'
+ * state, cons and face B~; NULL: no wait).  The step first enqueues its
+ * metric kernel, which reads only the ADM arrays, and then the wait: a caller
+ * that copies the state in on another stream overlaps those copies with the
+ * metric computation.  Not in the paper's hot path; its introduction (Sec. 1)
+ * motivates overlapping transfers with computation.  Same results as
+ * mhd_step.  Errors as mhd_step (MHD_ECUDA if the wait cannot be enqueued). */
+int mhd_step_overlap(mhd_ctx* ctx, const mhd_block* blocks, int nblocks, double dt, void* stream,
+                     void* state_ready);
 
 /* Autotuner for a block list: times each tunable kernel (the two con2prim
  * phases, the three flux directions, the two FOFC-estimate phases, the EMF

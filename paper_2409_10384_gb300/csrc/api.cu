@@ -24,6 +24,7 @@ struct mhd_ctx {
   // side streams and events of the forked flux sweeps (y, z)
   cudaStream_t side[2] = {nullptr, nullptr};
   cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+  cudaEvent_t state_ready = nullptr;   // mhd_step_overlap: the stages wait for it after the metric kernel
   // three-phase con2prim scratch: of the block list, and of independent cells
   char* krp = nullptr;
   long long krp_n = 0;
@@ -467,6 +468,7 @@ int enqueue_c2p(mhd_ctx* c, cudaStream_t s, const Work& w, const long long* item
     const long long tot = items[W_C2P] + items[W_FX] + items[W_FY] + items[W_FZ] + items[W_CELL];
     const long long g = std::max(1LL, std::min((tot + 255) / 256, (long long)c->nsm * std::max(c->occ_metric, 1)));
     timed(c, MHD_K_METRIC, s, [&] { launch_metric_cache(w, s, (int)g); });
+    if (c->state_ready && cudaStreamWaitEvent(s, c->state_ready, 0) != cudaSuccess) return MHD_ECUDA;
   }
   KrpBuf kb = krp_view(c->krp, items[W_C2P]);
   const mhd_ctx::Cfg& cp = c->cfg[T_C2P_PREP];
@@ -1240,6 +1242,16 @@ int mhd_check_rcp(const double* x, long n, double* rel_out, void* stream) {
   if (cudaPeekAtLastError() != cudaSuccess) return MHD_ECUDA;
   launch_check_rcp(x, n, rel_out, (cudaStream_t)stream, nsm);
   return cuda_ok(cudaPeekAtLastError());
+}
+
+int mhd_step_overlap(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, void* stream, void* state_ready) {
+  if (!c || !(dt > 0.0)) return MHD_EINVAL;
+  int r = prepare(c, blocks, nb);
+  if (r) return r;
+  c->state_ready = (cudaEvent_t)state_ready;
+  r = enqueue_step(c, dt, (cudaStream_t)stream);
+  c->state_ready = nullptr;
+  return r;
 }
 
 int mhd_graph_step(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, void* stream) {

@@ -71,6 +71,7 @@ _SIGS = {
     "mhd_rk_update": (_I, [_VP, C.POINTER(mhd_block), _I, _D, _I, _VP]),
     "mhd_step": (_I, [_VP, C.POINTER(mhd_block), _I, _D, _I, _VP]),
     "mhd_graph_step": (_I, [_VP, C.POINTER(mhd_block), _I, _D, _VP]),
+    "mhd_step_overlap": (_I, [_VP, C.POINTER(mhd_block), _I, _D, _VP, _VP]),
     "mhd_read_stats": (_I, [_VP, C.POINTER(mhd_stats), _VP]),
     "mhd_reset_stats": (_I, [_VP, _VP]),
     "mhd_scratch_copy": (_I, [_VP, _I, _I, _VP, _L, C.POINTER(_L), _VP]),
@@ -331,6 +332,14 @@ class Context:
         arr, nb = self._blocks(blocks)
         check(self.L.mhd_graph_step(self.h, arr, nb, float(dt), _sptr(stream)), "mhd_graph_step")
 
+    def step_overlap(self, blocks, dt, stream=None, state_ready=None):
+        """mhd_step_overlap: an ungraphed step whose stages wait for the torch
+        CUDA event state_ready (recorded after the state's copies) while its
+        metric kernel runs."""
+        arr, nb = self._blocks(blocks)
+        ev = None if state_ready is None else C.c_void_p(int(state_ready.cuda_event))
+        check(self.L.mhd_step_overlap(self.h, arr, nb, float(dt), _sptr(stream), ev), "mhd_step_overlap")
+
     def step_host(self, blk: DeviceBlock, host: dict, dt, stream=None, graph=False):
         """One RK step of a block whose state lives in (pinned) host memory:
         host["cons"], host["bf"][0..2] and host["adm"] are copied in, the step
@@ -347,6 +356,11 @@ class Context:
             host["cons"].copy_(blk.cons, non_blocking=True)
             for d in range(3):
                 host["bf"][d].copy_(blk.bf[d], non_blocking=True)
+
+    def host_stepper(self, blk: "DeviceBlock", host: dict, stream=None) -> "HostStepper":
+        """A stepper for a block whose state and metric live in pinned host
+        memory, with its host copies pipelined (see HostStepper)."""
+        return HostStepper(self, blk, host, stream)
 
     def autotune(self, blocks, dt, stream=None) -> dict:
         """Tune the launch configuration of this block list; {kernel: (CTA size, waves)}."""
@@ -489,3 +503,100 @@ class Context:
         n = (C.c_longlong * MHD_NKERNEL)()
         check(self.L.mhd_profile_read(self.h, ms, n), "mhd_profile_read")
         return {self.L.mhd_kernel_name(k).decode(): (ms[k], n[k]) for k in range(MHD_NKERNEL)}
+
+
+class HostStepper:
+    """RK steps of a block whose state (host["cons"], host["bf"][0..2]) and
+    metric (host["adm"]) live in pinned host memory.  Every step copies its
+    metric and its state in from the host and its state out to the host, as
+    Context.step_host does, with the copies pipelined:
+
+    - the metric of step k+1 travels into a device staging array on a side
+      stream while step k runs; step k+1 moves it into the block with one
+      device-to-device copy;
+    - after step k the state goes out array by array (five conserved
+      variables, three face fields) on a second stream, and each array comes
+      back in for step k+1 on a third as soon as it has reached the host, so
+      the two directions of the link overlap; step k+1 starts its metric
+      kernel meanwhile and its stages wait for the state (mhd_step_overlap).
+
+    The host state is read back as soon as it is written, so changes a caller
+    makes to it between steps are not seen (use Context.step_host for that).
+
+    step(dt, adm_next=None): one RK step; adm_next (pinned host, the shape of
+    host["adm"]) is the metric of the following step, host["adm"] when None.
+    join(): makes the stepper's stream wait until the last step's state has
+    reached the host (for timing on that stream, or before reading the host
+    state).  finish(): waits for every copy in flight."""
+
+    def __init__(self, ctx: Context, blk: DeviceBlock, host: dict, stream=None):
+        import torch
+        self.ctx, self.blk, self.host = ctx, blk, host
+        dev = blk.cons.device
+        self.s = stream or torch.cuda.current_stream()
+        self.sp = torch.cuda.Stream(device=dev)   # the metric coming in
+        self.so = torch.cuda.Stream(device=dev)   # the state going out
+        self.si = torch.cuda.Stream(device=dev)   # the state coming back in
+        self.stage = torch.empty_like(blk.adm)
+        self.ready = None      # event: the staging array holds the next step's metric
+        self.free = None       # event: the step has copied the staging array out
+        self.state_in = None   # event: the state of the next step is on the device
+        self.out = None        # event: the last step's state is on the host
+        self.pairs = [(blk.cons[v], host["cons"][v]) for v in range(5)] + \
+                     [(blk.bf[d], host["bf"][d]) for d in range(3)]
+
+    def _prefetch(self, adm_host):
+        # after the staging array is free and after the current step's state
+        # is in (the state's copies are on the critical path; the metric has
+        # the whole step to arrive)
+        import torch
+        with torch.cuda.stream(self.sp):
+            if self.free is not None:
+                self.sp.wait_event(self.free)
+            if self.state_in is not None:
+                self.sp.wait_event(self.state_in)
+            self.stage.copy_(adm_host, non_blocking=True)
+            self.ready = torch.cuda.Event()
+            self.ready.record(self.sp)
+
+    def step(self, dt, adm_next=None):
+        import torch
+        if self.ready is None:
+            self._prefetch(self.host["adm"])
+        s, blk = self.s, self.blk
+        with torch.cuda.stream(s):
+            if self.state_in is None:   # the first step copies its state in here
+                for dev, hst in self.pairs:
+                    dev.copy_(hst, non_blocking=True)
+            s.wait_event(self.ready)
+            blk.adm.copy_(self.stage, non_blocking=True)
+            self.free = torch.cuda.Event()
+            self.free.record(s)
+        self._prefetch(self.host["adm"] if adm_next is None else adm_next)
+        self.ctx.step_overlap([blk], dt, stream=s, state_ready=self.state_in)
+        done = torch.cuda.Event()
+        done.record(s)
+        evs = []
+        with torch.cuda.stream(self.so):
+            self.so.wait_event(done)
+            for dev, hst in self.pairs:
+                hst.copy_(dev, non_blocking=True)
+                e = torch.cuda.Event()
+                e.record(self.so)
+                evs.append(e)
+        self.out = evs[-1]
+        with torch.cuda.stream(self.si):
+            for (dev, hst), e in zip(self.pairs, evs):
+                self.si.wait_event(e)
+                dev.copy_(hst, non_blocking=True)
+            self.state_in = torch.cuda.Event()
+            self.state_in.record(self.si)
+
+    def join(self):
+        if self.out is not None:
+            self.s.wait_event(self.out)
+
+    def finish(self):
+        self.sp.synchronize()
+        self.so.synchronize()
+        self.si.synchronize()

@@ -187,3 +187,50 @@ def test_fast_reciprocal_within_two_ulp_of_the_division(G):
     d = G.check_rcp(torch.from_numpy(np.ascontiguousarray(x)).cuda()).cpu().numpy()
     assert np.all(np.isfinite(d))
     assert d.max() <= 2.0 ** -51, float(d.max())
+
+
+def test_host_stepper_equals_step_host(G):
+    """The pipelined host stepper (next metric copied in on a side stream while
+    the step runs, the state out and back in array by array while the next
+    step's metric kernel runs) gives the same bits as step_host over three RK3
+    steps, with the metric changing between steps (each step's own metric
+    arrives)."""
+    import torch
+    p = O.params(gamma=2.0, rho_atm=1e-12, T_atm=1e-10, f_thr=0.1, recon=2, rsolver=1, rk_order=3, fofc=1)
+    inp, ob = _star(G, p)
+    dt = 0.25 * inp.dx[0]
+
+    def host_of(db):
+        h = {"cons": db.cons.cpu().pin_memory(), "adm": db.adm.cpu().pin_memory(),
+             "bf": [x.cpu().pin_memory() for x in db.bf]}
+        return h
+
+    # three metrics: the block's, and two perturbed lapses (the step reads all 16 slots)
+    base = torch.from_numpy(np.ascontiguousarray(inp.adm))
+    adms = [base.clone().pin_memory()]
+    for k in (1, 2):
+        a = base.clone()
+        a[0] *= 1.0 + 1e-3 * k
+        adms.append(a.pin_memory())
+    s = torch.cuda.Stream()
+    ctx = T._ctx(G, p)
+    a = U.to_device(G, ob)
+    ha = host_of(a)
+    for k in range(3):
+        s.synchronize()   # the previous step's copy out of ha["adm"] has run
+        ha["adm"].copy_(adms[k])
+        ctx.step_host(a, ha, dt, s)
+    s.synchronize()
+    ctx2 = T._ctx(G, p)
+    b = U.to_device(G, ob)
+    hb = host_of(b)
+    hb["adm"] = adms[0]
+    st = ctx2.host_stepper(b, hb, stream=s)
+    for k in range(3):
+        st.step(dt, adm_next=adms[k + 1] if k + 1 < 3 else adms[0])
+    s.synchronize()
+    st.finish()
+    assert torch.equal(ha["cons"], hb["cons"])
+    for d in range(3):
+        assert torch.equal(ha["bf"][d], hb["bf"][d])
+    assert torch.equal(b.adm.cpu(), adms[2])
