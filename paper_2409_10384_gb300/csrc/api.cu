@@ -25,6 +25,8 @@ struct mhd_ctx {
   cudaStream_t side[2] = {nullptr, nullptr};
   cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
   cudaEvent_t state_ready = nullptr;   // mhd_step_overlap: the stages wait for it after the metric kernel
+  unsigned long long* fofc_list = nullptr;   // the FOFC estimate's flagged cells ([0] count)
+  long long fofc_cap = 0;
   // three-phase con2prim scratch: of the block list, and of independent cells
   char* krp = nullptr;
   long long krp_n = 0;
@@ -282,6 +284,9 @@ int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
   const long long nkrp = std::max(pre[(size_t)W_C2P * (nb + 1) + nb], pre[(size_t)W_CELL * (nb + 1) + nb]);
   const size_t krp_off = need;
   need += al256(krp_bytes(nkrp));
+  const long long ncell_all = pre[(size_t)W_CELL * (nb + 1) + nb];
+  const size_t list_off = need;
+  need += al256(sizeof(unsigned long long) * (size_t)(ncell_all + 1));
   const size_t mass_off = need;
   need += al256(sizeof(double) * (size_t)nb);
   const size_t led_off = need;
@@ -329,6 +334,8 @@ int prepare(mhd_ctx* c, const mhd_block* blocks, int nb) {
     }
   }
   c->krp = c->scratch + krp_off;
+  c->fofc_list = (unsigned long long*)(c->scratch + list_off);
+  c->fofc_cap = ncell_all;
   c->krp_n = nkrp;
   c->dmass = (double*)(c->scratch + mass_off);
   c->dledger = c->ledger_on ? (double*)(c->scratch + led_off) : nullptr;
@@ -512,6 +519,8 @@ int enqueue_rhs(mhd_ctx* c, double dt, int stage, cudaStream_t s, const Work& w,
   if (c->P.fofc) {
     if (c->P.guess == 1 && !c->mlp_ready) return MHD_ENOMLP;
     KrpBuf kb = krp_view(c->krp, items[W_CELL]);
+    kb.flist = c->fofc_list;
+    kb.fcap = c->fofc_cap;
     timed(c, MHD_K_FOFC_FLAG, s, [&] {
       launch_krp_prep_fofc(w, c->P, g0, g1, be * dt, kb, c->dstats, s, tgrid(c, T_FOFC_PREP, items[W_CELL]),
                            c->cfg[T_FOFC_PREP].threads, prep_mode(c->P.guess), nullptr);
@@ -522,10 +531,11 @@ int enqueue_rhs(mhd_ctx* c, double dt, int stage, cudaStream_t s, const Work& w,
       launch_krp_finish_fofc(w, c->P, kb, c->dstats, s, tgrid(c, T_FOFC_FIN, items[W_CELL]),
                              c->cfg[T_FOFC_FIN].threads);
     });
-    for (int d = 0; d < 3; d++) {
-      long long g = std::min<long long>((items[W_FX + d] + 127) / 128, (long long)c->nsm * c->occ_face[4]);
-      timed(c, MHD_K_FOFC_FIX, s, [&] { launch_fofc_fix(d, w, c->P, c->dstats, s, (int)std::max(1LL, g)); });
-    }
+    // the faces of the listed flagged cells (one launch; the list is short)
+    const long long g = std::min<long long>((items[W_CELL] + 127) / 128, (long long)c->nsm * std::max(c->occ_face[4], 1));
+    timed(c, MHD_K_FOFC_FIX, s, [&] {
+      launch_fofc_fix_list(w, c->P, kb.flist, kb.fcap, c->dstats, s, (int)std::max(1LL, g));
+    });
   }
   if (c->ledger_on) {
     // weight of this stage's L(U) in U^{n+1}; the floor mass of stage 0 enters U^n itself

@@ -232,6 +232,9 @@ struct KrpBuf {
                              // that give status 0, cleared by the finish after the
                              // solve: the solve returns at once on 0)
   long long n;
+  unsigned long long* flist = nullptr;   // FOFC estimate: [0] count, then the W_CELL
+                                         // items of the flagged cells (null: none kept)
+  long long fcap = 0;                    // entries flist can hold
 };
 
 struct Work {
@@ -1478,6 +1481,16 @@ __host__ __device__ inline void rk_weights(int order, int stage, double& g0, dou
 __device__ __forceinline__ void warp_flush(unsigned long long* ctr, unsigned v) {
   unsigned s = __reduce_add_sync(0xffffffffu, v);
   if ((threadIdx.x & 31) == 0 && s) atomicAdd(ctr, (unsigned long long)s);
+}
+// Interior cell (block bi, k, j, i) of item `it` of the interior-cell work
+// list (W_CELL, x fastest).
+__device__ __forceinline__ void fofc_cell(const Work& w, long long it, int& bi, int& k, int& j, int& i) {
+  const long long* pre = w.pre + (long long)W_CELL * (w.nblocks + 1);
+  bi = find_block(w, W_CELL, it);
+  const DevBlock& b = w.blk[bi];
+  long long loc = it - pre[bi];
+  i = loc % b.n[0]; long long r = loc / b.n[0]; j = r % b.n[1]; k = r / b.n[1];
+  i += b.ng; j += b.ng; k += b.ng;
 }
 // Marks the solve's work list as non-empty when any lane of the warp gave a
 // cell status 0 (every lane of the warp calls it).

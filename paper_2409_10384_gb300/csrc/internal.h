@@ -28,6 +28,10 @@ void launch_check_rcp(const double* x, long long n, double* out, cudaStream_t s,
 void launch_fofc_flag(const Work& w, const Par& P, double g0, double g1, double bdt, unsigned long long* stats,
                       cudaStream_t s, int grid);
 void launch_fofc_fix(int d, const Work& w, const Par& P, unsigned long long* stats, cudaStream_t s, int grid);
+// the flagged cells' faces from the list k_krp_finish_fofc keeps (list[0]
+// entries of at most cap)
+void launch_fofc_fix_list(const Work& w, const Par& P, const unsigned long long* list, long long cap,
+                          unsigned long long* stats, cudaStream_t s, int grid);
 void launch_emf(const Work& w, cudaStream_t s, int grid, int threads = 128);
 void launch_update_cells(const Work& w, const Par& P, double g0, double g1, double bdt, int first, cudaStream_t s,
                          int grid, int threads = 128);

@@ -127,6 +127,40 @@ __global__ void __launch_bounds__(128) k_fofc_fix(Work w, Par P, unsigned long l
   warp_flush(&stats[6], s_faces);
 }
 
+// The same recompute from the list of flagged interior cells that
+// k_krp_finish_fofc keeps (kb.flist): each cell takes its lower face along
+// each axis, and its upper face unless the cell above is a flagged interior
+// cell (which takes that face as its lower one), so every face touching a
+// flagged cell is recomputed once, with the values k_fofc_fix gives.
+template <int d>
+__device__ __forceinline__ void fix_face(const DevBlock& b, const Par& P, int k, int j, int i, unsigned& n) {
+  double F[7];
+  face_flux_donor<d>(b, P, k, j, i, F);
+  const long long f = fidx(b, d, k, j, i), nf = nface(b, d);
+  double* out = b.flux[d];
+#pragma unroll
+  for (int c = 0; c < 7; c++) out[c * nf + f] = F[c];
+  n++;
+}
+__global__ void __launch_bounds__(128) k_fofc_fix_list(Work w, Par P, const unsigned long long* __restrict__ list,
+                                                       long long cap, unsigned long long* stats) {
+  const long long cnt = (long long)list[0];
+  const long long n = cnt < cap ? cnt : cap;
+  unsigned s_faces = 0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    int bi, k, j, i;
+    fofc_cell(w, (long long)list[1 + q], bi, k, j, i);
+    const DevBlock& b = w.blk[bi];
+    fix_face<0>(b, P, k, j, i, s_faces);
+    fix_face<1>(b, P, k, j, i, s_faces);
+    fix_face<2>(b, P, k, j, i, s_faces);
+    if (!(interior(b, k, j, i + 1) && b.fflag[cidx(b, k, j, i + 1)])) fix_face<0>(b, P, k, j, i + 1, s_faces);
+    if (!(interior(b, k, j + 1, i) && b.fflag[cidx(b, k, j + 1, i)])) fix_face<1>(b, P, k, j + 1, i, s_faces);
+    if (!(interior(b, k + 1, j, i) && b.fflag[cidx(b, k + 1, j, i)])) fix_face<2>(b, P, k + 1, j, i, s_faces);
+  }
+  warp_flush(&stats[6], s_faces);
+}
+
 // The metric of one RK step (Z4c is not evolved: the ADM variables are an
 // input of the whole step): sqrt(gamma), 1/sqrt(gamma) and gamma^ij of every
 // cell of the con2prim region (DevBlock.mc), the interpolated face metric of
@@ -201,6 +235,10 @@ void launch_flux_dir(int d, const Work& w, const Par& P, cudaStream_t s, int gri
 void launch_fofc_flag(const Work& w, const Par& P, double g0, double g1, double bdt, unsigned long long* stats,
                       cudaStream_t s, int grid) {
   k_fofc_flag<<<grid, 128, 0, s>>>(w, P, g0, g1, bdt, stats);
+}
+void launch_fofc_fix_list(const Work& w, const Par& P, const unsigned long long* list, long long cap,
+                          unsigned long long* stats, cudaStream_t s, int grid) {
+  k_fofc_fix_list<<<grid, 128, 0, s>>>(w, P, list, cap, stats);
 }
 void launch_fofc_fix(int d, const Work& w, const Par& P, unsigned long long* stats, cudaStream_t s, int grid) {
   if (d == 0) k_fofc_fix<0><<<grid, 128, 0, s>>>(w, P, stats);

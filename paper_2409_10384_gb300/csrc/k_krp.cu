@@ -279,19 +279,14 @@ __global__ void __launch_bounds__(256) k_krp_finish_block(Work w, Par P, KrpBuf 
 }
 
 // ------------------------------------------------------------------ FOFC U*
-__device__ __forceinline__ void fofc_cell(const Work& w, long long it, int& bi, int& k, int& j, int& i) {
-  const long long* pre = w.pre + (long long)W_CELL * (w.nblocks + 1);
-  bi = find_block(w, W_CELL, it);
-  const DevBlock& b = w.blk[bi];
-  long long loc = it - pre[bi];
-  i = loc % b.n[0]; long long r = loc / b.n[0]; j = r % b.n[1]; k = r / b.n[1];
-  i += b.ng; j += b.ng; k += b.ng;
-}
 
 __global__ void __launch_bounds__(256) k_krp_prep_fofc(Work w, Par P, double g0, double g1, double bdt, KrpBuf kb,
                                                         int mode, float* feat, unsigned long long* stats) {
   const long long tot = w.pre[(long long)W_CELL * (w.nblocks + 1) + w.nblocks];
-  if (blockIdx.x == 0 && threadIdx.x == 0) *kb.ctr = 0ull;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *kb.ctr = 0ull;
+    if (kb.flist) kb.flist[0] = 0ull;   // the finish lists this stage's flagged cells
+  }
   const long long n = kb.n;
   unsigned s_f32 = 0, s_fb = 0;
   bool any0 = false;
@@ -369,6 +364,10 @@ __global__ void __launch_bounds__(256) k_krp_finish_fofc(Work w, Par P, KrpBuf k
       s_dmp += flag ? 1u : 0u;
     }
     b.fflag[c] = flag ? 1 : 0;
+    if (flag && kb.flist) {   // rare: one atomic per flagged cell
+      const unsigned long long pos = atomicAdd(kb.flist, 1ull);
+      if ((long long)pos < kb.fcap) kb.flist[1 + pos] = (unsigned long long)it;
+    }
     unsigned char f0 = b.flags[c];
     b.flags[c] = flag ? (unsigned char)(f0 | F_FOFC) : (unsigned char)(f0 & ~F_FOFC);
     s_flag += flag ? 1u : 0u;
