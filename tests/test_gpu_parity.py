@@ -365,9 +365,9 @@ def test_segment_length_leaves_every_face_unchanged(G):
     """A face's flux does not depend on how its line is cut into sweep
     segments.  Two ragged blocks stepped on their own get one-face segments
     (too few sweeps for longer ones).  In one list with a 104^3 block they get
-    the 128^3 bench block's lengths: at most 8 faces along x, as equal
-    segments plus a remainder per line (16 + 6 and 24 + 7 faces here), and at
-    most 16 along y and z.  Every cell and face must agree bit for bit."""
+    the 128^3 bench block's length, at most 16 faces: along x as equal
+    segments plus a remainder per line (11 + 11 and 16 + 15 faces here), along
+    y and z near-equal.  Every cell and face must agree bit for bit."""
     import torch
     p = O.params(gamma=2.0, rho_atm=1e-12, T_atm=1e-10, recon=2, rsolver=1, rk_order=3, fofc=1)
     st = synth.spacetime(2)
