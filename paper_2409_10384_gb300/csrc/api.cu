@@ -492,7 +492,10 @@ int enqueue_c2p(mhd_ctx* c, cudaStream_t s, const Work& w, const long long* item
   return cuda_ok(cudaGetLastError());
 }
 
-int enqueue_rhs(mhd_ctx* c, double dt, int stage, cudaStream_t s, const Work& w, const long long* items) {
+// emf: launch the edge EMFs here (the stage entry points); the whole step
+// launches them in enqueue_update instead, beside the cell update.
+int enqueue_rhs(mhd_ctx* c, double dt, int stage, cudaStream_t s, const Work& w, const long long* items,
+                bool emf = true) {
   double g0, g1, be;
   rk_weights(c->P.rk_order, stage, g0, g1, be);
   // The three sweeps read the stage's primitives and write their own flux
@@ -543,21 +546,27 @@ int enqueue_rhs(mhd_ctx* c, double dt, int stage, cudaStream_t s, const Work& w,
     const double bs = c->P.rk_order == 3 ? b3[stage] : b2[stage];
     timed(c, MHD_K_LEDGER, s, [&] { launch_ledger_stage(w, stage == 0 ? 1.0 : bs, dt * bs, s); });
   }
-  timed(c, MHD_K_EMF, s, [&] {
-    launch_emf(w, s, tgrid(c, T_EMF, items[W_EDGE]), c->cfg[T_EMF].threads);
-  });
+  if (emf)
+    timed(c, MHD_K_EMF, s, [&] {
+      launch_emf(w, s, tgrid(c, T_EMF, items[W_EDGE]), c->cfg[T_EMF].threads);
+    });
   c->rhs_list = c->list_version;
   c->rhs_stage = stage;
   return cuda_ok(cudaGetLastError());
 }
 
-int enqueue_update(mhd_ctx* c, double dt, int stage, cudaStream_t s, const Work& w, const long long* items) {
+// emf: launch the edge EMFs first on the face update's stream (the whole
+// step; the stage entry points have them from enqueue_rhs).
+int enqueue_update(mhd_ctx* c, double dt, int stage, cudaStream_t s, const Work& w, const long long* items,
+                   bool emf = false) {
   double g0, g1, be;
   rk_weights(c->P.rk_order, stage, g0, g1, be);
   const int first = stage == 0 ? 1 : 0;
   // U and the face B~ are updated from different inputs (fluxes and sources;
-  // edge EMFs) into different arrays: the face update runs on a side stream
-  // beside the cell update (sequentially with the per-kernel profile on).
+  // edge EMFs) into different arrays: the face update, and the EMFs it reads
+  // when they are launched here, run on a side stream beside the cell update
+  // (the EMF kernel waits on its scattered loads, the cell update on the FP64
+  // pipe); sequentially with the per-kernel profile on.
   const bool fork = !c->prof;
   cudaStream_t sf = fork ? c->side[0] : s;
   if (fork) {
@@ -567,6 +576,10 @@ int enqueue_update(mhd_ctx* c, double dt, int stage, cudaStream_t s, const Work&
   timed(c, MHD_K_UPDATE, s, [&] {
     launch_update_cells(w, c->P, g0, g1, be * dt, first, s, tgrid(c, T_UPD, items[W_CELL]), c->cfg[T_UPD].threads);
   });
+  if (emf)
+    timed(c, MHD_K_EMF, sf, [&] {
+      launch_emf(w, sf, tgrid(c, T_EMF, items[W_EDGE]), c->cfg[T_EMF].threads);
+    });
   long long gfa = std::min<long long>((items[W_FACE] + 255) / 256, (long long)c->nsm * std::max(c->occ_upd[2], 1));
   timed(c, MHD_K_FACEB, sf, [&] { launch_update_faces(w, g0, g1, be * dt, first, sf, (int)std::max(1LL, gfa)); });
   if (fork) {
@@ -599,15 +612,15 @@ int enqueue_c2p(mhd_ctx* c, cudaStream_t s, bool refresh) {
   list_items(c, it);
   return enqueue_c2p(c, s, work_of(c), it, refresh);
 }
-int enqueue_rhs(mhd_ctx* c, double dt, int stage, cudaStream_t s) {
+int enqueue_rhs(mhd_ctx* c, double dt, int stage, cudaStream_t s, bool emf = true) {
   long long it[W_NKIND];
   list_items(c, it);
-  return enqueue_rhs(c, dt, stage, s, work_of(c), it);
+  return enqueue_rhs(c, dt, stage, s, work_of(c), it, emf);
 }
-int enqueue_update(mhd_ctx* c, double dt, int stage, cudaStream_t s) {
+int enqueue_update(mhd_ctx* c, double dt, int stage, cudaStream_t s, bool emf = false) {
   long long it[W_NKIND];
   list_items(c, it);
-  return enqueue_update(c, dt, stage, s, work_of(c), it);
+  return enqueue_update(c, dt, stage, s, work_of(c), it, emf);
 }
 
 // every block on its own: one launch sequence per block and stage
@@ -618,8 +631,8 @@ int enqueue_step_per_block(mhd_ctx* c, double dt, cudaStream_t s) {
       block_items(c, b, it);
       Work w = block_work(c, b);
       int r = enqueue_c2p(c, s, w, it, st == 0);
-      if (!r) r = enqueue_rhs(c, dt, st, s, w, it);
-      if (!r) r = enqueue_update(c, dt, st, s, w, it);
+      if (!r) r = enqueue_rhs(c, dt, st, s, w, it, false);
+      if (!r) r = enqueue_update(c, dt, st, s, w, it, true);
       if (r) return r;
     }
   return MHD_OK;
@@ -630,8 +643,8 @@ int enqueue_step_per_block(mhd_ctx* c, double dt, cudaStream_t s) {
 int enqueue_step(mhd_ctx* c, double dt, cudaStream_t s) {
   for (int st = 0; st < c->P.rk_order; st++) {
     int r = enqueue_c2p(c, s, st == 0);
-    if (!r) r = enqueue_rhs(c, dt, st, s);
-    if (!r) r = enqueue_update(c, dt, st, s);
+    if (!r) r = enqueue_rhs(c, dt, st, s, false);
+    if (!r) r = enqueue_update(c, dt, st, s, true);
     if (r) return r;
   }
   return MHD_OK;
