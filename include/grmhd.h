@@ -119,7 +119,9 @@ typedef struct {
 /* Counters accumulated on the device since the last mhd_reset_stats. */
 typedef struct {
   long long cells;      /* con2prim solves on stage inputs */
-  long long iters;      /* summed root iterations of those solves */
+  long long iters;      /* FP64 evaluations of the master function in those
+                           solves (bracket, polish and root iteration; the FOFC
+                           estimate's solves are not counted) */
   long long fails;      /* failures (MHD_F_FAIL) */
   long long floors;     /* cells where a floor fired */
   long long fofc_cells; /* cells flagged by FOFC (incl. DMP) */
