@@ -287,13 +287,15 @@ def train_guess_blocks(ctx, blocks, per_block=640, epochs=30):
 
 def periodic32_leg(G, steps=50):
     """The 32^3 periodic flat block (Gamma 5/3, PLM + HLLE + CT, the main
-    leg's con2prim, SSP-RK2): one RK2 step per iteration, launched directly and as
+    leg's con2prim, SSP-RK2, a fixed flat metric whose cache is kept across
+    steps): one RK2 step per iteration, launched directly and as
     the captured graph, each with and without the periodic ghost fill
     (mhd_fill_ghosts) before the step."""
     import torch
     from paper_2409_10384_gb300 import synth
     p = dict(gamma=5.0 / 3.0, rho_atm=1e-12, T_atm=1e-10, f_thr=0.1, sigma_max=0.0, dmp_M=0.0, c2p_tol=1e-10,
-             W_max=1e3, recon=1, rsolver=1, fofc=0, rk_order=2, c2p_maxit=64, c2p_guess=C2P_GUESS)
+             W_max=1e3, recon=1, rsolver=1, fofc=0, rk_order=2, c2p_maxit=64, c2p_guess=C2P_GUESS,
+             fixed_metric=1)   # flat and constant: the metric cache is kept across steps
     inp = synth.periodic_flat(1)
     ctx = G.Context(G.params(**p))
     blk = G.DeviceBlock(inp.n, inp.ng, inp.dx, inp.adm)

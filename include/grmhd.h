@@ -99,6 +99,13 @@ typedef struct {
   double eos_gamma_th;  /* thermal index (> 1) */
   double eos_rho[3];    /* dividing densities, increasing, > 0 */
   double eos_gamma[4];  /* piece indices (> 1) */
+  int fixed_metric;     /* 1: a fixed spacetime (the Cowling runs of Sec. 4.4: the
+                           metric is not evolved): the caller keeps the ADM arrays
+                           unchanged between mhd_step calls, so the step's metric
+                           cache is computed once per block list and reused by
+                           later steps (a new block list recomputes it; mhd_c2p
+                           still recomputes it every call).  0: every mhd_step
+                           recomputes it from the ADM arrays. */
 } mhd_params;
 
 /* One meshblock: views into caller-owned device arrays. */

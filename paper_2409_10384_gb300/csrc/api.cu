@@ -82,7 +82,9 @@ struct mhd_ctx {
   // graph cache
   cudaGraphExec_t gexec = nullptr;
   long long g_list = -1, g_par = -1;
+  bool g_metric = true;   // the captured step includes the metric kernel
   double g_dt = 0.0;
+  long long metric_list = -1;   // block list whose ADM arrays the metric cache holds
   cudaStream_t g_stream = nullptr;
   long long par_version = 0;
   int g_launches = 0;
@@ -104,7 +106,8 @@ int fill_par(const mhd_params* p, Par& P, bool allow_guess) {
   if (!(p->gamma > 1.0) || !(p->rho_atm > 0.0) || !(p->T_atm > 0.0) || !(p->f_thr >= 0.0) || !(p->c2p_tol > 0.0) ||
       !(p->W_max > 1.0) || p->recon < 0 || p->recon > 4 || p->rsolver < 0 || p->rsolver > 1 ||
       (p->rk_order != 2 && p->rk_order != 3) || p->c2p_maxit < 1 || p->c2p_guess < 0 ||
-      p->c2p_guess > (allow_guess ? 3 : 0) || (p->dmp_M > 0.0 && p->dmp_M < 1.0) || p->eos < 0 || p->eos > 1)
+      p->c2p_guess > (allow_guess ? 3 : 0) || (p->dmp_M > 0.0 && p->dmp_M < 1.0) || p->eos < 0 || p->eos > 1 ||
+      p->fixed_metric < 0 || p->fixed_metric > 1)
     return MHD_EINVAL;
   std::memset(&P, 0, sizeof(P));
   P.eos = p->eos;
@@ -475,6 +478,7 @@ int enqueue_c2p(mhd_ctx* c, cudaStream_t s, const Work& w, const long long* item
     const long long tot = items[W_C2P] + items[W_FX] + items[W_FY] + items[W_FZ] + items[W_CELL];
     const long long g = std::max(1LL, std::min((tot + 255) / 256, (long long)c->nsm * std::max(c->occ_metric, 1)));
     timed(c, MHD_K_METRIC, s, [&] { launch_metric_cache(w, s, (int)g); });
+    c->metric_list = c->list_version;
     if (c->state_ready && cudaStreamWaitEvent(s, c->state_ready, 0) != cudaSuccess) return MHD_ECUDA;
   }
   KrpBuf kb = krp_view(c->krp, items[W_C2P]);
@@ -624,13 +628,13 @@ int enqueue_update(mhd_ctx* c, double dt, int stage, cudaStream_t s, bool emf = 
 }
 
 // every block on its own: one launch sequence per block and stage
-int enqueue_step_per_block(mhd_ctx* c, double dt, cudaStream_t s) {
+int enqueue_step_per_block(mhd_ctx* c, double dt, cudaStream_t s, bool metric) {
   for (int st = 0; st < c->P.rk_order; st++)
     for (int b = 0; b < (int)c->key.size(); b++) {
       long long it[W_NKIND];
       block_items(c, b, it);
       Work w = block_work(c, b);
-      int r = enqueue_c2p(c, s, w, it, st == 0);
+      int r = enqueue_c2p(c, s, w, it, st == 0 && metric);
       if (!r) r = enqueue_rhs(c, dt, st, s, w, it, false);
       if (!r) r = enqueue_update(c, dt, st, s, w, it, true);
       if (r) return r;
@@ -639,10 +643,14 @@ int enqueue_step_per_block(mhd_ctx* c, double dt, cudaStream_t s) {
 }
 
 // The metric is an input of the whole step: its cache is computed once,
-// before the first stage.
-int enqueue_step(mhd_ctx* c, double dt, cudaStream_t s) {
+// before the first stage, unless the spacetime is fixed (mhd_params.
+// fixed_metric) and the cache already holds this block list's metric.
+bool metric_needed(const mhd_ctx* c) { return !(c->hp.fixed_metric && c->metric_list == c->list_version); }
+int enqueue_step(mhd_ctx* c, double dt, cudaStream_t s, bool metric) {
+  // without the metric kernel the caller's state event is waited for here
+  if (!metric && c->state_ready && cudaStreamWaitEvent(s, c->state_ready, 0) != cudaSuccess) return MHD_ECUDA;
   for (int st = 0; st < c->P.rk_order; st++) {
-    int r = enqueue_c2p(c, s, st == 0);
+    int r = enqueue_c2p(c, s, st == 0 && metric);
     if (!r) r = enqueue_rhs(c, dt, st, s, false);
     if (!r) r = enqueue_update(c, dt, st, s, true);
     if (r) return r;
@@ -1228,14 +1236,16 @@ int mhd_step(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, int graph, 
   int r = prepare(c, blocks, nb);
   if (r) return r;
   cudaStream_t s = (cudaStream_t)stream;
-  if (graph == 2) return enqueue_step_per_block(c, dt, s);
-  if (!graph) return enqueue_step(c, dt, s);
+  const bool metric = metric_needed(c);
+  if (graph == 2) return enqueue_step_per_block(c, dt, s, metric);
+  if (!graph) return enqueue_step(c, dt, s, metric);
   if (!s) return MHD_EINVAL;  // the legacy default stream cannot be captured
-  if (!(c->gexec && c->g_list == c->list_version && c->g_par == c->par_version && c->g_dt == dt && c->g_stream == s)) {
+  if (!(c->gexec && c->g_list == c->list_version && c->g_par == c->par_version && c->g_dt == dt && c->g_stream == s &&
+        c->g_metric == metric)) {
     destroy_graph(c);
     long long before = c->launches;
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MHD_ECUDA;
-    int er = enqueue_step(c, dt, s);
+    int er = enqueue_step(c, dt, s, metric);
     cudaGraph_t g = nullptr;
     cudaError_t ce = cudaStreamEndCapture(s, &g);
     if (er || ce != cudaSuccess) {
@@ -1251,6 +1261,7 @@ int mhd_step(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, int graph, 
     c->g_par = c->par_version;
     c->g_dt = dt;
     c->g_stream = s;
+    c->g_metric = metric;
   }
   c->launches += c->g_launches;
   return cuda_ok(cudaGraphLaunch(c->gexec, s));
@@ -1272,7 +1283,7 @@ int mhd_step_overlap(mhd_ctx* c, const mhd_block* blocks, int nb, double dt, voi
   int r = prepare(c, blocks, nb);
   if (r) return r;
   c->state_ready = (cudaEvent_t)state_ready;
-  r = enqueue_step(c, dt, (cudaStream_t)stream);
+  r = enqueue_step(c, dt, (cudaStream_t)stream, metric_needed(c));
   c->state_ready = nullptr;
   return r;
 }

@@ -31,7 +31,7 @@ class mhd_params(C.Structure):
         ("recon", C.c_int), ("rsolver", C.c_int), ("fofc", C.c_int), ("rk_order", C.c_int),
         ("c2p_maxit", C.c_int), ("c2p_guess", C.c_int),
         ("eos", C.c_int), ("eos_pieces", C.c_int), ("eos_K0", C.c_double), ("eos_gamma_th", C.c_double),
-        ("eos_rho", C.c_double * 3), ("eos_gamma", C.c_double * 4),
+        ("eos_rho", C.c_double * 3), ("eos_gamma", C.c_double * 4), ("fixed_metric", C.c_int),
     ]
 
 
@@ -143,7 +143,7 @@ def params(**kw) -> mhd_params:
     d = dict(gamma=5.0 / 3.0, rho_atm=1e-12, T_atm=1e-10, f_thr=0.1, sigma_max=0.0, dmp_M=0.0, c2p_tol=1e-10,
              W_max=1e3, alpha_exc=0.0, recon=1, rsolver=1, fofc=0, rk_order=2, c2p_maxit=64, c2p_guess=0,
              eos=0, eos_pieces=1, eos_K0=100.0, eos_gamma_th=2.0, eos_rho=(0.0, 0.0, 0.0),
-             eos_gamma=(2.0, 2.0, 2.0, 2.0))
+             eos_gamma=(2.0, 2.0, 2.0, 2.0), fixed_metric=0)
     d.update(kw)
     p = mhd_params()
     for k, v in d.items():

@@ -39,6 +39,8 @@ def test_null_and_bad_arguments_rejected_without_device(L):
     assert L.mhd_init(C.byref(p), C.byref(h)) == -1
     p = grmhd.params(dmp_M=0.5)
     assert L.mhd_init(C.byref(p), C.byref(h)) == -1
+    p = grmhd.params(fixed_metric=2)
+    assert L.mhd_init(C.byref(p), C.byref(h)) == -1
     # hybrid EOS: pieces out of range, non-increasing dividing densities, a
     # thermal index <= 1, and the FP32 root searches (ideal gas only)
     for kw in (dict(eos_pieces=0), dict(eos_pieces=5), dict(eos_rho=(1e-4, 1e-8, 0.0)),
@@ -67,12 +69,12 @@ def test_blob_size_matches_header():
 
 
 def test_struct_layouts_match_header():
-    # mhd_params: 9 doubles + 8 ints + 9 doubles (EOS); mhd_block: 3+1 ints, 3 doubles, 12 pointers;
-    # mhd_stats: MHD_NSTATS int64
+    # mhd_params: 9 doubles + 8 ints + 9 doubles (EOS) + one int (fixed_metric) padded to 8;
+    # mhd_block: 3+1 ints, 3 doubles, 12 pointers; mhd_stats: MHD_NSTATS int64
     import re
     h = open(grmhd._build.ROOT + "/include/grmhd.h").read()
     nst = int(re.search(r"#define MHD_NSTATS (\d+)", h).group(1))
-    assert C.sizeof(grmhd.mhd_params) == 9 * 8 + 8 * 4 + 9 * 8
+    assert C.sizeof(grmhd.mhd_params) == 9 * 8 + 8 * 4 + 9 * 8 + 8
     assert C.sizeof(grmhd.mhd_block) == 16 + 24 + 12 * 8
     assert C.sizeof(grmhd.mhd_stats) == nst * 8 == 9 * 8
 

@@ -234,3 +234,44 @@ def test_host_stepper_equals_step_host(G):
     for d in range(3):
         assert torch.equal(ha["bf"][d], hb["bf"][d])
     assert torch.equal(b.adm.cpu(), adms[2])
+
+
+def test_fixed_metric_reuses_the_cache(G):
+    """mhd_params.fixed_metric (a fixed spacetime, the Cowling runs of Sec.
+    4.4): three RK3 steps, direct and graphed, give the bits of ordinary steps
+    with the ADM arrays unchanged; after the first step each step launches one
+    kernel fewer (no metric kernel), and a new block list computes the metric
+    again."""
+    import torch
+    p = O.params(gamma=2.0, rho_atm=1e-12, T_atm=1e-10, f_thr=0.1, recon=2, rsolver=1, rk_order=3, fofc=1)
+    kw = {k: getattr(p, k) for k, _ in p._fields_ if k != "pad_"}
+    inp, ob = _star(G, p)
+    dt = 0.25 * inp.dx[0]
+    s = torch.cuda.Stream()
+    ref = G.Context(G.params(**kw))
+    a = U.to_device(G, ob)
+    for _ in range(3):
+        ref.step([a], dt, stream=s)
+    s.synchronize()
+    for graph in (False, True):
+        ctx = G.Context(G.params(**kw, fixed_metric=1))
+        b = U.to_device(G, ob)
+        n = []
+        for _ in range(3):
+            l0 = ctx.launches()
+            ctx.step([b], dt, graph=graph, stream=s)
+            n.append(ctx.launches() - l0)
+        s.synchronize()
+        assert torch.equal(a.cons, b.cons), graph
+        for d in range(3):
+            assert torch.equal(a.bf[d], b.bf[d]), graph
+        assert n[1] == n[2] == n[0] - 1, (graph, n)
+        # another block list, then the first again: each computes its metric
+        c = U.to_device(G, ob)
+        l0 = ctx.launches()
+        ctx.step([c], dt, graph=graph, stream=s)
+        assert ctx.launches() - l0 == n[0], graph
+        l0 = ctx.launches()
+        ctx.step([b], dt, graph=graph, stream=s)
+        assert ctx.launches() - l0 == n[0], graph
+        s.synchronize()
