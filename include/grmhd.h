@@ -137,11 +137,16 @@ typedef struct {
   long long guess_fallbacks; /* c2p_guess 1, 2: cells whose FP64 polish was not
                                 taken as the root (the FP64 solve then runs from
                                 the bracket its two evaluations give) */
-  long long fp32_evals; /* c2p_guess 1, 2: FP32 evaluations of the master
-                           function in the searches (the two starting points
-                           and one per secant step) */
+  long long fp32_evals; /* FP32 evaluations of the master function in the
+                           searches of c2p_guess 1, 2 (the two starting points,
+                           one per secant step, two for the slope) and in the
+                           FP32 decisions of the FOFC estimate (every mode) */
+  long long fofc_fp32;  /* FOFC estimate cells (and cells of a flags-only
+                           mhd_c2p_cells) whose flag was decided from FP32
+                           values, without an FP64 evaluation of the master
+                           function (ideal gas) */
 } mhd_stats;
-#define MHD_NSTATS 9
+#define MHD_NSTATS 10
 
 /* Create a context on the current device.  *out receives it.  Copies p. */
 int mhd_init(const mhd_params* p, mhd_ctx** out);
@@ -166,8 +171,13 @@ int mhd_prim2cons(mhd_ctx* ctx, long n, const double* prim, const double* Bd, co
  * a floor changed it; prim [5][n] and flags [n] are written; iters [n] (may be
  * NULL) receives the FP64 evaluations of the master function per cell.
  * Device pointers.  stats (host, may be NULL): the counters this call added
- * (cells, iters, fails, floors, guess_fallbacks); a non-NULL stats makes the
- * call synchronise the stream (before and after its launches). */
+ * (cells, iters, fails, floors, guess_fallbacks, fp32_evals); a non-NULL stats
+ * makes the call synchronise the stream (before and after its launches).
+ * prim = NULL asks only the question of the FOFC estimate (Sec. 3.3): flags[c]
+ * = 1 where con2prim of the cell fails or a floor fires, else 0; cons is not
+ * written.  With the ideal gas most cells are then decided from FP32 values
+ * without an FP64 evaluation (stats: fofc_fp32; iters 0 for them), and the
+ * flagged cells are counted in fofc_cells (fails and floors are not). */
 int mhd_c2p_cells(mhd_ctx* ctx, long n, double* cons, const double* Bd, const double* g, double* prim,
                   unsigned char* flags, int* iters, void* stream, mhd_stats* stats);
 

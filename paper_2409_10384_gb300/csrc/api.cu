@@ -169,6 +169,12 @@ int fill_par(const mhd_params* p, Par& P, bool allow_guess) {
   P.exc_on = p->alpha_exc > 0.0 ? 1 : 0;
   P.sigma_on = p->sigma_max > 0.0 ? 1 : 0;
   P.thr_pos = P.rho_thr > 0.0 ? 1 : 0;
+  // the FP32 decision of the FOFC flags: ideal gas, thresholds inside the FP32 range
+  P.dec32 = (p->eos == 0 && P.eps_atm >= 1e-30 && P.eps_atm <= 1e30 &&
+             (!P.thr_pos || (P.rho_thr >= 1e-30 && P.rho_thr <= 1e30)))
+                ? 1
+                : 0;
+  P.rho_thr32 = (float)P.rho_thr;
   P.recon = p->recon;
   P.rsolver = p->rsolver;
   P.fofc = p->fofc ? 1 : 0;
@@ -931,7 +937,7 @@ extern "C" {
 
 int mhd_c2p_cells(mhd_ctx* c, long n, double* cons, const double* Bd, const double* g, double* prim,
                   unsigned char* flags, int* iters, void* stream, mhd_stats* stats) {
-  if (!c || n < 0 || (n > 0 && (!cons || !Bd || !g || !prim || !flags))) return MHD_EINVAL;
+  if (!c || n < 0 || (n > 0 && (!cons || !Bd || !g || !flags))) return MHD_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned long long h0[MHD_NSTATS], h1[MHD_NSTATS];
   int r = stats ? stats_host(c, s, h0) : MHD_OK;
@@ -956,7 +962,8 @@ int c2p_cells_enqueue(mhd_ctx* c, long n, double* cons, const double* Bd, const 
   int r = cells_scratch(c, n, s, &kb, &feat, &logmu);
   if (r) return r;
   timed(c, MHD_K_C2P, s, [&] {
-    launch_krp_prep_cells(c->P, kb, cons, Bd, g, mode, nullptr, c->dstats, s, cells_grid(c, n, c->occ_krp[5]));
+    launch_krp_prep_cells(c->P, kb, cons, Bd, g, mode, nullptr, c->dstats, s, cells_grid(c, n, c->occ_krp[5]),
+                          prim == nullptr);
   });
   c2p_seed(c, kb, n, s);
   timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, s, c->solve_grid(n)); });

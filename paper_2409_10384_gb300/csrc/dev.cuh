@@ -34,6 +34,10 @@ struct Par {
   int recon, rsolver, fofc, rk_order, maxit, guess, eos, npc;
   int exc_on, sigma_on;         // alpha_exc > 0, sigma_max > 0
   int thr_pos;                  // rho_thr > 0
+  int dec32;                    // the FOFC flags may come from FP32 values (fofc_decide32):
+                                // ideal gas, eps_atm and rho_thr (when > 0) within
+                                // [1e-30, 1e30]
+  float rho_thr32;              // rho_thr in FP32
 };
 
 // One meshblock as seen by the kernels: caller arrays plus context scratch.
@@ -206,7 +210,9 @@ enum {
 };
 // solve status: 0 solve needed, 1 root known, 2 no bracket / bad input,
 // 3 iteration cap, 4 bracket to be built from the learned guess, 5 FOFC
-// estimate flagged by a floor on U* before the solve (no solve)
+// estimate flagged without a recovery (a floor on U* before the solve, or the
+// FP32 decision, fofc_decide32), 7 FOFC estimate not flagged by the FP32
+// decision (no solve, no recovery)
 
 // Learned-guess network 5 -> 64 -> 64 -> 1: fp32 parameter offsets, bf16
 // operand copies (W1 padded to [64][16], W2 [64][64], w3 padded to [8][64]).
@@ -904,6 +910,86 @@ __device__ __forceinline__ int krp_polish(const KS& s, const Par& P, double m0, 
   if (!(lt0(Ga) && (eq0(Gb) || gt0(Gb)))) return 2;
   if (eq0(Gb)) { mu = b; return 1; }
   return 0;
+}
+
+// ------------------------------------------- FOFC flags from FP32 values
+// The FOFC estimate asks of con2prim(U*) only whether it fails or a floor on
+// the primitives fires (Sec. 3.3).  Away from every threshold the FP32 search
+// answers that.  f is evaluated in FP32 at lo, hi = m (1 -+ h) around the
+// FP32 root m, h eight times the error bound of f at m relative to m (within
+// [2^-20, 2^-10]).  When f(lo) < -e and f(hi) > e, with e a bound on the FP32
+// error of f, the root of the FP64 f lies in [lo, hi] (f has one root).  The
+// recovery takes the velocity cap where v^2 > vmax^2, the density floor where
+// rho = D/W < rho_thr, and the T floor where eps_raw < eps_atm (with the ideal
+// gas p < rho T_atm is eps < T_atm/(Gamma-1) = eps_atm).  When each of v^2,
+// rho and eps_raw lies on one side of its threshold at both ends, by more
+// than its change across [lo, hi] plus its FP32 error bound, the recovery at
+// the root takes the same decision.  The error bounds are 2^-18 (64 units of
+// FP32 rounding) of the sum of the magnitudes that form each value, times W^2
+// where 1 - v^2 is rounded.
+struct F32Rec {
+  float f, v2, W, eps_raw;
+  float S;    // the magnitude of eps_raw's terms (its error bound is 2^-18 S W^2)
+  float ef;   // the bound on the FP32 error of f: 2^-18 W^2 (mu + W/Z (1 + Gamma S)), Z >= 1
+};
+__device__ __forceinline__ void f32_rec(const KSf& s, float mu, F32Rec& e) {
+  const float x = 1.0f / fmaf(mu, s.b2, 1.0f);
+  const float mux = mu * x;
+  const float rbar2 = x * fmaf(s.r2, x, mu * (1.0f + x) * s.rb2);
+  const float qp = 0.5f * mux * mux * s.rp2;
+  const float v2 = mu * mu * rbar2;
+  const float vh2 = fminf(v2, s.vmax2);
+  const float W = rsqrtf(1.0f - vh2);
+  const float wm1 = vh2 * W * W / (1.0f + W);
+  const float murb = mu * rbar2;
+  const float eps_raw = fmaf(W, (s.qh - qp) - murb, wm1);
+  const float Z = fmaf(murb, W, fmaf(s.gam, fmaxf(eps_raw, s.emin), 1.0f));   // >= 1
+  const float WZ = W / Z;
+  const float W2 = W * W;
+  e.f = mu - WZ;
+  e.v2 = v2;
+  e.W = W;
+  e.eps_raw = eps_raw;
+  e.S = fmaf(W, fabsf(s.qh) + qp + murb, wm1);
+  e.ef = 3.81469727e-6f * fmaf(WZ, fmaf(s.gam, e.S, 1.0f), mu) * W2;
+}
+// 1: flagged for sure, 0: not flagged for sure, -1: undecided (the FP64
+// polish or solve and the recovery decide).  m: the FP32 root; D: D in FP32.
+// nf counts the FP32 evaluations of f.
+__device__ __forceinline__ int fofc_decide32(const KSf& s, const Par& P, float D, float m, unsigned& nf) {
+  if (!(m > 1e-30f && m <= 1.0f) || !(D >= 1e-30f && D <= 1e30f)) return -1;
+  const float u = 3.81469727e-6f;   // 2^-18
+  // the half-width: 8 error bounds of f at m (f' is about 1), within [2^-20, 2^-10]
+  F32Rec a, b;
+  f32_rec(s, m, a);
+  const float h = fminf(fmaxf(8.0f * a.ef / m, 9.53674316e-7f), 9.765625e-4f);
+  const float lo = m * (1.0f - h), hi = fminf(m * (1.0f + h), 1.0f);
+  f32_rec(s, lo, a);
+  f32_rec(s, hi, b);
+  nf += 3;
+  // at hi = 1 no sign test is needed: f(1) >= 0 for every eps >= eps_min > 0
+  // (Z >= 1 + vh^2 W + Gamma eps >= W, as W - 1 = vh^2 W^2/(1 + W) <= vh^2 W),
+  // which is where cold cells (root 1 - Gamma eps + ...) put their root
+  if (!(a.f < -a.ef && (hi >= 1.0f || b.f > b.ef))) return -1;
+  const float W2 = fmaxf(a.W * a.W, b.W * b.W);
+  // velocity cap
+  const float dv = fabsf(b.v2 - a.v2) + u * s.vmax2;
+  if (a.v2 > s.vmax2 + dv && b.v2 > s.vmax2 + dv) return 1;
+  if (!(a.v2 < s.vmax2 - dv && b.v2 < s.vmax2 - dv)) return -1;
+  // density floor (with rho_thr = 0 the floor takes rho < 0, and D > 0 here)
+  bool low_rho = false;
+  if (P.thr_pos) {
+    const float ra = D / a.W, rb = D / b.W, t = P.rho_thr32;
+    const float dr = fabsf(rb - ra) + u * (t + fmaxf(ra, rb) * W2);
+    if (ra < t - dr && rb < t - dr) low_rho = true;
+    else if (!(ra > t + dr && rb > t + dr)) return -1;
+  }
+  // T floor
+  const float t = s.emin;
+  const float de = fabsf(b.eps_raw - a.eps_raw) + u * fmaf(fmaxf(a.S, b.S), W2, t);
+  if (a.eps_raw < t - de && b.eps_raw < t - de) return 1;
+  if (!(a.eps_raw > t + de && b.eps_raw > t + de)) return low_rho ? 1 : -1;
+  return low_rho ? 1 : 0;
 }
 
 // Phase 3: primitives at the root mu (Sec. 3.4 recovery) and the floors on

@@ -57,8 +57,11 @@ void launch_krp_prep_fofc(const Work& w, const Par& P, double g0, double g1, dou
                           float* feat = nullptr);
 void launch_krp_finish_fofc(const Work& w, const Par& P, const KrpBuf& kb, unsigned long long* stats,
                             cudaStream_t s, int grid, int threads = 128);
+// fonly: flags only (the FOFC estimate's question, no recovery written; the
+// finish then gets prim = null)
 void launch_krp_prep_cells(const Par& P, const KrpBuf& kb, const double* cons, const double* Bd, const double* g,
-                           int mode, float* feat, unsigned long long* stats, cudaStream_t s, int grid);
+                           int mode, float* feat, unsigned long long* stats, cudaStream_t s, int grid,
+                           bool fonly = false);
 void launch_krp_finish_cells(const Par& P, const KrpBuf& kb, double* cons, const double* Bd, const double* g,
                              double* prim, unsigned char* flags, int* iters, unsigned long long* stats, cudaStream_t s,
                              int grid);

@@ -40,48 +40,72 @@ __device__ __forceinline__ void kw_load(const KrpBuf& kb, const Par& P, long lon
 // the cell's previous root; the FP64 bracket starts as guess (1 -+
 // WARM_DELTA), verified by the signs at both ends (krp_bracket).
 // fofc: the FOFC estimate, which only needs to know whether con2prim of U*
-// fails or a floor fires (Sec. 3.3); a floor on the conserved state decides
+// fails or a floor fires (Sec. 3.3).  A floor on the conserved state decides
 // that before the solve, so such a cell gets status 5 (flagged, no bracket,
-// no solve, no recovery).  nf32 / nfb count the FP32 evaluations and the
-// cells whose polish was not taken (mode 2).
+// no solve, no recovery); with P.dec32 the FP32 search from [0, mu+] runs in
+// every mode and fofc_decide32 settles most of the other cells (status 5 or
+// 7, counted in ndec) before any FP64 evaluation of f.  nf32 / nfb count the
+// FP32 evaluations and the cells whose polish was not taken (mode 2).
 __device__ __forceinline__ unsigned char prep_cell(const Par& P, const KrpBuf& kb, long long i, const double* U,
                                           const double* Bd, const Metric& m, int mode, unsigned& nf32,
                                           unsigned& nfb, float* feat = nullptr, double alpha = 1.0,
-                                          double guess = 0.0, bool fofc = false) {
+                                          double guess = 0.0, bool fofc = false, unsigned* ndec = nullptr) {
   KrpCell k;
   unsigned fl;
   const long long n = kb.n;
   unsigned char st = 2;
   int its = 0;
+  bool solved = false;   // a bracket and root were formed (statuses 0-2 from the solver)
+  double a = 0.0, b = 1.0, Ga = -1.0, Gb = 1.0, mu = 0.0;
   if (krp_prep(P, U, Bd, m, k, fl, alpha)) {
     if (feat) krp_features(k.s, feat + i * MLP_FSTRIDE);
     if (fofc && (fl & (F_DFLOOR | F_SIGMA | F_TAU))) {
       st = 5;
-    } else if (mode == 1) {
-      st = 4;
     } else {
-      double a = 0.0, b = 1.0, Ga = -1.0, Gb = 1.0, mu = 0.0;
-      int r;
-      if (mode == 2) {
-        const KSf sf = ks_f32(k.s);
-        const float m32 = krp_secant32(sf, 0.0f, f32_mu_plus(sf), 8, nf32);
-        const float isl = krp_islope32(sf, m32, nf32);
-        bool fb;
-        r = krp_polish(k.s, P, (double)m32, (double)isl, a, b, Ga, Gb, mu, its, fb);
-        nfb += fb ? 1u : 0u;
-      } else {
-        const bool warm = guess > 0.0 && guess <= 1.0;
-        const double glo = warm ? guess * (1.0 - WARM_DELTA) : -1.0;
-        const double ghi = warm ? fmin(guess * (1.0 + WARM_DELTA), 1.0) : -1.0;
-        r = krp_bracket(k.s, P, glo, ghi, a, b, Ga, Gb, mu, its);
+      KSf sf;
+      float m32 = 0.0f;
+      bool have32 = false;
+      if (fofc && P.dec32) {
+        sf = ks_f32(k.s);
+        m32 = krp_secant32(sf, 0.0f, f32_mu_plus(sf), 8, nf32);
+        have32 = true;
+        const int d = fofc_decide32(sf, P, (float)k.D, m32, nf32);
+        if (d >= 0) {
+          if (ndec) (*ndec)++;
+          kb.st[i] = d ? 5 : 7;
+          return kb.st[i];
+        }
       }
-      st = (unsigned char)(r == 0 ? 0 : (r == 1 ? 1 : 2));
-      kb.w[KW_A * n + i] = a; kb.w[KW_B * n + i] = b;
-      kb.w[KW_GA * n + i] = Ga; kb.w[KW_GB * n + i] = Gb;
-      kb.w[KW_MU * n + i] = mu;
+      if (mode == 1) {
+        st = 4;
+      } else {
+        int r;
+        if (mode == 2) {
+          if (!have32) {
+            sf = ks_f32(k.s);
+            m32 = krp_secant32(sf, 0.0f, f32_mu_plus(sf), 8, nf32);
+          }
+          const float isl = krp_islope32(sf, m32, nf32);
+          bool fb;
+          r = krp_polish(k.s, P, (double)m32, (double)isl, a, b, Ga, Gb, mu, its, fb);
+          nfb += fb ? 1u : 0u;
+        } else {
+          const bool warm = guess > 0.0 && guess <= 1.0;
+          const double glo = warm ? guess * (1.0 - WARM_DELTA) : -1.0;
+          const double ghi = warm ? fmin(guess * (1.0 + WARM_DELTA), 1.0) : -1.0;
+          r = krp_bracket(k.s, P, glo, ghi, a, b, Ga, Gb, mu, its);
+        }
+        st = (unsigned char)(r == 0 ? 0 : (r == 1 ? 1 : 2));
+        solved = true;
+      }
     }
   } else if (feat) {
     for (int f = 0; f < MLP_FSTRIDE; f++) feat[i * MLP_FSTRIDE + f] = 0.0f;
+  }
+  if (solved) {
+    kb.w[KW_A * n + i] = a; kb.w[KW_B * n + i] = b;
+    kb.w[KW_GA * n + i] = Ga; kb.w[KW_GB * n + i] = Gb;
+    kb.w[KW_MU * n + i] = mu;
   }
   kw_store(kb, i, k);
   kb.w[KW_SDET * n + i] = m.sdet;
@@ -288,7 +312,7 @@ __global__ void __launch_bounds__(256) k_krp_prep_fofc(Work w, Par P, double g0,
     if (kb.flist) kb.flist[0] = 0ull;   // the finish lists this stage's flagged cells
   }
   const long long n = kb.n;
-  unsigned s_f32 = 0, s_fb = 0;
+  unsigned s_f32 = 0, s_fb = 0, s_dec = 0;
   bool any0 = false;
   for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < tot; it += (long long)gridDim.x * blockDim.x) {
     int bi, k, j, i;
@@ -311,15 +335,17 @@ __global__ void __launch_bounds__(256) k_krp_prep_fofc(Work w, Par P, double g0,
     Metric m;
     metric_cell(b.adm, b.mc, nc, c, m);
     const double Bd[3] = {b.bcc[c], b.bcc[nc + c], b.bcc[2 * nc + c]};
-    any0 |= prep_cell(P, kb, it, U, Bd, m, mode, s_f32, s_fb, feat, b.adm[c], b.mu ? b.mu[c] : 0.0, true) == 0;
-    kb.w[KW_USD * n + it] = U[0];
-    kb.w[KW_UST * n + it] = U[4];
+    any0 |= prep_cell(P, kb, it, U, Bd, m, mode, s_f32, s_fb, feat, b.adm[c], b.mu ? b.mu[c] : 0.0, true,
+                      &s_dec) == 0;
+    if (P.dmp_M > 0.0) {   // the DMP test of the finish reads U*
+      kb.w[KW_USD * n + it] = U[0];
+      kb.w[KW_UST * n + it] = U[4];
+    }
   }
   warp_mark_solve(kb, any0);
-  if (mode == 2) {
-    warp_flush(&stats[7], s_fb);
-    warp_flush(&stats[8], s_f32);
-  }
+  if (mode == 2) warp_flush(&stats[7], s_fb);
+  warp_flush(&stats[8], s_f32);
+  warp_flush(&stats[9], s_dec);
 }
 
 __global__ void __launch_bounds__(256) k_krp_finish_fofc(Work w, Par P, KrpBuf kb, unsigned long long* stats) {
@@ -332,10 +358,10 @@ __global__ void __launch_bounds__(256) k_krp_finish_fofc(Work w, Par P, KrpBuf k
     fofc_cell(w, it, bi, k, j, i);
     const DevBlock& b = w.blk[bi];
     const long long nc = b.ncell, c = cidx(b, k, j, i);
-    unsigned fl = kb.fl[it];
     const unsigned char st = kb.st[it];
-    bool flag = true;   // status 5: a floor on U* already flagged the cell
-    if (st != 5) {
+    bool flag = st != 7;   // 5: flagged, 7: not flagged, both without a recovery
+    if (st != 5 && st != 7) {
+      unsigned fl = kb.fl[it];
       KrpCell kc;
       kw_load(kb, P, it, kc);
       double pr[5];
@@ -380,10 +406,10 @@ __global__ void __launch_bounds__(256) k_krp_finish_fofc(Work w, Par P, KrpBuf k
 __global__ void __launch_bounds__(128) k_krp_prep_cells(Par P, KrpBuf kb, const double* __restrict__ cons,
                                                         const double* __restrict__ Bd, const double* __restrict__ g,
                                                         int mode, float* __restrict__ feat,
-                                                        unsigned long long* stats) {
+                                                        unsigned long long* stats, bool fonly) {
   const long long n = kb.n;
   if (blockIdx.x == 0 && threadIdx.x == 0) *kb.ctr = 0ull;
-  unsigned s_f32 = 0, s_fb = 0;
+  unsigned s_f32 = 0, s_fb = 0, s_dec = 0;
   bool any0 = false;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
     Metric m;
@@ -393,13 +419,12 @@ __global__ void __launch_bounds__(128) k_krp_prep_cells(Par P, KrpBuf kb, const 
     for (int v = 0; v < 5; v++) U[v] = cons[v * n + c];
 #pragma unroll
     for (int v = 0; v < 3; v++) B[v] = Bd[v * n + c];
-    any0 |= prep_cell(P, kb, c, U, B, m, mode, s_f32, s_fb, feat) == 0;
+    any0 |= prep_cell(P, kb, c, U, B, m, mode, s_f32, s_fb, feat, 1.0, 0.0, fonly, &s_dec) == 0;
   }
   warp_mark_solve(kb, any0);
-  if (mode == 2) {
-    warp_flush(&stats[7], s_fb);
-    warp_flush(&stats[8], s_f32);
-  }
+  if (mode == 2) warp_flush(&stats[7], s_fb);
+  warp_flush(&stats[8], s_f32);
+  warp_flush(&stats[9], s_dec);
 }
 
 __global__ void __launch_bounds__(128) k_krp_finish_cells(Par P, KrpBuf kb, double* __restrict__ cons,
@@ -407,14 +432,34 @@ __global__ void __launch_bounds__(128) k_krp_finish_cells(Par P, KrpBuf kb, doub
                                                           double* __restrict__ prim, unsigned char* __restrict__ flags,
                                                           int* __restrict__ iters_out, unsigned long long* stats) {
   const long long n = kb.n;
-  unsigned s_cells = 0, s_fail = 0, s_floor = 0, s_it = 0;
+  unsigned s_cells = 0, s_fail = 0, s_floor = 0, s_it = 0, s_flag = 0;
   if (blockIdx.x == 0 && threadIdx.x == 0) kb.ctr[1] = 0ull;   // the solve has run
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    const unsigned char st = kb.st[c];
+    if (!prim) {   // flags only: 1 where con2prim fails or a floor fires
+      bool flag = st != 7;
+      int its = 0;
+      if (st != 5 && st != 7) {
+        KrpCell kc;
+        kw_load(kb, P, c, kc);
+        unsigned fl = kb.fl[c];
+        double pr[5];
+        krp_finish(P, kc, kb.w[KW_MU * n + c], st == 1, fl, pr);
+        flag = (fl & (FLOOR_BITS | F_FAIL)) != 0;
+        its = kb.it[c];
+      }
+      flags[c] = flag ? 1 : 0;
+      if (iters_out) iters_out[c] = its;
+      s_cells++;
+      s_it += (unsigned)its;
+      s_flag += flag ? 1u : 0u;
+      continue;
+    }
     KrpCell kc;
     kw_load(kb, P, c, kc);
     unsigned fl = kb.fl[c];
     double pr[5];
-    krp_finish(P, kc, kb.w[KW_MU * n + c], kb.st[c] == 1, fl, pr);
+    krp_finish(P, kc, kb.w[KW_MU * n + c], st == 1, fl, pr);
 #pragma unroll
     for (int v = 0; v < 5; v++) prim[v * n + c] = pr[v];
     if (fl & (FLOOR_BITS | F_FAIL)) {
@@ -440,6 +485,7 @@ __global__ void __launch_bounds__(128) k_krp_finish_cells(Par P, KrpBuf kb, doub
   warp_flush(&stats[1], s_it);
   warp_flush(&stats[2], s_fail);
   warp_flush(&stats[3], s_floor);
+  warp_flush(&stats[4], s_flag);
 }
 
 // ------------------------------------------------------------------ launchers
@@ -485,8 +531,8 @@ void launch_krp_finish_fofc(const Work& w, const Par& P, const KrpBuf& kb, unsig
   k_krp_finish_fofc<<<grid, threads, 0, s>>>(w, P, kb, stats);
 }
 void launch_krp_prep_cells(const Par& P, const KrpBuf& kb, const double* cons, const double* Bd, const double* g,
-                           int mode, float* feat, unsigned long long* stats, cudaStream_t s, int grid) {
-  k_krp_prep_cells<<<grid, 128, 0, s>>>(P, kb, cons, Bd, g, mode, feat, stats);
+                           int mode, float* feat, unsigned long long* stats, cudaStream_t s, int grid, bool fonly) {
+  k_krp_prep_cells<<<grid, 128, 0, s>>>(P, kb, cons, Bd, g, mode, feat, stats, fonly);
 }
 void launch_krp_finish_cells(const Par& P, const KrpBuf& kb, double* cons, const double* Bd, const double* g,
                              double* prim, unsigned char* flags, int* iters, unsigned long long* stats, cudaStream_t s,

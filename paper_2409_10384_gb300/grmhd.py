@@ -47,7 +47,8 @@ class mhd_block(C.Structure):
 class mhd_stats(C.Structure):
     _fields_ = [("cells", C.c_longlong), ("iters", C.c_longlong), ("fails", C.c_longlong),
                 ("floors", C.c_longlong), ("fofc_cells", C.c_longlong), ("dmp_cells", C.c_longlong),
-                ("fofc_faces", C.c_longlong), ("guess_fallbacks", C.c_longlong), ("fp32_evals", C.c_longlong)]
+                ("fofc_faces", C.c_longlong), ("guess_fallbacks", C.c_longlong), ("fp32_evals", C.c_longlong),
+                ("fofc_fp32", C.c_longlong)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -295,7 +296,8 @@ class Context:
 
     def c2p_cells(self, cons, Bd, g, prim, flags, iters=None, stream=None, stats=False):
         """con2prim of independent cells; with stats=True returns the counters
-        this call added (the call then synchronises the stream)."""
+        this call added (the call then synchronises the stream).  prim=None:
+        flags only (1 where con2prim fails or a floor fires; cons untouched)."""
         n = cons.shape[1]
         st = mhd_stats() if stats else None
         check(self.L.mhd_c2p_cells(self.h, n, _ptr(cons), _ptr(Bd), _ptr(g), _ptr(prim), _ptr(flags),
