@@ -256,6 +256,16 @@ int mhd_get_launch(const mhd_ctx* ctx, int kind, int* threads, int* waves);
  * 1 * r(x) and (x + 1) * r(x) from the correctly rounded 1/x and (x + 1)/x. */
 int mhd_check_rcp(const double* x, long n, double* rel_out, void* stream);
 
+/* Self-check of the FP32 enclosures (interval arithmetic with outward
+ * rounding) from which the FOFC estimate decides its flags (Sec. 3.3; the
+ * paper has no counterpart).  For n device values x, miss_out[i] (device)
+ * receives 0 when every enclosure of x and of y = x[(i + 1) % n] contains the
+ * FP64 value it encloses: x itself, 1/|x|, 1/sqrt(|x|), x y, x |y|, x^2,
+ * x + y and x - y; else a bit per miss (1, 2, 4, 8, 16, 32, 64 in that
+ * order).  Values whose FP32 image is not a normal float check x only, and an
+ * empty (NaN) enclosure, which decides nothing, counts as enclosing. */
+int mhd_check_enclosures(const double* x, long n, unsigned char* miss_out, void* stream);
+
 /* Copy the counters to *out (synchronises the stream) / zero them. */
 int mhd_read_stats(mhd_ctx* ctx, mhd_stats* out, void* stream);
 int mhd_reset_stats(mhd_ctx* ctx, void* stream);

@@ -18,7 +18,7 @@ struct mhd_ctx {
   Par P;
   int dev = 0, nsm = 1;
   int occ_c2p[2] = {1, 1}, occ_face[5] = {1, 1, 1, 1, 1}, occ_upd[3] = {1, 1, 1};
-  int occ_krp[7] = {1, 1, 1, 1, 1, 1, 1};
+  int occ_krp[8] = {1, 1, 1, 1, 1, 1, 1, 1};   // [7]: the flags-only cell prep
   int occ_seed = 1;   // the learned seed kernel
   int occ_metric = 1;         // metric cache kernel
   // side streams and events of the forked flux sweeps (y, z)
@@ -174,7 +174,6 @@ int fill_par(const mhd_params* p, Par& P, bool allow_guess) {
              (!P.thr_pos || (P.rho_thr >= 1e-30 && P.rho_thr <= 1e30)))
                 ? 1
                 : 0;
-  P.rho_thr32 = (float)P.rho_thr;
   P.recon = p->recon;
   P.rsolver = p->rsolver;
   P.fofc = p->fofc ? 1 : 0;
@@ -962,8 +961,8 @@ int c2p_cells_enqueue(mhd_ctx* c, long n, double* cons, const double* Bd, const 
   int r = cells_scratch(c, n, s, &kb, &feat, &logmu);
   if (r) return r;
   timed(c, MHD_K_C2P, s, [&] {
-    launch_krp_prep_cells(c->P, kb, cons, Bd, g, mode, nullptr, c->dstats, s, cells_grid(c, n, c->occ_krp[5]),
-                          prim == nullptr);
+    launch_krp_prep_cells(c->P, kb, cons, Bd, g, mode, nullptr, c->dstats, s,
+                          cells_grid(c, n, c->occ_krp[prim ? 5 : 7]), prim == nullptr);
   });
   c2p_seed(c, kb, n, s);
   timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, s, c->solve_grid(n)); });
@@ -1282,6 +1281,17 @@ int mhd_check_rcp(const double* x, long n, double* rel_out, void* stream) {
     return MHD_ECUDA;
   if (cudaPeekAtLastError() != cudaSuccess) return MHD_ECUDA;
   launch_check_rcp(x, n, rel_out, (cudaStream_t)stream, nsm);
+  return cuda_ok(cudaPeekAtLastError());
+}
+
+int mhd_check_enclosures(const double* x, long n, unsigned char* miss_out, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !miss_out))) return MHD_EINVAL;
+  if (n == 0) return MHD_OK;
+  int dev = 0, nsm = 1;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return MHD_ECUDA;
+  if (cudaPeekAtLastError() != cudaSuccess) return MHD_ECUDA;
+  launch_check_iv(x, n, miss_out, (cudaStream_t)stream, nsm);
   return cuda_ok(cudaPeekAtLastError());
 }
 

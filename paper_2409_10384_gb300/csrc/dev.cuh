@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ival.cuh"
+
 namespace grmhd {
 
 enum : unsigned {
@@ -34,10 +36,9 @@ struct Par {
   int recon, rsolver, fofc, rk_order, maxit, guess, eos, npc;
   int exc_on, sigma_on;         // alpha_exc > 0, sigma_max > 0
   int thr_pos;                  // rho_thr > 0
-  int dec32;                    // the FOFC flags may come from FP32 values (fofc_decide32):
-                                // ideal gas, eps_atm and rho_thr (when > 0) within
-                                // [1e-30, 1e30]
-  float rho_thr32;              // rho_thr in FP32
+  int dec32;                    // the FOFC flags may come from FP32 enclosures
+                                // (fofc_decide_iv): ideal gas, eps_atm and rho_thr
+                                // (when > 0) within [1e-30, 1e30]
 };
 
 // One meshblock as seen by the kernels: caller arrays plus context scratch.
@@ -211,7 +212,7 @@ enum {
 // solve status: 0 solve needed, 1 root known, 2 no bracket / bad input,
 // 3 iteration cap, 4 bracket to be built from the learned guess, 5 FOFC
 // estimate flagged without a recovery (a floor on U* before the solve, or the
-// FP32 decision, fofc_decide32), 7 FOFC estimate not flagged by the FP32
+// FP32 decision, fofc_decide_iv), 7 FOFC estimate not flagged by the FP32
 // decision (no solve, no recovery)
 
 // Learned-guess network 5 -> 64 -> 64 -> 1: fp32 parameter offsets, bf16
@@ -912,83 +913,160 @@ __device__ __forceinline__ int krp_polish(const KS& s, const Par& P, double m0, 
   return 0;
 }
 
-// ------------------------------------------- FOFC flags from FP32 values
+// ------------------------------------------- FOFC flags from FP32 enclosures
 // The FOFC estimate asks of con2prim(U*) only whether it fails or a floor on
-// the primitives fires (Sec. 3.3).  Away from every threshold the FP32 search
-// answers that.  f is evaluated in FP32 at lo, hi = m (1 -+ h) around the
-// FP32 root m, h eight times the error bound of f at m relative to m (within
-// [2^-20, 2^-10]).  When f(lo) < -e and f(hi) > e, with e a bound on the FP32
-// error of f, the root of the FP64 f lies in [lo, hi] (f has one root).  The
-// recovery takes the velocity cap where v^2 > vmax^2, the density floor where
-// rho = D/W < rho_thr, and the T floor where eps_raw < eps_atm (with the ideal
-// gas p < rho T_atm is eps < T_atm/(Gamma-1) = eps_atm).  When each of v^2,
-// rho and eps_raw lies on one side of its threshold at both ends, by more
-// than its change across [lo, hi] plus its FP32 error bound, the recovery at
-// the root takes the same decision.  The error bounds are 2^-18 (64 units of
-// FP32 rounding) of the sum of the magnitudes that form each value, times W^2
-// where 1 - v^2 is rounded.
-struct F32Rec {
-  float f, v2, W, eps_raw;
-  float S;    // the magnitude of eps_raw's terms (its error bound is 2^-18 S W^2)
-  float ef;   // the bound on the FP32 error of f: 2^-18 W^2 (mu + W/Z (1 + Gamma S)), Z >= 1
+// the conserved state or the primitives fires (Sec. 3.3).  Away from every
+// threshold FP32 interval arithmetic (ival.cuh) answers that: every quantity
+// is an enclosure of its exact value for every state in the enclosure of the
+// inputs, so a threshold test that holds for a whole enclosure holds for the
+// exact value, and with a gap of at least one FP32 unit it holds for the FP64
+// path's value too (FP64 rounding is 2^-29 of that).
+
+// KRP variables per unit D (krp_prep) as enclosures, and D.
+struct KSI {
+  Iv qh, r2, b2, rb2, rp2, D;
 };
-__device__ __forceinline__ void f32_rec(const KSf& s, float mu, F32Rec& e) {
-  const float x = 1.0f / fmaf(mu, s.b2, 1.0f);
-  const float mux = mu * x;
-  const float rbar2 = x * fmaf(s.r2, x, mu * (1.0f + x) * s.rb2);
-  const float qp = 0.5f * mux * mux * s.rp2;
-  const float v2 = mu * mu * rbar2;
-  const float vh2 = fminf(v2, s.vmax2);
-  const float W = rsqrtf(1.0f - vh2);
-  const float wm1 = vh2 * W * W / (1.0f + W);
-  const float murb = mu * rbar2;
-  const float eps_raw = fmaf(W, (s.qh - qp) - murb, wm1);
-  const float Z = fmaf(murb, W, fmaf(s.gam, fmaxf(eps_raw, s.emin), 1.0f));   // >= 1
-  const float WZ = W / Z;
-  const float W2 = W * W;
-  e.f = mu - WZ;
+
+// The floors on the conserved state (excision, D, magnetisation, tau) and the
+// KRP variables of krp_prep, from an enclosure U of the densitised conserved
+// state.  Returns 1 when a floor on the conserved state fires for the whole
+// enclosure (the FOFC estimate flags the cell), 0 when none fires (k holds the
+// KRP variables), -1 when an enclosure straddles a threshold.
+__device__ __forceinline__ int krp_prep_iv(const Par& P, const Iv* U, const double* Bd, const Metric& m, double alpha,
+                                           KSI& k) {
+  if (P.exc_on && alpha < P.alpha_exc) return 1;
+  const Iv isd = iv_d(m.isdet);
+  const Iv D = imul(U[0], isd), tau = imul(U[4], isd);
+  Iv Sl[3], B[3], Bl[3], g[6], gi[6];
+#pragma unroll
+  for (int v = 0; v < 3; v++) {
+    Sl[v] = imul(U[1 + v], isd);
+    B[v] = imul(iv_d(Bd[v]), isd);
+  }
+#pragma unroll
+  for (int v = 0; v < 6; v++) {
+    g[v] = iv_d(m.g[v]);
+    gi[v] = iv_d(m.gi[v]);
+  }
+  ilower3(g, B, Bl);
+  const Iv B2 = imax(idot3(B, Bl), iv_pt(0.0f));   // B^2 >= 0 (gamma positive definite)
+  if (P.thr_pos) {
+    const Iv t = iv_d(P.rho_thr);
+    if (ilt(D, t)) return 1;
+    if (!igt(D, t)) return -1;
+  } else {
+    if (D.hi < 0.0f) return 1;
+    if (!(D.lo > 0.0f)) return -1;
+  }
+  if (P.sigma_on) {
+    const Iv sD = imul(iv_d(P.sigma_max), D);
+    if (igt(B2, sD)) return 1;
+    if (!ilt(B2, sD)) return -1;
+  }
+  const Iv ta = iadd(imul(D, iv_d(P.eps_atm)), iscale(B2, 0.5f));
+  if (ilt(tau, ta)) return 1;
+  if (!igt(tau, ta)) return -1;
+  const Iv iD = idiv(iv_pt(1.0f), D), isD = irsqrt(D);
+  Iv rl[3], ru[3], bu[3];
+#pragma unroll
+  for (int v = 0; v < 3; v++) {
+    rl[v] = imul(Sl[v], iD);
+    bu[v] = imul(B[v], isD);
+  }
+  ilower3(gi, rl, ru);
+  k.b2 = imul(B2, iD);
+  k.r2 = imax(idot3(rl, ru), iv_pt(0.0f));   // r^2 >= 0
+  k.rb2 = isq(idot3(rl, bu));
+  k.rp2 = imax(isub(imul(k.r2, k.b2), k.rb2), iv_pt(0.0f));   // r_perp^2 = max(r^2 b^2 - (r.b)^2, 0)
+  k.qh = isub(imul(tau, iD), iscale(k.b2, 0.5f));
+  k.D = D;
+  return 0;
+}
+
+// The KRP variables of an FP64 krp_prep as enclosures (each exact value in its
+// FP32 interval).
+__device__ __forceinline__ void ksi_of(const KS& s, double D, KSI& k) {
+  k.qh = iv_d(s.qh); k.r2 = iv_d(s.r2); k.b2 = iv_d(s.b2); k.rb2 = iv_d(s.rb2); k.rp2 = iv_d(s.rperp2);
+  k.D = iv_d(D);
+}
+
+// Enclosures of f (the ideal-gas master function), v^2 (without the cap), W
+// and eps_raw at mu (an enclosure itself), for every state in k.
+struct RecIv {
+  Iv f, v2, W, eps_raw;
+};
+__device__ __forceinline__ void rec_iv(const KSI& k, Iv gam, Iv emin, Iv vmax2, Iv mu, RecIv& e) {
+  const Iv one = iv_pt(1.0f);
+  const Iv x = idiv(one, iadd(imul(mu, k.b2), one));
+  const Iv mux = imul(mu, x);
+  const Iv rbar2 = imul(x, iadd(imul(k.r2, x), imul(imul(mu, iadd(one, x)), k.rb2)));
+  const Iv qp = iscale(imul(isq(mux), k.rp2), 0.5f);
+  const Iv murb = imul(mu, rbar2);
+  const Iv v2 = imul(mu, murb);
+  const Iv vh2 = imin(v2, vmax2);
+  const Iv W = irsqrt(isub(one, vh2));
+  const Iv wm1 = idiv(imul(vh2, isq(W)), iadd(one, W));   // W - 1
+  const Iv eps_raw = iadd(imul(W, isub(isub(k.qh, qp), murb)), wm1);
+  const Iv Z = iadd(imul(murb, W), iadd(imul(gam, imax(eps_raw, emin)), one));
+  e.f = isub(mu, idiv(W, Z));
   e.v2 = v2;
   e.W = W;
   e.eps_raw = eps_raw;
-  e.S = fmaf(W, fabsf(s.qh) + qp + murb, wm1);
-  e.ef = 3.81469727e-6f * fmaf(WZ, fmaf(s.gam, e.S, 1.0f), mu) * W2;
 }
-// 1: flagged for sure, 0: not flagged for sure, -1: undecided (the FP64
-// polish or solve and the recovery decide).  m: the FP32 root; D: D in FP32.
-// nf counts the FP32 evaluations of f.
-__device__ __forceinline__ int fofc_decide32(const KSf& s, const Par& P, float D, float m, unsigned& nf) {
-  if (!(m > 1e-30f && m <= 1.0f) || !(D >= 1e-30f && D <= 1e30f)) return -1;
-  const float u = 3.81469727e-6f;   // 2^-18
-  // the half-width: 8 error bounds of f at m (f' is about 1), within [2^-20, 2^-10]
-  F32Rec a, b;
-  f32_rec(s, m, a);
-  const float h = fminf(fmaxf(8.0f * a.ef / m, 9.53674316e-7f), 9.765625e-4f);
-  const float lo = m * (1.0f - h), hi = fminf(m * (1.0f + h), 1.0f);
-  f32_rec(s, lo, a);
-  f32_rec(s, hi, b);
-  nf += 3;
-  // at hi = 1 no sign test is needed: f(1) >= 0 for every eps >= eps_min > 0
-  // (Z >= 1 + vh^2 W + Gamma eps >= W, as W - 1 = vh^2 W^2/(1 + W) <= vh^2 W),
-  // which is where cold cells (root 1 - Gamma eps + ...) put their root
-  if (!(a.f < -a.ef && (hi >= 1.0f || b.f > b.ef))) return -1;
-  const float W2 = fmaxf(a.W * a.W, b.W * b.W);
-  // velocity cap
-  const float dv = fabsf(b.v2 - a.v2) + u * s.vmax2;
-  if (a.v2 > s.vmax2 + dv && b.v2 > s.vmax2 + dv) return 1;
-  if (!(a.v2 < s.vmax2 - dv && b.v2 < s.vmax2 - dv)) return -1;
-  // density floor (with rho_thr = 0 the floor takes rho < 0, and D > 0 here)
-  bool low_rho = false;
-  if (P.thr_pos) {
-    const float ra = D / a.W, rb = D / b.W, t = P.rho_thr32;
-    const float dr = fabsf(rb - ra) + u * (t + fmaxf(ra, rb) * W2);
-    if (ra < t - dr && rb < t - dr) low_rho = true;
-    else if (!(ra > t + dr && rb > t + dr)) return -1;
+
+// The FOFC question for KRP enclosures k (ideal gas): 1 flagged for sure, 0 not
+// flagged for sure, -1 undecided (the FP64 path decides).  The FP32 secant
+// search from [0, mu+] on the enclosures' midpoints gives m; lo, hi = m (1 -+ h)
+// certify the root when the enclosure of f is below 0 at lo and above 0 at hi
+// (h = 2^-18, 2^-14, 2^-10 in turn).  At hi = 1 no test is needed: f(1) >= 0 for
+// every eps >= eps_min > 0 (Z >= 1 + vh^2 W + Gamma eps >= W, as W - 1 = vh^2
+// W^2/(1 + W) <= vh^2 W); cold cells, whose root is 1 - Gamma eps + ..., need
+// this.  Then v^2, rho = D/W and eps_raw are enclosed over mu in [lo, hi] and
+// compared with the velocity cap, the density floor and the T floor (with the
+// ideal gas p < rho T_atm is eps < T_atm/(Gamma - 1) = eps_atm).  nf counts the
+// FP32 evaluations of f.
+__device__ __forceinline__ int fofc_decide_iv(const KSI& k, const Par& P, unsigned& nf) {
+  const Iv gam = iv_d(P.gam), emin = iv_d(P.eps_atm), vmax2 = iv_d(P.vmax2);
+  KSf sf;
+  sf.qh = 0.5f * (k.qh.lo + k.qh.hi);
+  sf.r2 = 0.5f * (k.r2.lo + k.r2.hi);
+  sf.b2 = 0.5f * (k.b2.lo + k.b2.hi);
+  sf.rb2 = 0.5f * (k.rb2.lo + k.rb2.hi);
+  sf.rp2 = 0.5f * (k.rp2.lo + k.rp2.hi);
+  sf.gam = gam.lo;
+  sf.emin = fmaxf(emin.lo, 1e-37f);
+  sf.vmax2 = vmax2.lo;
+  const float m = krp_secant32(sf, 0.0f, f32_mu_plus(sf), 8, nf);
+  if (!(m > 1e-30f && m <= 1.0f)) return -1;
+  float lo = 0.0f, hi = 0.0f, h = 3.81469727e-6f;   // 2^-18
+  bool ok = false;
+  for (int t = 0; t < 3 && !ok; t++, h *= 16.0f) {
+    lo = m * (1.0f - h);
+    hi = fminf(m * (1.0f + h), 1.0f);
+    RecIv a;
+    rec_iv(k, gam, emin, vmax2, iv_pt(lo), a);
+    nf++;
+    ok = a.f.hi < 0.0f;
+    if (ok && hi < 1.0f) {
+      RecIv b;
+      rec_iv(k, gam, emin, vmax2, iv_pt(hi), b);
+      nf++;
+      ok = b.f.lo > 0.0f;
+    }
   }
-  // T floor
-  const float t = s.emin;
-  const float de = fabsf(b.eps_raw - a.eps_raw) + u * fmaf(fmaxf(a.S, b.S), W2, t);
-  if (a.eps_raw < t - de && b.eps_raw < t - de) return 1;
-  if (!(a.eps_raw > t + de && b.eps_raw > t + de)) return low_rho ? 1 : -1;
+  if (!ok) return -1;
+  RecIv q;
+  rec_iv(k, gam, emin, vmax2, Iv{lo, hi}, q);
+  if (igt(q.v2, vmax2)) return 1;     // the velocity cap
+  if (!ilt(q.v2, vmax2)) return -1;
+  bool low_rho = false;               // the density floor (rho_thr = 0: rho = D/W > 0 never floors)
+  if (P.thr_pos) {
+    const Iv rho = idiv(k.D, q.W), t = iv_d(P.rho_thr);
+    if (ilt(rho, t)) low_rho = true;
+    else if (!igt(rho, t)) return -1;
+  }
+  if (ilt(q.eps_raw, emin)) return 1;   // the T floor
+  if (!igt(q.eps_raw, emin)) return low_rho ? 1 : -1;
   return low_rho ? 1 : 0;
 }
 

@@ -25,6 +25,7 @@ void launch_metric_cache(const Work& w, cudaStream_t s, int grid);
 int occ_metric_kernel();
 // the fast reciprocal (rcp_nr) against the correctly rounded division
 void launch_check_rcp(const double* x, long long n, double* out, cudaStream_t s, int nsm);
+void launch_check_iv(const double* x, long long n, unsigned char* out, cudaStream_t s, int nsm);
 void launch_fofc_flag(const Work& w, const Par& P, double g0, double g1, double bdt, unsigned long long* stats,
                       cudaStream_t s, int grid);
 void launch_fofc_fix(int d, const Work& w, const Par& P, unsigned long long* stats, cudaStream_t s, int grid);
@@ -65,6 +66,8 @@ void launch_krp_prep_cells(const Par& P, const KrpBuf& kb, const double* cons, c
 void launch_krp_finish_cells(const Par& P, const KrpBuf& kb, double* cons, const double* Bd, const double* g,
                              double* prim, unsigned char* flags, int* iters, unsigned long long* stats, cudaStream_t s,
                              int grid);
+// per_sm[8]: prep / solve / finish of the block, prep / finish of the FOFC
+// estimate, prep / finish of independent cells, the flags-only cell prep
 int occupancy_krp(int* per_sm);
 int mlp_setup_attrs();
 void launch_mlp_infer(const float* feat, long long n, const MlpNorm& nm, const __nv_bfloat16* wb, const float* w,

@@ -199,6 +199,42 @@ void launch_check_rcp(const double* x, long long n, double* out, cudaStream_t s,
   k_check_rcp<<<grid < 1 ? 1 : grid, 256, 0, s>>>(x, n, out);
 }
 
+// The FP32 enclosures of the FOFC decision (ival.cuh) against FP64 values:
+// out[i] has bit 0 set when iv_d(x) misses x, bit 1 when ircp misses 1/|x|,
+// bit 2 when irsqrt misses 1/sqrt(|x|), bit 3 when imul misses x y, bit 4
+// when imulp misses x |y|, bit 5 when isq misses x^2, bit 6 when iadd / isub
+// miss x + y / x - y (y = x[(i + 1) % n]).  Values whose FP32 image is not a
+// normal float only check iv_d.  A NaN interval (what iv_d gives outside the
+// FP32 range) claims nothing and decides nothing, so it counts as enclosing.
+__global__ void k_check_iv(const double* __restrict__ x, long long n, unsigned char* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = x[i], u = x[(i + 1) % n];
+    const Iv a = iv_d(v), b = iv_d(u);
+    auto in = [](Iv r, double t) { return r.lo != r.lo || r.hi != r.hi || ((double)r.lo <= t && t <= (double)r.hi); };
+    unsigned char f = 0;
+    if (!in(a, v)) f |= 1;
+    const double av = fabs(v), au = fabs(u);
+    const bool nv = av >= 1.2e-38 && av < 3.0e38, nu = au >= 1.2e-38 && au < 3.0e38;
+    if (nv) {
+      const Iv aa = iv_d(av);
+      if (!in(ircp(aa), 1.0 / av)) f |= 2;
+      if (!in(irsqrt(aa), 1.0 / sqrt(av))) f |= 4;
+      if (!in(isq(a), v * v)) f |= 32;
+      if (nu) {
+        if (!in(imul(a, b), v * u)) f |= 8;
+        if (!in(imulp(a, iv_d(au)), v * au)) f |= 16;
+        if (!in(iadd(a, b), v + u) || !in(isub(a, b), v - u)) f |= 64;
+      }
+    }
+    out[i] = f;
+  }
+}
+void launch_check_iv(const double* x, long long n, unsigned char* out, cudaStream_t s, int nsm) {
+  long long nb = (n + 255) / 256;
+  int grid = (int)(nb < (long long)nsm * 8 ? nb : (long long)nsm * 8);
+  k_check_iv<<<grid < 1 ? 1 : grid, 256, 0, s>>>(x, n, out);
+}
+
 // ------------------------------------------------------------------ launchers
 void launch_init_block(const DevBlock& b, const Par& P, const double* const A[3], cudaStream_t s, int nsm) {
   k_init_faces<<<nsm * 8, 256, 0, s>>>(b, A[0], A[1], A[2]);

@@ -42,9 +42,9 @@ __device__ __forceinline__ void kw_load(const KrpBuf& kb, const Par& P, long lon
 // fofc: the FOFC estimate, which only needs to know whether con2prim of U*
 // fails or a floor fires (Sec. 3.3).  A floor on the conserved state decides
 // that before the solve, so such a cell gets status 5 (flagged, no bracket,
-// no solve, no recovery); with P.dec32 the FP32 search from [0, mu+] runs in
-// every mode and fofc_decide32 settles most of the other cells (status 5 or
-// 7, counted in ndec) before any FP64 evaluation of f.  nf32 / nfb count the
+// no solve, no recovery); with P.dec32 fofc_decide_iv settles most of the
+// other cells from enclosures of its FP64 KRP variables (status 5 or 7,
+// counted in ndec) before any FP64 evaluation of f.  nf32 / nfb count the
 // FP32 evaluations and the cells whose polish was not taken (mode 2).
 __device__ __forceinline__ unsigned char prep_cell(const Par& P, const KrpBuf& kb, long long i, const double* U,
                                           const double* Bd, const Metric& m, int mode, unsigned& nf32,
@@ -62,14 +62,10 @@ __device__ __forceinline__ unsigned char prep_cell(const Par& P, const KrpBuf& k
     if (fofc && (fl & (F_DFLOOR | F_SIGMA | F_TAU))) {
       st = 5;
     } else {
-      KSf sf;
-      float m32 = 0.0f;
-      bool have32 = false;
       if (fofc && P.dec32) {
-        sf = ks_f32(k.s);
-        m32 = krp_secant32(sf, 0.0f, f32_mu_plus(sf), 8, nf32);
-        have32 = true;
-        const int d = fofc_decide32(sf, P, (float)k.D, m32, nf32);
+        KSI ki;
+        ksi_of(k.s, k.D, ki);
+        const int d = fofc_decide_iv(ki, P, nf32);
         if (d >= 0) {
           if (ndec) (*ndec)++;
           kb.st[i] = d ? 5 : 7;
@@ -81,10 +77,8 @@ __device__ __forceinline__ unsigned char prep_cell(const Par& P, const KrpBuf& k
       } else {
         int r;
         if (mode == 2) {
-          if (!have32) {
-            sf = ks_f32(k.s);
-            m32 = krp_secant32(sf, 0.0f, f32_mu_plus(sf), 8, nf32);
-          }
+          const KSf sf = ks_f32(k.s);
+          const float m32 = krp_secant32(sf, 0.0f, f32_mu_plus(sf), 8, nf32);
           const float isl = krp_islope32(sf, m32, nf32);
           bool fb;
           r = krp_polish(k.s, P, (double)m32, (double)isl, a, b, Ga, Gb, mu, its, fb);
@@ -304,6 +298,11 @@ __global__ void __launch_bounds__(256) k_krp_finish_block(Work w, Par P, KrpBuf 
 
 // ------------------------------------------------------------------ FOFC U*
 
+// The FOFC estimate's prep: U* = g1 U + g0 U^n - bdt div F in FP64, then
+// prep_cell (fofc), which decides most cells from FP32 enclosures of their KRP
+// variables.  U* and the KRP variables stay FP64: computing them as enclosures
+// too (one FP32 interval kernel, no FP64) was measured slower, 0.25 against
+// 0.20 ms at 96^3, latency-bound on the ~56 scattered loads per cell.
 __global__ void __launch_bounds__(256) k_krp_prep_fofc(Work w, Par P, double g0, double g1, double bdt, KrpBuf kb,
                                                         int mode, float* feat, unsigned long long* stats) {
   const long long tot = w.pre[(long long)W_CELL * (w.nblocks + 1) + w.nblocks];
@@ -403,10 +402,13 @@ __global__ void __launch_bounds__(256) k_krp_finish_fofc(Work w, Par P, KrpBuf k
 }
 
 // ------------------------------------------------------- independent cells
+// fonly: flags only (the FOFC estimate's question), a template parameter so
+// that the full con2prim keeps its registers
+template <bool fonly>
 __global__ void __launch_bounds__(128) k_krp_prep_cells(Par P, KrpBuf kb, const double* __restrict__ cons,
                                                         const double* __restrict__ Bd, const double* __restrict__ g,
                                                         int mode, float* __restrict__ feat,
-                                                        unsigned long long* stats, bool fonly) {
+                                                        unsigned long long* stats) {
   const long long n = kb.n;
   if (blockIdx.x == 0 && threadIdx.x == 0) *kb.ctr = 0ull;
   unsigned s_f32 = 0, s_fb = 0, s_dec = 0;
@@ -419,6 +421,19 @@ __global__ void __launch_bounds__(128) k_krp_prep_cells(Par P, KrpBuf kb, const 
     for (int v = 0; v < 5; v++) U[v] = cons[v * n + c];
 #pragma unroll
     for (int v = 0; v < 3; v++) B[v] = Bd[v * n + c];
+    if (fonly && P.dec32) {   // the question in FP32 enclosures of U first
+      Iv Ui[5];
+#pragma unroll
+      for (int v = 0; v < 5; v++) Ui[v] = iv_d(U[v]);
+      KSI ki;
+      int d = krp_prep_iv(P, Ui, B, m, 1.0, ki);
+      if (d == 0) d = fofc_decide_iv(ki, P, s_f32);
+      if (d >= 0) {
+        kb.st[c] = d ? 5 : 7;
+        s_dec++;
+        continue;
+      }
+    }
     any0 |= prep_cell(P, kb, c, U, B, m, mode, s_f32, s_fb, feat, 1.0, 0.0, fonly, &s_dec) == 0;
   }
   warp_mark_solve(kb, any0);
@@ -532,7 +547,8 @@ void launch_krp_finish_fofc(const Work& w, const Par& P, const KrpBuf& kb, unsig
 }
 void launch_krp_prep_cells(const Par& P, const KrpBuf& kb, const double* cons, const double* Bd, const double* g,
                            int mode, float* feat, unsigned long long* stats, cudaStream_t s, int grid, bool fonly) {
-  k_krp_prep_cells<<<grid, 128, 0, s>>>(P, kb, cons, Bd, g, mode, feat, stats, fonly);
+  if (fonly) k_krp_prep_cells<true><<<grid, 128, 0, s>>>(P, kb, cons, Bd, g, mode, feat, stats);
+  else k_krp_prep_cells<false><<<grid, 128, 0, s>>>(P, kb, cons, Bd, g, mode, feat, stats);
 }
 void launch_krp_finish_cells(const Par& P, const KrpBuf& kb, double* cons, const double* Bd, const double* g,
                              double* prim, unsigned char* flags, int* iters, unsigned long long* stats, cudaStream_t s,
@@ -554,8 +570,9 @@ int occupancy_krp(int* per_sm) {
   e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[2], k_krp_finish_block, 128, 0));
   e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[3], k_krp_prep_fofc, 128, 0));
   e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[4], k_krp_finish_fofc, 128, 0));
-  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[5], k_krp_prep_cells, 128, 0));
+  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[5], k_krp_prep_cells<false>, 128, 0));
   e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[6], k_krp_finish_cells, 128, 0));
+  e = (cudaError_t)(e | cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[7], k_krp_prep_cells<true>, 128, 0));
   return e == cudaSuccess ? 0 : -1;
 }
 

@@ -99,6 +99,7 @@ _SIGS = {
     "mhd_mlp_save": (_I, [_VP, _VP, _L, C.POINTER(_L)]),
     "mhd_mlp_load": (_I, [_VP, _VP, _L]),
     "mhd_check_rcp": (_I, [_VP, _L, _VP, _VP]),
+    "mhd_check_enclosures": (_I, [_VP, _L, _VP, _VP]),
 }
 MHD_NKERNEL = 13
 MLP_NPARAM = 4609
@@ -228,6 +229,15 @@ def check_rcp(x, stream=None):
     import torch
     out = torch.empty((x.shape[0], 2), dtype=torch.float64, device="cuda")
     check(lib().mhd_check_rcp(_ptr(x), x.shape[0], _ptr(out), _sptr(stream)), "mhd_check_rcp")
+    return out
+
+
+def check_enclosures(x, stream=None):
+    """mhd_check_enclosures: per value, the bits of the FP32 enclosures that
+    miss their FP64 value (0: all enclose), [n] uint8."""
+    import torch
+    out = torch.empty((x.shape[0],), dtype=torch.uint8, device="cuda")
+    check(lib().mhd_check_enclosures(_ptr(x), x.shape[0], _ptr(out), _sptr(stream)), "mhd_check_enclosures")
     return out
 
 

@@ -157,3 +157,23 @@ def test_flags_only_equal_full_recovery_near_thresholds(G, which):
         return
     assert decided[0] > 0.2            # far from the threshold a share is decided
     assert decided[-1] < decided[0]    # near it they go to the FP64 recovery
+
+
+def test_enclosures_contain_their_values(G):
+    """The FP32 interval operations of the decision (ival.cuh): the interval
+    of a double, the widened hardware reciprocal and reciprocal square root,
+    products, squares, sums and differences contain the FP64 value they
+    enclose, over log-uniform values of both signs across the FP32 range,
+    powers of two and their neighbours, and values outside the FP32 range
+    (whose enclosure is empty and decides nothing)."""
+    import torch
+    rng = np.random.default_rng(31)
+    n = 1 << 20
+    x = np.concatenate([10.0 ** rng.uniform(-37.5, 37.5, n) * rng.choice([-1.0, 1.0], n),
+                        2.0 ** np.arange(-125, 127, dtype=np.float64),
+                        np.nextafter(2.0 ** np.arange(-125, 127, dtype=np.float64), 0.0),
+                        np.nextafter(2.0 ** np.arange(-125, 127, dtype=np.float64), np.inf),
+                        np.array([0.0, -0.0, 1e-300, -1e-300, 1e300, 1.0 + 2.0 ** -30, 1.0 - 2.0 ** -30])])
+    miss = G.check_enclosures(torch.from_numpy(np.ascontiguousarray(x)).cuda()).cpu().numpy()
+    bad = np.nonzero(miss)[0]
+    assert bad.size == 0, (bad.size, x[bad[:5]], miss[bad[:5]])
