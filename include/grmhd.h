@@ -143,8 +143,8 @@ typedef struct {
                            FP32 decisions of the FOFC estimate (every mode) */
   long long fofc_fp32;  /* FOFC estimate cells (and cells of a flags-only
                            mhd_c2p_cells) whose flag was decided from FP32
-                           values, without an FP64 evaluation of the master
-                           function (ideal gas) */
+                           interval enclosures, without an FP64 evaluation of
+                           the master function (ideal gas) */
 } mhd_stats;
 #define MHD_NSTATS 10
 
@@ -175,8 +175,9 @@ int mhd_prim2cons(mhd_ctx* ctx, long n, const double* prim, const double* Bd, co
  * makes the call synchronise the stream (before and after its launches).
  * prim = NULL asks only the question of the FOFC estimate (Sec. 3.3): flags[c]
  * = 1 where con2prim of the cell fails or a floor fires, else 0; cons is not
- * written.  With the ideal gas most cells are then decided from FP32 values
- * without an FP64 evaluation (stats: fofc_fp32; iters 0 for them), and the
+ * written.  With the ideal gas most cells are then decided from FP32 interval
+ * enclosures, which contain the exact values, without FP64 work (stats:
+ * fofc_fp32; iters 0 for them); the others take the FP64 con2prim.  The
  * flagged cells are counted in fofc_cells (fails and floors are not). */
 int mhd_c2p_cells(mhd_ctx* ctx, long n, double* cons, const double* Bd, const double* g, double* prim,
                   unsigned char* flags, int* iters, void* stream, mhd_stats* stats);
