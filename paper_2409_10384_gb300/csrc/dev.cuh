@@ -1071,10 +1071,12 @@ __device__ __forceinline__ int fofc_decide_iv(const KSI& k, const Par& P, unsign
 }
 
 // Phase 3: primitives at the root mu (Sec. 3.4 recovery) and the floors on
-// the primitives (Sec. 3.3).  On failure the static atmosphere.
+// the primitives (Sec. 3.3).  On failure the static atmosphere.  iWo
+// (optional): 1/W of the written velocity, W (1 - v^2) of the recovery (the
+// capped v^2 under the velocity cap), 1 where the velocity is set to 0.
 __device__ __forceinline__ void krp_finish(const Par& P, const KrpCell& k, double mu, bool ok, unsigned& flags,
-                                           double* prim) {
-  double rho = P.rho_atm, p = P.P_atm, w0 = 0.0, w1 = 0.0, w2 = 0.0;
+                                           double* prim, double* iWo = nullptr) {
+  double rho = P.rho_atm, p = P.P_atm, w0 = 0.0, w1 = 0.0, w2 = 0.0, iWr = 1.0;
   if (!ok || !isfinite(mu)) {
     flags |= F_FAIL;
   } else {
@@ -1086,11 +1088,13 @@ __device__ __forceinline__ void krp_finish(const Par& P, const KrpCell& k, doubl
       double iW = e.W * (1.0 - (e.vcap ? s.vmax2 : mu * mu * e.rbar2));
       rho = k.D * iW;
       p = P.gm1 * rho * e.eps;
+      iWr = iW;
     } else {
       kev_hyb(s, P, mu, e);
       if (e.eps_raw < e.eps_min) flags |= F_TEMP;
       rho = e.rho;
       p = e.P;
+      if (iWo) iWr = e.W * (1.0 - (e.vcap ? s.vmax2 : mu * mu * e.rbar2));
     }
     if (e.vcap) flags |= F_VMAX;
     double vs = 1.0;
@@ -1101,7 +1105,7 @@ __device__ __forceinline__ void krp_finish(const Par& P, const KrpCell& k, doubl
     w1 = f * fma(mrb, k.bu[1], k.ru[1]);
     w2 = f * fma(mrb, k.bu[2], k.ru[2]);
     if (below_thr(P, rho)) {
-      rho = P.rho_atm; p = P.P_atm; w0 = w1 = w2 = 0.0;
+      rho = P.rho_atm; p = P.P_atm; w0 = w1 = w2 = 0.0; iWr = 1.0;
       flags |= F_RHO;
     } else {
       // T floor: P >= P_c(rho) + rho T_atm (the cold part at this rho is
@@ -1114,9 +1118,10 @@ __device__ __forceinline__ void krp_finish(const Par& P, const KrpCell& k, doubl
     }
   }
   if (flags & F_FAIL) {
-    rho = P.rho_atm; p = P.P_atm; w0 = w1 = w2 = 0.0;
+    rho = P.rho_atm; p = P.P_atm; w0 = w1 = w2 = 0.0; iWr = 1.0;
   }
   prim[0] = rho; prim[1] = w0; prim[2] = w1; prim[3] = w2; prim[4] = p;
+  if (iWo) *iWo = iWr;
 }
 
 // The con2prim of one cell in one thread.  U: densitised conserved state
@@ -1125,7 +1130,7 @@ __device__ __forceinline__ void krp_finish(const Par& P, const KrpCell& k, doubl
 // (glo < 0: none); alpha: the lapse, for the excision floor.
 __device__ __forceinline__ void con2prim(const Par& P, double* U, const double* Bd, const Metric& m, double* prim,
                                          unsigned& flags, int& iters, bool write_cons, double glo = -1.0,
-                                         double ghi = -1.0, double alpha = 1.0) {
+                                         double ghi = -1.0, double alpha = 1.0, double* iWo = nullptr) {
   KrpCell k;
   iters = 0;
   bool ok = krp_prep(P, U, Bd, m, k, flags, alpha);
@@ -1140,7 +1145,7 @@ __device__ __forceinline__ void con2prim(const Par& P, double* U, const double* 
       iters += it;
     }
   }
-  krp_finish(P, k, mu, ok, flags, prim);
+  krp_finish(P, k, mu, ok, flags, prim, iWo);
   if (write_cons && (flags & (FLOOR_BITS | F_FAIL))) prim2cons(P, prim, Bd, m, U);
 }
 

@@ -147,12 +147,12 @@ __global__ void __launch_bounds__(128) k_c2p_block(Work w, Par P, unsigned long 
     for (int v = 0; v < 3; v++) b.bcc[v * nc + c] = Bd[v];
     Metric m;
     load_metric(b, c, m);
-    double U[5], pr[5];
+    double U[5], pr[5], iW;
 #pragma unroll
     for (int v = 0; v < 5; v++) U[v] = b.cons[v * nc + c];
     unsigned fl;
     int itn;
-    con2prim(P, U, Bd, m, pr, fl, itn, true, -1.0, -1.0, b.adm[c]);
+    con2prim(P, U, Bd, m, pr, fl, itn, true, -1.0, -1.0, b.adm[c], &iW);
 #pragma unroll
     for (int v = 0; v < 5; v++) b.prim[v * nc + c] = pr[v];
     if (fl & (FLOOR_BITS | F_FAIL)) {
@@ -163,10 +163,9 @@ __global__ void __launch_bounds__(128) k_c2p_block(Work w, Par P, unsigned long 
     if (ii >= 2 && ii <= b.n[0] + 3 && jj >= 2 && jj <= b.n[1] + 3 && kk >= 2 && kk <= b.n[2] + 3) {
       const double alpha = b.adm[c];
       const double be0 = b.adm[nc + c], be1 = b.adm[2 * nc + c], be2 = b.adm[3 * nc + c];
-      double wu[3] = {pr[1], pr[2], pr[3]}, wl[3];
-      lower3(m.g, wu, wl);
-      double iW = rsqrt(1.0 + dot3(wu, wl));
-      double a0 = fma(alpha * iW, wu[0], -be0), a1 = fma(alpha * iW, wu[1], -be1), a2 = fma(alpha * iW, wu[2], -be2);
+      // alpha v^i - beta^i with 1/W from the recovery
+      const double aiW = alpha * iW;
+      double a0 = fma(aiW, pr[1], -be0), a1 = fma(aiW, pr[2], -be1), a2 = fma(aiW, pr[3], -be2);
       b.ecc[c] = -(a1 * Bd[2] - a2 * Bd[1]);
       b.ecc[nc + c] = -(a2 * Bd[0] - a0 * Bd[2]);
       b.ecc[2 * nc + c] = -(a0 * Bd[1] - a1 * Bd[0]);

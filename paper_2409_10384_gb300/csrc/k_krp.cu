@@ -252,19 +252,19 @@ __global__ void __launch_bounds__(256) k_krp_finish_block(Work w, Par P, KrpBuf 
     kw_load(kb, P, it, kc);
     unsigned fl = kb.fl[it];
     const unsigned char st = kb.st[it];
-    double pr[5];
+    double pr[5], iW;
     const double root = kb.w[KW_MU * n + it];
-    krp_finish(P, kc, root, st == 1, fl, pr);
+    krp_finish(P, kc, root, st == 1, fl, pr, &iW);
     if (b.mu) b.mu[c] = (st == 1 && !(fl & F_FAIL)) ? root : 0.0;
 #pragma unroll
     for (int v = 0; v < 5; v++) b.prim[v * nc + c] = pr[v];
     const double Bd[3] = {b.bcc[c], b.bcc[nc + c], b.bcc[2 * nc + c]};
-    Metric m;
+    if (fl & (FLOOR_BITS | F_FAIL)) {   // only here is the metric needed
+      Metric m;
 #pragma unroll
-    for (int v = 0; v < 6; v++) m.g[v] = b.adm[(4 + v) * nc + c];
-    m.sdet = kb.w[KW_SDET * n + it];
-    m.isdet = kb.w[KW_ISDET * n + it];
-    if (fl & (FLOOR_BITS | F_FAIL)) {
+      for (int v = 0; v < 6; v++) m.g[v] = b.adm[(4 + v) * nc + c];
+      m.sdet = kb.w[KW_SDET * n + it];
+      m.isdet = kb.w[KW_ISDET * n + it];
       double U[5];
       prim2cons(P, pr, Bd, m, U);
       const double D0 = b.cons[c];
@@ -277,10 +277,9 @@ __global__ void __launch_bounds__(256) k_krp_finish_block(Work w, Par P, KrpBuf 
     if (ii >= 2 && ii <= b.n[0] + 3 && jj >= 2 && jj <= b.n[1] + 3 && kk >= 2 && kk <= b.n[2] + 3) {
       const double alpha = b.adm[c];
       const double be0 = b.adm[nc + c], be1 = b.adm[2 * nc + c], be2 = b.adm[3 * nc + c];
-      double wu[3] = {pr[1], pr[2], pr[3]}, wl[3];
-      lower3(m.g, wu, wl);
-      double iW = rsqrt(1.0 + dot3(wu, wl));
-      double a0 = fma(alpha * iW, wu[0], -be0), a1 = fma(alpha * iW, wu[1], -be1), a2 = fma(alpha * iW, wu[2], -be2);
+      // alpha v^i - beta^i with 1/W from the recovery
+      const double aiW = alpha * iW;
+      double a0 = fma(aiW, pr[1], -be0), a1 = fma(aiW, pr[2], -be1), a2 = fma(aiW, pr[3], -be2);
       b.ecc[c] = -(a1 * Bd[2] - a2 * Bd[1]);
       b.ecc[nc + c] = -(a2 * Bd[0] - a0 * Bd[2]);
       b.ecc[2 * nc + c] = -(a0 * Bd[1] - a1 * Bd[0]);
