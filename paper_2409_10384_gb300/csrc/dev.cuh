@@ -316,15 +316,22 @@ __host__ __device__ __forceinline__ bool below_thr(const Par& P, double x) {
 }
 // CT upwinding (k_emf) by the sign of the face mass flux fD: (a - b) for
 // fD > 0, (c - d) for fD < 0, their average for fD = 0 (or NaN).  The sign test
-// reads the bit pattern on the integer pipe and only the chosen difference is
-// formed in FP64: the same values as comparing fD with 0 in FP64, with one
-// subtraction where the select form takes two subtractions, two compares and
-// an average.
+// reads the bit pattern on the integer pipe, the operands of the chosen
+// difference are selected there too, and one FP64 subtraction forms it: the
+// same values as comparing fD with 0 in FP64.  The average (fD = 0, rare) is a
+// call of its own, so that the compiler branches to it instead of forming
+// both differences in every lane.
+static __host__ __device__ __noinline__ double upw_avg(double a, double b, double c, double d) {
+  return 0.5 * ((a - b) + (c - d));
+}
 __host__ __device__ __forceinline__ double upw(double fD, double a, double b, double c, double d) {
   const unsigned long long u = (unsigned long long)dbits(fD);
   const unsigned long long mag = u & 0x7FFFFFFFFFFFFFFFull;
-  if (mag - 1ull < 0x7FF0000000000000ull) return (u >> 63) ? c - d : a - b;   // fD != 0, not NaN
-  return 0.5 * ((a - b) + (c - d));
+  if (mag - 1ull < 0x7FF0000000000000ull) {   // fD != 0, not NaN
+    const bool neg = (u >> 63) != 0;
+    return (neg ? c : a) - (neg ? d : b);
+  }
+  return upw_avg(a, b, c, d);
 }
 // min / max of two doubles that are not NaN, on the integer pipe: the key
 // u ^ ((u >> 63) & 0x7FF..F) of the bit pattern u orders doubles as numbers
