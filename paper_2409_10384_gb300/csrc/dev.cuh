@@ -1420,8 +1420,11 @@ __device__ __forceinline__ void face_floor(const Par& P, double* s, double* cold
     eos_cold(P, s[0], cold[0], cold[1], cold[2]);
     const double pf = fma(s[0], P.T_atm, cold[0]);
     if (s[4] < pf) s[4] = pf;
-  } else if (s[4] < s[0] * P.T_atm) {
-    s[4] = s[0] * P.T_atm;
+  } else {
+    // p < rho T_atm by the integer key, as an FP64 compare decides it for
+    // p that is not NaN (a -0 pressure counts below +0)
+    const double pf = s[0] * P.T_atm;
+    if (okey(s[4]) < okey(pf)) s[4] = pf;
   }
 }
 
@@ -1555,7 +1558,8 @@ __device__ __forceinline__ void riemann(int rs, const FaceMetric& fm, double Bn,
       kdU = (lL * lR) * inv;
     }
   } else {
-    kdU = -0.5 * fmax(fmax(fabs(lmL), fabs(lpL)), fmax(fabs(lmR), fabs(lpR)));
+    // the largest |lambda| by the integer key (the speeds are finite)
+    kdU = -0.5 * imax(imax(fabs(lmL), fabs(lpL)), imax(fabs(lmR), fabs(lpR)));
   }
   // kFL F_L - kdU U_L and kFR F_R + kdU U_R per side vector
   const double gL = fma(kFL, L.avd, -kdU), gR = fma(kFR, R.avd, kdU);

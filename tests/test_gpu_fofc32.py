@@ -1,7 +1,8 @@
 """The FOFC estimate's flags from FP32 values (Sec. 3.3: the estimate only asks
 whether con2prim of U* fails or a floor fires).  With the ideal gas the library
-decides most cells from FP32 evaluations of the master function around the
-FP32 root, with error margins, and leaves the rest to the FP64 recovery.
+decides most cells from FP32 interval enclosures of the KRP variables, of the
+master function around the FP32 root and of v^2, rho and eps_raw, and leaves
+the rest to the FP64 recovery.
 Every decision must equal the FP64 recovery's: mhd_c2p_cells with prim = NULL
 (flags only, the same decision) is compared cell by cell with the full
 con2prim of the same cells, on stress states where floors fire and on states
@@ -150,11 +151,6 @@ def test_flags_only_equal_full_recovery_near_thresholds(G, which):
         assert bad.size == 0, (which, k, bad.size, bad[:10])
         decided.append(st["fofc_fp32"] / n)
     print(which, "decided in FP32 at 1e-1 .. 1e-9:", " ".join(f"{x:.3f}" for x in decided))
-    if which == "W":
-        # at the velocity cap (W ~ W_max = 5) the FP32 error bounds, which grow
-        # as W^2, are wider than the interval around the root: every cell goes
-        # to the FP64 recovery
-        return
     assert decided[0] > 0.2            # far from the threshold a share is decided
     assert decided[-1] < decided[0]    # near it they go to the FP64 recovery
 
