@@ -131,7 +131,7 @@ def _err(a, b, T, floor_frac=1e-10):
     return float(np.max(np.abs(a - b) / np.maximum(np.maximum(np.abs(b), T), s)))
 
 
-def survey_err(a, b, floor_frac=1e-10):
+def plain_rel_err(a, b, floor_frac=1e-10):
     """The plain error measure max|a - b| / max(|b|, s_f), s_f = 1e-10 max|b|,
     per cell, without the term scales (reported beside the bar, not a bar)."""
     if a.size == 0:
@@ -241,10 +241,10 @@ def compare_state(ob: O.Block, got: dict, what="", cons_tol=CONS_TOL, scales=Non
         errs[f"bf{d}"] = _err(got["bf"][d][F], ob.bf[d][F], TB[d][F])
     plain = {}
     for v in range(5):
-        plain[f"cons{v}"] = survey_err(got["cons"][v][I], ob.cons[v][I])
+        plain[f"cons{v}"] = plain_rel_err(got["cons"][v][I], ob.cons[v][I])
     for d in range(3):
         F = face_interior(ob, d)
-        plain[f"bf{d}"] = survey_err(got["bf"][d][F], ob.bf[d][F])
+        plain[f"bf{d}"] = plain_rel_err(got["bf"][d][F], ob.bf[d][F])
     _record("state", errs, plain, ties=getattr(ob, "ties", 0), flips=getattr(ob, "flips", 0))
     bad = {k: e for k, e in errs.items() if not e <= cons_tol}
     assert not bad, f"{what}: {bad}"
@@ -264,7 +264,7 @@ def compare_prims(ob: O.Block, got: dict, p, what=""):
     scale = pgm1(p) * np.abs(ob.cons[0][R] + ob.cons[4][R]) / np.sqrt(det)
     dP = np.abs(got["prim"][4][R] - ob.prim[4][R])
     errs["P"] = float(np.max(dP / (1e-10 * np.abs(ob.prim[4][R]) + 1e-12 * scale)))
-    plain = {f"prim{v}": survey_err(got["prim"][v][R], ob.prim[v][R]) for v in range(5)}
+    plain = {f"prim{v}": plain_rel_err(got["prim"][v][R], ob.prim[v][R]) for v in range(5)}
     _record("prims", {("P/bar" if k == "P" else k): v for k, v in errs.items()}, plain)
     bad = {k: e for k, e in errs.items() if not (e <= PRIM_TOL if k != "P" else e <= 1.0)}
     assert not bad, f"{what}: {bad}"
