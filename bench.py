@@ -73,7 +73,7 @@ TRAFFIC_STALE = set()
 # 104^3 case, which has the 128^3 segment lengths; profiles/ncu_flux_star104_fp64.md),
 # for the issue-based fraction: executed FP64 instructions per second over
 # the pipe's 2 thread instructions per clock per SM at the sampled SM clock.
-FP64_INST_PER_UNIT = {"flux_x": 597.4, "flux_y": 597.4, "flux_z": 597.4}
+FP64_INST_PER_UNIT = {"flux_x": 595.4, "flux_y": 595.4, "flux_z": 595.4}
 FP64_ISSUE_PER_CLK_SM = 2.0
 
 # Algorithmic HBM bytes per zone and RK stage of one fused pass: read U (5),
@@ -759,7 +759,7 @@ def run_ours(args):
                                "MEASURED_PEAKS.json",
                 "achieved_source": "algorithmic FP64 operations of the op-counting oracle (add, mul, div, sqrt "
                                    "each 1) x faces per launch / mean launch time from CUDA events",
-                "frac_note": "frac can pass 1: the sweep executes ~900 FP64 flops (597 instructions, FMAs "
+                "frac_note": "frac can pass 1: the sweep executes ~900 FP64 flops (595 instructions, FMAs "
                              "counted twice) per face for the oracle's 1438 operations (values shared "
                              "along the sweep and between the two sides, FMAs); frac_issue is the FP64 "
                              "pipe's issue fraction",
