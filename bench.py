@@ -290,7 +290,8 @@ def periodic32_leg(G, steps=50):
     leg's con2prim, SSP-RK2, a fixed flat metric whose cache is kept across
     steps): one RK2 step per iteration, launched directly and as
     the captured graph, each with and without the periodic ghost fill
-    (mhd_fill_ghosts) before the step."""
+    (mhd_fill_ghosts) before the step, then as a graph with the launch shapes
+    of the library's autotuner."""
     import torch
     from paper_2409_10384_gb300 import synth
     p = dict(gamma=5.0 / 3.0, rho_atm=1e-12, T_atm=1e-10, f_thr=0.1, sigma_max=0.0, dmp_M=0.0, c2p_tol=1e-10,
@@ -326,6 +327,22 @@ def periodic32_leg(G, steps=50):
         ms = e0.elapsed_time(e1) / steps
         out[name] = {"zone_cycles_per_s": 32 ** 3 / (ms * 1e-3), "ms_per_step": ms,
                      "launches_per_step": (ctx.launches() - l0) / steps}
+    # the library's autotuner picks launch shapes for this one small block (as
+    # for the AMR list), then the graph again
+    with torch.cuda.stream(stream):
+        out["autotune"] = ctx.autotune([blk], dt, stream=stream)
+        for _ in range(5):
+            ctx.step([blk], dt, graph=True, stream=stream)
+        l0 = ctx.launches()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            ctx.step([blk], dt, graph=True, stream=stream)
+        e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    out["tuned_graph"] = {"zone_cycles_per_s": 32 ** 3 / (ms * 1e-3), "ms_per_step": ms,
+                          "launches_per_step": (ctx.launches() - l0) / steps}
     # where a step's time goes: per-kernel CUDA events (direct launches), their
     # sum against the step time of the graph (the rest is launch and drain)
     ctx.profile(True)

@@ -464,6 +464,10 @@ Work work_of(const mhd_ctx* c) {
 // the seed kernel, 2 runs the FP32 search and FP64 polish in the prep, 0 and
 // 3 take the FP64 bracket (3 from the previous root where there is one).
 int prep_mode(int g) { return g == 1 || g == 2 ? g : 0; }
+// With the prep's polish (c2p_guess 2) a status-0 cell is a rare fallback:
+// the finish kernels solve such cells themselves and the refill solve
+// launch, which would find no work in most calls, is left out.
+bool inline_solve(int g) { return prep_mode(g) == 2; }
 // Between the prep and the FP64 root solve of the learned con2prim (c2p_guess
 // 1): the seed kernel, which runs the network on features it forms from the
 // prep's KRP variables, the FP32 search and the FP64 polish, and turns
@@ -494,9 +498,10 @@ int enqueue_c2p(mhd_ctx* c, cudaStream_t s, const Work& w, const long long* item
                           prep_mode(c->P.guess), nullptr);
   });
   c2p_seed(c, kb, items[W_C2P], s);
-  timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, s, c->solve_grid(items[W_C2P])); });
+  const bool inl = inline_solve(c->P.guess);
+  if (!inl) timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, s, c->solve_grid(items[W_C2P])); });
   timed(c, MHD_K_C2P, s, [&] {
-    launch_krp_finish_block(w, c->P, kb, c->dstats, s, tgrid(c, T_C2P_FIN, items[W_C2P]), cf.threads);
+    launch_krp_finish_block(w, c->P, kb, c->dstats, s, tgrid(c, T_C2P_FIN, items[W_C2P]), cf.threads, inl);
   });
   return cuda_ok(cudaGetLastError());
 }
@@ -538,10 +543,11 @@ int enqueue_rhs(mhd_ctx* c, double dt, int stage, cudaStream_t s, const Work& w,
                            c->cfg[T_FOFC_PREP].threads, prep_mode(c->P.guess), nullptr);
     });
     c2p_seed(c, kb, items[W_CELL], s);
-    timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, s, c->solve_grid(items[W_CELL])); });
+    const bool inl = inline_solve(c->P.guess);
+    if (!inl) timed(c, MHD_K_SOLVE, s, [&] { launch_krp_solve(c->P, kb, s, c->solve_grid(items[W_CELL])); });
     timed(c, MHD_K_FOFC_FLAG, s, [&] {
       launch_krp_finish_fofc(w, c->P, kb, c->dstats, s, tgrid(c, T_FOFC_FIN, items[W_CELL]),
-                             c->cfg[T_FOFC_FIN].threads);
+                             c->cfg[T_FOFC_FIN].threads, inl);
     });
     // the faces of the listed flagged cells (one launch; the list is short)
     const long long g = std::min<long long>((items[W_CELL] + 127) / 128, (long long)c->nsm * std::max(c->occ_face[4], 1));

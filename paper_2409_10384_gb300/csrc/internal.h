@@ -51,13 +51,14 @@ KrpBuf krp_view(void* base, long long n);
 void launch_krp_prep_block(const Work& w, const Par& P, const KrpBuf& kb, unsigned long long* stats, cudaStream_t s,
                            int grid, int threads = 128, int mode = 0, float* feat = nullptr);
 void launch_krp_solve(const Par& P, const KrpBuf& kb, cudaStream_t s, int grid);
+// inl: the finish solves status-0 cells itself (no solve launch before it)
 void launch_krp_finish_block(const Work& w, const Par& P, const KrpBuf& kb, unsigned long long* stats,
-                             cudaStream_t s, int grid, int threads = 128);
+                             cudaStream_t s, int grid, int threads = 128, bool inl = false);
 void launch_krp_prep_fofc(const Work& w, const Par& P, double g0, double g1, double bdt, const KrpBuf& kb,
                           unsigned long long* stats, cudaStream_t s, int grid, int threads = 128, int mode = 0,
                           float* feat = nullptr);
 void launch_krp_finish_fofc(const Work& w, const Par& P, const KrpBuf& kb, unsigned long long* stats,
-                            cudaStream_t s, int grid, int threads = 128);
+                            cudaStream_t s, int grid, int threads = 128, bool inl = false);
 // fonly: flags only (the FOFC estimate's question, no recovery written; the
 // finish then gets prim = null)
 void launch_krp_prep_cells(const Par& P, const KrpBuf& kb, const double* cons, const double* Bd, const double* g,

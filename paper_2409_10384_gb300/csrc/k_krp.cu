@@ -116,6 +116,52 @@ __device__ __forceinline__ void load_metric6(const double* g6, long long stride,
   metric_setup(m);
 }
 
+// The root solve of one status-0 cell in its own thread: the iteration of
+// k_krp_solve (Illinois with the end-point nudge from the prep's bracket,
+// its evaluations counted on from the prep's, capped at maxit in all)
+// without the lane refill.  The finish kernels use it when the prep polishes
+// the FP32 root (c2p_guess 2): a status-0 cell is then a rare fallback, and
+// the separate solve launch, which would find no work in most calls, is left
+// out.  Returns the status (1 root, 3 iteration cap); root and it as the
+// solve kernel writes them.
+__device__ __forceinline__ unsigned char solve_cell(const KS& s, const Par& P, double a, double Ga, double b,
+                                                    double Gb, int& it, double& root) {
+  double Fa = Ga, Fb = Gb;
+  int side = 0;
+  while (true) {
+    bool fin = !gt_nn(b - a, P.tol * b), cap = false, exact = false;
+    if (!fin) {
+      if (it >= P.maxit) {
+        cap = fin = true;
+      } else {
+        it++;
+        double c = (a * Fb - b * Fa) * rcp_nr(Fb - Fa);   // Fb > 0 > Fa
+        const double eta = 0.25 * P.tol * b;
+        c += side == -1 ? eta : (side == 1 ? -eta : 0.0);
+        if (!(gt_nn(c, a) && gt_nn(b, c))) c = 0.5 * (a + b);
+        const double G = kev_G(s, P, c);
+        if (lt0(G)) {
+          a = c; Ga = G; Fa = G;
+          if (side == -1) Fb *= 0.5;
+          side = -1;
+        } else if (gt0(G)) {
+          b = c; Gb = G; Fb = G;
+          if (side == 1) Fa *= 0.5;
+          side = 1;
+        } else {
+          exact = fin = true;
+          root = c;
+        }
+        if (!fin) fin = !gt_nn(b - a, P.tol * b);
+      }
+    }
+    if (fin) {
+      if (!exact && !cap) root = a - Ga * (b - a) * rcp_nr(Gb - Ga);   // Gb > 0 > Ga
+      return cap ? 3 : 1;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ root solve
 // Illinois regula falsi with the end-point nudge (as in `illinois`) and lane
 // refill.  Reads the
@@ -234,7 +280,9 @@ __global__ void __launch_bounds__(256) k_krp_prep_block(Work w, Par P, KrpBuf kb
   }
 }
 
-__global__ void __launch_bounds__(256) k_krp_finish_block(Work w, Par P, KrpBuf kb, unsigned long long* stats) {
+// inl: status-0 cells are solved here (solve_cell), no solve launch before
+__global__ void __launch_bounds__(256) k_krp_finish_block(Work w, Par P, KrpBuf kb, unsigned long long* stats,
+                                                           bool inl) {
   const long long* pre = w.pre + (long long)W_C2P * (w.nblocks + 1);
   const long long tot = pre[w.nblocks];
   const long long n = kb.n;
@@ -251,9 +299,13 @@ __global__ void __launch_bounds__(256) k_krp_finish_block(Work w, Par P, KrpBuf 
     KrpCell kc;
     kw_load(kb, P, it, kc);
     unsigned fl = kb.fl[it];
-    const unsigned char st = kb.st[it];
+    unsigned char st = kb.st[it];
     double pr[5], iW;
-    const double root = kb.w[KW_MU * n + it];
+    double root = kb.w[KW_MU * n + it];
+    int its = kb.it[it];
+    if (inl && st == 0)
+      st = solve_cell(kc.s, P, kb.w[KW_A * n + it], kb.w[KW_GA * n + it], kb.w[KW_B * n + it],
+                      kb.w[KW_GB * n + it], its, root);
     krp_finish(P, kc, root, st == 1, fl, pr, &iW);
     if (b.mu) b.mu[c] = (st == 1 && !(fl & F_FAIL)) ? root : 0.0;
 #pragma unroll
@@ -285,7 +337,7 @@ __global__ void __launch_bounds__(256) k_krp_finish_block(Work w, Par P, KrpBuf 
       b.ecc[2 * nc + c] = -(a0 * Bd[1] - a1 * Bd[0]);
     }
     s_cells++;
-    s_it += (unsigned)kb.it[it];
+    s_it += (unsigned)its;
     s_fail += (fl & F_FAIL) ? 1u : 0u;
     s_floor += (fl & FLOOR_BITS) ? 1u : 0u;
   }
@@ -346,7 +398,9 @@ __global__ void __launch_bounds__(256) k_krp_prep_fofc(Work w, Par P, double g0,
   warp_flush(&stats[9], s_dec);
 }
 
-__global__ void __launch_bounds__(256) k_krp_finish_fofc(Work w, Par P, KrpBuf kb, unsigned long long* stats) {
+// inl: status-0 cells are solved here (solve_cell), no solve launch before
+__global__ void __launch_bounds__(256) k_krp_finish_fofc(Work w, Par P, KrpBuf kb, unsigned long long* stats,
+                                                          bool inl) {
   const long long tot = w.pre[(long long)W_CELL * (w.nblocks + 1) + w.nblocks];
   const long long n = kb.n;
   unsigned s_flag = 0, s_dmp = 0;
@@ -363,7 +417,14 @@ __global__ void __launch_bounds__(256) k_krp_finish_fofc(Work w, Par P, KrpBuf k
       KrpCell kc;
       kw_load(kb, P, it, kc);
       double pr[5];
-      krp_finish(P, kc, kb.w[KW_MU * n + it], st == 1, fl, pr);
+      double root = kb.w[KW_MU * n + it];
+      unsigned char s2 = st;
+      if (inl && st == 0) {
+        int its = kb.it[it];
+        s2 = solve_cell(kc.s, P, kb.w[KW_A * n + it], kb.w[KW_GA * n + it], kb.w[KW_B * n + it],
+                        kb.w[KW_GB * n + it], its, root);
+      }
+      krp_finish(P, kc, root, s2 == 1, fl, pr);
       flag = (fl & (FLOOR_BITS | F_FAIL)) != 0;
     }
     if (!flag && P.dmp_M > 0.0) {
@@ -533,16 +594,16 @@ void launch_krp_solve(const Par& P, const KrpBuf& kb, cudaStream_t s, int grid) 
   k_krp_solve<<<grid, 256, 0, s>>>(P, kb);
 }
 void launch_krp_finish_block(const Work& w, const Par& P, const KrpBuf& kb, unsigned long long* stats,
-                             cudaStream_t s, int grid, int threads) {
-  k_krp_finish_block<<<grid, threads, 0, s>>>(w, P, kb, stats);
+                             cudaStream_t s, int grid, int threads, bool inl) {
+  k_krp_finish_block<<<grid, threads, 0, s>>>(w, P, kb, stats, inl);
 }
 void launch_krp_prep_fofc(const Work& w, const Par& P, double g0, double g1, double bdt, const KrpBuf& kb,
                           unsigned long long* stats, cudaStream_t s, int grid, int threads, int mode, float* feat) {
   k_krp_prep_fofc<<<grid, threads, 0, s>>>(w, P, g0, g1, bdt, kb, mode, feat, stats);
 }
 void launch_krp_finish_fofc(const Work& w, const Par& P, const KrpBuf& kb, unsigned long long* stats,
-                            cudaStream_t s, int grid, int threads) {
-  k_krp_finish_fofc<<<grid, threads, 0, s>>>(w, P, kb, stats);
+                            cudaStream_t s, int grid, int threads, bool inl) {
+  k_krp_finish_fofc<<<grid, threads, 0, s>>>(w, P, kb, stats, inl);
 }
 void launch_krp_prep_cells(const Par& P, const KrpBuf& kb, const double* cons, const double* Bd, const double* g,
                            int mode, float* feat, unsigned long long* stats, cudaStream_t s, int grid, bool fonly) {
