@@ -845,6 +845,8 @@ def main():
     ap.add_argument("--no-amr", action="store_true", help="skip the batched AMR leg (profiling cases)")
     ap.add_argument("--no-bns", action="store_true", help="skip the binary-shaped leg (profiling cases)")
     ap.add_argument("--no-small", action="store_true", help="skip the 32^3 periodic leg (profiling cases)")
+    ap.add_argument("--small-only", action="store_true",
+                    help="run the 32^3 periodic leg alone and print its JSON (profiling case)")
     ap.add_argument("--c2p-cells", type=int, default=1 << 24, help="cells of the con2prim leg (profiling cases)")
     ap.add_argument("--c2p-guess", type=int, default=None,
                     help="root search of the main leg's con2prims (default: the module's C2P_GUESS)")
@@ -857,6 +859,14 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.small_only:
+        import torch
+        from paper_2409_10384_gb300 import build as B
+        from paper_2409_10384_gb300 import grmhd as G
+        torch.cuda.set_device(0)
+        B.build()
+        print(json.dumps({"periodic32": periodic32_leg(G)}))
+        return 0
     return run_ours(args)
 
 
