@@ -4,7 +4,9 @@
 // finish (recovery, floors, write-back).  One thread per cell would leave most
 // lanes of a warp idle while the slowest cell iterates, and idle lanes still
 // occupy the narrow FP64 pipe; with refill the lanes stay busy until the
-// queue runs dry.
+// queue runs dry.  When the prep polishes an FP32 root (c2p_guess 2) a cell
+// left for the solve is a rare fallback: the finish kernels then solve it in
+// place (solve_cell) and the solve kernel is not launched.
 #include "dev.cuh"
 #include "internal.h"
 
