@@ -809,10 +809,31 @@ __device__ __forceinline__ int krp_bracket(const KS& s, const Par& P, double glo
 struct KSf {
   float qh, r2, b2, rb2, rp2, gam, emin, vmax2;
 };
+// Conversions between double and float on the integer pipe (a conversion
+// instruction takes an FP64 issue slot on this part).  f32_tz: toward zero,
+// which is all the search's start needs; beyond the float range inf (NaN
+// stays NaN), below 2^-126 a signed zero.  f64_of: exact for a normal float
+// and zero, the conversion instruction for the rest.
+__device__ __forceinline__ float f32_tz(double x) {
+  const unsigned h = (unsigned)__double2hiint(x), l = (unsigned)__double2loint(x);
+  const unsigned sg = h & 0x80000000u;
+  const int e = (int)((h >> 20) & 0x7FFu);
+  if (e >= 897 && e <= 1150) return __uint_as_float(sg | ((unsigned)(e - 896) << 23) | ((h & 0xFFFFFu) << 3) | (l >> 29));
+  if (e < 897) return __uint_as_float(sg);
+  const bool nan = e == 0x7FF && ((h & 0xFFFFFu) | l) != 0u;
+  return __uint_as_float(sg | 0x7F800000u | (nan ? 0x400000u : 0u));
+}
+__device__ __forceinline__ double f64_of(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e != 0u && e != 0xFFu)
+    return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3)), (int)(u << 29));
+  return (double)f;
+}
 __device__ __forceinline__ KSf ks_f32(const KS& s) {
   KSf f;
-  f.qh = (float)s.qh; f.r2 = (float)s.r2; f.b2 = (float)s.b2; f.rb2 = (float)s.rb2; f.rp2 = (float)s.rperp2;
-  f.gam = (float)s.gam; f.emin = fmaxf((float)s.eps_min, 1e-37f); f.vmax2 = (float)s.vmax2;
+  f.qh = f32_tz(s.qh); f.r2 = f32_tz(s.r2); f.b2 = f32_tz(s.b2); f.rb2 = f32_tz(s.rb2); f.rp2 = f32_tz(s.rperp2);
+  f.gam = f32_tz(s.gam); f.emin = fmaxf(f32_tz(s.eps_min), 1e-37f); f.vmax2 = f32_tz(s.vmax2);
   return f;
 }
 __device__ __forceinline__ float f32_master(const KSf& s, float mu) {
@@ -1574,6 +1595,15 @@ __device__ __forceinline__ void riemann(int rs, const FaceMetric& fm, double Bn,
   F[6] = fma(L.Bt2, gL, fma(R.Bt2, gR, -Bn * fma(kFL, L.avh2, kFR * R.avh2)));
 }
 
+// x / 16 on the integer pipe (the exponent field less 4) where the result is a
+// normal double, else (0, tiny, inf, NaN) by the FP64 multiply: exact either
+// way, so fma(9, s1, -s2) / 16 has the bits of fma(0.5625, s1, -0.0625 s2).
+__device__ __forceinline__ double mul_2m4(double x) {
+  const int h = __double2hiint(x);
+  const int e = (h >> 20) & 0x7FF;
+  if (e > 4 && e < 0x7FF) return __hiloint2double(h - (4 << 20), __double2loint(x));
+  return 0.0625 * x;
+}
 // Interpolates the ADM variables to the face between the cells at a and a+st
 // (4-point Lagrange, weights (-1, 9, 9, -1)/16) and prepares the metric.
 __device__ __forceinline__ void face_metric(const double* adm, long long nc, long long a, long long st, FaceMetric& fm) {
@@ -1581,7 +1611,7 @@ __device__ __forceinline__ void face_metric(const double* adm, long long nc, lon
 #pragma unroll
   for (int v = 0; v < 10; v++) {
     const double* q = adm + v * nc + a;
-    mv[v] = fma(0.5625, q[0] + q[st], -0.0625 * (q[-st] + q[2 * st]));
+    mv[v] = mul_2m4(fma(9.0, q[0] + q[st], -(q[-st] + q[2 * st])));   // (9 (q0 + q1) - (q-1 + q2)) / 16
   }
   fm.alpha = mv[0];
   fm.beta[0] = mv[1]; fm.beta[1] = mv[2]; fm.beta[2] = mv[3];

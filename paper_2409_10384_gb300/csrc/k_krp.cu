@@ -83,7 +83,7 @@ __device__ __forceinline__ unsigned char prep_cell(const Par& P, const KrpBuf& k
           const float m32 = krp_secant32(sf, 0.0f, f32_mu_plus(sf), 8, nf32);
           const float isl = krp_islope32(sf, m32, nf32);
           bool fb;
-          r = krp_polish(k.s, P, (double)m32, (double)isl, a, b, Ga, Gb, mu, its, fb);
+          r = krp_polish(k.s, P, f64_of(m32), f64_of(isl), a, b, Ga, Gb, mu, its, fb);
           nfb += fb ? 1u : 0u;
         } else {
           const bool warm = guess > 0.0 && guess <= 1.0;

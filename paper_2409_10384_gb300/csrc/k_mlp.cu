@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(128) k_krp_seed(Par P, KrpBuf kb, float delta,
     double a = 0.0, b = 1.0, Ga = -1.0, Gb = 1.0, mu = 0.0;
     int its = 0;
     bool fb;
-    const int r = krp_polish(s, P, (double)m32, (double)isl, a, b, Ga, Gb, mu, its, fb);
+    const int r = krp_polish(s, P, f64_of(m32), f64_of(isl), a, b, Ga, Gb, mu, its, fb);
     s_fb += fb ? 1u : 0u;
     kb.w[KW_A * n + i] = a; kb.w[KW_B * n + i] = b;
     kb.w[KW_GA * n + i] = Ga; kb.w[KW_GB * n + i] = Gb;
