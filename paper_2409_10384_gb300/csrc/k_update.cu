@@ -91,32 +91,30 @@ __device__ __forceinline__ void sources(const DevBlock& b, const Par& P, int k, 
   double w[3] = {pr[nc + c], pr[2 * nc + c], pr[3 * nc + c]};
   double wl[3];
   lower3(m.g, w, wl);
-  double W2 = 1.0 + dot3(w, wl);
-  double iW = rsqrt(W2);
-  double W = W2 * iW;
-  double v[3] = {w[0] * iW, w[1] * iW, w[2] * iW};
-  double vl[3] = {wl[0] * iW, wl[1] * iW, wl[2] * iW};
+  const double iW = rsqrt(1.0 + dot3(w, wl));
   double B[3] = {b.bcc[c] * m.isdet, b.bcc[nc + c] * m.isdet, b.bcc[2 * nc + c] * m.isdet};
   double Bl[3];
   lower3(m.g, B, Bl);
-  double B2 = dot3(B, Bl), Bv = dot3(B, vl);
-  double b2 = fma(B2, iW * iW, Bv * Bv);
-  double rhoh = P.eos == 0 ? fma(P.gfac, p, rho) : eos_rhoh(P, rho, p);
-  double Ptot = fma(0.5, b2, p);
-  double WBv = W * Bv;
-  double bb[3] = {fma(WBv, v[0], B[0] * iW), fma(WBv, v[1], B[1] * iW), fma(WBv, v[2], B[2] * iW)};
-  double e = (rhoh + b2) * W2;
-  // densitised S^{ij}
+  const double B2 = dot3(B, Bl), Bv = dot3(B, wl) * iW;   // B.v, with v_i = w_i / W
+  const double b2 = fma(B2, iW * iW, Bv * Bv);
+  const double rhoh = P.eos == 0 ? fma(P.gfac, p, rho) : eos_rhoh(P, rho, p);
+  const double Ptot = fma(0.5, b2, p);
+  // b^i = B^i/W + W (B.v) v^i = B^i/W + (B.v) w^i, and (rho h + b^2) W^2 v^i v^j
+  // = (rho h + b^2) w^i w^j, with w^i = W v^i: no v^i or W needed
+  const double bb[3] = {fma(Bv, w[0], B[0] * iW), fma(Bv, w[1], B[1] * iW), fma(Bv, w[2], B[2] * iW)};
+  const double eh = rhoh + b2;
+  // S^{ij} / sqrt(gamma); sqrt(gamma) rides in the coefficients of the contractions below
   double S[6];
   const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll
   for (int q = 0; q < 6; q++)
-    S[q] = m.sdet * fma(e * v[ia[q]], v[ib[q]], fma(Ptot, m.gi[q], -bb[ia[q]] * bb[ib[q]]));
+    S[q] = fma(eh * w[ia[q]], w[ib[q]], fma(Ptot, m.gi[q], -bb[ia[q]] * bb[ib[q]]));
   const double* U = b.cons;
   double Sl[3] = {U[nc + c], U[2 * nc + c], U[3 * nc + c]};
   double Su[3];
   lower3(m.gi, Sl, Su);
   double E = U[4 * nc + c] + U[c];
+  const double has = (0.5 * alpha) * m.sdet;   // alpha sqrt(gamma) / 2
   G[0] = 0.0;
   // S^{jk} d_i gamma_jk with the off-diagonal terms counted twice
 #pragma unroll
@@ -124,11 +122,11 @@ __device__ __forceinline__ void sources(const DevBlock& b, const Par& P, int k, 
     double t = S[0] * dg[a][0] + S[3] * dg[a][3] + S[5] * dg[a][5] +
                2.0 * (S[1] * dg[a][1] + S[2] * dg[a][2] + S[4] * dg[a][4]);
     double s2 = dot3(Sl, dbe[a]);
-    G[1 + a] = fma(0.5 * alpha, t, fma(-E, dal[a], s2));
+    G[1 + a] = fma(has, t, fma(-E, dal[a], s2));
   }
   const double* K = A + 10 * nc + c;
   double kt = S[0] * K[0] + S[3] * K[3 * nc] + S[5] * K[5 * nc] + 2.0 * (S[1] * K[nc] + S[2] * K[2 * nc] + S[4] * K[4 * nc]);
-  G[4] = fma(alpha, kt, -dot3(Su, dal));
+  G[4] = fma(2.0 * has, kt, -dot3(Su, dal));
 }
 
 __global__ void __launch_bounds__(256) k_update_cells(Work w, Par P, double g0, double g1, double bdt, int first) {
