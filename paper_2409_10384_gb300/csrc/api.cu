@@ -187,17 +187,6 @@ int fill_par(const mhd_params* p, Par& P, bool allow_guess) {
 
 namespace {
 
-int tkind_items(int k) {
-  switch (k) {
-    case T_C2P_PREP: case T_C2P_FIN: return W_C2P;
-    case T_FX: return W_SX;
-    case T_FY: return W_SY;
-    case T_FZ: return W_SZ;
-    case T_FOFC_PREP: case T_FOFC_FIN: case T_UPD: return W_CELL;
-    default: return W_EDGE;
-  }
-}
-
 int set_par(mhd_ctx* c, const mhd_params* p) {
   Par P;
   const int r = fill_par(p, P, true);

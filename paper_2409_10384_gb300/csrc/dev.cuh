@@ -448,13 +448,6 @@ __device__ __forceinline__ double eos_rhoh(const Par& P, double rho, double p) {
   eos_hyb_rhoh_chi(P, rho, p, Pc, epsc, Gi, rhoh, chi);
   return rhoh;
 }
-// pressure of the temperature floor at rho: P_c(rho) + rho T_atm
-__device__ __forceinline__ double eos_pfloor(const Par& P, double rho) {
-  if (P.eos == 0) return rho * P.T_atm;
-  double Pc, epsc, Gi;
-  eos_cold(P, rho, Pc, epsc, Gi);
-  return fma(rho, P.T_atm, Pc);
-}
 
 // ----------------------------------------------------- prim -> cons (Eq. 6)
 // prim = rho, w^i = W v^i, P;  Bd = densitised B~;  out = D~, S~_i, tau~.

@@ -41,7 +41,6 @@ __device__ __forceinline__ Iv iv_d(double x) {
 
 __device__ __forceinline__ Iv iadd(Iv a, Iv b) { return {__fadd_rd(a.lo, b.lo), __fadd_ru(a.hi, b.hi)}; }
 __device__ __forceinline__ Iv isub(Iv a, Iv b) { return {__fsub_rd(a.lo, b.hi), __fsub_ru(a.hi, b.lo)}; }
-__device__ __forceinline__ Iv ineg(Iv a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ Iv imul(Iv a, Iv b) {
   const float p = __fmul_rd(a.lo, b.lo), q = __fmul_rd(a.lo, b.hi), r = __fmul_rd(a.hi, b.lo),
               t = __fmul_rd(a.hi, b.hi);
@@ -53,8 +52,6 @@ __device__ __forceinline__ Iv imul(Iv a, Iv b) {
 __device__ __forceinline__ Iv imulp(Iv a, Iv b) {
   return {__fmul_rd(a.lo, a.lo >= 0.0f ? b.lo : b.hi), __fmul_ru(a.hi, a.hi >= 0.0f ? b.hi : b.lo)};
 }
-// a, b >= 0
-__device__ __forceinline__ Iv imulpp(Iv a, Iv b) { return {__fmul_rd(a.lo, b.lo), __fmul_ru(a.hi, b.hi)}; }
 // c >= 0 a point
 __device__ __forceinline__ Iv iscale(Iv a, float c) { return {__fmul_rd(a.lo, c), __fmul_ru(a.hi, c)}; }
 __device__ __forceinline__ Iv isq(Iv a) {
