@@ -1063,6 +1063,26 @@ static real upwind(real fD, real lowv, real highv) {
   return 0.5 * (lowv + highv);
 }
 
+// The upwind CT value of one edge (A-1/2, B-1/2) in the (a,b) plane of the edge:
+// the mean of its four face values plus, along each axis, the difference of the
+// EMF's derivatives a quarter and three quarters of a cell from the edge, each
+// taken from the cell upwind by the mass flux of the face it lies on (their mean
+// on a zero flux).
+// e = {E_af(A-1/2,B), E_af(A-1/2,B-1), E_bf(A,B-1/2), E_bf(A-1,B-1/2),
+//      E_cc(A,B), E_cc(A-1,B), E_cc(A,B-1), E_cc(A-1,B-1)},
+// f = mass fluxes {F^a_D(A-1/2,B), F^a_D(A-1/2,B-1), F^b_D(A,B-1/2), F^b_D(A-1,B-1/2)}.
+static real edge_emf(const real e[8], const real f[4]) {
+  const real Eaf_B = e[0], Eaf_Bm = e[1], Ebf_A = e[2], Ebf_Am = e[3];
+  const real E_AB = e[4], E_AmB = e[5], E_ABm = e[6], E_AmBm = e[7];
+  // derivatives along b near the a-faces, upwinded across a
+  real dEb_q = upwind(f[0], E_AmB - Ebf_Am, E_AB - Ebf_A);       // at B-1/4
+  real dEb_tq = upwind(f[1], Ebf_Am - E_AmBm, Ebf_A - E_ABm);    // at B-3/4
+  // derivatives along a near the b-faces, upwinded across b
+  real dEa_q = upwind(f[2], E_ABm - Eaf_Bm, E_AB - Eaf_B);       // at A-1/4
+  real dEa_tq = upwind(f[3], Eaf_Bm - E_AmBm, Eaf_B - E_AmB);    // at A-3/4
+  return 0.25 * (Eaf_B + Eaf_Bm + Ebf_A + Ebf_Am) + 0.25 * (dEb_tq - dEb_q) + 0.25 * (dEa_tq - dEa_q);
+}
+
 // Upwind constrained transport (Sec. 3.2; Gardiner & Stone 2005): edge EMF of
 // component cc at the edge (A-1/2, B-1/2, C) in the plane of axes a=(cc+1)%3,
 // b=(cc+2)%3.  On a-faces E_cc = -F_a[t1 comp], on b-faces E_cc = +F_b[t2 comp].
@@ -1112,14 +1132,9 @@ static void compute_emf(Ctx& C, std::vector<double> flux[3], std::vector<double>
           real E_ABm = ecc[cc * G.ncell + G.c(kk, jj, ii)];
           at(-1, -1, kk, jj, ii);
           real E_AmBm = ecc[cc * G.ncell + G.c(kk, jj, ii)];
-          // derivatives along b near the a-faces, upwinded across a
-          real dEb_q = upwind(fDa_B, E_AmB - Ebf_Am, E_AB - Ebf_A);       // at B-1/4
-          real dEb_tq = upwind(fDa_Bm, Ebf_Am - E_AmBm, Ebf_A - E_ABm);   // at B-3/4
-          // derivatives along a near the b-faces, upwinded across b
-          real dEa_q = upwind(fDb_A, E_ABm - Eaf_Bm, E_AB - Eaf_B);       // at A-1/4
-          real dEa_tq = upwind(fDb_Am, Eaf_Bm - E_AmBm, Eaf_B - E_AmB);   // at A-3/4
-          real E = 0.25 * (Eaf_B + Eaf_Bm + Ebf_A + Ebf_Am) + 0.25 * (dEb_tq - dEb_q) + 0.25 * (dEa_tq - dEa_q);
-          emf[cc][G.e(cc, k, j, i)] = val(E);
+          const real e8[8] = {Eaf_B, Eaf_Bm, Ebf_A, Ebf_Am, E_AB, E_AmB, E_ABm, E_AmBm};
+          const real f4[4] = {fDa_B, fDa_Bm, fDb_A, fDb_Am};
+          emf[cc][G.e(cc, k, j, i)] = val(edge_emf(e8, f4));
         }
   }
 }
@@ -1512,18 +1527,13 @@ void or_face_flux(const or_params* p, int d, const double* L7, const double* R7,
   for (int v = 0; v < 7; v++) F7[v] = val(F[v]);
 }
 
-// Upwind CT edge value from its neighbourhood, in the (a,b) plane of the edge:
-// e8 = {E_af(A-1/2,B), E_af(A-1/2,B-1), E_bf(A,B-1/2), E_bf(A-1,B-1/2),
-//       E_cc(A,B), E_cc(A-1,B), E_cc(A,B-1), E_cc(A-1,B-1)},
-// f4 = mass fluxes {F^a_D(A-1/2,B), F^a_D(A-1/2,B-1), F^b_D(A,B-1/2), F^b_D(A-1,B-1/2)}.
+// Upwind CT edge value from its neighbourhood (the stage's own edge function);
+// e8 and f4 as for edge_emf.
 double or_emf_edge(const double* e8, const double* f4) {
-  real Eaf_B = e8[0], Eaf_Bm = e8[1], Ebf_A = e8[2], Ebf_Am = e8[3];
-  real E_AB = e8[4], E_AmB = e8[5], E_ABm = e8[6], E_AmBm = e8[7];
-  real dEb_q = upwind(f4[0], E_AmB - Ebf_Am, E_AB - Ebf_A);
-  real dEb_tq = upwind(f4[1], Ebf_Am - E_AmBm, Ebf_A - E_ABm);
-  real dEa_q = upwind(f4[2], E_ABm - Eaf_Bm, E_AB - Eaf_B);
-  real dEa_tq = upwind(f4[3], Eaf_Bm - E_AmBm, Eaf_B - E_AmB);
-  return val(0.25 * (Eaf_B + Eaf_Bm + Ebf_A + Ebf_Am) + 0.25 * (dEb_tq - dEb_q) + 0.25 * (dEa_tq - dEa_q));
+  real e[8], f[4];
+  for (int q = 0; q < 8; q++) e[q] = e8[q];
+  for (int q = 0; q < 4; q++) f[q] = f4[q];
+  return val(edge_emf(e, f));
 }
 
 // Algorithmic FP64 operation counts (only meaningful in the counting build):

@@ -238,6 +238,54 @@ MUTATIONS = [
     ('stage 0 keeps no U^n',
      '          if (first) C.b->cons0[v * G.ncell + c] = C.b->cons[v * G.ncell + c];',
      '          if (false) C.b->cons0[v * G.ncell + c] = C.b->cons[v * G.ncell + c];'),
+    ('p2c D without W',
+     'real D = rho * W;\n  out[0]',
+     'real D = rho;\n  out[0]'),
+    ('p2c S drops Bv B_i',
+     'out[1 + i] = sdet * ((rhohW2 + B2) * vl[i] - Bv * Bl[i]);',
+     'out[1 + i] = sdet * ((rhohW2 + B2) * vl[i]);'),
+    ('p2c tau keeps D',
+     '- D);',
+     ');'),
+    ('metric det middle sign',
+     '- g[1] * (g[1] * g[5] - g[4] * g[2])',
+     '+ g[1] * (g[1] * g[5] - g[4] * g[2])'),
+    ('metric lower y index',
+     'out[1] = g[1] * in[0] + g[3] * in[1] + g[4] * in[2];',
+     'out[1] = g[1] * in[0] + g[3] * in[1] + g[2] * in[2];'),
+    ('krp rbar2 (1+x) factor',
+     'mu * e.x * (1.0 + e.x) * s.rb2;',
+     'mu * e.x * 2.0 * s.rb2;'),
+    ('krp qbar perp sign',
+     '- 0.5 * mu * mu * e.x * e.x * s.rperp2;',
+     '+ 0.5 * mu * mu * e.x * e.x * s.rperp2;'),
+    ('krp eps_raw drops v^2 W^2 term',
+     '+ e.vhat2 * e.What * e.What / (1.0 + e.What);',
+     ';'),
+    ('krp nuA drops 1/W',
+     '(1.0 + ahat) * (1.0 + e.eps) / e.What;',
+     '(1.0 + ahat) * (1.0 + e.eps);'),
+    ('krp rhohat times W',
+     'e.rhohat = s.D / e.What;',
+     'e.rhohat = s.D * e.What;'),
+    ('flux divergence sign',
+     'r = r - (fp - fm) / C.b->dx[d];',
+     'r = r + (fp - fm) / C.b->dx[d];'),
+    ('face B update sign',
+     'bnew = bnew - bdt * curl;',
+     'bnew = bnew + bdt * curl;'),
+    ('CT upwind tie takes one side',
+     'return 0.5 * (lowv + highv);',
+     'return lowv;'),
+    ('CT a-derivative weight',
+     '+ 0.25 * (dEa_tq - dEa_q);',
+     '+ 0.5 * (dEa_tq - dEa_q);'),
+    ('CT b-derivative operand order',
+     'real dEb_tq = upwind(f[1], Ebf_Am - E_AmBm, Ebf_A - E_ABm);',
+     'real dEb_tq = upwind(f[1], Ebf_A - E_ABm, Ebf_Am - E_AmBm);'),
+    ('mu_plus start from r^2',
+     'real rpar2 = s.b2 > 0.0 ? s.rb2 / s.b2 : s.r2;',
+     'real rpar2 = s.r2;'),
 ]
 
 # nu = max(nu_A, nu_B) in the master function: with eps_raw as defined and

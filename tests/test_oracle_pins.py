@@ -373,6 +373,25 @@ def test_c2p_master_function_vanishes_at_one_over_hW():
         assert abs(f) <= 1e-11 * mu, (c, f, mu)
 
 
+def test_c2p_bracket_top_lies_above_the_root():
+    """The bracket's upper end mu+ of Kastaun et al. (2021), used by the
+    recovery of Sec. 3.4, bounds the root from above: mu+ >= 1/(h W) of the
+    state behind the conserved variables, and f(mu+) >= 0 > f(0).  On cold
+    magnetised cells the two are within 1e-9 of each other."""
+    p, prim, Bd, g, cons = _stress(300, seed=7)
+    gaps = []
+    for c in range(300):
+        rho, w, P = prim[0, c], prim[1:4, c], prim[4, c]
+        gg = np.array([[g[0, c], g[1, c], g[2, c]], [g[1, c], g[3, c], g[4, c]], [g[2, c], g[4, c], g[5, c]]])
+        W = np.sqrt(1 + w @ gg @ w)
+        h = 1 + p.gamma / (p.gamma - 1) * P / rho
+        mu = 1.0 / (h * W)
+        _, (mu_plus, f0, f_plus) = O.c2p_master(p, cons[:, c], Bd[:, c], g[:, c], mu)
+        assert mu_plus >= mu * (1 - 1e-12) and f_plus >= 0.0 > f0, (c, mu_plus, mu, f0, f_plus)
+        gaps.append(mu_plus / mu - 1)
+    assert min(gaps) < 1e-6   # the bound is tight on some cells
+
+
 def test_c2p_bruteforce_bisection():
     """Brute force: bisection of f to machine precision inside [0, 1] agrees with
     the solver's root; the solver's bracket ends have the right signs."""
@@ -916,9 +935,77 @@ def test_emf_edge_exact_for_quadratic_upwind():
           E2(A, B), E2(A - 1, B), E2(A, B - 1), E2(A - 1, B - 1)]
     got = O.emf_edge(e8, [1.0, 1.0, -1.0, -1.0])
     assert abs(got - E2(A - 0.5, B - 0.5)) < 1e-13
+    # ties: on data whose two upwind choices differ, a zero mass flux takes
+    # their mean, so the value is the mean of the two fully upwinded ones
+    e8 = np.random.default_rng(3).normal(size=8)
     z = O.emf_edge(e8, [0.0, 0.0, 0.0, 0.0])
-    avg = 0.5 * (O.emf_edge(e8, [1.0, 1.0, 1.0, 1.0]) + O.emf_edge(e8, [-1.0, -1.0, -1.0, -1.0]))
-    assert abs(z - avg) < 1e-13
+    up, dn = O.emf_edge(e8, [1.0, 1.0, 1.0, 1.0]), O.emf_edge(e8, [-1.0, -1.0, -1.0, -1.0])
+    assert abs(up - dn) > 0.1 and abs(z - 0.5 * (up + dn)) < 1e-13
+
+
+def _edge_rows(rng, n):
+    """Random edge neighbourhoods (the 8 EMF values) and mass fluxes with
+    every sign, a third of them exactly zero."""
+    e8 = rng.normal(size=(n, 8))
+    f4 = rng.normal(size=(n, 4)) * rng.integers(0, 3, size=(n, 4))
+    return e8, f4
+
+
+def test_emf_edge_reduces_to_the_face_value_for_plane_parallel_data():
+    """Gardiner & Stone (2005) build the upwind CT EMF so that it reduces to
+    the 1D face flux when nothing varies along one of the two axes (Sec. 3.2):
+    with data that depend on a alone, the b-faces carry the value of their own
+    column (a Riemann problem between equal states) and the edge takes the
+    a-face value, whatever that value and the mass fluxes are; the same with a
+    and b exchanged."""
+    rng = np.random.default_rng(11)
+    for _ in range(200):
+        Ef, EA, EAm = rng.normal(size=3)
+        f4 = rng.normal(size=4) * rng.integers(0, 3, size=4)
+        got = O.emf_edge([Ef, Ef, EA, EAm, EA, EAm, EA, EAm], f4)
+        assert abs(got - Ef) < 1e-14 * (1 + abs(EA) + abs(EAm) + abs(Ef))
+        Eg, EB, EBm = rng.normal(size=3)
+        got = O.emf_edge([EB, EBm, Eg, Eg, EB, EB, EBm, EBm], f4)
+        assert abs(got - Eg) < 1e-14 * (1 + abs(EB) + abs(EBm) + abs(Eg))
+
+
+def test_emf_edge_mirror_and_axis_swap_symmetry():
+    """The edge EMF's own component is unchanged by a mirror across either axis
+    of its plane and by the exchange of the two axes, while every mass flux
+    normal to the mirror changes sign: the upwind value must map the same way
+    (Sec. 3.2), ties included."""
+    e8, f4 = _edge_rows(np.random.default_rng(12), 400)
+    for e, f in zip(e8, f4):
+        E = O.emf_edge(e, f)
+        Eaf_B, Eaf_Bm, Ebf_A, Ebf_Am, E_AB, E_AmB, E_ABm, E_AmBm = e
+        mir_a = O.emf_edge([Eaf_B, Eaf_Bm, Ebf_Am, Ebf_A, E_AmB, E_AB, E_AmBm, E_ABm], [-f[0], -f[1], f[3], f[2]])
+        mir_b = O.emf_edge([Eaf_Bm, Eaf_B, Ebf_A, Ebf_Am, E_ABm, E_AmBm, E_AB, E_AmB], [f[1], f[0], -f[2], -f[3]])
+        swap = O.emf_edge([Ebf_A, Ebf_Am, Eaf_B, Eaf_Bm, E_AB, E_ABm, E_AmB, E_AmBm], [f[2], f[3], f[0], f[1]])
+        tol = 1e-14 * np.abs(e).sum()
+        assert abs(mir_a - E) < tol and abs(mir_b - E) < tol and abs(swap - E) < tol, (e, f)
+
+
+def test_emf_edge_ignores_the_cell_downwind_along_both_axes():
+    """Upwinding (Sec. 3.2): when the mass fluxes through all four faces of
+    the edge point the same way along a and along b, the cell downwind of the
+    edge along both axes enters only the face values, never the edge's own
+    sum: changing its centred EMF leaves the edge value unchanged."""
+    rng = np.random.default_rng(13)
+    # position in e8 of E_cc at (A or A-1, B or B-1) for flow signs (sa, sb)
+    down = {(1, 1): 4, (-1, 1): 5, (1, -1): 6, (-1, -1): 7}
+    for _ in range(100):
+        e = rng.normal(size=8)
+        for (sa, sb), q in down.items():
+            f = np.abs(rng.normal(size=4)) + 0.1
+            f[:2] *= sa
+            f[2:] *= sb
+            e2 = e.copy()
+            e2[q] += rng.normal() * 10.0
+            assert abs(O.emf_edge(e2, f) - O.emf_edge(e, f)) < 1e-13 * np.abs(e2).sum(), (sa, sb)
+            # the cell upwind along both axes does enter it
+            e3 = e.copy()
+            e3[{4: 7, 5: 6, 6: 5, 7: 4}[q]] += 1.0
+            assert abs(O.emf_edge(e3, f) - O.emf_edge(e, f)) > 0.1
 
 
 def test_flop_counting_build_matches_plain_build():
