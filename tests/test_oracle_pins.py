@@ -101,6 +101,36 @@ def test_speeds_velocity_addition_lapse_shift():
         assert abs(sp[1] - (alpha * lp - bx)) < 1e-13
 
 
+def test_speeds_fluid_at_rest_in_a_curved_metric():
+    """A magnetised fluid at rest in the Eulerian frame, in a curved spatial
+    metric: a wave of speed c_f in that frame crosses the surfaces x^d = const
+    along their unit normal, whose contravariant d component is
+    sqrt(gamma^dd), so the coordinate speeds are +-alpha c_f sqrt(gamma^dd) -
+    beta^d (Eq. 5).  c_f is the fast magnetosonic speed across the field,
+    c_f^2 = c_s^2 + v_A^2 - c_s^2 v_A^2, with c_s^2 = Gamma P/(rho h) and
+    v_A^2 = b^2/(rho h + b^2), b^2 = gamma_ij B^i B^j for a fluid at rest."""
+    gam = 5.0 / 3.0
+    p = O.params(gamma=gam)
+    rng = np.random.default_rng(15)
+    for _ in range(100):
+        a, be, g6 = rand_metric(rng)
+        gm = np.array([[g6[0], g6[1], g6[2]], [g6[1], g6[3], g6[4]], [g6[2], g6[4], g6[5]]])
+        gi = np.linalg.inv(gm)
+        sg = np.sqrt(np.linalg.det(gm))
+        rho, P = 10 ** rng.uniform(-2, 0), 10 ** rng.uniform(-2, 0)
+        Bd = rng.normal(scale=0.5, size=3)
+        B = Bd / sg
+        b2 = B @ gm @ B
+        h = 1 + gam / (gam - 1) * P / rho
+        cs2, va2 = gam * P / (rho * h), b2 / (rho * h + b2)
+        cf = np.sqrt(cs2 + va2 - cs2 * va2)
+        for d in range(3):
+            t1, t2 = (d + 1) % 3, (d + 2) % 3
+            _, _, sp = O.face_side(p, d, [rho, 0.0, 0.0, 0.0, P, Bd[t1], Bd[t2]], Bd[d], [a, *be, *g6])
+            half = a * cf * np.sqrt(gi[d, d])
+            assert abs(sp[0] - (-half - be[d])) < 1e-13 and abs(sp[1] - (half - be[d])) < 1e-13, (d, sp)
+
+
 @pytest.mark.parametrize("rs", [0, 1])
 def test_riemann_consistency_equal_states(rs):
     """An approximate Riemann solver returns the physical flux when U_L = U_R
@@ -430,9 +460,10 @@ def test_c2p_unmagnetised_reduces_to_hydro():
     assert np.all(np.abs(r["prim"][4] - prim[4]) <= _P_tol(p, cons, g, prim[4]))
 
 
-def test_c2p_floors_and_failures():
-    """Sec. 3.3 atmosphere policy and the error policy, per case."""
-    gam = 2.0
+@pytest.mark.parametrize("gam", [2.0, 5.0 / 3.0])
+def test_c2p_floors_and_failures(gam):
+    """Sec. 3.3 atmosphere policy and the error policy, per case (Gamma = 2,
+    where Gamma - 1 = 1 hides a misplaced factor, and 5/3)."""
     p = O.params(gamma=gam, rho_atm=1e-10, T_atm=1e-8, f_thr=1.0)
     g = np.array([[1.0], [0], [0], [1.0], [0], [1.0]])
     Bd = np.array([[0.0], [1e-6], [0.0]])
@@ -466,14 +497,15 @@ def test_c2p_floors_and_failures():
     assert abs(r["prim"][1, 0] - 0.3) < 1e-6
 
 
-def test_c2p_floors_with_a_field_closed_forms():
+@pytest.mark.parametrize("gam", [2.0, 5.0 / 3.0])
+def test_c2p_floors_with_a_field_closed_forms(gam):
     """Sec. 3.3 floors in flat space (D~ = D, B^2 = sum B~_i^2) with a field
     that matters: the magnetisation cap sets D = B^2/sigma_max; the tau floor
     sets tau = D T_atm/(Gamma - 1) + B^2/2 (also for a tau above the first
     term alone); the density floor resets to
     rho_atm at rest with tau = rho_atm T_atm/(Gamma - 1) + B^2/2, which needs
     no further tau floor."""
-    gam, T = 2.0, 1e-8
+    T = 1e-8
     g = np.array([[1.0], [0], [0], [1.0], [0], [1.0]])
     p = O.params(gamma=gam, rho_atm=1e-12, T_atm=T, f_thr=1.0, sigma_max=50.0)
     Bd = np.array([[0.5], [0.0], [0.0]])
@@ -494,6 +526,15 @@ def test_c2p_floors_with_a_field_closed_forms():
     assert r["flags"][0] & O.F_DFLOOR and not r["flags"][0] & (O.F_TAU | O.F_FAIL)
     assert abs(r["cons"][4, 0] - tau) <= 1e-15 * tau and r["cons"][0, 0] == 1e-12
     assert np.all(r["prim"][1:4, 0] == 0.0)
+    # the tau floor's threshold itself, at rest without a field: 10% below
+    # D T_atm/(Gamma - 1) is floored, 10% above is a valid state at 1.1 T_atm
+    # (the post-solve floor would hide a wrong threshold in the prims)
+    Bd = np.zeros((3, 1))
+    for f, floored in ((0.9, True), (1.1, False)):
+        r = O.c2p_cells(p, np.array([[1e-3], [0.0], [0.0], [0.0], [f * 1e-3 * T / (gam - 1.0)]]), Bd, g)
+        assert bool(r["flags"][0] & O.F_TAU) == floored and not r["flags"][0] & O.F_FAIL, (f, r["flags"][0])
+        assert not floored or not r["flags"][0] & O.F_TEMP
+        assert floored or abs(r["prim"][4, 0] / r["prim"][0, 0] - 1.1 * T) <= 1e-9 * T
 
 
 def test_c2p_cold_dust_root_at_the_bracket_end():
@@ -809,6 +850,60 @@ def test_fofc_mask_gives_donor_fluxes_on_exactly_those_faces():
             a = om["flux"][d][c]
             assert np.array_equal(a[fm & computed], ol["flux"][d][c][fm & computed])
             assert np.array_equal(a[~fm], oh["flux"][d][c][~fm])
+
+
+def test_fofc_flags_the_cells_whose_unlimited_update_needs_a_floor():
+    """FOFC (Sec. 3.3) flags a cell when con2prim of the unlimited stage update
+    U* = g0 U^n + g1 U + b dt (-div F) fails or floors it.  In flat space with
+    no field the sources vanish exactly and the stage's B is irrelevant, so
+    U* is the cell's update by the stage without FOFC: at every stage of an
+    RK3 step on rough data (density over seven decades, temperature near the
+    floor), the flagged cells are exactly those whose unlimited update
+    con2prim floors or rejects."""
+    n, ng = 12, 4
+    N = n + 2 * ng
+    kw = dict(gamma=5.0 / 3.0, recon=2, rsolver=1, rk_order=3, rho_atm=1e-8, T_atm=1e-4, f_thr=1.0)
+    p1, p0 = O.params(fofc=1, **kw), O.params(fofc=0, **kw)
+    rng = np.random.default_rng(21)
+    rho = 10 ** rng.uniform(-7, 0, (N, N, N))
+    T = 10 ** rng.uniform(-4, -1, (N, N, N))
+    prim = np.stack([rho, *rng.normal(scale=0.4, size=(3, N, N, N)), rho * T])
+    adm = uniform_metric([N, N, N])
+    shape = O.new_block((n,) * 3, ng, (1.0,) * 3, adm)
+    b = O.init_block(p1, (n,) * 3, ng, (1.0,) * 3, adm, prim, [np.zeros(shape.edge_shape(c)) for c in range(3)])
+    I = interior(b)
+    m = n ** 3
+    flat = np.tile(np.array([[1.0], [0], [0], [1.0], [0], [1.0]]), (1, m))
+    for s in range(3):
+        bu = b.copy()
+        O.stage(p0, bu, 0.2, s)
+        r = O.c2p_cells(p1, bu.cons[(slice(None),) + I].reshape(5, m), np.zeros((3, m)), flat)
+        want = (r["flags"] & (O.F_FAIL | O.FLOOR_BITS)) != 0
+        O.stage(p1, b, 0.2, s)
+        got = (b.flags[I].reshape(m) & O.F_FOFC) != 0
+        assert want.sum() > 50 and np.array_equal(got, want), (s, int(want.sum()), int(got.sum()))
+        # floors alone, no failure, must flag a cell too
+        assert np.any(want & ((r["flags"] & O.F_FAIL) == 0))
+
+
+def test_fofc_flag_bit_marks_only_the_latest_stage():
+    """The F_FOFC bit of a cell records whether the last stage flagged it: a
+    cell flagged by one stage and not by the next loses the bit."""
+    p = O.params(gamma=5.0 / 3.0, recon=2, rsolver=1, rk_order=2, fofc=1)
+    b = _periodic_block(p)
+    N = b.cons.shape[1:]
+    I = interior(b)
+    rng = np.random.default_rng(4)
+    masks = []
+    for _ in range(2):
+        m = np.zeros(N, np.uint8)
+        sub = m[I]
+        sub[rng.random(sub.shape) < 0.1] = 1
+        m[I] = sub
+        masks.append(m)
+    for s, m in enumerate(masks):
+        O.stage(p, b, 0.25 / 32, s, mask=m)
+        assert np.array_equal((b.flags[I] & O.F_FOFC) != 0, m[I] != 0), s
 
 
 def test_dmp_truth_table_and_infinite_M():
