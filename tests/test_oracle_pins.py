@@ -593,14 +593,14 @@ def test_face_floor_density_threshold():
 
 # ------------------------------------------------------------- stage level
 
-def _small_block(p, n, adm, prim_cell, Bd):
+def _small_block(p, n, adm, prim_cell, Bd, dx=(0.1, 0.1, 0.1)):
     N = [x + 8 for x in n]
     prim = np.zeros((5, N[2], N[1], N[0]))
     for v in range(5):
         prim[v] = prim_cell[v]
     bf = [np.full((N[2], N[1], N[0] + 1), Bd[0]), np.full((N[2], N[1] + 1, N[0]), Bd[1]),
           np.full((N[2] + 1, N[1], N[0]), Bd[2])]
-    return init_from_faces(O, p, n, 4, (0.1, 0.1, 0.1), adm, prim, bf)
+    return init_from_faces(O, p, n, 4, dx, adm, prim, bf)
 
 
 @pytest.mark.parametrize("recon,rs", [(1, 1), (2, 0), (2, 1)])
@@ -690,12 +690,13 @@ def test_sources_match_covariant_form():
     """Eq. 9 against the covariant sources: S~_i gets (1/2) sqrt(-g) T^{mu nu}
     d_i g_{mu nu}; tau~ gets sqrt(-g)(K_ij S^ij - S^i d_i alpha / alpha), with
     S^ij, S^i the spatial projections of T.  Linear ADM fields make the centred
-    differences exact."""
+    differences exact.  The cells have three different sides, so each
+    derivative and each flux difference must use its own axis's spacing."""
     p = O.params(gamma=5.0 / 3.0, recon=0, rsolver=1, rk_order=2)
     n = (3, 3, 3)
     N = [x + 8 for x in n]
-    dx = (0.1, 0.1, 0.1)
-    z, y, x = np.meshgrid(*[(np.arange(Nd) - 4 + 0.5) * dx[0] for Nd in N[::-1]], indexing="ij")
+    dx = (0.1, 0.07, 0.13)
+    z, y, x = np.meshgrid(*[(np.arange(N[2 - a]) - 4 + 0.5) * dx[2 - a] for a in range(3)], indexing="ij")
     ga = dict(alpha=(0.8, 0.03, -0.02, 0.01), b1=(0.1, 0.02, 0.0, -0.01), b2=(-0.05, 0.0, 0.03, 0.01),
               b3=(0.02, -0.01, 0.01, 0.02))
     gl = [(1.1, 0.02, 0.01, -0.01), (0.05, 0.0, 0.01, 0.0), (-0.02, 0.01, 0.0, 0.01),
@@ -709,7 +710,7 @@ def test_sources_match_covariant_form():
         adm[4 + c] = lin(gl[c])
         adm[10 + c] = K6[c]
     rho, w, P, Bd = 0.5, np.array([0.2, -0.3, 0.1]), 0.3, np.array([0.2, 0.1, -0.3])
-    b = _small_block(p, n, adm, [rho, *w, P], Bd)
+    b = _small_block(p, n, adm, [rho, *w, P], Bd, dx)
     U0 = b.cons.copy()
     dt = 1e-3
     out = O.stage(p, b, dt, 0, keep=True)
@@ -783,6 +784,64 @@ def test_ssp_rk_amplification_factor(order):
 def _periodic_block(p):
     inp = synth.periodic_flat(1)
     return O.init_block(p, inp.n, inp.ng, inp.dx, inp.adm, inp.prim, inp.A)
+
+
+def test_stage_keeps_div_b_on_cells_of_unequal_sides():
+    """CT (Sec. 3.2): each face B~ changes by the circulation of the edge EMFs
+    around it, so the discrete divergence of every cell whose six faces are
+    updated stays as it was, to round-off, whatever the EMFs are; on cells
+    with three different sides, provided each difference uses its own
+    axis's spacing."""
+    p = O.params(gamma=5.0 / 3.0, recon=2, rsolver=1, rk_order=3, fofc=1, rho_atm=1e-12, T_atm=1e-10)
+    n, ng, dx = (6, 5, 7), 4, (0.1, 0.07, 0.13)
+    N = [x + 2 * ng for x in n]
+    rng = np.random.default_rng(31)
+    prim = np.stack([rng.uniform(0.5, 1.5, N[::-1]), *rng.normal(scale=0.2, size=(3,) + tuple(N[::-1])),
+                     rng.uniform(0.1, 1.0, N[::-1])])
+    adm = uniform_metric(N)
+    shape = O.new_block(n, ng, dx, adm)
+    A = [rng.normal(scale=0.02, size=shape.edge_shape(c)) for c in range(3)]
+    b = O.init_block(p, n, ng, dx, adm, prim, A)
+    I = interior(b)
+    d0 = O.divb(b)[I]
+    Bs = max(np.abs(f).max() for f in b.bf) / min(dx)
+    for s in range(3):
+        O.stage(p, b, 0.01, s)
+        assert np.max(np.abs(O.divb(b)[I] - d0)) < 1e-13 * Bs, s
+    assert max(np.abs(f - g).max() for f, g in zip(b.bf, O.init_block(p, n, ng, dx, adm, prim, A).bf)) > 1e-4
+
+
+def test_face_metric_is_exact_for_cubic_fields_along_the_face_normal():
+    """The metric at a face is the four-point Lagrange interpolation along the
+    face normal (Sec. 3.2), exact for fields cubic along that axis: with every
+    ADM field a sum of cubics in x, y and z and a uniform state, each face's
+    flux is the physical flux of that state at the exact face metric."""
+    p = O.params(gamma=5.0 / 3.0, recon=2, rsolver=1, rk_order=2, rho_atm=1e-12, T_atm=1e-10)
+    n, dx = (4, 4, 4), (0.1, 0.07, 0.13)
+    N = [x + 8 for x in n]
+    rng = np.random.default_rng(32)
+    coef = rng.normal(scale=0.02, size=(10, 3, 3))   # [field][axis][power 1..3]
+    base = np.array([0.9, 0.05, -0.03, 0.02, 1.1, 0.05, -0.02, 0.95, 0.03, 1.2])
+
+    def field(q, pos):
+        return base[q] + sum(coef[q, a, e] * pos[a] ** (e + 1) for a in range(3) for e in range(3))
+
+    cz, cy, cx = np.meshgrid(*[(np.arange(N[2 - a]) - 4 + 0.5) * dx[2 - a] for a in range(3)], indexing="ij")
+    adm = np.zeros((16,) + cx.shape)
+    for q in range(10):
+        adm[q] = field(q, (cx, cy, cz))
+    rho, w, P, Bd = 0.5, np.array([0.2, -0.3, 0.1]), 0.3, np.array([0.2, 0.1, -0.3])
+    b = _small_block(p, n, adm, [rho, *w, P], Bd, dx)
+    out = O.stage(p, b, 1e-3, 0, keep=True)
+    for d in range(3):
+        t1, t2 = (d + 1) % 3, (d + 2) % 3
+        st = [rho, *w, P, Bd[t1], Bd[t2]]
+        for (k, j, i) in [(4, 4, 4), (5, 6, 7), (7, 5, 6)]:
+            idx = (i, j, k)
+            pos = [(idx[a] - 4 + (0.0 if a == d else 0.5)) * dx[a] for a in range(3)]
+            want = O.face_flux(p, d, st, st, Bd[d], [field(q, pos) for q in range(10)])
+            got = out["flux"][d][:, k, j, i]
+            assert np.max(np.abs(got - want)) < 1e-9 * np.abs(want).max(), (d, idx, got - want)
 
 
 def test_periodic_flat_conservation_and_divb():
