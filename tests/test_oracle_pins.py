@@ -811,6 +811,31 @@ def test_stage_keeps_div_b_on_cells_of_unequal_sides():
     assert max(np.abs(f - g).max() for f, g in zip(b.bf, O.init_block(p, n, ng, dx, adm, prim, A).bf)) > 1e-4
 
 
+def test_stage_ignores_the_primitives_and_cell_field_it_is_handed():
+    """Each stage starts from the conserved variables and the face B~ alone: it
+    averages the faces to the cell-centred B~ and runs con2prim over every
+    cell its stencils reach (Sec. 3.2, 3.4).  So a block whose primitive and
+    cell-centred field arrays hold garbage on entry gives the same stages,
+    bit for bit, as one whose arrays are consistent."""
+    p = O.params(gamma=5.0 / 3.0, recon=2, rsolver=1, rk_order=3, fofc=1, rho_atm=1e-12, T_atm=1e-10)
+    n, ng, dx = (6, 5, 7), 4, (0.1, 0.07, 0.13)
+    N = [x + 2 * ng for x in n]
+    rng = np.random.default_rng(33)
+    prim = np.stack([rng.uniform(0.5, 1.5, N[::-1]), *rng.normal(scale=0.2, size=(3,) + tuple(N[::-1])),
+                     rng.uniform(0.1, 1.0, N[::-1])])
+    adm = uniform_metric(N)
+    shape = O.new_block(n, ng, dx, adm)
+    A = [rng.normal(scale=0.02, size=shape.edge_shape(c)) for c in range(3)]
+    a = O.init_block(p, n, ng, dx, adm, prim, A)
+    b = a.copy()
+    b.prim[...] = rng.normal(size=b.prim.shape)
+    b.bcc[...] = rng.normal(size=b.bcc.shape)
+    for s in range(3):
+        O.stage(p, a, 0.01, s)
+        O.stage(p, b, 0.01, s)
+        assert np.array_equal(a.cons, b.cons) and all(np.array_equal(f, g) for f, g in zip(a.bf, b.bf)), s
+
+
 def test_face_metric_is_exact_for_cubic_fields_along_the_face_normal():
     """The metric at a face is the four-point Lagrange interpolation along the
     face normal (Sec. 3.2), exact for fields cubic along that axis: with every
