@@ -365,6 +365,31 @@ static real krp_mu_plus(const KRP& s) {
   return mu;
 }
 
+// The KRP variables of one cell from its undensitised D, S_i, tau and B^i
+// (B2 = B^i B_i): q = tau/D, r_i = S_i/D (raised to r^i), bb^i = B^i/sqrt(D),
+// r^2, bb^2 = B^2/D, r.bb, its square and the part of r^2 bb^2 across bb
+// (clamped at 0 against rounding); the EOS and the speed cap W_max.  Also
+// returns r^i and bb^i, from which the velocity is rebuilt at the root.
+static void krp_setup(const or_params& p, real eps_min, real D, const real Sl[3], real tau, const real B[3],
+                      real B2, const real gi[6], KRP& s, real ru[3], real bu[3]) {
+  s.D = D;
+  s.gam = p.gamma;
+  s.eps_min = eps_min;
+  s.hyb = p.eos ? &p : nullptr;
+  s.vmax2 = 1.0 - 1.0 / (p.W_max * p.W_max);
+  s.q = tau / D;
+  real rl[3] = {Sl[0] / D, Sl[1] / D, Sl[2] / D};
+  metric_apply(gi, rl, ru);
+  real sD = sqrt_(D);
+  for (int i = 0; i < 3; i++) bu[i] = B[i] / sD;
+  s.r2 = dot3(rl, ru);
+  s.b2 = B2 / D;
+  s.rb = dot3(rl, bu);
+  s.rb2 = s.rb * s.rb;
+  s.rperp2 = s.r2 * s.b2 - s.rb2;
+  if (s.rperp2 < 0.0) s.rperp2 = 0.0;
+}
+
 struct C2POut {
   real prim[5];
   int flags;
@@ -415,7 +440,6 @@ static void c2p_cell(const or_params& p, real cons[5], const real Bd[3], const r
   o.iters = 0;
   o.mu = 0.0;
   o.eps_margin = 0.0;
-  const real gam = p.gamma;
   real det = metric_det(g);
   real sdet = sqrt_(det);
   real gi[6];
@@ -460,23 +484,8 @@ static void c2p_cell(const or_params& p, real cons[5], const real Bd[3], const r
       o.flags |= F_TAU;
     }
     KRP s;
-    s.D = D;
-    s.gam = gam;
-    s.eps_min = eps_atm;
-    s.hyb = p.eos ? &p : nullptr;
-    s.vmax2 = 1.0 - 1.0 / (p.W_max * p.W_max);
-    s.q = tau / D;
-    real rl[3] = {Sl[0] / D, Sl[1] / D, Sl[2] / D};
-    real ru[3];
-    metric_apply(gi, rl, ru);
-    real sD = sqrt_(D);
-    real bu[3] = {B[0] / sD, B[1] / sD, B[2] / sD};
-    s.r2 = dot3(rl, ru);
-    s.b2 = B2 / D;
-    s.rb = dot3(rl, bu);
-    s.rb2 = s.rb * s.rb;
-    s.rperp2 = s.r2 * s.b2 - s.rb2;
-    if (s.rperp2 < 0.0) s.rperp2 = 0.0;
+    real ru[3], bu[3];
+    krp_setup(p, eps_atm, D, Sl, tau, B, B2, gi, s, ru, bu);
     // bracket [0, mu+]; if f(mu+) < 0 the root lies in [mu+, 1/h0] = [mu+, 1]
     KRPEval e0, e1;
     real a = 0.0, b = krp_mu_plus(s);
@@ -1344,25 +1353,11 @@ double or_c2p_master(const or_params* p, const double* cons5, const double* Bd3,
   real D = cons5[0] / sdet;
   real Sl[3] = {cons5[1] / sdet, cons5[2] / sdet, cons5[3] / sdet};
   real tau = cons5[4] / sdet;
-  real B[3] = {Bd3[0] / sdet, Bd3[1] / sdet, Bd3[2] / sdet};
+  real B[3] = {Bd3[0] / sdet, Bd3[1] / sdet, Bd3[2] / sdet}, Bl[3];
+  metric_apply(g, B, Bl);
   KRP s;
-  s.D = D;
-  s.gam = p->gamma;
-  s.eps_min = p->T_atm / (eos_gth(*p) - 1.0);
-  s.hyb = p->eos ? p : nullptr;
-  s.vmax2 = 1.0 - 1.0 / (p->W_max * p->W_max);
-  s.q = tau / D;
-  real rl[3] = {Sl[0] / D, Sl[1] / D, Sl[2] / D}, ru[3];
-  metric_apply(gi, rl, ru);
-  real sD = sqrt_(D);
-  real bu[3] = {B[0] / sD, B[1] / sD, B[2] / sD}, bl[3];
-  metric_apply(g, bu, bl);
-  s.r2 = dot3(rl, ru);
-  s.b2 = dot3(bu, bl);
-  s.rb = dot3(rl, bu);
-  s.rb2 = s.rb * s.rb;
-  s.rperp2 = s.r2 * s.b2 - s.rb2;
-  if (s.rperp2 < 0.0) s.rperp2 = 0.0;
+  real ru[3], bu[3];
+  krp_setup(*p, p->T_atm / (eos_gth(*p) - 1.0), D, Sl, tau, B, dot3(B, Bl), gi, s, ru, bu);
   KRPEval e;
   if (out3) {
     real mp = krp_mu_plus(s);
