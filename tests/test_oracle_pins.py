@@ -307,6 +307,46 @@ def test_ppm_convergence_through_smooth_extrema():
     assert err[4][-1] < 0.05 * err[3][-1]
 
 
+@pytest.mark.parametrize("recon", [0, 1, 2, 3, 4])
+def test_reconstruction_is_odd_and_scale_free(recon):
+    """Every reconstruction of Sec. 3.2 is odd and positively homogeneous in
+    the data: negating a line negates its face values exactly (rounding to
+    nearest is symmetric, and each limiter's branch for a minimum mirrors the
+    one for a maximum), and scaling it by 8 scales them by 8 (to the rounding
+    of WENO-Z's epsilon)."""
+    rng = np.random.default_rng(40 + recon)
+    for _ in range(200):
+        q = rng.normal(size=24) * 10 ** rng.uniform(-3, 3)
+        L, R = O.recon_line(recon, q)
+        Ln, Rn = O.recon_line(recon, -q)
+        f = np.isfinite(L)
+        assert np.array_equal(Ln[f], -L[f]) and np.array_equal(Rn[f], -R[f])
+        Ls, Rs = O.recon_line(recon, 8.0 * q)
+        s = np.abs(q).max()
+        assert np.max(np.abs(Ls[f] - 8.0 * L[f])) <= 1e-13 * 8.0 * s
+        assert np.max(np.abs(Rs[f] - 8.0 * R[f])) <= 1e-13 * 8.0 * s
+
+
+def test_ppmx_flattens_an_extremum_whose_curvatures_disagree():
+    """PPMX (Colella & Sekora 2008, cited in Sec. 3.2) keeps a parabola at an
+    extremum of the cell averages only where the second differences around
+    it share a sign (a smooth extremum); where they disagree the limited
+    curvature is zero and the cell reconstructs to its average, as donor
+    cell.  Here cell j is a strict maximum (or minimum) of its neighbours
+    while the curvature centred on j-1 has the other sign: both of its faces
+    must equal a_j, also where its unlimited face values look monotone."""
+    rng = np.random.default_rng(44)
+    for _ in range(2000):
+        q = rng.normal(size=9)
+        j = 4
+        q[j] = max(q[j - 1], q[j + 1]) + rng.uniform(0.01, 1.0)
+        q[j - 2] = 2 * q[j - 1] - q[j] + rng.uniform(0.01, 1.0)
+        if rng.random() < 0.5:
+            q = -q
+        L, R = O.recon_line(4, q)
+        assert R[j] == q[j] and L[j + 1] == q[j], (q, R[j], L[j + 1])
+
+
 def test_wenoz_symmetric_stencil_takes_the_linear_weights():
     """On a stencil symmetric about its centre, (a, b, c, b, a), the end
     indicators beta_0 and beta_2 coincide, so WENO-Z's tau_5 = |beta_0 - beta_2|
